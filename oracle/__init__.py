@@ -1,0 +1,122 @@
+"""CPU oracle for the escape-time path (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its
+``cpu_baseline`` leg and ``--impl reference`` arm) may import this package.
+The product library never imports, links or calls it; it shares no code with
+the CUDA sources (``paper_1611_03079_b300/csrc``) and the CUDA path shares none
+with it.  Seeded inputs come from ``paper_1611_03079_b300.workloads``, which
+holds no arithmetic of the method.
+
+Contents
+  render / colour / hist / escape_point : the C oracle (jl_oracle.c), escape
+      time for Z <- Z^2 + C (paper Sec. 2; Mandelbrot mode Sec. 3), colour
+      levels and the normalised escape-count histogram;
+  precision_for_view : the binary32 / binary64 selection rule for deep zooms
+      (Sec. 3 deep zoom; threshold 1000 binary32 ulps of the largest coordinate);
+  mlp (submodule) : the surrogate network in float64 numpy.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+        vp = ctypes.c_void_p
+        lib.jlo_render.argtypes = [d, d, d, d, d, d, i32, i32, i32, i32, i32, vp, i32]
+        lib.jlo_render.restype = ctypes.c_int
+        lib.jlo_escape_point.argtypes = [d, d, d, d, i32, i32]
+        lib.jlo_escape_point.restype = i32
+        lib.jlo_colour.argtypes = [vp, i64, i32, vp, vp]
+        lib.jlo_colour.restype = ctypes.c_int
+        lib.jlo_hist.argtypes = [vp, i64, i32, vp]
+        lib.jlo_hist.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+JULIA, MANDELBROT = 0, 1
+FP32, FP64 = 0, 1
+
+
+def render(c, rect, W, H, max_iter=100, mode=JULIA, precision=FP32, threads=None):
+    """Escape counts (uint16, shape (H, W), row 0 at y = ymin) of a W x H grid over
+    rect = (xmin, xmax, ymin, ymax).  Paper Sec. 2 (region covering, escape time,
+    limit 100) and Sec. 3 (Mandelbrot mode: Z_0 = 0, C = pixel)."""
+    lib = _load()
+    out = np.zeros((H, W), dtype=np.uint16)
+    cr, ci = (complex(c).real, complex(c).imag) if c is not None else (0.0, 0.0)
+    xmin, xmax, ymin, ymax = (float(v) for v in rect)
+    if threads is None:
+        threads = min(os.cpu_count() or 1, 64)
+    rc = lib.jlo_render(cr, ci, xmin, xmax, ymin, ymax, int(W), int(H), int(max_iter), int(mode),
+                        int(precision), out.ctypes.data, int(threads))
+    if rc != 0:
+        raise ValueError("jlo_render: invalid arguments")
+    return out
+
+
+def escape_point(z0, c, max_iter=100, precision=FP32):
+    """Escape count of one starting point z0 under Z <- Z^2 + c (Sec. 2), both
+    rounded once to the working precision."""
+    lib = _load()
+    z0, c = complex(z0), complex(c)
+    return int(lib.jlo_escape_point(z0.real, z0.imag, c.real, c.imag, int(max_iter), int(precision)))
+
+
+def colour(counts, max_iter, palette):
+    """RGBA8 image (shape counts.shape + (4,)) from counts and a 256 x 4 uint8
+    palette: entry 255 where count == max_iter, else (count * 255) // max_iter
+    (Sec. 2 colour levels)."""
+    lib = _load()
+    counts = np.ascontiguousarray(counts, dtype=np.uint16)
+    palette = np.ascontiguousarray(palette, dtype=np.uint8).reshape(256, 4)
+    out = np.zeros(counts.shape + (4,), dtype=np.uint8)
+    rc = lib.jlo_colour(counts.ctypes.data, counts.size, int(max_iter), palette.ctypes.data,
+                        out.ctypes.data)
+    if rc != 0:
+        raise ValueError("jlo_colour: invalid arguments")
+    return out
+
+
+def hist(counts, max_iter):
+    """Normalised escape-count histogram, max_iter + 1 float32 bins; bin b holds
+    #{count == b} / #pixels, the quotient rounded once from binary64."""
+    lib = _load()
+    counts = np.ascontiguousarray(counts, dtype=np.uint16)
+    out = np.zeros(int(max_iter) + 1, dtype=np.float32)
+    rc = lib.jlo_hist(counts.ctypes.data, counts.size, int(max_iter), out.ctypes.data)
+    if rc != 0:
+        raise ValueError("jlo_hist: invalid arguments")
+    return out
+
+
+def ulp32(v):
+    """Spacing of binary32 numbers at |v| (the ulp of the float nearest |v|)."""
+    f = np.float32(abs(v))
+    return float(np.spacing(f))
+
+
+def precision_for_view(rect, W, H, factor=1000.0):
+    """Precision rule for deep zooms (Sec. 3): binary64 when the smaller pixel
+    spacing is below `factor` binary32 ulps of the largest coordinate magnitude
+    of the view, else binary32.  Returns FP32 or FP64."""
+    xmin, xmax, ymin, ymax = (float(v) for v in rect)
+    dx = (xmax - xmin) / W
+    dy = (ymax - ymin) / H
+    m = max(abs(xmin), abs(xmax), abs(ymin), abs(ymax))
+    return FP64 if min(dx, dy) < factor * ulp32(m) else FP32
+
+
+def hist_l1(p, q):
+    """L1 distance sum_b |p_b - q_b| between histograms (last axis), float64."""
+    return np.abs(np.asarray(p, np.float64) - np.asarray(q, np.float64)).sum(axis=-1)

@@ -1,0 +1,29 @@
+"""Compile the C oracle (test infrastructure only) into oracle/libjl_oracle.so.
+
+Flags: -O2 -ffp-contract=off and no fast-math, so each C statement of the
+iteration is one correctly rounded IEEE operation (no fused multiply-add) and
+subnormals are kept.  Run as ``python oracle/build.py``.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "jl_oracle.c")
+LIB = os.path.join(HERE, "libjl_oracle.so")
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+          "-fno-finite-math-only", "-frounding-math", "-pthread"]
+
+
+def build(force: bool = False) -> str:
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", *CFLAGS, SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))
