@@ -1,0 +1,159 @@
+/*
+ * jl.h — C ABI of libjl.so, a B300 (sm_103a) escape-time fractal renderer and
+ * parameter-space surveyor.
+ *
+ * The method is the escape-time algorithm of "Fractal Art Generation using
+ * GPUs" (arXiv:1611.03079):
+ *   Sec. 2  region covering: pixel (i, j) of a W x H grid is mapped to a point
+ *           of a rectangle of the complex plane; Z_{n+1} = Z_n^2 + C is
+ *           iterated from that point up to an iteration limit (100 in the
+ *           paper) and the pixel is coloured by the number of iterations
+ *           taken to escape;
+ *   Sec. 3  Mandelbrot (parameter-plane) mode: Z_0 = 0 and C = pixel; deep
+ *           zooms that need extra precision; paths of C for animation.
+ *
+ * Conventions shared by every entry point
+ *   - Pixel centres.  dx = (xmax - xmin) / W and dy = (ymax - ymin) / H in
+ *     binary64; pixel (i, j) is x = xmin + (i + 0.5) dx, y = ymin + (j + 0.5) dy,
+ *     evaluated in binary64 without fused multiply-add and then rounded once
+ *     (round-to-nearest-even) to the working precision.  Row j = 0 is y = ymin;
+ *     images are row-major with pitch W.
+ *   - Iteration.  With (x, y) = Z and (cr, ci) = C in the working precision,
+ *     each step is: x2 = x*x; y2 = y*y; escape if x2 + y2 > 4; y = (x + x)*y + ci;
+ *     x = (x2 - y2) + cr; every operation rounded to nearest, none fused.
+ *     C given in binary64 is rounded once to the working precision.
+ *   - Count.  The number of updates made before the first failing test; 0 if
+ *     |Z_0|^2 > 4; max_iter if no test among n = 0 .. max_iter-1 fails.
+ *   - Colour (Sec. 2 colour levels).  count == max_iter -> palette entry 255;
+ *     otherwise entry (count * 255) / max_iter (unsigned integer division).
+ *     The palette is 256 RGBA8 entries (1024 bytes, R first).
+ *   - Histogram.  hist[b] = #{pixels with count b} / (W*H), b = 0 .. max_iter,
+ *     the quotient formed in binary64 and rounded once to binary32.
+ *   - Memory.  Unless stated otherwise, output pointers are caller-owned device
+ *     memory; the library allocates only stream-ordered scratch
+ *     (cudaMallocAsync on the caller's stream) and frees it on that stream.
+ *   - Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Calls are asynchronous on that stream unless stated otherwise.
+ *   - Errors.  Every function returns a jl_status.  No exception crosses the
+ *     ABI.  jl_last_error() returns a thread-local message for the last
+ *     failure on the calling thread.  Argument errors are detected on the host
+ *     before anything is launched; JL_ECUDA reports a failed CUDA call.
+ */
+#ifndef JL_H
+#define JL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JL_OK = 0,
+    JL_EINVAL = 1,       /* invalid argument (checked on the host) */
+    JL_ECUDA = 2,        /* a CUDA runtime call failed */
+    JL_ENOMEM = 3,       /* device or host allocation failed */
+    JL_ETIMEOUT = 4,     /* a launch exceeded its cycle budget and stopped early */
+    JL_EUNSUPPORTED = 5  /* no usable sm_103a device */
+} jl_status;
+
+typedef enum { JL_FP32 = 0, JL_FP64 = 1, JL_AUTO = 2 } jl_precision;
+typedef enum { JL_JULIA = 0, JL_MANDELBROT = 1 } jl_mode;
+typedef enum { JL_COUNT_NONE = 0, JL_COUNT_U8 = 1, JL_COUNT_U16 = 2 } jl_count_type;
+
+/* Axis-aligned rectangle of the complex plane (Sec. 2 region covering).
+ * Requires finite values with xmin < xmax and ymin < ymax. */
+typedef struct {
+    double xmin, xmax, ymin, ymax;
+} jl_rect;
+
+/* Thread-local text of the last error on the calling thread ("" if none). */
+const char *jl_last_error(void);
+
+/* Library version string. */
+const char *jl_version(void);
+
+/*
+ * Precision rule for deep zooms (Sec. 3: deep zooms need extra precision).
+ * Returns JL_FP64 when min(dx, dy) < 1000 * ulp32(m), m being the largest of
+ * |xmin|, |xmax|, |ymin|, |ymax| rounded to binary32 and ulp32(m) the gap from
+ * m to the next larger binary32 value; otherwise JL_FP32.  Returns -1 on an
+ * invalid rectangle or size.  Host-only, no GPU needed.
+ */
+int jl_select_precision(jl_rect rect, int32_t width, int32_t height);
+
+/*
+ * Render one frame (Sec. 2; Sec. 3 for JL_MANDELBROT and deep zoom).
+ *   cr, ci      C for JL_JULIA (ignored for JL_MANDELBROT), binary64
+ *   rect        view, see jl_rect
+ *   width, height  1 .. 65536 each, width*height < 2^31
+ *   max_iter    iteration limit, 1 .. 65535 (the paper uses 100)
+ *   precision   JL_FP32, JL_FP64, or JL_AUTO (jl_select_precision)
+ *   mode        JL_JULIA (Z_0 = pixel) or JL_MANDELBROT (Z_0 = 0, C = pixel)
+ *   count_type  JL_COUNT_U8 (requires max_iter <= 255), JL_COUNT_U16, or
+ *               JL_COUNT_NONE (counts must then be NULL)
+ *   counts      device, width*height elements of count_type, or NULL
+ *   rgba        device, width*height*4 bytes, or NULL
+ *   palette     HOST pointer to 1024 bytes (256 RGBA8 entries) or NULL for
+ *               the built-in palette (see jl_default_palette); read before
+ *               the call returns
+ *   hist        device, max_iter + 1 floats, or NULL; the buffer is used as
+ *               uint32 bin storage during the call and holds the normalised
+ *               histogram when the stream reaches the end of the call
+ *   stream      cudaStream_t
+ * At least one of counts, rgba, hist must be non-NULL.
+ */
+int jl_render(double cr, double ci, jl_rect rect, int32_t width, int32_t height, int32_t max_iter,
+              int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
+              const uint8_t *palette, float *hist, void *stream);
+
+/*
+ * Same as jl_render but every output pointer is HOST memory (pinned or
+ * pageable).  The frame is rendered into stream-ordered device scratch and
+ * copied back; the call returns after the copies complete (it synchronises
+ * `stream`).  Used for end-to-end measurements that include the transfers.
+ */
+int jl_render_to_host(double cr, double ci, jl_rect rect, int32_t width, int32_t height,
+                      int32_t max_iter, int32_t precision, int32_t mode, int32_t count_type,
+                      void *counts_host, uint8_t *rgba_host, const uint8_t *palette,
+                      float *hist_host, void *stream);
+
+/*
+ * jl_render with an explicit kernel variant (used by the autotuner and the
+ * tests): ppt independent pixels per thread, unroll steps between service
+ * points, threads per CTA (multiple of 32, 32..256), ctas_per_sm (0 = the
+ * occupancy maximum).  Unsupported (ppt, unroll) pairs return JL_EINVAL;
+ * jl_variant_list() enumerates the supported ones.
+ */
+int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t height, int32_t max_iter,
+                      int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
+                      const uint8_t *palette, float *hist, int32_t ppt, int32_t unroll, int32_t threads,
+                      int32_t ctas_per_sm, void *stream);
+
+/*
+ * Writes up to `cap` supported (ppt, unroll) pairs for `precision` into
+ * `pairs` (2 ints each) and returns how many exist (may exceed cap), or -1
+ * for an invalid precision.
+ */
+int jl_variant_list(int32_t precision, int32_t *pairs, int32_t cap);
+
+/*
+ * Issue-rate probe of the binary32 (JL_FP32) or binary64 (JL_FP64) pipe:
+ * runs 8 independent multiply/add chains per thread on every SM (separate
+ * FMUL and FADD, no FMA) and returns the achieved lane operations per second
+ * in *lane_ops_per_s (and the kernel time in *seconds if non-NULL).  This is
+ * the denominator of the escape kernels' ALU roofline.  Synchronises
+ * `stream`.
+ */
+int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_per_s, double *seconds, void *stream);
+
+/* Writes the built-in 256-entry RGBA8 palette (1024 bytes) to `out` (host).
+ * Entry 255 (never-escaped points) is opaque black. */
+int jl_default_palette(uint8_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JL_H */

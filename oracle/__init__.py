@@ -34,6 +34,10 @@ def _load():
         vp = ctypes.c_void_p
         lib.jlo_render.argtypes = [d, d, d, d, d, d, i32, i32, i32, i32, i32, vp, i32]
         lib.jlo_render.restype = ctypes.c_int
+        lib.jlo_render_rows.argtypes = [d, d, d, d, d, d, i32, i32, i32, i32, i32, i32, i32, vp]
+        lib.jlo_render_rows.restype = ctypes.c_int
+        lib.jlo_render_strided.argtypes = [d, d, d, d, d, d, i32, i32, i32, i32, i32, i32, i32, i32, vp, i32]
+        lib.jlo_render_strided.restype = ctypes.c_int
         lib.jlo_escape_point.argtypes = [d, d, d, d, i32, i32]
         lib.jlo_escape_point.restype = i32
         lib.jlo_colour.argtypes = [vp, i64, i32, vp, vp]
@@ -62,6 +66,41 @@ def render(c, rect, W, H, max_iter=100, mode=JULIA, precision=FP32, threads=None
                         int(precision), out.ctypes.data, int(threads))
     if rc != 0:
         raise ValueError("jlo_render: invalid arguments")
+    return out
+
+
+def render_rows(c, rect, W, H, rows, max_iter=100, mode=JULIA, precision=FP32):
+    """Escape counts of the listed rows of the W x H frame (uint16, shape
+    (len(rows), W)); same arithmetic as render()."""
+    lib = _load()
+    cr, ci = (complex(c).real, complex(c).imag) if c is not None else (0.0, 0.0)
+    xmin, xmax, ymin, ymax = (float(v) for v in rect)
+    out = np.zeros((len(rows), W), dtype=np.uint16)
+    for k, j in enumerate(rows):
+        row = np.zeros((1, W), dtype=np.uint16)
+        rc = lib.jlo_render_rows(cr, ci, xmin, xmax, ymin, ymax, int(W), int(H), int(max_iter), int(mode),
+                                 int(precision), int(j), int(j) + 1, row.ctypes.data)
+        if rc != 0:
+            raise ValueError("jlo_render_rows: invalid arguments")
+        out[k] = row[0]
+    return out
+
+
+def render_strided(c, rect, W, H, row_start, row_stride, n_rows, max_iter=100, mode=JULIA,
+                   precision=FP32, threads=None):
+    """Rows row_start + k*row_stride (k < n_rows) of the W x H frame, threaded;
+    uint16 (n_rows, W).  Same arithmetic as render()."""
+    lib = _load()
+    cr, ci = (complex(c).real, complex(c).imag) if c is not None else (0.0, 0.0)
+    xmin, xmax, ymin, ymax = (float(v) for v in rect)
+    if threads is None:
+        threads = min(os.cpu_count() or 1, 64)
+    out = np.zeros((n_rows, W), dtype=np.uint16)
+    rc = lib.jlo_render_strided(cr, ci, xmin, xmax, ymin, ymax, int(W), int(H), int(max_iter), int(mode),
+                                int(precision), int(row_start), int(row_stride), int(n_rows), out.ctypes.data,
+                                int(threads))
+    if rc != 0:
+        raise ValueError("jlo_render_strided: invalid arguments")
     return out
 
 

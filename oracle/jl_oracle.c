@@ -26,6 +26,7 @@
  */
 #include <math.h>
 #include <pthread.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -73,6 +74,7 @@ typedef struct {
     double cr, ci, xmin, xmax, ymin, ymax;
     int32_t W, H, max_iter, mode, precision;
     int32_t row0, row1;
+    int32_t out_row_base;  /* row that maps to counts[0] */
     uint16_t *counts;
 } job_t;
 
@@ -98,7 +100,7 @@ static void render_rows(const job_t *jb)
                 else
                     n = escape_f64(0.0, 0.0, xd, yd, jb->max_iter);
             }
-            jb->counts[(size_t)j * (size_t)jb->W + (size_t)i] = (uint16_t)n;
+            jb->counts[(size_t)(j - jb->out_row_base) * (size_t)jb->W + (size_t)i] = (uint16_t)n;
         }
     }
 }
@@ -146,6 +148,7 @@ int jlo_render(double cr, double ci, double xmin, double xmax, double ymin, doub
         jb->precision = precision;
         jb->row0 = (int32_t)(((int64_t)H * k) / nthreads);
         jb->row1 = (int32_t)(((int64_t)H * (k + 1)) / nthreads);
+        jb->out_row_base = 0;
         jb->counts = counts;
     }
     if (nthreads == 1) {
@@ -156,6 +159,96 @@ int jlo_render(double cr, double ci, double xmin, double xmax, double ymin, doub
         for (int32_t k = 0; k < nthreads; ++k)
             pthread_join(th[k], NULL);
     }
+    free(jobs);
+    free(th);
+    return JLO_OK;
+}
+
+/*
+ * Rows row0 .. row1-1 of the same W x H frame (single thread); counts holds
+ * (row1 - row0) * W values.  Used to check sampled rows of large frames.
+ */
+int jlo_render_rows(double cr, double ci, double xmin, double xmax, double ymin, double ymax,
+                    int32_t W, int32_t H, int32_t max_iter, int32_t mode, int32_t precision,
+                    int32_t row0, int32_t row1, uint16_t *counts)
+{
+    if (W < 1 || H < 1 || max_iter < 1 || max_iter > 65535 || !counts)
+        return JLO_EINVAL;
+    if (row0 < 0 || row1 > H || row0 >= row1 || (mode != 0 && mode != 1) || (precision != 0 && precision != 1))
+        return JLO_EINVAL;
+    job_t jb;
+    jb.cr = cr; jb.ci = ci;
+    jb.xmin = xmin; jb.xmax = xmax; jb.ymin = ymin; jb.ymax = ymax;
+    jb.W = W; jb.H = H; jb.max_iter = max_iter; jb.mode = mode; jb.precision = precision;
+    jb.row0 = row0; jb.row1 = row1;
+    jb.out_row_base = row0;
+    jb.counts = counts;
+    render_rows(&jb);
+    return JLO_OK;
+}
+
+typedef struct {
+    job_t base;
+    int32_t row_start, row_stride, n_rows, first, step;
+} strided_t;
+
+/* Thread body: sample rows k = first, first + step, ... < n_rows. */
+static void *strided_worker(void *arg)
+{
+    const strided_t *st = (const strided_t *)arg;
+    for (int32_t k = st->first; k < st->n_rows; k += st->step) {
+        job_t jb = st->base;
+        jb.row0 = st->row_start + k * st->row_stride;
+        jb.row1 = jb.row0 + 1;
+        jb.out_row_base = jb.row0 - k;  /* sample row k lands at counts[k * W] */
+        render_rows(&jb);
+    }
+    return NULL;
+}
+
+/*
+ * Rows row_start + k*row_stride, k = 0 .. n_rows-1, of a W x H frame, split
+ * over nthreads POSIX threads (rows interleaved); counts holds n_rows * W
+ * values.  Used for the bounded CPU timing sample.
+ */
+int jlo_render_strided(double cr, double ci, double xmin, double xmax, double ymin, double ymax,
+                       int32_t W, int32_t H, int32_t max_iter, int32_t mode, int32_t precision,
+                       int32_t row_start, int32_t row_stride, int32_t n_rows, uint16_t *counts,
+                       int32_t nthreads)
+{
+    if (W < 1 || H < 1 || max_iter < 1 || max_iter > 65535 || !counts || n_rows < 1 || row_stride < 1)
+        return JLO_EINVAL;
+    if (row_start < 0 || (int64_t)row_start + (int64_t)(n_rows - 1) * row_stride >= H)
+        return JLO_EINVAL;
+    if ((mode != 0 && mode != 1) || (precision != 0 && precision != 1))
+        return JLO_EINVAL;
+    if (nthreads < 1)
+        nthreads = 1;
+    if (nthreads > n_rows)
+        nthreads = n_rows;
+    strided_t *jobs = (strided_t *)calloc((size_t)nthreads, sizeof(strided_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) {
+        free(jobs);
+        free(th);
+        return JLO_EINVAL;
+    }
+    for (int32_t t = 0; t < nthreads; ++t) {
+        job_t *jb = &jobs[t].base;
+        jb->cr = cr; jb->ci = ci;
+        jb->xmin = xmin; jb->xmax = xmax; jb->ymin = ymin; jb->ymax = ymax;
+        jb->W = W; jb->H = H; jb->max_iter = max_iter; jb->mode = mode; jb->precision = precision;
+        jb->counts = counts;
+        jobs[t].row_start = row_start;
+        jobs[t].row_stride = row_stride;
+        jobs[t].n_rows = n_rows;
+        jobs[t].first = t;
+        jobs[t].step = nthreads;
+    }
+    for (int32_t t = 0; t < nthreads; ++t)
+        pthread_create(&th[t], NULL, strided_worker, &jobs[t]);
+    for (int32_t t = 0; t < nthreads; ++t)
+        pthread_join(th[t], NULL);
     free(jobs);
     free(th);
     return JLO_OK;

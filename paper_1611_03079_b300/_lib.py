@@ -1,0 +1,71 @@
+"""ctypes loader for libjl.so (argument marshalling only).
+
+The shared library is built in-tree by ``paper_1611_03079_b300.build``.  If it
+is missing, loading raises ``RuntimeError`` -- there is no fallback path.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjl.so")
+
+JL_OK, JL_EINVAL, JL_ECUDA, JL_ENOMEM, JL_ETIMEOUT, JL_EUNSUPPORTED = range(6)
+JL_FP32, JL_FP64, JL_AUTO = 0, 1, 2
+JL_JULIA, JL_MANDELBROT = 0, 1
+JL_COUNT_NONE, JL_COUNT_U8, JL_COUNT_U16 = 0, 1, 2
+
+STATUS_NAMES = {0: "JL_OK", 1: "JL_EINVAL", 2: "JL_ECUDA", 3: "JL_ENOMEM", 4: "JL_ETIMEOUT",
+                5: "JL_EUNSUPPORTED"}
+
+
+class JLError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+class Rect(ctypes.Structure):
+    _fields_ = [("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("ymin", ctypes.c_double), ("ymax", ctypes.c_double)]
+
+
+_lib = None
+
+# Every entry point declared in include/*.h, with its ctypes signature.
+_d, _i32, _vp, _u64 = ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64
+SIGNATURES = {
+    "jl_last_error": (ctypes.c_char_p, []),
+    "jl_version": (ctypes.c_char_p, []),
+    "jl_select_precision": (ctypes.c_int, [Rect, _i32, _i32]),
+    "jl_default_palette": (ctypes.c_int, [_vp]),
+    "jl_render": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "jl_render_variant": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
+                                         _vp, _i32, _i32, _i32, _i32, _vp]),
+    "jl_variant_list": (ctypes.c_int, [_i32, _vp, _i32]),
+    "jl_probe_peak": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp]),
+    "jl_render_to_host": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
+                                         _vp, _vp]),
+}
+
+
+def lib():
+    """Load libjl.so once; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libjl.so not found at %s; run python -m paper_1611_03079_b300.build"
+                               % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != JL_OK:
+        msg = lib().jl_last_error()
+        raise JLError(rc, msg.decode() if msg else "")
+    return rc

@@ -1,0 +1,603 @@
+// Escape-time kernels for sm_103a (paper Sec. 2: region covering and the
+// escape-time iteration of Z <- Z^2 + C; Sec. 3: Mandelbrot mode, deep zoom).
+//
+// Design (B300-first, not the paper's one-thread-per-pixel kernel):
+//  * Coordinates.  x_i and y_j depend on one index each, so they are computed
+//    once per frame into tables (W + H values) by `coords_kernel`, in binary64
+//    without FMA, then rounded once to the working type.  This keeps binary64
+//    work (a narrow pipe on this part) out of the per-pixel path.
+//  * Persistent warps with lane refill.  Each warp pulls row segments
+//    ("chunks") from a global atomic counter and keeps PPT independent pixels
+//    per lane in flight (ILP).  A lane whose pixel finishes stores its result
+//    and takes the next pixel of the warp's chunk at the next service point,
+//    so escaped lanes do not idle while their neighbours keep iterating.
+//  * Blocks of U steps.  Between service points every slot runs U steps with
+//    no branch.  The escape test stays exact:
+//      - binary32: the value r_u = x2 + y2 of every step is kept in registers;
+//        because escape is monotone for the pixels that take this path (see
+//        `monotone_*` below) the slot escaped in the block iff r_{U-1} fails,
+//        and the count is n + #{u : r_u <= 4};
+//      - binary64: r is not formed in binary64.  A binary32 estimate built
+//        from the high words of x2 and y2 decides the test whenever it is
+//        outside a +-2^-16 relative band around 4; a block in which any live
+//        slot fell inside the band is replayed with exact binary64 tests.
+//    Pixels for which monotonicity is not proven (|C| within 2^-12 of 2) and
+//    tails shorter than U steps are iterated one exact step at a time.
+//  * Every arithmetic operation is an explicit round-to-nearest intrinsic
+//    (__fmul_rn, __fadd_rn, __dmul_rn, ...), which the compiler never
+//    contracts into an FMA; the library is also built with -fmad=false.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jl_internal.h"
+
+namespace jl {
+
+static constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Region covering (Sec. 2): coordinate tables.
+// Block b handles frame b / 2, axis b % 2 (0: x over W, 1: y over H).
+// ---------------------------------------------------------------------------
+struct CoordArgs {
+    const Frame *frames;
+    int32_t n_frames;
+    Frame single;
+};
+
+__global__ void coords_kernel(const __grid_constant__ CoordArgs a)
+{
+    const Frame *frames = a.frames ? a.frames : &a.single;
+    const int f = blockIdx.x >> 1;
+    const int axis = blockIdx.x & 1;
+    if (f >= a.n_frames)
+        return;
+    const Frame &F = frames[f];
+    const int n = axis ? F.H : F.W;
+    const double lo = axis ? F.ymin : F.xmin;
+    const double d = axis ? F.dy : F.dx;
+    void *out = const_cast<void *>(axis ? F.ys : F.xs);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        // lo + (i + 0.5) * d, binary64, no contraction.
+        double t = __dadd_rn((double)i, 0.5);
+        double v = __dadd_rn(lo, __dmul_rn(t, d));
+        if (F.precision == JL_FP64)
+            static_cast<double *>(out)[i] = v;
+        else
+            static_cast<float *>(out)[i] = __double2float_rn(v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Histogram finalisation: bins (uint32, in place) -> binary32 fractions.
+// ---------------------------------------------------------------------------
+struct HistArgs {
+    const Frame *frames;
+    int32_t n_frames;
+    Frame single;
+};
+
+__global__ void hist_finalize_kernel(const __grid_constant__ HistArgs a)
+{
+    const Frame *frames = a.frames ? a.frames : &a.single;
+    for (int f = blockIdx.x; f < a.n_frames; f += gridDim.x) {
+        const Frame &F = frames[f];
+        if (!F.hist_bins)
+            continue;
+        const double npix = (double)F.W * (double)F.H;
+        for (int b = threadIdx.x; b <= F.max_iter; b += blockDim.x) {
+            uint32_t c = F.hist_bins[b];
+            float v = __double2float_rn(__ddiv_rn((double)c, npix));
+            reinterpret_cast<float *>(F.hist_bins)[b] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exact single-step iteration (used for tails, unproven-monotone pixels and
+// nothing else).  Returns the count given that tests 0..n0-1 have passed and
+// (x, y) is Z_{n0}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int exact_from(float x, float y, float cr, float ci, int n0, int max_iter)
+{
+    for (int n = n0; n < max_iter; ++n) {
+        float x2 = __fmul_rn(x, x);
+        float y2 = __fmul_rn(y, y);
+        if (__fadd_rn(x2, y2) > 4.0f)
+            return n;
+        float t = __fadd_rn(x, x);
+        t = __fmul_rn(t, y);
+        y = __fadd_rn(t, ci);
+        x = __fadd_rn(__fsub_rn(x2, y2), cr);
+    }
+    return max_iter;
+}
+
+__device__ __forceinline__ int exact_from(double x, double y, double cr, double ci, int n0, int max_iter)
+{
+    for (int n = n0; n < max_iter; ++n) {
+        double x2 = __dmul_rn(x, x);
+        double y2 = __dmul_rn(y, y);
+        if (__dadd_rn(x2, y2) > 4.0)
+            return n;
+        double t = __dadd_rn(x, x);
+        t = __dmul_rn(t, y);
+        y = __dadd_rn(t, ci);
+        x = __dadd_rn(__dsub_rn(x2, y2), cr);
+    }
+    return max_iter;
+}
+
+// Monotone escape.  If |C| <= 2 - 2^-12 then, in binary32 or binary64
+// arithmetic with round-to-nearest, a failed test (x2 + y2 > 4) at step m
+// implies |Z_{m+1}| >= 2 + 2^-13 and the modulus keeps growing until it
+// overflows to inf/NaN, so every later test also fails (NaN fails "<= 4").
+// For Mandelbrot pixels with |C| >= 2 + 2^-12, Z_1 = C fails the test and the
+// same growth holds from there on.  Pixels with |C| in between are iterated
+// exactly one step at a time.  The band is tested here with margin so that
+// rounding in |C|^2 cannot hide a pixel that belongs to it.
+__device__ __forceinline__ bool in_unsafe_band(double cr, double ci)
+{
+    double m = __dadd_rn(__dmul_rn(cr, cr), __dmul_rn(ci, ci));
+    return m > 3.99 && m < 4.01;
+}
+__device__ __forceinline__ bool in_unsafe_band(float cr, float ci)
+{
+    float m = __fadd_rn(__fmul_rn(cr, cr), __fmul_rn(ci, ci));
+    return m > 3.99f && m < 4.01f;
+}
+
+// Binary32 estimate of a non-negative binary64 value from its high word,
+// truncated (never above the true value, relative error < 2^-20); 0 below
+// 2^-126, +inf at or above 2^128.
+__device__ __forceinline__ float hi_estimate(double v)
+{
+    int h = __double2hiint(v) & 0x7fffffff;
+    h -= 0x38000000;                 // rebias exponent 1023 -> 127
+    h = max(h, 0);
+    h = min(h, 0x0ff00000);          // exponent 255 -> +inf
+    return __int_as_float(h << 3);
+}
+
+// ---------------------------------------------------------------------------
+// The persistent escape kernel.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct WorkT;
+template <>
+struct WorkT<float> {
+    static __device__ __forceinline__ float from_double(double v) { return __double2float_rn(v); }
+};
+template <>
+struct WorkT<double> {
+    static __device__ __forceinline__ double from_double(double v) { return v; }
+};
+
+// Integer quotient (n * 255) / d for n <= d <= 65535 via a 40-bit reciprocal:
+// m = floor(2^40 / d) + 1 gives floor(n*255*m / 2^40) == floor(n*255 / d)
+// because the excess n*255*(m - 2^40/d)/2^40 < 2^-16 < 1/d.
+__device__ __forceinline__ uint32_t colour_index(uint32_t count, uint32_t max_iter, uint64_t magic)
+{
+    if (count >= max_iter)
+        return 255u;
+    uint64_t p = (uint64_t)(count * 255u) * magic;
+    return (uint32_t)(p >> 40);
+}
+
+template <typename T, int PPT, int U>
+__global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ EscapeArgs a)
+{
+    extern __shared__ uint32_t smem[];
+    uint32_t *pal = smem;
+    uint32_t *hbins = smem + 256;
+
+    const Frame *frames = a.frames ? a.frames : &a.single;
+    const int lane = threadIdx.x & 31;
+    const unsigned lane_bit = 1u << lane;
+    const unsigned lt_mask = lane_bit - 1u;
+
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        pal[t] = a.palette[t];
+    const int nb = a.hist_smem ? frames[0].max_iter + 1 : 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x)
+        hbins[t] = 0;
+    __syncthreads();
+
+    const long long t_start = clock64();
+
+    // ---- warp work queue (warp-uniform state) ----
+    int q_f = 0, q_row = 0, q_pos = 0, q_end = 0, q_W = 0, q_max = 0, q_mode = 0, q_safe = 1;
+    T q_cr = T(0), q_ci = T(0), q_y = T(0);
+    const T *q_xs = nullptr;
+    bool q_done = false;
+    unsigned long long next_c = 0;  // valid in lane 0: prefetched chunk id
+    if (lane == 0)
+        next_c = atomicAdd(a.chunk_counter, 1ull);
+
+    auto advance = [&]() -> bool {
+        if (q_done)
+            return false;
+        unsigned long long c = __shfl_sync(FULL, next_c, 0);
+        bool over_budget = false;
+        if (a.cycle_budget > 0 && (clock64() - t_start) > a.cycle_budget)
+            over_budget = true;
+        over_budget = __any_sync(FULL, over_budget);
+        if ((long long)c >= a.total_chunks || over_budget) {
+            if (over_budget && lane == 0 && a.status && (long long)c < a.total_chunks)
+                atomicExch(a.status, (int)JL_ETIMEOUT);
+            q_done = true;
+            return false;
+        }
+        if (lane == 0)
+            next_c = atomicAdd(a.chunk_counter, 1ull);
+        // frame containing chunk c: largest f with chunk_begin <= c
+        int lo = 0, hi = a.n_frames - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (frames[mid].chunk_begin <= (long long)c)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const Frame &F = frames[lo];
+        long long local = (long long)c - F.chunk_begin;
+        int row = (int)(local / F.chunks_per_row);
+        int seg = (int)(local - (long long)row * F.chunks_per_row);
+        q_f = lo;
+        q_row = row;
+        q_pos = seg * F.chunk_len;
+        q_end = min(q_pos + F.chunk_len, F.W);
+        q_W = F.W;
+        q_max = F.max_iter;
+        q_mode = F.mode;
+        q_safe = F.safe;
+        q_cr = WorkT<T>::from_double(F.cr);
+        q_ci = WorkT<T>::from_double(F.ci);
+        q_xs = static_cast<const T *>(F.xs);
+        q_y = static_cast<const T *>(F.ys)[row];
+        return true;
+    };
+
+    // ---- slot state ----
+    // rem >= 0: live, rem = max_iter - n (tests still allowed);
+    // rem < 0 : finished early, count = -1 - rem;  fid < 0: empty.
+    T x[PPT], y[PPT], cr[PPT], ci[PPT];
+    int rem[PPT], fid[PPT], pix[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        x[k] = y[k] = cr[k] = ci[k] = T(0);
+        rem[k] = 0x3fffffff;
+        fid[k] = -1;
+        pix[k] = 0;
+    }
+
+    auto finish = [&](int f, int p, int count) {
+        const Frame &F = frames[f];
+        if (F.counts) {
+            if (F.count_type == JL_COUNT_U8)
+                F.counts[p] = (uint8_t)count;
+            else
+                reinterpret_cast<uint16_t *>(F.counts)[p] = (uint16_t)count;
+        }
+        if (F.rgba) {
+            F.rgba[p] = pal[colour_index((uint32_t)count, (uint32_t)F.max_iter, F.colour_magic)];
+        }
+        if (F.hist_bins) {
+            if (a.hist_smem)
+                atomicAdd(&hbins[count], 1u);
+            else
+                atomicAdd(&F.hist_bins[count], 1u);
+        }
+    };
+
+    // Assign new pixels to slot k for the lanes in `want`.
+    auto refill = [&](int k, unsigned want) {
+        unsigned remaining = want;
+        while (remaining) {
+            if (q_pos >= q_end) {
+                if (!advance())
+                    break;
+                continue;
+            }
+            const int avail = q_end - q_pos;
+            const int take = min(avail, __popc(remaining));
+            const bool mine = (remaining & lane_bit) != 0;
+            const int rank = __popc(remaining & lt_mask);
+            const bool got = mine && rank < take;
+            if (got) {
+                const int i = q_pos + rank;
+                const T xv = q_xs[i];
+                fid[k] = q_f;
+                pix[k] = q_row * q_W + i;
+                rem[k] = q_max;
+                bool unsafe;
+                if (q_mode == JL_JULIA) {
+                    x[k] = xv;
+                    y[k] = q_y;
+                    cr[k] = q_cr;
+                    ci[k] = q_ci;
+                    unsafe = !q_safe;
+                } else {
+                    x[k] = T(0);
+                    y[k] = T(0);
+                    cr[k] = xv;
+                    ci[k] = q_y;
+                    unsafe = in_unsafe_band(xv, q_y);
+                }
+                if (unsafe || q_max < U) {
+                    const int c = exact_from(x[k], y[k], cr[k], ci[k], 0, q_max);
+                    rem[k] = -1 - c;
+                }
+            }
+            remaining &= ~__ballot_sync(FULL, got);
+            q_pos += take;
+        }
+    };
+
+    // Initial fill.
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+        refill(k, FULL);
+
+    // Per-slot "needs service" flags computed after each block.
+    bool need[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+        need[k] = false;
+
+    float rk[PPT][U];   // binary32 path: r_u of the last block
+    int cnt[PPT];       // binary64 path: passed tests in the last block
+
+    while (true) {
+        // ---------------- service ----------------
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (__any_sync(FULL, need[k])) {
+                if (need[k]) {
+                    int count;
+                    const int f = fid[k];
+                    const int mi = frames[f].max_iter;
+                    if (rem[k] < 0) {
+                        count = -1 - rem[k];
+                    } else if (rem[k] < U) {
+                        // tail shorter than a block: exact steps from n = mi - rem
+                        count = exact_from(x[k], y[k], cr[k], ci[k], mi - rem[k], mi);
+                    } else {
+                        // escaped inside the last block (tests n .. n+U-1, n = mi - rem)
+                        int passed;
+                        if constexpr (sizeof(T) == 4) {
+                            passed = 0;
+#pragma unroll
+                            for (int u = 0; u < U; ++u)
+                                passed += (rk[k][u] <= 4.0f) ? 1 : 0;
+                        } else {
+                            passed = cnt[k];
+                        }
+                        count = mi - rem[k] + passed;
+                    }
+                    finish(f, pix[k], count);
+                    fid[k] = -1;
+                    rem[k] = 0x3fffffff;
+                    x[k] = y[k] = cr[k] = ci[k] = T(0);
+                }
+                const unsigned want = __ballot_sync(FULL, need[k]);
+                if (!q_done)
+                    refill(k, want);
+            }
+        }
+
+        bool live = false;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)
+            live |= (fid[k] >= 0);
+        if (!__any_sync(FULL, live))
+            break;
+
+        // ---------------- block of U steps ----------------
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    float xx = (float)x[k], yy = (float)y[k];
+                    float x2 = __fmul_rn(xx, xx);
+                    float y2 = __fmul_rn(yy, yy);
+                    rk[k][u] = __fadd_rn(x2, y2);
+                    float t = __fadd_rn(xx, xx);
+                    t = __fmul_rn(t, yy);
+                    y[k] = (T)__fadd_rn(t, (float)ci[k]);
+                    x[k] = (T)__fadd_rn(__fsub_rn(x2, y2), (float)cr[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const bool live_k = rem[k] >= 0 && fid[k] >= 0;
+                const bool esc = !(rk[k][U - 1] <= 4.0f);
+                if (live_k && !esc)
+                    rem[k] -= U;
+                need[k] = (fid[k] >= 0) && (!live_k || esc || rem[k] < U);
+            }
+        } else {
+            double sx[PPT], sy[PPT];
+            bool amb = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                sx[k] = (double)x[k];
+                sy[k] = (double)y[k];
+                cnt[k] = 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    double xx = (double)x[k], yy = (double)y[k];
+                    double x2 = __dmul_rn(xx, xx);
+                    double y2 = __dmul_rn(yy, yy);
+                    float r32 = __fadd_rn(hi_estimate(x2), hi_estimate(y2));
+                    cnt[k] += (r32 < 3.9999847412109375f) ? 1 : 0;
+                    amb |= (rem[k] >= 0) & (r32 >= 3.9999847412109375f) & (r32 <= 4.0000152587890625f);
+                    double t = __dadd_rn(xx, xx);
+                    t = __dmul_rn(t, yy);
+                    y[k] = (T)__dadd_rn(t, (double)ci[k]);
+                    x[k] = (T)__dadd_rn(__dsub_rn(x2, y2), (double)cr[k]);
+                }
+            }
+            if (__any_sync(FULL, amb)) {
+                // replay the block with exact binary64 tests
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    x[k] = (T)sx[k];
+                    y[k] = (T)sy[k];
+                    cnt[k] = 0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        double xx = (double)x[k], yy = (double)y[k];
+                        double x2 = __dmul_rn(xx, xx);
+                        double y2 = __dmul_rn(yy, yy);
+                        cnt[k] += (__dadd_rn(x2, y2) <= 4.0) ? 1 : 0;
+                        double t = __dadd_rn(xx, xx);
+                        t = __dmul_rn(t, yy);
+                        y[k] = (T)__dadd_rn(t, (double)ci[k]);
+                        x[k] = (T)__dadd_rn(__dsub_rn(x2, y2), (double)cr[k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const bool live_k = rem[k] >= 0 && fid[k] >= 0;
+                const bool esc = cnt[k] < U;
+                if (live_k && !esc)
+                    rem[k] -= U;
+                need[k] = (fid[k] >= 0) && (!live_k || esc || rem[k] < U);
+            }
+        }
+    }
+
+    if (nb) {
+        __syncthreads();
+        uint32_t *gb = frames[0].hist_bins;
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            uint32_t v = hbins[t];
+            if (v)
+                atomicAdd(&gb[t], v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+int device_sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_coords(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st)
+{
+    CoordArgs a;
+    a.frames = frames_dev;
+    a.n_frames = n;
+    if (single)
+        a.single = *single;
+    coords_kernel<<<2 * n, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hist_finalize(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st)
+{
+    HistArgs a;
+    a.frames = frames_dev;
+    a.n_frames = n;
+    if (single)
+        a.single = *single;
+    int grid = n < 4096 ? n : 4096;
+    hist_finalize_kernel<<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int PPT, int U>
+static cudaError_t launch_one(const EscapeArgs &a, const Variant &v, int num_sms, size_t smem, cudaStream_t st)
+{
+    auto kern = escape_kernel<T, PPT, U>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    int per_sm = v.ctas_per_sm;
+    if (per_sm <= 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, v.threads, smem);
+        if (e != cudaSuccess)
+            return e;
+        if (per_sm < 1)
+            per_sm = 1;
+    }
+    long long grid = (long long)num_sms * per_sm;
+    // never more warps than chunks
+    long long max_ctas = (a.total_chunks + (v.threads / 32) - 1) / (v.threads / 32);
+    if (grid > max_ctas)
+        grid = max_ctas;
+    if (grid < 1)
+        grid = 1;
+    kern<<<(unsigned)grid, v.threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define JL_VARIANTS_F32(X) X(float, 1, 8) X(float, 2, 8) X(float, 4, 8) X(float, 2, 16) X(float, 4, 4) X(float, 8, 4)
+#define JL_VARIANTS_F64(X) X(double, 1, 4) X(double, 2, 4) X(double, 2, 8) X(double, 4, 4) X(double, 1, 8)
+
+bool variant_supported(int precision, int ppt, int unroll)
+{
+#define JL_CHECK(T, P, UU) \
+    if (((sizeof(T) == 8) == (precision == JL_FP64)) && ppt == P && unroll == UU) return true;
+    JL_VARIANTS_F32(JL_CHECK)
+    JL_VARIANTS_F64(JL_CHECK)
+#undef JL_CHECK
+    return false;
+}
+
+int variant_list(int precision, int32_t *pairs, int cap)
+{
+    int n = 0;
+#define JL_LIST(T, P, UU)                                            \
+    if ((sizeof(T) == 8) == (precision == JL_FP64)) {                \
+        if (pairs && n < cap) { pairs[2 * n] = P; pairs[2 * n + 1] = UU; } \
+        ++n;                                                         \
+    }
+    JL_VARIANTS_F32(JL_LIST)
+    JL_VARIANTS_F64(JL_LIST)
+#undef JL_LIST
+    return n;
+}
+
+cudaError_t launch_escape(const EscapeArgs &a, int precision, const Variant &v, int num_sms, cudaStream_t st)
+{
+    size_t smem = 256 * sizeof(uint32_t);
+    if (a.hist_smem)
+        smem += (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
+#define JL_DISPATCH(T, P, UU)                                                                 \
+    if (((sizeof(T) == 8) == (precision == JL_FP64)) && v.ppt == P && v.unroll == UU)         \
+        return launch_one<T, P, UU>(a, v, num_sms, smem, st);
+    JL_VARIANTS_F32(JL_DISPATCH)
+    JL_VARIANTS_F64(JL_DISPATCH)
+#undef JL_DISPATCH
+    return cudaErrorInvalidValue;
+}
+
+Variant default_variant(int precision, int max_iter)
+{
+    (void)max_iter;
+    if (precision == JL_FP64)
+        return Variant{2, 4, 128, 0};
+    return Variant{4, 8, 256, 0};
+}
+
+}  // namespace jl

@@ -1,0 +1,74 @@
+// Internal declarations shared by the libjl.so translation units (not part of
+// the public ABI; see include/jl.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/jl.h"
+
+namespace jl {
+
+// Device-side description of one frame.  The host fills it; kernels read it
+// from a table in global memory (batches) or from the launch parameters.
+struct Frame {
+    double cr, ci;                 // C for Julia frames (binary64, rounded in-kernel)
+    double xmin, ymin, dx, dy;     // region covering in binary64 (Sec. 2)
+    int32_t W, H, max_iter, mode;  // mode: JL_JULIA / JL_MANDELBROT
+    int32_t count_type;            // JL_COUNT_*
+    int32_t chunks_per_row;        // ceil(W / chunk_len)
+    int32_t chunk_len;             // pixels per work chunk (one row segment)
+    int32_t safe;                  // 1: escape is monotone for every pixel (see escape kernels)
+    int32_t precision;             // JL_FP32 / JL_FP64 (working type of xs/ys)
+    int32_t pad0;
+    uint64_t colour_magic;         // floor(2^40 / max_iter) + 1 (exact count*255/max_iter)
+    int64_t chunk_begin;           // index of this frame's first chunk in the launch
+    uint8_t *counts;               // device or NULL
+    uint32_t *rgba;                // device or NULL (one RGBA8 word per pixel)
+    uint32_t *hist_bins;           // device uint32[max_iter + 1] or NULL
+    const void *xs;                // coordinate table: W values of the working type
+    const void *ys;                // coordinate table: H values of the working type
+};
+
+// Launch parameters of the escape kernels (passed by value as a grid constant).
+struct EscapeArgs {
+    const Frame *frames;               // device table, or NULL to use `single`
+    int32_t n_frames;
+    int32_t hist_smem;                 // 1: accumulate histogram bins in shared memory (one frame)
+    int64_t total_chunks;
+    unsigned long long *chunk_counter; // zeroed before the launch
+    int32_t *status;                   // device status word (0 = ok), may be NULL
+    long long cycle_budget;            // per-CTA clock64 budget; <= 0: unlimited
+    uint32_t palette[256];
+    Frame single;
+};
+
+// Kernel variant knobs (chosen by the autotuner or the defaults).
+struct Variant {
+    int ppt;      // independent pixels per thread (ILP slots)
+    int unroll;   // steps per block between service points
+    int threads;  // threads per CTA
+    int ctas_per_sm;
+};
+
+// Thread-local last error.
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+// Launchers implemented in jl_escape.cu.
+// `frames_dev` is a device table of n frames, or NULL with `single` used instead.
+cudaError_t launch_coords(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st);
+cudaError_t launch_escape(const EscapeArgs &args, int precision, const Variant &v, int num_sms,
+                          cudaStream_t st);
+cudaError_t launch_hist_finalize(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st);
+bool variant_supported(int precision, int ppt, int unroll);
+int variant_list(int precision, int32_t *pairs, int cap);
+int device_sm_count();
+
+// Default variants.
+Variant default_variant(int precision, int max_iter);
+
+}  // namespace jl
