@@ -139,14 +139,15 @@ int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t
 int jl_variant_list(int32_t precision, int32_t *pairs, int32_t cap);
 
 /*
- * Issue-rate probe of the binary32 (JL_FP32) or binary64 (JL_FP64) pipe:
- * runs 8 independent multiply/add chains per thread on every SM (separate
- * FMUL and FADD, no FMA) and returns the achieved lane operations per second
- * in *lane_ops_per_s (and the kernel time in *seconds if non-NULL).  This is
- * the denominator of the escape kernels' ALU roofline.  Synchronises
- * `stream`.
+ * Issue-rate probe.  kind 0 (JL_FP32) / 1 (JL_FP64): 8 independent
+ * multiply/add chains per thread on every SM (separate FMUL and FADD, no
+ * FMA); kind 2: 32-bit xor + add chains; kind 3: 32-bit multiply-add chains;
+ * kind 4: high half of 32x32-bit products (xor-chained).  Returns the
+ * achieved lane operations per second in *lane_ops_per_s (and the kernel
+ * time in *seconds if non-NULL).  Kinds 0 and 1 are the denominators of the
+ * escape kernels' ALU roofline.  Synchronises `stream`.
  */
-int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_per_s, double *seconds, void *stream);
+int jl_probe_peak(int32_t kind, int32_t iters, double *lane_ops_per_s, double *seconds, void *stream);
 
 /* Writes the built-in 256-entry RGBA8 palette (1024 bytes) to `out` (host).
  * Entry 255 (never-escaped points) is opaque black. */

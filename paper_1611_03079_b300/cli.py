@@ -1,0 +1,89 @@
+"""Command-line renderer (through the C ABI).
+
+  python -m paper_1611_03079_b300.cli --workload sweep --index 13 --size 2048 --repeat 3
+  python -m paper_1611_03079_b300.cli --c -0.8+0.156j --rect -2 2 -2 2 --W 512 --H 512 --out f.npy
+
+Renders one frame `repeat` times on cuda:0 and prints the kernel-bracketed
+time and pixel-iterations per second; optionally saves counts (.npy).  Also
+used as the small, self-contained command that profiles are taken on.
+"""
+import argparse
+import json
+
+import numpy as np
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--workload", choices=["sweep", "single"], default=None)
+    p.add_argument("--index", type=int, default=0)
+    p.add_argument("--size", type=int, default=4096)
+    p.add_argument("--c", type=complex, default=complex(-0.8, 0.156))
+    p.add_argument("--rect", type=float, nargs=4, default=[-2.0, 2.0, -2.0, 2.0])
+    p.add_argument("--W", type=int, default=512)
+    p.add_argument("--H", type=int, default=512)
+    p.add_argument("--max-iter", type=int, default=100)
+    p.add_argument("--precision", default="fp32")
+    p.add_argument("--mode", default="julia")
+    p.add_argument("--repeat", type=int, default=1)
+    p.add_argument("--variant", type=int, nargs=4, default=None)
+    p.add_argument("--out", default=None)
+    p.add_argument("--probe", action="store_true", help="print the issue-rate probes and exit")
+    a = p.parse_args(argv)
+    if a.probe:
+        return probe()
+
+    import torch
+
+    import paper_1611_03079_b300 as jl
+    from paper_1611_03079_b300 import workloads as wl
+
+    if a.workload == "sweep":
+        f = wl.throughput_sweep(a.size)[a.index]
+    elif a.workload == "single":
+        f = wl.single_frame()
+    else:
+        f = dict(c=a.c, rect=tuple(a.rect), W=a.W, H=a.H, max_iter=a.max_iter,
+                 precision={"fp32": 0, "fp64": 1, "auto": 2}[a.precision],
+                 mode={"julia": 0, "mandelbrot": 1}[a.mode])
+    torch.cuda.set_device(0)
+    out = None
+    times = []
+    for _ in range(a.repeat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = jl.render(f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=f["precision"],
+                        mode=f["mode"], count_type="u16", rgba=True, out=out, variant=a.variant)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    iters = int(out["counts"].to(torch.int64).sum().item())
+    best = min(times)
+    print(json.dumps({"frame": {k: (str(v) if k == "c" else v) for k, v in f.items()}, "ms": times,
+                      "best_ms": best, "giter_s": iters / (best * 1e-3) / 1e9, "iterations": iters}))
+    if a.out:
+        np.save(a.out, out["counts"].view(torch.int16).cpu().numpy().view(np.uint16))
+
+
+def probe():
+    import ctypes
+
+    import torch
+
+    from paper_1611_03079_b300 import _lib
+    torch.cuda.set_device(0)
+    L = _lib.lib()
+    names = {0: "binary32 fmul+fadd", 1: "binary64 dmul+dadd", 2: "int32 xor+add", 3: "int32 mad",
+             4: "int32 mulhi+xor"}
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    res = {}
+    for kind, iters in ((0, 200000), (1, 4000), (2, 200000), (3, 200000), (4, 100000)):
+        ops, secs = ctypes.c_double(0), ctypes.c_double(0)
+        _lib.check(L.jl_probe_peak(kind, iters, ctypes.byref(ops), ctypes.byref(secs), None))
+        res[names[kind]] = {"G_lane_ops_s": ops.value / 1e9, "ms": secs.value * 1e3,
+                            "lane_ops_per_clk_per_sm_at_2032MHz": ops.value / (sms * 2.032e9)}
+    print(json.dumps(res, indent=1))
+
+
+if __name__ == "__main__":
+    main()

@@ -33,6 +33,37 @@ __global__ void __launch_bounds__(256) fp_probe_kernel(T *out, int iters, T a, T
         out[blockIdx.x] = s;
 }
 
+// Integer pipe probes: kind 2 = xor + add (logic/add pipe), kind 3 = 32-bit
+// multiply-add, kind 4 = high half of a 32x32 product.  One lane op per
+// statement; 8 independent chains per thread.
+template <int KIND>
+__global__ void __launch_bounds__(256) int_probe_kernel(uint32_t *out, int iters, uint32_t a, uint32_t b)
+{
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        v[k] = threadIdx.x * 2654435761u + k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if constexpr (KIND == 2) {
+                v[k] = (v[k] ^ a) + b;
+                asm volatile("" : "+r"(v[k]));
+            } else if constexpr (KIND == 3) {
+                v[k] = v[k] * a + b;
+            } else {
+                v[k] = __umulhi(v[k], a) ^ b;
+            }
+        }
+    }
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        s ^= v[k];
+    if (s == 0x9e3779b9u)
+        out[blockIdx.x] = s;
+}
+
 }  // namespace jl
 
 using namespace jl;
@@ -40,8 +71,8 @@ using namespace jl;
 extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_per_s, double *seconds,
                              void *stream)
 {
-    if (precision != JL_FP32 && precision != JL_FP64)
-        return fail(JL_EINVAL, "precision must be JL_FP32 or JL_FP64");
+    if (precision < 0 || precision > 4)
+        return fail(JL_EINVAL, "kind must be 0 (binary32), 1 (binary64), 2 (int xor+add), 3 (int mad), 4 (int mulhi)");
     if (iters < 1 || !lane_ops_per_s)
         return fail(JL_EINVAL, "iters must be >= 1 and lane_ops_per_s non-NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -62,8 +93,14 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
         cudaEventRecord(t0, st);
         if (precision == JL_FP32)
             fp_probe_kernel<float><<<grid, threads, 0, st>>>((float *)out, iters, 0.999f, 0.001f);
-        else
+        else if (precision == JL_FP64)
             fp_probe_kernel<double><<<grid, threads, 0, st>>>((double *)out, iters, 0.999, 0.001);
+        else if (precision == 2)
+            int_probe_kernel<2><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
+        else if (precision == 3)
+            int_probe_kernel<3><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
+        else
+            int_probe_kernel<4><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
         e = cudaGetLastError();
         if (e != cudaSuccess)
             rc = cuda_fail(e, "probe launch");
@@ -77,7 +114,8 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
     if (rc == JL_OK) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, t0, t1);
-        const double ops = (double)grid * threads * (double)iters * 8.0 * 2.0;
+        const double per = (precision == 3) ? 1.0 : 2.0;  // lane ops per chain step
+        const double ops = (double)grid * threads * (double)iters * 8.0 * per;
         *lane_ops_per_s = ops / (ms * 1e-3);
         if (seconds)
             *seconds = ms * 1e-3;
