@@ -149,6 +149,44 @@ int jl_variant_list(int32_t precision, int32_t *pairs, int32_t cap);
  */
 int jl_probe_peak(int32_t kind, int32_t iters, double *lane_ops_per_s, double *seconds, void *stream);
 
+/*
+ * Size of the static scratch array used by jl_render_static (bytes).
+ */
+#define JL_STATIC_SCRATCH_BYTES (256u * 1024u)
+
+/*
+ * jl_render_static — jl_render without any device allocation.  The paper has
+ * no counterpart; this entry point exists for callers that cannot allocate
+ * device memory when they render: a real-time display loop that must not
+ * stall on an allocation (cudaMalloc can synchronise the whole device), or a
+ * process whose device memory is reserved up front by another allocator (for
+ * example a framework's caching allocator), where any further allocation
+ * fails or fragments that reservation.
+ *
+ * Arguments, outputs and results are those of jl_render (counts, rgba and
+ * hist are caller-owned device buffers; palette is a host pointer or NULL).
+ * The scratch it needs (coordinate tables, work counter, status word) lives
+ * in one file-scope device array of JL_STATIC_SCRATCH_BYTES bytes, which
+ * every GPU that loads the library holds until the process exits.
+ *   - Limit: (width + height) * 4 bytes (binary32) or * 8 bytes (binary64),
+ *     rounded up to 256, plus 256 must fit in JL_STATIC_SCRATCH_BYTES, i.e.
+ *     width + height <= 65472 in binary32 and <= 32736 in binary64.  Larger
+ *     frames return JL_EINVAL with the limit in jl_last_error().
+ *   - Set-up: the first call on a device (with that device current) looks up
+ *     the array's device address with cudaGetSymbolAddress; make that first
+ *     call before any stream capture.
+ *   - Sharing: every call on a device uses the same array and leaves its
+ *     contents behind; each call clears the counter and status it relies on
+ *     (with cudaMemsetAsync, which does not allocate).  Calls whose work
+ *     overlaps on the GPU (concurrent streams, or host threads issuing to
+ *     different streams) race on the array: serialise them on one stream.
+ *   - It calls no cudaMalloc, cudaMallocAsync, cudaFree or other allocating
+ *     routine.
+ */
+int jl_render_static(double cr, double ci, jl_rect rect, int32_t width, int32_t height, int32_t max_iter,
+                     int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
+                     const uint8_t *palette, float *hist, void *stream);
+
 /* Writes the built-in 256-entry RGBA8 palette (1024 bytes) to `out` (host).
  * Entry 255 (never-escaped points) is opaque black. */
 int jl_default_palette(uint8_t *out);

@@ -41,6 +41,8 @@ SIGNATURES = {
     "jl_render": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "jl_render_variant": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
                                          _vp, _i32, _i32, _i32, _i32, _vp]),
+    "jl_render_static": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp,
+                                        _vp]),
     "jl_variant_list": (ctypes.c_int, [_i32, _vp, _i32]),
     "jl_probe_peak": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp]),
     "jl_render_to_host": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,

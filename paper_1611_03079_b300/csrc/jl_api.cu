@@ -49,6 +49,12 @@ static void make_default_palette(uint8_t *out)
     out[4 * 255 + 3] = 255;
 }
 
+int default_palette_bytes(uint8_t *out)
+{
+    make_default_palette(out);
+    return JL_OK;
+}
+
 static bool finite4(const jl_rect &r)
 {
     return isfinite(r.xmin) && isfinite(r.xmax) && isfinite(r.ymin) && isfinite(r.ymax);

@@ -1,0 +1,136 @@
+// jl_render_static: a single-frame render that allocates nothing.
+//
+// Some callers cannot allocate device memory when they render: a real-time
+// display loop that must not stall on an allocation (cudaMalloc can
+// synchronise the whole device), or a process whose device memory is reserved
+// up front by another allocator (for example a framework's caching
+// allocator), where any further allocation fails or fragments that
+// reservation.  This entry point serves them: its scratch (the per-frame
+// coordinate tables, the work counter and the status word) lives in the
+// file-scope array below instead of stream-ordered allocations.  Every GPU
+// that loads this library holds the array until the process exits.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "jl_internal.h"
+
+namespace jl {
+
+int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_iter, int precision, int mode,
+               int count_type, bool has_counts, bool has_rgba, bool has_hist, Frame *F, int *prec_out);
+
+// Built-in palette (jl_api.cu).
+int default_palette_bytes(uint8_t *out);
+
+static __device__ __align__(256) uint8_t g_static_scratch[JL_STATIC_SCRATCH_BYTES];
+
+// In host code `g_static_scratch` names a host-side stand-in, not device
+// memory, so the kernels get the device address looked up here: once per
+// device, with that device current.
+static constexpr int kMaxDevices = 64;
+static std::mutex g_static_mu;
+static void *g_static_addr[kMaxDevices] = {};
+
+static int static_scratch_address(void **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(JL_EUNSUPPORTED, "device index beyond the static scratch table");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return JL_OK;
+}
+
+}  // namespace jl
+
+using namespace jl;
+
+extern "C" int jl_render_static(double cr, double ci, jl_rect rect, int32_t width, int32_t height,
+                                int32_t max_iter, int32_t precision, int32_t mode, int32_t count_type,
+                                void *counts, uint8_t *rgba, const uint8_t *palette, float *hist, void *stream)
+{
+    Frame F;
+    int prec = 0;
+    int rc = make_frame(cr, ci, rect, width, height, max_iter, precision, mode, count_type, counts != nullptr,
+                        rgba != nullptr, hist != nullptr, &F, &prec);
+    if (rc != JL_OK)
+        return rc;
+    const size_t esz = prec == JL_FP64 ? 8 : 4;
+    const size_t coord_bytes = ((size_t)F.W + (size_t)F.H) * esz;
+    const size_t coord_pad = (coord_bytes + 255) & ~(size_t)255;
+    if (coord_pad + 256 > (size_t)JL_STATIC_SCRATCH_BYTES)
+        return fail(JL_EINVAL, "jl_render_static: (width + height) * " + std::to_string(esz) +
+                                   " bytes of coordinate tables exceed the static scratch of " +
+                                   std::to_string((size_t)JL_STATIC_SCRATCH_BYTES) +
+                                   " bytes (limit: width + height <= " +
+                                   std::to_string(((size_t)JL_STATIC_SCRATCH_BYTES - 256) / esz) + ")");
+    void *scratch = nullptr;
+    rc = static_scratch_address(&scratch);
+    if (rc != JL_OK)
+        return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t *base = static_cast<uint8_t *>(scratch);
+    F.xs = base;
+    F.ys = base + (size_t)F.W * esz;
+    F.counts = static_cast<uint8_t *>(counts);
+    F.rgba = reinterpret_cast<uint32_t *>(rgba);
+    F.hist_bins = reinterpret_cast<uint32_t *>(hist);
+    unsigned long long *counter = reinterpret_cast<unsigned long long *>(base + coord_pad);
+    int32_t *status = reinterpret_cast<int32_t *>(base + coord_pad + 8);
+
+    // The array keeps the previous call's contents: the work counter and the
+    // status word must start at zero, the coordinate tables are rewritten.
+    cudaError_t e = cudaMemsetAsync(base + coord_pad, 0, 16, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync(static counter)");
+    if (F.hist_bins) {
+        e = cudaMemsetAsync(F.hist_bins, 0, ((size_t)F.max_iter + 1) * 4, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync(hist)");
+    }
+    e = launch_coords(nullptr, &F, 1, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "coords kernel launch");
+
+    EscapeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.frames = nullptr;
+    a.n_frames = 1;
+    a.hist_smem = (F.hist_bins && F.max_iter + 1 <= 4096) ? 1 : 0;
+    a.total_chunks = (int64_t)F.H * F.chunks_per_row;
+    a.chunk_counter = counter;
+    a.status = status;
+    a.cycle_budget = 0;
+    uint8_t pal[1024];
+    if (palette)
+        memcpy(pal, palette, 1024);
+    else
+        default_palette_bytes(pal);
+    memcpy(a.palette, pal, 1024);
+    a.single = F;
+    const int sms = device_sm_count();
+    if (sms <= 0)
+        return fail(JL_EUNSUPPORTED, "no CUDA device");
+    e = launch_escape(a, prec, default_variant(prec, F.max_iter), sms, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "escape kernel launch");
+    if (F.hist_bins) {
+        e = launch_hist_finalize(nullptr, &F, 1, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "histogram finalize launch");
+    }
+    return JL_OK;
+}
