@@ -187,6 +187,103 @@ int jl_render_static(double cr, double ci, jl_rect rect, int32_t width, int32_t 
                      int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
                      const uint8_t *palette, float *hist, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batches (Sec. 3: paths of C rendered as animations; also the histogram
+ * targets of the surrogate).  A plan renders many frames -- each with its own
+ * C, view, size, limit, mode and precision -- in one CUDA-graph launch of
+ * persistent escape kernels.
+ * ------------------------------------------------------------------------ */
+
+/* One frame of a batch.  Offsets are in bytes from the base pointers given to
+ * jl_batch_create; -1 means "no such output".  rgba and hist offsets must be
+ * multiples of 4, uint16 counts offsets multiples of 2. */
+typedef struct {
+    double cr, ci;          /* C for JL_JULIA frames */
+    jl_rect rect;
+    int32_t width, height, max_iter;
+    int32_t mode;           /* JL_JULIA / JL_MANDELBROT */
+    int32_t precision;      /* JL_FP32 / JL_FP64 / JL_AUTO (jl_select_precision) */
+    int32_t count_type;     /* JL_COUNT_*; must be JL_COUNT_NONE when counts_offset < 0 */
+    int64_t counts_offset;
+    int64_t rgba_offset;
+    int64_t hist_offset;    /* max_iter + 1 floats at this offset */
+} jl_frame;
+
+/* Plan options; zero-initialise for defaults. */
+typedef struct {
+    int32_t chunk_len;      /* pixels per work chunk, 16..1024; 0 = 512 */
+    int32_t fp32_ppt, fp32_unroll, fp32_threads;  /* 0 = tuned or default variant */
+    int32_t fp64_ppt, fp64_unroll, fp64_threads;
+    int32_t reserved;
+    int64_t cycle_budget;   /* per-CTA clock64 budget; when exceeded the kernels stop
+                               taking work and the plan status becomes JL_ETIMEOUT;
+                               0 = unlimited */
+} jl_batch_opts;
+
+typedef struct jl_batch jl_batch;
+
+/*
+ * Build a plan for n frames writing to counts_base / rgba_base / hist_base
+ * (device memory, caller-owned, bound to the plan).  Allocates the plan's
+ * tables, computes every coordinate table, and captures the launch graph;
+ * synchronous.  palette: host, 1024 bytes, or NULL for the built-in one.
+ * On success *out owns device memory until jl_batch_destroy.
+ */
+int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_t *rgba_base, float *hist_base,
+                    const uint8_t *palette, const jl_batch_opts *opts, jl_batch **out);
+
+/* Render every frame of the plan: one cudaGraphLaunch on `stream`
+ * (asynchronous; nothing is allocated). */
+int jl_batch_launch(jl_batch *b, void *stream);
+
+/* Status word of the last launch (JL_OK or JL_ETIMEOUT); synchronises `stream`. */
+int jl_batch_status(jl_batch *b, void *stream, int32_t *status_out);
+
+/* Resolved precision of each frame (input order) into out[0..cap); returns n, or -1. */
+int jl_batch_precisions(const jl_batch *b, int32_t *out, int32_t cap);
+
+/* Pixel totals of the binary32 and binary64 frames of the plan. */
+int jl_batch_pixels(const jl_batch *b, int64_t *fp32_pixels, int64_t *fp64_pixels);
+
+/* Frees the plan (after its launches have completed). */
+void jl_batch_destroy(jl_batch *b);
+
+/* One-shot: create, launch, wait, destroy.  Synchronous; returns JL_ETIMEOUT
+ * never (no budget) and JL_OK on success. */
+int jl_render_batch(const jl_frame *frames, int32_t n, void *counts_base, uint8_t *rgba_base, float *hist_base,
+                    const uint8_t *palette, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Autotuner of the escape kernel's launch shape.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t ppt, unroll, threads, ctas_per_sm;
+    double ms;              /* mean time of the calibration set with this variant */
+    int32_t candidates;     /* candidates timed (jl_tune_get: 1 if tuned, 0 if default) */
+} jl_tune_result;
+
+/*
+ * Times every supported (ppt, unroll) x {128, 256} threads on the calibration
+ * frames (their own rect, size, mode and C; `precision` and `max_iter` as
+ * given), `reps` timed repetitions each after one warm-up, and records the
+ * fastest for (current device, precision, bucket of max_iter: <=128, <=1024,
+ * <=8192, larger).  calib may be NULL (built-in set: a 1024^2 Julia frame and
+ * a 1024^2 Mandelbrot frame).  jl_render and new batch plans use the
+ * recorded variant.  Synchronous.
+ */
+int jl_autotune(int32_t precision, int32_t max_iter, const jl_frame *calib, int32_t n_calib, int32_t reps,
+                jl_tune_result *out);
+
+/* The variant jl_render would use now for (precision, max_iter). */
+int jl_tune_get(int32_t precision, int32_t max_iter, jl_tune_result *out);
+
+/* Forget all tuned variants (back to the defaults). */
+int jl_tune_clear(void);
+
+/* Save / load the tuning table (text, one entry per line). */
+int jl_tune_save(const char *path);
+int jl_tune_load(const char *path);
+
 /* Writes the built-in 256-entry RGBA8 palette (1024 bytes) to `out` (host).
  * Entry 255 (never-escaped points) is opaque black. */
 int jl_default_palette(uint8_t *out);

@@ -139,3 +139,163 @@ def render_to_host(c, rect, width, height, max_iter=100, precision="fp32", mode=
     check(rc)
     del pal
     return out
+
+
+# ---------------------------------------------------------------------------
+# Batches (jl_batch_*) and the autotuner (jl_autotune, jl_tune_*)
+# ---------------------------------------------------------------------------
+def _frame_struct(f, counts_off, rgba_off, hist_off):
+    c = f.get("c")
+    cr, ci = _c(c)
+    return _lib.Frame(cr, ci, _rect(f["rect"]), int(f["W"]), int(f["H"]), int(f["max_iter"]),
+                      _MODE[f.get("mode", "julia")], _PREC[f.get("precision", "fp32")],
+                      _CT[f.get("count_type")], counts_off, rgba_off, hist_off)
+
+
+class Batch:
+    """A batch plan: frames rendered together by one CUDA-graph launch.
+
+    `frames` are dicts with keys c, rect, W, H, max_iter, mode, precision,
+    count_type (None for no counts), and optional rgba (default True) and hist
+    (default False).  Outputs are allocated here as flat device buffers;
+    `counts(i)`, `rgba(i)` and `hist(i)` return per-frame views.
+    """
+
+    def __init__(self, frames, palette=None, chunk_len=0, variants=None, cycle_budget=0):
+        import torch
+        self._L = _lib.lib()
+        self.frames = list(frames)
+        n = len(self.frames)
+        self._c_off, self._r_off, self._h_off = [], [], []
+        cb = rb = hb = 0
+        for f in self.frames:
+            ct = _CT[f.get("count_type")]
+            npx = int(f["W"]) * int(f["H"])
+            if ct != JL_COUNT_NONE:
+                cb = (cb + 1) & ~1
+                self._c_off.append(cb)
+                cb += npx * (1 if ct == JL_COUNT_U8 else 2)
+            else:
+                self._c_off.append(-1)
+            if f.get("rgba", True):
+                self._r_off.append(rb)
+                rb += npx * 4
+            else:
+                self._r_off.append(-1)
+            if f.get("hist", False):
+                self._h_off.append(hb)
+                hb += (int(f["max_iter"]) + 1) * 4
+            else:
+                self._h_off.append(-1)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.counts_buf = torch.empty(max(cb, 2), dtype=torch.uint8, device=dev)
+        self.rgba_buf = torch.empty(max(rb, 4), dtype=torch.uint8, device=dev)
+        self.hist_buf = torch.empty(max(hb // 4, 1), dtype=torch.float32, device=dev)
+        arr = (_lib.Frame * n)(*[_frame_struct(f, self._c_off[i], self._r_off[i], self._h_off[i])
+                                 for i, f in enumerate(self.frames)])
+        opts = _lib.BatchOpts()
+        opts.chunk_len = int(chunk_len)
+        if variants:
+            if "fp32" in variants:
+                opts.fp32_ppt, opts.fp32_unroll, opts.fp32_threads = (int(v) for v in variants["fp32"])
+            if "fp64" in variants:
+                opts.fp64_ppt, opts.fp64_unroll, opts.fp64_threads = (int(v) for v in variants["fp64"])
+        opts.cycle_budget = int(cycle_budget)
+        pal, pal_ptr = _palette_ptr(palette)
+        h = ctypes.c_void_p()
+        check(self._L.jl_batch_create(ctypes.cast(arr, ctypes.c_void_p), n, self.counts_buf.data_ptr(),
+                                      self.rgba_buf.data_ptr(), self.hist_buf.data_ptr(), pal_ptr,
+                                      ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        import torch
+        st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        check(self._L.jl_batch_launch(self._h, st))
+
+    def status(self, stream=None):
+        import torch
+        st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        v = ctypes.c_int32(0)
+        check(self._L.jl_batch_status(self._h, st, ctypes.byref(v)))
+        return v.value
+
+    def precisions(self):
+        n = len(self.frames)
+        buf = (ctypes.c_int32 * n)()
+        self._L.jl_batch_precisions(self._h, buf, n)
+        return list(buf)
+
+    def pixels(self):
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        check(self._L.jl_batch_pixels(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def counts(self, i):
+        import torch
+        f = self.frames[i]
+        o = self._c_off[i]
+        if o < 0:
+            return None
+        npx = int(f["W"]) * int(f["H"])
+        if _CT[f.get("count_type")] == JL_COUNT_U8:
+            return self.counts_buf[o:o + npx].view(int(f["H"]), int(f["W"]))
+        return self.counts_buf[o:o + 2 * npx].view(torch.int16).view(int(f["H"]), int(f["W"]))
+
+    def rgba(self, i):
+        f = self.frames[i]
+        o = self._r_off[i]
+        if o < 0:
+            return None
+        npx = int(f["W"]) * int(f["H"])
+        return self.rgba_buf[o:o + 4 * npx].view(int(f["H"]), int(f["W"]), 4)
+
+    def hist(self, i):
+        o = self._h_off[i]
+        if o < 0:
+            return None
+        return self.hist_buf[o // 4:o // 4 + int(self.frames[i]["max_iter"]) + 1]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.jl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(precision="fp32", max_iter=100, calib=None, reps=3):
+    """Run the launch-shape autotuner; returns the chosen variant as a dict."""
+    L = _lib.lib()
+    res = _lib.TuneResult()
+    if calib:
+        arr = (_lib.Frame * len(calib))(*[_frame_struct(f, -1, -1, -1) for f in calib])
+        ptr, n = ctypes.cast(arr, ctypes.c_void_p), len(calib)
+    else:
+        ptr, n = None, 0
+    check(L.jl_autotune(_PREC[precision], int(max_iter), ptr, n, int(reps), ctypes.byref(res)))
+    return {"ppt": res.ppt, "unroll": res.unroll, "threads": res.threads, "ctas_per_sm": res.ctas_per_sm,
+            "ms": res.ms, "candidates": res.candidates}
+
+
+def tune_get(precision="fp32", max_iter=100):
+    res = _lib.TuneResult()
+    check(_lib.lib().jl_tune_get(_PREC[precision], int(max_iter), ctypes.byref(res)))
+    return {"ppt": res.ppt, "unroll": res.unroll, "threads": res.threads, "ctas_per_sm": res.ctas_per_sm,
+            "tuned": bool(res.candidates)}
+
+
+def tune_clear():
+    check(_lib.lib().jl_tune_clear())
+
+
+def tune_save(path):
+    check(_lib.lib().jl_tune_save(str(path).encode()))
+
+
+def tune_load(path):
+    check(_lib.lib().jl_tune_load(str(path).encode()))

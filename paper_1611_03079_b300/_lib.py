@@ -29,6 +29,28 @@ class Rect(ctypes.Structure):
                 ("ymin", ctypes.c_double), ("ymax", ctypes.c_double)]
 
 
+class Frame(ctypes.Structure):
+    """jl_frame (include/jl.h)."""
+    _fields_ = [("cr", ctypes.c_double), ("ci", ctypes.c_double), ("rect", Rect),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("count_type", ctypes.c_int32),
+                ("counts_offset", ctypes.c_int64), ("rgba_offset", ctypes.c_int64),
+                ("hist_offset", ctypes.c_int64)]
+
+
+class BatchOpts(ctypes.Structure):
+    """jl_batch_opts (include/jl.h)."""
+    _fields_ = [("chunk_len", ctypes.c_int32), ("fp32_ppt", ctypes.c_int32), ("fp32_unroll", ctypes.c_int32),
+                ("fp32_threads", ctypes.c_int32), ("fp64_ppt", ctypes.c_int32), ("fp64_unroll", ctypes.c_int32),
+                ("fp64_threads", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cycle_budget", ctypes.c_int64)]
+
+
+class TuneResult(ctypes.Structure):
+    """jl_tune_result (include/jl.h)."""
+    _fields_ = [("ppt", ctypes.c_int32), ("unroll", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("ms", ctypes.c_double), ("candidates", ctypes.c_int32)]
+
+
 _lib = None
 
 # Every entry point declared in include/*.h, with its ctypes signature.
@@ -45,6 +67,18 @@ SIGNATURES = {
                                         _vp]),
     "jl_variant_list": (ctypes.c_int, [_i32, _vp, _i32]),
     "jl_probe_peak": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp]),
+    "jl_batch_create": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "jl_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "jl_batch_status": (ctypes.c_int, [_vp, _vp, _vp]),
+    "jl_batch_precisions": (ctypes.c_int, [_vp, _vp, _i32]),
+    "jl_batch_pixels": (ctypes.c_int, [_vp, _vp, _vp]),
+    "jl_batch_destroy": (None, [_vp]),
+    "jl_render_batch": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "jl_autotune": (ctypes.c_int, [_i32, _i32, _vp, _i32, _i32, _vp]),
+    "jl_tune_get": (ctypes.c_int, [_i32, _i32, _vp]),
+    "jl_tune_clear": (ctypes.c_int, []),
+    "jl_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "jl_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "jl_render_to_host": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
                                          _vp, _vp]),
 }

@@ -61,6 +61,7 @@ static bool finite4(const jl_rect &r)
 }
 
 int select_precision(const jl_rect &r, int W, int H)
+
 {
     if (!finite4(r) || !(r.xmin < r.xmax) || !(r.ymin < r.ymax) || W < 1 || H < 1)
         return -1;
@@ -78,7 +79,8 @@ int select_precision(const jl_rect &r, int W, int H)
 // Validates a frame request and fills the device descriptor (pointers to the
 // outputs and coordinate tables are filled by the caller).
 int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_iter, int precision, int mode,
-               int count_type, bool has_counts, bool has_rgba, bool has_hist, Frame *F, int *prec_out)
+               int count_type, bool has_counts, bool has_rgba, bool has_hist, Frame *F, int *prec_out,
+               int chunk_len)
 {
     if (W < 1 || H < 1 || W > 65536 || H > 65536 || (int64_t)W * (int64_t)H >= (1ll << 31))
         return fail(JL_EINVAL, "width/height out of range (1..65536 each, W*H < 2^31)");
@@ -116,8 +118,24 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
     F->max_iter = max_iter;
     F->mode = mode;
     F->count_type = count_type;
-    F->chunk_len = W < 256 ? W : 256;
-    F->chunks_per_row = (W + F->chunk_len - 1) / F->chunk_len;
+    if (chunk_len < 16 || chunk_len > 1024)
+        return fail(JL_EINVAL, "chunk_len must be 16..1024");
+    // Work chunks: row segments of chunk_len pixels, or whole rows grouped
+    // k = chunk_len / W at a time for narrow frames.  For the grouped form the
+    // row of pixel o < k*W <= 1024 is (o * ceil(2^20 / W)) >> 20, exact because
+    // the excess o * (ceil(2^20/W) - 2^20/W) / 2^20 < 2^-10 <= 1/W.
+    F->chunk_len = chunk_len;
+    if (W < chunk_len && chunk_len / W > 1) {
+        F->rows_per_chunk = chunk_len / W;
+        F->span_magic = (uint32_t)(((1u << 20) + (uint32_t)W - 1u) / (uint32_t)W);
+        F->chunks_per_row = 1;
+        F->chunk_count = (H + F->rows_per_chunk - 1) / F->rows_per_chunk;
+    } else {
+        F->rows_per_chunk = 1;
+        F->span_magic = 0;
+        F->chunks_per_row = (W + chunk_len - 1) / chunk_len;
+        F->chunk_count = H * F->chunks_per_row;
+    }
     F->precision = prec;
     F->colour_magic = (1ull << 40) / (uint64_t)max_iter + 1ull;
     // Monotone escape is proven for |C| <= 2 - 2^-12 (Julia); Mandelbrot pixels
@@ -171,7 +189,7 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
         a.frames = nullptr;
         a.n_frames = 1;
         a.hist_smem = (F.hist_bins && F.max_iter + 1 <= 4096) ? 1 : 0;
-        a.total_chunks = (int64_t)F.H * F.chunks_per_row;
+        a.total_chunks = F.chunk_count;
         a.chunk_counter = counter;
         a.status = status;
         a.cycle_budget = 0;
@@ -184,7 +202,7 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
         a.single = F;
         const int sms = device_sm_count();
         if (sms <= 0) { rc = fail(JL_EUNSUPPORTED, "no CUDA device"); break; }
-        Variant v = vopt ? *vopt : default_variant(prec, F.max_iter);
+        Variant v = vopt ? *vopt : tuned_variant(prec, F.max_iter);
         e = launch_escape(a, prec, v, sms, st);
         if (e != cudaSuccess) { rc = cuda_fail(e, "escape kernel launch"); break; }
         if (F.hist_bins) {

@@ -1,0 +1,341 @@
+// Batched rendering: many frames (different C, view, size, limit, mode and
+// precision) in one CUDA-graph launch of persistent escape kernels
+// (paper Sec. 3: parameter paths animated in real time; Sec. 2: the
+// escape-time kernel itself lives in jl_escape.cu).
+//
+// A plan resolves every frame's precision, builds the device frame tables and
+// the chunk -> frame table, computes all coordinate tables once, and captures
+// one graph: reset of the work counters and status word, zeroing of the
+// histogram bins, the binary32 and binary64 persistent escape kernels on two
+// forked branches (they run concurrently), and the histogram finalisation.
+// Launching the plan replays the graph; nothing is allocated per launch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "jl_internal.h"
+
+struct jl_batch {
+    int device = -1;
+    int n = 0;
+    std::vector<int32_t> prec;             // resolved precision of every frame (input order)
+    std::vector<int64_t> pixels;           // per group
+    jl::Frame *frames_dev[2] = {nullptr, nullptr};
+    int32_t *chunk_frame_dev[2] = {nullptr, nullptr};
+    int n_group[2] = {0, 0};
+    int64_t chunks[2] = {0, 0};
+    void *coords_dev = nullptr;
+    uint8_t *ctl_dev = nullptr;            // counters (2 x 8 B) + status (4 B), zeroed per launch
+    cudaStream_t s0 = nullptr, s1 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    jl::Variant variant[2];
+    bool any_hist = false;
+};
+
+namespace jl {
+
+static void destroy_plan(jl_batch *b)
+{
+    if (!b)
+        return;
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    if (b->graph)
+        cudaGraphDestroy(b->graph);
+    for (int g = 0; g < 2; ++g) {
+        if (b->frames_dev[g])
+            cudaFree(b->frames_dev[g]);
+        if (b->chunk_frame_dev[g])
+            cudaFree(b->chunk_frame_dev[g]);
+    }
+    if (b->coords_dev)
+        cudaFree(b->coords_dev);
+    if (b->ctl_dev)
+        cudaFree(b->ctl_dev);
+    if (b->fork)
+        cudaEventDestroy(b->fork);
+    if (b->join)
+        cudaEventDestroy(b->join);
+    if (b->s0)
+        cudaStreamDestroy(b->s0);
+    if (b->s1)
+        cudaStreamDestroy(b->s1);
+    delete b;
+}
+
+
+
+}  // namespace jl
+
+using namespace jl;
+
+extern "C" {
+
+int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_t *rgba_base, float *hist_base,
+                    const uint8_t *palette, const jl_batch_opts *opts, jl_batch **out)
+{
+    if (!out)
+        return fail(JL_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    if (!frames || n < 1)
+        return fail(JL_EINVAL, "need at least one frame");
+    jl_batch_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts)
+        o = *opts;
+    const int chunk_len = o.chunk_len ? o.chunk_len : 512;
+    if (o.cycle_budget < 0)
+        return fail(JL_EINVAL, "cycle_budget must be >= 0");
+
+    // ---- validate and describe every frame ----
+    std::vector<Frame> host[2];
+    std::vector<int32_t> prec(n);
+    std::vector<int> max_iter_max(2, 1);
+    bool any_hist = false;
+    for (int f = 0; f < n; ++f) {
+        const jl_frame &q = frames[f];
+        const bool hc = q.counts_offset >= 0, hr = q.rgba_offset >= 0, hh = q.hist_offset >= 0;
+        if ((hc && !counts_base) || (hr && !rgba_base) || (hh && !hist_base))
+            return fail(JL_EINVAL, "frame " + std::to_string(f) + ": output offset given but base pointer is NULL");
+        if (hh && (q.hist_offset & 3))
+            return fail(JL_EINVAL, "frame " + std::to_string(f) + ": hist_offset must be a multiple of 4");
+        if (hr && (q.rgba_offset & 3))
+            return fail(JL_EINVAL, "frame " + std::to_string(f) + ": rgba_offset must be a multiple of 4");
+        if (hc && q.count_type == JL_COUNT_U16 && (q.counts_offset & 1))
+            return fail(JL_EINVAL, "frame " + std::to_string(f) + ": uint16 counts_offset must be even");
+        Frame F;
+        int p = 0;
+        int rc = make_frame(q.cr, q.ci, q.rect, q.width, q.height, q.max_iter, q.precision, q.mode, q.count_type,
+                            hc, hr, hh, &F, &p, chunk_len);
+        if (rc != JL_OK)
+            return fail(rc, "frame " + std::to_string(f) + ": " + jl_last_error());
+        F.counts = hc ? static_cast<uint8_t *>(counts_base) + q.counts_offset : nullptr;
+        F.rgba = hr ? reinterpret_cast<uint32_t *>(rgba_base + q.rgba_offset) : nullptr;
+        F.hist_bins = hh ? reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(hist_base) + q.hist_offset)
+                         : nullptr;
+        any_hist |= hh;
+        prec[f] = p;
+        if (q.max_iter > max_iter_max[p])
+            max_iter_max[p] = q.max_iter;
+        host[p].push_back(F);
+    }
+
+    jl_batch *b = new jl_batch();
+    b->n = n;
+    b->prec = prec;
+    b->any_hist = any_hist;
+    b->pixels.assign(2, 0);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) {
+        destroy_plan(b);
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    int rc = JL_OK;
+    do {
+        // ---- coordinate tables (one allocation, 256-byte aligned pieces) ----
+        size_t coord_bytes = 0;
+        for (int g = 0; g < 2; ++g)
+            for (const Frame &F : host[g])
+                coord_bytes += (((size_t)F.W * (g ? 8 : 4) + 255) & ~(size_t)255) +
+                               (((size_t)F.H * (g ? 8 : 4) + 255) & ~(size_t)255);
+        e = cudaMalloc(&b->coords_dev, coord_bytes ? coord_bytes : 256);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(coordinate tables)"); break; }
+        size_t off = 0;
+        for (int g = 0; g < 2; ++g) {
+            int64_t chunk = 0;
+            for (Frame &F : host[g]) {
+                const size_t es = g ? 8 : 4;
+                F.xs = static_cast<uint8_t *>(b->coords_dev) + off;
+                off += ((size_t)F.W * es + 255) & ~(size_t)255;
+                F.ys = static_cast<uint8_t *>(b->coords_dev) + off;
+                off += ((size_t)F.H * es + 255) & ~(size_t)255;
+                F.chunk_begin = chunk;
+                chunk += F.chunk_count;
+                b->pixels[g] += (int64_t)F.W * F.H;
+            }
+            b->chunks[g] = chunk;
+            b->n_group[g] = (int)host[g].size();
+        }
+        e = cudaMalloc(&b->ctl_dev, 256);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(control words)"); break; }
+        e = cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&b->s1, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "stream/event creation"); break; }
+
+        for (int g = 0; g < 2 && rc == JL_OK; ++g) {
+            if (host[g].empty())
+                continue;
+            const size_t nb = host[g].size() * sizeof(Frame);
+            e = cudaMalloc(&b->frames_dev[g], nb);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(frame table)"); break; }
+            e = cudaMemcpy(b->frames_dev[g], host[g].data(), nb, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(frame table)"); break; }
+            std::vector<int32_t> cf((size_t)b->chunks[g]);
+            for (size_t f = 0; f < host[g].size(); ++f)
+                for (int32_t c = 0; c < host[g][f].chunk_count; ++c)
+                    cf[(size_t)host[g][f].chunk_begin + c] = (int32_t)f;
+            e = cudaMalloc(&b->chunk_frame_dev[g], cf.size() * sizeof(int32_t));
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(chunk table)"); break; }
+            e = cudaMemcpy(b->chunk_frame_dev[g], cf.data(), cf.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(chunk table)"); break; }
+            // coordinate tables, once per plan
+            e = launch_coords(b->frames_dev[g], nullptr, (int)host[g].size(), b->s0);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "coords kernel launch"); break; }
+            // kernel variant: explicit option, else the tuned/default one
+            const int pp = g ? o.fp64_ppt : o.fp32_ppt;
+            const int uu = g ? o.fp64_unroll : o.fp32_unroll;
+            const int tt = g ? o.fp64_threads : o.fp32_threads;
+            Variant v = tuned_variant(g, max_iter_max[g]);
+            if (pp || uu) {
+                if (!variant_supported(g, pp, uu)) { rc = fail(JL_EINVAL, "unsupported (ppt, unroll) option"); break; }
+                v.ppt = pp;
+                v.unroll = uu;
+            }
+            if (tt) {
+                if (tt < 32 || tt > 256 || (tt & 31)) { rc = fail(JL_EINVAL, "threads option must be 32..256, multiple of 32"); break; }
+                v.threads = tt;
+            }
+            b->variant[g] = v;
+        }
+        if (rc != JL_OK)
+            break;
+        e = cudaStreamSynchronize(b->s0);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "coordinate tables"); break; }
+
+        // ---- capture the launch graph ----
+        EscapeArgs args[2];
+        uint8_t pal[1024];
+        if (palette)
+            memcpy(pal, palette, 1024);
+        else
+            default_palette_bytes(pal);
+        for (int g = 0; g < 2; ++g) {
+            memset(&args[g], 0, sizeof(EscapeArgs));
+            args[g].frames = b->frames_dev[g];
+            args[g].chunk_frame = b->chunk_frame_dev[g];
+            args[g].n_frames = b->n_group[g];
+            args[g].hist_smem = 0;
+            args[g].total_chunks = b->chunks[g];
+            args[g].chunk_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 8 * g);
+            args[g].status = reinterpret_cast<int32_t *>(b->ctl_dev + 16);
+            args[g].cycle_budget = o.cycle_budget;
+            memcpy(args[g].palette, pal, 1024);
+        }
+        const int sms = device_sm_count();
+        if (sms <= 0) { rc = fail(JL_EUNSUPPORTED, "no CUDA device"); break; }
+        e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamBeginCapture"); break; }
+        cudaError_t ce = cudaMemsetAsync(b->ctl_dev, 0, 32, b->s0);
+        for (int g = 0; g < 2 && ce == cudaSuccess && any_hist; ++g)
+            if (b->n_group[g])
+                ce = launch_hist_zero(b->frames_dev[g], b->n_group[g], b->s0);
+        const bool both = b->n_group[0] && b->n_group[1];
+        if (ce == cudaSuccess && both) {
+            ce = cudaEventRecord(b->fork, b->s0);
+            if (ce == cudaSuccess)
+                ce = cudaStreamWaitEvent(b->s1, b->fork, 0);
+            if (ce == cudaSuccess)
+                ce = launch_escape(args[1], JL_FP64, b->variant[1], sms, b->s1);
+            if (ce == cudaSuccess)
+                ce = cudaEventRecord(b->join, b->s1);
+            if (ce == cudaSuccess)
+                ce = launch_escape(args[0], JL_FP32, b->variant[0], sms, b->s0);
+            if (ce == cudaSuccess)
+                ce = cudaStreamWaitEvent(b->s0, b->join, 0);
+        } else if (ce == cudaSuccess) {
+            const int g = b->n_group[0] ? 0 : 1;
+            ce = launch_escape(args[g], g, b->variant[g], sms, b->s0);
+        }
+        for (int g = 0; g < 2 && ce == cudaSuccess && any_hist; ++g)
+            if (b->n_group[g])
+                ce = launch_hist_finalize(b->frames_dev[g], nullptr, b->n_group[g], b->s0);
+        e = cudaStreamEndCapture(b->s0, &b->graph);
+        if (ce != cudaSuccess) { rc = cuda_fail(ce, "graph capture"); break; }
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamEndCapture"); break; }
+        e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaGraphInstantiate"); break; }
+    } while (0);
+    if (rc != JL_OK) {
+        destroy_plan(b);
+        return rc;
+    }
+    *out = b;
+    return JL_OK;
+}
+
+int jl_batch_launch(jl_batch *b, void *stream)
+{
+    if (!b || !b->exec)
+        return fail(JL_EINVAL, "invalid batch plan");
+    cudaError_t e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGraphLaunch");
+    return JL_OK;
+}
+
+int jl_batch_status(jl_batch *b, void *stream, int32_t *status_out)
+{
+    if (!b || !status_out)
+        return fail(JL_EINVAL, "invalid arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, b->ctl_dev + 16, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading batch status");
+    *status_out = v;
+    return JL_OK;
+}
+
+int jl_batch_precisions(const jl_batch *b, int32_t *out, int32_t cap)
+{
+    if (!b)
+        return fail(-1, "invalid batch plan");
+    for (int i = 0; i < b->n && i < cap && out; ++i)
+        out[i] = b->prec[i];
+    return b->n;
+}
+
+int jl_batch_pixels(const jl_batch *b, int64_t *fp32_pixels, int64_t *fp64_pixels)
+{
+    if (!b)
+        return fail(JL_EINVAL, "invalid batch plan");
+    if (fp32_pixels)
+        *fp32_pixels = b->pixels[0];
+    if (fp64_pixels)
+        *fp64_pixels = b->pixels[1];
+    return JL_OK;
+}
+
+void jl_batch_destroy(jl_batch *b) { destroy_plan(b); }
+
+int jl_render_batch(const jl_frame *frames, int32_t n, void *counts_base, uint8_t *rgba_base, float *hist_base,
+                    const uint8_t *palette, void *stream)
+{
+    jl_batch *b = nullptr;
+    int rc = jl_batch_create(frames, n, counts_base, rgba_base, hist_base, palette, nullptr, &b);
+    if (rc != JL_OK)
+        return rc;
+    rc = jl_batch_launch(b, stream);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (rc == JL_OK && e != cudaSuccess)
+        rc = cuda_fail(e, "cudaStreamSynchronize");
+    int32_t st = 0;
+    if (rc == JL_OK && jl_batch_status(b, stream, &st) == JL_OK && st != 0)
+        rc = fail(st, "batch stopped early (status " + std::to_string(st) + ")");
+    destroy_plan(b);
+    return rc;
+}
+
+}  // extern "C"

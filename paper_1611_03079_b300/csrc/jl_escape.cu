@@ -28,6 +28,7 @@
 //    contracts into an FMA; the library is also built with -fmad=false.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "jl_internal.h"
 
@@ -90,6 +91,19 @@ __global__ void hist_finalize_kernel(const __grid_constant__ HistArgs a)
             float v = __double2float_rn(__ddiv_rn((double)c, npix));
             reinterpret_cast<float *>(F.hist_bins)[b] = v;
         }
+    }
+}
+
+// Zero the uint32 bins of every frame that has a histogram (batch launches).
+__global__ void hist_zero_kernel(const __grid_constant__ HistArgs a)
+{
+    const Frame *frames = a.frames ? a.frames : &a.single;
+    for (int f = blockIdx.x; f < a.n_frames; f += gridDim.x) {
+        const Frame &F = frames[f];
+        if (!F.hist_bins)
+            continue;
+        for (int b = threadIdx.x; b <= F.max_iter; b += blockDim.x)
+            F.hist_bins[b] = 0u;
     }
 }
 
@@ -184,21 +198,29 @@ __device__ __forceinline__ uint32_t colour_index(uint32_t count, uint32_t max_it
     return (uint32_t)(p >> 40);
 }
 
-template <typename T, int PPT, int U>
+template <typename T, int PPT, int U, bool BATCH>
 __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ EscapeArgs a)
 {
     extern __shared__ uint32_t smem[];
     uint32_t *pal = smem;
     uint32_t *hbins = smem + 256;
 
-    const Frame *frames = a.frames ? a.frames : &a.single;
     const int lane = threadIdx.x & 31;
     const unsigned lane_bit = 1u << lane;
     const unsigned lt_mask = lane_bit - 1u;
 
+    // Frame f of the launch: the table in global memory for batches, the
+    // launch parameters for single frames.
+    auto FR = [&](int f) -> const Frame & {
+        if constexpr (BATCH)
+            return a.frames[f];
+        else
+            return a.single;
+    };
+
     for (int t = threadIdx.x; t < 256; t += blockDim.x)
         pal[t] = a.palette[t];
-    const int nb = a.hist_smem ? frames[0].max_iter + 1 : 0;
+    const int nb = (!BATCH && a.hist_smem) ? a.single.max_iter + 1 : 0;
     for (int t = threadIdx.x; t < nb; t += blockDim.x)
         hbins[t] = 0;
     __syncthreads();
@@ -206,9 +228,15 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
     const long long t_start = clock64();
 
     // ---- warp work queue (warp-uniform state) ----
-    int q_f = 0, q_row = 0, q_pos = 0, q_end = 0, q_W = 0, q_max = 0, q_mode = 0, q_safe = 1;
-    T q_cr = T(0), q_ci = T(0), q_y = T(0);
+    // A chunk is rows [q_j0, q_j0 + k) x columns [q_x0, q_x0 + q_span) of frame
+    // q_f, its pixels numbered o = 0 .. q_end-1 row-major; row offset of o is
+    // (o * q_magic) >> 20 (exact for o < 1024 <= 2^20 / span, see make_frame).
+    int q_f = 0, q_j0 = 0, q_x0 = 0, q_span = 1, q_pos = 0, q_end = 0, q_W = 0, q_max = 0, q_mode = 0;
+    int q_safe = 1;
+    uint32_t q_magic = 0;
+    T q_cr = T(0), q_ci = T(0);
     const T *q_xs = nullptr;
+    const T *q_ys = nullptr;
     bool q_done = false;
     unsigned long long next_c = 0;  // valid in lane 0: prefetched chunk id
     if (lane == 0)
@@ -230,23 +258,28 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
         }
         if (lane == 0)
             next_c = atomicAdd(a.chunk_counter, 1ull);
-        // frame containing chunk c: largest f with chunk_begin <= c
-        int lo = 0, hi = a.n_frames - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (frames[mid].chunk_begin <= (long long)c)
-                lo = mid;
-            else
-                hi = mid - 1;
+        int f = 0;
+        if constexpr (BATCH)
+            f = a.chunk_frame[c];
+        const Frame &F = FR(f);
+        const int lc = (int)((long long)c - F.chunk_begin);
+        q_f = f;
+        if (F.rows_per_chunk > 1) {
+            q_j0 = lc * F.rows_per_chunk;
+            q_x0 = 0;
+            q_span = F.W;
+            q_end = min(F.rows_per_chunk, F.H - q_j0) * F.W;
+            q_magic = F.span_magic;
+        } else {
+            const int row = lc / F.chunks_per_row;
+            const int seg = lc - row * F.chunks_per_row;
+            q_j0 = row;
+            q_x0 = seg * F.chunk_len;
+            q_span = min(F.chunk_len, F.W - q_x0);
+            q_end = q_span;
+            q_magic = 0;
         }
-        const Frame &F = frames[lo];
-        long long local = (long long)c - F.chunk_begin;
-        int row = (int)(local / F.chunks_per_row);
-        int seg = (int)(local - (long long)row * F.chunks_per_row);
-        q_f = lo;
-        q_row = row;
-        q_pos = seg * F.chunk_len;
-        q_end = min(q_pos + F.chunk_len, F.W);
+        q_pos = 0;
         q_W = F.W;
         q_max = F.max_iter;
         q_mode = F.mode;
@@ -254,7 +287,7 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
         q_cr = WorkT<T>::from_double(F.cr);
         q_ci = WorkT<T>::from_double(F.ci);
         q_xs = static_cast<const T *>(F.xs);
-        q_y = static_cast<const T *>(F.ys)[row];
+        q_ys = static_cast<const T *>(F.ys);
         return true;
     };
 
@@ -271,22 +304,29 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
         pix[k] = 0;
     }
 
+    // Store one finished pixel (count, colour, histogram bin).  Called by the
+    // lanes that finished a pixel in this slot (a divergent region).
     auto finish = [&](int f, int p, int count) {
-        const Frame &F = frames[f];
+        const Frame &F = FR(f);
         if (F.counts) {
             if (F.count_type == JL_COUNT_U8)
                 F.counts[p] = (uint8_t)count;
             else
                 reinterpret_cast<uint16_t *>(F.counts)[p] = (uint16_t)count;
         }
-        if (F.rgba) {
+        if (F.rgba)
             F.rgba[p] = pal[colour_index((uint32_t)count, (uint32_t)F.max_iter, F.colour_magic)];
-        }
         if (F.hist_bins) {
-            if (a.hist_smem)
+            if (!BATCH && a.hist_smem) {
                 atomicAdd(&hbins[count], 1u);
-            else
-                atomicAdd(&F.hist_bins[count], 1u);
+            } else {
+                // one atomic per distinct (frame, count) among the active lanes
+                const unsigned act = __activemask();
+                const unsigned long long key = ((unsigned long long)(unsigned)f << 32) | (unsigned)count;
+                const unsigned grp = __match_any_sync(act, key);
+                if ((grp & lt_mask) == 0)
+                    atomicAdd(&F.hist_bins[count], (unsigned)__popc(grp));
+            }
         }
     };
 
@@ -305,15 +345,19 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
             const int rank = __popc(remaining & lt_mask);
             const bool got = mine && rank < take;
             if (got) {
-                const int i = q_pos + rank;
+                const int o = q_pos + rank;
+                const int jj = (int)(((uint32_t)o * q_magic) >> 20);
+                const int i = q_x0 + o - jj * q_span;
+                const int j = q_j0 + jj;
                 const T xv = q_xs[i];
+                const T yv = q_ys[j];
                 fid[k] = q_f;
-                pix[k] = q_row * q_W + i;
+                pix[k] = j * q_W + i;
                 rem[k] = q_max;
                 bool unsafe;
                 if (q_mode == JL_JULIA) {
                     x[k] = xv;
-                    y[k] = q_y;
+                    y[k] = yv;
                     cr[k] = q_cr;
                     ci[k] = q_ci;
                     unsafe = !q_safe;
@@ -321,8 +365,8 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
                     x[k] = T(0);
                     y[k] = T(0);
                     cr[k] = xv;
-                    ci[k] = q_y;
-                    unsafe = in_unsafe_band(xv, q_y);
+                    ci[k] = yv;
+                    unsafe = in_unsafe_band(xv, yv);
                 }
                 if (unsafe || q_max < U) {
                     const int c = exact_from(x[k], y[k], cr[k], ci[k], 0, q_max);
@@ -356,7 +400,7 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
                 if (need[k]) {
                     int count;
                     const int f = fid[k];
-                    const int mi = frames[f].max_iter;
+                    const int mi = FR(f).max_iter;
                     if (rem[k] < 0) {
                         count = -1 - rem[k];
                     } else if (rem[k] < U) {
@@ -478,7 +522,7 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
 
     if (nb) {
         __syncthreads();
-        uint32_t *gb = frames[0].hist_bins;
+        uint32_t *gb = a.single.hist_bins;
         for (int t = threadIdx.x; t < nb; t += blockDim.x) {
             uint32_t v = hbins[t];
             if (v)
@@ -503,6 +547,7 @@ int device_sm_count()
 cudaError_t launch_coords(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st)
 {
     CoordArgs a;
+    memset(&a, 0, sizeof(a));
     a.frames = frames_dev;
     a.n_frames = n;
     if (single)
@@ -514,6 +559,7 @@ cudaError_t launch_coords(const Frame *frames_dev, const Frame *single, int n, c
 cudaError_t launch_hist_finalize(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st)
 {
     HistArgs a;
+    memset(&a, 0, sizeof(a));
     a.frames = frames_dev;
     a.n_frames = n;
     if (single)
@@ -523,10 +569,21 @@ cudaError_t launch_hist_finalize(const Frame *frames_dev, const Frame *single, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_hist_zero(const Frame *frames_dev, int n, cudaStream_t st)
+{
+    HistArgs a;
+    memset(&a, 0, sizeof(a));
+    a.frames = frames_dev;
+    a.n_frames = n;
+    int grid = n < 4096 ? n : 4096;
+    hist_zero_kernel<<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T, int PPT, int U>
 static cudaError_t launch_one(const EscapeArgs &a, const Variant &v, int num_sms, size_t smem, cudaStream_t st)
 {
-    auto kern = escape_kernel<T, PPT, U>;
+    auto kern = a.frames ? escape_kernel<T, PPT, U, true> : escape_kernel<T, PPT, U, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
@@ -581,7 +638,7 @@ int variant_list(int precision, int32_t *pairs, int cap)
 cudaError_t launch_escape(const EscapeArgs &a, int precision, const Variant &v, int num_sms, cudaStream_t st)
 {
     size_t smem = 256 * sizeof(uint32_t);
-    if (a.hist_smem)
+    if (a.hist_smem && !a.frames)
         smem += (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
 #define JL_DISPATCH(T, P, UU)                                                                 \
     if (((sizeof(T) == 8) == (precision == JL_FP64)) && v.ppt == P && v.unroll == UU)         \

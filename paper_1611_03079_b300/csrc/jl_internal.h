@@ -18,8 +18,12 @@ struct Frame {
     double xmin, ymin, dx, dy;     // region covering in binary64 (Sec. 2)
     int32_t W, H, max_iter, mode;  // mode: JL_JULIA / JL_MANDELBROT
     int32_t count_type;            // JL_COUNT_*
-    int32_t chunks_per_row;        // ceil(W / chunk_len)
-    int32_t chunk_len;             // pixels per work chunk (one row segment)
+    int32_t chunks_per_row;        // ceil(W / chunk_len) (rows_per_chunk == 1)
+    int32_t chunk_len;             // target pixels per work chunk (<= 1024)
+    int32_t rows_per_chunk;        // > 1: each chunk is this many whole rows (W < chunk_len)
+    uint32_t span_magic;           // ceil(2^20 / W) when rows_per_chunk > 1, else 0
+    int32_t chunk_count;           // chunks of this frame
+    int32_t pad1;
     int32_t safe;                  // 1: escape is monotone for every pixel (see escape kernels)
     int32_t precision;             // JL_FP32 / JL_FP64 (working type of xs/ys)
     int32_t pad0;
@@ -35,6 +39,7 @@ struct Frame {
 // Launch parameters of the escape kernels (passed by value as a grid constant).
 struct EscapeArgs {
     const Frame *frames;               // device table, or NULL to use `single`
+    const int32_t *chunk_frame;        // device: frame index of every chunk (batches)
     int32_t n_frames;
     int32_t hist_smem;                 // 1: accumulate histogram bins in shared memory (one frame)
     int64_t total_chunks;
@@ -64,11 +69,21 @@ cudaError_t launch_coords(const Frame *frames_dev, const Frame *single, int n, c
 cudaError_t launch_escape(const EscapeArgs &args, int precision, const Variant &v, int num_sms,
                           cudaStream_t st);
 cudaError_t launch_hist_finalize(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st);
+cudaError_t launch_hist_zero(const Frame *frames_dev, int n, cudaStream_t st);
 bool variant_supported(int precision, int ppt, int unroll);
 int variant_list(int precision, int32_t *pairs, int cap);
 int device_sm_count();
 
-// Default variants.
+// Validates a frame request and fills F (outputs and coordinate tables are
+// left NULL).  chunk_len: target pixels per work chunk (16 .. 1024).
+int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_iter, int precision, int mode,
+               int count_type, bool has_counts, bool has_rgba, bool has_hist, Frame *F, int *prec_out,
+               int chunk_len = 256);
+int default_palette_bytes(uint8_t *out);
+int select_precision(const jl_rect &r, int W, int H);
+
+// Default variants, and the autotuned one when the tuner has run.
 Variant default_variant(int precision, int max_iter);
+Variant tuned_variant(int precision, int max_iter);
 
 }  // namespace jl

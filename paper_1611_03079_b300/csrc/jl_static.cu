@@ -19,12 +19,6 @@
 
 namespace jl {
 
-int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_iter, int precision, int mode,
-               int count_type, bool has_counts, bool has_rgba, bool has_hist, Frame *F, int *prec_out);
-
-// Built-in palette (jl_api.cu).
-int default_palette_bytes(uint8_t *out);
-
 static __device__ __align__(256) uint8_t g_static_scratch[JL_STATIC_SCRATCH_BYTES];
 
 // In host code `g_static_scratch` names a host-side stand-in, not device
@@ -110,7 +104,7 @@ extern "C" int jl_render_static(double cr, double ci, jl_rect rect, int32_t widt
     a.frames = nullptr;
     a.n_frames = 1;
     a.hist_smem = (F.hist_bins && F.max_iter + 1 <= 4096) ? 1 : 0;
-    a.total_chunks = (int64_t)F.H * F.chunks_per_row;
+    a.total_chunks = F.chunk_count;
     a.chunk_counter = counter;
     a.status = status;
     a.cycle_budget = 0;

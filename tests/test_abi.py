@@ -115,3 +115,26 @@ def test_product_does_not_reference_oracle():
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text, path
             assert "jl_oracle" not in text and "jlo_" not in text, path
+
+
+def test_tune_load_rejects_malformed(L, tmp_path):
+    p = tmp_path / "bad.txt"
+    p.write_text("0 0 0 3 3 128 0 1.0\n")  # (ppt 3, unroll 3) is not a variant
+    assert L.jl_tune_load(str(p).encode()) == _lib.JL_EINVAL
+    assert b"malformed" in L.jl_last_error()
+    assert L.jl_tune_load(b"/nonexistent/x") == _lib.JL_EINVAL
+
+
+def test_batch_create_validation(L):
+    import ctypes
+    f = _lib.Frame(0.0, 0.0, _lib.Rect(-2, 2, -2, 2), 16, 16, 100, 0, 0, 2, 0, -1, -1)
+    h = ctypes.c_void_p()
+    # counts offset given but no base pointer
+    rc = L.jl_batch_create(ctypes.byref(f), 1, None, None, None, None, None, ctypes.byref(h))
+    assert rc == _lib.JL_EINVAL and b"base pointer" in L.jl_last_error()
+    # odd uint16 offset
+    f.counts_offset = 1
+    rc = L.jl_batch_create(ctypes.byref(f), 1, ctypes.c_void_p(256), None, None, None, None, ctypes.byref(h))
+    assert rc == _lib.JL_EINVAL and b"even" in L.jl_last_error()
+    rc = L.jl_batch_create(ctypes.byref(f), 0, None, None, None, None, None, ctypes.byref(h))
+    assert rc == _lib.JL_EINVAL
