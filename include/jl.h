@@ -284,6 +284,84 @@ int jl_tune_clear(void);
 int jl_tune_save(const char *path);
 int jl_tune_load(const char *path);
 
+/* ------------------------------------------------------------------------
+ * Learned screening surrogate (the paper's aim of sampling the parameter
+ * space quickly, Sec. 1, with the Mandelbrot set as the roadmap for C,
+ * Sec. 3).  A fixed network maps C to the normalised escape-count histogram of
+ * its Julia frame (128 x 128 over [-2,2]^2, limit 100):
+ *   phi(C) = [sin(2 pi B C), cos(2 pi B C)] with B (32 x 2, row-major) fixed,
+ *   h1 = relu(phi W1^T + b1) (64 -> 256), h2 = relu(h1 W2^T + b2) (256 -> 256),
+ *   p = softmax(h2 W3^T + b3) (256 -> 101);
+ * bfloat16 weights and activations in every matrix product, binary32
+ * accumulation (tcgen05 tensor cores), cross-entropy loss, Adam on binary32
+ * master weights.  Parameter block order (binary32, jl_model_num_params()
+ * values): W1[256x64] b1[256] W2[256x256] b2[256] W3[101x256] b3[101], W
+ * row-major (out x in).  All C arrays are device memory, n x 2 binary32
+ * (real, imaginary); histograms are n x 101 binary32.
+ * ------------------------------------------------------------------------ */
+typedef struct jl_model jl_model;
+
+/* Number of binary32 values in the parameter block (108389). */
+int jl_model_num_params(void);
+
+/* Creates a model on the current device from host arrays: fourier_B (64
+ * floats) and init_params (jl_model_num_params() floats); Adam state zero. */
+int jl_model_create(const float *fourier_B, const float *init_params, jl_model **out);
+void jl_model_destroy(jl_model *md);
+
+/* Copies parameters / Adam moments / step between host and device (NULL
+ * pointers are skipped).  Synchronous. */
+int jl_model_get_state(const jl_model *md, float *params, float *m, float *v, int32_t *step);
+int jl_model_set_state(jl_model *md, const float *params, const float *m, const float *v, const int32_t *step);
+
+/* Forward pass over n values of C: probs (n x 101) and/or score (n, the
+ * entropy of the predicted histogram in nats), either may be NULL.
+ * Asynchronous on `stream`. */
+int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, float *score, void *stream);
+
+/* Loss and gradients (host outputs, NULL skipped) of one batch of n <= 65536
+ * rows against target histograms; no parameter update.  Synchronous. */
+int jl_model_grads(jl_model *md, const float *c, const float *target, int32_t n, float *loss_host, float *grads_host,
+                   void *stream);
+
+/* Adam training: `epochs` passes over n samples in batches of `batch` (the
+ * last partial batch of each pass is dropped).  order: device, epochs x n
+ * sample indices (one permutation per pass, chosen by the caller), or NULL
+ * to take samples in order.  loss_curve: host, `epochs` mean batch losses, or
+ * NULL.  Synchronous. */
+int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const int32_t *order, int32_t epochs,
+             int32_t batch, float lr, float *loss_curve, void *stream);
+
+/* Top-k of n non-negative scores (device), ties broken by the smaller index,
+ * descending: out_idx (k int32) and out_score (k floats, may be NULL).
+ * 1 <= k <= min(n, 16384).  Allocates stream-ordered scratch. */
+int jl_topk(const float *score, int64_t n, int32_t k, int32_t *out_idx, float *out_score, void *stream);
+
+/* Screening: forward over n values of C (score = entropy of the predicted
+ * histogram, written to `score`, n floats), then the top k by score. */
+int jl_survey(jl_model *md, const float *c, int64_t n, int32_t k, int32_t *top_idx, float *top_score, float *score,
+              void *stream);
+
+/* Per-row L1 distance of two histogram arrays (device): out[i] = sum_b |p - q|. */
+int jl_hist_l1(const float *p, int32_t ldp, const float *q, int32_t ldq, int32_t n, int32_t bins, float *out,
+               void *stream);
+
+/* Checkpoint (parameters, Adam moments, step, Fourier matrix) to a
+ * little-endian binary file, and back.  Resuming continues bit-identically. */
+int jl_model_save(const jl_model *md, const char *path);
+int jl_model_load(const char *path, jl_model **out);
+
+/*
+ * The tensor-core product on its own: C[M x N] (binary32, row stride ldc) =
+ * A[M x K] * B[K x N] with bfloat16 operands (device).  a_trans = 0: A is
+ * row-major M x K (A[m*lda + k]); 1: A is stored K x M (A[k*lda + m]).
+ * b_trans = 0: B is stored N x K (B[n*ldb + k]); 1: B is stored K x N
+ * (B[k*ldb + n]).  1 <= N <= 256.  status: device int32 set to JL_ETIMEOUT if
+ * a wait gave up, or NULL.
+ */
+int jl_gemm_bf16(const void *A, int32_t lda, int32_t a_trans, const void *B, int32_t ldb, int32_t b_trans, int32_t M,
+                 int32_t N, int32_t K, float *C, int32_t ldc, int32_t *status, void *stream);
+
 /* Writes the built-in 256-entry RGBA8 palette (1024 bytes) to `out` (host).
  * Entry 255 (never-escaped points) is opaque black. */
 int jl_default_palette(uint8_t *out);

@@ -79,6 +79,20 @@ SIGNATURES = {
     "jl_tune_clear": (ctypes.c_int, []),
     "jl_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "jl_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "jl_model_num_params": (ctypes.c_int, []),
+    "jl_model_create": (ctypes.c_int, [_vp, _vp, _vp]),
+    "jl_model_destroy": (None, [_vp]),
+    "jl_model_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "jl_model_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "jl_model_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp]),
+    "jl_model_grads": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "jl_train": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _i32, _i32, ctypes.c_float, _vp, _vp]),
+    "jl_topk": (ctypes.c_int, [_vp, ctypes.c_int64, _i32, _vp, _vp, _vp]),
+    "jl_survey": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _i32, _vp, _vp, _vp, _vp]),
+    "jl_hist_l1": (ctypes.c_int, [_vp, _i32, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "jl_model_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "jl_model_load": (ctypes.c_int, [ctypes.c_char_p, _vp]),
+    "jl_gemm_bf16": (ctypes.c_int, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp]),
     "jl_render_to_host": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
                                          _vp, _vp]),
 }

@@ -1,0 +1,1219 @@
+// Learned screening surrogate on the sm_103a tensor cores.
+//
+// The network maps C to the normalised escape-count histogram of its Julia
+// frame (128x128 over [-2,2]^2, limit 100), so that many C can be screened
+// before any frame is rendered -- the paper's aim of sampling the parameter
+// space quickly (Sec. 1) with the Mandelbrot set as the roadmap for C
+// (Sec. 3).  Architecture (fixed): phi(C) = [sin 2piBC, cos 2piBC] (B: 32x2),
+// Linear 64->256, ReLU, Linear 256->256, ReLU, Linear 256->101, softmax;
+// bfloat16 weights and activations, binary32 accumulation, cross-entropy
+// against the target histogram, Adam on binary32 master weights.
+//
+// Every matrix product -- forward and backward -- is one launch of
+// `tc_gemm_kernel`: a 128-row tile per CTA, the whole N (<= 256) in one
+// tensor-memory accumulator, K in 64-wide chunks double-buffered in shared
+// memory (K-major core-matrix layout, operands transposed while staging when
+// the global layout is the other way round), tcgen05.mma issued by one
+// thread, completion tracked by tcgen05.commit on mbarriers, and a fused
+// epilogue read back with tcgen05.ld: bias + ReLU -> bf16, plain fp32, ReLU
+// mask -> bf16 + column sums (bias gradients), or softmax with cross-entropy
+// gradient, loss and entropy score.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "jl_internal.h"
+#include "jl_tc.cuh"
+
+namespace jl {
+
+static constexpr int kFreq = 32, kIn = 64, kHid = 256, kBins = 101;
+static constexpr int kBinsPad = 112;  // N of the last product (multiple of 16)
+// Parameter block (binary32, this order): W1[256x64] b1[256] W2[256x256] b2[256] W3[101x256] b3[101]
+static constexpr int kOffW1 = 0;
+static constexpr int kOffB1 = kOffW1 + kHid * kIn;
+static constexpr int kOffW2 = kOffB1 + kHid;
+static constexpr int kOffB2 = kOffW2 + kHid * kHid;
+static constexpr int kOffW3 = kOffB2 + kHid;
+static constexpr int kOffB3 = kOffW3 + kBins * kHid;
+static constexpr int kNumParams = kOffB3 + kBins;  // 108,389
+
+enum Epi { EPI_BIAS_ACT = 0, EPI_F32 = 1, EPI_MASK = 2, EPI_SOFTMAX = 3 };
+
+struct GemmArgs {
+    const __nv_bfloat16 *A;  // trans 0: A[m * lda + k]; trans 1: A[k * lda + m]
+    const __nv_bfloat16 *B;  // trans 0: B[n * ldb + k]; trans 1: B[k * ldb + n]
+    int lda, ldb, a_trans, b_trans;
+    int M, N, K, BN;         // BN: N rounded up to a multiple of 16 (<= 256)
+    const float *bias;       // [N] or NULL
+    int relu;
+    const __nv_bfloat16 *mask;  // EPI_MASK: keep where mask[m * ldm + n] > 0
+    int ldm;
+    __nv_bfloat16 *out_bf16;
+    int ld_out;
+    float *out_f32;
+    int ld_out32;
+    float *colsum;           // [gridDim.x x 256] per-CTA column sums (EPI_MASK, EPI_SOFTMAX with target)
+    // EPI_SOFTMAX
+    const float *target;     // [M x ldt] histogram targets or NULL
+    int ldt;
+    float inv_m;             // 1 / batch rows for the gradient
+    float *loss;             // [gridDim.x] per-CTA sums over rows of -sum_b t_b log p_b
+    float *probs;            // [M x ldp] or NULL
+    int ldp;
+    float *score;            // [M] entropy of p or NULL
+    int32_t *status;         // set to JL_ETIMEOUT if a wait gave up
+};
+
+static constexpr int kBM = 128, kBK = 64;
+static constexpr int kTileA = kBM * kBK * 2;   // 16 KB
+static constexpr int kTileB = 256 * kBK * 2;   // 32 KB
+static constexpr int kStage = kTileA + kTileB;
+static constexpr int kGemmSmem = 2 * kStage + 4 * 256 * 4 + 64;  // stages + column partials + barriers
+static constexpr long long kWaitLimit = 2000000000ll;  // ~1 s at 2 GHz
+
+// Stage rows [row0, row0 + nrows) x k [k0, k0 + 64) of an operand into the
+// K-major core-matrix layout: piece (r, g) (8 consecutive k) at byte
+// ((r/8)*8 + g)*128 + (r%8)*16.  Out-of-range elements are zero.
+__device__ __forceinline__ void stage_operand(uint8_t *dst, const __nv_bfloat16 *src, int ld, int trans, int row0,
+                                              int nrows, int rlim, int k0, int klim)
+{
+    const int pieces = nrows * 8;
+    for (int p = threadIdx.x; p < pieces; p += blockDim.x) {
+        int r, g;
+        if (!trans) {
+            // 8 consecutive threads fill one 128-byte core matrix (no bank conflicts)
+            r = (p >> 6) * 8 + (p & 7);
+            g = (p >> 3) & 7;
+        } else {
+            // consecutive threads take consecutive rows (contiguous in global)
+            r = p % nrows;
+            g = p / nrows;
+        }
+        const int row = row0 + r;
+        const int k = k0 + g * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (row < rlim) {
+            if (!trans) {
+                const __nv_bfloat16 *s = src + (size_t)row * ld + k;
+                if (k + 8 <= klim && ((reinterpret_cast<uintptr_t>(s) & 15) == 0)) {
+                    v = *reinterpret_cast<const uint4 *>(s);
+                } else {
+                    uint16_t e[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        e[i] = (k + i < klim) ? __bfloat16_as_ushort(s[i]) : (uint16_t)0;
+                    v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+                }
+            } else {
+                uint16_t e[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    e[i] = (k + i < klim) ? __bfloat16_as_ushort(src[(size_t)(k + i) * ld + row]) : (uint16_t)0;
+                v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+            }
+        }
+        *reinterpret_cast<uint4 *>(dst + ((r >> 3) * 8 + g) * 128 + (r & 7) * 16) = v;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ GemmArgs g)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *stage0 = sm;
+    float *part = reinterpret_cast<float *>(sm + 2 * kStage);           // [4][256] column partials
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * kStage + 4 * 256 * 4);  // 3 mbarriers
+    uint32_t *holder = reinterpret_cast<uint32_t *>(bars + 3);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM;
+
+    if (warp == 0)
+        tc::tmem_alloc(holder, 256);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bars[0], 1);
+        tc::mbar_init(&bars[1], 1);
+        tc::mbar_init(&bars[2], 1);
+        tc::fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x)
+        part[i] = 0.f;
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t taddr = *holder;
+
+    const uint32_t idesc = tc::idesc_bf16(kBM, (uint32_t)g.BN);
+    const int nk = (g.K + kBK - 1) / kBK;
+    bool ok = true;
+    for (int kc = 0; kc < nk; ++kc) {
+        const int s = kc & 1;
+        uint8_t *sA = stage0 + s * kStage;
+        uint8_t *sB = sA + kTileA;
+        if (kc >= 2) {
+            // buffer s was last read by the MMAs of chunk kc - 2
+            if (!tc::mbar_wait(&bars[s], ((kc - 2) >> 1) & 1, kWaitLimit))
+                ok = false;
+        }
+        stage_operand(sA, g.A, g.lda, g.a_trans, m0, kBM, g.M, kc * kBK, g.K);
+        stage_operand(sB, g.B, g.ldb, g.b_trans, 0, g.BN, g.N, kc * kBK, g.K);
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::tc_fence_after();
+            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+                const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, 1024);
+                const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, 1024);
+                tc::mma_bf16(taddr, ad, bd, idesc, (kc | kk) != 0);
+            }
+            tc::mma_commit(&bars[s]);
+        }
+    }
+    if (threadIdx.x == 0)
+        tc::mma_commit(&bars[2]);
+    if (!tc::mbar_wait(&bars[2], 0, kWaitLimit))
+        ok = false;
+    if (!ok && g.status)
+        atomicExch(g.status, (int32_t)JL_ETIMEOUT);
+    tc::tc_fence_after();
+
+    // ---------------- epilogue: this thread owns tile row `r` ----------------
+    const int r = warp * 32 + lane;
+    const int row = m0 + r;
+    const bool in = row < g.M;
+    const uint32_t tw = taddr + ((uint32_t)(warp * 32) << 16);
+
+    if constexpr (EPI == EPI_SOFTMAX) {
+        float mx = -INFINITY;
+        for (int c0 = 0; c0 < g.BN; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tw + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = c0 + j;
+                if (col < g.N)
+                    mx = fmaxf(mx, v[j] + g.bias[col]);
+            }
+        }
+        float sum = 0.f;
+        for (int c0 = 0; c0 < g.BN; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tw + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = c0 + j;
+                if (col < g.N)
+                    sum += expf(v[j] + g.bias[col] - mx);
+            }
+        }
+        const float inv = 1.f / sum;
+        const float lse = mx + logf(sum);
+        float ce = 0.f, ent = 0.f;
+        for (int c0 = 0; c0 < g.BN; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tw + c0, v);
+            float d[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = c0 + j;
+                d[j] = 0.f;
+                if (col < g.N) {
+                    const float z = v[j] + g.bias[col];
+                    const float p = expf(z - mx) * inv;
+                    const float lp = z - lse;
+                    if (p > 0.f)
+                        ent -= p * lp;
+                    if (in && g.probs)
+                        g.probs[(size_t)row * g.ldp + col] = p;
+                    if (g.target) {
+                        const float t = in ? g.target[(size_t)row * g.ldt + col] : 0.f;
+                        if (in) {
+                            ce -= t * lp;
+                            d[j] = (p - t) * g.inv_m;
+                        }
+                    }
+                }
+            }
+            if (g.target) {
+                if (in && g.out_bf16) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < g.BN)
+                            g.out_bf16[(size_t)row * g.ld_out + c0 + j] = __float2bfloat16_rn(d[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float s = warp_sum(d[j]);
+                    if (lane == 0 && c0 + j < 256)
+                        part[warp * 256 + c0 + j] = s;
+                }
+            }
+        }
+        if (in && g.score)
+            g.score[row] = ent;
+        if (g.target && g.loss) {
+            const float s = warp_sum(in ? ce : 0.f);
+            __shared__ float lw[4];
+            if (lane == 0)
+                lw[warp] = s;
+            __syncthreads();
+            if (threadIdx.x == 0)
+                g.loss[blockIdx.x] = (lw[0] + lw[1]) + (lw[2] + lw[3]);
+        }
+    } else {
+        for (int c0 = 0; c0 < g.BN; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tw + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = c0 + j;
+                float x = v[j];
+                if (col >= g.N || !in) {
+                    x = 0.f;
+                } else {
+                    if (g.bias)
+                        x += g.bias[col];
+                    if constexpr (EPI == EPI_BIAS_ACT) {
+                        if (g.relu)
+                            x = fmaxf(x, 0.f);
+                    }
+                    if constexpr (EPI == EPI_MASK) {
+                        const float mk = __bfloat162float(g.mask[(size_t)row * g.ldm + col]);
+                        x = (mk > 0.f) ? x : 0.f;
+                    }
+                }
+                v[j] = x;
+            }
+            if (in) {
+                if constexpr (EPI == EPI_F32) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < g.N)
+                            g.out_f32[(size_t)row * g.ld_out32 + c0 + j] = v[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < g.N)
+                            g.out_bf16[(size_t)row * g.ld_out + c0 + j] = __float2bfloat16_rn(v[j]);
+                }
+            }
+            if constexpr (EPI == EPI_MASK) {
+                if (g.colsum) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float s = warp_sum(v[j]);
+                        if (lane == 0)
+                            part[warp * 256 + c0 + j] = s;
+                    }
+                }
+            }
+        }
+    }
+
+    if ((EPI == EPI_MASK || EPI == EPI_SOFTMAX) && g.colsum) {
+        // deterministic: per-CTA partial row, summed in a fixed order later
+        __syncthreads();
+        for (int c = threadIdx.x; c < g.N; c += blockDim.x)
+            g.colsum[(size_t)blockIdx.x * 256 + c] = (part[c] + part[256 + c]) + (part[512 + c] + part[768 + c]);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        tc::tmem_dealloc(taddr, 256);
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels: features, Adam, weight casts, gathers, histogram L1.
+// ---------------------------------------------------------------------------
+// phi[i] = [sin(2 pi t_j), cos(2 pi t_j)], t_j = B_j . C_i, j < 32 (bf16 out).
+// Optional gather: row i takes C[idx[i]].
+__global__ void features_kernel(const float *__restrict__ c, const int32_t *__restrict__ idx, int64_t n,
+                                const float *__restrict__ Bm, __nv_bfloat16 *__restrict__ phi)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t >> 5;
+    const int j = (int)(t & 31);
+    if (i >= n)
+        return;
+    const int64_t src = idx ? idx[i] : i;
+    const float cr = c[2 * src], ci = c[2 * src + 1];
+    const float tj = Bm[2 * j] * cr + Bm[2 * j + 1] * ci;
+    float s, co;
+    sincospif(2.f * tj, &s, &co);
+    phi[i * kIn + j] = __float2bfloat16_rn(s);
+    phi[i * kIn + kFreq + j] = __float2bfloat16_rn(co);
+}
+
+__global__ void gather_rows_kernel(const float *__restrict__ src, const int32_t *__restrict__ idx, int n, int cols,
+                                   float *__restrict__ dst)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * cols)
+        return;
+    const int i = (int)(t / cols), j = (int)(t % cols);
+    dst[t] = src[(size_t)idx[i] * cols + j];
+}
+
+__global__ void cast_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *__restrict__ wb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // bf16 copies of W1, W2, W3 stored contiguously in that order
+    if (i < kHid * kIn)
+        wb[i] = __float2bfloat16_rn(p[kOffW1 + i]);
+    else if (i < kHid * kIn + kHid * kHid)
+        wb[i] = __float2bfloat16_rn(p[kOffW2 + (i - kHid * kIn)]);
+    else if (i < kHid * kIn + kHid * kHid + kBins * kHid)
+        wb[i] = __float2bfloat16_rn(p[kOffW3 + (i - kHid * kIn - kHid * kHid)]);
+}
+
+// Adam on the whole parameter block; the step counter lives in device memory
+// so a captured graph can replay steps.  Also refreshes the bf16 copies.
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ grad, float *__restrict__ m,
+                            float *__restrict__ v, __nv_bfloat16 *__restrict__ wb, int32_t *__restrict__ step,
+                            float lr, float beta1, float beta2, float eps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = *step + 1;
+    if (i < kNumParams) {
+        const float g = grad[i];
+        const float mi = beta1 * m[i] + (1.f - beta1) * g;
+        const float vi = beta2 * v[i] + (1.f - beta2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        const float bc1 = 1.f - powf(beta1, (float)t);
+        const float bc2 = 1.f - powf(beta2, (float)t);
+        const float upd = lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        const float w = p[i] - upd;
+        p[i] = w;
+        int wi = -1;
+        if (i < kOffB1)
+            wi = i - kOffW1;
+        else if (i >= kOffW2 && i < kOffB2)
+            wi = kHid * kIn + (i - kOffW2);
+        else if (i >= kOffW3 && i < kOffB3)
+            wi = kHid * kIn + kHid * kHid + (i - kOffW3);
+        if (wi >= 0)
+            wb[wi] = __float2bfloat16_rn(w);
+    }
+}
+
+// out[c] = sum over r < rows of part[r * stride + c], in row order (deterministic).
+__global__ void partial_reduce_kernel(const float *__restrict__ part, int rows, int cols, int stride,
+                                      float *__restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols)
+        return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r)
+        s += part[(size_t)r * stride + c];
+    out[c] = s;
+}
+
+__global__ void step_increment_kernel(int32_t *step)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        *step += 1;
+}
+
+// L1[i] = sum_b |p[i][b] - q[i][b]| over `bins` columns.
+__global__ void hist_l1_kernel(const float *__restrict__ p, int ldp, const float *__restrict__ q, int ldq, int n,
+                               int bins, float *__restrict__ out)
+{
+    const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n)
+        return;
+    float s = 0.f;
+    for (int b = lane; b < bins; b += 32)
+        s += fabsf(p[(size_t)i * ldp + b] - q[(size_t)i * ldq + b]);
+    s = warp_sum(s);
+    if (lane == 0)
+        out[i] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Device top-k: k largest non-negative binary32 scores, ties by smaller index.
+// Exact radix select on the float bits (ordered like the values for x >= 0)
+// in three digit levels (11, 11, 10 bits), then all keys above the threshold
+// plus the first `need` ties in index order, then a bitonic sort of the k
+// survivors by (score desc, index asc) in one CTA.
+// ---------------------------------------------------------------------------
+struct TopkState {
+    uint32_t prefix;     // fixed high bits of the threshold so far
+    uint32_t k_rem;      // rank still to find inside the current prefix
+    uint32_t count_gt;   // keys strictly above the final threshold
+    uint32_t need;       // ties to take
+    uint32_t n_sel;      // selected so far (atomic)
+    uint32_t pad[3];
+};
+
+__device__ __forceinline__ uint32_t score_key(float s) { return __float_as_uint(fmaxf(s, 0.f)); }
+
+__global__ void topk_hist_kernel(const float *__restrict__ score, int64_t n, const TopkState *st, int level,
+                                 uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t h[2048];
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+        h[i] = 0;
+    __syncthreads();
+    const int shift = level == 0 ? 21 : (level == 1 ? 10 : 0);
+    const uint32_t dmask = level == 2 ? 0x3FFu : 0x7FFu;
+    const int hi_bits = level == 0 ? 0 : (level == 1 ? 11 : 22);
+    const uint32_t prefix = st->prefix;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = score_key(score[i]);
+        if (hi_bits == 0 || (key >> (32 - hi_bits)) == prefix)
+            atomicAdd(&h[(key >> shift) & dmask], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+        if (h[i])
+            atomicAdd(&hist[i], h[i]);
+}
+
+// One thread: walk the digit histogram from the top to the bin holding rank k_rem.
+__global__ void topk_scan_kernel(uint32_t *hist, TopkState *st, int level)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    const int nb = level == 2 ? 1024 : 2048;
+    const int bits = level == 2 ? 10 : 11;
+    uint32_t above = 0;
+    int b = nb - 1;
+    for (; b > 0; --b) {
+        if (above + hist[b] >= st->k_rem)
+            break;
+        above += hist[b];
+    }
+    st->count_gt += above;
+    st->k_rem -= above;
+    st->prefix = (st->prefix << bits) | (uint32_t)b;
+    if (level == 2)
+        st->need = st->k_rem;
+    for (int i = 0; i < 2048; ++i)
+        hist[i] = 0;
+}
+
+// Keys above the threshold: appended in any order (sorted afterwards).
+__global__ void topk_collect_gt_kernel(const float *__restrict__ score, int64_t n, TopkState *st,
+                                       uint32_t *__restrict__ sel_key, uint32_t *__restrict__ sel_idx)
+{
+    const uint32_t thr = st->prefix;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = score_key(score[i]);
+        if (key > thr) {
+            const uint32_t pos = atomicAdd(&st->n_sel, 1u);
+            sel_key[pos] = key;
+            sel_idx[pos] = (uint32_t)i;
+        }
+    }
+}
+
+// Ties (key == threshold): count per block of a fixed index range.
+__global__ void topk_tie_count_kernel(const float *__restrict__ score, int64_t n, const TopkState *st,
+                                      int64_t per_block, uint32_t *__restrict__ counts)
+{
+    const uint32_t thr = st->prefix;
+    const int64_t b0 = (int64_t)blockIdx.x * per_block;
+    const int64_t b1 = min(n, b0 + per_block);
+    uint32_t c = 0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x)
+        c += (score_key(score[i]) == thr) ? 1u : 0u;
+    __shared__ uint32_t red[32];
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            s += red[w];
+        counts[blockIdx.x] = s;
+    }
+}
+
+// Ties in index order: block-exclusive prefix of the per-block counts, then
+// each block writes its ties whose global tie rank is below `need`.
+__global__ void topk_tie_select_kernel(const float *__restrict__ score, int64_t n, TopkState *st, int64_t per_block,
+                                       const uint32_t *__restrict__ counts, uint32_t *__restrict__ sel_key,
+                                       uint32_t *__restrict__ sel_idx)
+{
+    const uint32_t thr = st->prefix;
+    __shared__ uint32_t base_s;
+    __shared__ uint32_t warp_tot[32];
+    if (threadIdx.x == 0) {
+        uint32_t b = 0;
+        for (int i = 0; i < (int)blockIdx.x; ++i)
+            b += counts[i];
+        base_s = b;
+    }
+    __syncthreads();
+    const uint32_t need = st->need;
+    const uint32_t gt = st->count_gt;
+    uint32_t run = base_s;
+    if (run >= need)
+        return;
+    const int64_t b0 = (int64_t)blockIdx.x * per_block;
+    const int64_t b1 = min(n, b0 + per_block);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t s0 = b0; s0 < b1; s0 += blockDim.x) {
+        const int64_t i = s0 + threadIdx.x;
+        const bool tie = i < b1 && score_key(score[i]) == thr;
+        const unsigned bal = __ballot_sync(0xffffffffu, tie);
+        if (lane == 0)
+            warp_tot[w] = __popc(bal);
+        __syncthreads();
+        uint32_t off = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) {
+            if (q < w)
+                off += warp_tot[q];
+            tot += warp_tot[q];
+        }
+        const uint32_t rank = run + off + __popc(bal & ((1u << lane) - 1u));
+        if (tie && rank < need) {
+            sel_key[gt + rank] = thr;
+            sel_idx[gt + rank] = (uint32_t)i;
+        }
+        run += tot;
+        __syncthreads();
+        if (run >= need)
+            break;
+    }
+}
+
+// Bitonic sort of k <= 16384 (key, index) pairs, key descending then index
+// ascending, in one CTA; writes indices (int32) and scores.
+__global__ void __launch_bounds__(1024) topk_sort_kernel(const uint32_t *__restrict__ sel_key,
+                                                         const uint32_t *__restrict__ sel_idx, int k,
+                                                         int32_t *__restrict__ out_idx, float *__restrict__ out_score)
+{
+    extern __shared__ uint64_t keys[];
+    int P = 1;
+    while (P < k)
+        P <<= 1;
+    // composite: high 32 bits = ~key (ascending = score descending), low = index
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        keys[i] = (i < k) ? (((uint64_t)(~sel_key[i]) << 32) | sel_idx[i]) : ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const uint64_t a = keys[i], b = keys[j];
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        out_idx[i] = (int32_t)(keys[i] & 0xffffffffu);
+        if (out_score)
+            out_score[i] = __uint_as_float(~(uint32_t)(keys[i] >> 32));
+    }
+}
+
+}  // namespace jl
+
+// ---------------------------------------------------------------------------
+// Model object and host orchestration
+// ---------------------------------------------------------------------------
+struct jl_model {
+    int device = -1;
+    float *params = nullptr;   // binary32 master [kNumParams]
+    float *grads = nullptr;
+    float *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *wb = nullptr;  // bf16 W1 | W2 | W3
+    float *B = nullptr;        // Fourier matrix 32 x 2
+    int32_t *step = nullptr;   // Adam step counter (device)
+    float *loss = nullptr;     // device accumulator
+    int32_t *status = nullptr;
+    // work buffers for a batch of up to `cap` rows
+    int cap = 0;
+    __nv_bfloat16 *phi = nullptr, *h1 = nullptr, *h2 = nullptr, *dz = nullptr, *dz2 = nullptr, *dz1 = nullptr;
+    float *tgt = nullptr;
+    float *part = nullptr;      // per-CTA column sums [ctas x 256]
+    float *loss_part = nullptr; // per-CTA loss sums [ctas]
+};
+
+namespace jl {
+
+static bool g_gemm_attr_set[4] = {false, false, false, false};
+
+template <int EPI>
+static cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t st)
+{
+    auto kern = tc_gemm_kernel<EPI>;
+    if (!g_gemm_attr_set[EPI]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+        if (e != cudaSuccess)
+            return e;
+        g_gemm_attr_set[EPI] = true;
+    }
+    const int grid = (a.M + kBM - 1) / kBM;
+    kern<<<grid, 128, kGemmSmem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static GemmArgs gemm_args(const __nv_bfloat16 *A, int lda, int at, const __nv_bfloat16 *B, int ldb, int bt, int M,
+                          int N, int K, int32_t *status)
+{
+    GemmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.A = A;
+    a.lda = lda;
+    a.a_trans = at;
+    a.B = B;
+    a.ldb = ldb;
+    a.b_trans = bt;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.BN = (N + 15) / 16 * 16;
+    a.status = status;
+    return a;
+}
+
+static void free_work(jl_model *md)
+{
+    cudaFree(md->phi);
+    cudaFree(md->h1);
+    cudaFree(md->h2);
+    cudaFree(md->dz);
+    cudaFree(md->dz2);
+    cudaFree(md->dz1);
+    cudaFree(md->tgt);
+    cudaFree(md->part);
+    cudaFree(md->loss_part);
+    md->phi = md->h1 = md->h2 = md->dz = md->dz2 = md->dz1 = nullptr;
+    md->tgt = md->part = md->loss_part = nullptr;
+    md->cap = 0;
+}
+
+static int ensure_work(jl_model *md, int rows, bool train)
+{
+    if (rows <= md->cap && (!train || md->dz))
+        return JL_OK;
+    free_work(md);
+    const size_t r = (size_t)rows;
+    cudaError_t e = cudaMalloc(&md->phi, r * kIn * 2);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&md->h1, r * kHid * 2);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&md->h2, r * kHid * 2);
+    if (e == cudaSuccess && train)
+        e = cudaMalloc(&md->dz, r * kBinsPad * 2);
+    if (e == cudaSuccess && train)
+        e = cudaMalloc(&md->dz2, r * kHid * 2);
+    if (e == cudaSuccess && train)
+        e = cudaMalloc(&md->dz1, r * kHid * 2);
+    if (e == cudaSuccess && train)
+        e = cudaMalloc(&md->tgt, r * kBins * 4);
+    const size_t ctas = (r + kBM - 1) / kBM;
+    if (e == cudaSuccess && train)
+        e = cudaMalloc(&md->part, ctas * 256 * 4);
+    if (e == cudaSuccess && train)
+        e = cudaMalloc(&md->loss_part, ctas * 4);
+    if (e != cudaSuccess) {
+        free_work(md);
+        return cuda_fail(e, "cudaMalloc(surrogate work buffers)");
+    }
+    md->cap = rows;
+    return JL_OK;
+}
+
+// Forward of n rows (n <= cap): phi, h1, h2 and the softmax epilogue.
+static cudaError_t forward_rows(jl_model *md, const float *c, const int32_t *idx, int64_t n, float *probs,
+                                float *score, const float *target, float inv_m, cudaStream_t st)
+{
+    const int64_t threads = n * 32;
+    features_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(c, idx, n, md->B, md->phi);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const __nv_bfloat16 *W1 = md->wb, *W2 = md->wb + kHid * kIn, *W3 = md->wb + kHid * kIn + kHid * kHid;
+    GemmArgs a = gemm_args(md->phi, kIn, 0, W1, kIn, 0, (int)n, kHid, kIn, md->status);
+    a.bias = md->params + kOffB1;
+    a.relu = 1;
+    a.out_bf16 = md->h1;
+    a.ld_out = kHid;
+    if ((e = launch_gemm<EPI_BIAS_ACT>(a, st)) != cudaSuccess)
+        return e;
+    a = gemm_args(md->h1, kHid, 0, W2, kHid, 0, (int)n, kHid, kHid, md->status);
+    a.bias = md->params + kOffB2;
+    a.relu = 1;
+    a.out_bf16 = md->h2;
+    a.ld_out = kHid;
+    if ((e = launch_gemm<EPI_BIAS_ACT>(a, st)) != cudaSuccess)
+        return e;
+    a = gemm_args(md->h2, kHid, 0, W3, kHid, 0, (int)n, kBins, kHid, md->status);
+    a.bias = md->params + kOffB3;
+    a.probs = probs;
+    a.ldp = kBins;
+    a.score = score;
+    a.target = target;
+    a.ldt = kBins;
+    a.inv_m = inv_m;
+    if (target) {
+        a.loss = md->loss_part;
+        a.out_bf16 = md->dz;
+        a.ld_out = kBinsPad;
+        a.colsum = md->part;
+    }
+    if ((e = launch_gemm<EPI_SOFTMAX>(a, st)) != cudaSuccess)
+        return e;
+    if (target) {
+        const int ctas = (int)((n + kBM - 1) / kBM);
+        partial_reduce_kernel<<<1, 128, 0, st>>>(md->part, ctas, kBins, 256, md->grads + kOffB3);
+        partial_reduce_kernel<<<1, 32, 0, st>>>(md->loss_part, ctas, 1, 1, md->loss);
+    }
+    return cudaGetLastError();
+}
+
+// Backward of the batch in md's work buffers (after forward_rows with target).
+static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
+{
+    const __nv_bfloat16 *W2 = md->wb + kHid * kIn, *W3 = md->wb + kHid * kIn + kHid * kHid;
+    // dW3 = dZ^T H2  (101 x 256, K = n)
+    GemmArgs a = gemm_args(md->dz, kBinsPad, 1, md->h2, kHid, 1, kBins, kHid, n, md->status);
+    a.out_f32 = md->grads + kOffW3;
+    a.ld_out32 = kHid;
+    cudaError_t e = launch_gemm<EPI_F32>(a, st);
+    if (e != cudaSuccess)
+        return e;
+    // dZ2 = (dZ W3) * [h2 > 0]   (n x 256, K = 101), db2 = column sums
+    a = gemm_args(md->dz, kBinsPad, 0, W3, kHid, 1, n, kHid, kBins, md->status);
+    a.mask = md->h2;
+    a.ldm = kHid;
+    a.out_bf16 = md->dz2;
+    a.ld_out = kHid;
+    a.colsum = md->part;
+    if ((e = launch_gemm<EPI_MASK>(a, st)) != cudaSuccess)
+        return e;
+    const int ctas = (n + kBM - 1) / kBM;
+    partial_reduce_kernel<<<2, 128, 0, st>>>(md->part, ctas, kHid, 256, md->grads + kOffB2);
+    // dW2 = dZ2^T H1
+    a = gemm_args(md->dz2, kHid, 1, md->h1, kHid, 1, kHid, kHid, n, md->status);
+    a.out_f32 = md->grads + kOffW2;
+    a.ld_out32 = kHid;
+    if ((e = launch_gemm<EPI_F32>(a, st)) != cudaSuccess)
+        return e;
+    // dZ1 = (dZ2 W2) * [h1 > 0], db1
+    a = gemm_args(md->dz2, kHid, 0, W2, kHid, 1, n, kHid, kHid, md->status);
+    a.mask = md->h1;
+    a.ldm = kHid;
+    a.out_bf16 = md->dz1;
+    a.ld_out = kHid;
+    a.colsum = md->part;
+    if ((e = launch_gemm<EPI_MASK>(a, st)) != cudaSuccess)
+        return e;
+    partial_reduce_kernel<<<2, 128, 0, st>>>(md->part, ctas, kHid, 256, md->grads + kOffB1);
+    // dW1 = dZ1^T Phi (256 x 64)
+    a = gemm_args(md->dz1, kHid, 1, md->phi, kIn, 1, kHid, kIn, n, md->status);
+    a.out_f32 = md->grads + kOffW1;
+    a.ld_out32 = kIn;
+    return launch_gemm<EPI_F32>(a, st);
+}
+
+static cudaError_t zero_grads(jl_model *md, cudaStream_t st)
+{
+    // every gradient (and the loss) is overwritten by the backward pass; the
+    // status word is the only thing cleared per step
+    (void)md;
+    (void)st;
+    return cudaSuccess;
+}
+
+static void destroy_model(jl_model *md)
+{
+    if (!md)
+        return;
+    free_work(md);
+    cudaFree(md->params);
+    cudaFree(md->grads);
+    cudaFree(md->m);
+    cudaFree(md->v);
+    cudaFree(md->wb);
+    cudaFree(md->B);
+    cudaFree(md->step);
+    cudaFree(md->loss);
+    cudaFree(md->status);
+    delete md;
+}
+
+static int refresh_bf16(jl_model *md, cudaStream_t st)
+{
+    const int nw = kHid * kIn + kHid * kHid + kBins * kHid;
+    cast_weights_kernel<<<(nw + 255) / 256, 256, 0, st>>>(md->params, md->wb);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? JL_OK : cuda_fail(e, "cast weights");
+}
+
+static int check_status(jl_model *md, cudaStream_t st)
+{
+    int32_t s = 0;
+    cudaError_t e = cudaMemcpyAsync(&s, md->status, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "surrogate status");
+    if (s != 0)
+        return fail(s, "a tensor-core wait gave up (status " + std::to_string(s) + ")");
+    return JL_OK;
+}
+
+}  // namespace jl
+
+using namespace jl;
+
+extern "C" {
+
+int jl_model_num_params(void) { return kNumParams; }
+
+int jl_model_create(const float *fourier_B, const float *init_params, jl_model **out)
+{
+    if (!out || !fourier_B || !init_params)
+        return fail(JL_EINVAL, "fourier_B, init_params and out must not be NULL");
+    *out = nullptr;
+    jl_model *md = new jl_model();
+    cudaError_t e = cudaGetDevice(&md->device);
+    const size_t pb = (size_t)kNumParams * 4;
+    if (e == cudaSuccess) e = cudaMalloc(&md->params, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&md->grads, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&md->m, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&md->v, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&md->wb, (size_t)(kHid * kIn + kHid * kHid + kBins * kHid) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&md->B, kFreq * 2 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&md->step, 4);
+    if (e == cudaSuccess) e = cudaMalloc(&md->loss, 4);
+    if (e == cudaSuccess) e = cudaMalloc(&md->status, 4);
+    if (e == cudaSuccess) e = cudaMemcpy(md->params, init_params, pb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(md->B, fourier_B, kFreq * 2 * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(md->m, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(md->v, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(md->grads, 0, pb);
+    if (e == cudaSuccess) e = cudaMemset(md->step, 0, 4);
+    if (e == cudaSuccess) e = cudaMemset(md->status, 0, 4);
+    if (e != cudaSuccess) {
+        destroy_model(md);
+        return cuda_fail(e, "jl_model_create");
+    }
+    int rc = refresh_bf16(md, nullptr);
+    if (rc == JL_OK && (e = cudaDeviceSynchronize()) != cudaSuccess)
+        rc = cuda_fail(e, "jl_model_create");
+    if (rc != JL_OK) {
+        destroy_model(md);
+        return rc;
+    }
+    *out = md;
+    return JL_OK;
+}
+
+void jl_model_destroy(jl_model *md) { destroy_model(md); }
+
+int jl_model_get_state(const jl_model *md, float *params, float *m, float *v, int32_t *step)
+{
+    if (!md)
+        return fail(JL_EINVAL, "invalid model");
+    const size_t pb = (size_t)kNumParams * 4;
+    cudaError_t e = cudaSuccess;
+    if (params) e = cudaMemcpy(params, md->params, pb, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && m) e = cudaMemcpy(m, md->m, pb, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v) e = cudaMemcpy(v, md->v, pb, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && step) e = cudaMemcpy(step, md->step, 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? JL_OK : cuda_fail(e, "jl_model_get_state");
+}
+
+int jl_model_set_state(jl_model *md, const float *params, const float *m, const float *v, const int32_t *step)
+{
+    if (!md)
+        return fail(JL_EINVAL, "invalid model");
+    const size_t pb = (size_t)kNumParams * 4;
+    cudaError_t e = cudaSuccess;
+    if (params) e = cudaMemcpy(md->params, params, pb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m) e = cudaMemcpy(md->m, m, pb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && v) e = cudaMemcpy(md->v, v, pb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && step) e = cudaMemcpy(md->step, step, 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "jl_model_set_state");
+    int rc = refresh_bf16(md, nullptr);
+    if (rc == JL_OK && (e = cudaDeviceSynchronize()) != cudaSuccess)
+        rc = cuda_fail(e, "jl_model_set_state");
+    return rc;
+}
+
+int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, float *score, void *stream)
+{
+    if (!md || !c || n < 1)
+        return fail(JL_EINVAL, "invalid arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t chunk = 1 << 16;
+    int rc = ensure_work(md, (int)std::min<int64_t>(n, chunk), false);
+    if (rc != JL_OK)
+        return rc;
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t rows = std::min<int64_t>(chunk, n - r0);
+        cudaError_t e = forward_rows(md, c + 2 * r0, nullptr, rows, probs ? probs + r0 * kBins : nullptr,
+                                     score ? score + r0 : nullptr, nullptr, 0.f, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "surrogate forward");
+    }
+    return JL_OK;
+}
+
+int jl_model_grads(jl_model *md, const float *c, const float *target, int32_t n, float *loss_host, float *grads_host,
+                   void *stream)
+{
+    if (!md || !c || !target || n < 1)
+        return fail(JL_EINVAL, "invalid arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_work(md, n, true);
+    if (rc != JL_OK)
+        return rc;
+    cudaError_t e = zero_grads(md, st);
+    if (e == cudaSuccess)
+        e = forward_rows(md, c, nullptr, n, nullptr, nullptr, target, 1.f / (float)n, st);
+    if (e == cudaSuccess)
+        e = backward_rows(md, n, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "surrogate gradients");
+    rc = check_status(md, st);
+    if (rc != JL_OK)
+        return rc;
+    if (loss_host) {
+        float s = 0.f;
+        if ((e = cudaMemcpy(&s, md->loss, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "loss copy");
+        *loss_host = s / (float)n;
+    }
+    if (grads_host && (e = cudaMemcpy(grads_host, md->grads, (size_t)kNumParams * 4, cudaMemcpyDeviceToHost)) !=
+                          cudaSuccess)
+        return cuda_fail(e, "gradient copy");
+    return JL_OK;
+}
+
+int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const int32_t *order, int32_t epochs,
+             int32_t batch, float lr, float *loss_curve, void *stream)
+{
+    if (!md || !c || !hist || n < 1 || epochs < 1 || batch < 1 || batch > n || !(lr > 0.f))
+        return fail(JL_EINVAL, "invalid arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = ensure_work(md, batch, true);
+    if (rc != JL_OK)
+        return rc;
+    const int steps = n / batch;  // the last partial batch of an epoch is dropped
+    const int nparam_blocks = (kNumParams + 255) / 256;
+    for (int ep = 0; ep < epochs; ++ep) {
+        float ep_loss = 0.f;
+        for (int s = 0; s < steps; ++s) {
+            const int32_t *idx = order ? order + (size_t)ep * n + (size_t)s * batch : nullptr;
+            const float *cb = order ? c : c + 2 * (size_t)s * batch;
+            const float *tb;
+            cudaError_t e = zero_grads(md, st);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "zero gradients");
+            if (idx) {
+                const int64_t tt = (int64_t)batch * kBins;
+                gather_rows_kernel<<<(unsigned)((tt + 255) / 256), 256, 0, st>>>(hist, idx, batch, kBins, md->tgt);
+                tb = md->tgt;
+            } else {
+                tb = hist + (size_t)s * batch * kBins;
+            }
+            e = forward_rows(md, cb, idx, batch, nullptr, nullptr, tb, 1.f / (float)batch, st);
+            if (e == cudaSuccess)
+                e = backward_rows(md, batch, st);
+            if (e == cudaSuccess) {
+                adam_kernel<<<nparam_blocks, 256, 0, st>>>(md->params, md->grads, md->m, md->v, md->wb, md->step, lr,
+                                                           0.9f, 0.999f, 1e-8f);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) {
+                step_increment_kernel<<<1, 32, 0, st>>>(md->step);
+                e = cudaGetLastError();
+            }
+            if (e != cudaSuccess)
+                return cuda_fail(e, "training step");
+            if (loss_curve) {
+                float l = 0.f;
+                e = cudaMemcpyAsync(&l, md->loss, 4, cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess)
+                    e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess)
+                    return cuda_fail(e, "loss readback");
+                ep_loss += l / (float)batch;
+            }
+        }
+        if (loss_curve)
+            loss_curve[ep] = ep_loss / (float)steps;
+    }
+    return check_status(md, st);
+}
+
+int jl_topk(const float *score, int64_t n, int32_t k, int32_t *out_idx, float *out_score, void *stream)
+{
+    if (!score || !out_idx || n < 1 || k < 1 || k > n || k > 16384 || n > (int64_t)0x7fffffff)
+        return fail(JL_EINVAL, "jl_topk: need 1 <= k <= min(n, 16384), n < 2^31");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t per_block = 8192;
+    const int nblk = (int)((n + per_block - 1) / per_block);
+    const size_t bytes = 2048 * 4 + sizeof(TopkState) + (size_t)nblk * 4 + 2 * (size_t)k * 4 + 256;
+    uint8_t *w = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&w), bytes, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMallocAsync(topk)");
+    uint32_t *hist = reinterpret_cast<uint32_t *>(w);
+    TopkState *state = reinterpret_cast<TopkState *>(w + 2048 * 4);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(w + 2048 * 4 + sizeof(TopkState));
+    uint32_t *sel_key = counts + nblk;
+    uint32_t *sel_idx = sel_key + k;
+    TopkState init;
+    memset(&init, 0, sizeof(init));
+    init.k_rem = (uint32_t)k;
+    int rc = JL_OK;
+    do {
+        if ((e = cudaMemsetAsync(hist, 0, 2048 * 4, st)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        const int grid = 148 * 4;
+        for (int level = 0; level < 3 && e == cudaSuccess; ++level) {
+            topk_hist_kernel<<<grid, 256, 0, st>>>(score, n, state, level, hist);
+            topk_scan_kernel<<<1, 32, 0, st>>>(hist, state, level);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) break;
+        topk_collect_gt_kernel<<<grid, 256, 0, st>>>(score, n, state, sel_key, sel_idx);
+        topk_tie_count_kernel<<<nblk, 256, 0, st>>>(score, n, state, per_block, counts);
+        topk_tie_select_kernel<<<nblk, 256, 0, st>>>(score, n, state, per_block, counts, sel_key, sel_idx);
+        int P = 1;
+        while (P < k)
+            P <<= 1;
+        const size_t smem = (size_t)P * 8;
+        if ((e = cudaFuncSetAttribute(topk_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            break;
+        topk_sort_kernel<<<1, 1024, smem, st>>>(sel_key, sel_idx, k, out_idx, out_score);
+        e = cudaGetLastError();
+    } while (0);
+    if (e != cudaSuccess)
+        rc = cuda_fail(e, "jl_topk");
+    cudaError_t e2 = cudaFreeAsync(w, st);
+    if (rc == JL_OK && e2 != cudaSuccess)
+        rc = cuda_fail(e2, "cudaFreeAsync(topk)");
+    return rc;
+}
+
+int jl_survey(jl_model *md, const float *c, int64_t n, int32_t k, int32_t *top_idx, float *top_score, float *score,
+              void *stream)
+{
+    if (!md || !c || n < 1 || !top_idx || !score)
+        return fail(JL_EINVAL, "invalid arguments");
+    int rc = jl_model_forward(md, c, n, nullptr, score, stream);
+    if (rc != JL_OK)
+        return rc;
+    return jl_topk(score, n, k, top_idx, top_score, stream);
+}
+
+int jl_gemm_bf16(const void *A, int32_t lda, int32_t a_trans, const void *B, int32_t ldb, int32_t b_trans, int32_t M,
+                 int32_t N, int32_t K, float *C, int32_t ldc, int32_t *status, void *stream)
+{
+    if (!A || !B || !C || M < 1 || N < 1 || N > 256 || K < 1 || ldc < N || lda < 1 || ldb < 1)
+        return fail(JL_EINVAL, "jl_gemm_bf16: need M, K >= 1, 1 <= N <= 256, ldc >= N");
+    GemmArgs a = gemm_args(static_cast<const __nv_bfloat16 *>(A), lda, a_trans ? 1 : 0,
+                           static_cast<const __nv_bfloat16 *>(B), ldb, b_trans ? 1 : 0, M, N, K, status);
+    a.out_f32 = C;
+    a.ld_out32 = ldc;
+    cudaError_t e = launch_gemm<EPI_F32>(a, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? JL_OK : cuda_fail(e, "jl_gemm_bf16");
+}
+
+int jl_hist_l1(const float *p, int32_t ldp, const float *q, int32_t ldq, int32_t n, int32_t bins, float *out,
+               void *stream)
+{
+    if (!p || !q || !out || n < 1 || bins < 1 || ldp < bins || ldq < bins)
+        return fail(JL_EINVAL, "invalid arguments");
+    hist_l1_kernel<<<(n + 7) / 8, 256, 0, static_cast<cudaStream_t>(stream)>>>(p, ldp, q, ldq, n, bins, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? JL_OK : cuda_fail(e, "jl_hist_l1");
+}
+
+// Checkpoint: little-endian binary with a header; params, Adam m and v, step,
+// Fourier matrix.  Resuming from it continues training bit-identically.
+int jl_model_save(const jl_model *md, const char *path)
+{
+    if (!md || !path)
+        return fail(JL_EINVAL, "invalid arguments");
+    std::vector<float> p(kNumParams), m(kNumParams), v(kNumParams), B(kFreq * 2);
+    int32_t step = 0;
+    int rc = jl_model_get_state(md, p.data(), m.data(), v.data(), &step);
+    if (rc != JL_OK)
+        return rc;
+    cudaError_t e = cudaMemcpy(B.data(), md->B, B.size() * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "save: Fourier matrix");
+    FILE *fp = fopen(path, "wb");
+    if (!fp)
+        return fail(JL_EINVAL, std::string("cannot open ") + path);
+    const char magic[8] = {'J', 'L', 'M', 'L', 'P', '0', '0', '1'};
+    const int32_t hdr[4] = {kNumParams, kFreq, step, 0};
+    bool okw = fwrite(magic, 1, 8, fp) == 8 && fwrite(hdr, 4, 4, fp) == 4 &&
+               fwrite(B.data(), 4, B.size(), fp) == B.size() && fwrite(p.data(), 4, p.size(), fp) == p.size() &&
+               fwrite(m.data(), 4, m.size(), fp) == m.size() && fwrite(v.data(), 4, v.size(), fp) == v.size();
+    fclose(fp);
+    return okw ? JL_OK : fail(JL_EINVAL, "short write");
+}
+
+int jl_model_load(const char *path, jl_model **out)
+{
+    if (!path || !out)
+        return fail(JL_EINVAL, "invalid arguments");
+    *out = nullptr;
+    FILE *fp = fopen(path, "rb");
+    if (!fp)
+        return fail(JL_EINVAL, std::string("cannot open ") + path);
+    char magic[8];
+    int32_t hdr[4];
+    std::vector<float> p(kNumParams), m(kNumParams), v(kNumParams), B(kFreq * 2);
+    bool okr = fread(magic, 1, 8, fp) == 8 && memcmp(magic, "JLMLP001", 8) == 0 && fread(hdr, 4, 4, fp) == 4 &&
+               hdr[0] == kNumParams && hdr[1] == kFreq && fread(B.data(), 4, B.size(), fp) == B.size() &&
+               fread(p.data(), 4, p.size(), fp) == p.size() && fread(m.data(), 4, m.size(), fp) == m.size() &&
+               fread(v.data(), 4, v.size(), fp) == v.size();
+    fclose(fp);
+    if (!okr)
+        return fail(JL_EINVAL, "not a jl surrogate checkpoint (or truncated)");
+    jl_model *md = nullptr;
+    int rc = jl_model_create(B.data(), p.data(), &md);
+    if (rc != JL_OK)
+        return rc;
+    rc = jl_model_set_state(md, nullptr, m.data(), v.data(), &hdr[2]);
+    if (rc != JL_OK) {
+        destroy_model(md);
+        return rc;
+    }
+    *out = md;
+    return JL_OK;
+}
+
+}  // extern "C"
