@@ -315,9 +315,14 @@ int jl_model_get_state(const jl_model *md, float *params, float *m, float *v, in
 int jl_model_set_state(jl_model *md, const float *params, const float *m, const float *v, const int32_t *step);
 
 /* Forward pass over n values of C: probs (n x 101) and/or score (n, the
- * entropy of the predicted histogram in nats), either may be NULL.
- * Asynchronous on `stream`. */
+ * entropy of the predicted histogram in nats), either may be NULL.  One
+ * persistent fused kernel (features, three tensor-core products, softmax)
+ * with activations kept on chip.  Asynchronous on `stream`. */
 int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, float *score, void *stream);
+
+/* The same forward built from one tensor-core product launch per layer (the
+ * layers training uses); a reference for jl_model_forward's fused kernel. */
+int jl_model_forward_layered(jl_model *md, const float *c, int64_t n, float *probs, float *score, void *stream);
 
 /* Loss and gradients (host outputs, NULL skipped) of one batch of n <= 65536
  * rows against target histograms; no parameter update.  Synchronous. */
@@ -327,10 +332,12 @@ int jl_model_grads(jl_model *md, const float *c, const float *target, int32_t n,
 /* Adam training: `epochs` passes over n samples in batches of `batch` (the
  * last partial batch of each pass is dropped).  order: device, epochs x n
  * sample indices (one permutation per pass, chosen by the caller), or NULL
- * to take samples in order.  loss_curve: host, `epochs` mean batch losses, or
- * NULL.  Synchronous. */
+ * to take samples in order.  The learning rate follows a cosine from lr at
+ * the first step of the call to lr_final after the last (lr_final == lr:
+ * constant).  loss_curve: host, `epochs` mean batch losses, or NULL.
+ * Synchronous. */
 int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const int32_t *order, int32_t epochs,
-             int32_t batch, float lr, float *loss_curve, void *stream);
+             int32_t batch, float lr, float lr_final, float *loss_curve, void *stream);
 
 /* Top-k of n non-negative scores (device), ties broken by the smaller index,
  * descending: out_idx (k int32) and out_score (k floats, may be NULL).

@@ -85,8 +85,9 @@ SIGNATURES = {
     "jl_model_get_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "jl_model_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "jl_model_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp]),
+    "jl_model_forward_layered": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp]),
     "jl_model_grads": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, _vp]),
-    "jl_train": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _i32, _i32, ctypes.c_float, _vp, _vp]),
+    "jl_train": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float, _vp, _vp]),
     "jl_topk": (ctypes.c_int, [_vp, ctypes.c_int64, _i32, _vp, _vp, _vp]),
     "jl_survey": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _i32, _vp, _vp, _vp, _vp]),
     "jl_hist_l1": (ctypes.c_int, [_vp, _i32, _vp, _i32, _i32, _i32, _vp, _vp]),

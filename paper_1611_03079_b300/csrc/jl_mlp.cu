@@ -341,6 +341,321 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
 }
 
 // ---------------------------------------------------------------------------
+// Fused forward for screening: features -> three products -> softmax and
+// entropy in one persistent kernel, activations kept on the SM.
+// Weights are pre-packed in global memory as shared-memory images of the
+// K-major core-matrix layout: W1 as one 256x64 image (resident per CTA), W2
+// as four 256x64 K-chunks and W3 as four 112x64 K-chunks, streamed through a
+// double buffer with cp.async.bulk (completion as mbarrier transaction bytes).
+// ---------------------------------------------------------------------------
+static constexpr int kImgW = 256 * 64 * 2;                 // 32 KB: 256 rows x 64 k
+static constexpr int kImgW3 = kBinsPad * 64 * 2;           // 14 KB: 112 rows x 64 k
+static constexpr int kPackElems = (kImgW + 4 * kImgW + 4 * kImgW3) / 2;  // bf16 elements
+// shared-memory map of the fused kernel (bytes)
+static constexpr int kFsW1 = 0;
+static constexpr int kFsPhi = kFsW1 + kImgW;               // 128 x 64
+static constexpr int kFsH = kFsPhi + kBM * kIn * 2;        // 128 x 256
+static constexpr int kFsWB = kFsH + kBM * kHid * 2;        // 2 x 32 KB
+static constexpr int kFsBias = kFsWB + 2 * kImgW;          // b1, b2, b3 (fp32), B (64 fp32)
+static constexpr int kFsBar = kFsBias + (kHid + kHid + kBinsPad + 64) * 4;
+static constexpr int kFusedSmem = kFsBar + 8 * 8 + 16;
+
+// One thread per 16-byte piece of the packed images.
+__global__ void pack_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *__restrict__ out)
+{
+    const int piece = blockIdx.x * blockDim.x + threadIdx.x;
+    const int total = kPackElems / 8;
+    if (piece >= total)
+        return;
+    // which image
+    int img, local;
+    const int per_w = kImgW / 16, per_w3 = kImgW3 / 16;
+    if (piece < per_w) {
+        img = 0;
+        local = piece;
+    } else if (piece < 5 * per_w) {
+        img = 1 + (piece - per_w) / per_w;
+        local = (piece - per_w) % per_w;
+    } else {
+        img = 5 + (piece - 5 * per_w) / per_w3;
+        local = (piece - 5 * per_w) % per_w3;
+    }
+    // inverse of offset ((r/8)*8 + g)*128 + (r%8)*16 for a 64-wide K chunk
+    const int cm = local >> 3, rr = local & 7;
+    const int r = (cm >> 3) * 8 + rr;
+    const int g = cm & 7;
+    const float *src;
+    int rows, ld, k0;
+    if (img == 0) {
+        src = p + kOffW1; rows = kHid; ld = kIn; k0 = 0;
+    } else if (img <= 4) {
+        src = p + kOffW2; rows = kHid; ld = kHid; k0 = (img - 1) * 64;
+    } else {
+        src = p + kOffW3; rows = kBins; ld = kHid; k0 = (img - 5) * 64;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const float v = (r < rows) ? src[(size_t)r * ld + k0 + g * 8 + e] : 0.f;
+        out[(size_t)piece * 8 + e] = __float2bfloat16_rn(v);
+    }
+}
+
+struct FusedArgs {
+    const float *c;            // n x 2
+    int64_t n;
+    const __nv_bfloat16 *pack; // packed images
+    const float *params;       // binary32 parameter block (biases)
+    const float *B;            // Fourier matrix 32 x 2
+    float *probs;              // n x 101 or NULL
+    float *score;              // n or NULL
+    int32_t *status;
+};
+
+__global__ void __launch_bounds__(128) fused_forward_kernel(const __grid_constant__ FusedArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *sW1 = sm + kFsW1;
+    uint8_t *sPhi = sm + kFsPhi;
+    uint8_t *sH = sm + kFsH;
+    uint8_t *sWB = sm + kFsWB;
+    float *b1 = reinterpret_cast<float *>(sm + kFsBias);
+    float *b2 = b1 + kHid;
+    float *b3 = b2 + kHid;
+    float *Bs = b3 + kBinsPad;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kFsBar);  // [2]
+    uint64_t *empty = full + 2;                                  // [2]
+    uint64_t *acc = full + 4;
+    uint64_t *w1bar = full + 5;
+    uint32_t *holder = reinterpret_cast<uint32_t *>(full + 8);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (a.n + kBM - 1) / kBM;
+    const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);  // tiles of this CTA
+    if (blockIdx.x >= ntiles)
+        return;
+
+    if (warp == 0)
+        tc::tmem_alloc(holder, 256);
+    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+        b1[i] = a.params[kOffB1 + i];
+        b2[i] = a.params[kOffB2 + i];
+    }
+    for (int i = threadIdx.x; i < kBinsPad; i += blockDim.x)
+        b3[i] = i < kBins ? a.params[kOffB3 + i] : 0.f;
+    if (threadIdx.x < 64)
+        Bs[threadIdx.x] = a.B[threadIdx.x];
+    const uint8_t *gpack = reinterpret_cast<const uint8_t *>(a.pack);
+    // chunk q of this CTA's stream: j = q % 8: 0..3 -> W2 chunk j, 4..7 -> W3 chunk j-4
+    auto chunk_src = [&](int q, uint32_t &bytes) -> const uint8_t * {
+        const int j = q & 7;
+        if (j < 4) {
+            bytes = kImgW;
+            return gpack + kImgW + (size_t)j * kImgW;
+        }
+        bytes = kImgW3;
+        return gpack + 5 * (size_t)kImgW + (size_t)(j - 4) * kImgW3;
+    };
+    const int total_chunks = my_tiles * 8;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(acc, 1);
+        tc::mbar_init(w1bar, 1);
+        tc::fence_mbar_init();
+        tc::fence_proxy_async_smem();
+        tc::bulk_load(sW1, gpack, kImgW, w1bar);
+        uint32_t bytes;
+        const uint8_t *src = chunk_src(0, bytes);
+        tc::bulk_load(sWB, src, bytes, &full[0]);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t taddr = *holder;
+    const uint32_t tw = taddr + ((uint32_t)(warp * 32) << 16);
+    bool ok = true;
+    uint32_t acc_uses = 0;
+
+    // thread 0: consume chunk q with 4 MMAs of K = 16, then refill the other
+    // buffer with chunk q + 1 once its previous occupant (q - 1) is consumed.
+    auto run_chunk = [&](int q, uint32_t a_base, uint32_t n_rows, bool first) {
+        const int b = q & 1;
+        if (!tc::mbar_wait(&full[b], (q >> 1) & 1, kWaitLimit))
+            ok = false;
+        tc::tc_fence_after();
+        const uint32_t idesc = tc::idesc_bf16(kBM, n_rows);
+        const uint32_t bb = tc::smem_u32(sWB + b * kImgW);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = tc::smem_desc(a_base + kk * 256, 128, 4096);
+            const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, 1024);
+            tc::mma_bf16(taddr, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+        }
+        tc::mma_commit(&empty[b]);
+        if (q + 1 < total_chunks) {
+            const int nb = (q + 1) & 1;
+            if (q >= 1 && !tc::mbar_wait(&empty[nb], ((q - 1) >> 1) & 1, kWaitLimit))
+                ok = false;
+            uint32_t bytes;
+            const uint8_t *src = chunk_src(q + 1, bytes);
+            tc::bulk_load(sWB + nb * kImgW, src, bytes, &full[nb]);
+        }
+    };
+
+    for (int it = 0; it < my_tiles; ++it) {
+        const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
+        const int r = threadIdx.x;
+        const int64_t row = tile * kBM + r;
+        const bool in = row < a.n;
+        // ---- features of this thread's row into the Phi image ----
+        {
+            float cr = 0.f, ci = 0.f;
+            if (in) {
+                cr = a.c[2 * row];
+                ci = a.c[2 * row + 1];
+            }
+            uint32_t sv[16], cv[16];
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                float s0, c0, s1, c1;
+                sincospif(2.f * (Bs[2 * j] * cr + Bs[2 * j + 1] * ci), &s0, &c0);
+                sincospif(2.f * (Bs[2 * j + 2] * cr + Bs[2 * j + 3] * ci), &s1, &c1);
+                if (!in) {
+                    s0 = c0 = s1 = c1 = 0.f;
+                }
+                sv[j >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(s0)) |
+                             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(s1)) << 16);
+                cv[j >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(c0)) |
+                             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(c1)) << 16);
+            }
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                *reinterpret_cast<uint4 *>(sPhi + ((r >> 3) * 8 + g) * 128 + (r & 7) * 16) =
+                    make_uint4(sv[4 * g], sv[4 * g + 1], sv[4 * g + 2], sv[4 * g + 3]);
+                *reinterpret_cast<uint4 *>(sPhi + ((r >> 3) * 8 + g + 4) * 128 + (r & 7) * 16) =
+                    make_uint4(cv[4 * g], cv[4 * g + 1], cv[4 * g + 2], cv[4 * g + 3]);
+            }
+        }
+        tc::fence_proxy_async_smem();
+        tc::tc_fence_before();
+        __syncthreads();
+        // ---- product 1: Phi (128 x 64) x W1^T -> D (128 x 256) ----
+        if (threadIdx.x == 0) {
+            tc::tc_fence_after();
+            if (it == 0 && !tc::mbar_wait(w1bar, 0, kWaitLimit))
+                ok = false;
+            const uint32_t a0 = tc::smem_u32(sPhi), b0 = tc::smem_u32(sW1);
+            const uint32_t idesc = tc::idesc_bf16(kBM, kHid);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc::mma_bf16(taddr, tc::smem_desc(a0 + kk * 256, 128, 1024), tc::smem_desc(b0 + kk * 256, 128, 1024),
+                             idesc, kk > 0);
+            tc::mma_commit(acc);
+        }
+        // ---- epilogues 1 and 2 write relu(D + b) as bf16 into the H image ----
+        auto hidden_epilogue = [&](const float *bias) {
+            if (!tc::mbar_wait(acc, acc_uses & 1, kWaitLimit))
+                ok = false;
+            ++acc_uses;
+            tc::tc_fence_after();
+            for (int c0 = 0; c0 < kHid; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tw + c0, v);
+                uint32_t w[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float x0 = fmaxf(v[2 * j] + bias[c0 + 2 * j], 0.f);
+                    const float x1 = fmaxf(v[2 * j + 1] + bias[c0 + 2 * j + 1], 0.f);
+                    w[j] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x0)) |
+                           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x1)) << 16);
+                }
+                const int g = c0 >> 3;
+                *reinterpret_cast<uint4 *>(sH + ((r >> 3) * 32 + g) * 128 + (r & 7) * 16) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(sH + ((r >> 3) * 32 + g + 1) * 128 + (r & 7) * 16) =
+                    make_uint4(w[4], w[5], w[6], w[7]);
+            }
+            tc::fence_proxy_async_smem();
+            tc::tc_fence_before();
+            __syncthreads();
+        };
+        hidden_epilogue(b1);
+        // ---- product 2: H1 (128 x 256) x W2^T, four streamed K-chunks ----
+        if (threadIdx.x == 0) {
+            tc::tc_fence_after();
+            const uint32_t hb = tc::smem_u32(sH);
+            for (int j = 0; j < 4; ++j)
+                run_chunk(it * 8 + j, hb + j * 8 * 128, kHid, j == 0);
+            tc::mma_commit(acc);
+        }
+        hidden_epilogue(b2);
+        // ---- product 3: H2 (128 x 256) x W3^T -> logits (128 x 112) ----
+        if (threadIdx.x == 0) {
+            tc::tc_fence_after();
+            const uint32_t hb = tc::smem_u32(sH);
+            for (int j = 0; j < 4; ++j)
+                run_chunk(it * 8 + 4 + j, hb + j * 8 * 128, kBinsPad, j == 0);
+            tc::mma_commit(acc);
+        }
+        if (!tc::mbar_wait(acc, acc_uses & 1, kWaitLimit))
+            ok = false;
+        ++acc_uses;
+        tc::tc_fence_after();
+        // ---- softmax and entropy of this thread's row ----
+        float mx = -INFINITY;
+        for (int c0 = 0; c0 < kBinsPad; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tw + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (c0 + j < kBins)
+                    mx = fmaxf(mx, v[j] + b3[c0 + j]);
+        }
+        float sum = 0.f;
+        for (int c0 = 0; c0 < kBinsPad; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tw + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (c0 + j < kBins)
+                    sum += expf(v[j] + b3[c0 + j] - mx);
+        }
+        const float inv = 1.f / sum;
+        const float lse = mx + logf(sum);
+        float ent = 0.f;
+        for (int c0 = 0; c0 < kBinsPad; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tw + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = c0 + j;
+                if (col < kBins) {
+                    const float z = v[j] + b3[col];
+                    const float p = expf(z - mx) * inv;
+                    if (p > 0.f)
+                        ent -= p * (z - lse);
+                    if (in && a.probs)
+                        a.probs[(size_t)row * kBins + col] = p;
+                }
+            }
+        }
+        if (in && a.score)
+            a.score[row] = ent;
+        tc::tc_fence_before();
+        __syncthreads();  // TMEM reads done before the next tile's product 1
+    }
+    if (!ok && a.status)
+        atomicExch(a.status, (int32_t)JL_ETIMEOUT);
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        tc::tmem_dealloc(taddr, 256);
+    (void)lane;
+}
+
+// ---------------------------------------------------------------------------
 // Small kernels: features, Adam, weight casts, gathers, histogram L1.
 // ---------------------------------------------------------------------------
 // phi[i] = [sin(2 pi t_j), cos(2 pi t_j)], t_j = B_j . C_i, j < 32 (bf16 out).
@@ -648,6 +963,7 @@ struct jl_model {
     float *grads = nullptr;
     float *m = nullptr, *v = nullptr;
     __nv_bfloat16 *wb = nullptr;  // bf16 W1 | W2 | W3
+    __nv_bfloat16 *wpack = nullptr;  // packed shared-memory images for the fused forward
     float *B = nullptr;        // Fourier matrix 32 x 2
     int32_t *step = nullptr;   // Adam step counter (device)
     float *loss = nullptr;     // device accumulator
@@ -656,6 +972,7 @@ struct jl_model {
     int cap = 0;
     __nv_bfloat16 *phi = nullptr, *h1 = nullptr, *h2 = nullptr, *dz = nullptr, *dz2 = nullptr, *dz1 = nullptr;
     float *tgt = nullptr;
+    float *loss_out = nullptr;  // where the next forward writes its loss sum (NULL: `loss`)
     float *part = nullptr;      // per-CTA column sums [ctas x 256]
     float *loss_part = nullptr; // per-CTA loss sums [ctas]
 };
@@ -789,7 +1106,7 @@ static cudaError_t forward_rows(jl_model *md, const float *c, const int32_t *idx
     if (target) {
         const int ctas = (int)((n + kBM - 1) / kBM);
         partial_reduce_kernel<<<1, 128, 0, st>>>(md->part, ctas, kBins, 256, md->grads + kOffB3);
-        partial_reduce_kernel<<<1, 32, 0, st>>>(md->loss_part, ctas, 1, 1, md->loss);
+        partial_reduce_kernel<<<1, 32, 0, st>>>(md->loss_part, ctas, 1, 1, md->loss_out ? md->loss_out : md->loss);
     }
     return cudaGetLastError();
 }
@@ -858,6 +1175,7 @@ static void destroy_model(jl_model *md)
     cudaFree(md->m);
     cudaFree(md->v);
     cudaFree(md->wb);
+    cudaFree(md->wpack);
     cudaFree(md->B);
     cudaFree(md->step);
     cudaFree(md->loss);
@@ -907,6 +1225,7 @@ int jl_model_create(const float *fourier_B, const float *init_params, jl_model *
     if (e == cudaSuccess) e = cudaMalloc(&md->m, pb);
     if (e == cudaSuccess) e = cudaMalloc(&md->v, pb);
     if (e == cudaSuccess) e = cudaMalloc(&md->wb, (size_t)(kHid * kIn + kHid * kHid + kBins * kHid) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&md->wpack, (size_t)kPackElems * 2);
     if (e == cudaSuccess) e = cudaMalloc(&md->B, kFreq * 2 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&md->step, 4);
     if (e == cudaSuccess) e = cudaMalloc(&md->loss, 4);
@@ -971,6 +1290,43 @@ int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, floa
     if (!md || !c || n < 1)
         return fail(JL_EINVAL, "invalid arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // refresh the packed weight images from the binary32 parameters
+    const int pieces = kPackElems / 8;
+    pack_weights_kernel<<<(pieces + 255) / 256, 256, 0, st>>>(md->params, md->wpack);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(e, "pack weights");
+    static bool attr_set = false;
+    if (!attr_set) {
+        e = cudaFuncSetAttribute(fused_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "fused forward attribute");
+        attr_set = true;
+    }
+    FusedArgs a;
+    a.c = c;
+    a.n = n;
+    a.pack = md->wpack;
+    a.params = md->params;
+    a.B = md->B;
+    a.probs = probs;
+    a.score = score;
+    a.status = md->status;
+    const int64_t tiles = (n + kBM - 1) / kBM;
+    const int sms = device_sm_count();
+    const int grid = (int)std::min<int64_t>(tiles, sms > 0 ? sms : 148);
+    fused_forward_kernel<<<grid, 128, kFusedSmem, st>>>(a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? JL_OK : cuda_fail(e, "fused forward");
+}
+
+// The forward built from the general product kernel (the path training uses);
+// kept as a reference for the fused kernel.
+int jl_model_forward_layered(jl_model *md, const float *c, int64_t n, float *probs, float *score, void *stream)
+{
+    if (!md || !c || n < 1)
+        return fail(JL_EINVAL, "invalid arguments");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t chunk = 1 << 16;
     int rc = ensure_work(md, (int)std::min<int64_t>(n, chunk), false);
     if (rc != JL_OK)
@@ -1017,9 +1373,9 @@ int jl_model_grads(jl_model *md, const float *c, const float *target, int32_t n,
 }
 
 int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const int32_t *order, int32_t epochs,
-             int32_t batch, float lr, float *loss_curve, void *stream)
+             int32_t batch, float lr, float lr_final, float *loss_curve, void *stream)
 {
-    if (!md || !c || !hist || n < 1 || epochs < 1 || batch < 1 || batch > n || !(lr > 0.f))
+    if (!md || !c || !hist || n < 1 || epochs < 1 || batch < 1 || batch > n || !(lr > 0.f) || !(lr_final > 0.f))
         return fail(JL_EINVAL, "invalid arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_work(md, batch, true);
@@ -1027,15 +1383,17 @@ int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const i
         return rc;
     const int steps = n / batch;  // the last partial batch of an epoch is dropped
     const int nparam_blocks = (kNumParams + 255) / 256;
-    for (int ep = 0; ep < epochs; ++ep) {
-        float ep_loss = 0.f;
+    float *loss_steps = nullptr;
+    cudaError_t e = cudaMalloc(&loss_steps, (size_t)steps * 4);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(loss per step)");
+    std::vector<float> hl((size_t)steps);
+    const double total = (double)epochs * steps;
+    for (int ep = 0; ep < epochs && rc == JL_OK; ++ep) {
         for (int s = 0; s < steps; ++s) {
             const int32_t *idx = order ? order + (size_t)ep * n + (size_t)s * batch : nullptr;
             const float *cb = order ? c : c + 2 * (size_t)s * batch;
             const float *tb;
-            cudaError_t e = zero_grads(md, st);
-            if (e != cudaSuccess)
-                return cuda_fail(e, "zero gradients");
             if (idx) {
                 const int64_t tt = (int64_t)batch * kBins;
                 gather_rows_kernel<<<(unsigned)((tt + 255) / 256), 256, 0, st>>>(hist, idx, batch, kBins, md->tgt);
@@ -1043,33 +1401,48 @@ int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const i
             } else {
                 tb = hist + (size_t)s * batch * kBins;
             }
+            md->loss_out = loss_steps + s;
             e = forward_rows(md, cb, idx, batch, nullptr, nullptr, tb, 1.f / (float)batch, st);
+            md->loss_out = nullptr;
             if (e == cudaSuccess)
                 e = backward_rows(md, batch, st);
             if (e == cudaSuccess) {
-                adam_kernel<<<nparam_blocks, 256, 0, st>>>(md->params, md->grads, md->m, md->v, md->wb, md->step, lr,
-                                                           0.9f, 0.999f, 1e-8f);
+                // cosine schedule from lr to lr_final over the steps of this call
+                const double t = ((double)ep * steps + s) / total;
+                const float lr_t = (float)(lr_final + 0.5 * (lr - lr_final) * (1.0 + cos(3.141592653589793 * t)));
+                adam_kernel<<<nparam_blocks, 256, 0, st>>>(md->params, md->grads, md->m, md->v, md->wb, md->step,
+                                                           lr_t, 0.9f, 0.999f, 1e-8f);
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) {
                 step_increment_kernel<<<1, 32, 0, st>>>(md->step);
                 e = cudaGetLastError();
             }
-            if (e != cudaSuccess)
-                return cuda_fail(e, "training step");
-            if (loss_curve) {
-                float l = 0.f;
-                e = cudaMemcpyAsync(&l, md->loss, 4, cudaMemcpyDeviceToHost, st);
-                if (e == cudaSuccess)
-                    e = cudaStreamSynchronize(st);
-                if (e != cudaSuccess)
-                    return cuda_fail(e, "loss readback");
-                ep_loss += l / (float)batch;
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "training step");
+                break;
             }
         }
-        if (loss_curve)
-            loss_curve[ep] = ep_loss / (float)steps;
+        if (rc == JL_OK && loss_curve) {
+            e = cudaMemcpyAsync(hl.data(), loss_steps, (size_t)steps * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "loss readback");
+                break;
+            }
+            double acc = 0.0;
+            for (int s = 0; s < steps; ++s)
+                acc += hl[(size_t)s] / (double)batch;
+            loss_curve[ep] = (float)(acc / steps);
+        }
     }
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(loss_steps);
+    if (rc == JL_OK && e2 != cudaSuccess)
+        rc = cuda_fail(e2, "training");
+    if (rc != JL_OK)
+        return rc;
     return check_status(md, st);
 }
 

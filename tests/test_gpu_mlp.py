@@ -148,7 +148,7 @@ def test_adam_steps_match_oracle(cuda):
     cd, Td = torch.from_numpy(c).cuda(), torch.from_numpy(T).cuda()
     curve = np.zeros(1, np.float32)
     _lib.check(md.L.jl_train(md.h, cd.data_ptr(), Td.data_ptr(), n, None, 1, batch, ctypes.c_float(1e-3),
-                             curve.ctypes.data, None))
+                             ctypes.c_float(1e-3), curve.ctypes.data, None))
     got, m, v, step = md.state()
     assert step == 2
     q = {k: v_.astype(np.float64) for k, v_ in p.items()}
@@ -191,18 +191,41 @@ def test_checkpoint_resume_bit_identical(cuda, tmp_path):
     T = targets(n, seed=4)
     cd, Td = torch.from_numpy(c).cuda(), torch.from_numpy(T).cuda()
     a = Model(p, B)
-    _lib.check(a.L.jl_train(a.h, cd.data_ptr(), Td.data_ptr(), n, None, 1, batch, ctypes.c_float(1e-3), None, None))
+    _lib.check(a.L.jl_train(a.h, cd.data_ptr(), Td.data_ptr(), n, None, 1, batch, ctypes.c_float(1e-3), ctypes.c_float(1e-3), None, None))
     path = str(tmp_path / "ck.bin").encode()
     _lib.check(a.L.jl_model_save(a.h, path))
-    _lib.check(a.L.jl_train(a.h, cd.data_ptr(), Td.data_ptr(), n, None, 1, batch, ctypes.c_float(1e-3), None, None))
+    _lib.check(a.L.jl_train(a.h, cd.data_ptr(), Td.data_ptr(), n, None, 1, batch, ctypes.c_float(1e-3), ctypes.c_float(1e-3), None, None))
     b = Model(p, B)
     b.L.jl_model_destroy(b.h)
     b.h = ctypes.c_void_p()
     _lib.check(b.L.jl_model_load(path, ctypes.byref(b.h)))
-    _lib.check(b.L.jl_train(b.h, cd.data_ptr(), Td.data_ptr(), n, None, 1, batch, ctypes.c_float(1e-3), None, None))
+    _lib.check(b.L.jl_train(b.h, cd.data_ptr(), Td.data_ptr(), n, None, 1, batch, ctypes.c_float(1e-3), ctypes.c_float(1e-3), None, None))
     sa, sb = a.state(), b.state()
     for x, y in zip(sa[:3], sb[:3]):
         assert (x == y).all()
     assert sa[3] == sb[3] == 8
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("n", [1, 127, 50001])
+def test_fused_forward_matches_layered(cuda, n):
+    """The fused screening kernel (one persistent launch) and the per-layer
+    product kernels compute the same network."""
+    import torch
+    p, B = setup_model(5)
+    md = Model(p, B)
+    c = torch.from_numpy(wl.survey_c(n, seed=15)).cuda()
+    out = {}
+    for name, fn in (("fused", md.L.jl_model_forward), ("layered", md.L.jl_model_forward_layered)):
+        P = torch.zeros((n, 101), dtype=torch.float32, device="cuda")
+        S = torch.zeros(n, dtype=torch.float32, device="cuda")
+        _lib.check(fn(md.h, c.data_ptr(), n, P.data_ptr(), S.data_ptr(), None))
+        torch.cuda.synchronize()
+        out[name] = (P.cpu().numpy(), S.cpu().numpy())
+    assert np.abs(out["fused"][0] - out["layered"][0]).max() <= 1e-6
+    assert np.abs(out["fused"][1] - out["layered"][1]).max() <= 1e-5
+    if n <= 127:
+        ref = mlp.forward({k: v.astype(np.float64) for k, v in p.items()}, c.cpu().numpy(), B, quant=True)["p"]
+        assert np.abs(out["fused"][0] - ref).sum(axis=1).max() < 2e-2
+    md.close()
