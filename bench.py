@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-survey", action="store_true", help="skip the surrogate screening workload")
     p.add_argument("--survey-epochs", type=int, default=300)
+    p.add_argument("--no-extra", action="store_true", help="skip the path-animation and deep-zoom sections")
     return p.parse_args()
 
 
@@ -225,6 +226,78 @@ def cpu_sample(frames, target_s, threads=None):
     return iters / secs / 1e9, threads, desc, iters, secs
 
 
+def run_path_animation(K, W):
+    """720-frame path animation (C(t) = 0.7885 exp(it), three resolutions,
+    limit 100, RGBA8) as one batch plan: one CUDA-graph launch per step."""
+    import torch
+
+    import paper_1611_03079_b300 as jl
+    from paper_1611_03079_b300 import workloads as wl
+    frames = wl.path_animation()
+    for f in frames:
+        f["hist"] = True  # bins give the iteration count (sum of b * hist_b * W * H)
+    b = jl.Batch(frames, palette=wl.random_palette(7))
+    for _ in range(W):
+        b.launch()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        b.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / K
+    pix = sum(f["W"] * f["H"] for f in frames)
+    bins = torch.arange(101, dtype=torch.float64, device="cuda")
+    iters = sum(float((b.hist(i).double() * bins).sum()) * f["W"] * f["H"] for i, f in enumerate(frames))
+    res = {"frames": len(frames), "pixels": pix, "iterations": iters, "ms": t * 1e3, "frames_per_s": len(frames) / t,
+           "giter_s": iters / t / 1e9, "gpixel_s": pix / t / 1e9, "graph_launches_per_step": 1,
+           "status": b.status()}
+    b.close()
+    return res
+
+
+def run_deep_zoom(K, W):
+    """64 deep-zoom frames (1920x1080, limit 2000, precision chosen per frame)
+    as one batch plan; plus the binary32-vs-binary64 count mismatch rate of
+    every frame (forced renders of both)."""
+    import numpy as np
+    import torch
+
+    import paper_1611_03079_b300 as jl
+    from paper_1611_03079_b300 import workloads as wl
+    frames = wl.deep_zoom()
+    for f in frames:
+        f["rgba"] = False
+    b = jl.Batch(frames)
+    for _ in range(W):
+        b.launch()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        b.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / K
+    iters = sum(float((b.counts(i).to(torch.int32) & 0xFFFF).sum()) for i in range(len(frames)))
+    precs = b.precisions()
+    rates = []
+    for f in frames:
+        c = {}
+        for p in (0, 1):
+            r = jl.render(f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=p, count_type="u16", rgba=False)
+            c[p] = r["counts"].view(torch.int16)
+        rates.append(float((c[0] != c[1]).float().mean()))
+    res = {"frames": len(frames), "ms": t * 1e3, "giter_s": iters / t / 1e9, "iterations": iters,
+           "fp64_frames": int(sum(precs)), "fp32_frames": int(len(precs) - sum(precs)),
+           "mismatch_rate_fp32_vs_fp64": {"per_frame": [round(x, 6) for x in rates],
+                                          "auto_fp32_frames_max": max([r for r, p in zip(rates, precs) if p == 0],
+                                                                      default=0.0),
+                                          "auto_fp64_frames_mean": float(np.mean([r for r, p in zip(rates, precs)
+                                                                                  if p == 1] or [0.0]))}}
+    b.close()
+    return res
+
+
 def run_reference(args):
     world, rank, _ = dist_setup("gloo")
     if rank != 0:
@@ -373,6 +446,23 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                "seconds": secs}
 
+    # binary32-vs-binary64 count mismatch of the sweep frames (same frame, both precisions)
+    mismatch = {}
+    for i in range(n):
+        f = frames[i]
+        if f["precision"] != 0:
+            continue
+        j = next(jj for jj in range(n) if frames[jj]["precision"] == 1 and frames[jj]["c"] == f["c"] and
+                 frames[jj]["max_iter"] == f["max_iter"] and frames[jj]["mode"] == f["mode"])
+        key = "%s %s limit %d" % ("mandelbrot" if f["mode"] else "julia", f["c"], f["max_iter"])
+        a16, b16 = bufs[i]["counts"].view(torch.int16), bufs[j]["counts"].view(torch.int16)
+        mismatch[key] = float((a16 != b16).float().mean())
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra["path_animation"] = run_path_animation(K, max(args.warmup, 3))
+        extra["deep_zoom"] = run_deep_zoom(1, 1)
+
     survey = None
     if not args.no_survey and rank == 0:
         survey = run_survey(args, K, max(args.warmup, 3))
@@ -399,6 +489,8 @@ def main():
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 2 * n * K,
                 "survey": survey,
+                "mismatch_rate_fp32_vs_fp64_sweep": mismatch,
+                **extra,
                 "peaks_gops": {"binary32": peaks[0] / 1e9, "binary64": peaks[1] / 1e9}}
         print(json.dumps(line), flush=True)
     if world > 1:
