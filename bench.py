@@ -234,8 +234,14 @@ def run_path_animation(K, W):
     import paper_1611_03079_b300 as jl
     from paper_1611_03079_b300 import workloads as wl
     frames = wl.path_animation()
-    for f in frames:
-        f["hist"] = True  # bins give the iteration count (sum of b * hist_b * W * H)
+    # iteration count from the histogram bins of a separate plan (not timed)
+    hframes = [dict(f, hist=True, rgba=False) for f in frames]
+    hb = jl.Batch(hframes)
+    hb.launch()
+    torch.cuda.synchronize()
+    bins = torch.arange(101, dtype=torch.float64, device="cuda")
+    iters = sum(float((hb.hist(i).double() * bins).sum()) * f["W"] * f["H"] for i, f in enumerate(frames))
+    hb.close()
     b = jl.Batch(frames, palette=wl.random_palette(7))
     for _ in range(W):
         b.launch()
@@ -247,8 +253,6 @@ def run_path_animation(K, W):
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) * 1e-3 / K
     pix = sum(f["W"] * f["H"] for f in frames)
-    bins = torch.arange(101, dtype=torch.float64, device="cuda")
-    iters = sum(float((b.hist(i).double() * bins).sum()) * f["W"] * f["H"] for i, f in enumerate(frames))
     res = {"frames": len(frames), "pixels": pix, "iterations": iters, "ms": t * 1e3, "frames_per_s": len(frames) / t,
            "giter_s": iters / t / 1e9, "gpixel_s": pix / t / 1e9, "graph_launches_per_step": 1,
            "status": b.status()}
@@ -344,16 +348,6 @@ def main():
 
     frames = wl.throughput_sweep(args.size)
     pal = wl.random_palette(7)
-    bufs = []
-    for f in frames:
-        bufs.append({"counts": torch.empty((f["H"], f["W"]), dtype=torch.uint16, device=dev),
-                     "rgba": torch.empty((f["H"], f["W"], 4), dtype=torch.uint8, device=dev)})
-
-    def render(i):
-        f = frames[i]
-        jl.render(f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=f["precision"], mode=f["mode"],
-                  count_type="u16", rgba=True, palette=pal, out=bufs[i])
-
     # binary32 / binary64 issue peaks on this GPU (outside the timed region)
     import ctypes
     peaks = {}
@@ -363,16 +357,33 @@ def main():
         _lib.check(L.jl_probe_peak(prec, iters, ctypes.byref(ops), ctypes.byref(secs), stream.cuda_stream))
         peaks[prec] = ops.value
 
-    for _ in range(max(args.warmup, 3)):
-        for i in range(len(frames)):
-            render(i)
+    # launch-shape autotuning (one-off, before any timing): per precision and
+    # limit bucket, calibrated on the sweep frames themselves
+    tuned = {}
+    for prec in (0, 1):
+        for mi in (100, 1000):
+            calib = [f for f in frames if f["precision"] == prec and f["max_iter"] == mi]
+            r = jl.autotune("fp64" if prec else "fp32", mi, calib=calib, reps=1)
+            tuned["%s limit %d" % ("binary64" if prec else "binary32", mi)] = {
+                k: r[k] for k in ("ppt", "unroll", "threads", "ms", "candidates")}
+
+    # The sweep as one batch plan: one CUDA-graph launch per step renders all
+    # 16 frames (coordinate tables, binary32 and binary64 persistent kernels on
+    # concurrent branches).  Separate plans of the binary32 and of the binary64
+    # frames give the per-precision breakdown.
+    for f in frames:
+        f["count_type"], f["rgba"] = "u16", True
+    plan = jl.Batch(frames, palette=pal)
+    sub = {p: [i for i in range(len(frames)) if frames[i]["precision"] == p] for p in (0, 1)}
+    sub_plans = {p: jl.Batch([frames[i] for i in sub[p]], palette=pal) for p in (0, 1)}
+    W_ = max(args.warmup, 3)
+    for _ in range(W_):
+        plan.launch()
     torch.cuda.synchronize()
-    iters = [int(b["counts"].to(torch.int64).sum().item()) for b in bufs]
+    iters = [int((plan.counts(i).to(torch.int32) & 0xFFFF).to(torch.int64).sum().item()) for i in range(len(frames))]
 
     n = len(frames)
     K = args.steps
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-          for _ in range(K)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         torch.distributed.barrier()
@@ -381,10 +392,7 @@ def main():
     clk.start()
     t_start.record(stream)
     for s in range(K):
-        for i in range(n):
-            ev[s][i][0].record(stream)
-            render(i)
-            ev[s][i][1].record(stream)
+        plan.launch(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -395,26 +403,37 @@ def main():
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    per_frame_ms = [statistics.mean(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(K)) for i in range(n)]
     total_iters = sum(iters)
     value = world * K * total_iters / (total_ms * 1e-3) / 1e9
 
     # per-precision breakdown and roofline (escape kernels, ALU bound)
     by_prec = {}
     for prec in (0, 1):
-        idx = [i for i in range(n) if frames[i]["precision"] == prec]
-        t = sum(per_frame_ms[i] for i in idx) * 1e-3
-        it = sum(iters[i] for i in idx)
+        sp = sub_plans[prec]
+        for _ in range(2):
+            sp.launch(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            sp.launch(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3 / K
+        it = sum(iters[i] for i in sub[prec])
         ops = OPS_PER_ITER * it / t
         by_prec[prec] = {"giter_s": it / t / 1e9, "time_ms": t * 1e3, "iterations": it,
-                         "achieved_gops": ops / 1e9, "peak_gops": peaks[prec] / 1e9, "frac": ops / peaks[prec]}
+                         "achieved_gops": ops / 1e9, "peak_gops": peaks[prec] / 1e9, "frac": ops / peaks[prec],
+                         "frames": len(sub[prec])}
+        sp.close()
     dom = max((0, 1), key=lambda p: by_prec[p]["time_ms"])
     d = by_prec[dom]
     roofline = {"bound": "alu", "kernel": "escape_kernel<%s>" % ("double" if dom else "float"),
                 "achieved": d["achieved_gops"], "peak": d["peak_gops"], "unit": "Gop/s",
                 "frac": d["frac"], "traffic": None,
                 "peak_source": "measured on this GPU by jl_probe_peak (independent FMUL/FADD chains, no FMA)",
-                "algorithmic_unit": "8 %s lane ops per escape-time iteration" % ("binary64" if dom else "binary32")}
+                "algorithmic_unit": "8 %s lane ops per escape-time iteration" % ("binary64" if dom else "binary32"),
+                "timing": "CUDA events around a plan of the %s sweep frames alone" % ("binary64" if dom else
+                                                                                    "binary32")}
     roofline_other = {"precision": "binary32" if dom else "binary64", "achieved": by_prec[1 - dom]["achieved_gops"],
                       "peak": by_prec[1 - dom]["peak_gops"], "unit": "Gop/s", "frac": by_prec[1 - dom]["frac"]}
 
@@ -455,7 +474,7 @@ def main():
         j = next(jj for jj in range(n) if frames[jj]["precision"] == 1 and frames[jj]["c"] == f["c"] and
                  frames[jj]["max_iter"] == f["max_iter"] and frames[jj]["mode"] == f["mode"])
         key = "%s %s limit %d" % ("mandelbrot" if f["mode"] else "julia", f["c"], f["max_iter"])
-        a16, b16 = bufs[i]["counts"].view(torch.int16), bufs[j]["counts"].view(torch.int16)
+        a16, b16 = plan.counts(i), plan.counts(j)
         mismatch[key] = float((a16 != b16).float().mean())
 
     extra = {}
@@ -485,9 +504,11 @@ def main():
                     "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "roofline_other_precision": roofline_other,
                 "by_precision": {("binary64" if p else "binary32"): by_prec[p] for p in (0, 1)},
-                "per_frame_ms": per_frame_ms,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 2 * n * K,
+                "gpu_launches": 4 * K,
+                "gpu_launches_note": "one CUDA-graph launch per step holding 4 kernels of this library "
+                                     "(coordinate tables and escape kernel, binary32 and binary64)",
+                "autotuned_variants": tuned,
                 "survey": survey,
                 "mismatch_rate_fp32_vs_fp64_sweep": mismatch,
                 **extra,

@@ -123,7 +123,9 @@ int jl_render_to_host(double cr, double ci, jl_rect rect, int32_t width, int32_t
  * jl_render with an explicit kernel variant (used by the autotuner and the
  * tests): ppt independent pixels per thread, unroll steps between service
  * points, threads per CTA (multiple of 32, 32..256), ctas_per_sm (0 = the
- * occupancy maximum).  Unsupported (ppt, unroll) pairs return JL_EINVAL;
+ * occupancy maximum).  ppt = unroll = 0 selects the static kernel (one pixel
+ * per thread, 32 x 8 pixel CTAs, exact test every step; threads and
+ * ctas_per_sm are then ignored).  Unsupported (ppt, unroll) pairs return JL_EINVAL;
  * jl_variant_list() enumerates the supported ones.
  */
 int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t height, int32_t max_iter,
@@ -212,9 +214,10 @@ typedef struct {
 /* Plan options; zero-initialise for defaults. */
 typedef struct {
     int32_t chunk_len;      /* pixels per work chunk, 16..1024; 0 = 512 */
-    int32_t fp32_ppt, fp32_unroll, fp32_threads;  /* 0 = tuned or default variant */
+    int32_t fp32_ppt, fp32_unroll, fp32_threads;  /* all 0 = tuned or default variant */
     int32_t fp64_ppt, fp64_unroll, fp64_threads;
-    int32_t reserved;
+    int32_t variant_flags;  /* bit 0 / bit 1: the fp32 / fp64 (ppt, unroll) pair is given explicitly
+                               (needed for the static kernel, ppt = unroll = 0) */
     int64_t cycle_budget;   /* per-CTA clock64 budget; when exceeded the kernels stop
                                taking work and the plan status becomes JL_ETIMEOUT;
                                0 = unlimited */
@@ -368,6 +371,11 @@ int jl_model_load(const char *path, jl_model **out);
  */
 int jl_gemm_bf16(const void *A, int32_t lda, int32_t a_trans, const void *B, int32_t ldb, int32_t b_trans, int32_t M,
                  int32_t N, int32_t K, float *C, int32_t ldc, int32_t *status, void *stream);
+
+/* Self-test of the integer-pipe doubling the binary64 kernels use for x + x:
+ * out[i] = 2 * in[i] for n device doubles, computed exactly as the kernels do
+ * (bit-identical to IEEE x + x except for NaN payloads). */
+int jl_selftest_double(const double *in, double *out, int32_t n, void *stream);
 
 /* Writes the built-in 256-entry RGBA8 palette (1024 bytes) to `out` (host).
  * Entry 255 (never-escaped points) is opaque black. */

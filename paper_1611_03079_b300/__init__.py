@@ -198,8 +198,10 @@ class Batch:
         if variants:
             if "fp32" in variants:
                 opts.fp32_ppt, opts.fp32_unroll, opts.fp32_threads = (int(v) for v in variants["fp32"])
+                opts.variant_flags |= 1
             if "fp64" in variants:
                 opts.fp64_ppt, opts.fp64_unroll, opts.fp64_threads = (int(v) for v in variants["fp64"])
+                opts.variant_flags |= 2
         opts.cycle_budget = int(cycle_budget)
         pal, pal_ptr = _palette_ptr(palette)
         h = ctypes.c_void_p()

@@ -42,7 +42,8 @@ class BatchOpts(ctypes.Structure):
     """jl_batch_opts (include/jl.h)."""
     _fields_ = [("chunk_len", ctypes.c_int32), ("fp32_ppt", ctypes.c_int32), ("fp32_unroll", ctypes.c_int32),
                 ("fp32_threads", ctypes.c_int32), ("fp64_ppt", ctypes.c_int32), ("fp64_unroll", ctypes.c_int32),
-                ("fp64_threads", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cycle_budget", ctypes.c_int64)]
+                ("fp64_threads", ctypes.c_int32), ("variant_flags", ctypes.c_int32),
+                ("cycle_budget", ctypes.c_int64)]
 
 
 class TuneResult(ctypes.Structure):
@@ -94,6 +95,7 @@ SIGNATURES = {
     "jl_model_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "jl_model_load": (ctypes.c_int, [ctypes.c_char_p, _vp]),
     "jl_gemm_bf16": (ctypes.c_int, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp]),
+    "jl_selftest_double": (ctypes.c_int, [_vp, _vp, _i32, _vp]),
     "jl_render_to_host": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
                                          _vp, _vp]),
 }

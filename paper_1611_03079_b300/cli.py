@@ -15,7 +15,8 @@ import numpy as np
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--workload", choices=["sweep", "single"], default=None)
+    p.add_argument("--workload", choices=["sweep", "single", "path"], default=None)
+    p.add_argument("--frames", type=int, default=72, help="path workload: first N frames as one batch plan")
     p.add_argument("--index", type=int, default=0)
     p.add_argument("--size", type=int, default=4096)
     p.add_argument("--c", type=complex, default=complex(-0.8, 0.156))
@@ -38,6 +39,8 @@ def main(argv=None):
     import paper_1611_03079_b300 as jl
     from paper_1611_03079_b300 import workloads as wl
 
+    if a.workload == "path":
+        return path(a)
     if a.workload == "sweep":
         f = wl.throughput_sweep(a.size)[a.index]
     elif a.workload == "single":
@@ -63,6 +66,31 @@ def main(argv=None):
                       "best_ms": best, "giter_s": iters / (best * 1e-3) / 1e9, "iterations": iters}))
     if a.out:
         np.save(a.out, out["counts"].view(torch.int16).cpu().numpy().view(np.uint16))
+
+
+def path(a):
+    """First N frames of the path animation as one batch plan, launched
+    `repeat` times (RGBA8 only)."""
+    import torch
+
+    import paper_1611_03079_b300 as jl
+    from paper_1611_03079_b300 import workloads as wl
+    torch.cuda.set_device(0)
+    frames = wl.path_animation()[:a.frames]
+    variants = {"fp32": tuple(a.variant[:3])} if a.variant else None
+    b = jl.Batch(frames, variants=variants)
+    times = []
+    for _ in range(a.repeat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    pix = sum(f["W"] * f["H"] for f in frames)
+    print(json.dumps({"frames": len(frames), "pixels": pix, "ms": times, "gpixel_s": pix / (min(times) * 1e-3) / 1e9,
+                      "status": b.status()}))
+    b.close()
 
 
 def probe():

@@ -109,6 +109,8 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
     memset(F, 0, sizeof(*F));
     F->cr = mode == JL_JULIA ? cr : 0.0;
     F->ci = mode == JL_JULIA ? ci : 0.0;
+    F->cr32 = (float)F->cr;  // round to nearest even, as the binary32 path requires
+    F->ci32 = (float)F->ci;
     F->xmin = rect.xmin;
     F->ymin = rect.ymin;
     F->dx = (rect.xmax - rect.xmin) / (double)W;
@@ -136,6 +138,9 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
         F->chunks_per_row = (W + chunk_len - 1) / chunk_len;
         F->chunk_count = H * F->chunks_per_row;
     }
+    F->tiles_x = (W + 31) / 32;
+    F->tile_count = F->tiles_x * ((H + 7) / 8);
+    F->tile_begin = 0;
     F->precision = prec;
     F->colour_magic = (1ull << 40) / (uint64_t)max_iter + 1ull;
     // Monotone escape is proven for |C| <= 2 - 2^-12 (Julia); Mandelbrot pixels
@@ -190,6 +195,7 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
         a.n_frames = 1;
         a.hist_smem = (F.hist_bins && F.max_iter + 1 <= 4096) ? 1 : 0;
         a.total_chunks = F.chunk_count;
+        a.total_tiles = F.tile_count;
         a.chunk_counter = counter;
         a.status = status;
         a.cycle_budget = 0;
@@ -238,6 +244,14 @@ int jl_variant_list(int32_t precision, int32_t *pairs, int32_t cap)
     return variant_list(precision, pairs, cap < 0 ? 0 : cap);
 }
 
+int jl_selftest_double(const double *in, double *out, int32_t n, void *stream)
+{
+    if (!in || !out || n < 1)
+        return fail(JL_EINVAL, "invalid arguments");
+    cudaError_t e = launch_dbl2(in, out, n, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? JL_OK : cuda_fail(e, "jl_selftest_double");
+}
+
 int jl_default_palette(uint8_t *out)
 {
     if (!out)
@@ -276,6 +290,8 @@ int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t
         return rc;
     if (!variant_supported(prec, ppt, unroll))
         return fail(JL_EINVAL, "unsupported (ppt, unroll) for this precision");
+    if (ppt == 0)
+        threads = 256;  // the static kernel has a fixed CTA shape
     if (threads < 32 || threads > 256 || (threads & 31))
         return fail(JL_EINVAL, "threads must be a multiple of 32 in 32..256");
     if (ctas_per_sm < 0 || ctas_per_sm > 32)

@@ -4,10 +4,11 @@
 // escape-time kernel itself lives in jl_escape.cu).
 //
 // A plan resolves every frame's precision, builds the device frame tables and
-// the chunk -> frame table, computes all coordinate tables once, and captures
-// one graph: reset of the work counters and status word, zeroing of the
-// histogram bins, the binary32 and binary64 persistent escape kernels on two
-// forked branches (they run concurrently), and the histogram finalisation.
+// the work-unit -> frame table, and captures one graph: reset of the work
+// counters and status word, the coordinate tables of every frame, zeroing of
+// the histogram bins, the binary32 and binary64 persistent escape kernels on
+// two forked branches (they run concurrently, so binary32 work fills the issue
+// slots the narrow binary64 pipe leaves idle), and the histogram finalisation.
 // Launching the plan replays the graph; nothing is allocated per launch.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -24,7 +25,8 @@ struct jl_batch {
     std::vector<int32_t> prec;             // resolved precision of every frame (input order)
     std::vector<int64_t> pixels;           // per group
     jl::Frame *frames_dev[2] = {nullptr, nullptr};
-    int32_t *chunk_frame_dev[2] = {nullptr, nullptr};
+    int32_t *chunk_frame_dev[2] = {nullptr, nullptr};  // chunk -> frame, or tile -> frame (static kernel)
+    int64_t tiles[2] = {0, 0};
     int n_group[2] = {0, 0};
     int64_t chunks[2] = {0, 0};
     void *coords_dev = nullptr;
@@ -147,8 +149,10 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(coordinate tables)"); break; }
         size_t off = 0;
         for (int g = 0; g < 2; ++g) {
-            int64_t chunk = 0;
+            int64_t chunk = 0, tile = 0;
             for (Frame &F : host[g]) {
+                F.tile_begin = tile;
+                tile += F.tile_count;
                 const size_t es = g ? 8 : 4;
                 F.xs = static_cast<uint8_t *>(b->coords_dev) + off;
                 off += ((size_t)F.W * es + 255) & ~(size_t)255;
@@ -159,6 +163,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 b->pixels[g] += (int64_t)F.W * F.H;
             }
             b->chunks[g] = chunk;
+            b->tiles[g] = tile;
             b->n_group[g] = (int)host[g].size();
         }
         e = cudaMalloc(&b->ctl_dev, 256);
@@ -175,28 +180,13 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
         for (int g = 0; g < 2 && rc == JL_OK; ++g) {
             if (host[g].empty())
                 continue;
-            const size_t nb = host[g].size() * sizeof(Frame);
-            e = cudaMalloc(&b->frames_dev[g], nb);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(frame table)"); break; }
-            e = cudaMemcpy(b->frames_dev[g], host[g].data(), nb, cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(frame table)"); break; }
-            std::vector<int32_t> cf((size_t)b->chunks[g]);
-            for (size_t f = 0; f < host[g].size(); ++f)
-                for (int32_t c = 0; c < host[g][f].chunk_count; ++c)
-                    cf[(size_t)host[g][f].chunk_begin + c] = (int32_t)f;
-            e = cudaMalloc(&b->chunk_frame_dev[g], cf.size() * sizeof(int32_t));
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(chunk table)"); break; }
-            e = cudaMemcpy(b->chunk_frame_dev[g], cf.data(), cf.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(chunk table)"); break; }
-            // coordinate tables, once per plan
-            e = launch_coords(b->frames_dev[g], nullptr, (int)host[g].size(), b->s0);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "coords kernel launch"); break; }
             // kernel variant: explicit option, else the tuned/default one
             const int pp = g ? o.fp64_ppt : o.fp32_ppt;
             const int uu = g ? o.fp64_unroll : o.fp32_unroll;
             const int tt = g ? o.fp64_threads : o.fp32_threads;
+            const bool explicit_variant = pp || uu || ((o.variant_flags >> g) & 1);
             Variant v = tuned_variant(g, max_iter_max[g]);
-            if (pp || uu) {
+            if (explicit_variant) {
                 if (!variant_supported(g, pp, uu)) { rc = fail(JL_EINVAL, "unsupported (ppt, unroll) option"); break; }
                 v.ppt = pp;
                 v.unroll = uu;
@@ -206,11 +196,28 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 v.threads = tt;
             }
             b->variant[g] = v;
+            if (v.ppt == 0 && b->tiles[g] > 0x7fffffffll) { rc = fail(JL_EINVAL, "too many tiles for the static kernel"); break; }
+            const size_t nb = host[g].size() * sizeof(Frame);
+            e = cudaMalloc(&b->frames_dev[g], nb);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(frame table)"); break; }
+            e = cudaMemcpy(b->frames_dev[g], host[g].data(), nb, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(frame table)"); break; }
+            // work-unit -> frame table: 32x8 tiles for the static kernel, chunks otherwise
+            const bool stat = v.ppt == 0;
+            std::vector<int32_t> cf((size_t)(stat ? b->tiles[g] : b->chunks[g]));
+            for (size_t f = 0; f < host[g].size(); ++f) {
+                const int64_t begin = stat ? host[g][f].tile_begin : host[g][f].chunk_begin;
+                const int32_t cnt = stat ? host[g][f].tile_count : host[g][f].chunk_count;
+                for (int32_t c = 0; c < cnt; ++c)
+                    cf[(size_t)begin + c] = (int32_t)f;
+            }
+            e = cudaMalloc(&b->chunk_frame_dev[g], cf.size() * sizeof(int32_t));
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(work table)"); break; }
+            e = cudaMemcpy(b->chunk_frame_dev[g], cf.data(), cf.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(work table)"); break; }
         }
         if (rc != JL_OK)
             break;
-        e = cudaStreamSynchronize(b->s0);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "coordinate tables"); break; }
 
         // ---- capture the launch graph ----
         EscapeArgs args[2];
@@ -222,7 +229,9 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
         for (int g = 0; g < 2; ++g) {
             memset(&args[g], 0, sizeof(EscapeArgs));
             args[g].frames = b->frames_dev[g];
-            args[g].chunk_frame = b->chunk_frame_dev[g];
+            args[g].chunk_frame = b->variant[g].ppt ? b->chunk_frame_dev[g] : nullptr;
+            args[g].tile_frame = b->variant[g].ppt ? nullptr : b->chunk_frame_dev[g];
+            args[g].total_tiles = b->tiles[g];
             args[g].n_frames = b->n_group[g];
             args[g].hist_smem = 0;
             args[g].total_chunks = b->chunks[g];
@@ -236,6 +245,10 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
         e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamBeginCapture"); break; }
         cudaError_t ce = cudaMemsetAsync(b->ctl_dev, 0, 32, b->s0);
+        // region covering: coordinate tables of every frame, each launch
+        for (int g = 0; g < 2 && ce == cudaSuccess; ++g)
+            if (b->n_group[g])
+                ce = launch_coords(b->frames_dev[g], nullptr, b->n_group[g], b->s0);
         for (int g = 0; g < 2 && ce == cudaSuccess && any_hist; ++g)
             if (b->n_group[g])
                 ce = launch_hist_zero(b->frames_dev[g], b->n_group[g], b->s0);

@@ -107,6 +107,38 @@ __global__ void hist_zero_kernel(const __grid_constant__ HistArgs a)
     }
 }
 
+// x + x for binary64 on the integer pipes (the binary64 pipe is narrow on
+// this part).  Doubling is exact in IEEE arithmetic, so the bit pattern can be
+// formed directly: zero/subnormal -> magnitude shifted left by one (a carry
+// into the exponent field gives the correct normal number); exponent field
+// 1..2045 -> exponent + 1; 2046 -> signed infinity (what round-to-nearest
+// gives on overflow); 2047 (inf, NaN) -> unchanged (NaN stays NaN).
+__device__ __forceinline__ double dbl2(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long sign = b & 0x8000000000000000ull;
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    const unsigned e = (unsigned)(mag >> 52);
+    unsigned long long r = b + (1ull << 52);
+    r = (e == 0) ? (sign | (mag << 1)) : r;
+    r = (e == 2046) ? (sign | 0x7ff0000000000000ull) : r;
+    r = (e == 2047) ? b : r;
+    return __longlong_as_double((long long)r);
+}
+
+__global__ void dbl2_kernel(const double *in, double *out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        out[i] = dbl2(in[i]);
+}
+
+cudaError_t launch_dbl2(const double *in, double *out, int n, cudaStream_t st)
+{
+    dbl2_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Exact single-step iteration (used for tails, unproven-monotone pixels and
 // nothing else).  Returns the count given that tests 0..n0-1 have passed and
@@ -134,7 +166,7 @@ __device__ __forceinline__ int exact_from(double x, double y, double cr, double 
         double y2 = __dmul_rn(y, y);
         if (__dadd_rn(x2, y2) > 4.0)
             return n;
-        double t = __dadd_rn(x, x);
+        double t = dbl2(x);
         t = __dmul_rn(t, y);
         y = __dadd_rn(t, ci);
         x = __dadd_rn(__dsub_rn(x2, y2), cr);
@@ -176,15 +208,18 @@ __device__ __forceinline__ float hi_estimate(double v)
 // ---------------------------------------------------------------------------
 // The persistent escape kernel.
 // ---------------------------------------------------------------------------
+// C of a Julia frame in the working type (binary32 value rounded on the host).
 template <typename T>
 struct WorkT;
 template <>
 struct WorkT<float> {
-    static __device__ __forceinline__ float from_double(double v) { return __double2float_rn(v); }
+    static __device__ __forceinline__ float cr(const Frame &F) { return F.cr32; }
+    static __device__ __forceinline__ float ci(const Frame &F) { return F.ci32; }
 };
 template <>
 struct WorkT<double> {
-    static __device__ __forceinline__ double from_double(double v) { return v; }
+    static __device__ __forceinline__ double cr(const Frame &F) { return F.cr; }
+    static __device__ __forceinline__ double ci(const Frame &F) { return F.ci; }
 };
 
 // Integer quotient (n * 255) / d for n <= d <= 65535 via a 40-bit reciprocal:
@@ -284,8 +319,8 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
         q_max = F.max_iter;
         q_mode = F.mode;
         q_safe = F.safe;
-        q_cr = WorkT<T>::from_double(F.cr);
-        q_ci = WorkT<T>::from_double(F.ci);
+        q_cr = WorkT<T>::cr(F);
+        q_ci = WorkT<T>::ci(F);
         q_xs = static_cast<const T *>(F.xs);
         q_ys = static_cast<const T *>(F.ys);
         return true;
@@ -480,7 +515,7 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
                     float r32 = __fadd_rn(hi_estimate(x2), hi_estimate(y2));
                     cnt[k] += (r32 < 3.9999847412109375f) ? 1 : 0;
                     amb |= (rem[k] >= 0) & (r32 >= 3.9999847412109375f) & (r32 <= 4.0000152587890625f);
-                    double t = __dadd_rn(xx, xx);
+                    double t = dbl2(xx);
                     t = __dmul_rn(t, yy);
                     y[k] = (T)__dadd_rn(t, (double)ci[k]);
                     x[k] = (T)__dadd_rn(__dsub_rn(x2, y2), (double)cr[k]);
@@ -502,7 +537,7 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
                         double x2 = __dmul_rn(xx, xx);
                         double y2 = __dmul_rn(yy, yy);
                         cnt[k] += (__dadd_rn(x2, y2) <= 4.0) ? 1 : 0;
-                        double t = __dadd_rn(xx, xx);
+                        double t = dbl2(xx);
                         t = __dmul_rn(t, yy);
                         y[k] = (T)__dadd_rn(t, (double)ci[k]);
                         x[k] = (T)__dadd_rn(__dsub_rn(x2, y2), (double)cr[k]);
@@ -527,6 +562,157 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
             uint32_t v = hbins[t];
             if (v)
                 atomicAdd(&gb[t], v);
+        }
+    }
+}
+
+
+// Escape count of one pixel in blocks of 4 steps with one branch per block.
+// When escape is monotone (`mono`, see in_unsafe_band) the block keeps the
+// four values r = x2 + y2 and, once the last one fails, the count is the
+// number of passed tests; otherwise every step is tested exactly.
+template <typename T>
+__device__ __forceinline__ int escape_blocked(T x, T y, T cr, T ci, int max_iter, bool mono)
+{
+    if (!mono)
+        return exact_from(x, y, cr, ci, 0, max_iter);
+    int n = 0;
+    for (; n + 4 <= max_iter; n += 4) {
+        T r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            T x2, y2, t;
+            if constexpr (sizeof(T) == 4) {
+                x2 = __fmul_rn(x, x);
+                y2 = __fmul_rn(y, y);
+                r[u] = __fadd_rn(x2, y2);
+                t = __fmul_rn(__fadd_rn(x, x), y);
+                y = __fadd_rn(t, ci);
+                x = __fadd_rn(__fsub_rn(x2, y2), cr);
+            } else {
+                x2 = __dmul_rn(x, x);
+                y2 = __dmul_rn(y, y);
+                r[u] = __dadd_rn(x2, y2);
+                t = __dmul_rn(dbl2(x), y);
+                y = __dadd_rn(t, ci);
+                x = __dadd_rn(__dsub_rn(x2, y2), cr);
+            }
+        }
+        if (!(r[3] <= T(4))) {
+            int passed = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                passed += (r[u] <= T(4)) ? 1 : 0;
+            return n + passed;
+        }
+    }
+    // tail shorter than a block: Z_n is (x, y)
+    return exact_from(x, y, cr, ci, n, max_iter);
+}
+
+// ---------------------------------------------------------------------------
+// Static kernel: one pixel per thread, CTA = 32 x 8 pixels (8 warps of 8 x 4),
+// an exact test at every step and per-lane early exit.  No refill machinery,
+// so per-pixel overhead is minimal; lanes of a warp wait for the slowest
+// pixel of their 8 x 4 patch.  Best for frames with low escape counts.
+// ---------------------------------------------------------------------------
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constant__ EscapeArgs a)
+{
+    __shared__ uint32_t pal[256];
+    extern __shared__ uint32_t hbins[];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        pal[t] = a.palette[t];
+    const int nb = (!BATCH && a.hist_smem) ? a.single.max_iter + 1 : 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x)
+        hbins[t] = 0;
+    __syncthreads();
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int dx = (w & 3) * 8 + (lane & 7);
+    const int dy = (w >> 2) * 4 + (lane >> 3);
+    const long long t_start = clock64();
+
+    // Persistent: tiles blockIdx.x, blockIdx.x + gridDim.x, ...; the next
+    // tile's coordinates are loaded before the current tile is iterated.
+    struct Px {
+        int f, i, j;
+        bool ok;
+        T x, y;
+    };
+    auto locate = [&](long long tile) -> Px {
+        Px q;
+        q.f = 0;
+        if constexpr (BATCH)
+            q.f = a.tile_frame[tile];
+        const Frame &F = BATCH ? a.frames[q.f] : a.single;
+        const int lt = (int)(tile - F.tile_begin);
+        const int ty = lt / F.tiles_x;
+        const int tx = lt - ty * F.tiles_x;
+        q.i = tx * 32 + dx;
+        q.j = ty * 8 + dy;
+        q.ok = q.i < F.W && q.j < F.H;
+        q.x = q.ok ? static_cast<const T *>(F.xs)[q.i] : T(0);
+        q.y = q.ok ? static_cast<const T *>(F.ys)[q.j] : T(0);
+        return q;
+    };
+    long long tile = blockIdx.x;
+    if (tile >= a.total_tiles)
+        return;
+    Px cur = locate(tile);
+    while (true) {
+        const long long next = tile + gridDim.x;
+        const bool more = next < a.total_tiles;
+        bool stop = false;
+        if (a.cycle_budget > 0 && (clock64() - t_start) > a.cycle_budget)
+            stop = true;
+        Px nxt;
+        if (more && !stop)
+            nxt = locate(next);
+        if (cur.ok) {
+            const Frame &F = BATCH ? a.frames[cur.f] : a.single;
+            int count;
+            if (F.mode == JL_JULIA)
+                count = escape_blocked(cur.x, cur.y, WorkT<T>::cr(F), WorkT<T>::ci(F), F.max_iter, F.safe != 0);
+            else
+                count = escape_blocked(T(0), T(0), cur.x, cur.y, F.max_iter, !in_unsafe_band(cur.x, cur.y));
+            const int p = cur.j * F.W + cur.i;
+            if (F.counts) {
+                if (F.count_type == JL_COUNT_U8)
+                    F.counts[p] = (uint8_t)count;
+                else
+                    reinterpret_cast<uint16_t *>(F.counts)[p] = (uint16_t)count;
+            }
+            if (F.rgba)
+                F.rgba[p] = pal[colour_index((uint32_t)count, (uint32_t)F.max_iter, F.colour_magic)];
+            if (F.hist_bins) {
+                if (!BATCH && a.hist_smem) {
+                    atomicAdd(&hbins[count], 1u);
+                } else {
+                    const unsigned act = __activemask();
+                    const unsigned long long key = ((unsigned long long)(unsigned)cur.f << 32) | (unsigned)count;
+                    const unsigned grp = __match_any_sync(act, key);
+                    if ((grp & ((1u << lane) - 1u)) == 0)
+                        atomicAdd(&F.hist_bins[count], (unsigned)__popc(grp));
+                }
+            }
+        }
+        if (stop) {
+            if (threadIdx.x == 0 && a.status && more)
+                atomicExch(a.status, (int)JL_ETIMEOUT);
+            break;
+        }
+        if (!more)
+            break;
+        tile = next;
+        cur = nxt;
+    }
+    if (nb) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            const uint32_t v = hbins[t];
+            if (v)
+                atomicAdd(&a.single.hist_bins[t], v);
         }
     }
 }
@@ -613,6 +799,8 @@ static cudaError_t launch_one(const EscapeArgs &a, const Variant &v, int num_sms
 
 bool variant_supported(int precision, int ppt, int unroll)
 {
+    if (ppt == 0 && unroll == 0 && (precision == JL_FP32 || precision == JL_FP64))
+        return true;
 #define JL_CHECK(T, P, UU) \
     if (((sizeof(T) == 8) == (precision == JL_FP64)) && ppt == P && unroll == UU) return true;
     JL_VARIANTS_F32(JL_CHECK)
@@ -624,6 +812,12 @@ bool variant_supported(int precision, int ppt, int unroll)
 int variant_list(int precision, int32_t *pairs, int cap)
 {
     int n = 0;
+    // (0, 0): the static one-pixel-per-thread kernel
+    if (pairs && n < cap) {
+        pairs[0] = 0;
+        pairs[1] = 0;
+    }
+    ++n;
 #define JL_LIST(T, P, UU)                                            \
     if ((sizeof(T) == 8) == (precision == JL_FP64)) {                \
         if (pairs && n < cap) { pairs[2 * n] = P; pairs[2 * n + 1] = UU; } \
@@ -635,8 +829,36 @@ int variant_list(int precision, int32_t *pairs, int cap)
     return n;
 }
 
+template <typename T>
+static cudaError_t launch_static(const EscapeArgs &a, cudaStream_t st)
+{
+    size_t smem = 0;
+    if (a.hist_smem && !a.frames)
+        smem = (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
+    auto kern = a.frames ? escape_static_kernel<T, true> : escape_static_kernel<T, false>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (a.total_tiles < 1)
+        return cudaErrorInvalidValue;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess)
+        return e;
+    const int sms = device_sm_count();
+    long long grid = (long long)(sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
+    if (grid > a.total_tiles)
+        grid = a.total_tiles;
+    kern<<<(unsigned)grid, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_escape(const EscapeArgs &a, int precision, const Variant &v, int num_sms, cudaStream_t st)
 {
+    if (v.ppt == 0)
+        return precision == JL_FP64 ? launch_static<double>(a, st) : launch_static<float>(a, st);
     size_t smem = 256 * sizeof(uint32_t);
     if (a.hist_smem && !a.frames)
         smem += (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);

@@ -14,7 +14,9 @@ namespace jl {
 // Device-side description of one frame.  The host fills it; kernels read it
 // from a table in global memory (batches) or from the launch parameters.
 struct Frame {
-    double cr, ci;                 // C for Julia frames (binary64, rounded in-kernel)
+    double cr, ci;                 // C for Julia frames (binary64)
+    float cr32, ci32;              // the same C rounded once to binary32 on the host (kernels
+                                   // must not convert per pixel: binary64 ops are slow here)
     double xmin, ymin, dx, dy;     // region covering in binary64 (Sec. 2)
     int32_t W, H, max_iter, mode;  // mode: JL_JULIA / JL_MANDELBROT
     int32_t count_type;            // JL_COUNT_*
@@ -23,7 +25,10 @@ struct Frame {
     int32_t rows_per_chunk;        // > 1: each chunk is this many whole rows (W < chunk_len)
     uint32_t span_magic;           // ceil(2^20 / W) when rows_per_chunk > 1, else 0
     int32_t chunk_count;           // chunks of this frame
-    int32_t pad1;
+    int32_t tiles_x;               // static kernel: 32 x 8 pixel tiles per tile row
+    int32_t tile_count;            // static kernel: tiles of this frame
+    int32_t pad2;
+    int64_t tile_begin;            // static kernel: index of this frame's first tile in the launch
     int32_t safe;                  // 1: escape is monotone for every pixel (see escape kernels)
     int32_t precision;             // JL_FP32 / JL_FP64 (working type of xs/ys)
     int32_t pad0;
@@ -40,6 +45,8 @@ struct Frame {
 struct EscapeArgs {
     const Frame *frames;               // device table, or NULL to use `single`
     const int32_t *chunk_frame;        // device: frame index of every chunk (batches)
+    const int32_t *tile_frame;         // device: frame index of every 32x8 tile (static kernel, batches)
+    int64_t total_tiles;               // static kernel: tiles in the launch
     int32_t n_frames;
     int32_t hist_smem;                 // 1: accumulate histogram bins in shared memory (one frame)
     int64_t total_chunks;
@@ -52,7 +59,7 @@ struct EscapeArgs {
 
 // Kernel variant knobs (chosen by the autotuner or the defaults).
 struct Variant {
-    int ppt;      // independent pixels per thread (ILP slots)
+    int ppt;      // independent pixels per thread (ILP slots); 0 = static kernel (one pixel per thread)
     int unroll;   // steps per block between service points
     int threads;  // threads per CTA
     int ctas_per_sm;
@@ -73,6 +80,7 @@ cudaError_t launch_hist_zero(const Frame *frames_dev, int n, cudaStream_t st);
 bool variant_supported(int precision, int ppt, int unroll);
 int variant_list(int precision, int32_t *pairs, int cap);
 int device_sm_count();
+cudaError_t launch_dbl2(const double *in, double *out, int n, cudaStream_t st);
 
 // Validates a frame request and fills F (outputs and coordinate tables are
 // left NULL).  chunk_len: target pixels per work chunk (16 .. 1024).

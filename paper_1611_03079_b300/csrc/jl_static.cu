@@ -105,6 +105,7 @@ extern "C" int jl_render_static(double cr, double ci, jl_rect rect, int32_t widt
     a.n_frames = 1;
     a.hist_smem = (F.hist_bins && F.max_iter + 1 <= 4096) ? 1 : 0;
     a.total_chunks = F.chunk_count;
+    a.total_tiles = F.tile_count;
     a.chunk_counter = counter;
     a.status = status;
     a.cycle_budget = 0;

@@ -138,3 +138,21 @@ def test_autotune_choice_is_exact(cuda, tmp_path):
     jl.tune_load(p)
     assert jl.tune_get("fp32", 100)["tuned"]
     jl.tune_clear()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_static_variant_batch(cuda, prec):
+    """The static kernel (one pixel per thread) in a batch plan, chosen
+    explicitly, on ragged frames of both modes."""
+    frames = []
+    for i, f in enumerate(wl.random_views(24, seed=700 + prec)):
+        f = dict(f)
+        f["precision"] = prec
+        f["count_type"] = "u16"
+        f["hist"] = i % 2 == 0
+        frames.append(f)
+    key = "fp64" if prec else "fp32"
+    b = jl.Batch(frames, palette=PAL, variants={key: (0, 0, 256)})
+    b.launch()
+    _check_batch(b, frames)
+    b.close()

@@ -156,26 +156,70 @@ def test_deterministic(cuda):
         assert (a[key] == b[key]).all()
 
 
+@pytest.fixture(scope="module")
+def sweep_batch():
+    """The 16 sweep frames (4096 x 4096) as one batch plan, exactly as
+    bench.py launches them."""
+    import torch
+    frames = wl.throughput_sweep()
+    for f in frames:
+        f["count_type"], f["rgba"], f["hist"] = "u16", True, True
+    b = jl.Batch(frames, palette=PAL)
+    b.launch()
+    torch.cuda.synchronize()
+    yield frames, b
+    b.close()
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("idx", range(16))
-def test_throughput_sweep_full_size_sampled(cuda, idx):
-    """The 4096x4096 sweep frames in the benchmark's launch configuration:
-    sampled rows (64 spread rows including the first and last) checked
-    against the oracle row by row, plus full-frame invariants: 180-degree
-    symmetry of Julia frames where coordinates are exact negatives (checked
-    on the GPU output itself) and row symmetry of Mandelbrot frames."""
-    f = wl.throughput_sweep()[idx]
-    g = gpu_render(f, hist=True)
+def test_throughput_sweep_full_size_sampled(cuda, sweep_batch, idx):
+    """The 4096x4096 sweep frames in the benchmark's launch configuration (one
+    batch plan): sampled rows (64 spread rows including the first and last)
+    checked against the oracle row by row, plus full-frame invariants:
+    180-degree symmetry of binary32 Julia frames (their grids are exactly
+    antisymmetric), row symmetry of Mandelbrot frames, and histograms that
+    recover the bin counts of the whole frame."""
+    frames, b = sweep_batch
+    f = frames[idx]
+    c = b.counts(idx).cpu().numpy().view(np.uint16)
+    rgba = b.rgba(idx).cpu().numpy()
     rows = sorted(set([0, f["H"] - 1] + list(range(37, f["H"], 64))))
     k = oracle.render_rows(f["c"], f["rect"], f["W"], f["H"], rows, f["max_iter"], f["mode"], f["precision"])
-    assert (g["counts"][rows] == k).all()
-    assert (g["rgba"][rows] == oracle.colour(k, f["max_iter"], PAL)).all()
-    c = g["counts"]
+    assert (c[rows] == k).all()
+    assert (rgba[rows] == oracle.colour(k, f["max_iter"], PAL)).all()
     if f["precision"] == 0:
         if f["mode"] == 0:
             assert (c == c[::-1, ::-1]).all()
         else:
             assert (c == c[::-1, :]).all()
-    h = g["hist"].astype(np.float64)
+    h = b.hist(idx).cpu().numpy().astype(np.float64)
     assert abs(h.sum() - 1.0) < 1e-4
     assert (np.rint(h * f["W"] * f["H"]) == np.bincount(c.ravel(), minlength=f["max_iter"] + 1)).all()
+
+
+def test_integer_doubling_is_exact(cuda):
+    """The binary64 kernels form x + x on the integer pipes; it must equal
+    IEEE x + x bit for bit (zero, subnormals, carries into the exponent,
+    overflow to infinity, infinities; NaN stays NaN)."""
+    import torch
+    rng = np.random.default_rng(0)
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2250738585072009e-308, 2.2250738585072014e-308,
+                        1.1125369292536007e-308, 8.98846567431158e307, 8.988465674311579e307,
+                        1.7976931348623157e308, -1.7976931348623157e308, np.inf, -np.inf, 1.0, -2.0, 1e-310,
+                        4.0, 2.0 - 2 ** -52])
+    vals = np.concatenate([special, rng.standard_normal(4000) * 10.0 ** rng.uniform(-310, 308, 4000),
+                           np.frombuffer(rng.bytes(8 * 4000), dtype=np.float64)])
+    vals = vals[~np.isnan(vals)]
+    x = torch.from_numpy(vals).cuda()
+    y = torch.empty_like(x)
+    jl._lib.check(jl._lib.lib().jl_selftest_double(x.data_ptr(), y.data_ptr(), x.numel(), None))
+    torch.cuda.synchronize()
+    with np.errstate(over="ignore"):
+        ref = vals + vals
+    assert (y.cpu().numpy().view(np.uint64) == ref.view(np.uint64)).all()
+    z = torch.tensor([float("nan")], dtype=torch.float64, device="cuda")
+    w = torch.empty_like(z)
+    jl._lib.check(jl._lib.lib().jl_selftest_double(z.data_ptr(), w.data_ptr(), 1, None))
+    torch.cuda.synchronize()
+    assert torch.isnan(w).all()
