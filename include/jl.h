@@ -125,13 +125,17 @@ int jl_render_to_host(double cr, double ci, jl_rect rect, int32_t width, int32_t
  * points, threads per CTA (multiple of 32, 32..256), ctas_per_sm (0 = the
  * occupancy maximum).  ppt = unroll = 0 selects the static kernel (one pixel
  * per thread, 32 x 8 pixel CTAs, exact test every step; threads and
- * ctas_per_sm are then ignored).  Unsupported (ppt, unroll) pairs return JL_EINVAL;
+ * ctas_per_sm are then ignored).  emu (binary64 with ppt > 0 only): 1 = all
+ * arithmetic on the hardware binary64 pipe; k > 1 = one warp group (4 warps)
+ * in every k uses the hardware pipe and the others the bit-exact
+ * integer-pipe binary64 arithmetic (see jl_selftest_f64), so both kinds of
+ * units work at once.  Unsupported (ppt, unroll) pairs return JL_EINVAL;
  * jl_variant_list() enumerates the supported ones.
  */
 int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t height, int32_t max_iter,
                       int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
                       const uint8_t *palette, float *hist, int32_t ppt, int32_t unroll, int32_t threads,
-                      int32_t ctas_per_sm, void *stream);
+                      int32_t ctas_per_sm, int32_t emu, void *stream);
 
 /*
  * Writes up to `cap` supported (ppt, unroll) pairs for `precision` into
@@ -218,6 +222,8 @@ typedef struct {
     int32_t fp64_ppt, fp64_unroll, fp64_threads;
     int32_t variant_flags;  /* bit 0 / bit 1: the fp32 / fp64 (ppt, unroll) pair is given explicitly
                                (needed for the static kernel, ppt = unroll = 0) */
+    int32_t fp64_emu;       /* 0 = tuned or default; else as `emu` of jl_render_variant */
+    int32_t reserved;
     int64_t cycle_budget;   /* per-CTA clock64 budget; when exceeded the kernels stop
                                taking work and the plan status becomes JL_ETIMEOUT;
                                0 = unlimited */
@@ -261,12 +267,15 @@ int jl_render_batch(const jl_frame *frames, int32_t n, void *counts_base, uint8_
  * ------------------------------------------------------------------------ */
 typedef struct {
     int32_t ppt, unroll, threads, ctas_per_sm;
+    int32_t emu;            /* binary64 integer-pipe share, see jl_render_variant */
+    int32_t reserved;
     double ms;              /* mean time of the calibration set with this variant */
     int32_t candidates;     /* candidates timed (jl_tune_get: 1 if tuned, 0 if default) */
 } jl_tune_result;
 
 /*
- * Times every supported (ppt, unroll) x {128, 256} threads on the calibration
+ * Times every supported (ppt, unroll) x {128, 256} threads (x emu in {1, 2,
+ * 3, 4} for binary64 with ppt > 0 at 256 threads) on the calibration
  * frames (their own rect, size, mode and C; `precision` and `max_iter` as
  * given), `reps` timed repetitions each after one warm-up, and records the
  * fastest for (current device, precision, bucket of max_iter: <=128, <=1024,
@@ -376,6 +385,15 @@ int jl_gemm_bf16(const void *A, int32_t lda, int32_t a_trans, const void *B, int
  * out[i] = 2 * in[i] for n device doubles, computed exactly as the kernels do
  * (bit-identical to IEEE x + x except for NaN payloads). */
 int jl_selftest_double(const double *in, double *out, int32_t n, void *stream);
+
+/* Self-test of the integer-pipe binary64 arithmetic the binary64 escape
+ * kernels may use: op 0 out = a*b, op 1 out = a*a, op 2 out = a+b (n device
+ * doubles each; b ignored for op 1).  special[i] = 1 marks operands or
+ * results outside the emulated range (subnormal, infinite, NaN, overflow),
+ * for which the kernels use the hardware instructions instead; elsewhere the
+ * result equals the IEEE round-to-nearest-even result bit for bit. */
+int jl_selftest_f64(int32_t op, const double *a, const double *b, double *out, int32_t *special, int32_t n,
+                    void *stream);
 
 /* Writes the built-in 256-entry RGBA8 palette (1024 bytes) to `out` (host).
  * Entry 255 (never-escaped points) is opaque black. */

@@ -71,8 +71,8 @@ def render(c, rect, width, height, max_iter=100, precision="fp32", mode="julia",
     Returns a dict with 'counts' (torch uint8/uint16, shape (H, W)), 'rgba'
     (torch uint8, (H, W, 4)) and 'hist' (torch float32, max_iter + 1) for the
     outputs requested.  `out` may supply preallocated tensors under the same
-    keys.  `variant` = (ppt, unroll, threads, ctas_per_sm) selects a kernel
-    variant explicitly.  Asynchronous on `stream` (default: torch's current
+    keys.  `variant` = (ppt, unroll, threads, ctas_per_sm[, emu]) selects a
+    kernel variant explicitly.  Asynchronous on `stream` (default: torch's current
     stream).
     """
     import torch
@@ -99,9 +99,10 @@ def render(c, rect, width, height, max_iter=100, precision="fp32", mode="julia",
         rc = L.jl_render(cr, ci, _rect(rect), W, H, int(max_iter), prec, md, ct, cnt_ptr, rgba_ptr, pal_ptr,
                          hist_ptr, st)
     else:
-        ppt, unroll, threads, per_sm = (int(v) for v in variant)
+        v = [int(x) for x in variant] + [1] * (5 - len(variant))
+        ppt, unroll, threads, per_sm, emu = v[:5]
         rc = L.jl_render_variant(cr, ci, _rect(rect), W, H, int(max_iter), prec, md, ct, cnt_ptr, rgba_ptr,
-                                 pal_ptr, hist_ptr, ppt, unroll, threads, per_sm, st)
+                                 pal_ptr, hist_ptr, ppt, unroll, threads, per_sm, emu, st)
     check(rc)
     del pal
     return out
@@ -200,7 +201,10 @@ class Batch:
                 opts.fp32_ppt, opts.fp32_unroll, opts.fp32_threads = (int(v) for v in variants["fp32"])
                 opts.variant_flags |= 1
             if "fp64" in variants:
-                opts.fp64_ppt, opts.fp64_unroll, opts.fp64_threads = (int(v) for v in variants["fp64"])
+                v64 = [int(v) for v in variants["fp64"]]
+                opts.fp64_ppt, opts.fp64_unroll, opts.fp64_threads = v64[:3]
+                if len(v64) > 3:
+                    opts.fp64_emu = v64[3]
                 opts.variant_flags |= 2
         opts.cycle_budget = int(cycle_budget)
         pal, pal_ptr = _palette_ptr(palette)
@@ -281,14 +285,14 @@ def autotune(precision="fp32", max_iter=100, calib=None, reps=3):
         ptr, n = None, 0
     check(L.jl_autotune(_PREC[precision], int(max_iter), ptr, n, int(reps), ctypes.byref(res)))
     return {"ppt": res.ppt, "unroll": res.unroll, "threads": res.threads, "ctas_per_sm": res.ctas_per_sm,
-            "ms": res.ms, "candidates": res.candidates}
+            "emu": res.emu, "ms": res.ms, "candidates": res.candidates}
 
 
 def tune_get(precision="fp32", max_iter=100):
     res = _lib.TuneResult()
     check(_lib.lib().jl_tune_get(_PREC[precision], int(max_iter), ctypes.byref(res)))
     return {"ppt": res.ppt, "unroll": res.unroll, "threads": res.threads, "ctas_per_sm": res.ctas_per_sm,
-            "tuned": bool(res.candidates)}
+            "emu": res.emu, "tuned": bool(res.candidates)}
 
 
 def tune_clear():

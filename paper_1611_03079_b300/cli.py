@@ -27,7 +27,7 @@ def main(argv=None):
     p.add_argument("--precision", default="fp32")
     p.add_argument("--mode", default="julia")
     p.add_argument("--repeat", type=int, default=1)
-    p.add_argument("--variant", type=int, nargs=4, default=None)
+    p.add_argument("--variant", type=int, nargs="+", default=None, help="ppt unroll threads ctas_per_sm [emu]")
     p.add_argument("--out", default=None)
     p.add_argument("--probe", action="store_true", help="print the issue-rate probes and exit")
     a = p.parse_args(argv)

@@ -195,6 +195,10 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 if (tt < 32 || tt > 256 || (tt & 31)) { rc = fail(JL_EINVAL, "threads option must be 32..256, multiple of 32"); break; }
                 v.threads = tt;
             }
+            if (g == 1 && o.fp64_emu) {
+                if (o.fp64_emu < 1 || o.fp64_emu > 8) { rc = fail(JL_EINVAL, "fp64_emu must be 1..8"); break; }
+                v.emu = o.fp64_emu;
+            }
             b->variant[g] = v;
             if (v.ppt == 0 && b->tiles[g] > 0x7fffffffll) { rc = fail(JL_EINVAL, "too many tiles for the static kernel"); break; }
             const size_t nb = host[g].size() * sizeof(Frame);

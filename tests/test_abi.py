@@ -120,7 +120,7 @@ def test_product_does_not_reference_oracle():
 
 def test_tune_load_rejects_malformed(L, tmp_path):
     p = tmp_path / "bad.txt"
-    p.write_text("0 0 0 3 3 128 0 1.0\n")  # (ppt 3, unroll 3) is not a variant
+    p.write_text("0 0 0 3 3 128 0 1 1.0\n")  # (ppt 3, unroll 3) is not a variant
     assert L.jl_tune_load(str(p).encode()) == _lib.JL_EINVAL
     assert b"malformed" in L.jl_last_error()
     assert L.jl_tune_load(b"/nonexistent/x") == _lib.JL_EINVAL
