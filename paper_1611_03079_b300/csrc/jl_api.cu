@@ -139,7 +139,10 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
         F->chunk_count = H * F->chunks_per_row;
     }
     F->tiles_x = (W + 31) / 32;
-    F->tile_count = F->tiles_x * ((H + 7) / 8);
+    F->tile_count = F->tiles_x * ((H + 31) / 32);
+    // t / tiles_x = (t * m) >> 40 with m = floor(2^40 / tiles_x) + 1 is exact for
+    // t < 2^40 / tiles_x; here t < tile_count <= 2^22 and tiles_x <= 2^11.
+    F->tiles_x_magic = (1ull << 40) / (uint64_t)F->tiles_x + 1ull;
     F->tile_begin = 0;
     F->precision = prec;
     F->colour_magic = (1ull << 40) / (uint64_t)max_iter + 1ull;

@@ -687,84 +687,74 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
         hbins[t] = 0;
     __syncthreads();
 
+    // tile of 32 x 32 pixels per CTA step; warp w covers an 8 x 4 patch and
+    // each thread four pixels of one column, 8 rows apart
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int dx = (w & 3) * 8 + (lane & 7);
     const int dy = (w >> 2) * 4 + (lane >> 3);
     const long long t_start = clock64();
 
-    // Persistent: tiles blockIdx.x, blockIdx.x + gridDim.x, ...; the next
-    // tile's coordinates are loaded before the current tile is iterated.
-    struct Px {
-        int f, i, j;
-        bool ok;
-        T x, y;
-    };
-    auto locate = [&](long long tile) -> Px {
-        Px q;
-        q.f = 0;
+    for (long long tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x) {
+        if (a.cycle_budget > 0 && (clock64() - t_start) > a.cycle_budget) {
+            if (threadIdx.x == 0 && a.status)
+                atomicExch(a.status, (int)JL_ETIMEOUT);
+            break;
+        }
+        int f = 0;
         if constexpr (BATCH)
-            q.f = a.tile_frame[tile];
-        const Frame &F = BATCH ? a.frames[q.f] : a.single;
-        const int lt = (int)(tile - F.tile_begin);
-        const int ty = lt / F.tiles_x;
-        const int tx = lt - ty * F.tiles_x;
-        q.i = tx * 32 + dx;
-        q.j = ty * 8 + dy;
-        q.ok = q.i < F.W && q.j < F.H;
-        q.x = q.ok ? static_cast<const T *>(F.xs)[q.i] : T(0);
-        q.y = q.ok ? static_cast<const T *>(F.ys)[q.j] : T(0);
-        return q;
-    };
-    long long tile = blockIdx.x;
-    if (tile >= a.total_tiles)
-        return;
-    Px cur = locate(tile);
-    while (true) {
-        const long long next = tile + gridDim.x;
-        const bool more = next < a.total_tiles;
-        bool stop = false;
-        if (a.cycle_budget > 0 && (clock64() - t_start) > a.cycle_budget)
-            stop = true;
-        Px nxt;
-        if (more && !stop)
-            nxt = locate(next);
-        if (cur.ok) {
-            const Frame &F = BATCH ? a.frames[cur.f] : a.single;
+            f = a.tile_frame[tile];
+        const Frame &F = BATCH ? a.frames[f] : a.single;
+        // frame fields used below, read once per tile
+        const int W = F.W, H = F.H, mi = F.max_iter;
+        const bool julia = F.mode == JL_JULIA;
+        const bool safe = F.safe != 0;
+        const T fcr = WorkT<T>::cr(F), fci = WorkT<T>::ci(F);
+        const T *xs = static_cast<const T *>(F.xs);
+        const T *ys = static_cast<const T *>(F.ys);
+        uint8_t *counts = F.counts;
+        const bool u8 = F.count_type == JL_COUNT_U8;
+        uint32_t *rgba = F.rgba;
+        uint32_t *bins = F.hist_bins;
+        const uint64_t cmagic = F.colour_magic;
+        const uint32_t lt = (uint32_t)(tile - F.tile_begin);
+        const uint32_t ty = (uint32_t)(((uint64_t)lt * F.tiles_x_magic) >> 40);
+        const uint32_t tx = lt - ty * (uint32_t)F.tiles_x;
+        const int i = (int)tx * 32 + dx;
+        if (i >= W)
+            continue;
+        const T xv = xs[i];
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int j = (int)ty * 32 + dy + 8 * q;
+            if (j >= H)
+                break;
+            const T yv = ys[j];
             int count;
-            if (F.mode == JL_JULIA)
-                count = escape_blocked(cur.x, cur.y, WorkT<T>::cr(F), WorkT<T>::ci(F), F.max_iter, F.safe != 0);
+            if (julia)
+                count = escape_blocked(xv, yv, fcr, fci, mi, safe);
             else
-                count = escape_blocked(T(0), T(0), cur.x, cur.y, F.max_iter, !in_unsafe_band(cur.x, cur.y));
-            const int p = cur.j * F.W + cur.i;
-            if (F.counts) {
-                if (F.count_type == JL_COUNT_U8)
-                    F.counts[p] = (uint8_t)count;
+                count = escape_blocked(T(0), T(0), xv, yv, mi, !in_unsafe_band(xv, yv));
+            const int p = j * W + i;
+            if (counts) {
+                if (u8)
+                    counts[p] = (uint8_t)count;
                 else
-                    reinterpret_cast<uint16_t *>(F.counts)[p] = (uint16_t)count;
+                    reinterpret_cast<uint16_t *>(counts)[p] = (uint16_t)count;
             }
-            if (F.rgba)
-                F.rgba[p] = pal[colour_index((uint32_t)count, (uint32_t)F.max_iter, F.colour_magic)];
-            if (F.hist_bins) {
+            if (rgba)
+                rgba[p] = pal[colour_index((uint32_t)count, (uint32_t)mi, cmagic)];
+            if (bins) {
                 if (!BATCH && a.hist_smem) {
                     atomicAdd(&hbins[count], 1u);
                 } else {
                     const unsigned act = __activemask();
-                    const unsigned long long key = ((unsigned long long)(unsigned)cur.f << 32) | (unsigned)count;
+                    const unsigned long long key = ((unsigned long long)(unsigned)f << 32) | (unsigned)count;
                     const unsigned grp = __match_any_sync(act, key);
                     if ((grp & ((1u << lane) - 1u)) == 0)
-                        atomicAdd(&F.hist_bins[count], (unsigned)__popc(grp));
+                        atomicAdd(&bins[count], (unsigned)__popc(grp));
                 }
             }
         }
-        if (stop) {
-            if (threadIdx.x == 0 && a.status && more)
-                atomicExch(a.status, (int)JL_ETIMEOUT);
-            break;
-        }
-        if (!more)
-            break;
-        tile = next;
-        cur = nxt;
     }
     if (nb) {
         __syncthreads();

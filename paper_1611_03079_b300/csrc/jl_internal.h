@@ -25,9 +25,10 @@ struct Frame {
     int32_t rows_per_chunk;        // > 1: each chunk is this many whole rows (W < chunk_len)
     uint32_t span_magic;           // ceil(2^20 / W) when rows_per_chunk > 1, else 0
     int32_t chunk_count;           // chunks of this frame
-    int32_t tiles_x;               // static kernel: 32 x 8 pixel tiles per tile row
+    int32_t tiles_x;               // static kernel: 32 x 32 pixel tiles per tile row
     int32_t tile_count;            // static kernel: tiles of this frame
     int32_t pad2;
+    uint64_t tiles_x_magic;        // floor(2^40 / tiles_x) + 1: exact t / tiles_x for t < 2^29
     int64_t tile_begin;            // static kernel: index of this frame's first tile in the launch
     int32_t safe;                  // 1: escape is monotone for every pixel (see escape kernels)
     int32_t precision;             // JL_FP32 / JL_FP64 (working type of xs/ys)
