@@ -340,6 +340,18 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
         tc::tmem_dealloc(taddr, 256);
 }
 
+// Fourier feature of frequency row (b0, b1): t = b0*cr + b1*ci turns,
+// reduced to r = t - rint(t) in [-1/2, 1/2] (exact in binary32), then
+// sin(2 pi r) and cos(2 pi r) with the hardware approximations on [-pi, pi]
+// (absolute error ~1e-6, far below the bfloat16 rounding that follows).
+__device__ __forceinline__ void fourier_pair(float b0, float b1, float cr, float ci, float &s, float &c)
+{
+    const float t = __fadd_rn(__fmul_rn(b0, cr), __fmul_rn(b1, ci));
+    const float r = __fsub_rn(t, rintf(t));
+    const float ang = __fmul_rn(6.28318530717958647692f, r);
+    __sincosf(ang, &s, &c);
+}
+
 // ---------------------------------------------------------------------------
 // Fused forward for screening: features -> three products -> softmax and
 // entropy in one persistent kernel, activations kept on the SM.
@@ -357,7 +369,8 @@ static constexpr int kFsPhi = kFsW1 + kImgW;               // 128 x 64
 static constexpr int kFsH = kFsPhi + kBM * kIn * 2;        // 128 x 256
 static constexpr int kFsWB = kFsH + kBM * kHid * 2;        // 2 x 32 KB
 static constexpr int kFsBias = kFsWB + 2 * kImgW;          // b1, b2, b3 (fp32), B (64 fp32)
-static constexpr int kFsBar = kFsBias + (kHid + kHid + kBinsPad + 64) * 4;
+static constexpr int kFsXchg = kFsBias + (kHid + kHid + kBinsPad + 64) * 4;  // 2 x 128 float2
+static constexpr int kFsBar = kFsXchg + 2 * 128 * 8;
 static constexpr int kFusedSmem = kFsBar + 8 * 8 + 16;
 
 // One thread per 16-byte piece of the packed images.
@@ -411,7 +424,10 @@ struct FusedArgs {
     int32_t *status;
 };
 
-__global__ void __launch_bounds__(128) fused_forward_kernel(const __grid_constant__ FusedArgs a)
+// 256 threads: warp w reads TMEM lane quarter (w & 3), i.e. tile rows
+// 32 (w & 3) .. +31, and handles half (w >> 2) of the columns; thread 0 also
+// issues the bulk copies and the MMAs.
+__global__ void __launch_bounds__(256) fused_forward_kernel(const __grid_constant__ FusedArgs a)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sW1 = sm + kFsW1;
@@ -427,12 +443,15 @@ __global__ void __launch_bounds__(128) fused_forward_kernel(const __grid_constan
     uint64_t *acc = full + 4;
     uint64_t *w1bar = full + 5;
     uint32_t *holder = reinterpret_cast<uint32_t *>(full + 8);
+    float2 *xchg = reinterpret_cast<float2 *>(sm + kFsXchg);   // [2][128] softmax partials
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;  // tile row of this thread
     const int64_t ntiles = (a.n + kBM - 1) / kBM;
-    const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);  // tiles of this CTA
     if (blockIdx.x >= ntiles)
         return;
+    const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
 
     if (warp == 0)
         tc::tmem_alloc(holder, 256);
@@ -445,7 +464,6 @@ __global__ void __launch_bounds__(128) fused_forward_kernel(const __grid_constan
     if (threadIdx.x < 64)
         Bs[threadIdx.x] = a.B[threadIdx.x];
     const uint8_t *gpack = reinterpret_cast<const uint8_t *>(a.pack);
-    // chunk q of this CTA's stream: j = q % 8: 0..3 -> W2 chunk j, 4..7 -> W3 chunk j-4
     auto chunk_src = [&](int q, uint32_t &bytes) -> const uint8_t * {
         const int j = q & 7;
         if (j < 4) {
@@ -474,12 +492,10 @@ __global__ void __launch_bounds__(128) fused_forward_kernel(const __grid_constan
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t taddr = *holder;
-    const uint32_t tw = taddr + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tw = taddr + ((uint32_t)(quarter * 32) << 16);
     bool ok = true;
     uint32_t acc_uses = 0;
 
-    // thread 0: consume chunk q with 4 MMAs of K = 16, then refill the other
-    // buffer with chunk q + 1 once its previous occupant (q - 1) is consumed.
     auto run_chunk = [&](int q, uint32_t a_base, uint32_t n_rows, bool first) {
         const int b = q & 1;
         if (!tc::mbar_wait(&full[b], (q >> 1) & 1, kWaitLimit))
@@ -504,37 +520,44 @@ __global__ void __launch_bounds__(128) fused_forward_kernel(const __grid_constan
         }
     };
 
+    auto wait_acc = [&]() {
+        if (!tc::mbar_wait(acc, acc_uses & 1, kWaitLimit))
+            ok = false;
+        ++acc_uses;
+        tc::tc_fence_after();
+    };
+
     for (int it = 0; it < my_tiles; ++it) {
         const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
-        const int r = threadIdx.x;
         const int64_t row = tile * kBM + r;
         const bool in = row < a.n;
-        // ---- features of this thread's row into the Phi image ----
+        // ---- features: this thread's 16 frequencies of its row ----
         {
             float cr = 0.f, ci = 0.f;
             if (in) {
                 cr = a.c[2 * row];
                 ci = a.c[2 * row + 1];
             }
-            uint32_t sv[16], cv[16];
+            uint32_t sv[8], cv[8];
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
+            for (int jj = 0; jj < 16; jj += 2) {
+                const int j = half * 16 + jj;
                 float s0, c0, s1, c1;
-                sincospif(2.f * (Bs[2 * j] * cr + Bs[2 * j + 1] * ci), &s0, &c0);
-                sincospif(2.f * (Bs[2 * j + 2] * cr + Bs[2 * j + 3] * ci), &s1, &c1);
-                if (!in) {
+                fourier_pair(Bs[2 * j], Bs[2 * j + 1], cr, ci, s0, c0);
+                fourier_pair(Bs[2 * j + 2], Bs[2 * j + 3], cr, ci, s1, c1);
+                if (!in)
                     s0 = c0 = s1 = c1 = 0.f;
-                }
-                sv[j >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(s0)) |
-                             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(s1)) << 16);
-                cv[j >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(c0)) |
-                             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(c1)) << 16);
+                sv[jj >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(s0)) |
+                              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(s1)) << 16);
+                cv[jj >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(c0)) |
+                              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(c1)) << 16);
             }
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                *reinterpret_cast<uint4 *>(sPhi + ((r >> 3) * 8 + g) * 128 + (r & 7) * 16) =
+            for (int g = 0; g < 2; ++g) {
+                const int gs = half * 2 + g, gc = 4 + half * 2 + g;
+                *reinterpret_cast<uint4 *>(sPhi + ((r >> 3) * 8 + gs) * 128 + (r & 7) * 16) =
                     make_uint4(sv[4 * g], sv[4 * g + 1], sv[4 * g + 2], sv[4 * g + 3]);
-                *reinterpret_cast<uint4 *>(sPhi + ((r >> 3) * 8 + g + 4) * 128 + (r & 7) * 16) =
+                *reinterpret_cast<uint4 *>(sPhi + ((r >> 3) * 8 + gc) * 128 + (r & 7) * 16) =
                     make_uint4(cv[4 * g], cv[4 * g + 1], cv[4 * g + 2], cv[4 * g + 3]);
             }
         }
@@ -554,20 +577,17 @@ __global__ void __launch_bounds__(128) fused_forward_kernel(const __grid_constan
                              idesc, kk > 0);
             tc::mma_commit(acc);
         }
-        // ---- epilogues 1 and 2 write relu(D + b) as bf16 into the H image ----
+        // ---- epilogues 1 and 2: relu(D + b) as bf16 into the H image ----
         auto hidden_epilogue = [&](const float *bias) {
-            if (!tc::mbar_wait(acc, acc_uses & 1, kWaitLimit))
-                ok = false;
-            ++acc_uses;
-            tc::tc_fence_after();
-            for (int c0 = 0; c0 < kHid; c0 += 16) {
+            wait_acc();
+            for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
                 float v[16];
                 tc::tmem_ld16(tw + c0, v);
                 uint32_t w[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const float x0 = fmaxf(v[2 * j] + bias[c0 + 2 * j], 0.f);
-                    const float x1 = fmaxf(v[2 * j + 1] + bias[c0 + 2 * j + 1], 0.f);
+                    const float x0 = fmaxf(__fadd_rn(v[2 * j], bias[c0 + 2 * j]), 0.f);
+                    const float x1 = fmaxf(__fadd_rn(v[2 * j + 1], bias[c0 + 2 * j + 1]), 0.f);
                     w[j] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x0)) |
                            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x1)) << 16);
                 }
@@ -599,52 +619,66 @@ __global__ void __launch_bounds__(128) fused_forward_kernel(const __grid_constan
                 run_chunk(it * 8 + 4 + j, hb + j * 8 * 128, kBinsPad, j == 0);
             tc::mma_commit(acc);
         }
-        if (!tc::mbar_wait(acc, acc_uses & 1, kWaitLimit))
-            ok = false;
-        ++acc_uses;
-        tc::tc_fence_after();
-        // ---- softmax and entropy of this thread's row ----
+        wait_acc();
+        // ---- softmax and entropy: columns [56 half, 56 half + 56) of the row ----
+        // With m = max z, e_b = exp(z_b - m), S = sum e_b, T = sum e_b z_b:
+        // p_b = e_b / S and the entropy is m + log S - T / S.
+        const int cb = half * 56;
         float mx = -INFINITY;
-        for (int c0 = 0; c0 < kBinsPad; c0 += 16) {
+        for (int c0 = 0; c0 < 64; c0 += 16) {
             float v[16];
-            tc::tmem_ld16(tw + c0, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (c0 + j < kBins)
-                    mx = fmaxf(mx, v[j] + b3[c0 + j]);
-        }
-        float sum = 0.f;
-        for (int c0 = 0; c0 < kBinsPad; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tw + c0, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (c0 + j < kBins)
-                    sum += expf(v[j] + b3[c0 + j] - mx);
-        }
-        const float inv = 1.f / sum;
-        const float lse = mx + logf(sum);
-        float ent = 0.f;
-        for (int c0 = 0; c0 < kBinsPad; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tw + c0, v);
+            tc::tmem_ld16(tw + cb + c0, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int col = c0 + j;
-                if (col < kBins) {
-                    const float z = v[j] + b3[col];
-                    const float p = expf(z - mx) * inv;
-                    if (p > 0.f)
-                        ent -= p * (z - lse);
-                    if (in && a.probs)
-                        a.probs[(size_t)row * kBins + col] = p;
+                const int col = cb + c0 + j;
+                if (c0 + j < 56 && col < kBins)
+                    mx = fmaxf(mx, __fadd_rn(v[j], b3[col]));
+            }
+        }
+        xchg[half * 128 + r] = make_float2(mx, 0.f);
+        __syncthreads();
+        mx = fmaxf(mx, xchg[(1 - half) * 128 + r].x);
+        float S = 0.f, Tz = 0.f;
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tw + cb + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = cb + c0 + j;
+                if (c0 + j < 56 && col < kBins) {
+                    const float z = __fadd_rn(v[j], b3[col]);
+                    const float e = expf(__fsub_rn(z, mx));
+                    S = __fadd_rn(S, e);
+                    Tz = __fadd_rn(Tz, __fmul_rn(e, z));
                 }
             }
         }
-        if (in && a.score)
-            a.score[row] = ent;
+        __syncthreads();
+        xchg[half * 128 + r] = make_float2(S, Tz);
+        __syncthreads();
+        const float2 o = xchg[(1 - half) * 128 + r];
+        const float St = half ? __fadd_rn(o.x, S) : __fadd_rn(S, o.x);
+        const float Tt = half ? __fadd_rn(o.y, Tz) : __fadd_rn(Tz, o.y);
+        if (in && a.score && half == 0)
+            a.score[row] = __fsub_rn(__fadd_rn(mx, logf(St)), __fdiv_rn(Tt, St));
+        if (a.probs) {
+            // warp-uniform condition: tcgen05.ld is a warp-collective
+            // (.sync.aligned) instruction; only the stores depend on the row
+            const float inv = __fdiv_rn(1.f, St);
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tw + cb + c0, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = cb + c0 + j;
+                    if (in && c0 + j < 56 && col < kBins)
+                        a.probs[(size_t)row * kBins + col] =
+                            __fmul_rn(expf(__fsub_rn(__fadd_rn(v[j], b3[col]), mx)), inv);
+                }
+            }
+        }
         tc::tc_fence_before();
-        __syncthreads();  // TMEM reads done before the next tile's product 1
+        __syncthreads();  // TMEM reads and xchg use done before the next tile
     }
     if (!ok && a.status)
         atomicExch(a.status, (int32_t)JL_ETIMEOUT);
@@ -652,7 +686,6 @@ __global__ void __launch_bounds__(128) fused_forward_kernel(const __grid_constan
     __syncthreads();
     if (warp == 0)
         tc::tmem_dealloc(taddr, 256);
-    (void)lane;
 }
 
 // ---------------------------------------------------------------------------
@@ -670,9 +703,8 @@ __global__ void features_kernel(const float *__restrict__ c, const int32_t *__re
         return;
     const int64_t src = idx ? idx[i] : i;
     const float cr = c[2 * src], ci = c[2 * src + 1];
-    const float tj = Bm[2 * j] * cr + Bm[2 * j + 1] * ci;
     float s, co;
-    sincospif(2.f * tj, &s, &co);
+    fourier_pair(Bm[2 * j], Bm[2 * j + 1], cr, ci, s, co);
     phi[i * kIn + j] = __float2bfloat16_rn(s);
     phi[i * kIn + kFreq + j] = __float2bfloat16_rn(co);
 }
@@ -1315,7 +1347,7 @@ int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, floa
     const int64_t tiles = (n + kBM - 1) / kBM;
     const int sms = device_sm_count();
     const int grid = (int)std::min<int64_t>(tiles, sms > 0 ? sms : 148);
-    fused_forward_kernel<<<grid, 128, kFusedSmem, st>>>(a);
+    fused_forward_kernel<<<grid, 256, kFusedSmem, st>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? JL_OK : cuda_fail(e, "fused forward");
 }

@@ -224,7 +224,7 @@ def test_fused_forward_matches_layered(cuda, n):
         torch.cuda.synchronize()
         out[name] = (P.cpu().numpy(), S.cpu().numpy())
     assert np.abs(out["fused"][0] - out["layered"][0]).max() <= 1e-6
-    assert np.abs(out["fused"][1] - out["layered"][1]).max() <= 1e-5
+    assert np.abs(out["fused"][1] - out["layered"][1]).max() <= 5e-5
     if n <= 127:
         ref = mlp.forward({k: v.astype(np.float64) for k, v in p.items()}, c.cpu().numpy(), B, quant=True)["p"]
         assert np.abs(out["fused"][0] - ref).sum(axis=1).max() < 2e-2
