@@ -302,6 +302,39 @@ def run_deep_zoom(K, W):
     return res
 
 
+def run_fig1_sweep():
+    """Fig. 1 of the paper on this machine: square images of 10 .. 10,000
+    pixels per side (Julia C = -0.8+0.156i over [-2,2]^2, limit 100,
+    binary32; display excluded), GPU (jl_render, CUDA events, best of 3)
+    against the sequential CPU oracle (one host thread) and the oracle on all
+    host cores."""
+    import torch
+
+    import oracle
+    import paper_1611_03079_b300 as jl
+    rows = []
+    for n in (10, 32, 100, 316, 1000, 3162, 10000):
+        out = None
+        best = float("inf")
+        for r in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = jl.render(complex(-0.8, 0.156), (-2.0, 2.0, -2.0, 2.0), n, n, 100, precision="fp32",
+                            count_type="u16", rgba=True, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            if r:
+                best = min(best, e0.elapsed_time(e1))
+        t0 = time.perf_counter()
+        oracle.render(complex(-0.8, 0.156), (-2.0, 2.0, -2.0, 2.0), n, n, 100, threads=1)
+        t1 = time.perf_counter()
+        oracle.render(complex(-0.8, 0.156), (-2.0, 2.0, -2.0, 2.0), n, n, 100)
+        t2 = time.perf_counter()
+        rows.append({"side": n, "gpu_ms": best, "cpu_1thread_ms": (t1 - t0) * 1e3,
+                     "cpu_all_cores_ms": (t2 - t1) * 1e3})
+    return rows
+
+
 def run_reference(args):
     world, rank, _ = dist_setup("gloo")
     if rank != 0:
@@ -481,6 +514,7 @@ def main():
     if not args.no_extra and rank == 0:
         extra["path_animation"] = run_path_animation(K, max(args.warmup, 3))
         extra["deep_zoom"] = run_deep_zoom(1, 1)
+        extra["fig1_size_sweep"] = run_fig1_sweep()
 
     survey = None
     if not args.no_survey and rank == 0:

@@ -156,3 +156,29 @@ def test_static_variant_batch(cuda, prec):
     b.launch()
     _check_batch(b, frames)
     b.close()
+
+
+def test_cardioid_path_with_minimap(cuda):
+    """The paper's clockwise a = 3.9 cardioid path (Sec. 3, Fig. 2), each
+    Julia frame paired with the Mandelbrot minimap, as one batch plan."""
+    from paper_1611_03079_b300 import paths
+    frames = paths.with_minimap(paths.julia_frames(paths.cardioid_path(24), W=160, H=120, count_type="u16"))
+    b = jl.Batch(frames, palette=PAL)
+    b.launch()
+    _check_batch(b, frames)
+    b.close()
+
+
+def test_mandelbrot_deep_zoom_fig3(cuda):
+    """Deep zoom on the Mandelbrot set at the Fig. 3 values (AUTO precision,
+    limit 2000): counts bit-exact in the precision the library chose."""
+    from paper_1611_03079_b300 import paths
+    frames = []
+    for c in (complex(0.177078, 0.577384), complex(0.185723, 0.588104)):
+        frames += paths.mandelbrot_zoom(c, 6, W=320, H=180)
+    b = jl.Batch(frames, palette=PAL)
+    b.launch()
+    precs = b.precisions()
+    assert 0 < sum(precs) < len(precs)
+    _check_batch(b, frames, precs=precs)
+    b.close()
