@@ -340,6 +340,14 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
         tc::tmem_dealloc(taddr, 256);
 }
 
+// 2^x with the hardware approximation (relative error about 2^-22).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Fourier feature of frequency row (b0, b1): t = b0*cr + b1*ci turns,
 // reduced to r = t - rint(t) in [-1/2, 1/2] (exact in binary32), then
 // sin(2 pi r) and cos(2 pi r) with the hardware approximations on [-pi, pi]
@@ -356,22 +364,22 @@ __device__ __forceinline__ void fourier_pair(float b0, float b1, float cr, float
 // Fused forward for screening: features -> three products -> softmax and
 // entropy in one persistent kernel, activations kept on the SM.
 // Weights are pre-packed in global memory as shared-memory images of the
-// K-major core-matrix layout: W1 as one 256x64 image (resident per CTA), W2
-// as four 256x64 K-chunks and W3 as four 112x64 K-chunks, streamed through a
-// double buffer with cp.async.bulk (completion as mbarrier transaction bytes).
+// K-major core-matrix layout: W1 as one 256x64 image, W2 as four 256x64
+// K-chunks and W3 as four 112x64 K-chunks, all nine streamed per tile through
+// a double buffer with cp.async.bulk (completion as mbarrier transaction
+// bytes); the chunks stay L2-resident across CTAs.
 // ---------------------------------------------------------------------------
 static constexpr int kImgW = 256 * 64 * 2;                 // 32 KB: 256 rows x 64 k
 static constexpr int kImgW3 = kBinsPad * 64 * 2;           // 14 KB: 112 rows x 64 k
 static constexpr int kPackElems = (kImgW + 4 * kImgW + 4 * kImgW3) / 2;  // bf16 elements
-// shared-memory map of the fused kernel (bytes)
-static constexpr int kFsW1 = 0;
-static constexpr int kFsPhi = kFsW1 + kImgW;               // 128 x 64
-static constexpr int kFsH = kFsPhi + kBM * kIn * 2;        // 128 x 256
-static constexpr int kFsWB = kFsH + kBM * kHid * 2;        // 2 x 32 KB
-static constexpr int kFsBias = kFsWB + 2 * kImgW;          // b1, b2, b3 (fp32), B (64 fp32)
-static constexpr int kFsXchg = kFsBias + (kHid + kHid + kBinsPad + 64) * 4;  // 2 x 128 float2
-static constexpr int kFsBar = kFsXchg + 2 * 128 * 8;
-static constexpr int kFusedSmem = kFsBar + 8 * 8 + 16;
+// shared-memory map of the fused kernel (bytes): two 128-row halves
+static constexpr int kFsPhi = 0;                               // 2 x (128 x 64 bf16)
+static constexpr int kFsH = kFsPhi + 2 * kBM * kIn * 2;        // 2 x (128 x 256 bf16)
+static constexpr int kFsWB = kFsH + 2 * kBM * kHid * 2;        // 2 x 32 KB weight chunks
+static constexpr int kFsBias = kFsWB + 2 * kImgW;              // b1, b2, b3 (fp32), B (64 fp32)
+static constexpr int kFsBar = kFsBias + (kHid + kHid + kBinsPad + 64) * 4;
+static constexpr int kFusedSmem = kFsBar + 8 * 8;
+static_assert(kFusedSmem <= 232448, "fused forward exceeds the shared-memory limit");
 
 // One thread per 16-byte piece of the packed images.
 __global__ void pack_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *__restrict__ out)
@@ -424,16 +432,19 @@ struct FusedArgs {
     int32_t *status;
 };
 
-// 256 threads: warp w reads TMEM lane quarter (w & 3), i.e. tile rows
-// 32 (w & 3) .. +31, and handles half (w >> 2) of the columns; thread 0 also
-// issues the bulk copies and the MMAs.
+// 256 threads, 256-row tiles.  Warp w serves tile half h = w >> 2 (rows
+// 128 h .. 128 h + 127) and reads TMEM lane quarter (w & 3) of that half's
+// accumulator (columns 256 h .. 256 h + 255).  Each streamed weight chunk is
+// consumed by the MMAs of both halves before it is replaced, so the weight
+// traffic per row is half that of a 128-row tile.  Chunks per tile:
+// W1 (256 x 64), W2 K-chunks 0..3 (256 x 64), W3 K-chunks 0..3 (112 x 64).
+// Thread 0 also issues the bulk copies and the MMAs.
 __global__ void __launch_bounds__(256) fused_forward_kernel(const __grid_constant__ FusedArgs a)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *sW1 = sm + kFsW1;
-    uint8_t *sPhi = sm + kFsPhi;
-    uint8_t *sH = sm + kFsH;
-    uint8_t *sWB = sm + kFsWB;
+    uint8_t *sPhi = sm + kFsPhi;           // [2][16 KB]
+    uint8_t *sH = sm + kFsH;               // [2][64 KB]
+    uint8_t *sWB = sm + kFsWB;             // [2][32 KB]
     float *b1 = reinterpret_cast<float *>(sm + kFsBias);
     float *b2 = b1 + kHid;
     float *b3 = b2 + kHid;
@@ -441,20 +452,18 @@ __global__ void __launch_bounds__(256) fused_forward_kernel(const __grid_constan
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + kFsBar);  // [2]
     uint64_t *empty = full + 2;                                  // [2]
     uint64_t *acc = full + 4;
-    uint64_t *w1bar = full + 5;
-    uint32_t *holder = reinterpret_cast<uint32_t *>(full + 8);
-    float2 *xchg = reinterpret_cast<float2 *>(sm + kFsXchg);   // [2][128] softmax partials
+    uint32_t *holder = reinterpret_cast<uint32_t *>(full + 6);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quarter = warp & 3, half = warp >> 2;
-    const int r = quarter * 32 + lane;  // tile row of this thread
-    const int64_t ntiles = (a.n + kBM - 1) / kBM;
+    const int r = quarter * 32 + lane;  // row within this warp group's half
+    const int64_t ntiles = (a.n + 2 * kBM - 1) / (2 * kBM);
     if (blockIdx.x >= ntiles)
         return;
     const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
 
     if (warp == 0)
-        tc::tmem_alloc(holder, 256);
+        tc::tmem_alloc(holder, 512);
     for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
         b1[i] = a.params[kOffB1 + i];
         b2[i] = a.params[kOffB2 + i];
@@ -464,26 +473,25 @@ __global__ void __launch_bounds__(256) fused_forward_kernel(const __grid_constan
     if (threadIdx.x < 64)
         Bs[threadIdx.x] = a.B[threadIdx.x];
     const uint8_t *gpack = reinterpret_cast<const uint8_t *>(a.pack);
+    // chunk q of this CTA's stream: j = q % 9: 0 -> W1, 1..4 -> W2, 5..8 -> W3
     auto chunk_src = [&](int q, uint32_t &bytes) -> const uint8_t * {
-        const int j = q & 7;
-        if (j < 4) {
+        const int j = q % 9;
+        if (j < 5) {
             bytes = kImgW;
-            return gpack + kImgW + (size_t)j * kImgW;
+            return gpack + (size_t)j * kImgW;
         }
         bytes = kImgW3;
-        return gpack + 5 * (size_t)kImgW + (size_t)(j - 4) * kImgW3;
+        return gpack + 5 * (size_t)kImgW + (size_t)(j - 5) * kImgW3;
     };
-    const int total_chunks = my_tiles * 8;
+    const int total_chunks = my_tiles * 9;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&empty[i], 1);
         }
         tc::mbar_init(acc, 1);
-        tc::mbar_init(w1bar, 1);
         tc::fence_mbar_init();
         tc::fence_proxy_async_smem();
-        tc::bulk_load(sW1, gpack, kImgW, w1bar);
         uint32_t bytes;
         const uint8_t *src = chunk_src(0, bytes);
         tc::bulk_load(sWB, src, bytes, &full[0]);
@@ -492,11 +500,14 @@ __global__ void __launch_bounds__(256) fused_forward_kernel(const __grid_constan
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t taddr = *holder;
-    const uint32_t tw = taddr + ((uint32_t)(quarter * 32) << 16);
+    // this thread's TMEM row: lane quarter of the warp, accumulator of the half
+    const uint32_t tw = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 256);
     bool ok = true;
     uint32_t acc_uses = 0;
 
-    auto run_chunk = [&](int q, uint32_t a_base, uint32_t n_rows, bool first) {
+    // thread 0: wait for chunk q, issue the MMAs of both halves, and refill
+    // the other buffer with chunk q + 1 once its previous occupant is consumed.
+    auto run_chunk = [&](int q, uint32_t a0, uint32_t a1, uint32_t a_sbo, uint32_t n_rows, bool first) {
         const int b = q & 1;
         if (!tc::mbar_wait(&full[b], (q >> 1) & 1, kWaitLimit))
             ok = false;
@@ -504,10 +515,14 @@ __global__ void __launch_bounds__(256) fused_forward_kernel(const __grid_constan
         const uint32_t idesc = tc::idesc_bf16(kBM, n_rows);
         const uint32_t bb = tc::smem_u32(sWB + b * kImgW);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = tc::smem_desc(a_base + kk * 256, 128, 4096);
-            const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, 1024);
-            tc::mma_bf16(taddr, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t ab = h ? a1 : a0;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = tc::smem_desc(ab + kk * 256, 128, a_sbo);
+                const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, 1024);
+                tc::mma_bf16(taddr + (uint32_t)(h * 256), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+            }
         }
         tc::mma_commit(&empty[b]);
         if (q + 1 < total_chunks) {
@@ -527,165 +542,151 @@ __global__ void __launch_bounds__(256) fused_forward_kernel(const __grid_constan
         tc::tc_fence_after();
     };
 
-    for (int it = 0; it < my_tiles; ++it) {
-        const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
-        const int64_t row = tile * kBM + r;
-        const bool in = row < a.n;
-        // ---- features: this thread's 16 frequencies of its row ----
-        {
-            float cr = 0.f, ci = 0.f;
-            if (in) {
-                cr = a.c[2 * row];
-                ci = a.c[2 * row + 1];
-            }
-            uint32_t sv[8], cv[8];
+    uint8_t *myPhi = sPhi + half * (kBM * kIn * 2);
+    uint8_t *myH = sH + half * (kBM * kHid * 2);
+
+    // Features of this thread's row of tile `tile` into its half's Phi image.
+    auto make_features = [&](int64_t tile) {
+        const int64_t row = tile * (2 * kBM) + half * kBM + r;
+        float cr = 0.f, ci = 0.f;
+        if (row < a.n) {
+            cr = a.c[2 * row];
+            ci = a.c[2 * row + 1];
+        }
+        uint32_t sv[16], cv[16];
 #pragma unroll
-            for (int jj = 0; jj < 16; jj += 2) {
-                const int j = half * 16 + jj;
-                float s0, c0, s1, c1;
-                fourier_pair(Bs[2 * j], Bs[2 * j + 1], cr, ci, s0, c0);
-                fourier_pair(Bs[2 * j + 2], Bs[2 * j + 3], cr, ci, s1, c1);
-                if (!in)
-                    s0 = c0 = s1 = c1 = 0.f;
-                sv[jj >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(s0)) |
-                              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(s1)) << 16);
-                cv[jj >> 1] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(c0)) |
-                              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(c1)) << 16);
-            }
+        for (int j = 0; j < 32; j += 2) {
+            float s0, c0, s1, c1;
+            fourier_pair(Bs[2 * j], Bs[2 * j + 1], cr, ci, s0, c0);
+            fourier_pair(Bs[2 * j + 2], Bs[2 * j + 3], cr, ci, s1, c1);
+            sv[j >> 1] = tc::pack_bf16x2(s0, s1);
+            cv[j >> 1] = tc::pack_bf16x2(c0, c1);
+        }
+        if (row >= a.n) {
 #pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                const int gs = half * 2 + g, gc = 4 + half * 2 + g;
-                *reinterpret_cast<uint4 *>(sPhi + ((r >> 3) * 8 + gs) * 128 + (r & 7) * 16) =
-                    make_uint4(sv[4 * g], sv[4 * g + 1], sv[4 * g + 2], sv[4 * g + 3]);
-                *reinterpret_cast<uint4 *>(sPhi + ((r >> 3) * 8 + gc) * 128 + (r & 7) * 16) =
-                    make_uint4(cv[4 * g], cv[4 * g + 1], cv[4 * g + 2], cv[4 * g + 3]);
+            for (int j = 0; j < 16; ++j)
+                sv[j] = cv[j] = 0u;
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            *reinterpret_cast<uint4 *>(myPhi + ((r >> 3) * 8 + g) * 128 + (r & 7) * 16) =
+                make_uint4(sv[4 * g], sv[4 * g + 1], sv[4 * g + 2], sv[4 * g + 3]);
+            *reinterpret_cast<uint4 *>(myPhi + ((r >> 3) * 8 + g + 4) * 128 + (r & 7) * 16) =
+                make_uint4(cv[4 * g], cv[4 * g + 1], cv[4 * g + 2], cv[4 * g + 3]);
+        }
+        tc::fence_proxy_async_smem();
+    };
+
+    // relu(D + b) as bf16 into this half's H image, 32 columns per TMEM load.
+    auto hidden_epilogue = [&](const float *bias) {
+        wait_acc();
+#pragma unroll 1
+        for (int c0 = 0; c0 < kHid; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(tw + c0, v);
+            uint32_t w[16];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 bq = *reinterpret_cast<const float4 *>(bias + c0 + 4 * q);
+                w[2 * q] = tc::pack_relu_bf16x2(__fadd_rn(v[4 * q], bq.x), __fadd_rn(v[4 * q + 1], bq.y));
+                w[2 * q + 1] = tc::pack_relu_bf16x2(__fadd_rn(v[4 * q + 2], bq.z), __fadd_rn(v[4 * q + 3], bq.w));
             }
+            const int g = c0 >> 3;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4 *>(myH + ((r >> 3) * 32 + g + q) * 128 + (r & 7) * 16) =
+                    make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         }
         tc::fence_proxy_async_smem();
         tc::tc_fence_before();
         __syncthreads();
-        // ---- product 1: Phi (128 x 64) x W1^T -> D (128 x 256) ----
+    };
+
+    make_features(blockIdx.x);
+    tc::tc_fence_before();
+    __syncthreads();
+    // Each later tile's features are written during the previous tile's
+    // product 2 and published by the barrier that ends its second epilogue.
+    for (int it = 0; it < my_tiles; ++it) {
+        const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
+        const int64_t row = tile * (2 * kBM) + half * kBM + r;
+        const bool in = row < a.n;
+        // ---- product 1: Phi (2 x 128 x 64) x W1^T ----
         if (threadIdx.x == 0) {
             tc::tc_fence_after();
-            if (it == 0 && !tc::mbar_wait(w1bar, 0, kWaitLimit))
-                ok = false;
-            const uint32_t a0 = tc::smem_u32(sPhi), b0 = tc::smem_u32(sW1);
-            const uint32_t idesc = tc::idesc_bf16(kBM, kHid);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                tc::mma_bf16(taddr, tc::smem_desc(a0 + kk * 256, 128, 1024), tc::smem_desc(b0 + kk * 256, 128, 1024),
-                             idesc, kk > 0);
+            run_chunk(it * 9, tc::smem_u32(sPhi), tc::smem_u32(sPhi + kBM * kIn * 2), 1024, kHid, true);
             tc::mma_commit(acc);
         }
-        // ---- epilogues 1 and 2: relu(D + b) as bf16 into the H image ----
-        auto hidden_epilogue = [&](const float *bias) {
-            wait_acc();
-            for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
-                float v[16];
-                tc::tmem_ld16(tw + c0, v);
-                uint32_t w[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float x0 = fmaxf(__fadd_rn(v[2 * j], bias[c0 + 2 * j]), 0.f);
-                    const float x1 = fmaxf(__fadd_rn(v[2 * j + 1], bias[c0 + 2 * j + 1]), 0.f);
-                    w[j] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x0)) |
-                           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x1)) << 16);
-                }
-                const int g = c0 >> 3;
-                *reinterpret_cast<uint4 *>(sH + ((r >> 3) * 32 + g) * 128 + (r & 7) * 16) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4 *>(sH + ((r >> 3) * 32 + g + 1) * 128 + (r & 7) * 16) =
-                    make_uint4(w[4], w[5], w[6], w[7]);
-            }
-            tc::fence_proxy_async_smem();
-            tc::tc_fence_before();
-            __syncthreads();
-        };
         hidden_epilogue(b1);
-        // ---- product 2: H1 (128 x 256) x W2^T, four streamed K-chunks ----
+        // ---- product 2: H1 x W2^T, four streamed K-chunks ----
         if (threadIdx.x == 0) {
             tc::tc_fence_after();
-            const uint32_t hb = tc::smem_u32(sH);
+            const uint32_t h0 = tc::smem_u32(sH), h1 = tc::smem_u32(sH + kBM * kHid * 2);
             for (int j = 0; j < 4; ++j)
-                run_chunk(it * 8 + j, hb + j * 8 * 128, kHid, j == 0);
+                run_chunk(it * 9 + 1 + j, h0 + j * 8 * 128, h1 + j * 8 * 128, 4096, kHid, j == 0);
             tc::mma_commit(acc);
         }
+        // the Phi images were consumed by product 1 (its commit was waited
+        // for), so the next tile's features are built while product 2 runs
+        if (it + 1 < my_tiles)
+            make_features(tile + gridDim.x);
         hidden_epilogue(b2);
-        // ---- product 3: H2 (128 x 256) x W3^T -> logits (128 x 112) ----
+        // ---- product 3: H2 x W3^T -> logits (112 columns) ----
         if (threadIdx.x == 0) {
             tc::tc_fence_after();
-            const uint32_t hb = tc::smem_u32(sH);
+            const uint32_t h0 = tc::smem_u32(sH), h1 = tc::smem_u32(sH + kBM * kHid * 2);
             for (int j = 0; j < 4; ++j)
-                run_chunk(it * 8 + 4 + j, hb + j * 8 * 128, kBinsPad, j == 0);
+                run_chunk(it * 9 + 5 + j, h0 + j * 8 * 128, h1 + j * 8 * 128, 4096, kBinsPad, j == 0);
             tc::mma_commit(acc);
         }
         wait_acc();
-        // ---- softmax and entropy: columns [56 half, 56 half + 56) of the row ----
-        // With m = max z, e_b = exp(z_b - m), S = sum e_b, T = sum e_b z_b:
-        // p_b = e_b / S and the entropy is m + log S - T / S.
-        const int cb = half * 56;
-        float mx = -INFINITY;
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tw + cb + c0, v);
+        // ---- softmax and entropy of this thread's row ----
+        // z_b = D_b + b3_b, m = max z, e_b = 2^((z_b - m) log2 e), S = sum e_b,
+        // T = sum e_b z_b: p_b = e_b / S and the entropy is m + log S - T / S.
+        float z[kBinsPad];
+        tc::tmem_ld32(tw, z);
+        tc::tmem_ld32(tw + 32, z + 32);
+        tc::tmem_ld32(tw + 64, z + 64);
+        {
+            float t16[16];
+            tc::tmem_ld16(tw + 96, t16);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = cb + c0 + j;
-                if (c0 + j < 56 && col < kBins)
-                    mx = fmaxf(mx, __fadd_rn(v[j], b3[col]));
-            }
-        }
-        xchg[half * 128 + r] = make_float2(mx, 0.f);
-        __syncthreads();
-        mx = fmaxf(mx, xchg[(1 - half) * 128 + r].x);
-        float S = 0.f, Tz = 0.f;
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tw + cb + c0, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = cb + c0 + j;
-                if (c0 + j < 56 && col < kBins) {
-                    const float z = __fadd_rn(v[j], b3[col]);
-                    const float e = expf(__fsub_rn(z, mx));
-                    S = __fadd_rn(S, e);
-                    Tz = __fadd_rn(Tz, __fmul_rn(e, z));
-                }
-            }
-        }
-        __syncthreads();
-        xchg[half * 128 + r] = make_float2(S, Tz);
-        __syncthreads();
-        const float2 o = xchg[(1 - half) * 128 + r];
-        const float St = half ? __fadd_rn(o.x, S) : __fadd_rn(S, o.x);
-        const float Tt = half ? __fadd_rn(o.y, Tz) : __fadd_rn(Tz, o.y);
-        if (in && a.score && half == 0)
-            a.score[row] = __fsub_rn(__fadd_rn(mx, logf(St)), __fdiv_rn(Tt, St));
-        if (a.probs) {
-            // warp-uniform condition: tcgen05.ld is a warp-collective
-            // (.sync.aligned) instruction; only the stores depend on the row
-            const float inv = __fdiv_rn(1.f, St);
-            for (int c0 = 0; c0 < 64; c0 += 16) {
-                float v[16];
-                tc::tmem_ld16(tw + cb + c0, v);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = cb + c0 + j;
-                    if (in && c0 + j < 56 && col < kBins)
-                        a.probs[(size_t)row * kBins + col] =
-                            __fmul_rn(expf(__fsub_rn(__fadd_rn(v[j], b3[col]), mx)), inv);
-                }
-            }
+            for (int j = 0; j < 16; ++j)
+                z[96 + j] = t16[j];
         }
         tc::tc_fence_before();
-        __syncthreads();  // TMEM reads and xchg use done before the next tile
+        __syncthreads();  // every TMEM read of this tile is done: the next product 1 may overwrite it
+        float mx = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < kBins; ++j) {
+            z[j] = __fadd_rn(z[j], b3[j]);
+            mx = fmaxf(mx, z[j]);
+        }
+        const float kLog2e = 1.4426950408889634f;
+        const float mb = -__fmul_rn(mx, kLog2e);
+        float S = 0.f, Tz = 0.f;
+#pragma unroll
+        for (int j = 0; j < kBins; ++j) {
+            const float e = ex2_approx(__fmaf_rn(z[j], kLog2e, mb));
+            S = __fadd_rn(S, e);
+            Tz = __fmaf_rn(e, z[j], Tz);
+        }
+        if (in && a.score)
+            a.score[row] = __fsub_rn(__fadd_rn(mx, logf(S)), __fdiv_rn(Tz, S));
+        if (in && a.probs) {
+            const float inv = __fdiv_rn(1.f, S);
+            float *prow = a.probs + (size_t)row * kBins;
+#pragma unroll
+            for (int j = 0; j < kBins; ++j)
+                prow[j] = __fmul_rn(ex2_approx(__fmaf_rn(z[j], kLog2e, mb)), inv);
+        }
     }
     if (!ok && a.status)
         atomicExch(a.status, (int32_t)JL_ETIMEOUT);
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        tc::tmem_dealloc(taddr, 256);
+        tc::tmem_dealloc(taddr, 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -1344,7 +1345,7 @@ int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, floa
     a.probs = probs;
     a.score = score;
     a.status = md->status;
-    const int64_t tiles = (n + kBM - 1) / kBM;
+    const int64_t tiles = (n + 2 * kBM - 1) / (2 * kBM);
     const int sms = device_sm_count();
     const int grid = (int)std::min<int64_t>(tiles, sms > 0 ? sms : 148);
     fused_forward_kernel<<<grid, 256, kFusedSmem, st>>>(a);
