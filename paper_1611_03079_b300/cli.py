@@ -2,6 +2,7 @@
 
   python -m paper_1611_03079_b300.cli --workload sweep --index 13 --size 2048 --repeat 3
   python -m paper_1611_03079_b300.cli --c -0.8+0.156j --rect -2 2 -2 2 --W 512 --H 512 --out f.npy
+  python -m paper_1611_03079_b300.cli --workload forward --n 1048576 --repeat 3
 
 Renders one frame `repeat` times on cuda:0 and prints the kernel-bracketed
 time and pixel-iterations per second; optionally saves counts (.npy).  Also
@@ -15,7 +16,8 @@ import numpy as np
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--workload", choices=["sweep", "single", "path"], default=None)
+    p.add_argument("--workload", choices=["sweep", "single", "path", "forward"], default=None)
+    p.add_argument("--n", type=int, default=1 << 20, help="forward workload: number of C values screened")
     p.add_argument("--frames", type=int, default=72, help="path workload: first N frames as one batch plan")
     p.add_argument("--index", type=int, default=0)
     p.add_argument("--size", type=int, default=4096)
@@ -41,6 +43,8 @@ def main(argv=None):
 
     if a.workload == "path":
         return path(a)
+    if a.workload == "forward":
+        return forward(a)
     if a.workload == "sweep":
         f = wl.throughput_sweep(a.size)[a.index]
     elif a.workload == "single":
@@ -91,6 +95,30 @@ def path(a):
     print(json.dumps({"frames": len(frames), "pixels": pix, "ms": times, "gpixel_s": pix / (min(times) * 1e-3) / 1e9,
                       "status": b.status()}))
     b.close()
+
+
+def forward(a):
+    """The fused surrogate forward (entropy scores only) over n seeded C
+    values, with a seeded random-init network, `repeat` times."""
+    import torch
+
+    from paper_1611_03079_b300 import surrogate, workloads as wl
+    torch.cuda.set_device(0)
+    model = surrogate.Surrogate(wl.fourier_matrix(), wl.mlp_init())
+    c = torch.from_numpy(wl.survey_candidates(a.n)).cuda()
+    times = []
+    for _ in range(a.repeat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, score = model.forward(c, probs=False, score=True)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    flop = 215552.0 * a.n
+    best = min(times)
+    print(json.dumps({"n": a.n, "ms": times, "best_ms": best, "tflop_s": flop / (best * 1e-3) / 1e12,
+                      "mean_score": float(score.mean().item())}))
+    model.close()
 
 
 def probe():
