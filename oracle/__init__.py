@@ -13,6 +13,8 @@ Contents
       levels and the normalised escape-count histogram;
   precision_for_view : the binary32 / binary64 selection rule for deep zooms
       (Sec. 3 deep zoom; threshold 1000 binary32 ulps of the largest coordinate);
+  render_map / map_escape_point / map_step : generic maps Z <- Z^d + C and
+      Z <- P(Z)/Q(Z) + C (jl_oracle_maps.c; Sec. 2 "other functions", Fig. 4);
   mlp (submodule) : the surrogate network in float64 numpy.
 """
 import ctypes
@@ -44,6 +46,12 @@ def _load():
         lib.jlo_colour.restype = ctypes.c_int
         lib.jlo_hist.argtypes = [vp, i64, i32, vp]
         lib.jlo_hist.restype = ctypes.c_int
+        lib.jlo_render_map.argtypes = [vp, d, d, d, d, d, d, i32, i32, i32, i32, i32, vp, i32]
+        lib.jlo_render_map.restype = ctypes.c_int
+        lib.jlo_map_escape_point.argtypes = [vp, d, d, d, d, i32, i32]
+        lib.jlo_map_escape_point.restype = i32
+        lib.jlo_map_step.argtypes = [vp, d, d, d, d, i32, vp]
+        lib.jlo_map_step.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -159,3 +167,69 @@ def precision_for_view(rect, W, H, factor=1000.0):
 def hist_l1(p, q):
     """L1 distance sum_b |p_b - q_b| between histograms (last axis), float64."""
     return np.abs(np.asarray(p, np.float64) - np.asarray(q, np.float64)).sum(axis=-1)
+
+
+class _Map(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("degree", ctypes.c_int32), ("num_degree", ctypes.c_int32),
+                ("den_degree", ctypes.c_int32), ("num", ctypes.c_double * 18), ("den", ctypes.c_double * 18),
+                ("bailout", ctypes.c_double), ("z0r", ctypes.c_double), ("z0i", ctypes.c_double)]
+
+
+def _map_struct(m):
+    """m: {"kind": "power", "degree": d} or {"kind": "rational", "num": [a_0..a_n],
+    "den": [b_0..b_m]} (complex coefficients, constant term first), with optional
+    "bailout" (default 4.0) and "z0" (parameter-plane start, default 0)."""
+    s = _Map()
+    s.bailout = float(m.get("bailout", 4.0))
+    z0 = complex(m.get("z0", 0.0))
+    s.z0r, s.z0i = z0.real, z0.imag
+    if m["kind"] == "power":
+        s.kind, s.degree = 0, int(m["degree"])
+    elif m["kind"] == "rational":
+        s.kind = 1
+        num, den = [complex(v) for v in m["num"]], [complex(v) for v in m["den"]]
+        if not (1 <= len(num) <= 9 and 1 <= len(den) <= 9):
+            raise ValueError("rational map: 1..9 coefficients each")
+        s.num_degree, s.den_degree = len(num) - 1, len(den) - 1
+        for k, v in enumerate(num):
+            s.num[2 * k], s.num[2 * k + 1] = v.real, v.imag
+        for k, v in enumerate(den):
+            s.den[2 * k], s.den[2 * k + 1] = v.real, v.imag
+    else:
+        raise ValueError("unknown map kind")
+    return s
+
+
+def render_map(m, c, rect, W, H, max_iter=100, mode=JULIA, precision=FP32, threads=None):
+    """Escape counts (uint16, (H, W)) of a grid under a generic map (see
+    _map_struct); region covering and count rule as in render()."""
+    lib = _load()
+    out = np.zeros((H, W), dtype=np.uint16)
+    s = _map_struct(m)
+    c = complex(c)
+    nt = threads if threads else (os.cpu_count() or 1)
+    rc = lib.jlo_render_map(ctypes.byref(s), c.real, c.imag, *map(float, rect), W, H, max_iter, mode, precision,
+                            out.ctypes.data, nt)
+    if rc != 0:
+        raise ValueError("jlo_render_map: invalid arguments")
+    return out
+
+
+def map_escape_point(m, z0, c, max_iter, precision=FP32):
+    """Escape count from Z_0 = z0 with constant c under a generic map."""
+    s = _map_struct(m)
+    z0, c = complex(z0), complex(c)
+    n = _load().jlo_map_escape_point(ctypes.byref(s), z0.real, z0.imag, c.real, c.imag, max_iter, precision)
+    if n < 0:
+        raise ValueError("jlo_map_escape_point: invalid arguments")
+    return n
+
+
+def map_step(m, z, c, precision=FP32):
+    """One update F(z) + c (no escape test), as a Python complex."""
+    s = _map_struct(m)
+    z, c = complex(z), complex(c)
+    out = np.zeros(2, np.float64)
+    if _load().jlo_map_step(ctypes.byref(s), z.real, z.imag, c.real, c.imag, precision, out.ctypes.data) != 0:
+        raise ValueError("jlo_map_step: invalid arguments")
+    return complex(out[0], out[1])

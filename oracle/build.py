@@ -9,7 +9,9 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "jl_oracle.c")
+SRC = os.path.join(HERE, "jl_oracle.c")              # Z^2 + C (Sec. 2, 3)
+MAPS_SRC = os.path.join(HERE, "jl_oracle_maps.c")    # Z^d + C and P/Q + C (Sec. 2, Fig. 4)
+MAPS_INC = os.path.join(HERE, "map_iter.inc")
 LIB = os.path.join(HERE, "libjl_oracle.so")
 
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
@@ -17,10 +19,11 @@ CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-s
 
 
 def build(force: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    newest = max(os.path.getmtime(f) for f in (SRC, MAPS_SRC, MAPS_INC))
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", *CFLAGS, SRC, "-o", tmp, "-lm"])
+    subprocess.check_call(["gcc", *CFLAGS, "-I", HERE, SRC, MAPS_SRC, "-o", tmp, "-lm"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -181,3 +181,58 @@ def random_views(n, seed, max_side=97):
                         max_iter=int(rng.choice([1, 2, 7, 50, 100, 255, 300])), mode=mode,
                         precision=int(rng.integers(0, 2))))
     return out
+
+
+# ---- generic maps (Sec. 2: other functions than Z^2 + C; Fig. 4) ----------
+# Map descriptions are plain data: {"kind": "power", "degree": d} or
+# {"kind": "rational", "num": [a_0 .. a_n], "den": [b_0 .. b_m]} with complex
+# coefficients, constant term first, plus "bailout" (|Z|^2 escape threshold)
+# and "z0" (Z_0 of the parameter-plane mode).
+
+FIG4_C = complex(0.862085, 0.64695)
+
+
+def power_map(d, bailout=4.0):
+    """Z <- Z^d + C (Multibrot / Multi-Julia family)."""
+    return {"kind": "power", "degree": int(d), "bailout": float(bailout), "z0": 0j}
+
+
+def rational_map(num, den, bailout=4.0, z0=0j):
+    return {"kind": "rational", "num": [complex(v) for v in num], "den": [complex(v) for v in den],
+            "bailout": float(bailout), "z0": complex(z0)}
+
+
+def fig4_map():
+    """Fig. 4's map as printed, z^4 + (z^2 + 1)/(z^2 + 1) + C, as one quotient
+    P/Q + C: P = z^4 (z^2 + 1) + (z^2 + 1) = 1 + z^2 + z^4 + z^6, Q = 1 + z^2.
+    (As printed the fraction cancels, so away from z = +-i this is z^4 + 1 + C.)"""
+    return rational_map([1, 0, 1, 0, 1, 0, 1], [1, 0, 1])
+
+
+def random_rational_map(seed, num_degree=3, den_degree=2, scale=0.6, bailout=16.0):
+    """Seeded rational map with complex Gaussian coefficients (scale^k damping
+    on the k-th coefficient keeps the orbit scale moderate)."""
+    rng = np.random.default_rng(seed)
+
+    def coeffs(n):
+        z = rng.standard_normal(n + 1) + 1j * rng.standard_normal(n + 1)
+        return [complex(v * scale ** k) for k, v in enumerate(z)]
+    num = coeffs(num_degree)
+    num[-1] = 1.0 + 0j
+    return rational_map(num, coeffs(den_degree), bailout=bailout)
+
+
+def map_sweep(size=4096):
+    """Generic-map benchmark frames: Multibrot parameter planes for d = 3, 4,
+    5, 8 over [-1.6, 1.6]^2 and Fig. 4's map (as printed) at C = .862085 +
+    .64695i over [-1.6, 1.6]^2, limit 100, binary32; plus the d = 3 plane in
+    binary64."""
+    frames = []
+    for d in (3, 4, 5, 8):
+        frames.append(dict(map=power_map(d), c=0j, rect=(-1.6, 1.6, -1.6, 1.6), W=size, H=size, max_iter=100,
+                           mode=MANDELBROT, precision=FP32))
+    frames.append(dict(map=fig4_map(), c=FIG4_C, rect=(-1.6, 1.6, -1.6, 1.6), W=size, H=size, max_iter=100,
+                       mode=JULIA, precision=FP32))
+    frames.append(dict(map=power_map(3), c=0j, rect=(-1.6, 1.6, -1.6, 1.6), W=size, H=size, max_iter=100,
+                       mode=MANDELBROT, precision=FP64))
+    return frames

@@ -67,3 +67,69 @@ def test_pins_catch_mutant(name, tmp_path, monkeypatch):
         except AssertionError:
             caught += 1
     assert caught >= 1, "mutant %s survived every pin" % name
+
+
+# ---- generic maps (jl_oracle_maps.c / map_iter.inc) -----------------------
+from tests import test_oracle_maps as mpins  # noqa: E402
+
+MAP_MUTANTS = {
+    "mul_sign": ("map_iter.inc", "            wx = ac - bd;", "            wx = ac + bd;"),
+    "mul_cross": ("map_iter.inc", "            wy = ad + bc;", "            wy = ad - bc;"),
+    "square_no_doubling": ("map_iter.inc", "REAL tw = wx + wx;", "REAL tw = wx;"),
+    "top_bit_high": ("map_iter.inc", "while ((d >> (top + 1)) != 0)", "while ((d >> top) != 0)"),
+    "skip_multiply": ("map_iter.inc", "if ((d >> b) & 1) {", "if (!((d >> b) & 1)) {"),
+    "horner_sign": ("map_iter.inc", "REAL mr = ac - bd;", "REAL mr = ac + bd;"),
+    "horner_index": ("map_iter.inc", "pr = mr + a[2 * k];", "pr = mr + a[2 * k + 2];"),
+    "quotient_sign": ("map_iter.inc", "REAL ni = s3 - s4;", "REAL ni = s3 + s4;"),
+    "quotient_norm": ("map_iter.inc", "REAL q2 = q2r + q2i;", "REAL q2 = q2r - q2i;"),
+    "bailout_strict": ("map_iter.inc", "if (!(r <= bail))", "if (!(r < bail))"),
+    "drop_c": ("map_iter.inc", "x = fx + cr;", "x = fx;"),
+    "z0_ignored": ("jl_oracle_maps.c", "n = map_escape_f64(jb->m, jb->m->z0r, jb->m->z0i, xd, yd, jb->max_iter);",
+                   "n = map_escape_f64(jb->m, 0.0, 0.0, xd, yd, jb->max_iter);"),
+}
+
+MAP_CHECKS = [
+    lambda: mpins.test_power2_equals_quadratic(oracle.FP64, oracle.JULIA),
+    lambda: mpins.test_rational_forms_of_the_quadratic(oracle.FP64, oracle.MANDELBROT),
+    lambda: mpins.test_power_c0_closed_form(oracle.FP64, 3),
+    lambda: mpins.test_power_c0_closed_form(oracle.FP64, 5),
+    lambda: mpins.test_power_step_against_high_precision(oracle.FP64),
+    lambda: mpins.test_rational_step_against_high_precision(oracle.FP64),
+    lambda: mpins.test_fig4_as_printed_is_z4_plus_1(oracle.FP64),
+    lambda: mpins.test_exact_orbits_and_bailout(oracle.FP64),
+    lambda: mpins.test_parameter_plane_starts_from_z0(oracle.FP64),
+]
+
+
+@pytest.mark.parametrize("name", sorted(MAP_MUTANTS))
+def test_map_pins_catch_mutant(name, tmp_path, monkeypatch):
+    fname, old, new = MAP_MUTANTS[name]
+    for f in ("jl_oracle_maps.c", "map_iter.inc"):
+        src = open(os.path.join(os.path.dirname(obuild.SRC), f)).read()
+        if f == fname:
+            assert src.count(old) >= 1, old
+            src = src.replace(old, new, 1)
+        (tmp_path / f).write_text(src)
+    so = tmp_path / "m.so"
+    subprocess.check_call(["gcc", *obuild.CFLAGS, "-I", str(tmp_path), obuild.SRC, str(tmp_path / "jl_oracle_maps.c"),
+                           "-o", str(so), "-lm"])
+    real = oracle._load()
+    L = ctypes.CDLL(str(so))
+    for fn in ("jlo_render", "jlo_escape_point", "jlo_colour", "jlo_hist", "jlo_render_map",
+               "jlo_map_escape_point", "jlo_map_step"):
+        f = getattr(L, fn)
+        r = getattr(real, fn)
+        f.argtypes, f.restype = r.argtypes, r.restype
+
+    class Proxy:
+        def __getattr__(self, k):
+            return getattr(L, k)
+
+    monkeypatch.setattr(oracle, "_lib", Proxy())
+    caught = 0
+    for chk in MAP_CHECKS:
+        try:
+            chk()
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, "mutant %s survived every map pin" % name
