@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--no-survey", action="store_true", help="skip the surrogate screening workload")
     p.add_argument("--survey-epochs", type=int, default=300)
     p.add_argument("--no-extra", action="store_true", help="skip the path-animation and deep-zoom sections")
+    p.add_argument("--tune-save", default=None, help="write the autotuned launch shapes to this file")
+    p.add_argument("--tune-load", default=None,
+                   help="load launch shapes from this file instead of autotuning (e.g. to replay a plain run's "
+                        "choices under a profiler, whose per-launch overhead would distort the tuning)")
     return p.parse_args()
 
 
@@ -335,6 +339,71 @@ def run_fig1_sweep():
     return rows
 
 
+def map_ops_per_iteration(m):
+    """Algorithmic IEEE operations of one step of a generic map (escape test
+    included; a division counts as one operation although the hardware
+    sequence is longer).  Z^2 + C gives 8, as for the quadratic path."""
+    if m["kind"] == "power":
+        d = int(m["degree"])
+        top = d.bit_length() - 1
+        return 3 + 3 + 5 * (top - 1) + 6 * (bin(d).count("1") - 1) + 2
+    nd, nq = len(m["num"]) - 1, len(m["den"]) - 1
+    # test 3; Horner 8 per degree (complex product 6, coefficient 2);
+    # quotient 11 (|Q|^2 3, two numerators 3 + 3, two divisions); + C 2
+    return 3 + 8 * (nd + nq) + 11 + 2
+
+
+def run_generic_maps(K, W, peaks):
+    """Generic maps (Sec. 2 other functions, Fig. 4): Multibrot parameter
+    planes d = 3, 4, 5, 8, Fig. 4's map as printed, and the d = 3 plane in
+    binary64, each 4096 x 4096 (uint16 counts + RGBA8) through jl_render_map;
+    CUDA events around K renders after W warm-ups.  The oracle is timed on a
+    64-row band of each frame on all host cores for context."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1611_03079_b300 as jl
+    from paper_1611_03079_b300 import workloads as wl
+    rows = []
+    for f in wl.map_sweep(4096):
+        prec = "fp64" if f["precision"] else "fp32"
+        mode = "mandelbrot" if f["mode"] else "julia"
+        out = None
+        for _ in range(W):
+            out = jl.render_map(f["map"], f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=prec,
+                                mode=mode, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            out = jl.render_map(f["map"], f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=prec,
+                                mode=mode, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        iters = int((out["counts"].view(torch.int16).to(torch.int32) & 0xFFFF).to(torch.int64).sum().item())
+        ops = map_ops_per_iteration(f["map"])
+        achieved = iters * ops / (ms * 1e-3)
+        # oracle on a central band of 64 rows
+        xmin, xmax, ymin, ymax = f["rect"]
+        dy = (ymax - ymin) / f["H"]
+        j0 = f["H"] // 2 - 32
+        band = (xmin, xmax, ymin + j0 * dy, ymin + (j0 + 64) * dy)
+        t0 = time.perf_counter()
+        ref = oracle.render_map(f["map"], f["c"], band, f["W"], 64, f["max_iter"], f["mode"], f["precision"])
+        cpu_s = time.perf_counter() - t0
+        name = ("d=%d parameter plane" % f["map"]["degree"]) if f["map"]["kind"] == "power" else \
+            "Fig. 4 map as printed, Julia C=%s" % f["c"]
+        rows.append({"map": name, "precision": "binary64" if f["precision"] else "binary32",
+                     "W": f["W"], "H": f["H"], "max_iter": f["max_iter"], "ms": ms, "iterations": iters,
+                     "giter_s": iters / (ms * 1e-3) / 1e9, "ops_per_iteration": ops,
+                     "achieved_gops": achieved / 1e9, "peak_gops": peaks[f["precision"]] / 1e9,
+                     "frac": achieved / peaks[f["precision"]],
+                     "cpu_band_giter_s": float(ref.astype(np.int64).sum()) / cpu_s / 1e9,
+                     "cpu_cores": os.cpu_count()})
+    return rows
+
+
 def run_reference(args):
     world, rank, _ = dist_setup("gloo")
     if rank != 0:
@@ -393,12 +462,19 @@ def main():
     # launch-shape autotuning (one-off, before any timing): per precision and
     # limit bucket, calibrated on the sweep frames themselves
     tuned = {}
+    if args.tune_load:
+        jl.tune_load(args.tune_load)
     for prec in (0, 1):
         for mi in (100, 1000):
-            calib = [f for f in frames if f["precision"] == prec and f["max_iter"] == mi]
-            r = jl.autotune("fp64" if prec else "fp32", mi, calib=calib, reps=1)
+            if args.tune_load:
+                r = jl.tune_get("fp64" if prec else "fp32", mi)
+            else:
+                calib = [f for f in frames if f["precision"] == prec and f["max_iter"] == mi]
+                r = jl.autotune("fp64" if prec else "fp32", mi, calib=calib, reps=1)
             tuned["%s limit %d" % ("binary64" if prec else "binary32", mi)] = {
                 k: r[k] for k in ("ppt", "unroll", "threads", "ms", "candidates")}
+    if args.tune_save:
+        jl.tune_save(args.tune_save)
 
     # The sweep as one batch plan: one CUDA-graph launch per step renders all
     # 16 frames (coordinate tables, binary32 and binary64 persistent kernels on
@@ -515,6 +591,7 @@ def main():
         extra["path_animation"] = run_path_animation(K, max(args.warmup, 3))
         extra["deep_zoom"] = run_deep_zoom(1, 1)
         extra["fig1_size_sweep"] = run_fig1_sweep()
+        extra["generic_maps"] = run_generic_maps(K, max(args.warmup, 3), peaks)
 
     survey = None
     if not args.no_survey and rank == 0:

@@ -194,6 +194,49 @@ int jl_render_static(double cr, double ci, jl_rect rect, int32_t width, int32_t 
                      const uint8_t *palette, float *hist, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Generic maps (Sec. 2: many other functions than Z^2 + C give fractal
+ * images; Fig. 4: a rational map with C = .862085 + .64695i; Sec. 5: freer
+ * functional forms).  Two families, iterated as Z <- F(Z) + C:
+ *   JL_MAP_POWER     F(Z) = Z^d, 2 <= d <= 16;
+ *   JL_MAP_RATIONAL  F(Z) = P(Z) / Q(Z), P and Q of degree 0..8 with complex
+ *                    coefficients (Fig. 4's formula as printed is one case).
+ * Step, in the working precision, every operation rounded to nearest and
+ * none fused: x2 = x*x; y2 = y*y; escape unless x2 + y2 <= bailout (a NaN
+ * escapes); (fx, fy) = F(x, y); x = fx + cr; y = fy + ci.
+ *   Z^d: W = Z, then for each bit of d below the leading one, from high to
+ *     low: W = (a*a - b*b, (a + a)*b) for W = (a, b), and, when the bit is
+ *     set, W = (a*x - b*y, a*y + b*x).  d = 2 reproduces the quadratic
+ *     iteration of the other entry points bit for bit.
+ *   P(Z): Horner from the leading coefficient, P = P*Z + a_k with the
+ *     product formed as above; P/Q = ((pr*qr + pi*qi) / (qr*qr + qi*qi),
+ *     (pi*qr - pr*qi) / (qr*qr + qi*qi)) with correctly rounded division.
+ * Coefficients, bailout and z0 are given in binary64 and rounded once to the
+ * working precision.  Count, colour, histogram, pixel centres and precision
+ * selection are those of jl_render.
+ * ------------------------------------------------------------------------ */
+typedef enum { JL_MAP_POWER = 0, JL_MAP_RATIONAL = 1 } jl_map_kind;
+
+typedef struct {
+    int32_t kind;        /* jl_map_kind */
+    int32_t degree;      /* JL_MAP_POWER: d, 2..16 */
+    int32_t num_degree;  /* JL_MAP_RATIONAL: degree of P, 0..8 */
+    int32_t den_degree;  /* JL_MAP_RATIONAL: degree of Q, 0..8 */
+    double num[18];      /* P: (re, im) pairs, constant term first; unused entries ignored */
+    double den[18];      /* Q: (re, im) pairs, constant term first */
+    double bailout;      /* escape radius squared, > 0 and finite (4 for radius 2) */
+    double z0r, z0i;     /* JL_MANDELBROT mode: Z_0 (usually a critical point of F; 0 for Z^d) */
+} jl_map;
+
+/* Render one frame of a generic map.  Arguments after `map` as jl_render
+ * (mode JL_JULIA: Z_0 = pixel, C = (cr, ci); JL_MANDELBROT: Z_0 = (z0r, z0i),
+ * C = pixel).  `map` is a host pointer read during the call only.
+ * JL_EINVAL for a NULL map, an unknown kind, a degree out of range, a
+ * non-finite coefficient, bailout or z0, or any jl_render argument error. */
+int jl_render_map(const jl_map *map, double cr, double ci, jl_rect rect, int32_t width, int32_t height,
+                  int32_t max_iter, int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
+                  const uint8_t *palette, float *hist, void *stream);
+
+/* ------------------------------------------------------------------------
  * Batches (Sec. 3: paths of C rendered as animations; also the histogram
  * targets of the surrogate).  A plan renders many frames -- each with its own
  * C, view, size, limit, mode and precision -- in one CUDA-graph launch of

@@ -108,6 +108,61 @@ def render(c, rect, width, height, max_iter=100, precision="fp32", mode="julia",
     return out
 
 
+def make_map(m):
+    """jl_map from a description: {"kind": "power", "degree": d} or
+    {"kind": "rational", "num": [a_0, ..., a_n], "den": [b_0, ..., b_m]}
+    (complex coefficients, constant term first), with optional "bailout"
+    (escape radius squared, default 4.0) and "z0" (Z_0 in parameter-plane
+    mode, default 0)."""
+    s = _lib.Map()
+    s.bailout = float(m.get("bailout", 4.0))
+    z0 = complex(m.get("z0", 0.0))
+    s.z0r, s.z0i = z0.real, z0.imag
+    if m["kind"] == "power":
+        s.kind, s.degree = 0, int(m["degree"])
+    elif m["kind"] == "rational":
+        num, den = [complex(v) for v in m["num"]], [complex(v) for v in m["den"]]
+        if not (1 <= len(num) <= 9 and 1 <= len(den) <= 9):
+            raise ValueError("a rational map takes 1..9 coefficients for each of P and Q")
+        s.kind, s.num_degree, s.den_degree = 1, len(num) - 1, len(den) - 1
+        for k, v in enumerate(num):
+            s.num[2 * k], s.num[2 * k + 1] = v.real, v.imag
+        for k, v in enumerate(den):
+            s.den[2 * k], s.den[2 * k + 1] = v.real, v.imag
+    else:
+        raise ValueError("map kind must be 'power' or 'rational'")
+    return s
+
+
+def render_map(m, c, rect, width, height, max_iter=100, precision="fp32", mode="julia", count_type="u16",
+               rgba=True, hist=False, palette=None, out=None, stream=None):
+    """Render one frame of a generic map Z <- F(Z) + C (jl_render_map); `m`
+    as for make_map, other arguments and the result as for render()."""
+    import torch
+
+    spec = make_map(m)
+    prec, md, ct = _PREC[precision], _MODE[mode], _CT[count_type]
+    W, H = int(width), int(height)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = dict(out or {})
+    if ct != JL_COUNT_NONE and "counts" not in out:
+        out["counts"] = torch.empty((H, W), dtype=torch.uint8 if ct == JL_COUNT_U8 else torch.uint16,
+                                    device=dev)
+    if rgba and "rgba" not in out:
+        out["rgba"] = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
+    if hist and "hist" not in out:
+        out["hist"] = torch.empty((int(max_iter) + 1,), dtype=torch.float32, device=dev)
+    pal, pal_ptr = _palette_ptr(palette)
+    st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+    cr, ci = _c(c)
+    check(_lib.lib().jl_render_map(ctypes.byref(spec), cr, ci, _rect(rect), W, H, int(max_iter), prec, md, ct,
+                                   out["counts"].data_ptr() if ct != JL_COUNT_NONE else None,
+                                   out["rgba"].data_ptr() if rgba else None, pal_ptr,
+                                   out["hist"].data_ptr() if hist else None, st))
+    del pal
+    return out
+
+
 def render_to_host(c, rect, width, height, max_iter=100, precision="fp32", mode="julia",
                    count_type="u16", rgba=True, hist=False, palette=None, out=None, stream=None):
     """Render one frame into host (numpy) buffers through jl_render_to_host;
@@ -292,7 +347,7 @@ def tune_get(precision="fp32", max_iter=100):
     res = _lib.TuneResult()
     check(_lib.lib().jl_tune_get(_PREC[precision], int(max_iter), ctypes.byref(res)))
     return {"ppt": res.ppt, "unroll": res.unroll, "threads": res.threads, "ctas_per_sm": res.ctas_per_sm,
-            "emu": res.emu, "tuned": bool(res.candidates)}
+            "emu": res.emu, "tuned": bool(res.candidates), "ms": res.ms, "candidates": res.candidates}
 
 
 def tune_clear():

@@ -46,6 +46,13 @@ class BatchOpts(ctypes.Structure):
                 ("fp64_emu", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cycle_budget", ctypes.c_int64)]
 
 
+class Map(ctypes.Structure):
+    """jl_map (include/jl.h)."""
+    _fields_ = [("kind", ctypes.c_int32), ("degree", ctypes.c_int32), ("num_degree", ctypes.c_int32),
+                ("den_degree", ctypes.c_int32), ("num", ctypes.c_double * 18), ("den", ctypes.c_double * 18),
+                ("bailout", ctypes.c_double), ("z0r", ctypes.c_double), ("z0i", ctypes.c_double)]
+
+
 class TuneResult(ctypes.Structure):
     """jl_tune_result (include/jl.h)."""
     _fields_ = [("ppt", ctypes.c_int32), ("unroll", ctypes.c_int32), ("threads", ctypes.c_int32),
@@ -63,6 +70,8 @@ SIGNATURES = {
     "jl_select_precision": (ctypes.c_int, [Rect, _i32, _i32]),
     "jl_default_palette": (ctypes.c_int, [_vp]),
     "jl_render": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "jl_render_map": (ctypes.c_int, [ctypes.POINTER(Map), _d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp,
+                                     _vp, _vp, _vp, _vp]),
     "jl_render_variant": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
                                          _vp, _i32, _i32, _i32, _i32, _i32, _vp]),
     "jl_render_static": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp,

@@ -30,6 +30,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "jl_common.cuh"
 #include "jl_f64emu.cuh"
 #include "jl_internal.h"
 
@@ -106,25 +107,6 @@ __global__ void hist_zero_kernel(const __grid_constant__ HistArgs a)
         for (int b = threadIdx.x; b <= F.max_iter; b += blockDim.x)
             F.hist_bins[b] = 0u;
     }
-}
-
-// x + x for binary64 on the integer pipes (the binary64 pipe is narrow on
-// this part).  Doubling is exact in IEEE arithmetic, so the bit pattern can be
-// formed directly: zero/subnormal -> magnitude shifted left by one (a carry
-// into the exponent field gives the correct normal number); exponent field
-// 1..2045 -> exponent + 1; 2046 -> signed infinity (what round-to-nearest
-// gives on overflow); 2047 (inf, NaN) -> unchanged (NaN stays NaN).
-__device__ __forceinline__ double dbl2(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long sign = b & 0x8000000000000000ull;
-    const unsigned long long mag = b & 0x7fffffffffffffffull;
-    const unsigned e = (unsigned)(mag >> 52);
-    unsigned long long r = b + (1ull << 52);
-    r = (e == 0) ? (sign | (mag << 1)) : r;
-    r = (e == 2046) ? (sign | 0x7ff0000000000000ull) : r;
-    r = (e == 2047) ? b : r;
-    return __longlong_as_double((long long)r);
 }
 
 __global__ void dbl2_kernel(const double *in, double *out, int n)
@@ -246,17 +228,6 @@ struct WorkT<double> {
     static __device__ __forceinline__ double cr(const Frame &F) { return F.cr; }
     static __device__ __forceinline__ double ci(const Frame &F) { return F.ci; }
 };
-
-// Integer quotient (n * 255) / d for n <= d <= 65535 via a 40-bit reciprocal:
-// m = floor(2^40 / d) + 1 gives floor(n*255*m / 2^40) == floor(n*255 / d)
-// because the excess n*255*(m - 2^40/d)/2^40 < 2^-16 < 1/d.
-__device__ __forceinline__ uint32_t colour_index(uint32_t count, uint32_t max_iter, uint64_t magic)
-{
-    if (count >= max_iter)
-        return 255u;
-    uint64_t p = (uint64_t)(count * 255u) * magic;
-    return (uint32_t)(p >> 40);
-}
 
 template <typename T, int PPT, int U, bool BATCH>
 __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ EscapeArgs a)

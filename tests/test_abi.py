@@ -139,3 +139,39 @@ def test_batch_create_validation(L):
     assert rc == _lib.JL_EINVAL and b"even" in L.jl_last_error()
     rc = L.jl_batch_create(ctypes.byref(f), 0, None, None, None, None, None, ctypes.byref(h))
     assert rc == _lib.JL_EINVAL
+
+
+def _map_call(L, m, **kw):
+    import paper_1611_03079_b300 as jl
+    spec = m if isinstance(m, _lib.Map) else jl.make_map(m)
+    args = dict(cr=0.0, ci=0.0, rect=(-2.0, 2.0, -2.0, 2.0), W=16, H=16, max_iter=100, prec=0, mode=0, ct=2,
+                counts=1)
+    args.update(kw)
+    return L.jl_render_map(ctypes.byref(spec), args["cr"], args["ci"], _lib.Rect(*args["rect"]), args["W"],
+                           args["H"], args["max_iter"], args["prec"], args["mode"], args["ct"], args["counts"],
+                           None, None, None, None)
+
+
+def test_render_map_validation(L):
+    """Generic-map arguments are rejected on the host, before any device use."""
+    cases = [
+        (wl.power_map(1), {}, "degree"), (wl.power_map(17), {}, "degree"),
+        (dict(wl.power_map(3), bailout=0.0), {}, "bailout"),
+        (dict(wl.power_map(3), bailout=float("inf")), {}, "bailout"),
+        (dict(wl.power_map(3), z0=complex(float("nan"), 0)), {}, "z0"),
+        (wl.rational_map([1, float("inf")], [1]), {}, "numerator"),
+        (wl.rational_map([1], [complex(0, float("nan"))]), {}, "denominator"),
+        (wl.power_map(3), dict(W=0), "width"), (wl.power_map(3), dict(max_iter=0), "max_iter"),
+        (wl.fig4_map(), dict(mode=5), "mode"),
+    ]
+    for m, kw, frag in cases:
+        assert _map_call(L, m, **kw) == _lib.JL_EINVAL, (m, kw)
+        assert frag in L.jl_last_error().decode(), (frag, L.jl_last_error())
+    bad = _lib.Map()
+    bad.kind = 7
+    assert _map_call(L, bad) == _lib.JL_EINVAL and "kind" in L.jl_last_error().decode()
+    bad = _lib.Map()
+    bad.kind, bad.num_degree, bad.den_degree, bad.bailout = 1, 9, 0, 4.0
+    assert _map_call(L, bad) == _lib.JL_EINVAL and "degrees" in L.jl_last_error().decode()
+    assert L.jl_render_map(None, 0.0, 0.0, _lib.Rect(-1, 1, -1, 1), 4, 4, 10, 0, 0, 2, 1, None, None, None,
+                           None) == _lib.JL_EINVAL
