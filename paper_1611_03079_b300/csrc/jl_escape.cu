@@ -666,8 +666,9 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
     const long long t_start = clock64();
 
     for (long long tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x) {
-        if (a.cycle_budget > 0 && (clock64() - t_start) > a.cycle_budget) {
-            if (threadIdx.x == 0 && a.status)
+        // budget check, uniform across the warp (the loop below has warp collectives)
+        if (a.cycle_budget > 0 && __any_sync(FULL, (clock64() - t_start) > a.cycle_budget)) {
+            if (lane == 0 && a.status)
                 atomicExch(a.status, (int)JL_ETIMEOUT);
             break;
         }
@@ -832,7 +833,7 @@ bool variant_supported(int precision, int ppt, int unroll)
 int variant_list(int precision, int32_t *pairs, int cap)
 {
     int n = 0;
-    // (0, 0): the static one-pixel-per-thread kernel
+    // (0, 0): the static tile kernel
     if (pairs && n < cap) {
         pairs[0] = 0;
         pairs[1] = 0;

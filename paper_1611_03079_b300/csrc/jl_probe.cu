@@ -64,6 +64,50 @@ __global__ void __launch_bounds__(256) int_probe_kernel(uint32_t *out, int iters
         out[blockIdx.x] = s;
 }
 
+// Packed binary32 pairs (add/mul.rn.f32x2, sm_100 and later), kind 5:
+// four chains of packed adds and four of packed multiplies per thread, so
+// no product ever feeds a sum (the compiler contracts a packed multiply and
+// a following packed add into one fused operation).  Each instruction is two
+// binary32 lane operations; the probe tells whether packing raises the
+// lane-operation rate of separately rounded adds and multiplies.  (Measured
+// on this part: it does not; a packed instruction holds the pipe twice as
+// long as a scalar one.)
+__device__ __forceinline__ unsigned long long mul_f32x2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long add_f32x2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__global__ void __launch_bounds__(256) f32x2_probe_kernel(unsigned long long *out, int iters, float a, float b)
+{
+    const unsigned long long a2 = ((unsigned long long)__float_as_uint(a) << 32) | __float_as_uint(a);
+    const unsigned long long b2 = ((unsigned long long)__float_as_uint(b) << 32) | __float_as_uint(b);
+    unsigned long long v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float lo = (float)(threadIdx.x + k) * 1e-3f, hi = (float)(threadIdx.x + 2 * k) * 1e-3f;
+        v[k] = ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+    }
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            v[k] = (k & 1) ? mul_f32x2(v[k], a2) : add_f32x2(v[k], b2);
+    }
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        s ^= v[k];
+    if (s == 0x9e3779b97f4a7c15ull)
+        out[blockIdx.x] = s;
+}
+
 }  // namespace jl
 
 using namespace jl;
@@ -71,8 +115,9 @@ using namespace jl;
 extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_per_s, double *seconds,
                              void *stream)
 {
-    if (precision < 0 || precision > 4)
-        return fail(JL_EINVAL, "kind must be 0 (binary32), 1 (binary64), 2 (int xor+add), 3 (int mad), 4 (int mulhi)");
+    if (precision < 0 || precision > 5)
+        return fail(JL_EINVAL, "kind must be 0 (binary32), 1 (binary64), 2 (int xor+add), 3 (int mad), 4 (int mulhi), "
+                               "5 (packed binary32 pairs)");
     if (iters < 1 || !lane_ops_per_s)
         return fail(JL_EINVAL, "iters must be >= 1 and lane_ops_per_s non-NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -99,6 +144,8 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
             int_probe_kernel<2><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
         else if (precision == 3)
             int_probe_kernel<3><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
+        else if (precision == 5)
+            f32x2_probe_kernel<<<grid, threads, 0, st>>>((unsigned long long *)out, iters, 0.999f, 0.001f);
         else
             int_probe_kernel<4><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
         e = cudaGetLastError();

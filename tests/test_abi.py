@@ -99,7 +99,7 @@ def test_variant_list(L):
         buf = (ctypes.c_int32 * (2 * n))()
         assert L.jl_variant_list(prec, buf, n) == n
         pairs = [(buf[2 * i], buf[2 * i + 1]) for i in range(n)]
-        assert pairs[0] == (0, 0)  # the static kernel
+        assert pairs[0] == (0, 0)  # the static tile kernel
         assert all(p >= 1 and u >= 1 for p, u in pairs[1:])
     assert L.jl_variant_list(5, None, 0) == -1
 
