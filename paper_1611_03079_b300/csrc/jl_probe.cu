@@ -108,6 +108,40 @@ __global__ void __launch_bounds__(256) f32x2_probe_kernel(unsigned long long *ou
         out[blockIdx.x] = s;
 }
 
+// 64-bit integer probes: kind 6 = 64-bit add chains, kind 7 = 64-bit
+// shift-and-xor chains, kind 8 = 64-bit compare-and-select chains.  They tell
+// which pipe the 64-bit integer forms use (the integer-pipe binary64
+// arithmetic is built from them).
+template <int KIND>
+__global__ void __launch_bounds__(256) int64_probe_kernel(unsigned long long *out, int iters, unsigned long long a,
+                                                          unsigned long long b)
+{
+    unsigned long long v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        v[k] = (unsigned long long)threadIdx.x * 0x9e3779b97f4a7c15ull + k;
+    const int s = (int)(a & 31ull) + 1;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if constexpr (KIND == 6) {
+                v[k] = v[k] + a;
+                asm volatile("" : "+l"(v[k]));
+            } else if constexpr (KIND == 7) {
+                v[k] = (v[k] << s) ^ (v[k] >> (s + 3));
+            } else {
+                v[k] = (v[k] > a) ? v[k] - b : v[k] + a;
+            }
+        }
+    }
+    unsigned long long t = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        t ^= v[k];
+    if (t == 0x9e3779b97f4a7c15ull)
+        out[blockIdx.x] = t;
+}
+
 }  // namespace jl
 
 using namespace jl;
@@ -115,9 +149,9 @@ using namespace jl;
 extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_per_s, double *seconds,
                              void *stream)
 {
-    if (precision < 0 || precision > 5)
+    if (precision < 0 || precision > 8)
         return fail(JL_EINVAL, "kind must be 0 (binary32), 1 (binary64), 2 (int xor+add), 3 (int mad), 4 (int mulhi), "
-                               "5 (packed binary32 pairs)");
+                               "5 (packed binary32 pairs), 6 (int64 add), 7 (int64 shift+xor), 8 (int64 compare+select)");
     if (iters < 1 || !lane_ops_per_s)
         return fail(JL_EINVAL, "iters must be >= 1 and lane_ops_per_s non-NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -146,6 +180,12 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
             int_probe_kernel<3><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
         else if (precision == 5)
             f32x2_probe_kernel<<<grid, threads, 0, st>>>((unsigned long long *)out, iters, 0.999f, 0.001f);
+        else if (precision == 6)
+            int64_probe_kernel<6><<<grid, threads, 0, st>>>((unsigned long long *)out, iters, 0x9e3779b97f4a7c15ull, 7ull);
+        else if (precision == 7)
+            int64_probe_kernel<7><<<grid, threads, 0, st>>>((unsigned long long *)out, iters, 0x5ull, 7ull);
+        else if (precision == 8)
+            int64_probe_kernel<8><<<grid, threads, 0, st>>>((unsigned long long *)out, iters, 0x7fffffffffffull, 0x12345ull);
         else
             int_probe_kernel<4><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
         e = cudaGetLastError();
@@ -161,7 +201,9 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
     if (rc == JL_OK) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, t0, t1);
-        const double per = (precision == 3) ? 1.0 : 2.0;  // lane ops per chain step
+        // lane ops per chain step (64-bit kinds: one 64-bit operation per step
+        // for add, two shifts and an xor, a compare and a select plus the add)
+        const double per = (precision == 3 || precision == 6) ? 1.0 : (precision == 7 ? 3.0 : (precision == 8 ? 2.0 : 2.0));
         const double ops = (double)grid * threads * (double)iters * 8.0 * per;
         *lane_ops_per_s = ops / (ms * 1e-3);
         if (seconds)
