@@ -437,6 +437,7 @@ def main():
         return run_reference(args)
 
     import numpy as np
+    import numpy as np
     import torch
 
     import paper_1611_03079_b300 as jl
@@ -553,25 +554,24 @@ def main():
 
     e2e = None
     if not args.no_e2e and rank == 0:
-        host = []
-        for f in frames:
-            host.append({"counts": torch.empty((f["H"], f["W"]), dtype=torch.int16, pin_memory=True).numpy(),
-                         "rgba": torch.empty((f["H"], f["W"], 4), dtype=torch.uint8, pin_memory=True).numpy()})
-        for i, f in enumerate(frames):  # warm-up pass
-            jl.render_to_host(f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=f["precision"],
-                              mode=f["mode"], count_type="u16", rgba=True, palette=pal, out=host[i],
-                              stream=stream)
-        t0 = time.perf_counter()
-        for i, f in enumerate(frames):
-            jl.render_to_host(f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=f["precision"],
-                              mode=f["mode"], count_type="u16", rgba=True, palette=pal, out=host[i],
-                              stream=stream)
-        e2e_s = time.perf_counter() - t0
-        d2h = sum(h["counts"].nbytes + h["rgba"].nbytes for h in host)
-        e2e = {"value": total_iters / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 1024 * n,
-               "d2h_bytes_per_step": d2h,
-               "note": "jl_render_to_host per frame: render into device scratch, copy counts + RGBA8 to "
-                       "pinned host memory, synchronise; host wall clock over one full sweep"}
+        # the public host-output path: jl_render_frames_to_host renders the 16
+        # frames into pinned host memory, copies overlapped with rendering
+        hf = jl.HostFrames([dict(f, count_type="u16", rgba=True) for f in frames], palette=pal, depth=0)
+        hf.render(stream)  # warm-up
+        times = []
+        for _ in range(max(K, 1)):
+            t0 = time.perf_counter()
+            hf.render(stream)
+            times.append(time.perf_counter() - t0)
+        e2e_s = statistics.median(times)
+        ok = all((hf.counts(i).astype(np.int64).sum() == iters[i]) for i in range(len(frames)))
+        e2e = {"value": total_iters / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 96 * n,
+               "d2h_bytes_per_step": int(hf.d2h_bytes), "ms_per_step": e2e_s * 1e3, "steps": len(times),
+               "counts_match_device": bool(ok),
+               "note": "jl_render_frames_to_host: 16 frames per step rendered on 3 internal streams into "
+                       "device slots and copied to pinned host memory (counts + RGBA8) as each frame "
+                       "finishes; host wall clock per call (median of steps), the call returns after the "
+                       "last copy; h2d = the frame descriptions (96 B each)"}
 
     cpu = None
     if not args.no_cpu and rank == 0:

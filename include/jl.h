@@ -309,6 +309,23 @@ void jl_batch_destroy(jl_batch *b);
 int jl_render_batch(const jl_frame *frames, int32_t n, void *counts_base, uint8_t *rgba_base, float *hist_base,
                     const uint8_t *palette, void *stream);
 
+/*
+ * Render n frames into HOST memory with the device-to-host copies overlapped
+ * with rendering.  Frames as in jl_batch_create (offsets in bytes from the
+ * host base pointers, -1 = no such output; counts_host / rgba_host /
+ * hist_host may be NULL when no frame uses them).  Frame i renders on
+ * internal stream i mod depth into a device slot of that stream and is
+ * copied out on the same stream, so up to `depth` frames are in flight
+ * (depth 0 = 6; 1..8).  The host buffers should be pinned (page-locked) for
+ * the copies to overlap; pageable memory works but serialises.  Work queued
+ * earlier on `stream` is waited for; the call returns when every copy has
+ * completed (synchronous).  The library allocates depth slots of the largest
+ * frame's outputs for the duration of the call.  Errors: as jl_batch_create
+ * for the frame descriptions; JL_ECUDA / JL_ENOMEM from the device.
+ */
+int jl_render_frames_to_host(const jl_frame *frames, int32_t n, void *counts_host, uint8_t *rgba_host,
+                             float *hist_host, const uint8_t *palette, int32_t depth, void *stream);
+
 /* ------------------------------------------------------------------------
  * Autotuner of the escape kernel's launch shape.
  * ------------------------------------------------------------------------ */

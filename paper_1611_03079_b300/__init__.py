@@ -208,6 +208,84 @@ def _frame_struct(f, counts_off, rgba_off, hist_off):
                       _CT[f.get("count_type")], counts_off, rgba_off, hist_off)
 
 
+def _layout(frames):
+    """Byte offsets of every frame's outputs in flat counts / RGBA8 /
+    histogram buffers (-1 = none) and the three buffer sizes."""
+    c_off, r_off, h_off = [], [], []
+    cb = rb = hb = 0
+    for f in frames:
+        ct = _CT[f.get("count_type")]
+        npx = int(f["W"]) * int(f["H"])
+        if ct != JL_COUNT_NONE:
+            cb = (cb + 1) & ~1
+            c_off.append(cb)
+            cb += npx * (1 if ct == JL_COUNT_U8 else 2)
+        else:
+            c_off.append(-1)
+        if f.get("rgba", True):
+            r_off.append(rb)
+            rb += npx * 4
+        else:
+            r_off.append(-1)
+        if f.get("hist", False):
+            h_off.append(hb)
+            hb += (int(f["max_iter"]) + 1) * 4
+        else:
+            h_off.append(-1)
+    return c_off, r_off, h_off, cb, rb, hb
+
+
+class HostFrames:
+    """Frames rendered into (pinned) host memory by jl_render_frames_to_host:
+    copies to the host overlap with rendering, `depth` frames in flight.
+    `frames` as for Batch.  The host buffers are allocated once (page-locked
+    through torch) and reused by every render() call; counts(i), rgba(i) and
+    hist(i) return numpy views of frame i."""
+
+    def __init__(self, frames, palette=None, depth=0):
+        import torch
+        self._L = _lib.lib()
+        self.frames = list(frames)
+        self.depth = int(depth)
+        self._c_off, self._r_off, self._h_off, cb, rb, hb = _layout(self.frames)
+        self.counts_buf = torch.empty(max(cb, 2), dtype=torch.uint8, pin_memory=True).numpy()
+        self.rgba_buf = torch.empty(max(rb, 4), dtype=torch.uint8, pin_memory=True).numpy()
+        self.hist_buf = torch.empty(max(hb // 4, 1), dtype=torch.float32, pin_memory=True).numpy()
+        self._arr = (_lib.Frame * len(self.frames))(
+            *[_frame_struct(f, self._c_off[i], self._r_off[i], self._h_off[i]) for i, f in enumerate(self.frames)])
+        self._pal, self._pal_ptr = _palette_ptr(palette)
+        self.d2h_bytes = sum(cb_ for cb_ in (cb, rb, hb))
+
+    def render(self, stream=None):
+        import torch
+        st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        check(self._L.jl_render_frames_to_host(self._arr, len(self.frames), self.counts_buf.ctypes.data,
+                                               self.rgba_buf.ctypes.data, self.hist_buf.ctypes.data, self._pal_ptr,
+                                               self.depth, st))
+
+    def counts(self, i):
+        f, o = self.frames[i], self._c_off[i]
+        if o < 0:
+            return None
+        npx = int(f["W"]) * int(f["H"])
+        if _CT[f.get("count_type")] == JL_COUNT_U8:
+            return self.counts_buf[o:o + npx].reshape(int(f["H"]), int(f["W"]))
+        return self.counts_buf[o:o + 2 * npx].view(np.uint16).reshape(int(f["H"]), int(f["W"]))
+
+    def rgba(self, i):
+        f, o = self.frames[i], self._r_off[i]
+        if o < 0:
+            return None
+        npx = int(f["W"]) * int(f["H"])
+        return self.rgba_buf[o:o + 4 * npx].reshape(int(f["H"]), int(f["W"]), 4)
+
+    def hist(self, i):
+        o = self._h_off[i]
+        if o < 0:
+            return None
+        return self.hist_buf[o // 4:o // 4 + int(self.frames[i]["max_iter"]) + 1]
+
+
 class Batch:
     """A batch plan: frames rendered together by one CUDA-graph launch.
 

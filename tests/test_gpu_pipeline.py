@@ -1,0 +1,76 @@
+"""jl_render_frames_to_host: frames rendered into pinned host memory with the
+copies overlapped.  Every depth (1 .. 8, and more than the frame count) gives
+counts, colours and histograms identical to the oracle and to the device
+render of the same frame; repeated calls reuse the buffers; frames without
+counts or with histograms only; bad frames are rejected before any work."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1611_03079_b300 as jl
+from paper_1611_03079_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def mixed_frames():
+    frames = []
+    for i, f in enumerate(wl.random_views(9, seed=77)):
+        f = dict(f)
+        f["count_type"] = "u8" if f["max_iter"] <= 255 and i % 3 == 0 else "u16"
+        f["rgba"] = i % 4 != 1
+        f["hist"] = i % 2 == 0
+        frames.append(f)
+    frames.append(dict(c=complex(-0.7269, 0.1889), rect=(-1.6, 1.6, -1.6, 1.6), W=640, H=480, max_iter=500,
+                       mode="julia", precision="fp64", count_type="u16", rgba=True, hist=True))
+    frames.append(dict(c=None, rect=(-2.5, 1.0, -1.75, 1.75), W=777, H=333, max_iter=300, mode="mandelbrot",
+                       precision="fp32", count_type=None, rgba=True, hist=False))
+    return frames
+
+
+def _oracle_counts(f):
+    mode = 0 if f.get("mode", "julia") in ("julia", 0) else 1
+    prec = {"fp32": 0, "fp64": 1, 0: 0, 1: 1}[f.get("precision", "fp32")]
+    return oracle.render(f["c"] if f["c"] is not None else 0j, f["rect"], f["W"], f["H"], f["max_iter"], mode, prec)
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3, 8, 0])
+def test_host_frames_match_oracle(cuda, depth):
+    frames = mixed_frames()
+    pal = wl.random_palette(5)
+    hf = jl.HostFrames(frames, palette=pal, depth=depth)
+    for _ in range(2):
+        hf.render()
+    for i, f in enumerate(frames):
+        ref = _oracle_counts(f)
+        if f.get("count_type"):
+            assert (hf.counts(i) == ref).all(), i
+        else:
+            assert hf.counts(i) is None
+        if f.get("rgba", True):
+            assert (hf.rgba(i) == oracle.colour(ref, f["max_iter"], pal)).all(), i
+        if f.get("hist"):
+            assert (hf.hist(i) == oracle.hist(ref, f["max_iter"])).all(), i
+
+
+def test_matches_device_render(cuda):
+    import torch
+    frames = wl.throughput_sweep(512)
+    for f in frames:
+        f["count_type"], f["rgba"] = "u16", True
+    hf = jl.HostFrames(frames, depth=3)
+    hf.render()
+    for i, f in enumerate(frames):
+        d = jl.render(f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=f["precision"], mode=f["mode"],
+                      count_type="u16", rgba=True)
+        torch.cuda.synchronize()
+        assert (d["counts"].view(torch.int16).cpu().numpy().view(np.uint16) == hf.counts(i)).all()
+        assert (d["rgba"].cpu().numpy() == hf.rgba(i)).all()
+
+
+def test_rejects_bad_frames(cuda):
+    bad = [dict(c=0.1, rect=(1.0, -1.0, 0.0, 1.0), W=8, H=8, max_iter=10, count_type="u16")]
+    with pytest.raises(jl.JLError):
+        jl.HostFrames(bad).render()
+    with pytest.raises(jl.JLError):
+        jl.HostFrames([dict(c=0.1, rect=(-1, 1, -1, 1), W=8, H=8, max_iter=10, count_type="u16")], depth=9).render()
