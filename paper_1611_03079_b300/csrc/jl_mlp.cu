@@ -69,6 +69,11 @@ struct GemmArgs {
     int ldp;
     float *score;            // [M] entropy of p or NULL
     int32_t *status;         // set to JL_ETIMEOUT if a wait gave up
+    // EPI_F32 split-K: CTA (x, y) covers K chunks [y * kc_per_split, (y + 1) * kc_per_split)
+    // and writes its partial M x N product to out_f32 + y * split_stride
+    // (ld_out32 as given); a fixed-order reduction sums the splits.
+    int ksplit, kc_per_split;
+    long long split_stride;
 };
 
 static constexpr int kBM = 128, kBK = 64;
@@ -77,6 +82,7 @@ static constexpr int kTileB = 256 * kBK * 2;   // 32 KB
 static constexpr int kStage = kTileA + kTileB;
 static constexpr int kGemmSmem = 2 * kStage + 4 * 256 * 4 + 64;  // stages + column partials + barriers
 static constexpr long long kWaitLimit = 2000000000ll;  // ~1 s at 2 GHz
+static constexpr int kSplitK = 16;  // K splits of the weight-gradient products (K = batch rows)
 
 // Stage rows [row0, row0 + nrows) x k [k0, k0 + 64) of an operand into the
 // K-major core-matrix layout: piece (r, g) (8 consecutive k) at byte
@@ -160,15 +166,20 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
     const uint32_t taddr = *holder;
 
     const uint32_t idesc = tc::idesc_bf16(kBM, (uint32_t)g.BN);
-    const int nk = (g.K + kBK - 1) / kBK;
+    int kc_begin = 0, kc_end = (g.K + kBK - 1) / kBK;
+    if (EPI == EPI_F32 && g.ksplit > 1) {
+        kc_begin = blockIdx.y * g.kc_per_split;
+        kc_end = min(kc_end, kc_begin + g.kc_per_split);
+    }
     bool ok = true;
-    for (int kc = 0; kc < nk; ++kc) {
-        const int s = kc & 1;
+    for (int kc = kc_begin; kc < kc_end; ++kc) {
+        const int lk = kc - kc_begin;  // chunk index within this CTA's range
+        const int s = lk & 1;
         uint8_t *sA = stage0 + s * kStage;
         uint8_t *sB = sA + kTileA;
-        if (kc >= 2) {
-            // buffer s was last read by the MMAs of chunk kc - 2
-            if (!tc::mbar_wait(&bars[s], ((kc - 2) >> 1) & 1, kWaitLimit))
+        if (lk >= 2) {
+            // buffer s was last read by the MMAs of chunk lk - 2
+            if (!tc::mbar_wait(&bars[s], ((lk - 2) >> 1) & 1, kWaitLimit))
                 ok = false;
         }
         stage_operand(sA, g.A, g.lda, g.a_trans, m0, kBM, g.M, kc * kBK, g.K);
@@ -182,7 +193,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
             for (int kk = 0; kk < kBK / 16; ++kk) {
                 const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, 1024);
                 const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, 1024);
-                tc::mma_bf16(taddr, ad, bd, idesc, (kc | kk) != 0);
+                tc::mma_bf16(taddr, ad, bd, idesc, (lk | kk) != 0);
             }
             tc::mma_commit(&bars[s]);
         }
@@ -304,10 +315,11 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
             }
             if (in) {
                 if constexpr (EPI == EPI_F32) {
+                    float *o = g.out_f32 + (g.ksplit > 1 ? (size_t)blockIdx.y * (size_t)g.split_stride : 0);
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
                         if (c0 + j < g.N)
-                            g.out_f32[(size_t)row * g.ld_out32 + c0 + j] = v[j];
+                            o[(size_t)row * g.ld_out32 + c0 + j] = v[j];
                 } else {
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
@@ -1008,6 +1020,7 @@ struct jl_model {
     float *loss_out = nullptr;  // where the next forward writes its loss sum (NULL: `loss`)
     float *part = nullptr;      // per-CTA column sums [ctas x 256]
     float *loss_part = nullptr; // per-CTA loss sums [ctas]
+    float *ws = nullptr;        // split-K partials of the weight gradients [kSplitK x 256 x 256]
 };
 
 namespace jl {
@@ -1025,7 +1038,50 @@ static cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t st)
         g_gemm_attr_set[EPI] = true;
     }
     const int grid = (a.M + kBM - 1) / kBM;
-    kern<<<grid, 128, kGemmSmem, st>>>(a);
+    const int splits = (EPI == EPI_F32 && a.ksplit > 1) ? a.ksplit : 1;
+    kern<<<dim3(grid, splits), 128, kGemmSmem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// out[m * ld + n] = sum over s = 0 .. S-1, in that order, of ws[s][m][n]
+// (deterministic reduction of split-K partials).
+__global__ void splitk_reduce_kernel(const float *__restrict__ ws, int S, int M, int N, float *__restrict__ out,
+                                     int ld)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)M * N)
+        return;
+    const int m = (int)(i / N), n = (int)(i % N);
+    float acc = 0.f;
+    for (int sp = 0; sp < S; ++sp)
+        acc += ws[(size_t)sp * M * N + i];
+    out[(size_t)m * ld + n] = acc;
+}
+
+// C (fp32, M x N, row stride ld_out32 at out) = A B over K split into
+// `splits` ranges of whole 64-wide chunks: partials in ws (splits x M x N), then
+// the fixed-order reduction.  ws must hold splits * M * N floats.
+static cudaError_t launch_gemm_f32_splitk(GemmArgs a, float *ws, int splits, cudaStream_t st)
+{
+    float *out = a.out_f32;
+    const int ld = a.ld_out32;
+    const int nk = (a.K + kBK - 1) / kBK;
+    if (splits > nk)
+        splits = nk;
+    if (splits <= 1 || !ws) {
+        a.ksplit = 1;
+        return launch_gemm<EPI_F32>(a, st);
+    }
+    a.kc_per_split = (nk + splits - 1) / splits;
+    a.ksplit = (nk + a.kc_per_split - 1) / a.kc_per_split;
+    a.out_f32 = ws;
+    a.ld_out32 = a.N;
+    a.split_stride = (long long)a.M * a.N;
+    cudaError_t e = launch_gemm<EPI_F32>(a, st);
+    if (e != cudaSuccess)
+        return e;
+    const int64_t total = (int64_t)a.M * a.N;
+    splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ws, a.ksplit, a.M, a.N, out, ld);
     return cudaGetLastError();
 }
 
@@ -1059,8 +1115,9 @@ static void free_work(jl_model *md)
     cudaFree(md->tgt);
     cudaFree(md->part);
     cudaFree(md->loss_part);
+    cudaFree(md->ws);
     md->phi = md->h1 = md->h2 = md->dz = md->dz2 = md->dz1 = nullptr;
-    md->tgt = md->part = md->loss_part = nullptr;
+    md->tgt = md->part = md->loss_part = md->ws = nullptr;
     md->cap = 0;
 }
 
@@ -1088,6 +1145,8 @@ static int ensure_work(jl_model *md, int rows, bool train)
         e = cudaMalloc(&md->part, ctas * 256 * 4);
     if (e == cudaSuccess && train)
         e = cudaMalloc(&md->loss_part, ctas * 4);
+    if (e == cudaSuccess && train)
+        e = cudaMalloc(&md->ws, (size_t)kSplitK * kHid * kHid * 4);
     if (e != cudaSuccess) {
         free_work(md);
         return cuda_fail(e, "cudaMalloc(surrogate work buffers)");
@@ -1152,7 +1211,7 @@ static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
     GemmArgs a = gemm_args(md->dz, kBinsPad, 1, md->h2, kHid, 1, kBins, kHid, n, md->status);
     a.out_f32 = md->grads + kOffW3;
     a.ld_out32 = kHid;
-    cudaError_t e = launch_gemm<EPI_F32>(a, st);
+    cudaError_t e = launch_gemm_f32_splitk(a, md->ws, kSplitK, st);
     if (e != cudaSuccess)
         return e;
     // dZ2 = (dZ W3) * [h2 > 0]   (n x 256, K = 101), db2 = column sums
@@ -1170,7 +1229,7 @@ static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
     a = gemm_args(md->dz2, kHid, 1, md->h1, kHid, 1, kHid, kHid, n, md->status);
     a.out_f32 = md->grads + kOffW2;
     a.ld_out32 = kHid;
-    if ((e = launch_gemm<EPI_F32>(a, st)) != cudaSuccess)
+    if ((e = launch_gemm_f32_splitk(a, md->ws, kSplitK, st)) != cudaSuccess)
         return e;
     // dZ1 = (dZ2 W2) * [h1 > 0], db1
     a = gemm_args(md->dz2, kHid, 0, W2, kHid, 1, n, kHid, kHid, md->status);
@@ -1186,7 +1245,7 @@ static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
     a = gemm_args(md->dz1, kHid, 1, md->phi, kIn, 1, kHid, kIn, n, md->status);
     a.out_f32 = md->grads + kOffW1;
     a.ld_out32 = kIn;
-    return launch_gemm<EPI_F32>(a, st);
+    return launch_gemm_f32_splitk(a, md->ws, kSplitK, st);
 }
 
 static cudaError_t zero_grads(jl_model *md, cudaStream_t st)
