@@ -388,10 +388,13 @@ static constexpr int kPackElems = (kImgW + 4 * kImgW + 4 * kImgW3) / 2;  // bf16
 static constexpr int kFsPhi = 0;                               // 2 x (128 x 64 bf16)
 static constexpr int kFsH = kFsPhi + 2 * kBM * kIn * 2;        // 2 x (128 x 256 bf16)
 static constexpr int kFsWB = kFsH + 2 * kBM * kHid * 2;        // 2 x 32 KB weight chunks
-static constexpr int kFsBias = kFsWB + 2 * kImgW;              // b1, b2, b3 (fp32), B (64 fp32)
-static constexpr int kFsBar = kFsBias + (kHid + kHid + kBinsPad + 64) * 4;
-static constexpr int kFusedSmem = kFsBar + 8 * 8;
+static constexpr int kFsB3 = kFsWB + 2 * kImgW;                // b3 (112 fp32), Fourier B (64 fp32)
+static constexpr int kFsX = kFsB3 + (kBinsPad + 64) * 4;       // softmax partials: 256 rows x 2 fp32
+static constexpr int kFsBar = kFsX + 2 * kBM * 2 * 4;          // mbarriers, TMEM holder, abort flag
+static constexpr int kFusedSmem = kFsBar + 20 * 8;
 static_assert(kFusedSmem <= 232448, "fused forward exceeds the shared-memory limit");
+static constexpr int kFusedEpiWarps = 16;                      // two per row (column halves)
+static constexpr int kFusedThreads = (kFusedEpiWarps + 1) * 32;  // + one producer warp
 
 // One thread per 16-byte piece of the packed images.
 __global__ void pack_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *__restrict__ out)
@@ -444,31 +447,40 @@ struct FusedArgs {
     int32_t *status;
 };
 
-// 256 threads, 256-row tiles.  Warp w serves tile half h = w >> 2 (rows
-// 128 h .. 128 h + 127) and reads TMEM lane quarter (w & 3) of that half's
-// accumulator (columns 256 h .. 256 h + 255).  Each streamed weight chunk is
-// consumed by the MMAs of both halves before it is replaced, so the weight
-// traffic per row is half that of a 128-row tile.  Chunks per tile:
-// W1 (256 x 64), W2 K-chunks 0..3 (256 x 64), W3 K-chunks 0..3 (112 x 64).
-// Thread 0 also issues the bulk copies and the MMAs.
-__global__ void __launch_bounds__(256) fused_forward_kernel(const __grid_constant__ FusedArgs a)
+// Warp-specialised fused forward over 256-row tiles (two 128-row halves,
+// each with its own 256-column TMEM accumulator; 512 columns allocated).
+//   producer (warp 16, one thread): streams the nine weight chunks of every
+//     tile (W1, W2 x 4, W3 x 4; cp.async.bulk into a 2 x 32 KB double
+//     buffer) and issues each chunk's MMAs for both halves, so every chunk is
+//     read from L2 once per 256 rows;
+//   epilogue (warps 0..15): warp w serves TMEM lane quarter (w & 3) of half
+//     (w >> 2) & 1 and column half w >> 3, so each row has two threads.  They
+//     build Fourier features, turn accumulators into relu(D + b) bf16
+//     activations in shared memory, and form softmax and entropy.
+// Hand-offs are mbarriers: feat / h1 / h2 / tfree (one arrival per epilogue
+// warp, waited by the producer) and acc (MMA completion, waited by the
+// epilogue).  The next tile's features are built while product 2 runs, and
+// its product 1 may start while the softmax of this tile is still computed.
+// Every wait is bounded; a timeout sets a shared abort flag that ends all
+// other waits, in-flight copies and MMAs are waited for, TMEM is freed and
+// the status word reads JL_ETIMEOUT.
+__global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const __grid_constant__ FusedArgs a)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *sPhi = sm + kFsPhi;           // [2][16 KB]
-    uint8_t *sH = sm + kFsH;               // [2][64 KB]
-    uint8_t *sWB = sm + kFsWB;             // [2][32 KB]
-    float *b1 = reinterpret_cast<float *>(sm + kFsBias);
-    float *b2 = b1 + kHid;
-    float *b3 = b2 + kHid;
+    uint8_t *sPhi = sm + kFsPhi;
+    uint8_t *sH = sm + kFsH;
+    uint8_t *sWB = sm + kFsWB;
+    float *b3 = reinterpret_cast<float *>(sm + kFsB3);
     float *Bs = b3 + kBinsPad;
-    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kFsBar);  // [2]
-    uint64_t *empty = full + 2;                                  // [2]
-    uint64_t *acc = full + 4;
-    uint32_t *holder = reinterpret_cast<uint32_t *>(full + 6);
+    float2 *xbuf = reinterpret_cast<float2 *>(sm + kFsX);           // [256 rows]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kFsBar);
+    uint64_t *full = bars, *empty = bars + 2, *acc = bars + 4, *feat = bars + 5, *h1b = bars + 6, *h2b = bars + 7,
+             *tfree = bars + 8, *fin = bars + 9;
+    uint32_t *holder = reinterpret_cast<uint32_t *>(bars + 10);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 11);
+    uint64_t *pairb = bars + 12;  // [8]: the two warps serving the same rows (w, w + 8)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int quarter = warp & 3, half = warp >> 2;
-    const int r = quarter * 32 + lane;  // row within this warp group's half
     const int64_t ntiles = (a.n + 2 * kBM - 1) / (2 * kBM);
     if (blockIdx.x >= ntiles)
         return;
@@ -476,224 +488,306 @@ __global__ void __launch_bounds__(256) fused_forward_kernel(const __grid_constan
 
     if (warp == 0)
         tc::tmem_alloc(holder, 512);
-    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
-        b1[i] = a.params[kOffB1 + i];
-        b2[i] = a.params[kOffB2 + i];
-    }
     for (int i = threadIdx.x; i < kBinsPad; i += blockDim.x)
         b3[i] = i < kBins ? a.params[kOffB3 + i] : 0.f;
     if (threadIdx.x < 64)
         Bs[threadIdx.x] = a.B[threadIdx.x];
-    const uint8_t *gpack = reinterpret_cast<const uint8_t *>(a.pack);
-    // chunk q of this CTA's stream: j = q % 9: 0 -> W1, 1..4 -> W2, 5..8 -> W3
-    auto chunk_src = [&](int q, uint32_t &bytes) -> const uint8_t * {
-        const int j = q % 9;
-        if (j < 5) {
-            bytes = kImgW;
-            return gpack + (size_t)j * kImgW;
-        }
-        bytes = kImgW3;
-        return gpack + 5 * (size_t)kImgW + (size_t)(j - 5) * kImgW3;
-    };
-    const int total_chunks = my_tiles * 9;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&empty[i], 1);
         }
         tc::mbar_init(acc, 1);
+        tc::mbar_init(feat, kFusedEpiWarps);
+        tc::mbar_init(h1b, kFusedEpiWarps);
+        tc::mbar_init(h2b, kFusedEpiWarps);
+        tc::mbar_init(tfree, kFusedEpiWarps);
+        tc::mbar_init(fin, 1);
+        for (int i = 0; i < 8; ++i)
+            tc::mbar_init(&pairb[i], 2);
+        *abort_flag = 0;
         tc::fence_mbar_init();
-        tc::fence_proxy_async_smem();
-        uint32_t bytes;
-        const uint8_t *src = chunk_src(0, bytes);
-        tc::bulk_load(sWB, src, bytes, &full[0]);
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t taddr = *holder;
-    // this thread's TMEM row: lane quarter of the warp, accumulator of the half
-    const uint32_t tw = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 256);
-    bool ok = true;
-    uint32_t acc_uses = 0;
 
-    // thread 0: wait for chunk q, issue the MMAs of both halves, and refill
-    // the other buffer with chunk q + 1 once its previous occupant is consumed.
-    auto run_chunk = [&](int q, uint32_t a0, uint32_t a1, uint32_t a_sbo, uint32_t n_rows, bool first) {
-        const int b = q & 1;
-        if (!tc::mbar_wait(&full[b], (q >> 1) & 1, kWaitLimit))
-            ok = false;
-        tc::tc_fence_after();
-        const uint32_t idesc = tc::idesc_bf16(kBM, n_rows);
-        const uint32_t bb = tc::smem_u32(sWB + b * kImgW);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t ab = h ? a1 : a0;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = tc::smem_desc(ab + kk * 256, 128, a_sbo);
-                const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, 1024);
-                tc::mma_bf16(taddr + (uint32_t)(h * 256), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+    if (warp == kFusedEpiWarps) {
+        // ------------------------------ producer ------------------------------
+        if (lane == 0) {
+            const uint8_t *gpack = reinterpret_cast<const uint8_t *>(a.pack);
+            auto chunk_src = [&](int q, uint32_t &bytes) -> const uint8_t * {
+                const int j = q % 9;  // 0 -> W1, 1..4 -> W2, 5..8 -> W3
+                if (j < 5) {
+                    bytes = kImgW;
+                    return gpack + (size_t)j * kImgW;
+                }
+                bytes = kImgW3;
+                return gpack + 5 * (size_t)kImgW + (size_t)(j - 5) * kImgW3;
+            };
+            const int total_chunks = my_tiles * 9;
+            int loads_issued = 1, loads_waited = 0;  // per-buffer accounting for the abort path
+            {
+                uint32_t bytes;
+                const uint8_t *src = chunk_src(0, bytes);
+                tc::fence_proxy_async_smem();
+                tc::bulk_load(sWB, src, bytes, &full[0]);
             }
-        }
-        tc::mma_commit(&empty[b]);
-        if (q + 1 < total_chunks) {
-            const int nb = (q + 1) & 1;
-            if (q >= 1 && !tc::mbar_wait(&empty[nb], ((q - 1) >> 1) & 1, kWaitLimit))
-                ok = false;
-            uint32_t bytes;
-            const uint8_t *src = chunk_src(q + 1, bytes);
-            tc::bulk_load(sWB + nb * kImgW, src, bytes, &full[nb]);
-        }
-    };
-
-    auto wait_acc = [&]() {
-        if (!tc::mbar_wait(acc, acc_uses & 1, kWaitLimit))
-            ok = false;
-        ++acc_uses;
-        tc::tc_fence_after();
-    };
-
-    uint8_t *myPhi = sPhi + half * (kBM * kIn * 2);
-    uint8_t *myH = sH + half * (kBM * kHid * 2);
-
-    // Features of this thread's row of tile `tile` into its half's Phi image.
-    auto make_features = [&](int64_t tile) {
-        const int64_t row = tile * (2 * kBM) + half * kBM + r;
-        float cr = 0.f, ci = 0.f;
-        if (row < a.n) {
-            cr = a.c[2 * row];
-            ci = a.c[2 * row + 1];
-        }
-        uint32_t sv[16], cv[16];
+            bool okp = true;
+            // wait for chunk q, issue both halves' MMAs, refill the other buffer with chunk q + 1
+            auto run_chunk = [&](int q, uint32_t a0, uint32_t a1, uint32_t a_sbo, uint32_t n_rows, bool first) -> bool {
+                const int b = q & 1;
+                if (!tc::mbar_wait_or_abort(&full[b], (q >> 1) & 1, kWaitLimit, abort_flag))
+                    return false;
+                ++loads_waited;
+                tc::tc_fence_after();
+                const uint32_t idesc = tc::idesc_bf16(kBM, n_rows);
+                const uint32_t bb = tc::smem_u32(sWB + b * kImgW);
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-            float s0, c0, s1, c1;
-            fourier_pair(Bs[2 * j], Bs[2 * j + 1], cr, ci, s0, c0);
-            fourier_pair(Bs[2 * j + 2], Bs[2 * j + 3], cr, ci, s1, c1);
-            sv[j >> 1] = tc::pack_bf16x2(s0, s1);
-            cv[j >> 1] = tc::pack_bf16x2(c0, c1);
-        }
-        if (row >= a.n) {
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t ab = h ? a1 : a0;
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                sv[j] = cv[j] = 0u;
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = tc::smem_desc(ab + kk * 256, 128, a_sbo);
+                        const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, 1024);
+                        tc::mma_bf16(taddr + (uint32_t)(h * 256), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                    }
+                }
+                tc::mma_commit(&empty[b]);
+                if (q + 1 < total_chunks) {
+                    const int nb = (q + 1) & 1;
+                    if (q >= 1 && !tc::mbar_wait_or_abort(&empty[nb], ((q - 1) >> 1) & 1, kWaitLimit, abort_flag))
+                        return false;
+                    uint32_t bytes;
+                    const uint8_t *src = chunk_src(q + 1, bytes);
+                    tc::bulk_load(sWB + nb * kImgW, src, bytes, &full[nb]);
+                    ++loads_issued;
+                }
+                return true;
+            };
+            const uint32_t phi0 = tc::smem_u32(sPhi), phi1 = tc::smem_u32(sPhi + kBM * kIn * 2);
+            const uint32_t hh0 = tc::smem_u32(sH), hh1 = tc::smem_u32(sH + kBM * kHid * 2);
+            for (int it = 0; it < my_tiles && okp; ++it) {
+                // product 1: the tile's features are in place and the previous
+                // tile's logits have been read out of TMEM
+                okp = tc::mbar_wait_or_abort(feat, it & 1, kWaitLimit, abort_flag);
+                if (okp && it > 0)
+                    okp = tc::mbar_wait_or_abort(tfree, (it - 1) & 1, kWaitLimit, abort_flag);
+                if (!okp)
+                    break;
+                tc::tc_fence_after();
+                okp = run_chunk(it * 9, phi0, phi1, 1024, kHid, true);
+                if (!okp)
+                    break;
+                tc::mma_commit(acc);
+                // product 2: H1 written by every epilogue warp
+                okp = tc::mbar_wait_or_abort(h1b, it & 1, kWaitLimit, abort_flag);
+                if (!okp)
+                    break;
+                tc::tc_fence_after();
+                for (int j = 0; j < 4 && okp; ++j)
+                    okp = run_chunk(it * 9 + 1 + j, hh0 + j * 8 * 128, hh1 + j * 8 * 128, 4096, kHid, j == 0);
+                if (!okp)
+                    break;
+                tc::mma_commit(acc);
+                // product 3: H2 written
+                okp = tc::mbar_wait_or_abort(h2b, it & 1, kWaitLimit, abort_flag);
+                if (!okp)
+                    break;
+                tc::tc_fence_after();
+                for (int j = 0; j < 4 && okp; ++j)
+                    okp = run_chunk(it * 9 + 5 + j, hh0 + j * 8 * 128, hh1 + j * 8 * 128, 4096, kBinsPad, j == 0);
+                if (!okp)
+                    break;
+                tc::mma_commit(acc);
+            }
+            // let every copy and product already issued land before TMEM is
+            // freed (nothing is outstanding on the normal path but the last MMAs)
+            for (int q = loads_waited; q < loads_issued; ++q)
+                tc::mbar_wait(&full[q & 1], (q >> 1) & 1, kWaitLimit);
+            tc::mma_commit(fin);
+            tc::mbar_wait(fin, 0, kWaitLimit);
         }
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            *reinterpret_cast<uint4 *>(myPhi + ((r >> 3) * 8 + g) * 128 + (r & 7) * 16) =
-                make_uint4(sv[4 * g], sv[4 * g + 1], sv[4 * g + 2], sv[4 * g + 3]);
-            *reinterpret_cast<uint4 *>(myPhi + ((r >> 3) * 8 + g + 4) * 128 + (r & 7) * 16) =
-                make_uint4(cv[4 * g], cv[4 * g + 1], cv[4 * g + 2], cv[4 * g + 3]);
-        }
-        tc::fence_proxy_async_smem();
-    };
+    } else {
+        // ------------------------------ epilogue ------------------------------
+        const int quarter = warp & 3, half = (warp >> 2) & 1, ch = warp >> 3;
+        const int r = quarter * 32 + lane;  // row within the half
+        const uint32_t tw = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 256);
+        uint8_t *myPhi = sPhi + half * (kBM * kIn * 2);
+        uint8_t *myH = sH + half * (kBM * kHid * 2);
+        const float *b1g = a.params + kOffB1, *b2g = a.params + kOffB2;
+        uint32_t acc_uses = 0;
+        bool ok = true;
 
-    // relu(D + b) as bf16 into this half's H image, 32 columns per TMEM load.
-    auto hidden_epilogue = [&](const float *bias) {
-        wait_acc();
+        auto arrive = [&](uint64_t *bar) {
+            __syncwarp();
+            if (lane == 0)
+                tc::mbar_arrive(bar);
+        };
+        auto wait_acc = [&]() -> bool {
+            const bool w = tc::mbar_wait_or_abort(acc, acc_uses & 1, kWaitLimit, abort_flag);
+            ++acc_uses;
+            tc::tc_fence_after();
+            return w;
+        };
+        // this thread's 16 Fourier frequencies (16 ch .. 16 ch + 15) of its row
+        auto make_features = [&](int64_t tile) {
+            const int64_t row = tile * (2 * kBM) + half * kBM + r;
+            float cr = 0.f, ci = 0.f;
+            if (row < a.n) {
+                cr = a.c[2 * row];
+                ci = a.c[2 * row + 1];
+            }
+            uint32_t sv[8], cv[8];
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                const int f0 = 16 * ch + j;
+                float s0, c0, s1, c1;
+                fourier_pair(Bs[2 * f0], Bs[2 * f0 + 1], cr, ci, s0, c0);
+                fourier_pair(Bs[2 * f0 + 2], Bs[2 * f0 + 3], cr, ci, s1, c1);
+                sv[j >> 1] = tc::pack_bf16x2(s0, s1);
+                cv[j >> 1] = tc::pack_bf16x2(c0, c1);
+            }
+            if (row >= a.n) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    sv[j] = cv[j] = 0u;
+            }
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                *reinterpret_cast<uint4 *>(myPhi + ((r >> 3) * 8 + 2 * ch + g) * 128 + (r & 7) * 16) =
+                    make_uint4(sv[4 * g], sv[4 * g + 1], sv[4 * g + 2], sv[4 * g + 3]);
+                *reinterpret_cast<uint4 *>(myPhi + ((r >> 3) * 8 + 4 + 2 * ch + g) * 128 + (r & 7) * 16) =
+                    make_uint4(cv[4 * g], cv[4 * g + 1], cv[4 * g + 2], cv[4 * g + 3]);
+            }
+            tc::fence_proxy_async_smem();
+        };
+        // relu(D + b) as bf16 into this half's H image, this thread's 128 columns
+        auto hidden_epilogue = [&](const float *bias) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < kHid; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(tw + c0, v);
-            uint32_t w[16];
+            for (int c0 = 128 * ch; c0 < 128 * ch + 128; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tw + c0, v);
+                uint32_t wv[16];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float4 bq = *reinterpret_cast<const float4 *>(bias + c0 + 4 * q);
-                w[2 * q] = tc::pack_relu_bf16x2(__fadd_rn(v[4 * q], bq.x), __fadd_rn(v[4 * q + 1], bq.y));
-                w[2 * q + 1] = tc::pack_relu_bf16x2(__fadd_rn(v[4 * q + 2], bq.z), __fadd_rn(v[4 * q + 3], bq.w));
+                for (int q = 0; q < 8; ++q) {
+                    const float4 bq = __ldg(reinterpret_cast<const float4 *>(bias + c0 + 4 * q));
+                    wv[2 * q] = tc::pack_relu_bf16x2(__fadd_rn(v[4 * q], bq.x), __fadd_rn(v[4 * q + 1], bq.y));
+                    wv[2 * q + 1] = tc::pack_relu_bf16x2(__fadd_rn(v[4 * q + 2], bq.z), __fadd_rn(v[4 * q + 3], bq.w));
+                }
+                const int g = c0 >> 3;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<uint4 *>(myH + ((r >> 3) * 32 + g + q) * 128 + (r & 7) * 16) =
+                        make_uint4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
             }
-            const int g = c0 >> 3;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<uint4 *>(myH + ((r >> 3) * 32 + g + q) * 128 + (r & 7) * 16) =
-                    make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-        }
-        tc::fence_proxy_async_smem();
-        tc::tc_fence_before();
-        __syncthreads();
-    };
+            tc::fence_proxy_async_smem();
+            tc::tc_fence_before();
+        };
 
-    make_features(blockIdx.x);
-    tc::tc_fence_before();
-    __syncthreads();
-    // Each later tile's features are written during the previous tile's
-    // product 2 and published by the barrier that ends its second epilogue.
-    for (int it = 0; it < my_tiles; ++it) {
-        const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
-        const int64_t row = tile * (2 * kBM) + half * kBM + r;
-        const bool in = row < a.n;
-        // ---- product 1: Phi (2 x 128 x 64) x W1^T ----
-        if (threadIdx.x == 0) {
-            tc::tc_fence_after();
-            run_chunk(it * 9, tc::smem_u32(sPhi), tc::smem_u32(sPhi + kBM * kIn * 2), 1024, kHid, true);
-            tc::mma_commit(acc);
-        }
-        hidden_epilogue(b1);
-        // ---- product 2: H1 x W2^T, four streamed K-chunks ----
-        if (threadIdx.x == 0) {
-            tc::tc_fence_after();
-            const uint32_t h0 = tc::smem_u32(sH), h1 = tc::smem_u32(sH + kBM * kHid * 2);
-            for (int j = 0; j < 4; ++j)
-                run_chunk(it * 9 + 1 + j, h0 + j * 8 * 128, h1 + j * 8 * 128, 4096, kHid, j == 0);
-            tc::mma_commit(acc);
-        }
-        // the Phi images were consumed by product 1 (its commit was waited
-        // for), so the next tile's features are built while product 2 runs
-        if (it + 1 < my_tiles)
-            make_features(tile + gridDim.x);
-        hidden_epilogue(b2);
-        // ---- product 3: H2 x W3^T -> logits (112 columns) ----
-        if (threadIdx.x == 0) {
-            tc::tc_fence_after();
-            const uint32_t h0 = tc::smem_u32(sH), h1 = tc::smem_u32(sH + kBM * kHid * 2);
-            for (int j = 0; j < 4; ++j)
-                run_chunk(it * 9 + 5 + j, h0 + j * 8 * 128, h1 + j * 8 * 128, 4096, kBinsPad, j == 0);
-            tc::mma_commit(acc);
-        }
-        wait_acc();
-        // ---- softmax and entropy of this thread's row ----
-        // z_b = D_b + b3_b, m = max z, e_b = 2^((z_b - m) log2 e), S = sum e_b,
-        // T = sum e_b z_b: p_b = e_b / S and the entropy is m + log S - T / S.
-        float z[kBinsPad];
-        tc::tmem_ld32(tw, z);
-        tc::tmem_ld32(tw + 32, z + 32);
-        tc::tmem_ld32(tw + 64, z + 64);
-        {
-            float t16[16];
-            tc::tmem_ld16(tw + 96, t16);
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                z[96 + j] = t16[j];
-        }
-        tc::tc_fence_before();
-        __syncthreads();  // every TMEM read of this tile is done: the next product 1 may overwrite it
-        float mx = -INFINITY;
-#pragma unroll
-        for (int j = 0; j < kBins; ++j) {
-            z[j] = __fadd_rn(z[j], b3[j]);
-            mx = fmaxf(mx, z[j]);
-        }
+        // bounded rendezvous of warps w and w + 8 (never a hardware barrier:
+        // a partner that gave up must not leave the other waiting forever)
+        uint32_t pair_uses = 0;
+        auto pair_sync = [&]() -> bool {
+            __syncwarp();
+            if (lane == 0)
+                tc::mbar_arrive(&pairb[warp & 7]);
+            const bool w = tc::mbar_wait_or_abort(&pairb[warp & 7], pair_uses & 1, kWaitLimit, abort_flag);
+            ++pair_uses;
+            return w;
+        };
+
+        make_features(blockIdx.x);
+        arrive(feat);
         const float kLog2e = 1.4426950408889634f;
-        const float mb = -__fmul_rn(mx, kLog2e);
-        float S = 0.f, Tz = 0.f;
+        for (int it = 0; it < my_tiles; ++it) {
+            const int64_t tile = blockIdx.x + (int64_t)it * gridDim.x;
+            const int64_t row = tile * (2 * kBM) + half * kBM + r;
+            const bool in = row < a.n;
+            // ---- product 1 done: activations 1 ----
+            if (!(ok = wait_acc()))
+                break;
+            hidden_epilogue(b1g);
+            arrive(h1b);
+            // the Phi images were consumed by product 1: next tile's features
+            if (it + 1 < my_tiles) {
+                make_features(tile + gridDim.x);
+                arrive(feat);
+            }
+            // ---- product 2 done: activations 2 ----
+            if (!(ok = wait_acc()))
+                break;
+            hidden_epilogue(b2g);
+            arrive(h2b);
+            // ---- product 3 done: logits of this thread's 56 columns ----
+            if (!(ok = wait_acc()))
+                break;
+            float z[56];
+            const int cb = 56 * ch;
+            tc::tmem_ld32(tw + cb, z);
+            tc::tmem_ld16(tw + cb + 32, *reinterpret_cast<float(*)[16]>(z + 32));
+            tc::tmem_ld8(tw + cb + 48, z + 48);
+            tc::tc_fence_before();
+            arrive(tfree);  // TMEM may now take the next tile's product 1
+            // partial softmax over the valid columns of this thread:
+            // m = max z, S = sum 2^((z - m) log2 e), T = sum e z;
+            // sent as L = m + log S (log-sum-exp) and A = T / S (mean logit)
+            const int nv = ch ? (kBins - 56) : 56;
+            float mx = -INFINITY;
 #pragma unroll
-        for (int j = 0; j < kBins; ++j) {
-            const float e = ex2_approx(__fmaf_rn(z[j], kLog2e, mb));
-            S = __fadd_rn(S, e);
-            Tz = __fmaf_rn(e, z[j], Tz);
-        }
-        if (in && a.score)
-            a.score[row] = __fsub_rn(__fadd_rn(mx, logf(S)), __fdiv_rn(Tz, S));
-        if (in && a.probs) {
-            const float inv = __fdiv_rn(1.f, S);
-            float *prow = a.probs + (size_t)row * kBins;
+            for (int j = 0; j < 56; ++j) {
+                z[j] = __fadd_rn(z[j], b3[cb + j]);
+                if (j < nv)
+                    mx = fmaxf(mx, z[j]);
+            }
+            const float mb = -__fmul_rn(mx, kLog2e);
+            float S = 0.f, Tz = 0.f;
 #pragma unroll
-            for (int j = 0; j < kBins; ++j)
-                prow[j] = __fmul_rn(ex2_approx(__fmaf_rn(z[j], kLog2e, mb)), inv);
+            for (int j = 0; j < 56; ++j) {
+                if (j < nv) {
+                    const float e = ex2_approx(__fmaf_rn(z[j], kLog2e, mb));
+                    S = __fadd_rn(S, e);
+                    Tz = __fmaf_rn(e, z[j], Tz);
+                }
+            }
+            const float Lc = __fadd_rn(mx, logf(S));
+            const float Ac = __fdiv_rn(Tz, S);
+            const int xi = half * kBM + r;
+            if (ch)
+                xbuf[xi] = make_float2(Lc, Ac);
+            if (!(ok = pair_sync()))
+                break;
+            float L = 0.f;
+            if (!ch) {
+                const float2 o = xbuf[xi];
+                // L = logaddexp(Lc, o.x); entropy = L - (w0 A0 + w1 A1), w = e^(Lc - L)
+                const float hi = fmaxf(Lc, o.x), lo = fminf(Lc, o.x);
+                L = __fadd_rn(hi, log1pf(expf(__fsub_rn(lo, hi))));
+                const float w0 = expf(__fsub_rn(Lc, L)), w1 = expf(__fsub_rn(o.x, L));
+                const float Am = __fadd_rn(__fmul_rn(w0, Ac), __fmul_rn(w1, o.y));
+                if (in && a.score)
+                    a.score[row] = __fsub_rn(L, Am);
+                if (a.probs)
+                    xbuf[xi].x = L;
+            }
+            if (a.probs) {
+                if (!(ok = pair_sync()))
+                    break;
+                if (ch)
+                    L = xbuf[xi].x;
+                if (in) {
+                    const float lb = -__fmul_rn(L, kLog2e);
+                    float *prow = a.probs + (size_t)row * kBins + cb;
+#pragma unroll
+                    for (int j = 0; j < 56; ++j)
+                        if (j < nv)
+                            prow[j] = ex2_approx(__fmaf_rn(z[j], kLog2e, lb));
+                }
+            }
         }
     }
-    if (!ok && a.status)
+    if (*abort_flag && a.status)
         atomicExch(a.status, (int32_t)JL_ETIMEOUT);
     tc::tc_fence_before();
     __syncthreads();
@@ -1407,7 +1501,7 @@ int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, floa
     const int64_t tiles = (n + 2 * kBM - 1) / (2 * kBM);
     const int sms = device_sm_count();
     const int grid = (int)std::min<int64_t>(tiles, sms > 0 ? sms : 148);
-    fused_forward_kernel<<<grid, 256, kFusedSmem, st>>>(a);
+    fused_forward_kernel<<<grid, kFusedThreads, kFusedSmem, st>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? JL_OK : cuda_fail(e, "fused forward");
 }
