@@ -618,7 +618,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
         uint8_t *myH = sH + half * (kBM * kHid * 2);
         const float *b1g = a.params + kOffB1, *b2g = a.params + kOffB2;
         uint32_t acc_uses = 0;
-        bool ok = true;
 
         auto arrive = [&](uint64_t *bar) {
             __syncwarp();
@@ -706,7 +705,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
             const int64_t row = tile * (2 * kBM) + half * kBM + r;
             const bool in = row < a.n;
             // ---- product 1 done: activations 1 ----
-            if (!(ok = wait_acc()))
+            if (!wait_acc())
                 break;
             hidden_epilogue(b1g);
             arrive(h1b);
@@ -716,12 +715,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
                 arrive(feat);
             }
             // ---- product 2 done: activations 2 ----
-            if (!(ok = wait_acc()))
+            if (!wait_acc())
                 break;
             hidden_epilogue(b2g);
             arrive(h2b);
             // ---- product 3 done: logits of this thread's 56 columns ----
-            if (!(ok = wait_acc()))
+            if (!wait_acc())
                 break;
             float z[56];
             const int cb = 56 * ch;
@@ -756,7 +755,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
             const int xi = half * kBM + r;
             if (ch)
                 xbuf[xi] = make_float2(Lc, Ac);
-            if (!(ok = pair_sync()))
+            if (!pair_sync())
                 break;
             float L = 0.f;
             if (!ch) {
@@ -772,7 +771,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
                     xbuf[xi].x = L;
             }
             if (a.probs) {
-                if (!(ok = pair_sync()))
+                if (!pair_sync())
                     break;
                 if (ch)
                     L = xbuf[xi].x;
