@@ -326,6 +326,22 @@ int jl_render_batch(const jl_frame *frames, int32_t n, void *counts_base, uint8_
 int jl_render_frames_to_host(const jl_frame *frames, int32_t n, void *counts_host, uint8_t *rgba_host,
                              float *hist_host, const uint8_t *palette, int32_t depth, void *stream);
 
+/*
+ * The same as a reusable plan: jl_host_plan_create validates the frames and
+ * does the once-per-frame-set work (coordinate tables of every frame, `depth`
+ * device slots, internal streams); jl_host_plan_run renders every frame into
+ * the host buffers given at creation (which must stay valid while the plan
+ * lives), with the copies overlapped, and returns when the last copy has
+ * completed.  Runs on the device current at creation (JL_EINVAL otherwise).
+ * The palette (1024 bytes, or NULL for the default) is copied at creation.
+ * jl_host_plan_destroy waits for outstanding work and frees everything.
+ */
+typedef struct jl_host_plan jl_host_plan;
+int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, uint8_t *rgba_host, float *hist_host,
+                        const uint8_t *palette, int32_t depth, jl_host_plan **out);
+int jl_host_plan_run(jl_host_plan *plan, void *stream);
+void jl_host_plan_destroy(jl_host_plan *plan);
+
 /* ------------------------------------------------------------------------
  * Autotuner of the escape kernel's launch shape.
  * ------------------------------------------------------------------------ */

@@ -236,11 +236,12 @@ def _layout(frames):
 
 
 class HostFrames:
-    """Frames rendered into (pinned) host memory by jl_render_frames_to_host:
-    copies to the host overlap with rendering, `depth` frames in flight.
-    `frames` as for Batch.  The host buffers are allocated once (page-locked
-    through torch) and reused by every render() call; counts(i), rgba(i) and
-    hist(i) return numpy views of frame i."""
+    """Frames rendered into (pinned) host memory through a host plan
+    (jl_host_plan_*): copies to the host overlap with rendering, `depth`
+    frames in flight.  `frames` as for Batch.  The host buffers are allocated
+    once (page-locked through torch) and the plan (coordinate tables, device
+    slots, streams) once; every render() call renders all frames again.
+    counts(i), rgba(i) and hist(i) return numpy views of frame i."""
 
     def __init__(self, frames, palette=None, depth=0):
         import torch
@@ -255,13 +256,27 @@ class HostFrames:
             *[_frame_struct(f, self._c_off[i], self._r_off[i], self._h_off[i]) for i, f in enumerate(self.frames)])
         self._pal, self._pal_ptr = _palette_ptr(palette)
         self.d2h_bytes = sum(cb_ for cb_ in (cb, rb, hb))
+        h = ctypes.c_void_p()
+        check(self._L.jl_host_plan_create(self._arr, len(self.frames), self.counts_buf.ctypes.data,
+                                          self.rgba_buf.ctypes.data, self.hist_buf.ctypes.data, self._pal_ptr,
+                                          self.depth, ctypes.byref(h)))
+        self._h = h
 
     def render(self, stream=None):
         import torch
         st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
-        check(self._L.jl_render_frames_to_host(self._arr, len(self.frames), self.counts_buf.ctypes.data,
-                                               self.rgba_buf.ctypes.data, self.hist_buf.ctypes.data, self._pal_ptr,
-                                               self.depth, st))
+        check(self._L.jl_host_plan_run(self._h, st))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.jl_host_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
     def counts(self, i):
         f, o = self.frames[i], self._c_off[i]

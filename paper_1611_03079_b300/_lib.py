@@ -71,6 +71,10 @@ SIGNATURES = {
     "jl_default_palette": (ctypes.c_int, [_vp]),
     "jl_render": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "jl_render_frames_to_host": (ctypes.c_int, [ctypes.c_void_p, _i32, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "jl_host_plan_create": (ctypes.c_int, [ctypes.c_void_p, _i32, _vp, _vp, _vp, _vp, _i32,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "jl_host_plan_run": (ctypes.c_int, [_vp, _vp]),
+    "jl_host_plan_destroy": (None, [_vp]),
     "jl_render_map": (ctypes.c_int, [ctypes.POINTER(Map), _d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp,
                                      _vp, _vp, _vp, _vp]),
     "jl_render_variant": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,

@@ -164,6 +164,54 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
     return JL_OK;
 }
 
+// Launches the escape kernel of one frame whose coordinate tables (F.xs,
+// F.ys) are already filled: clears the 16-byte control block `ctl` (work
+// counter, status) and the histogram, runs the kernel and finalises the
+// histogram.  All pointers are device pointers.
+int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStream_t st, const Variant *vopt)
+{
+    unsigned long long *counter = static_cast<unsigned long long *>(ctl);
+    int32_t *status = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ctl) + 8);
+    cudaError_t e = cudaMemsetAsync(ctl, 0, 16, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaMemsetAsync(counter)");
+    if (F.hist_bins) {
+        e = cudaMemsetAsync(F.hist_bins, 0, ((size_t)F.max_iter + 1) * 4, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync(hist)");
+    }
+    EscapeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.frames = nullptr;
+    a.n_frames = 1;
+    a.hist_smem = (F.hist_bins && F.max_iter + 1 <= 4096) ? 1 : 0;
+    a.total_chunks = F.chunk_count;
+    a.total_tiles = F.tile_count;
+    a.chunk_counter = counter;
+    a.status = status;
+    a.cycle_budget = 0;
+    uint8_t pal[1024];
+    if (palette)
+        memcpy(pal, palette, 1024);
+    else
+        make_default_palette(pal);
+    memcpy(a.palette, pal, 1024);
+    a.single = F;
+    const int sms = device_sm_count();
+    if (sms <= 0)
+        return fail(JL_EUNSUPPORTED, "no CUDA device");
+    Variant v = vopt ? *vopt : tuned_variant(prec, F.max_iter);
+    e = launch_escape(a, prec, v, sms, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "escape kernel launch");
+    if (F.hist_bins) {
+        e = launch_hist_finalize(nullptr, &F, 1, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "histogram finalize launch");
+    }
+    return JL_OK;
+}
+
 // Renders one frame whose descriptor is complete except for scratch-backed
 // fields; all pointers in F are device pointers.
 int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, const Variant *vopt)
@@ -179,46 +227,12 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
     uint8_t *base = static_cast<uint8_t *>(scratch);
     F.xs = base;
     F.ys = base + (size_t)F.W * esz;
-    unsigned long long *counter = reinterpret_cast<unsigned long long *>(base + coord_pad);
-    int32_t *status = reinterpret_cast<int32_t *>(base + coord_pad + 8);
     int rc = JL_OK;
-    do {
-        e = cudaMemsetAsync(base + coord_pad, 0, 16, st);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync(counter)"); break; }
-        if (F.hist_bins) {
-            e = cudaMemsetAsync(F.hist_bins, 0, ((size_t)F.max_iter + 1) * 4, st);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync(hist)"); break; }
-        }
-        e = launch_coords(nullptr, &F, 1, st);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "coords kernel launch"); break; }
-
-        EscapeArgs a;
-        memset(&a, 0, sizeof(a));
-        a.frames = nullptr;
-        a.n_frames = 1;
-        a.hist_smem = (F.hist_bins && F.max_iter + 1 <= 4096) ? 1 : 0;
-        a.total_chunks = F.chunk_count;
-        a.total_tiles = F.tile_count;
-        a.chunk_counter = counter;
-        a.status = status;
-        a.cycle_budget = 0;
-        uint8_t pal[1024];
-        if (palette)
-            memcpy(pal, palette, 1024);
-        else
-            make_default_palette(pal);
-        memcpy(a.palette, pal, 1024);
-        a.single = F;
-        const int sms = device_sm_count();
-        if (sms <= 0) { rc = fail(JL_EUNSUPPORTED, "no CUDA device"); break; }
-        Variant v = vopt ? *vopt : tuned_variant(prec, F.max_iter);
-        e = launch_escape(a, prec, v, sms, st);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "escape kernel launch"); break; }
-        if (F.hist_bins) {
-            e = launch_hist_finalize(nullptr, &F, 1, st);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "histogram finalize launch"); break; }
-        }
-    } while (0);
+    e = launch_coords(nullptr, &F, 1, st);
+    if (e != cudaSuccess)
+        rc = cuda_fail(e, "coords kernel launch");
+    if (rc == JL_OK)
+        rc = launch_frame(F, prec, palette, base + coord_pad, st, vopt);
     cudaError_t e2 = cudaFreeAsync(scratch, st);
     if (rc == JL_OK && e2 != cudaSuccess)
         rc = cuda_fail(e2, "cudaFreeAsync(scratch)");

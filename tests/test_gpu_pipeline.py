@@ -74,3 +74,18 @@ def test_rejects_bad_frames(cuda):
         jl.HostFrames(bad).render()
     with pytest.raises(jl.JLError):
         jl.HostFrames([dict(c=0.1, rect=(-1, 1, -1, 1), W=8, H=8, max_iter=10, count_type="u16")], depth=9).render()
+
+
+def test_one_shot_call_matches_plan(cuda):
+    """jl_render_frames_to_host (plan created, run and destroyed in one call)
+    writes the same bytes as a reused plan."""
+    frames = mixed_frames()
+    hf = jl.HostFrames(frames, depth=4)
+    hf.render()
+    c2 = np.zeros_like(hf.counts_buf)
+    r2 = np.zeros_like(hf.rgba_buf)
+    h2 = np.zeros_like(hf.hist_buf)
+    jl._lib.check(jl._lib.lib().jl_render_frames_to_host(hf._arr, len(frames), c2.ctypes.data, r2.ctypes.data,
+                                                         h2.ctypes.data, None, 2, None))
+    assert (c2 == hf.counts_buf).all() and (r2 == hf.rgba_buf).all() and (h2 == hf.hist_buf).all()
+    hf.close()
