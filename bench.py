@@ -568,7 +568,7 @@ def main():
         e2e = {"value": total_iters / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 96 * n,
                "d2h_bytes_per_step": int(hf.d2h_bytes), "ms_per_step": e2e_s * 1e3, "steps": len(times),
                "counts_match_device": bool(ok),
-               "note": "jl_render_frames_to_host: 16 frames per step rendered on 3 internal streams into "
+               "note": "host plan (jl_host_plan_run): 16 frames per step rendered on 6 internal streams into "
                        "device slots and copied to pinned host memory (counts + RGBA8) as each frame "
                        "finishes; host wall clock per call (median of steps), the call returns after the "
                        "last copy; h2d = the frame descriptions (96 B each)"}
