@@ -376,58 +376,70 @@ __device__ __forceinline__ void fourier_pair(float b0, float b1, float cr, float
 // Fused forward for screening: features -> three products -> softmax and
 // entropy in one persistent kernel, activations kept on the SM.
 // Weights are pre-packed in global memory as shared-memory images of the
-// K-major core-matrix layout: W1 as one 256x64 image, W2 as four 256x64
-// K-chunks and W3 as four 112x64 K-chunks, all nine streamed per tile through
-// a double buffer with cp.async.bulk (completion as mbarrier transaction
-// bytes); the chunks stay L2-resident across CTAs.
+// K-major core-matrix layout in 32-wide K chunks: W1 as two 256x32 chunks,
+// W2 as eight 256x32 and W3 as eight 112x32, all eighteen streamed per tile
+// through a four-slot ring with cp.async.bulk (completion as mbarrier
+// transaction bytes), three chunks ahead; the chunks stay L2-resident across
+// CTAs.
 // ---------------------------------------------------------------------------
-static constexpr int kImgW = 256 * 64 * 2;                 // 32 KB: 256 rows x 64 k
-static constexpr int kImgW3 = kBinsPad * 64 * 2;           // 14 KB: 112 rows x 64 k
-static constexpr int kPackElems = (kImgW + 4 * kImgW + 4 * kImgW3) / 2;  // bf16 elements
+static constexpr int kChK = 32;                              // K width of a weight chunk
+static constexpr int kImgW = 256 * kChK * 2;                 // 16 KB: 256 rows x 32 k
+static constexpr int kImgW3 = kBinsPad * kChK * 2;           // 7 KB: 112 rows x 32 k
+static constexpr int kChunksPerTile = 2 + 8 + 8;             // W1, W2, W3
+static constexpr int kRing = 4;                              // weight slots
+static constexpr int kPackElems = (10 * kImgW + 8 * kImgW3) / 2;  // bf16 elements
 // shared-memory map of the fused kernel (bytes): two 128-row halves
 static constexpr int kFsPhi = 0;                               // 2 x (128 x 64 bf16)
 static constexpr int kFsH = kFsPhi + 2 * kBM * kIn * 2;        // 2 x (128 x 256 bf16)
-static constexpr int kFsWB = kFsH + 2 * kBM * kHid * 2;        // 2 x 32 KB weight chunks
-static constexpr int kFsB3 = kFsWB + 2 * kImgW;                // b3 (112 fp32), Fourier B (64 fp32)
+static constexpr int kFsWB = kFsH + 2 * kBM * kHid * 2;        // kRing x 16 KB weight chunks
+static constexpr int kFsB3 = kFsWB + kRing * kImgW;            // b3 (112 fp32), Fourier B (64 fp32)
 static constexpr int kFsX = kFsB3 + (kBinsPad + 64) * 4;       // softmax partials: 256 rows x 2 fp32
 static constexpr int kFsBar = kFsX + 2 * kBM * 2 * 4;          // mbarriers, TMEM holder, abort flag
-static constexpr int kFusedSmem = kFsBar + 20 * 8;
+static constexpr int kFusedSmem = kFsBar + 24 * 8;
 static_assert(kFusedSmem <= 232448, "fused forward exceeds the shared-memory limit");
 static constexpr int kFusedEpiWarps = 16;                      // two per row (column halves)
-static constexpr int kFusedThreads = (kFusedEpiWarps + 1) * 32;  // + one producer warp
+static constexpr int kFusedThreads = (kFusedEpiWarps + 2) * 32;  // + MMA warp + loader warp
 
-// One thread per 16-byte piece of the packed images.
+// Byte offset and size of chunk j (0..17) in the packed images.
+__host__ __device__ inline size_t chunk_offset(int j, uint32_t &bytes)
+{
+    if (j < 10) {
+        bytes = kImgW;
+        return (size_t)j * kImgW;
+    }
+    bytes = kImgW3;
+    return 10 * (size_t)kImgW + (size_t)(j - 10) * kImgW3;
+}
+
+// One thread per 16-byte piece of the packed images.  Chunk j: 0, 1 -> W1
+// k 0..31, 32..63; 2..9 -> W2 k 32(j-2) ..; 10..17 -> W3 k 32(j-10) ..
 __global__ void pack_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *__restrict__ out)
 {
     const int piece = blockIdx.x * blockDim.x + threadIdx.x;
     const int total = kPackElems / 8;
     if (piece >= total)
         return;
-    // which image
-    int img, local;
     const int per_w = kImgW / 16, per_w3 = kImgW3 / 16;
-    if (piece < per_w) {
-        img = 0;
-        local = piece;
-    } else if (piece < 5 * per_w) {
-        img = 1 + (piece - per_w) / per_w;
-        local = (piece - per_w) % per_w;
+    int img, local;
+    if (piece < 10 * per_w) {
+        img = piece / per_w;
+        local = piece % per_w;
     } else {
-        img = 5 + (piece - 5 * per_w) / per_w3;
-        local = (piece - 5 * per_w) % per_w3;
+        img = 10 + (piece - 10 * per_w) / per_w3;
+        local = (piece - 10 * per_w) % per_w3;
     }
-    // inverse of offset ((r/8)*8 + g)*128 + (r%8)*16 for a 64-wide K chunk
+    // inverse of offset ((r/8)*4 + g)*128 + (r%8)*16 for a 32-wide K chunk
     const int cm = local >> 3, rr = local & 7;
-    const int r = (cm >> 3) * 8 + rr;
-    const int g = cm & 7;
+    const int r = (cm >> 2) * 8 + rr;
+    const int g = cm & 3;
     const float *src;
     int rows, ld, k0;
-    if (img == 0) {
-        src = p + kOffW1; rows = kHid; ld = kIn; k0 = 0;
-    } else if (img <= 4) {
-        src = p + kOffW2; rows = kHid; ld = kHid; k0 = (img - 1) * 64;
+    if (img < 2) {
+        src = p + kOffW1; rows = kHid; ld = kIn; k0 = img * kChK;
+    } else if (img < 10) {
+        src = p + kOffW2; rows = kHid; ld = kHid; k0 = (img - 2) * kChK;
     } else {
-        src = p + kOffW3; rows = kBins; ld = kHid; k0 = (img - 5) * 64;
+        src = p + kOffW3; rows = kBins; ld = kHid; k0 = (img - 10) * kChK;
     }
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -449,21 +461,24 @@ struct FusedArgs {
 
 // Warp-specialised fused forward over 256-row tiles (two 128-row halves,
 // each with its own 256-column TMEM accumulator; 512 columns allocated).
-//   producer (warp 16, one thread): streams the nine weight chunks of every
-//     tile (W1, W2 x 4, W3 x 4; cp.async.bulk into a 2 x 32 KB double
-//     buffer) and issues each chunk's MMAs for both halves, so every chunk is
-//     read from L2 once per 256 rows;
+//   loader (warp 17, one thread): streams the eighteen 16 KB weight chunks of
+//     every tile (W1 x 2, W2 x 8, W3 x 8) into a four-slot ring as soon as a
+//     slot's previous MMAs have completed;
+//   MMA issuer (warp 16, one thread): issues each chunk's MMAs for both
+//     halves, so every chunk is read from L2 once per 256 rows;
 //   epilogue (warps 0..15): warp w serves TMEM lane quarter (w & 3) of half
 //     (w >> 2) & 1 and column half w >> 3, so each row has two threads.  They
 //     build Fourier features, turn accumulators into relu(D + b) bf16
 //     activations in shared memory, and form softmax and entropy.
-// Hand-offs are mbarriers: feat / h1 / h2 / tfree (one arrival per epilogue
-// warp, waited by the producer) and acc (MMA completion, waited by the
-// epilogue).  The next tile's features are built while product 2 runs, and
+// Hand-offs are mbarriers: full / empty (ring slots), feat / h1 / h2 / tfree
+// (one arrival per epilogue warp, waited by the MMA issuer) and acc (MMA
+// completion, waited by the epilogue).  The next tile's features are built while product 2 runs, and
 // its product 1 may start while the softmax of this tile is still computed.
 // Every wait is bounded; a timeout sets a shared abort flag that ends all
 // other waits, in-flight copies and MMAs are waited for, TMEM is freed and
-// the status word reads JL_ETIMEOUT.
+// the status word reads JL_ETIMEOUT.  (One issuing thread that also refilled
+// the ring waited for each chunk's MMAs before the next copy, which tied the
+// products to MMA completion latency; the two roles are separate warps.)
 __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const __grid_constant__ FusedArgs a)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
@@ -474,11 +489,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
     float *Bs = b3 + kBinsPad;
     float2 *xbuf = reinterpret_cast<float2 *>(sm + kFsX);           // [256 rows]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kFsBar);
-    uint64_t *full = bars, *empty = bars + 2, *acc = bars + 4, *feat = bars + 5, *h1b = bars + 6, *h2b = bars + 7,
-             *tfree = bars + 8, *fin = bars + 9;
-    uint32_t *holder = reinterpret_cast<uint32_t *>(bars + 10);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 11);
-    uint64_t *pairb = bars + 12;  // [8]: the two warps serving the same rows (w, w + 8)
+    uint64_t *full = bars, *empty = bars + kRing, *acc = bars + 2 * kRing, *feat = acc + 1, *h1b = acc + 2,
+             *h2b = acc + 3, *tfree = acc + 4, *fin = acc + 5;
+    uint32_t *holder = reinterpret_cast<uint32_t *>(acc + 6);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(acc + 7);
+    uint64_t *pairb = acc + 8;  // [8]: the two warps serving the same rows (w, w + 8)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ntiles = (a.n + 2 * kBM - 1) / (2 * kBM);
@@ -493,7 +508,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
     if (threadIdx.x < 64)
         Bs[threadIdx.x] = a.B[threadIdx.x];
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kRing; ++i) {
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&empty[i], 1);
         }
@@ -513,34 +528,38 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
     tc::tc_fence_after();
     const uint32_t taddr = *holder;
 
-    if (warp == kFusedEpiWarps) {
-        // ------------------------------ producer ------------------------------
+    const uint8_t *gpack = reinterpret_cast<const uint8_t *>(a.pack);
+    const int total_chunks = my_tiles * kChunksPerTile;
+    if (warp == kFusedEpiWarps + 1) {
+        // ------------------------------- loader -------------------------------
+        // chunk q goes to slot q % kRing once the MMAs of chunk q - kRing have
+        // completed (their commit arrives on empty[slot])
         if (lane == 0) {
-            const uint8_t *gpack = reinterpret_cast<const uint8_t *>(a.pack);
-            auto chunk_src = [&](int q, uint32_t &bytes) -> const uint8_t * {
-                const int j = q % 9;  // 0 -> W1, 1..4 -> W2, 5..8 -> W3
-                if (j < 5) {
-                    bytes = kImgW;
-                    return gpack + (size_t)j * kImgW;
-                }
-                bytes = kImgW3;
-                return gpack + 5 * (size_t)kImgW + (size_t)(j - 5) * kImgW3;
-            };
-            const int total_chunks = my_tiles * 9;
-            int loads_issued = 1, loads_waited = 0;  // per-buffer accounting for the abort path
-            {
+            int issued = 0;
+            for (int q = 0; q < total_chunks; ++q) {
+                const int slot = q % kRing;
+                if (q >= kRing && !tc::mbar_wait_or_abort(&empty[slot], ((q / kRing) - 1) & 1, kWaitLimit, abort_flag))
+                    break;
                 uint32_t bytes;
-                const uint8_t *src = chunk_src(0, bytes);
-                tc::fence_proxy_async_smem();
-                tc::bulk_load(sWB, src, bytes, &full[0]);
+                const size_t off = chunk_offset(q % kChunksPerTile, bytes);
+                tc::bulk_load(sWB + slot * kImgW, gpack + off, bytes, &full[slot]);
+                ++issued;
             }
+            // the last kRing copies issued sit in distinct slots: let them land
+            for (int q = issued - kRing; q < issued; ++q)
+                if (q >= 0)
+                    tc::mbar_wait(&full[q % kRing], (q / kRing) & 1, kWaitLimit);
+        }
+    } else if (warp == kFusedEpiWarps) {
+        // ------------------------------ MMA issuer ----------------------------
+        if (lane == 0) {
             bool okp = true;
-            // wait for chunk q, issue both halves' MMAs, refill the other buffer with chunk q + 1
+            // wait for chunk q, issue both halves' MMAs (two K-steps of 16) and
+            // release the slot to the loader when they complete
             auto run_chunk = [&](int q, uint32_t a0, uint32_t a1, uint32_t a_sbo, uint32_t n_rows, bool first) -> bool {
-                const int b = q & 1;
-                if (!tc::mbar_wait_or_abort(&full[b], (q >> 1) & 1, kWaitLimit, abort_flag))
+                const int b = q % kRing;
+                if (!tc::mbar_wait_or_abort(&full[b], (q / kRing) & 1, kWaitLimit, abort_flag))
                     return false;
-                ++loads_waited;
                 tc::tc_fence_after();
                 const uint32_t idesc = tc::idesc_bf16(kBM, n_rows);
                 const uint32_t bb = tc::smem_u32(sWB + b * kImgW);
@@ -548,27 +567,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t ab = h ? a1 : a0;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
+                    for (int kk = 0; kk < 2; ++kk) {
                         const uint64_t ad = tc::smem_desc(ab + kk * 256, 128, a_sbo);
-                        const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, 1024);
+                        const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, 512);
                         tc::mma_bf16(taddr + (uint32_t)(h * 256), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
                     }
                 }
                 tc::mma_commit(&empty[b]);
-                if (q + 1 < total_chunks) {
-                    const int nb = (q + 1) & 1;
-                    if (q >= 1 && !tc::mbar_wait_or_abort(&empty[nb], ((q - 1) >> 1) & 1, kWaitLimit, abort_flag))
-                        return false;
-                    uint32_t bytes;
-                    const uint8_t *src = chunk_src(q + 1, bytes);
-                    tc::bulk_load(sWB + nb * kImgW, src, bytes, &full[nb]);
-                    ++loads_issued;
-                }
                 return true;
             };
             const uint32_t phi0 = tc::smem_u32(sPhi), phi1 = tc::smem_u32(sPhi + kBM * kIn * 2);
             const uint32_t hh0 = tc::smem_u32(sH), hh1 = tc::smem_u32(sH + kBM * kHid * 2);
             for (int it = 0; it < my_tiles && okp; ++it) {
+                const int q0 = it * kChunksPerTile;
                 // product 1: the tile's features are in place and the previous
                 // tile's logits have been read out of TMEM
                 okp = tc::mbar_wait_or_abort(feat, it & 1, kWaitLimit, abort_flag);
@@ -577,7 +588,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
                 if (!okp)
                     break;
                 tc::tc_fence_after();
-                okp = run_chunk(it * 9, phi0, phi1, 1024, kHid, true);
+                // K chunk j of Phi starts at core-matrix column 4 j (512 bytes)
+                for (int j = 0; j < 2 && okp; ++j)
+                    okp = run_chunk(q0 + j, phi0 + j * 512, phi1 + j * 512, 1024, kHid, j == 0);
                 if (!okp)
                     break;
                 tc::mma_commit(acc);
@@ -586,8 +599,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
                 if (!okp)
                     break;
                 tc::tc_fence_after();
-                for (int j = 0; j < 4 && okp; ++j)
-                    okp = run_chunk(it * 9 + 1 + j, hh0 + j * 8 * 128, hh1 + j * 8 * 128, 4096, kHid, j == 0);
+                for (int j = 0; j < 8 && okp; ++j)
+                    okp = run_chunk(q0 + 2 + j, hh0 + j * 512, hh1 + j * 512, 4096, kHid, j == 0);
                 if (!okp)
                     break;
                 tc::mma_commit(acc);
@@ -596,16 +609,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
                 if (!okp)
                     break;
                 tc::tc_fence_after();
-                for (int j = 0; j < 4 && okp; ++j)
-                    okp = run_chunk(it * 9 + 5 + j, hh0 + j * 8 * 128, hh1 + j * 8 * 128, 4096, kBinsPad, j == 0);
+                for (int j = 0; j < 8 && okp; ++j)
+                    okp = run_chunk(q0 + 10 + j, hh0 + j * 512, hh1 + j * 512, 4096, kBinsPad, j == 0);
                 if (!okp)
                     break;
                 tc::mma_commit(acc);
             }
-            // let every copy and product already issued land before TMEM is
-            // freed (nothing is outstanding on the normal path but the last MMAs)
-            for (int q = loads_waited; q < loads_issued; ++q)
-                tc::mbar_wait(&full[q & 1], (q >> 1) & 1, kWaitLimit);
+            // every product issued has completed before TMEM is freed
             tc::mma_commit(fin);
             tc::mbar_wait(fin, 0, kWaitLimit);
         }
