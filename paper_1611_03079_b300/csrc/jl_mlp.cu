@@ -376,18 +376,18 @@ __device__ __forceinline__ void fourier_pair(float b0, float b1, float cr, float
 // Fused forward for screening: features -> three products -> softmax and
 // entropy in one persistent kernel, activations kept on the SM.
 // Weights are pre-packed in global memory as shared-memory images of the
-// K-major core-matrix layout in 32-wide K chunks: W1 as two 256x32 chunks,
-// W2 as eight 256x32 and W3 as eight 112x32, all eighteen streamed per tile
-// through a four-slot ring with cp.async.bulk (completion as mbarrier
-// transaction bytes), three chunks ahead; the chunks stay L2-resident across
-// CTAs.
+// K-major core-matrix layout: W1 as two 256x32 K-chunks, W2 as eight 256x32
+// and W3 as four 112x64, all fourteen streamed per tile through a four-slot
+// ring of 16 KB slots with cp.async.bulk (completion as mbarrier transaction
+// bytes); the four W3 chunks fit the ring at once, so they all arrive while
+// the second epilogue runs.  The chunks stay L2-resident across CTAs.
 // ---------------------------------------------------------------------------
 static constexpr int kChK = 32;                              // K width of a weight chunk
 static constexpr int kImgW = 256 * kChK * 2;                 // 16 KB: 256 rows x 32 k
-static constexpr int kImgW3 = kBinsPad * kChK * 2;           // 7 KB: 112 rows x 32 k
-static constexpr int kChunksPerTile = 2 + 8 + 8;             // W1, W2, W3
-static constexpr int kRing = 4;                              // weight slots
-static constexpr int kPackElems = (10 * kImgW + 8 * kImgW3) / 2;  // bf16 elements
+static constexpr int kImgW3 = kBinsPad * 64 * 2;             // 14 KB: 112 rows x 64 k
+static constexpr int kChunksPerTile = 2 + 8 + 4;             // W1, W2, W3
+static constexpr int kRing = 4;                              // weight slots (16 KB)
+static constexpr int kPackElems = (10 * kImgW + 4 * kImgW3) / 2;  // bf16 elements
 // shared-memory map of the fused kernel (bytes): two 128-row halves
 static constexpr int kFsPhi = 0;                               // 2 x (128 x 64 bf16)
 static constexpr int kFsH = kFsPhi + 2 * kBM * kIn * 2;        // 2 x (128 x 256 bf16)
@@ -400,7 +400,7 @@ static_assert(kFusedSmem <= 232448, "fused forward exceeds the shared-memory lim
 static constexpr int kFusedEpiWarps = 16;                      // two per row (column halves)
 static constexpr int kFusedThreads = (kFusedEpiWarps + 2) * 32;  // + MMA warp + loader warp
 
-// Byte offset and size of chunk j (0..17) in the packed images.
+// Byte offset and size of chunk j (0..13) in the packed images.
 __host__ __device__ inline size_t chunk_offset(int j, uint32_t &bytes)
 {
     if (j < 10) {
@@ -412,7 +412,7 @@ __host__ __device__ inline size_t chunk_offset(int j, uint32_t &bytes)
 }
 
 // One thread per 16-byte piece of the packed images.  Chunk j: 0, 1 -> W1
-// k 0..31, 32..63; 2..9 -> W2 k 32(j-2) ..; 10..17 -> W3 k 32(j-10) ..
+// k 0..31, 32..63; 2..9 -> W2 k 32(j-2) ..; 10..13 -> W3 k 64(j-10) ..
 __global__ void pack_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *__restrict__ out)
 {
     const int piece = blockIdx.x * blockDim.x + threadIdx.x;
@@ -428,10 +428,12 @@ __global__ void pack_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *
         img = 10 + (piece - 10 * per_w) / per_w3;
         local = (piece - 10 * per_w) % per_w3;
     }
-    // inverse of offset ((r/8)*4 + g)*128 + (r%8)*16 for a 32-wide K chunk
+    // inverse of offset ((r/8)*G + g)*128 + (r%8)*16 for a chunk of G 8-wide
+    // K groups (G = 4 for the 32-wide W1/W2 chunks, 8 for the 64-wide W3 ones)
+    const int G = img < 10 ? 4 : 8;
     const int cm = local >> 3, rr = local & 7;
-    const int r = (cm >> 2) * 8 + rr;
-    const int g = cm & 3;
+    const int r = (cm / G) * 8 + rr;
+    const int g = cm % G;
     const float *src;
     int rows, ld, k0;
     if (img < 2) {
@@ -439,7 +441,7 @@ __global__ void pack_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *
     } else if (img < 10) {
         src = p + kOffW2; rows = kHid; ld = kHid; k0 = (img - 2) * kChK;
     } else {
-        src = p + kOffW3; rows = kBins; ld = kHid; k0 = (img - 10) * kChK;
+        src = p + kOffW3; rows = kBins; ld = kHid; k0 = (img - 10) * 64;
     }
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -461,9 +463,9 @@ struct FusedArgs {
 
 // Warp-specialised fused forward over 256-row tiles (two 128-row halves,
 // each with its own 256-column TMEM accumulator; 512 columns allocated).
-//   loader (warp 17, one thread): streams the eighteen 16 KB weight chunks of
-//     every tile (W1 x 2, W2 x 8, W3 x 8) into a four-slot ring as soon as a
-//     slot's previous MMAs have completed;
+//   loader (warp 17, one thread): streams the fourteen weight chunks of every
+//     tile (W1 x 2 and W2 x 8 of 16 KB, W3 x 4 of 14 KB) into a four-slot ring
+//     as soon as a slot's previous MMAs have completed;
 //   MMA issuer (warp 16, one thread): issues each chunk's MMAs for both
 //     halves, so every chunk is read from L2 once per 256 rows;
 //   epilogue (warps 0..15): warp w serves TMEM lane quarter (w & 3) of half
@@ -556,7 +558,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
             bool okp = true;
             // wait for chunk q, issue both halves' MMAs (two K-steps of 16) and
             // release the slot to the loader when they complete
-            auto run_chunk = [&](int q, uint32_t a0, uint32_t a1, uint32_t a_sbo, uint32_t n_rows, bool first) -> bool {
+            // ksteps: K steps of 16 in the chunk (2 for W1/W2, 4 for W3);
+            // b_sbo: the chunk image's 8-row group stride (128 * K groups)
+            auto run_chunk = [&](int q, uint32_t a0, uint32_t a1, uint32_t a_sbo, uint32_t n_rows, bool first,
+                                 int ksteps, uint32_t b_sbo) -> bool {
                 const int b = q % kRing;
                 if (!tc::mbar_wait_or_abort(&full[b], (q / kRing) & 1, kWaitLimit, abort_flag))
                     return false;
@@ -566,10 +571,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t ab = h ? a1 : a0;
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
+                    for (int kk = 0; kk < ksteps; ++kk) {
                         const uint64_t ad = tc::smem_desc(ab + kk * 256, 128, a_sbo);
-                        const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, 512);
+                        const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, b_sbo);
                         tc::mma_bf16(taddr + (uint32_t)(h * 256), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
                     }
                 }
@@ -590,7 +594,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
                 tc::tc_fence_after();
                 // K chunk j of Phi starts at core-matrix column 4 j (512 bytes)
                 for (int j = 0; j < 2 && okp; ++j)
-                    okp = run_chunk(q0 + j, phi0 + j * 512, phi1 + j * 512, 1024, kHid, j == 0);
+                    okp = run_chunk(q0 + j, phi0 + j * 512, phi1 + j * 512, 1024, kHid, j == 0, 2, 512);
                 if (!okp)
                     break;
                 tc::mma_commit(acc);
@@ -600,7 +604,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
                     break;
                 tc::tc_fence_after();
                 for (int j = 0; j < 8 && okp; ++j)
-                    okp = run_chunk(q0 + 2 + j, hh0 + j * 512, hh1 + j * 512, 4096, kHid, j == 0);
+                    okp = run_chunk(q0 + 2 + j, hh0 + j * 512, hh1 + j * 512, 4096, kHid, j == 0, 2, 512);
                 if (!okp)
                     break;
                 tc::mma_commit(acc);
@@ -609,8 +613,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
                 if (!okp)
                     break;
                 tc::tc_fence_after();
-                for (int j = 0; j < 8 && okp; ++j)
-                    okp = run_chunk(q0 + 10 + j, hh0 + j * 512, hh1 + j * 512, 4096, kBinsPad, j == 0);
+                // W3 K chunk j (64 wide) starts at core-matrix column 8 j (1024 bytes)
+                for (int j = 0; j < 4 && okp; ++j)
+                    okp = run_chunk(q0 + 10 + j, hh0 + j * 1024, hh1 + j * 1024, 4096, kBinsPad, j == 0, 4, 1024);
                 if (!okp)
                     break;
                 tc::mma_commit(acc);
