@@ -86,46 +86,64 @@ static constexpr int kSplitK = 16;  // K splits of the weight-gradient products 
 
 // Stage rows [row0, row0 + nrows) x k [k0, k0 + 64) of an operand into the
 // K-major core-matrix layout: piece (r, g) (8 consecutive k) at byte
-// ((r/8)*8 + g)*128 + (r%8)*16.  Out-of-range elements are zero.
+// ((r/8)*8 + g)*128 + (r%8)*16.  Out-of-range elements are zero.  Each
+// thread gathers up to eight pieces into registers before storing any, so
+// their global-load latencies overlap.
 __device__ __forceinline__ void stage_operand(uint8_t *dst, const __nv_bfloat16 *src, int ld, int trans, int row0,
                                               int nrows, int rlim, int k0, int klim)
 {
     const int pieces = nrows * 8;
-    for (int p = threadIdx.x; p < pieces; p += blockDim.x) {
-        int r, g;
-        if (!trans) {
-            // 8 consecutive threads fill one 128-byte core matrix (no bank conflicts)
-            r = (p >> 6) * 8 + (p & 7);
-            g = (p >> 3) & 7;
-        } else {
-            // consecutive threads take consecutive rows (contiguous in global)
-            r = p % nrows;
-            g = p / nrows;
-        }
-        const int row = row0 + r;
-        const int k = k0 + g * 8;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (row < rlim) {
+    const int step = blockDim.x;
+    for (int base = threadIdx.x; base < pieces; base += 8 * step) {
+        uint4 v[8];
+        int off[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int p = base + u * step;
+            v[u] = make_uint4(0, 0, 0, 0);
+            off[u] = -1;
+            if (p >= pieces)
+                continue;
+            int r, g;
             if (!trans) {
-                const __nv_bfloat16 *s = src + (size_t)row * ld + k;
-                if (k + 8 <= klim && ((reinterpret_cast<uintptr_t>(s) & 15) == 0)) {
-                    v = *reinterpret_cast<const uint4 *>(s);
+                // 8 consecutive threads fill one 128-byte core matrix (no bank conflicts)
+                r = (p >> 6) * 8 + (p & 7);
+                g = (p >> 3) & 7;
+            } else {
+                // consecutive threads take consecutive rows (contiguous in global)
+                r = p % nrows;
+                g = p / nrows;
+            }
+            off[u] = ((r >> 3) * 8 + g) * 128 + (r & 7) * 16;
+            const int row = row0 + r;
+            const int k = k0 + g * 8;
+            if (row < rlim) {
+                if (!trans) {
+                    const __nv_bfloat16 *s = src + (size_t)row * ld + k;
+                    if (k + 8 <= klim && ((reinterpret_cast<uintptr_t>(s) & 15) == 0)) {
+                        v[u] = *reinterpret_cast<const uint4 *>(s);
+                    } else {
+                        uint16_t e[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            e[i] = (k + i < klim) ? __bfloat16_as_ushort(s[i]) : (uint16_t)0;
+                        v[u] = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16),
+                                          e[6] | (e[7] << 16));
+                    }
                 } else {
                     uint16_t e[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
-                        e[i] = (k + i < klim) ? __bfloat16_as_ushort(s[i]) : (uint16_t)0;
-                    v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
+                        e[i] = (k + i < klim) ? __bfloat16_as_ushort(src[(size_t)(k + i) * ld + row]) : (uint16_t)0;
+                    v[u] = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16),
+                                      e[6] | (e[7] << 16));
                 }
-            } else {
-                uint16_t e[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    e[i] = (k + i < klim) ? __bfloat16_as_ushort(src[(size_t)(k + i) * ld + row]) : (uint16_t)0;
-                v = make_uint4(e[0] | (e[1] << 16), e[2] | (e[3] << 16), e[4] | (e[5] << 16), e[6] | (e[7] << 16));
             }
         }
-        *reinterpret_cast<uint4 *>(dst + ((r >> 3) * 8 + g) * 128 + (r & 7) * 16) = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (off[u] >= 0)
+                *reinterpret_cast<uint4 *>(dst + off[u]) = v[u];
     }
 }
 
@@ -207,10 +225,17 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
     tc::tc_fence_after();
 
     // ---------------- epilogue: this thread owns tile row `r` ----------------
+    // Results pass through an fp32 tile in the (now idle) staging buffers,
+    // 65 words per row (odd, so one-row-per-thread accesses are free of bank
+    // conflicts); the tile is then written out a row at a time by whole
+    // warps (coalesced), and column sums are read down its columns.
     const int r = warp * 32 + lane;
     const int row = m0 + r;
     const bool in = row < g.M;
     const uint32_t tw = taddr + ((uint32_t)(warp * 32) << 16);
+    constexpr int kTP = 65;                               // tile pitch (words)
+    float *T = reinterpret_cast<float *>(stage0);         // [128][kTP]
+    uint16_t *Mk = reinterpret_cast<uint16_t *>(stage0 + kBM * kTP * 4);  // [128][130] bf16 mask tile
 
     if constexpr (EPI == EPI_SOFTMAX) {
         float mx = -INFINITY;
@@ -238,113 +263,148 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
         const float inv = 1.f / sum;
         const float lse = mx + logf(sum);
         float ce = 0.f, ent = 0.f;
-        for (int c0 = 0; c0 < g.BN; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tw + c0, v);
-            float d[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = c0 + j;
-                d[j] = 0.f;
-                if (col < g.N) {
-                    const float z = v[j] + g.bias[col];
-                    const float p = expf(z - mx) * inv;
-                    const float lp = z - lse;
-                    if (p > 0.f)
-                        ent -= p * lp;
-                    if (in && g.probs)
-                        g.probs[(size_t)row * g.ldp + col] = p;
-                    if (g.target) {
-                        const float t = in ? g.target[(size_t)row * g.ldt + col] : 0.f;
-                        if (in) {
-                            ce -= t * lp;
-                            d[j] = (p - t) * g.inv_m;
-                        }
-                    }
-                }
-            }
+        // column blocks of 64: targets in, probabilities or gradients out, via the tile
+        for (int cb0 = 0; cb0 < g.BN; cb0 += 64) {
+            const int ncol = min(64, g.N - cb0);
+            __syncthreads();  // the previous block's readers of the tile are done
             if (g.target) {
-                if (in && g.out_bf16) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < g.BN)
-                            g.out_bf16[(size_t)row * g.ld_out + c0 + j] = __float2bfloat16_rn(d[j]);
+                for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
+                    const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
+                    T[rr * kTP + cc] = (grow < g.M && cc < ncol) ? g.target[(size_t)grow * g.ldt + cb0 + cc] : 0.f;
                 }
+                __syncthreads();
+            }
+            for (int c0 = cb0; c0 < cb0 + 64 && c0 < g.BN; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tw + c0, v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float s = warp_sum(d[j]);
-                    if (lane == 0 && c0 + j < 256)
-                        part[warp * 256 + c0 + j] = s;
+                    const int col = c0 + j, tc_ = col - cb0;
+                    float out = 0.f;
+                    if (col < g.N) {
+                        const float z = v[j] + g.bias[col];
+                        const float p = expf(z - mx) * inv;
+                        const float lp = z - lse;
+                        if (p > 0.f)
+                            ent -= p * lp;
+                        out = p;
+                        if (g.target && g.probs && in)
+                            g.probs[(size_t)row * g.ldp + col] = p;
+                        if (g.target) {
+                            const float t = T[r * kTP + tc_];
+                            out = 0.f;
+                            if (in) {
+                                ce -= t * lp;
+                                out = (p - t) * g.inv_m;
+                            }
+                        }
+                    }
+                    T[r * kTP + tc_] = in ? out : 0.f;
+                }
+            }
+            __syncthreads();
+            if (g.target) {
+                // column sums of the gradient (bias gradient partials)
+                for (int c = threadIdx.x; c < 64; c += blockDim.x) {
+                    float s2 = 0.f;
+                    for (int rr = 0; rr < kBM; ++rr)
+                        s2 += T[rr * kTP + c];
+                    if (cb0 + c < 256)
+                        part[cb0 + c] = s2;
+                }
+                if (g.out_bf16)
+                    for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
+                        const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
+                        if (grow < g.M && cb0 + cc < g.BN)
+                            g.out_bf16[(size_t)grow * g.ld_out + cb0 + cc] = __float2bfloat16_rn(T[rr * kTP + cc]);
+                    }
+            } else if (g.probs) {
+                for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
+                    const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
+                    if (grow < g.M && cc < ncol)
+                        g.probs[(size_t)grow * g.ldp + cb0 + cc] = T[rr * kTP + cc];
                 }
             }
         }
         if (in && g.score)
             g.score[row] = ent;
         if (g.target && g.loss) {
-            const float s = warp_sum(in ? ce : 0.f);
+            const float s2 = warp_sum(in ? ce : 0.f);
             __shared__ float lw[4];
             if (lane == 0)
-                lw[warp] = s;
+                lw[warp] = s2;
             __syncthreads();
             if (threadIdx.x == 0)
                 g.loss[blockIdx.x] = (lw[0] + lw[1]) + (lw[2] + lw[3]);
         }
     } else {
-        for (int c0 = 0; c0 < g.BN; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tw + c0, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = c0 + j;
-                float x = v[j];
-                if (col >= g.N || !in) {
-                    x = 0.f;
-                } else {
-                    if (g.bias)
-                        x += g.bias[col];
-                    if constexpr (EPI == EPI_BIAS_ACT) {
-                        if (g.relu)
-                            x = fmaxf(x, 0.f);
-                    }
-                    if constexpr (EPI == EPI_MASK) {
-                        const float mk = __bfloat162float(g.mask[(size_t)row * g.ldm + col]);
-                        x = (mk > 0.f) ? x : 0.f;
-                    }
-                }
-                v[j] = x;
-            }
-            if (in) {
-                if constexpr (EPI == EPI_F32) {
-                    float *o = g.out_f32 + (g.ksplit > 1 ? (size_t)blockIdx.y * (size_t)g.split_stride : 0);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < g.N)
-                            o[(size_t)row * g.ld_out32 + c0 + j] = v[j];
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < g.N)
-                            g.out_bf16[(size_t)row * g.ld_out + c0 + j] = __float2bfloat16_rn(v[j]);
-                }
-            }
+        float *o32 = nullptr;
+        if constexpr (EPI == EPI_F32)
+            o32 = g.out_f32 + (g.ksplit > 1 ? (size_t)blockIdx.y * (size_t)g.split_stride : 0);
+        for (int cb0 = 0; cb0 < g.BN; cb0 += 64) {
+            const int ncol = min(64, g.N - cb0);
+            __syncthreads();  // the previous block's readers of the tile are done
             if constexpr (EPI == EPI_MASK) {
-                if (g.colsum) {
+                for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
+                    const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
+                    Mk[rr * 130 + cc] = (grow < g.M && cc < ncol)
+                                            ? __bfloat16_as_ushort(g.mask[(size_t)grow * g.ldm + cb0 + cc])
+                                            : (uint16_t)0;
+                }
+                __syncthreads();
+            }
+            for (int c0 = cb0; c0 < cb0 + 64 && c0 < g.BN; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tw + c0, v);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float s = warp_sum(v[j]);
-                        if (lane == 0)
-                            part[warp * 256 + c0 + j] = s;
+                for (int j = 0; j < 16; ++j) {
+                    const int col = c0 + j;
+                    float x = v[j];
+                    if (col >= g.N || !in) {
+                        x = 0.f;
+                    } else {
+                        if (g.bias)
+                            x += g.bias[col];
+                        if constexpr (EPI == EPI_BIAS_ACT) {
+                            if (g.relu)
+                                x = fmaxf(x, 0.f);
+                        }
+                        if constexpr (EPI == EPI_MASK) {
+                            const float mk = __bfloat162float(__ushort_as_bfloat16(Mk[r * 130 + (col - cb0)]));
+                            x = (mk > 0.f) ? x : 0.f;
+                        }
                     }
+                    T[r * kTP + (col - cb0)] = x;
+                }
+            }
+            __syncthreads();
+            if constexpr (EPI == EPI_MASK) {
+                if (g.colsum)
+                    for (int c = threadIdx.x; c < 64; c += blockDim.x) {
+                        float s2 = 0.f;
+                        for (int rr = 0; rr < kBM; ++rr)
+                            s2 += T[rr * kTP + c];
+                        part[cb0 + c] = s2;
+                    }
+            }
+            for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
+                const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
+                if (grow < g.M && cc < ncol) {
+                    if constexpr (EPI == EPI_F32)
+                        o32[(size_t)grow * g.ld_out32 + cb0 + cc] = T[rr * kTP + cc];
+                    else
+                        g.out_bf16[(size_t)grow * g.ld_out + cb0 + cc] = __float2bfloat16_rn(T[rr * kTP + cc]);
                 }
             }
         }
     }
 
     if ((EPI == EPI_MASK || EPI == EPI_SOFTMAX) && g.colsum) {
-        // deterministic: per-CTA partial row, summed in a fixed order later
+        // deterministic: per-CTA column sums (fixed row order), summed across
+        // CTAs in a fixed order later
         __syncthreads();
         for (int c = threadIdx.x; c < g.N; c += blockDim.x)
-            g.colsum[(size_t)blockIdx.x * 256 + c] = (part[c] + part[256 + c]) + (part[512 + c] + part[768 + c]);
+            g.colsum[(size_t)blockIdx.x * 256 + c] = part[c];
     }
     tc::tc_fence_before();
     __syncthreads();
