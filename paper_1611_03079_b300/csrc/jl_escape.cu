@@ -739,6 +739,335 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
 }
 
 // ---------------------------------------------------------------------------
+// Compacting tile kernel (binary32).
+//
+// The static kernel's two losses on low-count frames are per-pixel
+// instructions and warp divergence: a warp runs as long as the slowest of its
+// 32 pixels while finished lanes idle.  Here each warp walks the same 8 x 4
+// patches as the static kernel, but a patch whose live lanes have dropped to
+// `T` or fewer (checked after the first 16 steps and after every super-block)
+// parks them: the live lanes write their
+// state (Z, C, n, pixel, frame) to a ring of 64 entries owned by the warp in
+// shared memory, and the warp moves on.  Once 32 parked pixels have
+// accumulated the warp resumes them together as one full batch (which may park
+// its own stragglers again).  At the end the warp merges what is left into its
+// last batches.  Parked pixels continue from exactly where they stopped, so the
+// arithmetic of every pixel is the same sequence of steps as the oracle's.
+//
+// A patch runs its first 16 steps in blocks of four, then super-blocks of
+// four blocks of S2 steps, with the monotone blocked test of `escape_blocked`
+// (the count is n + the number of passed tests in the block whose last test
+// failed; only that last test value is formed on the way).  A lane that cannot
+// run a whole super-block before its limit finishes with `escape_from` (blocks
+// of four, then exact single steps).
+// ---------------------------------------------------------------------------
+static constexpr int kQCap = 64;  // parked pixels per warp (power of two)
+
+struct ParkRing {
+    float x[kQCap], y[kQCap], cr[kQCap], ci[kQCap];
+    int32_t n[kQCap], f[kQCap];
+    uint32_t p[kQCap];
+};
+
+// Count of a pixel whose tests 0..n-1 passed, from Z_n = (x, y).
+__device__ __forceinline__ int escape_from(float x, float y, float cr, float ci, int n, int max_iter)
+{
+    for (; n + 4 <= max_iter; n += 4) {
+        float r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float x2 = __fmul_rn(x, x);
+            const float y2 = __fmul_rn(y, y);
+            r[u] = __fadd_rn(x2, y2);
+            const float t = __fmul_rn(__fadd_rn(x, x), y);
+            y = __fadd_rn(t, ci);
+            x = __fadd_rn(__fsub_rn(x2, y2), cr);
+        }
+        if (!(r[3] <= 4.0f))
+            return n + (r[0] <= 4.0f) + (r[1] <= 4.0f) + (r[2] <= 4.0f);
+    }
+    return exact_from(x, y, cr, ci, n, max_iter);
+}
+
+// One binary32 step of Z <- Z^2 + C, returning the test value x^2 + y^2 of Z.
+__device__ __forceinline__ float step32(float &x, float &y, float cr, float ci)
+{
+    const float x2 = __fmul_rn(x, x);
+    const float y2 = __fmul_rn(y, y);
+    const float r = __fadd_rn(x2, y2);
+    const float t = __fmul_rn(__fadd_rn(x, x), y);
+    y = __fadd_rn(t, ci);
+    x = __fadd_rn(__fsub_rn(x2, y2), cr);
+    return r;
+}
+
+// Four blocks of S steps each (4 S steps) from Z_n with the monotone blocked
+// test.  Returns the count of a pixel whose test failed in one of the blocks,
+// else -1 (Z_{n+4S} is then in x, y).  Only the last test value of a block is
+// formed on the way; the others (x2 + y2 of the earlier steps) are formed on
+// the exit path from the squares kept in registers.
+template <int S>
+__device__ __forceinline__ int superblock(float &x, float &y, float cr, float ci, int n)
+{
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float x2s[S], y2s[S];
+#pragma unroll
+        for (int u = 0; u < S; ++u) {
+            const float x2 = __fmul_rn(x, x);
+            const float y2 = __fmul_rn(y, y);
+            x2s[u] = x2;
+            y2s[u] = y2;
+            const float t = __fmul_rn(__fadd_rn(x, x), y);
+            y = __fadd_rn(t, ci);
+            x = __fadd_rn(__fsub_rn(x2, y2), cr);
+        }
+        if (!(__fadd_rn(x2s[S - 1], y2s[S - 1]) <= 4.0f)) {
+            int passed = 0;
+#pragma unroll
+            for (int u = 0; u < S - 1; ++u)
+                passed += (__fadd_rn(x2s[u], y2s[u]) <= 4.0f) ? 1 : 0;
+            return n + S * b + passed;
+        }
+    }
+    return -1;
+}
+
+template <bool BATCH>
+__device__ __forceinline__ void store_result(const EscapeArgs &a, const uint32_t *pal, uint32_t *hbins, int fr,
+                                             uint32_t p, int count, int mi, unsigned lt_mask)
+{
+    const Frame &F = BATCH ? a.frames[fr] : a.single;
+    if (F.counts) {
+        if (F.count_type == JL_COUNT_U8)
+            F.counts[p] = (uint8_t)count;
+        else
+            reinterpret_cast<uint16_t *>(F.counts)[p] = (uint16_t)count;
+    }
+    if (F.rgba)
+        F.rgba[p] = pal[colour_index((uint32_t)count, (uint32_t)mi, F.colour_magic)];
+    if (F.hist_bins) {
+        if (!BATCH && a.hist_smem) {
+            atomicAdd(&hbins[count], 1u);
+        } else {
+            const unsigned act = __activemask();
+            const unsigned long long key = ((unsigned long long)(unsigned)fr << 32) | (unsigned)count;
+            const unsigned grp = __match_any_sync(act, key);
+            if ((grp & lt_mask) == 0)
+                atomicAdd(&F.hist_bins[count], (unsigned)__popc(grp));
+        }
+    }
+}
+
+// S2: steps per block after the first 16 steps (super-blocks of 4 S2 steps).
+template <bool BATCH, int S2>
+__global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_constant__ EscapeArgs a, int T)
+{
+    __shared__ uint32_t pal[256];
+    __shared__ ParkRing rings[8];
+    extern __shared__ uint32_t hbins[];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        pal[t] = a.palette[t];
+    const int nb = (!BATCH && a.hist_smem) ? a.single.max_iter + 1 : 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x)
+        hbins[t] = 0;
+    __syncthreads();
+
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    ParkRing &R = rings[w];
+    const int dx = (w & 3) * 8 + (lane & 7);
+    const int dy = (w >> 2) * 4 + (lane >> 3);
+    const long long t_start = clock64();
+    int qh = 0, qn = 0;  // ring head and fill (warp-uniform)
+    bool stop = false;
+
+    // Park the live lanes (state Z_n, C, n, pixel, frame) at the ring's tail.
+    auto park = [&](unsigned m, bool &live, float x, float y, float cr, float ci, int n, int fr, uint32_t p) {
+        if (live) {
+            const int s = (qh + qn + __popc(m & lt_mask)) & (kQCap - 1);
+            R.x[s] = x;
+            R.y[s] = y;
+            R.cr[s] = cr;
+            R.ci[s] = ci;
+            R.n[s] = n;
+            R.f[s] = fr;
+            R.p[s] = p;
+            live = false;
+        }
+        qn += __popc(m);
+        __syncwarp();
+    };
+
+    // Resume up to 32 parked pixels and run them until they finish or, when
+    // few are left, park them again (`merge_only`: the tiles are done, park
+    // only to merge with pixels already in the ring).
+    auto resume = [&](bool merge_only) {
+        float x = 0.f, y = 0.f, cr = 0.f, ci = 0.f;
+        int n = 0, fr = 0, mi = 0, count = 0;
+        uint32_t p = 0;
+        bool live = false, fin = false;
+        const int take = min(qn, 32);
+        if (lane < take) {
+            const int s = (qh + lane) & (kQCap - 1);
+            x = R.x[s];
+            y = R.y[s];
+            cr = R.cr[s];
+            ci = R.ci[s];
+            n = R.n[s];
+            fr = R.f[s];
+            p = R.p[s];
+            live = true;
+            mi = (BATCH ? a.frames[fr] : a.single).max_iter;
+        }
+        qh = (qh + take) & (kQCap - 1);
+        qn -= take;
+        __syncwarp();
+        for (int it = 0;; ++it) {
+            if (live && n + 4 * S2 > mi) {
+                count = escape_from(x, y, cr, ci, n, mi);
+                live = false;
+                fin = true;
+            }
+            const unsigned m = __ballot_sync(FULL, live);
+            if (m == 0)
+                break;
+            const int nl = __popc(m);
+            if (it > 0 && nl <= T && qn + nl <= kQCap && (!merge_only || qn > 0)) {
+                park(m, live, x, y, cr, ci, n, fr, p);
+                break;
+            }
+            if (live) {
+                const int c = superblock<S2>(x, y, cr, ci, n);
+                if (c < 0) {
+                    n += 4 * S2;
+                } else {
+                    count = c;
+                    live = false;
+                    fin = true;
+                }
+            }
+        }
+        if (fin)
+            store_result<BATCH>(a, pal, hbins, fr, p, count, mi, lt_mask);
+    };
+
+    for (long long tile = blockIdx.x; tile < a.total_tiles && !stop; tile += gridDim.x) {
+        if (a.cycle_budget > 0 && __any_sync(FULL, (clock64() - t_start) > a.cycle_budget)) {
+            if (lane == 0 && a.status)
+                atomicExch(a.status, (int)JL_ETIMEOUT);
+            stop = true;
+            break;
+        }
+        int fr = 0;
+        if constexpr (BATCH)
+            fr = a.tile_frame[tile];
+        const Frame &F = BATCH ? a.frames[fr] : a.single;
+        const int W = F.W, H = F.H, mi = F.max_iter;
+        const bool julia = F.mode == JL_JULIA;
+        const bool safe = F.safe != 0;
+        const float fcr = F.cr32, fci = F.ci32;
+        const float *ys = static_cast<const float *>(F.ys);
+        const uint32_t lt = (uint32_t)(tile - F.tile_begin);
+        const uint32_t ty = (uint32_t)(((uint64_t)lt * F.tiles_x_magic) >> 40);
+        const uint32_t tx = lt - ty * (uint32_t)F.tiles_x;
+        const int i = (int)tx * 32 + dx;
+        const float xv = i < W ? static_cast<const float *>(F.xs)[i] : 0.f;
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            if (qn >= 32)
+                resume(false);
+            const int j = (int)ty * 32 + dy + 8 * q;
+            const bool valid = i < W && j < H;
+            if (!__any_sync(FULL, valid))
+                break;  // rows beyond the frame: so are the later patches of this tile
+            const float yv = valid ? ys[j] : 0.f;
+            float x, y, cr, ci;
+            if (julia) {
+                x = xv;
+                y = yv;
+                cr = fcr;
+                ci = fci;
+            } else {
+                x = 0.f;
+                y = 0.f;
+                cr = xv;
+                ci = yv;
+            }
+            bool live = valid, fin = false;
+            int count = 0;
+            const uint32_t p = (uint32_t)j * (uint32_t)W + (uint32_t)i;
+            if (valid && !(julia ? safe : !in_unsafe_band(cr, ci))) {
+                count = exact_from(x, y, cr, ci, 0, mi);
+                live = false;
+                fin = true;
+            }
+            if (mi < 16) {
+                if (live) {
+                    count = escape_from(x, y, cr, ci, 0, mi);
+                    live = false;
+                    fin = true;
+                }
+            } else {
+                // first 16 steps in blocks of 4 (most pixels leave here), then
+                // super-blocks of 32 steps in blocks of 8; n is the same for
+                // every live lane of the patch
+                if (live) {
+                    const int c = superblock<4>(x, y, cr, ci, 0);
+                    if (c >= 0) {
+                        count = c;
+                        live = false;
+                        fin = true;
+                    }
+                }
+                int n = 16;
+                for (;;) {
+                    const unsigned m = __ballot_sync(FULL, live);
+                    if (m == 0)
+                        break;
+                    const int nl = __popc(m);
+                    if (nl <= T && qn + nl <= kQCap) {
+                        park(m, live, x, y, cr, ci, n, fr, p);
+                        break;
+                    }
+                    if (n + 4 * S2 > mi) {
+                        if (live) {
+                            count = escape_from(x, y, cr, ci, n, mi);
+                            live = false;
+                            fin = true;
+                        }
+                        break;
+                    }
+                    if (live) {
+                        const int c = superblock<S2>(x, y, cr, ci, n);
+                        if (c >= 0) {
+                            count = c;
+                            live = false;
+                            fin = true;
+                        }
+                    }
+                    n += 4 * S2;
+                }
+            }
+            if (fin)
+                store_result<BATCH>(a, pal, hbins, fr, p, count, mi, lt_mask);
+        }
+    }
+    // the tiles are done: finish the parked pixels, merging partial batches
+    while (qn > 0 && !stop)
+        resume(true);
+
+    if (nb) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            const uint32_t v = hbins[t];
+            if (v)
+                atomicAdd(&a.single.hist_bins[t], v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 int device_sm_count()
@@ -822,6 +1151,9 @@ bool variant_supported(int precision, int ppt, int unroll)
 {
     if (ppt == 0 && unroll == 0 && (precision == JL_FP32 || precision == JL_FP64))
         return true;
+    // (0, T): the compacting tile kernel (binary32), parking threshold T lanes
+    if (ppt == 0 && precision == JL_FP32 && (unroll == 8 || unroll == 16))
+        return true;
 #define JL_CHECK(T, P, UU) \
     if (((sizeof(T) == 8) == (precision == JL_FP64)) && ppt == P && unroll == UU) return true;
     JL_VARIANTS_F32(JL_CHECK)
@@ -839,6 +1171,14 @@ int variant_list(int precision, int32_t *pairs, int cap)
         pairs[1] = 0;
     }
     ++n;
+    if (precision == JL_FP32)
+        for (int t : {8, 16}) {
+            if (pairs && n < cap) {
+                pairs[2 * n] = 0;
+                pairs[2 * n + 1] = t;
+            }
+            ++n;
+        }
 #define JL_LIST(T, P, UU)                                            \
     if ((sizeof(T) == 8) == (precision == JL_FP64)) {                \
         if (pairs && n < cap) { pairs[2 * n] = P; pairs[2 * n + 1] = UU; } \
@@ -876,11 +1216,38 @@ static cudaError_t launch_static(const EscapeArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+static cudaError_t launch_compact(const EscapeArgs &a, int T, cudaStream_t st)
+{
+    size_t smem = 0;
+    if (a.hist_smem && !a.frames)
+        smem = (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
+    auto kern = a.frames ? escape_compact_kernel<true, 8> : escape_compact_kernel<false, 8>;
+    if (smem > 16 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (a.total_tiles < 1)
+        return cudaErrorInvalidValue;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess)
+        return e;
+    const int sms = device_sm_count();
+    long long grid = (long long)(sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
+    if (grid > a.total_tiles)
+        grid = a.total_tiles;
+    kern<<<(unsigned)grid, 256, smem, st>>>(a, T);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_escape(const EscapeArgs &a_in, int precision, const Variant &v, int num_sms, cudaStream_t st)
 {
     EscapeArgs a = a_in;
     a.emu_ratio = (precision == JL_FP64 && v.emu > 1) ? v.emu : 1;
     a.num_sms = num_sms;
+    if (v.ppt == 0 && v.unroll > 0 && precision == JL_FP32)
+        return launch_compact(a, v.unroll, st);
     if (v.ppt == 0)
         return precision == JL_FP64 ? launch_static<double>(a, st) : launch_static<float>(a, st);
     size_t smem = 256 * sizeof(uint32_t);

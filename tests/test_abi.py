@@ -100,7 +100,10 @@ def test_variant_list(L):
         assert L.jl_variant_list(prec, buf, n) == n
         pairs = [(buf[2 * i], buf[2 * i + 1]) for i in range(n)]
         assert pairs[0] == (0, 0)  # the static tile kernel
-        assert all(p >= 1 and u >= 1 for p, u in pairs[1:])
+        # (0, T): the compacting tile kernel (binary32 only), parking threshold T
+        compact = [u for p, u in pairs[1:] if p == 0]
+        assert all(1 <= u <= 32 for u in compact) and (prec == 0 or not compact)
+        assert all(p >= 1 and u >= 1 for p, u in pairs[1:] if p != 0)
     assert L.jl_variant_list(5, None, 0) == -1
 
 

@@ -182,3 +182,24 @@ def test_mandelbrot_deep_zoom_fig3(cuda):
     assert 0 < sum(precs) < len(precs)
     _check_batch(b, frames, precs=precs)
     b.close()
+
+
+@pytest.mark.parametrize("T", [8, 16])
+def test_compact_variant_batch(cuda, T):
+    """The compacting tile kernel in a batch plan: parked pixels of different
+    frames (limits, modes, count types, histograms) share resumed batches."""
+    frames = []
+    for i, f in enumerate(wl.random_views(24, seed=800 + T)):
+        f = dict(f)
+        f["precision"] = 0
+        f["count_type"] = "u8" if (i % 3 == 0 and f["max_iter"] <= 255) else "u16"
+        f["hist"] = i % 2 == 0
+        frames.append(f)
+    frames.append(dict(c=complex(-0.7269, 0.1889), rect=(-1.6, 1.6, -1.6, 1.6), W=300, H=257, max_iter=1000,
+                       mode=0, precision=0, count_type="u16", hist=True))
+    frames.append(dict(c=None, rect=(-2.5, 1.0, -1.75, 1.75), W=257, H=300, max_iter=700, mode=1, precision=0,
+                       count_type="u16", hist=False))
+    b = jl.Batch(frames, palette=PAL, variants={"fp32": (0, T, 256)})
+    b.launch()
+    _check_batch(b, frames)
+    b.close()

@@ -244,3 +244,28 @@ def test_integer_doubling_is_exact(cuda):
     jl._lib.check(jl._lib.lib().jl_selftest_double(z.data_ptr(), w.data_ptr(), 1, None))
     torch.cuda.synchronize()
     assert torch.isnan(w).all()
+
+
+@pytest.mark.parametrize("T", [8, 16])
+def test_compact_kernel_frames(cuda, T):
+    """The compacting tile kernel (binary32; stragglers parked in per-warp
+    rings and resumed in full batches): bit-exact counts, colours and
+    histograms on frames where many pixels are parked and resumed several
+    times (limits up to 65535), on the edge cases and on ragged views."""
+    v = (0, T, 256, 0)
+    heavy = [dict(c=complex(-0.7269, 0.1889), rect=(-1.6, 1.6, -1.6, 1.6), W=517, H=389, max_iter=1000, mode=0,
+                  precision=0),
+             dict(c=complex(-0.4, 0.6), rect=(-1.6, 1.6, -1.6, 1.6), W=256, H=256, max_iter=5000, mode=0,
+                  precision=0),
+             dict(c=None, rect=(-2.5, 1.0, -1.75, 1.75), W=401, H=333, max_iter=1000, mode=1, precision=0),
+             dict(c=None, rect=(-0.7530, -0.7490, 0.0990, 0.1030), W=64, H=40, max_iter=65535, mode=1,
+                  precision=0)]
+    for f in heavy:
+        check_frame(f, variant=v, hist=f["max_iter"] <= 5000)
+    for f in EDGE:
+        if f["precision"] == 0:
+            check_frame(f, variant=v)
+    for f in wl.random_views(12, seed=300 + T):
+        f = dict(f)
+        f["precision"] = 0
+        check_frame(f, variant=v)
