@@ -658,20 +658,33 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
         hbins[t] = 0;
     __syncthreads();
 
-    // tile of 32 x 32 pixels per CTA step; warp w covers an 8 x 4 patch and
-    // each thread four pixels of one column, 8 rows apart
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int dx = (w & 3) * 8 + (lane & 7);
-    const int dy = (w >> 2) * 4 + (lane >> 3);
+    // Tiles of 32 x 32 pixels in eight 8 x 16 parts; a warp takes parts one at
+    // a time from the launch's counter (the next index fetched a part ahead).
+    // In part k the warp covers 8 x 4 patches and each thread four pixels of
+    // one column, 8 rows apart.
+    const int lane = threadIdx.x & 31;
     const long long t_start = clock64();
+    const long long total_units = a.total_tiles * 8;
+    unsigned long long next_u = 0;
+    if (lane == 0)
+        next_u = atomicAdd(a.chunk_counter, 1ull);
 
-    for (long long tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x) {
+    for (;;) {
+        const long long unit = (long long)__shfl_sync(FULL, next_u, 0);
+        if (unit >= total_units)
+            break;
         // budget check, uniform across the warp (the loop below has warp collectives)
         if (a.cycle_budget > 0 && __any_sync(FULL, (clock64() - t_start) > a.cycle_budget)) {
             if (lane == 0 && a.status)
                 atomicExch(a.status, (int)JL_ETIMEOUT);
             break;
         }
+        if (lane == 0)
+            next_u = atomicAdd(a.chunk_counter, 1ull);
+        const long long tile = unit >> 3;
+        const int part = (int)(unit & 7);
+        const int dx = (part & 3) * 8 + (lane & 7);
+        const int dy = (part >> 2) * 4 + (lane >> 3);
         int f = 0;
         if constexpr (BATCH)
             f = a.tile_frame[tile];
@@ -833,6 +846,51 @@ __device__ __forceinline__ int superblock(float &x, float &y, float cr, float ci
     return -1;
 }
 
+// Output fields of the frame of a tile, held in registers for its patches
+// (loads from the frame table could not be hoisted past the output stores).
+struct TileOut {
+    uint8_t *counts;
+    uint32_t *rgba;
+    uint32_t *bins;
+    uint64_t magic;  // colour reciprocal (40-bit, exact for any limit)
+    uint32_t m32;    // floor(2^32 / max_iter) + 1: exact count*255/max_iter for max_iter <= 4096
+    int mi;
+    bool u8, small;
+};
+
+__device__ __forceinline__ uint32_t tile_colour(const TileOut &o, int count)
+{
+    if (count >= o.mi)
+        return 255u;
+    return o.small ? __umulhi((uint32_t)count * 255u, o.m32)
+                   : (uint32_t)(((uint64_t)((uint32_t)count * 255u) * o.magic) >> 40);
+}
+
+template <bool BATCH>
+__device__ __forceinline__ void store_tile(const EscapeArgs &a, const TileOut &o, const uint32_t *pal,
+                                           uint32_t *hbins, int fr, uint32_t p, int count, unsigned lt_mask)
+{
+    if (o.counts) {
+        if (o.u8)
+            o.counts[p] = (uint8_t)count;
+        else
+            reinterpret_cast<uint16_t *>(o.counts)[p] = (uint16_t)count;
+    }
+    if (o.rgba)
+        o.rgba[p] = pal[tile_colour(o, count)];
+    if (o.bins) {
+        if (!BATCH && a.hist_smem) {
+            atomicAdd(&hbins[count], 1u);
+        } else {
+            const unsigned act = __activemask();
+            const unsigned long long key = ((unsigned long long)(unsigned)fr << 32) | (unsigned)count;
+            const unsigned grp = __match_any_sync(act, key);
+            if ((grp & lt_mask) == 0)
+                atomicAdd(&o.bins[count], (unsigned)__popc(grp));
+        }
+    }
+}
+
 template <bool BATCH>
 __device__ __forceinline__ void store_result(const EscapeArgs &a, const uint32_t *pal, uint32_t *hbins, int fr,
                                              uint32_t p, int count, int mi, unsigned lt_mask)
@@ -876,8 +934,6 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     ParkRing &R = rings[w];
-    const int dx = (w & 3) * 8 + (lane & 7);
-    const int dy = (w >> 2) * 4 + (lane >> 3);
     const long long t_start = clock64();
     int qh = 0, qn = 0;  // ring head and fill (warp-uniform)
     bool stop = false;
@@ -952,13 +1008,29 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
             store_result<BATCH>(a, pal, hbins, fr, p, count, mi, lt_mask);
     };
 
-    for (long long tile = blockIdx.x; tile < a.total_tiles && !stop; tile += gridDim.x) {
+    // Work units: the eight 8 x 16 parts of every 32 x 32 tile (part k: columns
+    // (k % 4) * 8 .. +7, rows (k / 4) * 4 + {0..3} + 8 q), taken one at a time
+    // from the launch's counter; the next unit's index is fetched a unit ahead.
+    const long long total_units = a.total_tiles * 8;
+    unsigned long long next_u = 0;
+    if (lane == 0)
+        next_u = atomicAdd(a.chunk_counter, 1ull);
+    for (;;) {
+        const long long unit = (long long)__shfl_sync(FULL, next_u, 0);
+        if (unit >= total_units)
+            break;
         if (a.cycle_budget > 0 && __any_sync(FULL, (clock64() - t_start) > a.cycle_budget)) {
             if (lane == 0 && a.status)
                 atomicExch(a.status, (int)JL_ETIMEOUT);
             stop = true;
             break;
         }
+        if (lane == 0)
+            next_u = atomicAdd(a.chunk_counter, 1ull);
+        const long long tile = unit >> 3;
+        const int part = (int)(unit & 7);
+        const int dx = (part & 3) * 8 + (lane & 7);
+        const int dy = (part >> 2) * 4 + (lane >> 3);
         int fr = 0;
         if constexpr (BATCH)
             fr = a.tile_frame[tile];
@@ -968,11 +1040,23 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
         const bool safe = F.safe != 0;
         const float fcr = F.cr32, fci = F.ci32;
         const float *ys = static_cast<const float *>(F.ys);
+        TileOut o;
+        o.counts = F.counts;
+        o.rgba = F.rgba;
+        o.bins = F.hist_bins;
+        o.magic = F.colour_magic;
+        o.m32 = (uint32_t)((o.magic - 1u) >> 8) + 1u;
+        o.mi = mi;
+        o.u8 = F.count_type == JL_COUNT_U8;
+        o.small = mi <= 4096;
         const uint32_t lt = (uint32_t)(tile - F.tile_begin);
         const uint32_t ty = (uint32_t)(((uint64_t)lt * F.tiles_x_magic) >> 40);
         const uint32_t tx = lt - ty * (uint32_t)F.tiles_x;
         const int i = (int)tx * 32 + dx;
         const float xv = i < W ? static_cast<const float *>(F.xs)[i] : 0.f;
+        // Julia: Z_0 = pixel, C = frame constant; Mandelbrot: Z_0 = 0, C = pixel
+        const float x0 = julia ? xv : 0.f;
+        const float c0r = julia ? fcr : xv;
 #pragma unroll 1
         for (int q = 0; q < 4; ++q) {
             if (qn >= 32)
@@ -982,22 +1066,15 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
             if (!__any_sync(FULL, valid))
                 break;  // rows beyond the frame: so are the later patches of this tile
             const float yv = valid ? ys[j] : 0.f;
-            float x, y, cr, ci;
-            if (julia) {
-                x = xv;
-                y = yv;
-                cr = fcr;
-                ci = fci;
-            } else {
-                x = 0.f;
-                y = 0.f;
-                cr = xv;
-                ci = yv;
-            }
+            float x = x0, y = julia ? yv : 0.f;
+            const float cr = c0r, ci = julia ? fci : yv;
             bool live = valid, fin = false;
             int count = 0;
             const uint32_t p = (uint32_t)j * (uint32_t)W + (uint32_t)i;
-            if (valid && !(julia ? safe : !in_unsafe_band(cr, ci))) {
+            bool mono = safe;
+            if (!julia)
+                mono = !in_unsafe_band(cr, ci);
+            if (valid && !mono) {
                 count = exact_from(x, y, cr, ci, 0, mi);
                 live = false;
                 fin = true;
@@ -1050,7 +1127,7 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
                 }
             }
             if (fin)
-                store_result<BATCH>(a, pal, hbins, fr, p, count, mi, lt_mask);
+                store_tile<BATCH>(a, o, pal, hbins, fr, p, count, lt_mask);
         }
     }
     // the tiles are done: finish the parked pixels, merging partial batches
