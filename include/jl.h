@@ -124,8 +124,11 @@ int jl_render_to_host(double cr, double ci, jl_rect rect, int32_t width, int32_t
  * tests): ppt independent pixels per thread, unroll steps between service
  * points, threads per CTA (multiple of 32, 32..256), ctas_per_sm (0 = the
  * occupancy maximum).  ppt = unroll = 0 selects the static kernel (one pixel
- * per thread, 32 x 8 pixel CTAs, exact test every step; threads and
- * ctas_per_sm are then ignored).  emu (binary64 with ppt > 0 only): 1 = all
+ * per thread, 32 x 32 pixel tiles taken by warps in 8 x 16 parts; threads and
+ * ctas_per_sm are then ignored).  ppt = 0 with unroll = T in 1..32 (binary32
+ * only) selects the compacting tile kernel: the static kernel's tiles, with a
+ * patch's live pixels parked in a per-warp ring once T or fewer of its 32
+ * are left and resumed later as full batches of 32.  emu (binary64 with ppt > 0 only): 1 = all
  * arithmetic on the hardware binary64 pipe; k > 1 = one warp group (4 warps)
  * in every k uses the hardware pipe and the others the bit-exact
  * integer-pipe binary64 arithmetic (see jl_selftest_f64), so both kinds of

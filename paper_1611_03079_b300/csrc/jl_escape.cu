@@ -1229,7 +1229,7 @@ bool variant_supported(int precision, int ppt, int unroll)
     if (ppt == 0 && unroll == 0 && (precision == JL_FP32 || precision == JL_FP64))
         return true;
     // (0, T): the compacting tile kernel (binary32), parking threshold T lanes
-    if (ppt == 0 && precision == JL_FP32 && (unroll == 8 || unroll == 16))
+    if (ppt == 0 && precision == JL_FP32 && unroll >= 1 && unroll <= 32)
         return true;
 #define JL_CHECK(T, P, UU) \
     if (((sizeof(T) == 8) == (precision == JL_FP64)) && ppt == P && unroll == UU) return true;
