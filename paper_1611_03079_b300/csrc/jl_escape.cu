@@ -665,12 +665,20 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
     const int lane = threadIdx.x & 31;
     const long long t_start = clock64();
     const long long total_units = a.total_tiles * 8;
+    const unsigned long long claim = (unsigned long long)a.claim;
     unsigned long long next_u = 0;
     if (lane == 0)
-        next_u = atomicAdd(a.chunk_counter, 1ull);
+        next_u = atomicAdd(a.chunk_counter, claim);
+    long long cur = 0, end = 0;
 
     for (;;) {
-        const long long unit = (long long)__shfl_sync(FULL, next_u, 0);
+        if (cur == end) {
+            cur = (long long)__shfl_sync(FULL, next_u, 0);
+            end = cur + (long long)claim;
+            if (lane == 0)
+                next_u = atomicAdd(a.chunk_counter, claim);
+        }
+        const long long unit = cur++;
         if (unit >= total_units)
             break;
         // budget check, uniform across the warp (the loop below has warp collectives)
@@ -679,8 +687,6 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
                 atomicExch(a.status, (int)JL_ETIMEOUT);
             break;
         }
-        if (lane == 0)
-            next_u = atomicAdd(a.chunk_counter, 1ull);
         const long long tile = unit >> 3;
         const int part = (int)(unit & 7);
         const int dx = (part & 3) * 8 + (lane & 7);
@@ -1012,11 +1018,19 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
     // (k % 4) * 8 .. +7, rows (k / 4) * 4 + {0..3} + 8 q), taken one at a time
     // from the launch's counter; the next unit's index is fetched a unit ahead.
     const long long total_units = a.total_tiles * 8;
+    const unsigned long long claim = (unsigned long long)a.claim;
     unsigned long long next_u = 0;
     if (lane == 0)
-        next_u = atomicAdd(a.chunk_counter, 1ull);
+        next_u = atomicAdd(a.chunk_counter, claim);
+    long long cur = 0, end = 0;
     for (;;) {
-        const long long unit = (long long)__shfl_sync(FULL, next_u, 0);
+        if (cur == end) {
+            cur = (long long)__shfl_sync(FULL, next_u, 0);
+            end = cur + (long long)claim;
+            if (lane == 0)
+                next_u = atomicAdd(a.chunk_counter, claim);
+        }
+        const long long unit = cur++;
         if (unit >= total_units)
             break;
         if (a.cycle_budget > 0 && __any_sync(FULL, (clock64() - t_start) > a.cycle_budget)) {
@@ -1025,8 +1039,6 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
             stop = true;
             break;
         }
-        if (lane == 0)
-            next_u = atomicAdd(a.chunk_counter, 1ull);
         const long long tile = unit >> 3;
         const int part = (int)(unit & 7);
         const int dx = (part & 3) * 8 + (lane & 7);
@@ -1267,6 +1279,19 @@ int variant_list(int precision, int32_t *pairs, int cap)
     return n;
 }
 
+// Tile parts a warp claims per increment of the launch counter.  One part at a
+// time balances best, but with thousands of parts per warp (large batches of
+// low-count frames) the one counter becomes a hot spot: then up to 8 parts
+// (one tile) per claim, keeping at least ~500 claims per warp.
+static int32_t tile_claim(long long total_tiles, long long grid)
+{
+    const long long per_warp = (total_tiles * 8) / (grid * 8 > 0 ? grid * 8 : 1);
+    int32_t c = 1;
+    while (c < 8 && per_warp >= 1024LL * c)
+        c *= 2;
+    return c;
+}
+
 template <typename T>
 static cudaError_t launch_static(const EscapeArgs &a, cudaStream_t st)
 {
@@ -1289,7 +1314,9 @@ static cudaError_t launch_static(const EscapeArgs &a, cudaStream_t st)
     long long grid = (long long)(sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
     if (grid > a.total_tiles)
         grid = a.total_tiles;
-    kern<<<(unsigned)grid, 256, smem, st>>>(a);
+    EscapeArgs b = a;
+    b.claim = tile_claim(a.total_tiles, grid);
+    kern<<<(unsigned)grid, 256, smem, st>>>(b);
     return cudaGetLastError();
 }
 
@@ -1314,7 +1341,9 @@ static cudaError_t launch_compact(const EscapeArgs &a, int T, cudaStream_t st)
     long long grid = (long long)(sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
     if (grid > a.total_tiles)
         grid = a.total_tiles;
-    kern<<<(unsigned)grid, 256, smem, st>>>(a, T);
+    EscapeArgs b = a;
+    b.claim = tile_claim(a.total_tiles, grid);
+    kern<<<(unsigned)grid, 256, smem, st>>>(b, T);
     return cudaGetLastError();
 }
 

@@ -56,6 +56,8 @@ struct EscapeArgs {
     unsigned long long *chunk_counter; // zeroed before the launch
     int32_t *status;                   // device status word (0 = ok), may be NULL
     long long cycle_budget;            // per-CTA clock64 budget; <= 0: unlimited
+    int32_t claim;                     // tile kernels: 8 x 16 parts per counter claim (set by the launcher)
+    int32_t pad_claim;
     uint32_t palette[256];
     Frame single;
 };
