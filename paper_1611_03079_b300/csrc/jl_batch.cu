@@ -242,6 +242,10 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             args[g].chunk_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 8 * g);
             args[g].status = reinterpret_cast<int32_t *>(b->ctl_dev + 16);
             args[g].cycle_budget = o.cycle_budget;
+            bool u16_rgba = !host[g].empty();
+            for (const Frame &F : host[g])
+                u16_rgba = u16_rgba && F.counts && F.count_type == JL_COUNT_U16 && F.rgba && !F.hist_bins;
+            args[g].out_mode = u16_rgba ? 1 : 0;
             memcpy(args[g].palette, pal, 1024);
         }
         const int sms = device_sm_count();

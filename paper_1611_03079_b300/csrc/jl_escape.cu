@@ -872,10 +872,16 @@ __device__ __forceinline__ uint32_t tile_colour(const TileOut &o, int count)
                    : (uint32_t)(((uint64_t)((uint32_t)count * 255u) * o.magic) >> 40);
 }
 
-template <bool BATCH>
+template <bool BATCH, int OUT>
 __device__ __forceinline__ void store_tile(const EscapeArgs &a, const TileOut &o, const uint32_t *pal,
                                            uint32_t *hbins, int fr, uint32_t p, int count, unsigned lt_mask)
 {
+    if constexpr (OUT == 1) {
+        // uint16 counts and RGBA8, no histogram: no per-frame tests
+        reinterpret_cast<uint16_t *>(o.counts)[p] = (uint16_t)count;
+        o.rgba[p] = pal[tile_colour(o, count)];
+        return;
+    }
     if (o.counts) {
         if (o.u8)
             o.counts[p] = (uint8_t)count;
@@ -897,11 +903,16 @@ __device__ __forceinline__ void store_tile(const EscapeArgs &a, const TileOut &o
     }
 }
 
-template <bool BATCH>
+template <bool BATCH, int OUT>
 __device__ __forceinline__ void store_result(const EscapeArgs &a, const uint32_t *pal, uint32_t *hbins, int fr,
                                              uint32_t p, int count, int mi, unsigned lt_mask)
 {
     const Frame &F = BATCH ? a.frames[fr] : a.single;
+    if constexpr (OUT == 1) {
+        reinterpret_cast<uint16_t *>(F.counts)[p] = (uint16_t)count;
+        F.rgba[p] = pal[colour_index((uint32_t)count, (uint32_t)mi, F.colour_magic)];
+        return;
+    }
     if (F.counts) {
         if (F.count_type == JL_COUNT_U8)
             F.counts[p] = (uint8_t)count;
@@ -924,8 +935,10 @@ __device__ __forceinline__ void store_result(const EscapeArgs &a, const uint32_t
 }
 
 // S2: steps per block after the first 16 steps (super-blocks of 4 S2 steps).
-template <bool BATCH, int S2>
-__global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_constant__ EscapeArgs a, int T)
+// OUT = 1: every frame of the launch has uint16 counts and RGBA8 and no
+// histogram (stores without per-frame tests); 0: any outputs.
+template <bool BATCH, int S2, int OUT>
+__global__ void __launch_bounds__(256, 4) escape_compact_kernel(const __grid_constant__ EscapeArgs a, int T)
 {
     __shared__ uint32_t pal[256];
     __shared__ ParkRing rings[8];
@@ -1011,7 +1024,7 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
             }
         }
         if (fin)
-            store_result<BATCH>(a, pal, hbins, fr, p, count, mi, lt_mask);
+            store_result<BATCH, OUT>(a, pal, hbins, fr, p, count, mi, lt_mask);
     };
 
     // Work units: the eight 8 x 16 parts of every 32 x 32 tile (part k: columns
@@ -1083,10 +1096,15 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
             bool live = valid, fin = false;
             int count = 0;
             const uint32_t p = (uint32_t)j * (uint32_t)W + (uint32_t)i;
-            bool mono = safe;
-            if (!julia)
-                mono = !in_unsafe_band(cr, ci);
-            if (valid && !mono) {
+            // pixels whose escape is not proven monotone: exact single steps
+            if (!julia) {
+                const bool unsafe = valid && in_unsafe_band(cr, ci);
+                if (__any_sync(FULL, unsafe) && unsafe) {
+                    count = exact_from(x, y, cr, ci, 0, mi);
+                    live = false;
+                    fin = true;
+                }
+            } else if (!safe && valid) {
                 count = exact_from(x, y, cr, ci, 0, mi);
                 live = false;
                 fin = true;
@@ -1139,7 +1157,7 @@ __global__ void __launch_bounds__(256) escape_compact_kernel(const __grid_consta
                 }
             }
             if (fin)
-                store_tile<BATCH>(a, o, pal, hbins, fr, p, count, lt_mask);
+                store_tile<BATCH, OUT>(a, o, pal, hbins, fr, p, count, lt_mask);
         }
     }
     // the tiles are done: finish the parked pixels, merging partial batches
@@ -1325,7 +1343,13 @@ static cudaError_t launch_compact(const EscapeArgs &a, int T, cudaStream_t st)
     size_t smem = 0;
     if (a.hist_smem && !a.frames)
         smem = (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
-    auto kern = a.frames ? escape_compact_kernel<true, 8> : escape_compact_kernel<false, 8>;
+    int out_mode = a.out_mode;
+    if (!a.frames) {
+        const Frame &F = a.single;
+        out_mode = (F.counts && F.count_type == JL_COUNT_U16 && F.rgba && !F.hist_bins) ? 1 : 0;
+    }
+    auto kern = a.frames ? (out_mode == 1 ? escape_compact_kernel<true, 8, 1> : escape_compact_kernel<true, 8, 0>)
+                         : (out_mode == 1 ? escape_compact_kernel<false, 8, 1> : escape_compact_kernel<false, 8, 0>);
     if (smem > 16 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
