@@ -982,8 +982,8 @@ __global__ void hist_l1_kernel(const float *__restrict__ p, int ldp, const float
 // Device top-k: k largest non-negative binary32 scores, ties by smaller index.
 // Exact radix select on the float bits (ordered like the values for x >= 0)
 // in three digit levels (11, 11, 10 bits), then all keys above the threshold
-// plus the first `need` ties in index order, then a bitonic sort of the k
-// survivors by (score desc, index asc) in one CTA.
+// plus the first `need` ties in index order, then each of the k survivors
+// placed at its rank by (score desc, index asc).
 // ---------------------------------------------------------------------------
 struct TopkState {
     uint32_t prefix;     // fixed high bits of the threshold so far
@@ -1018,27 +1018,86 @@ __global__ void topk_hist_kernel(const float *__restrict__ score, int64_t n, con
             atomicAdd(&hist[i], h[i]);
 }
 
-// One thread: walk the digit histogram from the top to the bin holding rank k_rem.
-__global__ void topk_scan_kernel(uint32_t *hist, TopkState *st, int level)
+// Initial state (rank k, empty prefix), a zeroed digit histogram and zeroed
+// output ranks.
+__global__ void topk_init_kernel(uint32_t *hist, TopkState *st, uint32_t k, uint32_t *rank)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0)
-        return;
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+        hist[i] = 0;
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x)
+        rank[i] = 0;
+    if (threadIdx.x == 0) {
+        st->prefix = 0;
+        st->k_rem = k;
+        st->count_gt = 0;
+        st->need = 0;
+        st->n_sel = 0;
+    }
+}
+
+// Find the digit bin holding rank k_rem counted from the top: the bins in
+// descending digit order, an inclusive prefix sum over them (one CTA of 1024
+// threads, two bins each), and the bin where the running count reaches k_rem.
+// The histogram is zeroed for the next level.
+__global__ void __launch_bounds__(1024) topk_scan_kernel(uint32_t *hist, TopkState *st, int level)
+{
+    __shared__ uint32_t v[2048];
+    __shared__ uint32_t wsum[32];
+    __shared__ int found;
     const int nb = level == 2 ? 1024 : 2048;
     const int bits = level == 2 ? 10 : 11;
-    uint32_t above = 0;
-    int b = nb - 1;
-    for (; b > 0; --b) {
-        if (above + hist[b] >= st->k_rem)
-            break;
-        above += hist[b];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    // element e = bin nb - 1 - e (descending digits)
+    const uint32_t a0 = (2 * t < nb) ? hist[nb - 1 - 2 * t] : 0u;
+    const uint32_t a1 = (2 * t + 1 < nb) ? hist[nb - 2 - 2 * t] : 0u;
+    if (t == 0)
+        found = -1;
+    __syncthreads();
+    hist[2 * t] = 0;
+    hist[2 * t + 1] = 0;
+    // inclusive scan of the pair sums across the CTA
+    uint32_t x = a0 + a1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o)
+            x += y;
     }
-    st->count_gt += above;
-    st->k_rem -= above;
-    st->prefix = (st->prefix << bits) | (uint32_t)b;
-    if (level == 2)
-        st->need = st->k_rem;
-    for (int i = 0; i < 2048; ++i)
-        hist[i] = 0;
+    if (lane == 31)
+        wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t z = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o)
+                z += y;
+        }
+        wsum[lane] = z;
+    }
+    __syncthreads();
+    const uint32_t incl1 = x + (w > 0 ? wsum[w - 1] : 0u);  // through element 2t + 1
+    const uint32_t incl0 = incl1 - a1;                       // through element 2t
+    const uint32_t k_rem = st->k_rem;
+    // the first element whose running count reaches k_rem (unique)
+    if (incl0 >= k_rem && incl0 - a0 < k_rem)
+        found = 2 * t;
+    else if (incl1 >= k_rem && incl1 - a1 < k_rem)
+        found = 2 * t + 1;
+    v[2 * t] = incl0;
+    v[2 * t + 1] = incl1;
+    __syncthreads();
+    if (t == 0) {
+        // no bin reaches k_rem (cannot happen for a consistent state): bin 0
+        const int e = found >= 0 ? found : nb - 1;
+        const uint32_t above = e > 0 ? v[e - 1] : 0u;  // elements before e: bins strictly above
+        st->count_gt += above;
+        st->k_rem = k_rem - above;
+        st->prefix = (st->prefix << bits) | (uint32_t)(nb - 1 - e);
+        if (level == 2)
+            st->need = k_rem - above;
+    }
 }
 
 // Keys above the threshold: appended in any order (sorted afterwards).
@@ -1088,13 +1147,23 @@ __global__ void topk_tie_select_kernel(const float *__restrict__ score, int64_t 
     const uint32_t thr = st->prefix;
     __shared__ uint32_t base_s;
     __shared__ uint32_t warp_tot[32];
-    if (threadIdx.x == 0) {
+    {
+        // ties in the blocks before this one (block-wide sum of their counts)
         uint32_t b = 0;
-        for (int i = 0; i < (int)blockIdx.x; ++i)
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x)
             b += counts[i];
-        base_s = b;
+        b = __reduce_add_sync(0xffffffffu, b);
+        if ((threadIdx.x & 31) == 0)
+            warp_tot[threadIdx.x >> 5] = b;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                t += warp_tot[w];
+            base_s = t;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const uint32_t need = st->need;
     const uint32_t gt = st->count_gt;
     uint32_t run = base_s;
@@ -1128,41 +1197,61 @@ __global__ void topk_tie_select_kernel(const float *__restrict__ score, int64_t 
     }
 }
 
-// Bitonic sort of k <= 16384 (key, index) pairs, key descending then index
-// ascending, in one CTA; writes indices (int32) and scores.
-__global__ void __launch_bounds__(1024) topk_sort_kernel(const uint32_t *__restrict__ sel_key,
-                                                         const uint32_t *__restrict__ sel_idx, int k,
-                                                         int32_t *__restrict__ out_idx, float *__restrict__ out_score)
+// Sort of the k selected (key, index) pairs, key descending then index
+// ascending, by ranks: the position of a pair is the number of pairs that
+// precede it (composite keys are unique, so the positions are a permutation).
+// Grid (pair blocks of 256, splits of the pairs compared against); partial
+// ranks are added atomically into `rank` (zeroed by topk_init_kernel).
+static constexpr int kRankSplit = 8;
+static constexpr int kRankTile = 1024;
+
+__device__ __forceinline__ uint64_t topk_comp(uint32_t key, uint32_t idx)
 {
-    extern __shared__ uint64_t keys[];
-    int P = 1;
-    while (P < k)
-        P <<= 1;
-    // composite: high 32 bits = ~key (ascending = score descending), low = index
-    for (int i = threadIdx.x; i < P; i += blockDim.x)
-        keys[i] = (i < k) ? (((uint64_t)(~sel_key[i]) << 32) | sel_idx[i]) : ~0ull;
-    __syncthreads();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < P; i += blockDim.x) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    const bool up = (i & size) == 0;
-                    const uint64_t a = keys[i], b = keys[j];
-                    if ((a > b) == up) {
-                        keys[i] = b;
-                        keys[j] = a;
-                    }
-                }
-            }
-            __syncthreads();
+    return ((uint64_t)(~key) << 32) | idx;  // ascending = score descending, then index ascending
+}
+
+__global__ void __launch_bounds__(256) topk_rank_kernel(const uint32_t *__restrict__ sel_key,
+                                                         const uint32_t *__restrict__ sel_idx, int k,
+                                                         uint32_t *__restrict__ rank)
+{
+    __shared__ uint64_t tile[kRankTile];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t ci = i < k ? topk_comp(sel_key[i], sel_idx[i]) : ~0ull;
+    const int per = (k + kRankSplit - 1) / kRankSplit;
+    const int j0 = blockIdx.y * per, j1 = min(k, j0 + per);
+    uint32_t r = 0;
+    for (int base = j0; base < j1; base += kRankTile) {
+        const int nt = min(kRankTile, j1 - base);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nt; t += blockDim.x)
+            tile[t] = topk_comp(sel_key[base + t], sel_idx[base + t]);
+        __syncthreads();
+        int t = 0;
+        for (; t + 8 <= nt; t += 8) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                r += (tile[t + u] < ci) ? 1u : 0u;
         }
+        for (; t < nt; ++t)
+            r += (tile[t] < ci) ? 1u : 0u;
     }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        out_idx[i] = (int32_t)(keys[i] & 0xffffffffu);
-        if (out_score)
-            out_score[i] = __uint_as_float(~(uint32_t)(keys[i] >> 32));
-    }
+    if (i < k && r)
+        atomicAdd(&rank[i], r);
+}
+
+__global__ void topk_scatter_kernel(const uint32_t *__restrict__ sel_key, const uint32_t *__restrict__ sel_idx,
+                                    const uint32_t *__restrict__ rank, int k, int32_t *__restrict__ out_idx,
+                                    float *__restrict__ out_score)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k)
+        return;
+    const uint32_t r = rank[i];
+    if (r >= (uint32_t)k)
+        return;  // cannot happen for unique keys; never write out of range
+    out_idx[r] = (int32_t)sel_idx[i];
+    if (out_score)
+        out_score[r] = __uint_as_float(sel_key[i]);
 }
 
 }  // namespace jl
@@ -1713,7 +1802,7 @@ int jl_topk(const float *score, int64_t n, int32_t k, int32_t *out_idx, float *o
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t per_block = 8192;
     const int nblk = (int)((n + per_block - 1) / per_block);
-    const size_t bytes = 2048 * 4 + sizeof(TopkState) + (size_t)nblk * 4 + 2 * (size_t)k * 4 + 256;
+    const size_t bytes = 2048 * 4 + sizeof(TopkState) + (size_t)nblk * 4 + 3 * (size_t)k * 4 + 256;
     uint8_t *w = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&w), bytes, st);
     if (e != cudaSuccess)
@@ -1723,31 +1812,23 @@ int jl_topk(const float *score, int64_t n, int32_t k, int32_t *out_idx, float *o
     uint32_t *counts = reinterpret_cast<uint32_t *>(w + 2048 * 4 + sizeof(TopkState));
     uint32_t *sel_key = counts + nblk;
     uint32_t *sel_idx = sel_key + k;
-    TopkState init;
-    memset(&init, 0, sizeof(init));
-    init.k_rem = (uint32_t)k;
+    uint32_t *rank = sel_idx + k;
     int rc = JL_OK;
     do {
-        if ((e = cudaMemsetAsync(hist, 0, 2048 * 4, st)) != cudaSuccess) break;
-        if ((e = cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+        topk_init_kernel<<<1, 1024, 0, st>>>(hist, state, (uint32_t)k, rank);
         const int grid = 148 * 4;
         for (int level = 0; level < 3 && e == cudaSuccess; ++level) {
             topk_hist_kernel<<<grid, 256, 0, st>>>(score, n, state, level, hist);
-            topk_scan_kernel<<<1, 32, 0, st>>>(hist, state, level);
+            topk_scan_kernel<<<1, 1024, 0, st>>>(hist, state, level);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) break;
         topk_collect_gt_kernel<<<grid, 256, 0, st>>>(score, n, state, sel_key, sel_idx);
         topk_tie_count_kernel<<<nblk, 256, 0, st>>>(score, n, state, per_block, counts);
         topk_tie_select_kernel<<<nblk, 256, 0, st>>>(score, n, state, per_block, counts, sel_key, sel_idx);
-        int P = 1;
-        while (P < k)
-            P <<= 1;
-        const size_t smem = (size_t)P * 8;
-        if ((e = cudaFuncSetAttribute(topk_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-            break;
-        topk_sort_kernel<<<1, 1024, smem, st>>>(sel_key, sel_idx, k, out_idx, out_score);
+        topk_rank_kernel<<<dim3((unsigned)((k + 255) / 256), kRankSplit), 256, 0, st>>>(sel_key, sel_idx, k, rank);
+        topk_scatter_kernel<<<(unsigned)((k + 255) / 256), 256, 0, st>>>(sel_key, sel_idx, rank, k, out_idx,
+                                                                       out_score);
         e = cudaGetLastError();
     } while (0);
     if (e != cudaSuccess)

@@ -170,9 +170,19 @@ def test_topk_exact(cuda):
     import torch
     L = _lib.lib()
     rng = np.random.default_rng(4)
+    cases = []
     for n, k in ((1000, 10), (100000, 1000), (1 << 20, 10486)):
         s = rng.random(n).astype(np.float32) * 4.6
         s[rng.choice(n, n // 10, replace=False)] = np.float32(2.5)  # many ties
+        cases.append((s, k))
+    cases.append((rng.random(5000).astype(np.float32), 5000))                    # k = n
+    cases.append((np.full(70000, 1.75, np.float32), 1))                           # all equal: first index
+    cases.append((np.full(70000, 1.75, np.float32), 16384))                       # all equal, k at its maximum
+    # values sharing their top 22 bits: the rank is decided in the last digit level
+    cases.append(((1.0 + rng.integers(0, 1024, 300000) * 2.0 ** -23).astype(np.float32), 16384))
+    cases.append((np.zeros(40000, np.float32), 123))                              # all zero
+    for s, k in cases:
+        n = s.shape[0]
         sd = torch.from_numpy(s).cuda()
         idx = torch.zeros(k, dtype=torch.int32, device="cuda")
         val = torch.zeros(k, dtype=torch.float32, device="cuda")
