@@ -1430,7 +1430,10 @@ Variant default_variant(int precision, int max_iter)
     (void)max_iter;
     if (precision == JL_FP64)
         return Variant{2, 4, 128, 0};
-    return Variant{4, 8, 256, 0};
+    // binary32: the compacting tile kernel, parking threshold 16 (ahead of the
+    // lane-refill kernel on every sweep frame; within a few % of the static
+    // kernel on frames that escape early, far ahead on divergent ones)
+    return Variant{0, 16, 256, 0};
 }
 
 }  // namespace jl
