@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "jl_internal.h"
@@ -206,14 +207,36 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(frame table)"); break; }
             e = cudaMemcpy(b->frames_dev[g], host[g].data(), nb, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(frame table)"); break; }
-            // work-unit -> frame table: 32x8 tiles for the static kernel, chunks otherwise
+            // work-unit -> frame table.  Lane-refill kernel: chunks in frame
+            // order.  Tile kernels: 32x32 tiles with the frames interleaved
+            // (round-robin over the frames that still have tiles), followed by
+            // each tile's index within its frame, so that warps claiming work
+            // meet cheap and costly frames alike rather than one frame's
+            // far field at a time (cheap tiles claimed in a burst make the
+            // launch counter the bottleneck).
             const bool stat = v.ppt == 0;
-            std::vector<int32_t> cf((size_t)(stat ? b->tiles[g] : b->chunks[g]));
-            for (size_t f = 0; f < host[g].size(); ++f) {
-                const int64_t begin = stat ? host[g][f].tile_begin : host[g][f].chunk_begin;
-                const int32_t cnt = stat ? host[g][f].tile_count : host[g][f].chunk_count;
-                for (int32_t c = 0; c < cnt; ++c)
-                    cf[(size_t)begin + c] = (int32_t)f;
+            std::vector<int32_t> cf;
+            if (stat) {
+                const size_t T = (size_t)b->tiles[g];
+                cf.resize(2 * T);
+                int32_t most = 0;
+                for (const Frame &F : host[g])
+                    most = std::max(most, F.tile_count);
+                size_t pos = 0;
+                for (int32_t k = 0; k < most; ++k)
+                    for (size_t f = 0; f < host[g].size(); ++f)
+                        if (k < host[g][f].tile_count) {
+                            cf[pos] = (int32_t)f;
+                            cf[T + pos] = k;
+                            ++pos;
+                        }
+            } else {
+                cf.resize((size_t)b->chunks[g]);
+                for (size_t f = 0; f < host[g].size(); ++f) {
+                    const int64_t begin = host[g][f].chunk_begin;
+                    for (int32_t c = 0; c < host[g][f].chunk_count; ++c)
+                        cf[(size_t)begin + c] = (int32_t)f;
+                }
             }
             e = cudaMalloc(&b->chunk_frame_dev[g], cf.size() * sizeof(int32_t));
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(work table)"); break; }
@@ -235,6 +258,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             args[g].frames = b->frames_dev[g];
             args[g].chunk_frame = b->variant[g].ppt ? b->chunk_frame_dev[g] : nullptr;
             args[g].tile_frame = b->variant[g].ppt ? nullptr : b->chunk_frame_dev[g];
+            args[g].tile_local = b->variant[g].ppt ? nullptr : b->chunk_frame_dev[g] + b->tiles[g];
             args[g].total_tiles = b->tiles[g];
             args[g].n_frames = b->n_group[g];
             args[g].hist_smem = 0;

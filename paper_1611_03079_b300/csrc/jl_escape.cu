@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
         uint32_t *rgba = F.rgba;
         uint32_t *bins = F.hist_bins;
         const uint64_t cmagic = F.colour_magic;
-        const uint32_t lt = (uint32_t)(tile - F.tile_begin);
+        const uint32_t lt = BATCH ? (uint32_t)a.tile_local[tile] : (uint32_t)(tile - F.tile_begin);
         const uint32_t ty = (uint32_t)(((uint64_t)lt * F.tiles_x_magic) >> 40);
         const uint32_t tx = lt - ty * (uint32_t)F.tiles_x;
         const int i = (int)tx * 32 + dx;
@@ -1074,7 +1074,7 @@ __global__ void __launch_bounds__(256, 4) escape_compact_kernel(const __grid_con
         o.mi = mi;
         o.u8 = F.count_type == JL_COUNT_U8;
         o.small = mi <= 4096;
-        const uint32_t lt = (uint32_t)(tile - F.tile_begin);
+        const uint32_t lt = BATCH ? (uint32_t)a.tile_local[tile] : (uint32_t)(tile - F.tile_begin);
         const uint32_t ty = (uint32_t)(((uint64_t)lt * F.tiles_x_magic) >> 40);
         const uint32_t tx = lt - ty * (uint32_t)F.tiles_x;
         const int i = (int)tx * 32 + dx;

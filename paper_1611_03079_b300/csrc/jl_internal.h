@@ -46,7 +46,8 @@ struct Frame {
 struct EscapeArgs {
     const Frame *frames;               // device table, or NULL to use `single`
     const int32_t *chunk_frame;        // device: frame index of every chunk (batches)
-    const int32_t *tile_frame;         // device: frame index of every 32x8 tile (static kernel, batches)
+    const int32_t *tile_frame;         // device: frame of every 32x32 tile (tile kernels, batches)
+    const int32_t *tile_local;         // device: index of every tile within its frame (tile kernels, batches)
     int64_t total_tiles;               // static kernel: tiles in the launch
     int32_t n_frames;
     int32_t hist_smem;                 // 1: accumulate histogram bins in shared memory (one frame)
