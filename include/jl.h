@@ -440,7 +440,13 @@ int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const i
 int jl_topk(const float *score, int64_t n, int32_t k, int32_t *out_idx, float *out_score, void *stream);
 
 /* Screening: forward over n values of C (score = entropy of the predicted
- * histogram, written to `score`, n floats), then the top k by score. */
+ * histogram, written to `score`, n floats), then the top k by score
+ * (1 <= k <= min(n, 16384)).  When a call has the same (c, n, k, output)
+ * pointers as the previous call on the model, its work is captured as a CUDA
+ * graph and replayed by later such calls (one graph launch instead of ~14
+ * kernel launches); weights updated by training are picked up (the graph
+ * re-packs them).  On a stream that is itself being captured, the launches are
+ * issued directly.  Calls on one model must not overlap in time. */
 int jl_survey(jl_model *md, const float *c, int64_t n, int32_t k, int32_t *top_idx, float *top_score, float *score,
               void *stream);
 

@@ -171,13 +171,18 @@ class Surrogate:
                                curve.ctypes.data if loss_curve else None, st))
         return curve
 
-    def survey(self, c, k):
-        """Screen c (torch n x 2): returns (top_idx, top_score, score)."""
+    def survey(self, c, k, out=None):
+        """Screen c (torch n x 2): returns (top_idx, top_score, score).  `out`
+        may supply (top_idx int32[k], top_score float32[k], score float32[n]);
+        repeated calls with the same c and outputs replay one CUDA graph."""
         import torch
         n = c.shape[0]
-        S = torch.empty(n, dtype=torch.float32, device=c.device)
-        idx = torch.empty(int(k), dtype=torch.int32, device=c.device)
-        val = torch.empty(int(k), dtype=torch.float32, device=c.device)
+        if out is not None:
+            idx, val, S = out
+        else:
+            S = torch.empty(n, dtype=torch.float32, device=c.device)
+            idx = torch.empty(int(k), dtype=torch.int32, device=c.device)
+            val = torch.empty(int(k), dtype=torch.float32, device=c.device)
         st = torch.cuda.current_stream().cuda_stream
         check(self._L.jl_survey(self._h, c.data_ptr(), n, int(k), idx.data_ptr(), val.data_ptr(), S.data_ptr(), st))
         return idx, val, S

@@ -71,3 +71,43 @@ def test_surrogate_gain(cuda):
     assert (sel == mlp.top_k(S.cpu().numpy(), k)).all()
     plan.close()
     m.close()
+
+
+def test_survey_graph_replay(cuda):
+    """Repeated screening calls with the same inputs and outputs replay one
+    captured CUDA graph: results equal the direct forward + top-k, and a
+    replay after the weights changed uses the new weights."""
+    import torch
+    from paper_1611_03079_b300 import _lib
+    rng = np.random.default_rng(11)
+    n, k = 50000, 500
+    c = torch.from_numpy(wl.survey_c(n, seed=21)).cuda()
+    m = sg.Surrogate(wl.fourier_matrix(), wl.mlp_init())
+    out = (torch.empty(k, dtype=torch.int32, device="cuda"), torch.empty(k, dtype=torch.float32, device="cuda"),
+           torch.empty(n, dtype=torch.float32, device="cuda"))
+
+    def direct():
+        _, S = m.forward(c, probs=False, score=True)
+        idx = torch.empty(k, dtype=torch.int32, device="cuda")
+        val = torch.empty(k, dtype=torch.float32, device="cuda")
+        _lib.check(_lib.lib().jl_topk(S.data_ptr(), n, k, idx.data_ptr(), val.data_ptr(), None))
+        torch.cuda.synchronize()
+        return idx.cpu().numpy(), val.cpu().numpy(), S.cpu().numpy()
+
+    ref = direct()
+    for _ in range(4):  # first call direct, second captures, then replays
+        idx, val, S = m.survey(c, k, out=out)
+        torch.cuda.synchronize()
+        assert (idx.cpu().numpy() == ref[0]).all() and (val.cpu().numpy() == ref[1]).all()
+        assert (S.cpu().numpy() == ref[2]).all()
+    # change the weights: one training epoch on random targets
+    h = rng.random((2048, 101)).astype(np.float32)
+    h /= h.sum(1, keepdims=True)
+    m.train(c[:2048].contiguous(), torch.from_numpy(h).cuda(), epochs=1, batch=512, lr=1e-2)
+    torch.cuda.synchronize()
+    ref2 = direct()
+    assert not (ref2[2] == ref[2]).all()
+    idx, val, S = m.survey(c, k, out=out)
+    torch.cuda.synchronize()
+    assert (S.cpu().numpy() == ref2[2]).all() and (idx.cpu().numpy() == ref2[0]).all()
+    m.close()
