@@ -307,10 +307,11 @@ class Batch:
     `frames` are dicts with keys c, rect, W, H, max_iter, mode, precision,
     count_type (None for no counts), and optional rgba (default True) and hist
     (default False).  Outputs are allocated here as flat device buffers;
-    `counts(i)`, `rgba(i)` and `hist(i)` return per-frame views.
+    `counts(i)`, `rgba(i)` and `hist(i)` return per-frame views.  `tune=True`
+    lets the plan time candidate kernels on its own frames at creation.
     """
 
-    def __init__(self, frames, palette=None, chunk_len=0, variants=None, cycle_budget=0):
+    def __init__(self, frames, palette=None, chunk_len=0, variants=None, cycle_budget=0, tune=False):
         import torch
         self._L = _lib.lib()
         self.frames = list(frames)
@@ -355,6 +356,7 @@ class Batch:
                     opts.fp64_emu = v64[3]
                 opts.variant_flags |= 2
         opts.cycle_budget = int(cycle_budget)
+        opts.tune = 1 if tune else 0
         pal, pal_ptr = _palette_ptr(palette)
         h = ctypes.c_void_p()
         check(self._L.jl_batch_create(ctypes.cast(arr, ctypes.c_void_p), n, self.counts_buf.data_ptr(),

@@ -43,7 +43,7 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("chunk_len", ctypes.c_int32), ("fp32_ppt", ctypes.c_int32), ("fp32_unroll", ctypes.c_int32),
                 ("fp32_threads", ctypes.c_int32), ("fp64_ppt", ctypes.c_int32), ("fp64_unroll", ctypes.c_int32),
                 ("fp64_threads", ctypes.c_int32), ("variant_flags", ctypes.c_int32),
-                ("fp64_emu", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cycle_budget", ctypes.c_int64)]
+                ("fp64_emu", ctypes.c_int32), ("tune", ctypes.c_int32), ("cycle_budget", ctypes.c_int64)]
 
 
 class Map(ctypes.Structure):

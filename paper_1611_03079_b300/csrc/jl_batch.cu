@@ -26,7 +26,9 @@ struct jl_batch {
     std::vector<int32_t> prec;             // resolved precision of every frame (input order)
     std::vector<int64_t> pixels;           // per group
     jl::Frame *frames_dev[2] = {nullptr, nullptr};
-    int32_t *chunk_frame_dev[2] = {nullptr, nullptr};  // chunk -> frame, or tile -> frame (static kernel)
+    int32_t *chunk_frame_dev[2] = {nullptr, nullptr};  // chunk -> frame (lane-refill kernel)
+    int32_t *tile_dev[2] = {nullptr, nullptr};         // tile kernels: tile -> frame, then tile -> index in frame
+    bool tuned[2] = {false, false};                    // variant chosen by timing the plan's own frames
     int64_t tiles[2] = {0, 0};
     int n_group[2] = {0, 0};
     int64_t chunks[2] = {0, 0};
@@ -55,6 +57,8 @@ static void destroy_plan(jl_batch *b)
             cudaFree(b->frames_dev[g]);
         if (b->chunk_frame_dev[g])
             cudaFree(b->chunk_frame_dev[g]);
+        if (b->tile_dev[g])
+            cudaFree(b->tile_dev[g]);
     }
     if (b->coords_dev)
         cudaFree(b->coords_dev);
@@ -207,18 +211,28 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(frame table)"); break; }
             e = cudaMemcpy(b->frames_dev[g], host[g].data(), nb, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(frame table)"); break; }
-            // work-unit -> frame table.  Lane-refill kernel: chunks in frame
-            // order.  Tile kernels: 32x32 tiles with the frames interleaved
-            // (round-robin over the frames that still have tiles), followed by
-            // each tile's index within its frame, so that warps claiming work
-            // meet cheap and costly frames alike rather than one frame's
-            // far field at a time (cheap tiles claimed in a burst make the
-            // launch counter the bottleneck).
-            const bool stat = v.ppt == 0;
-            std::vector<int32_t> cf;
-            if (stat) {
+            // Work tables, both kinds (a tuned plan may try either).  Lane-refill
+            // kernel: chunk -> frame, in frame order.  Tile kernels: 32x32 tiles
+            // with the frames interleaved (round-robin over the frames that still
+            // have tiles), then each tile's index within its frame, so that warps
+            // claiming work meet cheap and costly frames alike rather than one
+            // frame's far field at a time (cheap tiles claimed in a burst make
+            // the launch counter the bottleneck).
+            {
+                std::vector<int32_t> cf((size_t)b->chunks[g]);
+                for (size_t f = 0; f < host[g].size(); ++f) {
+                    const int64_t begin = host[g][f].chunk_begin;
+                    for (int32_t c = 0; c < host[g][f].chunk_count; ++c)
+                        cf[(size_t)begin + c] = (int32_t)f;
+                }
+                e = cudaMalloc(&b->chunk_frame_dev[g], std::max<size_t>(cf.size(), 1) * sizeof(int32_t));
+                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(chunk table)"); break; }
+                e = cudaMemcpy(b->chunk_frame_dev[g], cf.data(), cf.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(chunk table)"); break; }
+            }
+            if (b->tiles[g] <= 0x7fffffffll) {
                 const size_t T = (size_t)b->tiles[g];
-                cf.resize(2 * T);
+                std::vector<int32_t> tf(2 * T);
                 int32_t most = 0;
                 for (const Frame &F : host[g])
                     most = std::max(most, F.tile_count);
@@ -226,22 +240,16 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 for (int32_t k = 0; k < most; ++k)
                     for (size_t f = 0; f < host[g].size(); ++f)
                         if (k < host[g][f].tile_count) {
-                            cf[pos] = (int32_t)f;
-                            cf[T + pos] = k;
+                            tf[pos] = (int32_t)f;
+                            tf[T + pos] = k;
                             ++pos;
                         }
-            } else {
-                cf.resize((size_t)b->chunks[g]);
-                for (size_t f = 0; f < host[g].size(); ++f) {
-                    const int64_t begin = host[g][f].chunk_begin;
-                    for (int32_t c = 0; c < host[g][f].chunk_count; ++c)
-                        cf[(size_t)begin + c] = (int32_t)f;
-                }
+                e = cudaMalloc(&b->tile_dev[g], std::max<size_t>(tf.size(), 1) * sizeof(int32_t));
+                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(tile table)"); break; }
+                e = cudaMemcpy(b->tile_dev[g], tf.data(), tf.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(tile table)"); break; }
             }
-            e = cudaMalloc(&b->chunk_frame_dev[g], cf.size() * sizeof(int32_t));
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(work table)"); break; }
-            e = cudaMemcpy(b->chunk_frame_dev[g], cf.data(), cf.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(work table)"); break; }
+            b->tuned[g] = o.tune != 0 && !explicit_variant;
         }
         if (rc != JL_OK)
             break;
@@ -253,27 +261,98 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             memcpy(pal, palette, 1024);
         else
             default_palette_bytes(pal);
-        for (int g = 0; g < 2; ++g) {
-            memset(&args[g], 0, sizeof(EscapeArgs));
-            args[g].frames = b->frames_dev[g];
-            args[g].chunk_frame = b->variant[g].ppt ? b->chunk_frame_dev[g] : nullptr;
-            args[g].tile_frame = b->variant[g].ppt ? nullptr : b->chunk_frame_dev[g];
-            args[g].tile_local = b->variant[g].ppt ? nullptr : b->chunk_frame_dev[g] + b->tiles[g];
-            args[g].total_tiles = b->tiles[g];
-            args[g].n_frames = b->n_group[g];
-            args[g].hist_smem = 0;
-            args[g].total_chunks = b->chunks[g];
-            args[g].chunk_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 8 * g);
-            args[g].status = reinterpret_cast<int32_t *>(b->ctl_dev + 16);
-            args[g].cycle_budget = o.cycle_budget;
+        auto make_args = [&](int g, const Variant &v) {
+            EscapeArgs x;
+            memset(&x, 0, sizeof(EscapeArgs));
+            x.frames = b->frames_dev[g];
+            x.chunk_frame = v.ppt ? b->chunk_frame_dev[g] : nullptr;
+            x.tile_frame = v.ppt ? nullptr : b->tile_dev[g];
+            x.tile_local = v.ppt ? nullptr : b->tile_dev[g] + b->tiles[g];
+            x.total_tiles = b->tiles[g];
+            x.n_frames = b->n_group[g];
+            x.hist_smem = 0;
+            x.total_chunks = b->chunks[g];
+            x.chunk_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 8 * g);
+            x.status = reinterpret_cast<int32_t *>(b->ctl_dev + 16);
+            x.cycle_budget = o.cycle_budget;
             bool u16_rgba = !host[g].empty();
             for (const Frame &F : host[g])
                 u16_rgba = u16_rgba && F.counts && F.count_type == JL_COUNT_U16 && F.rgba && !F.hist_bins;
-            args[g].out_mode = u16_rgba ? 1 : 0;
-            memcpy(args[g].palette, pal, 1024);
-        }
+            x.out_mode = u16_rgba ? 1 : 0;
+            memcpy(x.palette, pal, 1024);
+            return x;
+        };
         const int sms = device_sm_count();
         if (sms <= 0) { rc = fail(JL_EUNSUPPORTED, "no CUDA device"); break; }
+        // Tuned plan: time candidate kernels on the plan's own frames (each run
+        // once to warm up, then twice), keep the fastest.  Outputs written by
+        // these runs are overwritten by every launch of the plan.
+        if (b->tuned[0] || b->tuned[1]) {
+            cudaEvent_t t0 = nullptr, t1 = nullptr;
+            e = cudaEventCreate(&t0);
+            if (e == cudaSuccess)
+                e = cudaEventCreate(&t1);
+            for (int g = 0; g < 2 && e == cudaSuccess && rc == JL_OK; ++g)
+                if (b->n_group[g])
+                    e = launch_coords(b->frames_dev[g], nullptr, b->n_group[g], b->s0);
+            for (int g = 0; g < 2 && e == cudaSuccess && rc == JL_OK; ++g) {
+                if (!b->tuned[g] || !b->n_group[g])
+                    continue;
+                std::vector<Variant> cand;
+                cand.push_back(b->variant[g]);
+                if (b->tile_dev[g]) {
+                    cand.push_back(Variant{0, 0, 256, 0});
+                    if (g == 0)
+                        cand.push_back(Variant{0, 16, 256, 0});
+                }
+                cand.push_back(default_variant(g, 0));
+                float best_ms = 0.f;
+                int best = -1;
+                for (size_t ci = 0; ci < cand.size() && e == cudaSuccess; ++ci) {
+                    const Variant &v = cand[ci];
+                    if (v.ppt == 0 && !b->tile_dev[g])
+                        continue;
+                    bool seen = false;
+                    for (size_t cj = 0; cj < ci; ++cj)
+                        seen = seen || (cand[cj].ppt == v.ppt && cand[cj].unroll == v.unroll &&
+                                        cand[cj].threads == v.threads && cand[cj].emu == v.emu);
+                    if (seen)
+                        continue;
+                    const EscapeArgs x = make_args(g, v);
+                    float ms = 0.f;
+                    for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                        e = cudaMemsetAsync(b->ctl_dev, 0, 32, b->s0);
+                        if (e == cudaSuccess)
+                            e = cudaEventRecord(t0, b->s0);
+                        if (e == cudaSuccess)
+                            e = launch_escape(x, g, v, sms, b->s0);
+                        if (e == cudaSuccess)
+                            e = cudaEventRecord(t1, b->s0);
+                        if (e == cudaSuccess)
+                            e = cudaEventSynchronize(t1);
+                        float one = 0.f;
+                        if (e == cudaSuccess)
+                            e = cudaEventElapsedTime(&one, t0, t1);
+                        if (r > 0)
+                            ms += one;
+                    }
+                    // a later candidate must win by more than 1 % (run-to-run noise)
+                    if (e == cudaSuccess && (best < 0 || ms < best_ms * 0.99f)) {
+                        best = (int)ci;
+                        best_ms = ms;
+                    }
+                }
+                if (e == cudaSuccess && best >= 0)
+                    b->variant[g] = cand[(size_t)best];
+            }
+            if (t0)
+                cudaEventDestroy(t0);
+            if (t1)
+                cudaEventDestroy(t1);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "plan tuning"); break; }
+        }
+        for (int g = 0; g < 2; ++g)
+            args[g] = make_args(g, b->variant[g]);
         e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamBeginCapture"); break; }
         cudaError_t ce = cudaMemsetAsync(b->ctl_dev, 0, 32, b->s0);

@@ -203,3 +203,27 @@ def test_compact_variant_batch(cuda, T):
     b.launch()
     _check_batch(b, frames)
     b.close()
+
+
+def test_tuned_plan(cuda):
+    """A plan that times candidate kernels on its own frames at creation
+    (both precisions, histograms on some frames) renders them bit-exactly,
+    and launching it again gives the same outputs."""
+    import torch
+    frames = []
+    for i, f in enumerate(wl.random_views(20, seed=950)):
+        f = dict(f)
+        f["count_type"] = "u16"
+        f["hist"] = i % 3 == 0
+        frames.append(f)
+    frames.append(dict(c=complex(-0.7269, 0.1889), rect=(-1.6, 1.6, -1.6, 1.6), W=256, H=200, max_iter=1000, mode=0,
+                       precision=0, count_type="u16", hist=True))
+    b = jl.Batch(frames, palette=PAL, tune=True)
+    b.launch()
+    _check_batch(b, frames)
+    first = b.counts_buf.clone()
+    b.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(first, b.counts_buf)
+    _check_batch(b, frames)
+    b.close()
