@@ -256,7 +256,7 @@ def run_single_frame(K, W, peak32):
     torch.cuda.synchronize()
     t1 = e0.elapsed_time(e1) * 1e-3 / reps
     nb = 1024
-    b = jl.Batch([dict(f) for _ in range(nb)])
+    b = jl.Batch([dict(f) for _ in range(nb)], tune=True)
     for _ in range(W):
         b.launch()
     e0.record()
