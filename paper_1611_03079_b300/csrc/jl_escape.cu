@@ -30,6 +30,10 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "jl_common.cuh"
 #include "jl_f64emu.cuh"
 #include "jl_internal.h"
@@ -1210,6 +1214,37 @@ __global__ void __launch_bounds__(256, 4) escape_compact_kernel(const __grid_con
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Resident CTAs per SM of a kernel for a block size and dynamic shared
+// memory, asked of the runtime once per (device, kernel, threads, bytes): the
+// query costs microseconds of host time, which would otherwise be paid on
+// every small render.
+cudaError_t occupancy_per_sm(const void *kern, int threads, size_t smem, int *out)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    const auto key = std::make_tuple(dev, kern, threads, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const auto it = cache.find(key);
+        if (it != cache.end()) {
+            *out = it->second;
+            return cudaSuccess;
+        }
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = per_sm;
+    *out = per_sm;
+    return cudaSuccess;
+}
+
 int device_sm_count()
 {
     int dev = 0, n = 0;
@@ -1267,7 +1302,7 @@ static cudaError_t launch_one(const EscapeArgs &a, const Variant &v, int num_sms
     }
     int per_sm = v.ctas_per_sm;
     if (per_sm <= 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, v.threads, smem);
+        cudaError_t e = occupancy_per_sm(reinterpret_cast<const void *>(kern), v.threads, smem, &per_sm);
         if (e != cudaSuccess)
             return e;
         if (per_sm < 1)
@@ -1358,7 +1393,7 @@ static cudaError_t launch_static(const EscapeArgs &a, cudaStream_t st)
     if (a.total_tiles < 1)
         return cudaErrorInvalidValue;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    cudaError_t e = occupancy_per_sm(reinterpret_cast<const void *>(kern), 256, smem, &per_sm);
     if (e != cudaSuccess)
         return e;
     const int sms = device_sm_count();
@@ -1391,7 +1426,7 @@ static cudaError_t launch_compact(const EscapeArgs &a, int T, cudaStream_t st)
     if (a.total_tiles < 1)
         return cudaErrorInvalidValue;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    cudaError_t e = occupancy_per_sm(reinterpret_cast<const void *>(kern), 256, smem, &per_sm);
     if (e != cudaSuccess)
         return e;
     const int sms = device_sm_count();

@@ -87,6 +87,7 @@ cudaError_t launch_hist_zero(const Frame *frames_dev, int n, cudaStream_t st);
 bool variant_supported(int precision, int ppt, int unroll);
 int variant_list(int precision, int32_t *pairs, int cap);
 int device_sm_count();
+cudaError_t occupancy_per_sm(const void *kern, int threads, size_t smem, int *out);
 cudaError_t launch_dbl2(const double *in, double *out, int n, cudaStream_t st);
 cudaError_t launch_f64emu(int op, const double *a, const double *b, double *out, int32_t *sp, int n, cudaStream_t st);
 

@@ -262,7 +262,7 @@ static cudaError_t launch_map_t(const MapArgs &a, cudaStream_t st)
             return e;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    cudaError_t e = occupancy_per_sm(reinterpret_cast<const void *>(kern), 256, smem, &per_sm);
     if (e != cudaSuccess)
         return e;
     const int sms = device_sm_count();
