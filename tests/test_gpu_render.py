@@ -219,6 +219,24 @@ def test_throughput_sweep_full_size_sampled(cuda, sweep_batch, idx):
     assert (np.rint(h * f["W"] * f["H"]) == np.bincount(c.ravel(), minlength=f["max_iter"] + 1)).all()
 
 
+@pytest.mark.slow
+def test_throughput_sweep_bench_outputs(cuda, sweep_batch):
+    """The sweep as bench.py renders it (uint16 counts and RGBA8, no
+    histograms, so the tile kernels take their store path without per-frame
+    tests) gives the same bytes as the plan above, whose counts are checked
+    against the oracle."""
+    import torch
+    frames, b = sweep_batch
+    bf = [dict(f, hist=False) for f in frames]
+    b2 = jl.Batch(bf, palette=PAL)
+    b2.launch()
+    torch.cuda.synchronize()
+    for i in range(len(frames)):
+        assert torch.equal(b2.counts(i), b.counts(i)), i
+        assert torch.equal(b2.rgba(i), b.rgba(i)), i
+    b2.close()
+
+
 def test_integer_doubling_is_exact(cuda):
     """The binary64 kernels form x + x on the integer pipes; it must equal
     IEEE x + x bit for bit (zero, subnormals, carries into the exponent,
