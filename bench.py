@@ -535,9 +535,13 @@ def main():
     # frames give the per-precision breakdown.
     for f in frames:
         f["count_type"], f["rgba"] = "u16", True
-    plan = jl.Batch(frames, palette=pal)
+    # The plan also times candidate kernels on its own launch (the tuner's
+    # single-frame calibration can misjudge a concurrent multi-frame launch);
+    # the per-precision plans use the kernels it chose.
+    plan = jl.Batch(frames, palette=pal, tune=True)
     sub = {p: [i for i in range(len(frames)) if frames[i]["precision"] == p] for p in (0, 1)}
-    sub_plans = {p: jl.Batch([frames[i] for i in sub[p]], palette=pal) for p in (0, 1)}
+    chosen = {"fp32": plan.variant(0)[:3], "fp64": plan.variant(1)}
+    sub_plans = {p: jl.Batch([frames[i] for i in sub[p]], palette=pal, variants=chosen) for p in (0, 1)}
     W_ = max(args.warmup, 3)
     for _ in range(W_):
         plan.launch()

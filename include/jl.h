@@ -294,6 +294,12 @@ typedef struct jl_batch jl_batch;
 int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_t *rgba_base, float *hist_base,
                     const uint8_t *palette, const jl_batch_opts *opts, jl_batch **out);
 
+/* The kernel variant the plan uses for a precision group (chosen at creation:
+ * explicit option, the plan's own timing with opts.tune, else the tuned or
+ * default one); meaningful for groups that have frames. */
+int jl_batch_variant(const jl_batch *b, int32_t precision, int32_t *ppt, int32_t *unroll, int32_t *threads,
+                     int32_t *emu);
+
 /* Render every frame of the plan: one cudaGraphLaunch on `stream`
  * (asynchronous; nothing is allocated). */
 int jl_batch_launch(jl_batch *b, void *stream);

@@ -376,6 +376,13 @@ class Batch:
         check(self._L.jl_batch_status(self._h, st, ctypes.byref(v)))
         return v.value
 
+    def variant(self, precision):
+        """(ppt, unroll, threads, emu) of the kernel the plan uses for
+        precision 0 (binary32) or 1 (binary64)."""
+        v = [ctypes.c_int32(0) for _ in range(4)]
+        check(self._L.jl_batch_variant(self._h, int(precision), *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
     def precisions(self):
         n = len(self.frames)
         buf = (ctypes.c_int32 * n)()

@@ -84,6 +84,7 @@ SIGNATURES = {
     "jl_variant_list": (ctypes.c_int, [_i32, _vp, _i32]),
     "jl_probe_peak": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp]),
     "jl_batch_create": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "jl_batch_variant": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "jl_batch_launch": (ctypes.c_int, [_vp, _vp]),
     "jl_batch_status": (ctypes.c_int, [_vp, _vp, _vp]),
     "jl_batch_precisions": (ctypes.c_int, [_vp, _vp, _i32]),

@@ -397,6 +397,23 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
     return JL_OK;
 }
 
+int jl_batch_variant(const jl_batch *b, int32_t precision, int32_t *ppt, int32_t *unroll, int32_t *threads,
+                     int32_t *emu)
+{
+    if (!b || (precision != JL_FP32 && precision != JL_FP64))
+        return fail(JL_EINVAL, "invalid arguments");
+    const Variant &v = b->variant[precision];
+    if (ppt)
+        *ppt = v.ppt;
+    if (unroll)
+        *unroll = v.unroll;
+    if (threads)
+        *threads = v.threads;
+    if (emu)
+        *emu = v.emu;
+    return JL_OK;
+}
+
 int jl_batch_launch(jl_batch *b, void *stream)
 {
     if (!b || !b->exec)

@@ -219,6 +219,9 @@ def test_tuned_plan(cuda):
     frames.append(dict(c=complex(-0.7269, 0.1889), rect=(-1.6, 1.6, -1.6, 1.6), W=256, H=200, max_iter=1000, mode=0,
                        precision=0, count_type="u16", hist=True))
     b = jl.Batch(frames, palette=PAL, tune=True)
+    for prec in (0, 1):
+        ppt, unroll, threads, emu = b.variant(prec)
+        assert ppt >= 0 and unroll >= 0 and threads in (128, 256) and emu >= 1
     b.launch()
     _check_batch(b, frames)
     first = b.counts_buf.clone()
