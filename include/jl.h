@@ -274,9 +274,10 @@ typedef struct {
                                (needed for the static kernel, ppt = unroll = 0) */
     int32_t fp64_emu;       /* 0 = tuned or default; else as `emu` of jl_render_variant */
     int32_t tune;           /* 1: for each precision group without an explicit variant, time
-                               candidate kernels (the tuned or default variant, the static and
-                               compacting tile kernels) on the plan's own frames at creation
-                               and keep the fastest; 0: the tuned or default variant */
+                               candidate kernels (the tuned and the default variant, the tile
+                               kernels, a few lane-refill shapes for binary64) on the plan's own
+                               frames at creation and keep the fastest; 0: the tuned or default
+                               variant */
     int64_t cycle_budget;   /* per-CTA clock64 budget; when exceeded the kernels stop
                                taking work and the plan status becomes JL_ETIMEOUT;
                                0 = unlimited */

@@ -302,10 +302,17 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 cand.push_back(b->variant[g]);
                 if (b->tile_dev[g]) {
                     cand.push_back(Variant{0, 0, 256, 0});
-                    if (g == 0)
+                    if (g == 0) {
                         cand.push_back(Variant{0, 16, 256, 0});
+                        cand.push_back(Variant{0, 8, 256, 0});
+                    }
                 }
                 cand.push_back(default_variant(g, 0));
+                if (g == 1) {
+                    cand.push_back(Variant{2, 4, 256, 0});
+                    cand.push_back(Variant{4, 4, 128, 0});
+                    cand.push_back(Variant{4, 4, 256, 0});
+                }
                 float best_ms = 0.f;
                 int best = -1;
                 for (size_t ci = 0; ci < cand.size() && e == cudaSuccess; ++ci) {
