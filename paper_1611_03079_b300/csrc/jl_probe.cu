@@ -142,6 +142,28 @@ __global__ void __launch_bounds__(256) int64_probe_kernel(unsigned long long *ou
         out[blockIdx.x] = t;
 }
 
+// binary64 fused multiply-add chains, kind 9: v = fma(v, a, b), one DFMA per
+// chain step (the lane-refill kernel's steps have exact fused forms; this
+// tells the rate of that instruction against kind 1's separate DMUL + DADD).
+__global__ void __launch_bounds__(256) dfma_probe_kernel(double *out, int iters, double a, double b)
+{
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        v[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            v[k] = __fma_rn(v[k], a, b);
+    }
+    double s = v[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k)
+        s = s + v[k];
+    if (s == 12345.678)
+        out[blockIdx.x] = s;
+}
+
 }  // namespace jl
 
 using namespace jl;
@@ -149,9 +171,10 @@ using namespace jl;
 extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_per_s, double *seconds,
                              void *stream)
 {
-    if (precision < 0 || precision > 8)
+    if (precision < 0 || precision > 9)
         return fail(JL_EINVAL, "kind must be 0 (binary32), 1 (binary64), 2 (int xor+add), 3 (int mad), 4 (int mulhi), "
-                               "5 (packed binary32 pairs), 6 (int64 add), 7 (int64 shift+xor), 8 (int64 compare+select)");
+                               "5 (packed binary32 pairs), 6 (int64 add), 7 (int64 shift+xor), 8 (int64 compare+select), "
+                               "9 (binary64 fused multiply-add)");
     if (iters < 1 || !lane_ops_per_s)
         return fail(JL_EINVAL, "iters must be >= 1 and lane_ops_per_s non-NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -186,6 +209,8 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
             int64_probe_kernel<7><<<grid, threads, 0, st>>>((unsigned long long *)out, iters, 0x5ull, 7ull);
         else if (precision == 8)
             int64_probe_kernel<8><<<grid, threads, 0, st>>>((unsigned long long *)out, iters, 0x7fffffffffffull, 0x12345ull);
+        else if (precision == 9)
+            dfma_probe_kernel<<<grid, threads, 0, st>>>((double *)out, iters, 0.999, 0.001);
         else
             int_probe_kernel<4><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
         e = cudaGetLastError();
@@ -203,7 +228,8 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
         cudaEventElapsedTime(&ms, t0, t1);
         // lane ops per chain step (64-bit kinds: one 64-bit operation per step
         // for add, two shifts and an xor, a compare and a select plus the add)
-        const double per = (precision == 3 || precision == 6) ? 1.0 : (precision == 7 ? 3.0 : (precision == 8 ? 2.0 : 2.0));
+        const double per =
+            (precision == 3 || precision == 6 || precision == 9) ? 1.0 : (precision == 7 ? 3.0 : 2.0);
         const double ops = (double)grid * threads * (double)iters * 8.0 * per;
         *lane_ops_per_s = ops / (ms * 1e-3);
         if (seconds)
