@@ -621,10 +621,12 @@ def main():
         e2e = {"value": total_iters / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 96 * n,
                "d2h_bytes_per_step": int(hf.d2h_bytes), "ms_per_step": e2e_s * 1e3, "steps": len(times),
                "counts_match_device": bool(ok),
-               "note": "host plan (jl_host_plan_run): 16 frames per step rendered on 6 internal streams into "
-                       "device slots and copied to pinned host memory (counts + RGBA8) as each frame "
-                       "finishes; host wall clock per call (median of steps), the call returns after the "
-                       "last copy; h2d = the frame descriptions (96 B each)"}
+               "launches_per_step": hf.launches(),
+               "note": "host plan (jl_host_plan_run): 16 frames per step rendered on 4 internal render "
+                       "streams into one device slot each (the last frame as 4 row bands) and copied to "
+                       "pinned host memory (counts + RGBA8) on 2 copy streams as each frame (band) finishes; "
+                       "host wall clock per call (median of steps), the call returns after the last copy; "
+                       "h2d = the frame descriptions (96 B each)"}
 
     cpu = None
     if not args.no_cpu and rank == 0:

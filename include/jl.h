@@ -327,15 +327,18 @@ int jl_render_batch(const jl_frame *frames, int32_t n, void *counts_base, uint8_
  * Render n frames into HOST memory with the device-to-host copies overlapped
  * with rendering.  Frames as in jl_batch_create (offsets in bytes from the
  * host base pointers, -1 = no such output; counts_host / rgba_host /
- * hist_host may be NULL when no frame uses them).  Frame i renders on
- * internal stream i mod depth into a device slot of that stream and is
- * copied out on the same stream, so up to `depth` frames are in flight
- * (depth 0 = 6; 1..8).  The host buffers should be pinned (page-locked) for
- * the copies to overlap; pageable memory works but serialises.  Work queued
- * earlier on `stream` is waited for; the call returns when every copy has
- * completed (synchronous).  The library allocates depth slots of the largest
- * frame's outputs for the duration of the call.  Errors: as jl_batch_create
- * for the frame descriptions; JL_ECUDA / JL_ENOMEM from the device.
+ * hist_host may be NULL when no frame uses them).  Renders and copies run
+ * on separate internal streams (up to 4 render and 2 copy streams): frame i
+ * renders into device slot i mod depth and is copied out as soon as its
+ * render is done, while later frames render; a render waits for a copy only
+ * to reuse a slot.  `depth` = device slots, 1..64, or 0 for the default (one
+ * slot per frame up to 16 frames, at most 4 GiB of slots).  The host buffers
+ * should be pinned (page-locked) for the copies to overlap; pageable memory
+ * works but serialises.  Work queued earlier on `stream` is waited for; the
+ * call returns when every copy has completed (synchronous).  The library
+ * allocates `depth` slots of the largest frame's outputs for the duration of
+ * the call.  Errors: as jl_batch_create for the frame descriptions;
+ * JL_EINVAL for a depth outside 0..64; JL_ECUDA / JL_ENOMEM from the device.
  */
 int jl_render_frames_to_host(const jl_frame *frames, int32_t n, void *counts_host, uint8_t *rgba_host,
                              float *hist_host, const uint8_t *palette, int32_t depth, void *stream);
@@ -343,7 +346,7 @@ int jl_render_frames_to_host(const jl_frame *frames, int32_t n, void *counts_hos
 /*
  * The same as a reusable plan: jl_host_plan_create validates the frames and
  * does the once-per-frame-set work (coordinate tables of every frame, `depth`
- * device slots, internal streams); jl_host_plan_run renders every frame into
+ * device slots, internal streams and events); jl_host_plan_run renders every frame into
  * the host buffers given at creation (which must stay valid while the plan
  * lives), with the copies overlapped, and returns when the last copy has
  * completed.  Runs on the device current at creation (JL_EINVAL otherwise).
@@ -355,6 +358,11 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
                         const uint8_t *palette, int32_t depth, jl_host_plan **out);
 int jl_host_plan_run(jl_host_plan *plan, void *stream);
 void jl_host_plan_destroy(jl_host_plan *plan);
+/* Escape-kernel launches per run: one per frame, plus the row bands of the
+ * last frame (a last frame without a histogram whose counts + RGBA reach
+ * 8 MB renders as bands of about 8 MB, at most 4, each a multiple of 32 rows,
+ * copied out band by band).  -1 for a NULL plan. */
+int32_t jl_host_plan_launches(const jl_host_plan *plan);
 
 /* ------------------------------------------------------------------------
  * Autotuner of the escape kernel's launch shape.

@@ -238,7 +238,7 @@ def _layout(frames):
 class HostFrames:
     """Frames rendered into (pinned) host memory through a host plan
     (jl_host_plan_*): copies to the host overlap with rendering, `depth`
-    frames in flight.  `frames` as for Batch.  The host buffers are allocated
+    device output slots (0 = one per frame up to 16).  `frames` as for Batch.  The host buffers are allocated
     once (page-locked through torch) and the plan (coordinate tables, device
     slots, streams) once; every render() call renders all frames again.
     counts(i), rgba(i) and hist(i) return numpy views of frame i."""
@@ -266,6 +266,10 @@ class HostFrames:
         import torch
         st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
         check(self._L.jl_host_plan_run(self._h, st))
+
+    def launches(self):
+        """Escape-kernel launches per render(): frames plus the last frame's row bands."""
+        return int(self._L.jl_host_plan_launches(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -75,6 +75,7 @@ SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "jl_host_plan_run": (ctypes.c_int, [_vp, _vp]),
     "jl_host_plan_destroy": (None, [_vp]),
+    "jl_host_plan_launches": (_i32, [_vp]),
     "jl_render_map": (ctypes.c_int, [ctypes.POINTER(Map), _d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp,
                                      _vp, _vp, _vp, _vp]),
     "jl_render_variant": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,

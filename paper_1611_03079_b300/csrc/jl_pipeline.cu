@@ -2,17 +2,25 @@
 // overlapped with rendering (jl_host_plan_*, jl_render_frames_to_host).
 //
 // Rendering a frame and copying its counts and colours to the host are both
-// long for large frames (a 4096^2 frame is 100 MB of output).  Done one frame
-// after the other, the copy time adds to the render time.  Here frame i is
-// rendered on internal stream i mod D into device slot i mod D and copied out
-// on the same stream, so up to D frames are in flight: copies of one frame
-// run while the next frames render, and frames on different streams may also
-// render side by side.  Stream order alone makes slot reuse safe (frame i + D
-// is queued on the same stream after frame i's copies).
+// long for large frames (a 4096^2 frame is 96 MB of output, 1.7 ms over a
+// 57 GB/s link).  Done one frame after the other, the copy time adds to the
+// render time.  Here the renders and the copies run on separate internal
+// streams: frame i renders on render stream i mod R into device slot
+// i mod S and is copied out on copy stream i mod C once an event says its
+// render is done.  A render never waits for a copy except to reuse a slot
+// (frame i + S waits for frame i's copy), so with as many slots as frames
+// the renders follow one another as closely as a single batched launch while
+// the copy engine drains finished frames behind them; only the last frame's
+// copy is left outside the rendering.  Several render streams let the next
+// frame's blocks fill the SMs that the tail of the previous frame leaves idle.
+// The last frame is rendered as row bands (launches over row ranges of the
+// frame, sharing its coordinate tables, so every pixel gets the coordinates
+// of the whole frame) spread over the render streams, each band copied out
+// when it is done: what remains outside the rendering is the last band's copy.
 //
 // A plan does the once-per-frame-set work at creation: validation, the
-// coordinate tables of every frame, the device slots and the streams.  A run
-// then only launches the escape kernels and the copies.
+// coordinate tables of every frame, the device slots, streams and events.  A
+// run then only launches the escape kernels and the copies.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -28,9 +36,16 @@ int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStre
 
 using namespace jl;
 
+// One launch of the plan: rows [row0, row0 + rows) of frame `frame`, with
+// its own control block (work counter and status word) at ctl_off.
+struct Unit {
+    int frame, row0, rows;
+    size_t ctl_off;
+};
+
 struct jl_host_plan {
     int device = 0;
-    int n = 0, depth = 0;
+    int n = 0, depth = 0;  // depth = device slots (frames whose outputs may be on the device at once)
     std::vector<Frame> F;
     std::vector<int> prec;
     std::vector<size_t> cbytes, rbytes, hbytes, ctl_off;
@@ -40,7 +55,10 @@ struct jl_host_plan {
     float *hist_host = nullptr;
     uint8_t palette[1024];
     bool has_palette = false;
-    std::vector<cudaStream_t> st;
+    std::vector<Unit> units;                  // launches in order: whole frames, then the last frame's bands
+    std::vector<cudaStream_t> rs, cs;         // render streams, copy streams
+    std::vector<cudaEvent_t> rendered;        // per unit: its render is done
+    std::vector<cudaEvent_t> copied;          // per slot: the last copy out of it
     cudaEvent_t fork = nullptr;
     void *slots = nullptr;
     size_t slot_bytes = 0;
@@ -49,15 +67,36 @@ struct jl_host_plan {
 
 static size_t pad256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// At most this many render and copy streams.  Together they stay within the
+// device's default 8 hardware work queues, so no stream shares a queue (and a
+// false dependency) with another.  Four render streams were the fastest of
+// 2, 3, 4 and 6 on the 16-frame 4096^2 sweep (each fills the tail of one
+// launch with the next).
+static constexpr int kRenderStreams = 4, kCopyStreams = 2;
+// The last frame is split into row bands when its outputs (counts + RGBA,
+// no histogram) reach kBandMinBytes: bands of about kBandBytes, at most
+// kMaxBands, each a multiple of 32 rows (whole 32 x 32 tiles).  Four bands
+// beat one and eight on the sweep: more bands add launch tails.
+static constexpr size_t kBandMinBytes = (size_t)8 << 20, kBandBytes = (size_t)8 << 20;
+static constexpr int kMaxBands = 4;
+// Default slot count: one per frame up to 16, and at most 4 GiB of slots.
+static constexpr int kDefaultSlots = 16;
+static constexpr size_t kDefaultSlotBudget = (size_t)4 << 30;
+
 static void destroy_host_plan(jl_host_plan *p)
 {
     if (!p)
         return;
-    for (cudaStream_t s : p->st)
-        if (s) {
-            cudaStreamSynchronize(s);
-            cudaStreamDestroy(s);
-        }
+    for (auto *v : {&p->rs, &p->cs})
+        for (cudaStream_t s : *v)
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+    for (auto *v : {&p->rendered, &p->copied})
+        for (cudaEvent_t e : *v)
+            if (e)
+                cudaEventDestroy(e);
     if (p->fork)
         cudaEventDestroy(p->fork);
     cudaFree(p->slots);
@@ -75,13 +114,10 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
     *out = nullptr;
     if (!frames || n < 1)
         return fail(JL_EINVAL, "frames must be non-NULL and n >= 1");
-    if (depth == 0)
-        depth = 6;
-    if (depth < 1 || depth > 8)
-        return fail(JL_EINVAL, "depth must be 0 (default 6) or 1..8");
+    if (depth < 0 || depth > 64)
+        return fail(JL_EINVAL, "depth must be 0 (default) or 1..64");
     jl_host_plan *p = new jl_host_plan();
     p->n = n;
-    p->depth = depth > n ? n : depth;
     p->counts_host = counts_host;
     p->rgba_host = rgba_host;
     p->hist_host = hist_host;
@@ -130,16 +166,47 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
         p->ctl_off[(size_t)i] = table_bytes;
         table_bytes += 256;
     }
+    // launches: every frame whole, the last one in row bands (see kBandBytes)
+    for (int i = 0; i < n; ++i)
+        if (i < n - 1 || p->hbytes[(size_t)i] || p->cbytes[(size_t)i] + p->rbytes[(size_t)i] < kBandMinBytes) {
+            p->units.push_back(Unit{i, 0, p->F[(size_t)i].H, p->ctl_off[(size_t)i]});
+        } else {
+            const Frame &F = p->F[(size_t)i];
+            const size_t bytes = p->cbytes[(size_t)i] + p->rbytes[(size_t)i];
+            int bands = (int)((bytes + kBandBytes - 1) / kBandBytes);
+            bands = bands > kMaxBands ? kMaxBands : bands;
+            int rows = (F.H + bands - 1) / bands;
+            rows = (rows + 31) & ~31;
+            for (int r0 = 0; r0 < F.H; r0 += rows) {
+                const size_t ctl = r0 == 0 ? p->ctl_off[(size_t)i] : table_bytes;
+                if (r0 > 0)
+                    table_bytes += 256;
+                p->units.push_back(Unit{i, r0, F.H - r0 < rows ? F.H - r0 : rows, ctl});
+            }
+        }
     p->slot_bytes = slot_bytes;
+    if (depth == 0) {
+        size_t fit = kDefaultSlotBudget / slot_bytes;
+        depth = (int)(fit < (size_t)kDefaultSlots ? (fit < 1 ? 1 : fit) : kDefaultSlots);
+    }
+    p->depth = depth > n ? n : depth;
+    const int nr = n < kRenderStreams ? n : kRenderStreams, nc = n < kCopyStreams ? n : kCopyStreams;
     int rc = JL_OK;
     cudaError_t e = cudaGetDevice(&p->device);
     do {
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaGetDevice"); break; }
-        p->st.assign((size_t)p->depth, nullptr);
-        for (int s = 0; s < p->depth; ++s) {
-            e = cudaStreamCreateWithFlags(&p->st[(size_t)s], cudaStreamNonBlocking);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamCreate"); break; }
-        }
+        p->rs.assign((size_t)nr, nullptr);
+        p->cs.assign((size_t)nc, nullptr);
+        for (auto *v : {&p->rs, &p->cs})
+            for (cudaStream_t &s : *v)
+                if (rc == JL_OK && (e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+                    rc = cuda_fail(e, "cudaStreamCreate");
+        p->rendered.assign(p->units.size(), nullptr);
+        p->copied.assign((size_t)p->depth, nullptr);
+        for (auto *v : {&p->rendered, &p->copied})
+            for (cudaEvent_t &ev : *v)
+                if (rc == JL_OK && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                    rc = cuda_fail(e, "cudaEventCreate");
         if (rc != JL_OK)
             break;
         e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
@@ -155,13 +222,13 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
             uint8_t *base = static_cast<uint8_t *>(p->tables) + table_off[(size_t)i];
             F.xs = base;
             F.ys = base + (size_t)F.W * esz;
-            e = launch_coords(nullptr, &F, 1, p->st[0]);
+            e = launch_coords(nullptr, &F, 1, p->rs[0]);
             if (e != cudaSuccess)
                 rc = cuda_fail(e, "coords kernel launch");
         }
         if (rc != JL_OK)
             break;
-        e = cudaStreamSynchronize(p->st[0]);
+        e = cudaStreamSynchronize(p->rs[0]);
         if (e != cudaSuccess) { rc = cuda_fail(e, "coordinate tables"); break; }
     } while (0);
     if (rc != JL_OK) {
@@ -183,47 +250,90 @@ int jl_host_plan_run(jl_host_plan *p, void *stream)
     int rc = JL_OK;
     // work already queued on the caller's stream comes first
     cudaError_t e = cudaEventRecord(p->fork, user);
-    for (int s = 0; s < p->depth && e == cudaSuccess; ++s)
-        e = cudaStreamWaitEvent(p->st[(size_t)s], p->fork, 0);
+    for (auto *v : {&p->rs, &p->cs})
+        for (cudaStream_t s : *v)
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(s, p->fork, 0);
     if (e != cudaSuccess)
         rc = cuda_fail(e, "stream fork");
     const uint8_t *pal = p->has_palette ? p->palette : nullptr;
-    for (int i = 0; i < p->n && rc == JL_OK; ++i) {
-        const size_t k = (size_t)i;
-        Frame F = p->F[k];
-        cudaStream_t s = p->st[(size_t)(i % p->depth)];
-        uint8_t *b = static_cast<uint8_t *>(p->slots) + p->slot_bytes * (size_t)(i % p->depth);
-        F.counts = p->cbytes[k] ? b : nullptr;
-        F.rgba = p->rbytes[k] ? reinterpret_cast<uint32_t *>(b + pad256(p->cbytes[k])) : nullptr;
-        F.hist_bins = p->hbytes[k] ? reinterpret_cast<uint32_t *>(b + pad256(p->cbytes[k]) + pad256(p->rbytes[k]))
-                                   : nullptr;
-        rc = launch_frame(F, p->prec[k], pal, static_cast<uint8_t *>(p->tables) + p->ctl_off[k], s, nullptr);
-        if (rc != JL_OK)
-            break;
-        if (p->cbytes[k]) {
-            e = cudaMemcpyAsync(static_cast<uint8_t *>(p->counts_host) + p->coff[k], F.counts, p->cbytes[k],
-                                cudaMemcpyDeviceToHost, s);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(counts)"); break; }
+    const size_t nr = p->rs.size(), nc = p->cs.size();
+    for (size_t u0 = 0; u0 < p->units.size() && rc == JL_OK;) {
+        // the units of one frame: [u0, u1)
+        const size_t k = (size_t)p->units[u0].frame, slot = k % (size_t)p->depth;
+        size_t u1 = u0 + 1;
+        while (u1 < p->units.size() && (size_t)p->units[u1].frame == k)
+            ++u1;
+        const Frame &F0 = p->F[k];
+        const size_t csz = F0.count_type == JL_COUNT_U8 ? 1 : 2, esz = p->prec[k] == JL_FP64 ? 8 : 4;
+        uint8_t *b = static_cast<uint8_t *>(p->slots) + p->slot_bytes * slot;
+        uint8_t *cnt = p->cbytes[k] ? b : nullptr;
+        uint32_t *rgba = p->rbytes[k] ? reinterpret_cast<uint32_t *>(b + pad256(p->cbytes[k])) : nullptr;
+        uint32_t *bins = p->hbytes[k] ? reinterpret_cast<uint32_t *>(b + pad256(p->cbytes[k]) + pad256(p->rbytes[k]))
+                                      : nullptr;
+        cudaStream_t c = p->cs[k % nc];
+        for (size_t u = u0; u < u1 && rc == JL_OK; ++u) {
+            const Unit &U = p->units[u];
+            cudaStream_t r = p->rs[u % nr];
+            // the slot's previous frame (k - depth) must be copied out first
+            if (k >= (size_t)p->depth && (e = cudaStreamWaitEvent(r, p->copied[slot], 0)) != cudaSuccess) {
+                rc = cuda_fail(e, "cudaStreamWaitEvent(slot copied)");
+                break;
+            }
+            Frame F = F0;
+            const size_t pix0 = (size_t)U.row0 * (size_t)F0.W;
+            F.counts = cnt ? cnt + pix0 * csz : nullptr;
+            F.rgba = rgba ? rgba + pix0 : nullptr;
+            F.hist_bins = bins;  // only whole frames carry a histogram
+            if (U.rows != F0.H) {
+                F.H = U.rows;
+                F.ys = static_cast<const uint8_t *>(F0.ys) + (size_t)U.row0 * esz;
+                F.chunk_count = F0.rows_per_chunk > 1 ? (U.rows + F0.rows_per_chunk - 1) / F0.rows_per_chunk
+                                                      : U.rows * F0.chunks_per_row;
+                F.tile_count = F0.tiles_x * ((U.rows + 31) / 32);
+            }
+            rc = launch_frame(F, p->prec[k], pal, static_cast<uint8_t *>(p->tables) + U.ctl_off, r, nullptr);
+            if (rc != JL_OK)
+                break;
+            if ((e = cudaEventRecord(p->rendered[u], r)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(c, p->rendered[u], 0)) != cudaSuccess) {
+                rc = cuda_fail(e, "render -> copy event");
+                break;
+            }
+            const size_t npx = (size_t)U.rows * (size_t)F0.W;
+            if (cnt) {
+                e = cudaMemcpyAsync(static_cast<uint8_t *>(p->counts_host) + p->coff[k] + pix0 * csz, F.counts,
+                                    npx * csz, cudaMemcpyDeviceToHost, c);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(counts)"); break; }
+            }
+            if (rgba) {
+                e = cudaMemcpyAsync(p->rgba_host + p->roff[k] + pix0 * 4, F.rgba, npx * 4, cudaMemcpyDeviceToHost, c);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(rgba)"); break; }
+            }
+            if (bins) {
+                e = cudaMemcpyAsync(reinterpret_cast<uint8_t *>(p->hist_host) + p->hoff[k], bins, p->hbytes[k],
+                                    cudaMemcpyDeviceToHost, c);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(hist)"); break; }
+            }
         }
-        if (p->rbytes[k]) {
-            e = cudaMemcpyAsync(p->rgba_host + p->roff[k], F.rgba, p->rbytes[k], cudaMemcpyDeviceToHost, s);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(rgba)"); break; }
-        }
-        if (p->hbytes[k]) {
-            e = cudaMemcpyAsync(reinterpret_cast<uint8_t *>(p->hist_host) + p->hoff[k], F.hist_bins, p->hbytes[k],
-                                cudaMemcpyDeviceToHost, s);
-            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpyAsync(hist)"); break; }
-        }
+        if (rc == JL_OK && (e = cudaEventRecord(p->copied[slot], c)) != cudaSuccess)
+            rc = cuda_fail(e, "cudaEventRecord(slot copied)");
+        u0 = u1;
     }
-    for (int s = 0; s < p->depth; ++s) {
-        cudaError_t e2 = cudaStreamSynchronize(p->st[(size_t)s]);
-        if (rc == JL_OK && e2 != cudaSuccess)
-            rc = cuda_fail(e2, "cudaStreamSynchronize");
-    }
+    // every stream is drained before returning, also after an error, so that
+    // no copy into the caller's buffers is still running when the call returns
+    for (auto *v : {&p->rs, &p->cs})
+        for (cudaStream_t s : *v) {
+            cudaError_t e2 = cudaStreamSynchronize(s);
+            if (rc == JL_OK && e2 != cudaSuccess)
+                rc = cuda_fail(e2, "cudaStreamSynchronize");
+        }
     return rc;
 }
 
 void jl_host_plan_destroy(jl_host_plan *p) { destroy_host_plan(p); }
+
+int32_t jl_host_plan_launches(const jl_host_plan *p) { return p ? (int32_t)p->units.size() : -1; }
 
 int jl_render_frames_to_host(const jl_frame *frames, int32_t n, void *counts_host, uint8_t *rgba_host,
                              float *hist_host, const uint8_t *palette, int32_t depth, void *stream)
