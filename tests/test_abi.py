@@ -178,3 +178,22 @@ def test_render_map_validation(L):
     assert _map_call(L, bad) == _lib.JL_EINVAL and "degrees" in L.jl_last_error().decode()
     assert L.jl_render_map(None, 0.0, 0.0, _lib.Rect(-1, 1, -1, 1), 4, 4, 10, 0, 0, 2, 1, None, None, None,
                            None) == _lib.JL_EINVAL
+
+
+def test_host_plan_validation(L):
+    """Host plans reject bad depths and frames on the host, before any device
+    use; the launch count of a NULL plan is -1."""
+    f = _lib.Frame(0.0, 0.0, _lib.Rect(-2, 2, -2, 2), 16, 16, 100, 0, 0, 2, 0, -1, -1)
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(1024)
+    for depth in (-1, 65):
+        rc = L.jl_host_plan_create(ctypes.byref(f), 1, buf, None, None, None, depth, ctypes.byref(h))
+        assert rc == _lib.JL_EINVAL and b"depth" in L.jl_last_error(), depth
+        assert not h.value
+    rc = L.jl_host_plan_create(ctypes.byref(f), 0, buf, None, None, None, 0, ctypes.byref(h))
+    assert rc == _lib.JL_EINVAL
+    # counts offset given but no base pointer
+    rc = L.jl_host_plan_create(ctypes.byref(f), 1, None, None, None, None, 0, ctypes.byref(h))
+    assert rc == _lib.JL_EINVAL and b"base pointer" in L.jl_last_error()
+    assert L.jl_host_plan_run(None, None) == _lib.JL_EINVAL
+    assert L.jl_host_plan_launches(None) == -1
