@@ -593,9 +593,16 @@ def main():
         sp.close()
     dom = max((0, 1), key=lambda p: by_prec[p]["time_ms"])
     d = by_prec[dom]
+    # DRAM bytes (read + write) of one launch of each precision's plan, from the
+    # ncu capture of the same launch in profiles/escape_kernel_sweep4096.md
+    traffic = {1: 8481792 + 751060736, 0: 31006976 + 780272384} if args.size == 4096 else {}
     roofline = {"bound": "alu", "kernel": "escape_kernel<%s>" % ("double" if dom else "float"),
                 "achieved": d["achieved_gops"], "peak": d["peak_gops"], "unit": "Gop/s",
-                "frac": d["frac"], "traffic": None,
+                "frac": d["frac"], "traffic": traffic.get(dom),
+                "traffic_note": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of "
+                                "this plan launch, profiles/escape_kernel_sweep4096.md); algorithmic bytes per "
+                                "launch: %d (uint16 count + RGBA8 per pixel)" % (6 * sum(
+                                    frames[i]["W"] * frames[i]["H"] for i in sub[dom])),
                 "peak_source": "measured on this GPU by jl_probe_peak (independent multiply/add chains, no FMA; "
                                "binary32: the larger of scalar FMUL/FADD, %.0f G lane-ops/s, and packed "
                                "add/mul.f32x2, %.0f)" % (probes[0] / 1e9, probes[5] / 1e9),
@@ -603,7 +610,8 @@ def main():
                 "timing": "CUDA events around a plan of the %s sweep frames alone" % ("binary64" if dom else
                                                                                     "binary32")}
     roofline_other = {"precision": "binary32" if dom else "binary64", "achieved": by_prec[1 - dom]["achieved_gops"],
-                      "peak": by_prec[1 - dom]["peak_gops"], "unit": "Gop/s", "frac": by_prec[1 - dom]["frac"]}
+                      "peak": by_prec[1 - dom]["peak_gops"], "unit": "Gop/s", "frac": by_prec[1 - dom]["frac"],
+                      "traffic": traffic.get(1 - dom)}
 
     e2e = None
     if not args.no_e2e and rank == 0:

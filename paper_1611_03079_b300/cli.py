@@ -3,6 +3,7 @@
   python -m paper_1611_03079_b300.cli --workload sweep --index 13 --size 2048 --repeat 3
   python -m paper_1611_03079_b300.cli --c -0.8+0.156j --rect -2 2 -2 2 --W 512 --H 512 --out f.npy
   python -m paper_1611_03079_b300.cli --workload forward --n 1048576 --repeat 3
+  python -m paper_1611_03079_b300.cli --workload sweep-plan --precision fp64 --repeat 3
 
 Renders one frame `repeat` times on cuda:0 and prints the kernel-bracketed
 time and pixel-iterations per second; optionally saves counts (.npy).  Also
@@ -16,7 +17,7 @@ import numpy as np
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--workload", choices=["sweep", "single", "path", "forward"], default=None)
+    p.add_argument("--workload", choices=["sweep", "sweep-plan", "single", "path", "forward"], default=None)
     p.add_argument("--n", type=int, default=1 << 20, help="forward workload: number of C values screened")
     p.add_argument("--frames", type=int, default=72, help="path workload: first N frames as one batch plan")
     p.add_argument("--index", type=int, default=0)
@@ -45,6 +46,8 @@ def main(argv=None):
         return path(a)
     if a.workload == "forward":
         return forward(a)
+    if a.workload == "sweep-plan":
+        return sweep_plan(a)
     if a.workload == "sweep":
         f = wl.throughput_sweep(a.size)[a.index]
     elif a.workload == "single":
@@ -70,6 +73,35 @@ def main(argv=None):
                       "best_ms": best, "giter_s": iters / (best * 1e-3) / 1e9, "iterations": iters}))
     if a.out:
         np.save(a.out, out["counts"].view(torch.int16).cpu().numpy().view(np.uint16))
+
+
+def sweep_plan(a):
+    """The throughput-sweep frames of one precision (--precision fp32 / fp64)
+    as one batch plan with uint16 counts and RGBA8, launched `repeat` times:
+    the launch whose kernel the benchmark's roofline reports."""
+    import torch
+
+    import paper_1611_03079_b300 as jl
+    from paper_1611_03079_b300 import workloads as wl
+    torch.cuda.set_device(0)
+    prec = {"fp32": 0, "fp64": 1}[a.precision]
+    frames = [dict(f, count_type="u16", rgba=True) for f in wl.throughput_sweep(a.size) if f["precision"] == prec]
+    variants = {a.precision: tuple(a.variant)} if a.variant else None
+    b = jl.Batch(frames, palette=wl.random_palette(7), variants=variants)
+    times = []
+    for _ in range(a.repeat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    iters = sum(int((b.counts(i).to(torch.int32) & 0xFFFF).to(torch.int64).sum().item()) for i in range(len(frames)))
+    pix = sum(f["W"] * f["H"] for f in frames)
+    print(json.dumps({"frames": len(frames), "pixels": pix, "output_bytes": 6 * pix, "iterations": iters,
+                      "ms": times, "best_ms": min(times), "giter_s": iters / (min(times) * 1e-3) / 1e9,
+                      "variant": list(b.variant(prec)), "status": b.status()}))
+    b.close()
 
 
 def path(a):
