@@ -156,7 +156,10 @@ int jl_variant_list(int32_t precision, int32_t *pairs, int32_t cap);
  * lane operations per instruction; no product feeds a sum); kinds 6, 7, 8:
  * 64-bit integer add, shift-and-xor (3 operations), compare-and-select
  * (2 operations) chains; kind 9: binary64 fused multiply-add chains (one
- * DFMA per step; compare with kind 1).  Returns the
+ * DFMA per step; compare with kind 1); kinds 10, 11: two chains per thread
+ * of the binary64 escape step as the lane-refill kernel forms it (six
+ * binary64 operations per step, counted as the lane operations), kind 11
+ * with that kernel's per-step binary32 test work.  Returns the
  * achieved lane operations per second in *lane_ops_per_s (and the kernel
  * time in *seconds if non-NULL).  Kinds 0 and 1 are the denominators of the
  * escape kernels' ALU roofline.  Synchronises `stream`.

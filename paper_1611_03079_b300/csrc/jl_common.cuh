@@ -25,6 +25,18 @@ __device__ __forceinline__ double dbl2(double x)
     return __longlong_as_double((long long)r);
 }
 
+// Binary32 estimate of a non-negative binary64 value from its high word,
+// truncated (never above the true value, relative error < 2^-20); 0 below
+// 2^-126, +inf at or above 2^128.
+__device__ __forceinline__ float hi_estimate(double v)
+{
+    int h = __double2hiint(v) & 0x7fffffff;
+    h -= 0x38000000;                 // rebias exponent 1023 -> 127
+    h = max(h, 0);
+    h = min(h, 0x0ff00000);          // exponent 255 -> +inf
+    return __int_as_float(h << 3);
+}
+
 // Integer quotient (n * 255) / d for n <= d <= 65535 via a 40-bit reciprocal:
 // m = floor(2^40 / d) + 1 gives floor(n*255*m / 2^40) == floor(n*255 / d)
 // because the excess n*255*(m - 2^40/d)/2^40 < 2^-16 < 1/d.

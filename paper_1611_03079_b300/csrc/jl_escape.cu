@@ -204,18 +204,6 @@ __device__ __forceinline__ bool in_unsafe_band(float cr, float ci)
     return m > 3.99f && m < 4.01f;
 }
 
-// Binary32 estimate of a non-negative binary64 value from its high word,
-// truncated (never above the true value, relative error < 2^-20); 0 below
-// 2^-126, +inf at or above 2^128.
-__device__ __forceinline__ float hi_estimate(double v)
-{
-    int h = __double2hiint(v) & 0x7fffffff;
-    h -= 0x38000000;                 // rebias exponent 1023 -> 127
-    h = max(h, 0);
-    h = min(h, 0x0ff00000);          // exponent 255 -> +inf
-    return __int_as_float(h << 3);
-}
-
 // ---------------------------------------------------------------------------
 // The persistent escape kernel.
 // ---------------------------------------------------------------------------

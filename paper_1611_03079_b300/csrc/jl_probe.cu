@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "jl_common.cuh"
 #include "jl_internal.h"
 
 namespace jl {
@@ -164,6 +165,44 @@ __global__ void __launch_bounds__(256) dfma_probe_kernel(double *out, int iters,
         out[blockIdx.x] = s;
 }
 
+// binary64 escape steps, kinds 10 and 11: two independent chains per thread
+// (as the lane-refill kernel's two pixel slots) of Z <- Z^2 + C formed as
+// that kernel forms them: products x*x, y*y and (2x)*y, sums (x2 - y2) + cr
+// and t + ci, 2x on the integer pipe (dbl2); six binary64 lane operations per
+// step.  Kind 11 adds the kernel's per-step binary32 estimate of |Z|^2 and its
+// counters.  No refill, service or stores: the step's own ceiling.  C in the
+// main cardioid keeps every orbit bounded (and away from subnormals).
+template <bool TEST>
+__global__ void __launch_bounds__(256) escape_step_probe_kernel(double *out, int iters, double cr, double ci)
+{
+    double x[2], y[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        x[k] = (double)(threadIdx.x + 7 * k) * 1e-4;
+        y[k] = (double)(blockIdx.x & 255) * 1e-4 + k * 1e-3;
+    }
+    int cnt = 0;
+    bool amb = false;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const double x2 = __dmul_rn(x[k], x[k]);
+            const double y2 = __dmul_rn(y[k], y[k]);
+            if constexpr (TEST) {
+                const float r32 = __fadd_rn(hi_estimate(x2), hi_estimate(y2));
+                cnt += (r32 < 3.9999847412109375f) ? 1 : 0;
+                amb |= (r32 >= 3.9999847412109375f) & (r32 <= 4.0000152587890625f);
+            }
+            const double t = __dmul_rn(dbl2(x[k]), y[k]);
+            y[k] = __dadd_rn(t, ci);
+            x[k] = __dadd_rn(__dsub_rn(x2, y2), cr);
+        }
+    }
+    const double s = __dadd_rn(__dadd_rn(x[0], x[1]), __dadd_rn(y[0], y[1]));
+    if (s == 12345.678 || cnt == 7 || amb)  // practically never; keeps the chains live
+        out[blockIdx.x] = s + cnt;
+}
+
 }  // namespace jl
 
 using namespace jl;
@@ -171,10 +210,11 @@ using namespace jl;
 extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_per_s, double *seconds,
                              void *stream)
 {
-    if (precision < 0 || precision > 9)
+    if (precision < 0 || precision > 11)
         return fail(JL_EINVAL, "kind must be 0 (binary32), 1 (binary64), 2 (int xor+add), 3 (int mad), 4 (int mulhi), "
                                "5 (packed binary32 pairs), 6 (int64 add), 7 (int64 shift+xor), 8 (int64 compare+select), "
-                               "9 (binary64 fused multiply-add)");
+                               "9 (binary64 fused multiply-add), 10 (binary64 escape step), "
+                               "11 (binary64 escape step with the binary32 test)");
     if (iters < 1 || !lane_ops_per_s)
         return fail(JL_EINVAL, "iters must be >= 1 and lane_ops_per_s non-NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -211,6 +251,10 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
             int64_probe_kernel<8><<<grid, threads, 0, st>>>((unsigned long long *)out, iters, 0x7fffffffffffull, 0x12345ull);
         else if (precision == 9)
             dfma_probe_kernel<<<grid, threads, 0, st>>>((double *)out, iters, 0.999, 0.001);
+        else if (precision == 10)
+            escape_step_probe_kernel<false><<<grid, threads, 0, st>>>((double *)out, iters, -0.1, 0.1);
+        else if (precision == 11)
+            escape_step_probe_kernel<true><<<grid, threads, 0, st>>>((double *)out, iters, -0.1, 0.1);
         else
             int_probe_kernel<4><<<grid, threads, 0, st>>>((uint32_t *)out, iters, 0x5bd1e995u, 0x1b873593u);
         e = cudaGetLastError();
@@ -228,9 +272,11 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
         cudaEventElapsedTime(&ms, t0, t1);
         // lane ops per chain step (64-bit kinds: one 64-bit operation per step
         // for add, two shifts and an xor, a compare and a select plus the add)
+        // (escape steps: two chains of six binary64 operations per step)
         const double per =
             (precision == 3 || precision == 6 || precision == 9) ? 1.0 : (precision == 7 ? 3.0 : 2.0);
-        const double ops = (double)grid * threads * (double)iters * 8.0 * per;
+        const double chains_x_per = precision >= 10 ? 2.0 * 6.0 : 8.0 * per;
+        const double ops = (double)grid * threads * (double)iters * chains_x_per;
         *lane_ops_per_s = ops / (ms * 1e-3);
         if (seconds)
             *seconds = ms * 1e-3;
