@@ -159,7 +159,9 @@ int jl_variant_list(int32_t precision, int32_t *pairs, int32_t cap);
  * DFMA per step; compare with kind 1); kinds 10, 11: two chains per thread
  * of the binary64 escape step as the lane-refill kernel forms it (six
  * binary64 operations per step, counted as the lane operations), kind 11
- * with that kernel's per-step binary32 test work.  Returns the
+ * with that kernel's per-step binary32 test work; kinds 12, 13: kind 10 with
+ * two or three CTAs of 256 threads per SM (4 or 6 warps per scheduler; the
+ * others run 8 CTAs per SM, as many as fit).  Returns the
  * achieved lane operations per second in *lane_ops_per_s (and the kernel
  * time in *seconds if non-NULL).  Kinds 0 and 1 are the denominators of the
  * escape kernels' ALU roofline.  Synchronises `stream`.

@@ -164,11 +164,14 @@ def probe():
     names = {0: "binary32 fmul+fadd", 1: "binary64 dmul+dadd", 2: "int32 xor+add", 3: "int32 mad",
              4: "int32 mulhi+xor", 5: "binary32x2 packed add / mul chains", 6: "int64 add",
              7: "int64 shift+xor", 8: "int64 compare+select", 9: "binary64 fused multiply-add",
-             10: "binary64 escape step (6 ops)", 11: "binary64 escape step (6 ops) with the binary32 test"}
+             10: "binary64 escape step (6 ops)", 11: "binary64 escape step (6 ops) with the binary32 test",
+             12: "binary64 escape step (6 ops), 4 warps per scheduler",
+             13: "binary64 escape step (6 ops), 6 warps per scheduler"}
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     res = {}
     for kind, iters in ((0, 200000), (1, 4000), (2, 200000), (3, 200000), (4, 100000), (5, 200000), (6, 20000),
-                        (7, 20000), (8, 20000), (9, 8000), (10, 2000), (11, 2000)):
+                        (7, 20000), (8, 20000), (9, 8000), (10, 2000), (11, 2000), (12, 8000),
+                        (13, 6000)):
         ops, secs = ctypes.c_double(0), ctypes.c_double(0)
         _lib.check(L.jl_probe_peak(kind, iters, ctypes.byref(ops), ctypes.byref(secs), None))
         res[names[kind]] = {"G_lane_ops_s": ops.value / 1e9, "ms": secs.value * 1e3,

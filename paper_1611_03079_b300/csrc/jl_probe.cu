@@ -210,11 +210,12 @@ using namespace jl;
 extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_per_s, double *seconds,
                              void *stream)
 {
-    if (precision < 0 || precision > 11)
+    if (precision < 0 || precision > 13)
         return fail(JL_EINVAL, "kind must be 0 (binary32), 1 (binary64), 2 (int xor+add), 3 (int mad), 4 (int mulhi), "
                                "5 (packed binary32 pairs), 6 (int64 add), 7 (int64 shift+xor), 8 (int64 compare+select), "
                                "9 (binary64 fused multiply-add), 10 (binary64 escape step), "
-                               "11 (binary64 escape step with the binary32 test)");
+                               "11 (binary64 escape step with the binary32 test), 12 / 13 (kind 10 with 4 / 6 "
+                               "warps per scheduler)");
     if (iters < 1 || !lane_ops_per_s)
         return fail(JL_EINVAL, "iters must be >= 1 and lane_ops_per_s non-NULL");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -222,7 +223,9 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
     if (sms <= 0)
         return fail(JL_EUNSUPPORTED, "no CUDA device");
     const int threads = 256;
-    const int grid = sms * 8;
+    // kinds 12 and 13: two or three CTAs of 256 threads per SM, i.e. 4 or 6
+    // warps per scheduler (the lane-refill kernel runs about 4)
+    const int grid = sms * (precision == 12 ? 2 : precision == 13 ? 3 : 8);
     void *out = nullptr;
     cudaError_t e = cudaMallocAsync(&out, (size_t)grid * 8, st);
     if (e != cudaSuccess)
@@ -251,7 +254,7 @@ extern "C" int jl_probe_peak(int32_t precision, int32_t iters, double *lane_ops_
             int64_probe_kernel<8><<<grid, threads, 0, st>>>((unsigned long long *)out, iters, 0x7fffffffffffull, 0x12345ull);
         else if (precision == 9)
             dfma_probe_kernel<<<grid, threads, 0, st>>>((double *)out, iters, 0.999, 0.001);
-        else if (precision == 10)
+        else if (precision == 10 || precision == 12 || precision == 13)
             escape_step_probe_kernel<false><<<grid, threads, 0, st>>>((double *)out, iters, -0.1, 0.1);
         else if (precision == 11)
             escape_step_probe_kernel<true><<<grid, threads, 0, st>>>((double *)out, iters, -0.1, 0.1);
