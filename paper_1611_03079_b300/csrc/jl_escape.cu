@@ -591,8 +591,10 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
 
 // Escape count of one pixel in blocks of 4 steps with one branch per block.
 // When escape is monotone (`mono`, see in_unsafe_band) the block keeps the
-// four values r = x2 + y2 and, once the last one fails, the count is the
-// number of passed tests; otherwise every step is tested exactly.
+// squares of its four steps, forms only the last test value r = x2 + y2 on
+// the way and, once that one fails, the count is the number of passed tests
+// (the first three r formed on the exit path from the kept squares: the same
+// roundings); otherwise every step is tested exactly.
 template <typename T>
 __device__ __forceinline__ int escape_blocked(T x, T y, T cr, T ci, int max_iter, bool mono)
 {
@@ -600,153 +602,45 @@ __device__ __forceinline__ int escape_blocked(T x, T y, T cr, T ci, int max_iter
         return exact_from(x, y, cr, ci, 0, max_iter);
     int n = 0;
     for (; n + 4 <= max_iter; n += 4) {
-        T r[4];
+        T x2s[4], y2s[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            T x2, y2, t;
+            T t;
             if constexpr (sizeof(T) == 4) {
-                x2 = __fmul_rn(x, x);
-                y2 = __fmul_rn(y, y);
-                r[u] = __fadd_rn(x2, y2);
+                x2s[u] = __fmul_rn(x, x);
+                y2s[u] = __fmul_rn(y, y);
                 t = __fmul_rn(__fadd_rn(x, x), y);
                 y = __fadd_rn(t, ci);
-                x = __fadd_rn(__fsub_rn(x2, y2), cr);
+                x = __fadd_rn(__fsub_rn(x2s[u], y2s[u]), cr);
             } else {
-                x2 = __dmul_rn(x, x);
-                y2 = __dmul_rn(y, y);
-                r[u] = __dadd_rn(x2, y2);
+                x2s[u] = __dmul_rn(x, x);
+                y2s[u] = __dmul_rn(y, y);
                 t = __dmul_rn(dbl2(x), y);
                 y = __dadd_rn(t, ci);
-                x = __dadd_rn(__dsub_rn(x2, y2), cr);
+                x = __dadd_rn(__dsub_rn(x2s[u], y2s[u]), cr);
             }
         }
-        if (!(r[3] <= T(4))) {
+        T r3;
+        if constexpr (sizeof(T) == 4)
+            r3 = __fadd_rn(x2s[3], y2s[3]);
+        else
+            r3 = __dadd_rn(x2s[3], y2s[3]);
+        if (!(r3 <= T(4))) {
             int passed = 0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                passed += (r[u] <= T(4)) ? 1 : 0;
+            for (int u = 0; u < 3; ++u) {
+                T r;
+                if constexpr (sizeof(T) == 4)
+                    r = __fadd_rn(x2s[u], y2s[u]);
+                else
+                    r = __dadd_rn(x2s[u], y2s[u]);
+                passed += (r <= T(4)) ? 1 : 0;
+            }
             return n + passed;
         }
     }
     // tail shorter than a block: Z_n is (x, y)
     return exact_from(x, y, cr, ci, n, max_iter);
-}
-
-// ---------------------------------------------------------------------------
-// Static kernel: one pixel per thread, CTA = 32 x 8 pixels (8 warps of 8 x 4),
-// an exact test at every step and per-lane early exit.  No refill machinery,
-// so per-pixel overhead is minimal; lanes of a warp wait for the slowest
-// pixel of their 8 x 4 patch.  Best for frames with low escape counts.
-// ---------------------------------------------------------------------------
-template <typename T, bool BATCH>
-__global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constant__ EscapeArgs a)
-{
-    __shared__ uint32_t pal[256];
-    extern __shared__ uint32_t hbins[];
-    for (int t = threadIdx.x; t < 256; t += blockDim.x)
-        pal[t] = a.palette[t];
-    const int nb = (!BATCH && a.hist_smem) ? a.single.max_iter + 1 : 0;
-    for (int t = threadIdx.x; t < nb; t += blockDim.x)
-        hbins[t] = 0;
-    __syncthreads();
-
-    // Tiles of 32 x 32 pixels in eight 8 x 16 parts; a warp takes parts one at
-    // a time from the launch's counter (the next index fetched a part ahead).
-    // In part k the warp covers 8 x 4 patches and each thread four pixels of
-    // one column, 8 rows apart.
-    const int lane = threadIdx.x & 31;
-    const long long t_start = clock64();
-    const long long total_units = a.total_tiles * 8;
-    const unsigned long long claim = (unsigned long long)a.claim;
-    unsigned long long next_u = 0;
-    if (lane == 0)
-        next_u = atomicAdd(a.chunk_counter, claim);
-    long long cur = 0, end = 0;
-
-    for (;;) {
-        if (cur == end) {
-            cur = (long long)__shfl_sync(FULL, next_u, 0);
-            end = cur + (long long)claim;
-            if (lane == 0)
-                next_u = atomicAdd(a.chunk_counter, claim);
-        }
-        const long long unit = cur++;
-        if (unit >= total_units)
-            break;
-        // budget check, uniform across the warp (the loop below has warp collectives)
-        if (a.cycle_budget > 0 && __any_sync(FULL, (clock64() - t_start) > a.cycle_budget)) {
-            if (lane == 0 && a.status)
-                atomicExch(a.status, (int)JL_ETIMEOUT);
-            break;
-        }
-        const long long tile = unit >> 3;
-        const int part = (int)(unit & 7);
-        const int dx = (part & 3) * 8 + (lane & 7);
-        const int dy = (part >> 2) * 4 + (lane >> 3);
-        int f = 0;
-        if constexpr (BATCH)
-            f = a.tile_frame[tile];
-        const Frame &F = BATCH ? a.frames[f] : a.single;
-        // frame fields used below, read once per tile
-        const int W = F.W, H = F.H, mi = F.max_iter;
-        const bool julia = F.mode == JL_JULIA;
-        const bool safe = F.safe != 0;
-        const T fcr = WorkT<T>::cr(F), fci = WorkT<T>::ci(F);
-        const T *xs = static_cast<const T *>(F.xs);
-        const T *ys = static_cast<const T *>(F.ys);
-        uint8_t *counts = F.counts;
-        const bool u8 = F.count_type == JL_COUNT_U8;
-        uint32_t *rgba = F.rgba;
-        uint32_t *bins = F.hist_bins;
-        const uint64_t cmagic = F.colour_magic;
-        const uint32_t lt = BATCH ? (uint32_t)a.tile_local[tile] : (uint32_t)(tile - F.tile_begin);
-        const uint32_t ty = (uint32_t)(((uint64_t)lt * F.tiles_x_magic) >> 40);
-        const uint32_t tx = lt - ty * (uint32_t)F.tiles_x;
-        const int i = (int)tx * 32 + dx;
-        if (i >= W)
-            continue;
-        const T xv = xs[i];
-#pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-            const int j = (int)ty * 32 + dy + 8 * q;
-            if (j >= H)
-                break;
-            const T yv = ys[j];
-            int count;
-            if (julia)
-                count = escape_blocked(xv, yv, fcr, fci, mi, safe);
-            else
-                count = escape_blocked(T(0), T(0), xv, yv, mi, !in_unsafe_band(xv, yv));
-            const int p = j * W + i;
-            if (counts) {
-                if (u8)
-                    counts[p] = (uint8_t)count;
-                else
-                    reinterpret_cast<uint16_t *>(counts)[p] = (uint16_t)count;
-            }
-            if (rgba)
-                rgba[p] = pal[colour_index((uint32_t)count, (uint32_t)mi, cmagic)];
-            if (bins) {
-                if (!BATCH && a.hist_smem) {
-                    atomicAdd(&hbins[count], 1u);
-                } else {
-                    const unsigned act = __activemask();
-                    const unsigned long long key = ((unsigned long long)(unsigned)f << 32) | (unsigned)count;
-                    const unsigned grp = __match_any_sync(act, key);
-                    if ((grp & ((1u << lane) - 1u)) == 0)
-                        atomicAdd(&bins[count], (unsigned)__popc(grp));
-                }
-            }
-        }
-    }
-    if (nb) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-            const uint32_t v = hbins[t];
-            if (v)
-                atomicAdd(&a.single.hist_bins[t], v);
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -874,6 +768,11 @@ __device__ __forceinline__ void store_tile(const EscapeArgs &a, const TileOut &o
         o.rgba[p] = pal[tile_colour(o, count)];
         return;
     }
+    if constexpr (OUT == 2) {
+        // RGBA8 only
+        o.rgba[p] = pal[tile_colour(o, count)];
+        return;
+    }
     if (o.counts) {
         if (o.u8)
             o.counts[p] = (uint8_t)count;
@@ -922,6 +821,111 @@ __device__ __forceinline__ void store_result(const EscapeArgs &a, const uint32_t
             const unsigned grp = __match_any_sync(act, key);
             if ((grp & lt_mask) == 0)
                 atomicAdd(&F.hist_bins[count], (unsigned)__popc(grp));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Static kernel: one pixel per thread, CTA = 32 x 8 pixels (8 warps of 8 x 4),
+// an exact test at every step and per-lane early exit.  No refill machinery,
+// so per-pixel overhead is minimal; lanes of a warp wait for the slowest
+// pixel of their 8 x 4 patch.  Best for frames with low escape counts.
+// OUT (binary32 only): 1 = every frame has uint16 counts and RGBA8 and no
+// histogram, 2 = every frame has RGBA8 only; the stores then skip the
+// per-frame output tests.  0: any outputs.
+// ---------------------------------------------------------------------------
+template <typename T, bool BATCH, int OUT>
+__global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constant__ EscapeArgs a)
+{
+    __shared__ uint32_t pal[256];
+    extern __shared__ uint32_t hbins[];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        pal[t] = a.palette[t];
+    const int nb = (!BATCH && a.hist_smem) ? a.single.max_iter + 1 : 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x)
+        hbins[t] = 0;
+    __syncthreads();
+
+    // Tiles of 32 x 32 pixels in eight 8 x 16 parts; a warp takes parts one at
+    // a time from the launch's counter (the next index fetched a part ahead).
+    // In part k the warp covers 8 x 4 patches and each thread four pixels of
+    // one column, 8 rows apart.
+    const int lane = threadIdx.x & 31;
+    const long long t_start = clock64();
+    const long long total_units = a.total_tiles * 8;
+    const unsigned long long claim = (unsigned long long)a.claim;
+    unsigned long long next_u = 0;
+    if (lane == 0)
+        next_u = atomicAdd(a.chunk_counter, claim);
+    long long cur = 0, end = 0;
+
+    for (;;) {
+        if (cur == end) {
+            cur = (long long)__shfl_sync(FULL, next_u, 0);
+            end = cur + (long long)claim;
+            if (lane == 0)
+                next_u = atomicAdd(a.chunk_counter, claim);
+        }
+        const long long unit = cur++;
+        if (unit >= total_units)
+            break;
+        // budget check, uniform across the warp (the loop below has warp collectives)
+        if (a.cycle_budget > 0 && __any_sync(FULL, (clock64() - t_start) > a.cycle_budget)) {
+            if (lane == 0 && a.status)
+                atomicExch(a.status, (int)JL_ETIMEOUT);
+            break;
+        }
+        const long long tile = unit >> 3;
+        const int part = (int)(unit & 7);
+        const int dx = (part & 3) * 8 + (lane & 7);
+        const int dy = (part >> 2) * 4 + (lane >> 3);
+        int f = 0;
+        if constexpr (BATCH)
+            f = a.tile_frame[tile];
+        const Frame &F = BATCH ? a.frames[f] : a.single;
+        // frame fields used below, read once per tile
+        const int W = F.W, H = F.H, mi = F.max_iter;
+        const bool julia = F.mode == JL_JULIA;
+        const bool safe = F.safe != 0;
+        const T fcr = WorkT<T>::cr(F), fci = WorkT<T>::ci(F);
+        const T *xs = static_cast<const T *>(F.xs);
+        const T *ys = static_cast<const T *>(F.ys);
+        TileOut o;
+        o.counts = F.counts;
+        o.rgba = F.rgba;
+        o.bins = F.hist_bins;
+        o.magic = F.colour_magic;
+        o.m32 = (uint32_t)((o.magic - 1u) >> 8) + 1u;
+        o.mi = mi;
+        o.u8 = F.count_type == JL_COUNT_U8;
+        o.small = mi <= 4096;
+        const uint32_t lt = BATCH ? (uint32_t)a.tile_local[tile] : (uint32_t)(tile - F.tile_begin);
+        const uint32_t ty = (uint32_t)(((uint64_t)lt * F.tiles_x_magic) >> 40);
+        const uint32_t tx = lt - ty * (uint32_t)F.tiles_x;
+        const int i = (int)tx * 32 + dx;
+        if (i >= W)
+            continue;
+        const T xv = xs[i];
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int j = (int)ty * 32 + dy + 8 * q;
+            if (j >= H)
+                break;
+            const T yv = ys[j];
+            int count;
+            if (julia)
+                count = escape_blocked(xv, yv, fcr, fci, mi, safe);
+            else
+                count = escape_blocked(T(0), T(0), xv, yv, mi, !in_unsafe_band(xv, yv));
+            store_tile<BATCH, OUT>(a, o, pal, hbins, f, (uint32_t)(j * W + i), count, (1u << lane) - 1u);
+        }
+    }
+    if (nb) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            const uint32_t v = hbins[t];
+            if (v)
+                atomicAdd(&a.single.hist_bins[t], v);
         }
     }
 }
@@ -1368,13 +1372,34 @@ static int32_t tile_claim(long long total_tiles, long long grid)
     return c;
 }
 
+// Output specialisation of a launch: the batch plan's (computed over its
+// frames), or that of the single frame.
+static int launch_out_mode(const EscapeArgs &a)
+{
+    if (a.frames)
+        return a.out_mode;
+    const Frame &F = a.single;
+    if (F.hist_bins || !F.rgba)
+        return 0;
+    if (!F.counts)
+        return 2;
+    return F.count_type == JL_COUNT_U16 ? 1 : 0;
+}
+
 template <typename T>
 static cudaError_t launch_static(const EscapeArgs &a, cudaStream_t st)
 {
     size_t smem = 0;
     if (a.hist_smem && !a.frames)
         smem = (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
-    auto kern = a.frames ? escape_static_kernel<T, true> : escape_static_kernel<T, false>;
+    auto kern = a.frames ? escape_static_kernel<T, true, 0> : escape_static_kernel<T, false, 0>;
+    if constexpr (sizeof(T) == 4) {
+        const int out_mode = launch_out_mode(a);
+        if (out_mode == 1)
+            kern = a.frames ? escape_static_kernel<T, true, 1> : escape_static_kernel<T, false, 1>;
+        else if (out_mode == 2)
+            kern = a.frames ? escape_static_kernel<T, true, 2> : escape_static_kernel<T, false, 2>;
+    }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
@@ -1401,11 +1426,8 @@ static cudaError_t launch_compact(const EscapeArgs &a, int T, cudaStream_t st)
     size_t smem = 0;
     if (a.hist_smem && !a.frames)
         smem = (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
-    int out_mode = a.out_mode;
-    if (!a.frames) {
-        const Frame &F = a.single;
-        out_mode = (F.counts && F.count_type == JL_COUNT_U16 && F.rgba && !F.hist_bins) ? 1 : 0;
-    }
+    // (the compacting kernel has the uint16 + RGBA8 specialisation only)
+    const int out_mode = launch_out_mode(a);
     auto kern = a.frames ? (out_mode == 1 ? escape_compact_kernel<true, 8, 1> : escape_compact_kernel<true, 8, 0>)
                          : (out_mode == 1 ? escape_compact_kernel<false, 8, 1> : escape_compact_kernel<false, 8, 0>);
     if (smem > 16 * 1024) {

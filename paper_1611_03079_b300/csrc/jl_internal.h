@@ -58,7 +58,7 @@ struct EscapeArgs {
     int32_t *status;                   // device status word (0 = ok), may be NULL
     long long cycle_budget;            // per-CTA clock64 budget; <= 0: unlimited
     int32_t claim;                     // tile kernels: 8 x 16 parts per counter claim (set by the launcher)
-    int32_t out_mode;                  // 1: every frame has uint16 counts and RGBA8 and no histogram
+    int32_t out_mode;                  // batches: 1 = every frame uint16 counts + RGBA8, 2 = RGBA8 only (no histograms)
     uint32_t palette[256];
     Frame single;
 };
