@@ -336,8 +336,9 @@ int jl_render_batch(const jl_frame *frames, int32_t n, void *counts_base, uint8_
  * on separate internal streams (up to 4 render and 2 copy streams): frame i
  * renders into device slot i mod depth and is copied out as soon as its
  * render is done, while later frames render; a render waits for a copy only
- * to reuse a slot.  `depth` = device slots, 1..64, or 0 for the default (one
- * slot per frame up to 16 frames, at most 4 GiB of slots).  The host buffers
+ * to reuse a slot; the last frame may render as row bands copied band by
+ * band (see jl_host_plan_launches).  `depth` = device slots, 1..64, or 0 for
+ * the default (one slot per frame up to 16 frames, at most 4 GiB of slots).  The host buffers
  * should be pinned (page-locked) for the copies to overlap; pageable memory
  * works but serialises.  Work queued earlier on `stream` is waited for; the
  * call returns when every copy has completed (synchronous).  The library
