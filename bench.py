@@ -406,7 +406,8 @@ def run_generic_maps(K, W, peaks):
     """Generic maps (Sec. 2 other functions, Fig. 4): Multibrot parameter
     planes d = 3, 4, 5, 8, Fig. 4's map as printed, and the d = 3 plane in
     binary64, each 4096 x 4096 (uint16 counts + RGBA8) through jl_render_map;
-    CUDA events around K renders after W warm-ups, median of three such windows.  The oracle is timed on a
+    CUDA events around K renders after W warm-ups (queued behind a GPU sleep so
+    that they run back to back), median of three such windows.  The oracle is timed on a
     64-row band of each frame on all host cores for context."""
     import numpy as np
     import torch
@@ -422,11 +423,14 @@ def run_generic_maps(K, W, peaks):
         for _ in range(W):
             out = jl.render_map(f["map"], f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=prec,
                                 mode=mode, out=out)
-        # median of three windows of K renders (one render is a few hundred
-        # microseconds, so a host stall inside one window would show)
+        # median of three windows of K renders.  A render is a few hundred
+        # microseconds of device work, about as long as the Python call that
+        # launches it, so each window's renders are queued behind a fixed-length
+        # GPU sleep and then run back to back: the events time the device.
         windows = []
         for _ in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda._sleep(int(4e6 * K))
             e0.record()
             for _ in range(K):
                 out = jl.render_map(f["map"], f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=prec,

@@ -74,6 +74,10 @@ struct GemmArgs {
     // (ld_out32 as given); a fixed-order reduction sums the splits.
     int ksplit, kc_per_split;
     long long split_stride;
+    // column split (not EPI_SOFTMAX, whose rows need every column): CTA
+    // (x, y, z) computes columns [z * n_per_cta, (z + 1) * n_per_cta) of its
+    // rows; 0 = all BN columns in one CTA.  A multiple of 64.
+    int n_per_cta;
 };
 
 static constexpr int kBM = 128, kBK = 64;
@@ -183,7 +187,11 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
     tc::tc_fence_after();
     const uint32_t taddr = *holder;
 
-    const uint32_t idesc = tc::idesc_bf16(kBM, (uint32_t)g.BN);
+    // this CTA's columns [n0, n0 + nbn) (a multiple of 16 wide)
+    const int npc = (EPI != EPI_SOFTMAX && g.n_per_cta > 0) ? g.n_per_cta : g.BN;
+    const int n0 = (int)blockIdx.z * npc;
+    const int nbn = min(npc, g.BN - n0);
+    const uint32_t idesc = tc::idesc_bf16(kBM, (uint32_t)nbn);
     int kc_begin = 0, kc_end = (g.K + kBK - 1) / kBK;
     if (EPI == EPI_F32 && g.ksplit > 1) {
         kc_begin = blockIdx.y * g.kc_per_split;
@@ -201,7 +209,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
                 ok = false;
         }
         stage_operand(sA, g.A, g.lda, g.a_trans, m0, kBM, g.M, kc * kBK, g.K);
-        stage_operand(sB, g.B, g.ldb, g.b_trans, 0, g.BN, g.N, kc * kBK, g.K);
+        stage_operand(sB, g.B, g.ldb, g.b_trans, n0, nbn, g.N, kc * kBK, g.K);
         tc::fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
         float *o32 = nullptr;
         if constexpr (EPI == EPI_F32)
             o32 = g.out_f32 + (g.ksplit > 1 ? (size_t)blockIdx.y * (size_t)g.split_stride : 0);
-        for (int cb0 = 0; cb0 < g.BN; cb0 += 64) {
+        for (int cb0 = n0; cb0 < n0 + nbn; cb0 += 64) {
             const int ncol = min(64, g.N - cb0);
             __syncthreads();  // the previous block's readers of the tile are done
             if constexpr (EPI == EPI_MASK) {
@@ -353,9 +361,9 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
                 }
                 __syncthreads();
             }
-            for (int c0 = cb0; c0 < cb0 + 64 && c0 < g.BN; c0 += 16) {
+            for (int c0 = cb0; c0 < cb0 + 64 && c0 < n0 + nbn; c0 += 16) {
                 float v[16];
-                tc::tmem_ld16(tw + c0, v);
+                tc::tmem_ld16(tw + (uint32_t)(c0 - n0), v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = c0 + j;
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
         // deterministic: per-CTA column sums (fixed row order), summed across
         // CTAs in a fixed order later
         __syncthreads();
-        for (int c = threadIdx.x; c < g.N; c += blockDim.x)
+        for (int c = n0 + threadIdx.x; c < g.N && c < n0 + nbn; c += blockDim.x)
             g.colsum[(size_t)blockIdx.x * 256 + c] = part[c];
     }
     tc::tc_fence_before();
@@ -1303,7 +1311,12 @@ static cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t st)
     }
     const int grid = (a.M + kBM - 1) / kBM;
     const int splits = (EPI == EPI_F32 && a.ksplit > 1) ? a.ksplit : 1;
-    kern<<<dim3(grid, splits), 128, kGemmSmem, st>>>(a);
+    // columns in blocks of 64 per CTA (a batch of 1024 rows is only 8 row
+    // tiles: with whole rows per CTA most SMs would idle)
+    GemmArgs b = a;
+    b.n_per_cta = EPI == EPI_SOFTMAX ? 0 : 64;
+    const int nz = b.n_per_cta ? (a.BN + b.n_per_cta - 1) / b.n_per_cta : 1;
+    kern<<<dim3(grid, splits, nz), 128, kGemmSmem, st>>>(b);
     return cudaGetLastError();
 }
 
