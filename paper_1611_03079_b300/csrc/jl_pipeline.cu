@@ -62,7 +62,7 @@ struct jl_host_plan {
     cudaEvent_t fork = nullptr;
     void *slots = nullptr;
     size_t slot_bytes = 0;
-    void *tables = nullptr;  // coordinate tables and a 256-byte control block per frame
+    void *tables = nullptr;  // coordinate tables, a 256-byte control block per frame and per extra band
 };
 
 static size_t pad256(size_t b) { return (b + 255) & ~(size_t)255; }
