@@ -495,7 +495,6 @@ def main():
         return run_reference(args)
 
     import numpy as np
-    import numpy as np
     import torch
 
     import paper_1611_03079_b300 as jl
