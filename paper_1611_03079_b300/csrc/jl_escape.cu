@@ -858,15 +858,28 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
     if (lane == 0)
         next_u = atomicAdd(a.chunk_counter, claim);
     long long cur = 0, end = 0;
-
-    for (;;) {
+    // next unit of this warp (warp-uniform; claims of `claim` units, the next
+    // claim fetched one ahead)
+    auto take_unit = [&]() -> long long {
         if (cur == end) {
             cur = (long long)__shfl_sync(FULL, next_u, 0);
             end = cur + (long long)claim;
             if (lane == 0)
                 next_u = atomicAdd(a.chunk_counter, claim);
         }
-        const long long unit = cur++;
+        return cur++;
+    };
+    // batches: a unit's tile record (frame, index in the frame) is loaded one
+    // unit ahead, so its latency overlaps the previous unit's work
+    long long unit = take_unit();
+    int f_cur = 0;
+    uint32_t lt_cur = 0;
+    if (BATCH && unit < total_units) {
+        f_cur = a.tile_frame[unit >> 3];
+        lt_cur = (uint32_t)a.tile_local[unit >> 3];
+    }
+
+    for (;;) {
         if (unit >= total_units)
             break;
         // budget check, uniform across the warp (the loop below has warp collectives)
@@ -875,13 +888,18 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
                 atomicExch(a.status, (int)JL_ETIMEOUT);
             break;
         }
+        const long long nunit = take_unit();
+        int f_nxt = 0;
+        uint32_t lt_nxt = 0;
+        if (BATCH && nunit < total_units) {
+            f_nxt = a.tile_frame[nunit >> 3];
+            lt_nxt = (uint32_t)a.tile_local[nunit >> 3];
+        }
         const long long tile = unit >> 3;
         const int part = (int)(unit & 7);
         const int dx = (part & 3) * 8 + (lane & 7);
         const int dy = (part >> 2) * 4 + (lane >> 3);
-        int f = 0;
-        if constexpr (BATCH)
-            f = a.tile_frame[tile];
+        const int f = f_cur;
         const Frame &F = BATCH ? a.frames[f] : a.single;
         // frame fields used below, read once per tile
         const int W = F.W, H = F.H, mi = F.max_iter;
@@ -899,26 +917,29 @@ __global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constan
         o.mi = mi;
         o.u8 = F.count_type == JL_COUNT_U8;
         o.small = mi <= 4096;
-        const uint32_t lt = BATCH ? (uint32_t)a.tile_local[tile] : (uint32_t)(tile - F.tile_begin);
+        const uint32_t lt = BATCH ? lt_cur : (uint32_t)(tile - F.tile_begin);
         const uint32_t ty = (uint32_t)(((uint64_t)lt * F.tiles_x_magic) >> 40);
         const uint32_t tx = lt - ty * (uint32_t)F.tiles_x;
         const int i = (int)tx * 32 + dx;
-        if (i >= W)
-            continue;
-        const T xv = xs[i];
+        if (i < W) {
+            const T xv = xs[i];
 #pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-            const int j = (int)ty * 32 + dy + 8 * q;
-            if (j >= H)
-                break;
-            const T yv = ys[j];
-            int count;
-            if (julia)
-                count = escape_blocked(xv, yv, fcr, fci, mi, safe);
-            else
-                count = escape_blocked(T(0), T(0), xv, yv, mi, !in_unsafe_band(xv, yv));
-            store_tile<BATCH, OUT>(a, o, pal, hbins, f, (uint32_t)(j * W + i), count, (1u << lane) - 1u);
+            for (int q = 0; q < 4; ++q) {
+                const int j = (int)ty * 32 + dy + 8 * q;
+                if (j >= H)
+                    break;
+                const T yv = ys[j];
+                int count;
+                if (julia)
+                    count = escape_blocked(xv, yv, fcr, fci, mi, safe);
+                else
+                    count = escape_blocked(T(0), T(0), xv, yv, mi, !in_unsafe_band(xv, yv));
+                store_tile<BATCH, OUT>(a, o, pal, hbins, f, (uint32_t)(j * W + i), count, (1u << lane) - 1u);
+            }
         }
+        unit = nunit;
+        f_cur = f_nxt;
+        lt_cur = lt_nxt;
     }
     if (nb) {
         __syncthreads();
