@@ -835,7 +835,7 @@ __device__ __forceinline__ void store_result(const EscapeArgs &a, const uint32_t
 // per-frame output tests.  0: any outputs.
 // ---------------------------------------------------------------------------
 template <typename T, bool BATCH, int OUT>
-__global__ void __launch_bounds__(256) escape_static_kernel(const __grid_constant__ EscapeArgs a)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) escape_static_kernel(const __grid_constant__ EscapeArgs a)
 {
     __shared__ uint32_t pal[256];
     extern __shared__ uint32_t hbins[];
