@@ -276,13 +276,15 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             x.status = reinterpret_cast<int32_t *>(b->ctl_dev + 16);
             x.cycle_budget = o.cycle_budget;
             // output specialisation: 1 = every frame uint16 counts + RGBA8, 2 =
-            // every frame RGBA8 only (neither with a histogram), else 0
-            bool u16_rgba = !host[g].empty(), rgba_only = !host[g].empty();
+            // every frame RGBA8 only, 3 = every frame uint8 counts + RGBA8
+            // (none with a histogram), else 0
+            bool u16_rgba = !host[g].empty(), rgba_only = !host[g].empty(), u8_rgba = !host[g].empty();
             for (const Frame &F : host[g]) {
                 u16_rgba = u16_rgba && F.counts && F.count_type == JL_COUNT_U16 && F.rgba && !F.hist_bins;
                 rgba_only = rgba_only && !F.counts && F.rgba && !F.hist_bins;
+                u8_rgba = u8_rgba && F.counts && F.count_type == JL_COUNT_U8 && F.rgba && !F.hist_bins;
             }
-            x.out_mode = u16_rgba ? 1 : rgba_only ? 2 : 0;
+            x.out_mode = u16_rgba ? 1 : rgba_only ? 2 : u8_rgba ? 3 : 0;
             memcpy(x.palette, pal, 1024);
             return x;
         };

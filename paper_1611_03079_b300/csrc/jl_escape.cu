@@ -773,6 +773,12 @@ __device__ __forceinline__ void store_tile(const EscapeArgs &a, const TileOut &o
         o.rgba[p] = pal[tile_colour(o, count)];
         return;
     }
+    if constexpr (OUT == 3) {
+        // uint8 counts and RGBA8, no histogram
+        o.counts[p] = (uint8_t)count;
+        o.rgba[p] = pal[tile_colour(o, count)];
+        return;
+    }
     if (o.counts) {
         if (o.u8)
             o.counts[p] = (uint8_t)count;
@@ -831,8 +837,9 @@ __device__ __forceinline__ void store_result(const EscapeArgs &a, const uint32_t
 // so per-pixel overhead is minimal; lanes of a warp wait for the slowest
 // pixel of their 8 x 4 patch.  Best for frames with low escape counts.
 // OUT (binary32 only): 1 = every frame has uint16 counts and RGBA8 and no
-// histogram, 2 = every frame has RGBA8 only; the stores then skip the
-// per-frame output tests.  0: any outputs.
+// histogram, 2 = every frame has RGBA8 only, 3 = every frame has uint8 counts
+// and RGBA8 and no histogram; the stores then skip the per-frame output
+// tests.  0: any outputs.
 // ---------------------------------------------------------------------------
 template <typename T, bool BATCH, int OUT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) escape_static_kernel(const __grid_constant__ EscapeArgs a)
@@ -1404,7 +1411,7 @@ static int launch_out_mode(const EscapeArgs &a)
         return 0;
     if (!F.counts)
         return 2;
-    return F.count_type == JL_COUNT_U16 ? 1 : 0;
+    return F.count_type == JL_COUNT_U16 ? 1 : F.count_type == JL_COUNT_U8 ? 3 : 0;
 }
 
 template <typename T>
@@ -1420,6 +1427,8 @@ static cudaError_t launch_static(const EscapeArgs &a, cudaStream_t st)
             kern = a.frames ? escape_static_kernel<T, true, 1> : escape_static_kernel<T, false, 1>;
         else if (out_mode == 2)
             kern = a.frames ? escape_static_kernel<T, true, 2> : escape_static_kernel<T, false, 2>;
+        else if (out_mode == 3)
+            kern = a.frames ? escape_static_kernel<T, true, 3> : escape_static_kernel<T, false, 3>;
     }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -58,7 +58,7 @@ struct EscapeArgs {
     int32_t *status;                   // device status word (0 = ok), may be NULL
     long long cycle_budget;            // per-CTA clock64 budget; <= 0: unlimited
     int32_t claim;                     // tile kernels: 8 x 16 parts per counter claim (set by the launcher)
-    int32_t out_mode;                  // batches: 1 = every frame uint16 counts + RGBA8, 2 = RGBA8 only (no histograms)
+    int32_t out_mode;                  // batches: 1 = uint16 counts + RGBA8, 2 = RGBA8 only, 3 = uint8 counts + RGBA8 (every frame, no histograms)
     uint32_t palette[256];
     Frame single;
 };
