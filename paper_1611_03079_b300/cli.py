@@ -4,6 +4,7 @@
   python -m paper_1611_03079_b300.cli --c -0.8+0.156j --rect -2 2 -2 2 --W 512 --H 512 --out f.npy
   python -m paper_1611_03079_b300.cli --workload forward --n 1048576 --repeat 3
   python -m paper_1611_03079_b300.cli --workload sweep-plan --precision fp64 --repeat 3
+  python -m paper_1611_03079_b300.cli --workload train --epochs 2
 
 Renders one frame `repeat` times on cuda:0 and prints the kernel-bracketed
 time and pixel-iterations per second; optionally saves counts (.npy).  Also
@@ -17,7 +18,8 @@ import numpy as np
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--workload", choices=["sweep", "sweep-plan", "single", "path", "forward"], default=None)
+    p.add_argument("--workload", choices=["sweep", "sweep-plan", "single", "path", "forward", "train"], default=None)
+    p.add_argument("--epochs", type=int, default=2, help="train workload: epochs over 65,536 seeded C values")
     p.add_argument("--n", type=int, default=1 << 20, help="forward workload: number of C values screened")
     p.add_argument("--frames", type=int, default=72, help="path workload: first N frames as one batch plan")
     p.add_argument("--index", type=int, default=0)
@@ -48,6 +50,8 @@ def main(argv=None):
         return forward(a)
     if a.workload == "sweep-plan":
         return sweep_plan(a)
+    if a.workload == "train":
+        return train(a)
     if a.workload == "sweep":
         f = wl.throughput_sweep(a.size)[a.index]
     elif a.workload == "single":
@@ -150,6 +154,32 @@ def forward(a):
     best = min(times)
     print(json.dumps({"n": a.n, "ms": times, "best_ms": best, "tflop_s": flop / (best * 1e-3) / 1e12,
                       "mean_score": float(score.mean().item())}))
+    model.close()
+
+
+def train(a):
+    """Surrogate training (batch 1024, Adam) on the 65,536 seeded training C
+    values with seeded random target histograms (the products and kernels of
+    a training step, without rendering the targets), `epochs` epochs."""
+    import time
+
+    import torch
+
+    from paper_1611_03079_b300 import surrogate, workloads as wl
+    torch.cuda.set_device(0)
+    c = torch.from_numpy(wl.survey_train()).cuda()
+    g = torch.Generator(device="cpu").manual_seed(5)
+    t = torch.rand((c.shape[0], 101), generator=g).cuda()
+    t = t / t.sum(1, keepdim=True)
+    model = surrogate.Surrogate(wl.fourier_matrix(), wl.mlp_init())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    curve = model.train(c, t, a.epochs, batch=1024, lr=2e-3, lr_final=1e-5, order_seed=1)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    steps = a.epochs * (c.shape[0] // 1024)
+    print(json.dumps({"epochs": a.epochs, "steps": steps, "s": secs, "ms_per_step": secs / steps * 1e3,
+                      "final_loss": float(curve[-1])}))
     model.close()
 
 
