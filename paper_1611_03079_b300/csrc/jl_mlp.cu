@@ -908,16 +908,31 @@ __global__ void gather_rows_kernel(const float *__restrict__ src, const int32_t 
     dst[t] = src[(size_t)idx[i] * cols + j];
 }
 
+// bf16 weight copies, contiguous: W1, W2, W3 as stored ([out][in]), then the
+// transposes W2^T ([in][out], kHid x kHid) and W3^T ([in][out], kHid rows of
+// kBinsPad, zero past kBins) that the backward products read as K-major
+// operands (16-byte staging instead of 2-byte gathers).
+static constexpr int kWbW = kHid * kIn + kHid * kHid + kBins * kHid;  // W1 | W2 | W3
+static constexpr int kWbT2 = kWbW;                                     // W2^T
+static constexpr int kWbT3 = kWbT2 + kHid * kHid;                      // W3^T
+static constexpr int kWbAll = kWbT3 + kHid * kBinsPad;
+
 __global__ void cast_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *__restrict__ wb)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    // bf16 copies of W1, W2, W3 stored contiguously in that order
-    if (i < kHid * kIn)
+    if (i < kHid * kIn) {
         wb[i] = __float2bfloat16_rn(p[kOffW1 + i]);
-    else if (i < kHid * kIn + kHid * kHid)
+    } else if (i < kHid * kIn + kHid * kHid) {
         wb[i] = __float2bfloat16_rn(p[kOffW2 + (i - kHid * kIn)]);
-    else if (i < kHid * kIn + kHid * kHid + kBins * kHid)
+    } else if (i < kWbW) {
         wb[i] = __float2bfloat16_rn(p[kOffW3 + (i - kHid * kIn - kHid * kHid)]);
+    } else if (i < kWbT3) {
+        const int t = i - kWbT2, n = t / kHid, k = t - n * kHid;  // W2^T[n][k] = W2[k][n]
+        wb[i] = __float2bfloat16_rn(p[kOffW2 + k * kHid + n]);
+    } else if (i < kWbAll) {
+        const int t = i - kWbT3, n = t / kBinsPad, k = t - n * kBinsPad;  // W3^T[n][k] = W3[k][n]
+        wb[i] = __float2bfloat16_rn(k < kBins ? p[kOffW3 + k * kHid + n] : 0.f);
+    }
 }
 
 // Adam on the whole parameter block; the step counter lives in device memory
@@ -939,15 +954,22 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ gra
         const float upd = lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
         const float w = p[i] - upd;
         p[i] = w;
-        int wi = -1;
-        if (i < kOffB1)
+        int wi = -1, wt = -1;
+        if (i < kOffB1) {
             wi = i - kOffW1;
-        else if (i >= kOffW2 && i < kOffB2)
-            wi = kHid * kIn + (i - kOffW2);
-        else if (i >= kOffW3 && i < kOffB3)
-            wi = kHid * kIn + kHid * kHid + (i - kOffW3);
+        } else if (i >= kOffW2 && i < kOffB2) {
+            const int t = i - kOffW2, r = t / kHid, c = t - r * kHid;
+            wi = kHid * kIn + t;
+            wt = kWbT2 + c * kHid + r;
+        } else if (i >= kOffW3 && i < kOffB3) {
+            const int t = i - kOffW3, r = t / kHid, c = t - r * kHid;
+            wi = kHid * kIn + kHid * kHid + t;
+            wt = kWbT3 + c * kBinsPad + r;
+        }
         if (wi >= 0)
             wb[wi] = __float2bfloat16_rn(w);
+        if (wt >= 0)
+            wb[wt] = __float2bfloat16_rn(w);
     }
 }
 
@@ -1272,7 +1294,7 @@ struct jl_model {
     float *params = nullptr;   // binary32 master [kNumParams]
     float *grads = nullptr;
     float *m = nullptr, *v = nullptr;
-    __nv_bfloat16 *wb = nullptr;  // bf16 W1 | W2 | W3
+    __nv_bfloat16 *wb = nullptr;  // bf16 W1 | W2 | W3 | W2^T | W3^T (see kWbAll)
     __nv_bfloat16 *wpack = nullptr;  // packed shared-memory images for the fused forward
     float *B = nullptr;        // Fourier matrix 32 x 2
     int32_t *step = nullptr;   // Adam step counter (device)
@@ -1483,7 +1505,6 @@ static cudaError_t forward_rows(jl_model *md, const float *c, const int32_t *idx
 // Backward of the batch in md's work buffers (after forward_rows with target).
 static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
 {
-    const __nv_bfloat16 *W2 = md->wb + kHid * kIn, *W3 = md->wb + kHid * kIn + kHid * kHid;
     // dW3 = dZ^T H2  (101 x 256, K = n)
     GemmArgs a = gemm_args(md->dz, kBinsPad, 1, md->h2, kHid, 1, kBins, kHid, n, md->status);
     a.out_f32 = md->grads + kOffW3;
@@ -1491,8 +1512,9 @@ static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
     cudaError_t e = launch_gemm_f32_splitk(a, md->ws, kSplitK, st);
     if (e != cudaSuccess)
         return e;
-    // dZ2 = (dZ W3) * [h2 > 0]   (n x 256, K = 101), db2 = column sums
-    a = gemm_args(md->dz, kBinsPad, 0, W3, kHid, 1, n, kHid, kBins, md->status);
+    // dZ2 = (dZ W3) * [h2 > 0]   (n x 256, K = 101 padded to 112 with zeros on
+    // both sides: dZ's columns past kBins and W3^T's), db2 = column sums
+    a = gemm_args(md->dz, kBinsPad, 0, md->wb + kWbT3, kBinsPad, 0, n, kHid, kBinsPad, md->status);
     a.mask = md->h2;
     a.ldm = kHid;
     a.out_bf16 = md->dz2;
@@ -1509,7 +1531,7 @@ static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
     if ((e = launch_gemm_f32_splitk(a, md->ws, kSplitK, st)) != cudaSuccess)
         return e;
     // dZ1 = (dZ2 W2) * [h1 > 0], db1
-    a = gemm_args(md->dz2, kHid, 0, W2, kHid, 1, n, kHid, kHid, md->status);
+    a = gemm_args(md->dz2, kHid, 0, md->wb + kWbT2, kHid, 0, n, kHid, kHid, md->status);
     a.mask = md->h1;
     a.ldm = kHid;
     a.out_bf16 = md->dz1;
@@ -1558,8 +1580,7 @@ static void destroy_model(jl_model *md)
 
 static int refresh_bf16(jl_model *md, cudaStream_t st)
 {
-    const int nw = kHid * kIn + kHid * kHid + kBins * kHid;
-    cast_weights_kernel<<<(nw + 255) / 256, 256, 0, st>>>(md->params, md->wb);
+    cast_weights_kernel<<<(kWbAll + 255) / 256, 256, 0, st>>>(md->params, md->wb);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? JL_OK : cuda_fail(e, "cast weights");
 }
@@ -1597,7 +1618,7 @@ int jl_model_create(const float *fourier_B, const float *init_params, jl_model *
     if (e == cudaSuccess) e = cudaMalloc(&md->grads, pb);
     if (e == cudaSuccess) e = cudaMalloc(&md->m, pb);
     if (e == cudaSuccess) e = cudaMalloc(&md->v, pb);
-    if (e == cudaSuccess) e = cudaMalloc(&md->wb, (size_t)(kHid * kIn + kHid * kHid + kBins * kHid) * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&md->wb, (size_t)kWbAll * 2);
     if (e == cudaSuccess) e = cudaMalloc(&md->wpack, (size_t)kPackElems * 2);
     if (e == cudaSuccess) e = cudaMalloc(&md->B, kFreq * 2 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&md->step, 4);
