@@ -133,3 +133,54 @@ def test_map_pins_catch_mutant(name, tmp_path, monkeypatch):
         except AssertionError:
             caught += 1
     assert caught >= 1, "mutant %s survived every map pin" % name
+
+
+# ---- surrogate network (oracle/mlp.py) -------------------------------------
+import importlib.util  # noqa: E402
+
+from oracle import mlp as real_mlp  # noqa: E402
+from tests import test_oracle_mlp as mlp_pins  # noqa: E402
+
+MLP_MUTANTS = {
+    "drop_relu1": ("h1 = _q(np.maximum(a1, 0.0), quant)", "h1 = _q(a1, quant)"),
+    "drop_relu2": ("h2 = _q(np.maximum(a2, 0.0), quant)", "h2 = _q(a2, quant)"),
+    "drop_bias1": ('.T + P["b1"]', ".T"),
+    "drop_bias2": ('.T + P["b2"]', ".T"),
+    "drop_bias3": ('.T + P["b3"]', ".T"),
+    "sin_cos_swapped": ("[np.sin(2 * np.pi * t), np.cos(2 * np.pi * t)]",
+                        "[np.cos(2 * np.pi * t), np.sin(2 * np.pi * t)]"),
+    "no_two_pi": ("[np.sin(2 * np.pi * t), np.cos(2 * np.pi * t)]", "[np.sin(np.pi * t), np.cos(np.pi * t)]"),
+    "c_parts_swapped": ("np.asarray(c, np.float64) @", "np.asarray(c, np.float64)[:, ::-1] @"),
+    "w2_transposed": ('a2 = h1 @ _q(P["W2"], quant).T', 'a2 = h1 @ _q(P["W2"], quant)'),
+    "dz_not_rounded": ("dzq = _q(dz, quant)", "dzq = dz"),
+    "dz2_not_rounded": ("dz2q = _q(dz2, quant)", "dz2q = dz2"),
+    "bias_grad_rounded": ('"b3": dz.sum(axis=0)', '"b3": dzq.sum(axis=0)'),
+    "no_mean_over_rows": ('dz = (f["p"] - T) / n', 'dz = (f["p"] - T)'),
+    "mask_dropped": ('dz1 = dh1 * (f["h1"] > 0)', "dz1 = dh1"),
+    "mask_wrong_layer": ('dz2 = dh2 * (f["h2"] > 0)', 'dz2 = dh2 * (f["h1"] > 0)'),
+    "dw2_wrong_input": ('g["W2"] = dz2q.T @ f["h1"]', 'g["W2"] = dz2q.T @ f["h2"]'),
+    "dh1_not_transposed": ('dh1 = dz2q @ _q(P["W2"], quant)', 'dh1 = dz2q @ _q(P["W2"], quant).T'),
+    "adam_bias_correction": ("mh = mk / (1 - beta1 ** t)", "mh = mk / (1 - beta1 ** (t + 1))"),
+    "adam_no_sqrt": ("(np.sqrt(vh) + eps)", "(vh + eps)"),
+}
+
+MLP_CHECKS = [mlp_pins.check_hand_forward, mlp_pins.check_hand_grads, mlp_pins.check_adam_constant_gradient]
+
+
+@pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
+def test_mlp_pins_catch_mutant(name, tmp_path):
+    old, new = MLP_MUTANTS[name]
+    src = open(real_mlp.__file__).read()
+    assert src.count(old) == 1, old
+    path = tmp_path / "mlp_mutant.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("mlp_mutant", str(path))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    caught = 0
+    for chk in MLP_CHECKS:
+        try:
+            chk(m)
+        except (AssertionError, ValueError):
+            caught += 1
+    assert caught >= 1, "mutant %s survived every surrogate pin" % name
