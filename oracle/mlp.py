@@ -5,7 +5,7 @@ its Julia frame, so that many C can be screened before any is rendered (the
 paper's motivation: sample the parameter space quickly and comprehensively,
 Sec. 1, and use the Mandelbrot set as a roadmap for C, Sec. 3).  Network:
 
-    phi(C) = [sin(2 pi B C), cos(2 pi B C)]        B: 32 x 2, fixed
+    phi(C) = [sin(2 pi B C), cos(2 pi B C)]        B: 32 x 2, fixed (B C in binary32)
     h1 = relu(phi W1^T + b1)                          64 -> 256
     h2 = relu(h1 W2^T + b2)                           256 -> 256
     p  = softmax(h2 W3^T + b3)                        256 -> 101
@@ -34,8 +34,16 @@ def bf16(x):
 
 
 def features(c, B):
-    """phi(C): (n, 64) = [sin(2 pi C B^T), cos(2 pi C B^T)]; c (n, 2), B (32, 2)."""
-    t = np.asarray(c, np.float64) @ np.asarray(B, np.float64).T
+    """phi(C): (n, 64) = [sin(2 pi t), cos(2 pi t)] with t = C B^T; c (n, 2),
+    B (32, 2).  C and B are binary32 values and the phase t_j = B_j0 cr +
+    B_j1 ci is formed in binary32 (each product and the sum rounded, no fused
+    multiply-add), the precision the network accumulates in; the features
+    are rounded to bfloat16 next, and that rounding must be decided from the
+    same t on both sides.  Sine and cosine are then evaluated in float64."""
+    c32 = np.asarray(c, np.float32)
+    B32 = np.asarray(B, np.float32)
+    t = c32[:, None, 0] * B32[None, :, 0] + c32[:, None, 1] * B32[None, :, 1]   # binary32 throughout
+    t = t.astype(np.float64)
     return np.concatenate([np.sin(2 * np.pi * t), np.cos(2 * np.pi * t)], axis=1)
 
 
@@ -66,8 +74,10 @@ def loss(params, c, B, T, quant=False):
     return float(-(np.asarray(T, np.float64) * np.log(f["p"])).sum(axis=1).mean())
 
 
-def grads(params, c, B, T, quant=False):
-    """Loss and gradients of every parameter (backpropagation, float64)."""
+def grads(params, c, B, T, quant=False, terms=False):
+    """Loss and gradients of every parameter (backpropagation, float64).
+    With terms=True also returns the forward values and the backward error
+    terms (dz, dz2, dz1 and their rounded forms) as a third result."""
     P = {k: np.asarray(v, np.float64) for k, v in params.items()}
     f = forward(params, c, B, quant)
     n = f["p"].shape[0]
@@ -86,6 +96,8 @@ def grads(params, c, B, T, quant=False):
     dz1q = _q(dz1, quant)
     g["W1"] = dz1q.T @ f["phi"]
     g["b1"] = dz1.sum(axis=0)
+    if terms:
+        return L, g, dict(f, dz=dz, dzq=dzq, dz2=dz2, dz2q=dz2q, dz1=dz1, dz1q=dz1q)
     return L, g
 
 

@@ -70,10 +70,21 @@ def test_features():
     z = mlp.features(np.zeros((1, 2)), B)
     assert (z[0, :32] == 0).all() and (z[0, 32:] == 1).all()
     # integer-period shift: C -> C + e with B e integer leaves phi unchanged
+    # (dyadic C, so every binary32 phase is exact)
     Bi = np.array([[1.0, 0.0], [2.0, 3.0]])
-    a = mlp.features(np.array([[0.1, 0.2]]), Bi)
-    b = mlp.features(np.array([[1.1, 0.2]]), Bi)
+    a = mlp.features(np.array([[0.125, 0.375]]), Bi)
+    b = mlp.features(np.array([[1.125, 0.375]]), Bi)
     assert np.allclose(a[:, [0, 2]], b[:, [0, 2]], atol=1e-12)
+    check_features_binary32_phase()
+
+
+def check_features_binary32_phase(m=mlp):
+    """The phase is rounded to binary32: C = (0.1, 0.3) and B row (3, 7) give
+    t = fl(fl(3 * 0.1f) + fl(7 * 0.3f)) = 2.4000000953674316, not 2.4."""
+    t32 = np.float32(np.float32(3) * np.float32(0.1)) + np.float32(np.float32(7) * np.float32(0.3))
+    assert float(t32) == 2.4000000953674316
+    f = m.features(np.array([[0.1, 0.3]]), np.array([[3.0, 7.0]]))
+    assert f[0, 0] == math.sin(2 * math.pi * float(t32)) and f[0, 1] == math.cos(2 * math.pi * float(t32))
 
 
 def test_adam_first_step_closed_form():

@@ -150,7 +150,9 @@ MLP_MUTANTS = {
     "sin_cos_swapped": ("[np.sin(2 * np.pi * t), np.cos(2 * np.pi * t)]",
                         "[np.cos(2 * np.pi * t), np.sin(2 * np.pi * t)]"),
     "no_two_pi": ("[np.sin(2 * np.pi * t), np.cos(2 * np.pi * t)]", "[np.sin(np.pi * t), np.cos(np.pi * t)]"),
-    "c_parts_swapped": ("np.asarray(c, np.float64) @", "np.asarray(c, np.float64)[:, ::-1] @"),
+    "c_parts_swapped": ("c32[:, None, 0] * B32[None, :, 0] + c32[:, None, 1] * B32[None, :, 1]",
+                        "c32[:, None, 1] * B32[None, :, 0] + c32[:, None, 0] * B32[None, :, 1]"),
+    "phase_in_float64": ("    t = t.astype(np.float64)\n", "    t = c32.astype(np.float64) @ B32.astype(np.float64).T\n"),
     "w2_transposed": ('a2 = h1 @ _q(P["W2"], quant).T', 'a2 = h1 @ _q(P["W2"], quant)'),
     "dz_not_rounded": ("dzq = _q(dz, quant)", "dzq = dz"),
     "dz2_not_rounded": ("dz2q = _q(dz2, quant)", "dz2q = dz2"),
@@ -164,7 +166,8 @@ MLP_MUTANTS = {
     "adam_no_sqrt": ("(np.sqrt(vh) + eps)", "(vh + eps)"),
 }
 
-MLP_CHECKS = [mlp_pins.check_hand_forward, mlp_pins.check_hand_grads, mlp_pins.check_adam_constant_gradient]
+MLP_CHECKS = [mlp_pins.check_hand_forward, mlp_pins.check_hand_grads, mlp_pins.check_adam_constant_gradient,
+              mlp_pins.check_features_binary32_phase]
 
 
 @pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
