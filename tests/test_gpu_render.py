@@ -287,3 +287,65 @@ def test_compact_kernel_frames(cuda, T):
         f = dict(f)
         f["precision"] = 0
         check_frame(f, variant=v)
+
+
+# Julia frames with |C|^2 >= 3.99: the monotone-escape argument behind the
+# blocked test does not cover them, so the binary64 kernels take their exact
+# step-by-step branch for every pixel (and the binary32 kernels theirs).
+UNSAFE_C = [
+    dict(c=2.5 + 0.1j, rect=(-2.0, 2.0, -1.5, 1.5), W=480, H=360, max_iter=100),
+    dict(c=-1.9999 + 0j, rect=(-2.0, 2.0, -1.0, 1.0), W=640, H=321, max_iter=1000),
+    dict(c=-2 + 0j, rect=(-2.1, 2.1, -0.5, 0.5), W=640, H=161, max_iter=1000),
+    dict(c=-2 + 0j, rect=(-2.0, 2.0, -0.25, 0.25), W=1001, H=1, max_iter=2000),     # the segment [-2, 2]
+    dict(c=1.414 + 1.414j, rect=(-2.0, 2.0, -2.0, 2.0), W=512, H=512, max_iter=200),  # |C|^2 = 3.998792
+    dict(c=-2.0001 + 0j, rect=(-2.1, 2.1, -1.0, 1.0), W=400, H=200, max_iter=5000),
+    dict(c=2j, rect=(-1.6, 1.6, -1.6, 1.6), W=333, H=297, max_iter=1000),           # |C| = 2 exactly
+]
+
+
+@pytest.mark.parametrize("idx", range(len(UNSAFE_C)))
+@pytest.mark.parametrize("prec", [1, 0])
+def test_unsafe_band_full_views(cuda, idx, prec):
+    """Full views of Julia sets with |C|^2 >= 3.99 in every kernel variant of
+    the precision, bit-exact against the oracle (counts and colours; the
+    histogram for the default variant)."""
+    import ctypes
+    f = dict(UNSAFE_C[idx], mode=0, precision=prec)
+    k = oracle_render(f)
+    L = jl._lib.lib()
+    n = L.jl_variant_list(prec, None, 0)
+    buf = (ctypes.c_int32 * (2 * n))()
+    L.jl_variant_list(prec, buf, n)
+    variants = [None] + [(buf[2 * i], buf[2 * i + 1], t, 0) for i in range(n) for t in (128, 256)]
+    for v in variants:
+        g = gpu_render(f, variant=v, hist=v is None)
+        mism = int((g["counts"] != k).sum())
+        assert mism == 0, "%d count mismatches (of %d), variant %s" % (mism, k.size, v)
+        assert (g["rgba"] == oracle.colour(k, f["max_iter"], PAL)).all()
+        if v is None:
+            assert (g["hist"] == oracle.hist(k, f["max_iter"])).all()
+
+
+@pytest.mark.parametrize("side", [10, 32, 100, 316, 1000, 3162, 10000])
+def test_fig1_size_sweep_frames(cuda, side):
+    """The square frames of the Fig. 1 size sweep (Julia C = -0.8+0.156i over
+    [-2,2]^2, limit 100, binary32, uint16 + RGBA8) in the launch the bench
+    times: whole frames up to 1000 per side; above that 32 rows (the first,
+    the last, the middle and 29 seeded ones) against the oracle, plus the
+    histogram of the whole frame against the GPU counts' own histogram."""
+    f = dict(c=-0.8 + 0.156j, rect=(-2.0, 2.0, -2.0, 2.0), W=side, H=side, max_iter=100, mode=0, precision=0)
+    if side <= 1000:
+        check_frame(f)
+        return
+    g = gpu_render(f, hist=True)
+    rng = np.random.default_rng(side)
+    rows = np.unique(np.concatenate([[0, side - 1, side // 2], rng.choice(side, 29, replace=False)]))
+    k = oracle.render_rows(f["c"], f["rect"], side, side, rows, 100, 0, 0)
+    mism = int((g["counts"][rows] != k).sum())
+    assert mism == 0, "%d mismatches in %d sampled rows" % (mism, rows.size)
+    assert (g["rgba"][rows] == oracle.colour(k, 100, PAL)).all()
+    assert (g["hist"] == oracle.hist(g["counts"], 100)).all()
+    # 180-degree rotation symmetry of the whole frame (the grid's coordinates
+    # are exact negatives of each other when the side is even)
+    if side % 2 == 0:
+        assert (g["counts"] == g["counts"][::-1, ::-1]).all()
