@@ -183,7 +183,9 @@ int jl_probe_peak(int32_t kind, int32_t iters, double *lane_ops_per_s, double *s
  * fails or fragments that reservation.
  *
  * Arguments, outputs and results are those of jl_render (counts, rgba and
- * hist are caller-owned device buffers; palette is a host pointer or NULL).
+ * hist are caller-owned device buffers; palette is a host pointer or NULL),
+ * and so is the kernel: the autotuned variant when jl_autotune has run or a
+ * tuning table was loaded, else the default one.
  * The scratch it needs (coordinate tables, work counter, status word) lives
  * in one file-scope device array of JL_STATIC_SCRATCH_BYTES bytes, which
  * every GPU that loads the library holds until the process exits.
@@ -192,8 +194,11 @@ int jl_probe_peak(int32_t kind, int32_t iters, double *lane_ops_per_s, double *s
  *     width + height <= 65472 in binary32 and <= 32736 in binary64.  Larger
  *     frames return JL_EINVAL with the limit in jl_last_error().
  *   - Set-up: the first call on a device (with that device current) looks up
- *     the array's device address with cudaGetSymbolAddress; make that first
- *     call before any stream capture.
+ *     the array's device address with cudaGetSymbolAddress and keeps it for
+ *     the life of the process; make that first call before any stream
+ *     capture.  cudaDeviceReset destroys the module that holds the array, so
+ *     the kept address is stale afterwards: do not call this entry point
+ *     after resetting the device.
  *   - Sharing: every call on a device uses the same array and leaves its
  *     contents behind; each call clears the counter and status it relies on
  *     (with cudaMemsetAsync, which does not allocate).  Calls whose work

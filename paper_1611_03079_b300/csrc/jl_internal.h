@@ -99,6 +99,12 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
 int default_palette_bytes(uint8_t *out);
 int select_precision(const jl_rect &r, int W, int H);
 
+// Launches the escape kernel of one frame whose coordinate tables are filled:
+// clears the 16-byte control block `ctl` (work counter, status) and the
+// histogram, runs the tuned (or `vopt`'s) variant, finalises the histogram.
+// Allocates nothing.
+int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStream_t st, const Variant *vopt);
+
 // Default variants, and the autotuned one when the tuner has run.
 Variant default_variant(int precision, int max_iter);
 Variant tuned_variant(int precision, int max_iter);

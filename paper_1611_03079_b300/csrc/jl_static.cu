@@ -82,50 +82,11 @@ extern "C" int jl_render_static(double cr, double ci, jl_rect rect, int32_t widt
     F.counts = static_cast<uint8_t *>(counts);
     F.rgba = reinterpret_cast<uint32_t *>(rgba);
     F.hist_bins = reinterpret_cast<uint32_t *>(hist);
-    unsigned long long *counter = reinterpret_cast<unsigned long long *>(base + coord_pad);
-    int32_t *status = reinterpret_cast<int32_t *>(base + coord_pad + 8);
-
-    // The array keeps the previous call's contents: the work counter and the
-    // status word must start at zero, the coordinate tables are rewritten.
-    cudaError_t e = cudaMemsetAsync(base + coord_pad, 0, 16, st);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaMemsetAsync(static counter)");
-    if (F.hist_bins) {
-        e = cudaMemsetAsync(F.hist_bins, 0, ((size_t)F.max_iter + 1) * 4, st);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "cudaMemsetAsync(hist)");
-    }
-    e = launch_coords(nullptr, &F, 1, st);
+    cudaError_t e = launch_coords(nullptr, &F, 1, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "coords kernel launch");
-
-    EscapeArgs a;
-    memset(&a, 0, sizeof(a));
-    a.frames = nullptr;
-    a.n_frames = 1;
-    a.hist_smem = (F.hist_bins && F.max_iter + 1 <= 4096) ? 1 : 0;
-    a.total_chunks = F.chunk_count;
-    a.total_tiles = F.tile_count;
-    a.chunk_counter = counter;
-    a.status = status;
-    a.cycle_budget = 0;
-    uint8_t pal[1024];
-    if (palette)
-        memcpy(pal, palette, 1024);
-    else
-        default_palette_bytes(pal);
-    memcpy(a.palette, pal, 1024);
-    a.single = F;
-    const int sms = device_sm_count();
-    if (sms <= 0)
-        return fail(JL_EUNSUPPORTED, "no CUDA device");
-    e = launch_escape(a, prec, default_variant(prec, F.max_iter), sms, st);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "escape kernel launch");
-    if (F.hist_bins) {
-        e = launch_hist_finalize(nullptr, &F, 1, st);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "histogram finalize launch");
-    }
-    return JL_OK;
+    // The array keeps the previous call's contents: launch_frame clears the
+    // work counter and status word (the 16 bytes after the tables) and the
+    // histogram with cudaMemsetAsync, and the tables were just rewritten.
+    return launch_frame(F, prec, palette, base + coord_pad, st, nullptr);
 }

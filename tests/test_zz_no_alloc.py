@@ -71,3 +71,74 @@ def test_static_rejects_oversized_frames():
     assert rc == _lib.JL_EINVAL
     msg = L.jl_last_error().decode()
     assert "static scratch" in msg and "32736" in msg
+
+
+def _pool():
+    """The device's default memory pool (the one stream-ordered allocations
+    such as jl_render's scratch come from), through the driver API."""
+    from cuda.bindings import driver as drv
+    drv.cuInit(0)
+    err, dev = drv.cuDeviceGet(0)
+    assert err == drv.CUresult.CUDA_SUCCESS
+    err, pool = drv.cuDeviceGetDefaultMemPool(dev)
+    assert err == drv.CUresult.CUDA_SUCCESS
+    attr = drv.CUmemPool_attribute.CU_MEMPOOL_ATTR_USED_MEM_HIGH
+
+    def reset():
+        (e,) = drv.cuMemPoolSetAttribute(pool, attr, drv.cuuint64_t(0))
+        assert e == drv.CUresult.CUDA_SUCCESS
+
+    def high():
+        e, v = drv.cuMemPoolGetAttribute(pool, attr)
+        assert e == drv.CUresult.CUDA_SUCCESS
+        return int(v)
+    return reset, high
+
+
+def test_static_allocates_nothing():
+    """The pool's high-water mark of memory in use stays where it was across
+    jl_render_static calls, while jl_render (which takes its scratch from the
+    pool) raises it: the positive control that shows the measurement works."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_03079_b300 import _lib, workloads as wl
+    L = _lib.lib()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    pal = np.ascontiguousarray(wl.random_palette(7))
+    reset, high = _pool()
+    for frame in FRAMES:
+        _call(L.jl_render_static, frame, torch, dev, pal)      # set-up done before measuring
+        torch.cuda.synchronize()
+        reset()
+        h0 = high()
+        _call(L.jl_render_static, frame, torch, dev, pal)
+        _call(L.jl_render_static, frame, torch, dev, pal)
+        torch.cuda.synchronize()
+        assert high() == h0
+        _call(L.jl_render, frame, torch, dev, pal)
+        torch.cuda.synchronize()
+        assert high() > h0
+
+
+@pytest.mark.parametrize("prec,limit", [(1, 32736), (0, 65472)])
+def test_static_size_limit_exact(prec, limit):
+    """width + height at the stated limit is rendered (and equals jl_render);
+    one more is refused with JL_EINVAL."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_03079_b300 import _lib
+    L = _lib.lib()
+    for W, expect in ((limit - 1, _lib.JL_OK), (limit, _lib.JL_EINVAL)):
+        outs = []
+        for fn in (L.jl_render_static, L.jl_render) if expect == _lib.JL_OK else (L.jl_render_static,):
+            counts = torch.zeros((1, W), dtype=torch.int16, device="cuda")
+            rc = fn(-0.8, 0.156, _lib.Rect(-2, 2, -0.5, 0.5), W, 1, 100, prec, 0, _lib.JL_COUNT_U16,
+                    ctypes.c_void_p(counts.data_ptr()), None, None, None, None)
+            torch.cuda.synchronize()
+            assert rc == expect, (W, rc, L.jl_last_error())
+            outs.append(counts.cpu().numpy())
+        if expect == _lib.JL_OK:
+            assert (outs[0] == outs[1]).all()
