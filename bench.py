@@ -4,8 +4,9 @@
 One step = the throughput sweep: 16 renders of 4096x4096 pixels (Julia over
 [-1.6,1.6]^2 for C in {0.285+0.01i, -0.7269+0.1889i, -0.4+0.6i} and the
 Mandelbrot plane over [-2.5,1]x[-1.75,1.75], limits 100 and 1000, binary32 and
-binary64), uint16 counts + RGBA8 from a 256-entry palette, every render
-through the C ABI (jl_render).  The metric is pixel-iterations per second
+binary64), uint16 counts + RGBA8 from a 256-entry palette, all 16 frames as
+one batch plan through the C ABI (one jl_batch_launch, a captured CUDA graph,
+per step).  The metric is pixel-iterations per second
 (sum of escape counts / time) and the fraction of the binary32 / binary64
 issue peak measured on the same GPU by jl_probe_peak.
 
@@ -13,8 +14,9 @@ issue peak measured on the same GPU by jl_probe_peak.
 
 N > 1 (torchrun): each rank renders its own full sweep (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.  --impl reference
-times the CPU oracle on the host cores on a bounded row sample of the same
-workload.
+times the CPU oracle on the host cores on a fixed row sample of the same
+workload (every ORACLE_ROW_STRIDE-th row of every frame), the same sample as
+the JSON line's cpu_baseline.
 """
 import argparse
 import json
@@ -33,6 +35,9 @@ WORKLOAD = ("throughput sweep: 16 renders of 4096x4096 (Julia [-1.6,1.6]^2, C in
             "-0.7269+0.1889i, -0.4+0.6i}; Mandelbrot [-2.5,1]x[-1.75,1.75]) x limit {100,1000} x "
             "{binary32, binary64}; uint16 counts + RGBA8")
 OPS_PER_ITER = 8  # 3 multiplies + 5 adds per escape-time step (no FMA)
+# The oracle's sample of the sweep: every 8th row of each frame (512 rows of
+# 4096, interleaved over the host threads), about a second of all-core work.
+ORACLE_ROW_STRIDE = 8
 
 
 def parse():
@@ -42,7 +47,6 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--size", type=int, default=4096)
-    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU sample")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-survey", action="store_true", help="skip the surrogate screening workload")
@@ -205,32 +209,22 @@ def dist_setup(backend):
     return world, rank, local
 
 
-def cpu_sample(frames, target_s, threads=None):
-    """Oracle (as it stands) on a strided row sample of every frame, sized to
-    about target_s seconds of CPU work.  Returns (Giter/s, cores, description,
-    iterations, seconds)."""
+def cpu_sample(frames, stride=ORACLE_ROW_STRIDE, threads=None):
+    """The oracle (as it stands) on every stride-th row of every frame, rows
+    interleaved over the host threads.  Returns (Giter/s, threads,
+    description, iterations, seconds)."""
     import numpy as np
     import oracle
     threads = threads or min(os.cpu_count() or 1, 64)
-
-    def run(stride):
-        t0 = time.perf_counter()
-        iters = 0
-        rows = 0
-        for f in frames:
-            n_rows = len(range(stride // 2, f["H"], stride))
-            k = oracle.render_strided(f["c"], f["rect"], f["W"], f["H"], stride // 2, stride, n_rows,
-                                      f["max_iter"], f["mode"], f["precision"], threads=threads)
-            iters += int(k.astype(np.int64).sum())
-            rows += n_rows
-        return iters, time.perf_counter() - t0, rows
-
-    probe_stride = 512
-    it0, t0, _ = run(probe_stride)
-    est_full = t0 * probe_stride
-    stride = max(1, int(round(est_full / max(target_s, 0.1))))
-    stride = min(stride, probe_stride)
-    iters, secs, rows = run(stride)
+    t0 = time.perf_counter()
+    iters = rows = 0
+    for f in frames:
+        n_rows = len(range(stride // 2, f["H"], stride))
+        k = oracle.render_strided(f["c"], f["rect"], f["W"], f["H"], stride // 2, stride, n_rows,
+                                  f["max_iter"], f["mode"], f["precision"], threads=threads)
+        iters += int(k.astype(np.int64).sum())
+        rows += n_rows
+    secs = time.perf_counter() - t0
     desc = ("every %d-th row of each of the %d sweep frames (%d rows, %.3g G iterations), %d threads"
             % (stride, len(frames), rows, iters / 1e9, threads))
     return iters / secs / 1e9, threads, desc, iters, secs
@@ -468,14 +462,13 @@ def run_reference(args):
         return
     from paper_1611_03079_b300 import workloads as wl
     frames = wl.throughput_sweep(args.size)
-    per_step = max(args.cpu_seconds / max(args.steps + args.warmup, 1), 1.0)
     for _ in range(args.warmup):
-        cpu_sample(frames, per_step)
+        cpu_sample(frames)
     vals = []
     t_all = time.perf_counter()
     desc = cores = None
     for _ in range(args.steps):
-        v, cores, desc, _, _ = cpu_sample(frames, per_step)
+        v, cores, desc, _, _ = cpu_sample(frames)
         vals.append(v)
     wall = time.perf_counter() - t_all
     value = statistics.mean(vals)
@@ -513,12 +506,12 @@ def main():
     # The binary32 denominator is the larger of the scalar FMUL/FADD rate and
     # the packed add/mul.rn.f32x2 rate (separately rounded operations either way).
     probes = {}
-    for kind, iters in ((0, 200000), (1, 4000), (5, 200000)):
+    for kind, iters in ((0, 200000), (1, 4000), (2, 200000)):
         ops = ctypes.c_double(0)
         secs = ctypes.c_double(0)
         _lib.check(L.jl_probe_peak(kind, iters, ctypes.byref(ops), ctypes.byref(secs), stream.cuda_stream))
         probes[kind] = ops.value
-    peaks = {0: max(probes[0], probes[5]), 1: probes[1]}
+    peaks = {0: max(probes[0], probes[2]), 1: probes[1]}
 
     # launch-shape autotuning (one-off, before any timing): per precision and
     # limit bucket, calibrated on the sweep frames themselves
@@ -548,7 +541,7 @@ def main():
     # the per-precision plans use the kernels it chose.
     plan = jl.Batch(frames, palette=pal, tune=True)
     sub = {p: [i for i in range(len(frames)) if frames[i]["precision"] == p] for p in (0, 1)}
-    chosen = {"fp32": plan.variant(0)[:3], "fp64": plan.variant(1)}
+    chosen = {"fp32": plan.variant(0), "fp64": plan.variant(1)}
     sub_plans = {p: jl.Batch([frames[i] for i in sub[p]], palette=pal, variants=chosen) for p in (0, 1)}
     W_ = max(args.warmup, 3)
     for _ in range(W_):
@@ -613,7 +606,7 @@ def main():
                                     frames[i]["W"] * frames[i]["H"] for i in sub[dom])),
                 "peak_source": "measured on this GPU by jl_probe_peak (independent multiply/add chains, no FMA; "
                                "binary32: the larger of scalar FMUL/FADD, %.0f G lane-ops/s, and packed "
-                               "add/mul.f32x2, %.0f)" % (probes[0] / 1e9, probes[5] / 1e9),
+                               "add/mul.f32x2, %.0f)" % (probes[0] / 1e9, probes[2] / 1e9),
                 "algorithmic_unit": "8 %s lane ops per escape-time iteration" % ("binary64" if dom else "binary32"),
                 "timing": "CUDA events around a plan of the %s sweep frames alone" % ("binary64" if dom else
                                                                                     "binary32")}
@@ -633,22 +626,33 @@ def main():
             hf.render(stream)
             times.append(time.perf_counter() - t0)
         e2e_s = statistics.median(times)
-        ok = all((hf.counts(i).astype(np.int64).sum() == iters[i]) for i in range(len(frames)))
+        ok = all(np.array_equal(hf.counts(i), plan.counts(i).cpu().numpy().view(np.uint16)) and
+                 np.array_equal(hf.rgba(i), plan.rgba(i).cpu().numpy()) for i in range(len(frames)))
         e2e = {"value": total_iters / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 96 * n,
                "d2h_bytes_per_step": int(hf.d2h_bytes), "ms_per_step": e2e_s * 1e3, "steps": len(times),
-               "counts_match_device": bool(ok),
+               "outputs_match_device_plan": bool(ok),
                "launches_per_step": hf.launches(),
-               "note": "host plan (jl_host_plan_run): 16 frames per step rendered on 4 internal render "
-                       "streams into one device slot each (the last frame as 4 row bands) and copied to "
+               "note": "host plan (jl_host_plan_run): per step, each frame's coordinate tables are computed "
+                       "from its description (step A1), then the 16 frames render on 4 internal render "
+                       "streams into one device slot each (the last frame as 4 row bands) and are copied to "
                        "pinned host memory (counts + RGBA8) on 2 copy streams as each frame (band) finishes; "
                        "host wall clock per call (median of steps), the call returns after the last copy; "
-                       "h2d = the frame descriptions (96 B each)"}
+                       "h2d = the 16 frame descriptions (96 B each), which reach the device as kernel "
+                       "parameters of the coordinate and escape launches (no separate copy); the host "
+                       "outputs equal the device plan's byte for byte"}
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        v, cores, desc, it, secs = cpu_sample(frames, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
-               "seconds": secs}
+        # the reference arm itself, in a fresh process (the same code and
+        # sample; in this process torch's host threads would compete with
+        # the oracle's for the cores)
+        env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "3",
+                              "--warmup", "1", "--size", str(args.size)], capture_output=True, text=True, env=env,
+                             check=True).stdout
+        ref = json.loads(out.strip().splitlines()[-1])
+        cpu = dict(ref["cpu_baseline"])
+        cpu["sample"] += "; mean of 3 timed runs after 1 warm-up, in a separate process (bench.py --impl reference)"
 
     # binary32-vs-binary64 count mismatch of the sweep frames (same frame, both precisions)
     mismatch = {}
@@ -690,6 +694,9 @@ def main():
                     f["W"] * f["H"] for f in frames), "iterations_per_step": total_iters,
                     "l2": "outputs are 1.6 GB per step, larger than the 126 MB L2; no flush needed",
                     "parallelism": "replicas" if world > 1 else "single GPU"},
+                "survey_summary": None if survey is None else {
+                    k: survey[k] for k in ("screened_per_s", "speedup_vs_plain_render", "judge_l1_mean",
+                                           "l1_target_met", "heldout_l1_mean", "train_s")},
                 "roofline": roofline, "roofline_other_precision": roofline_other,
                 "by_precision": {("binary64" if p else "binary32"): by_prec[p] for p in (0, 1)},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
@@ -702,7 +709,7 @@ def main():
                 **extra,
                 "peaks_gops": {"binary32": peaks[0] / 1e9, "binary64": peaks[1] / 1e9,
                                "binary32_scalar_fmul_fadd": probes[0] / 1e9,
-                               "binary32_packed_add_mul": probes[5] / 1e9}}
+                               "binary32_packed_add_mul": probes[2] / 1e9}}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -128,17 +128,13 @@ int jl_render_to_host(double cr, double ci, jl_rect rect, int32_t width, int32_t
  * ctas_per_sm are then ignored).  ppt = 0 with unroll = T in 1..32 (binary32
  * only) selects the compacting tile kernel: the static kernel's tiles, with a
  * patch's live pixels parked in a per-warp ring once T or fewer of its 32
- * are left and resumed later as full batches of 32.  emu (binary64 with ppt > 0 only): 1 = all
- * arithmetic on the hardware binary64 pipe; k > 1 = one warp group (4 warps)
- * in every k uses the hardware pipe and the others the bit-exact
- * integer-pipe binary64 arithmetic (see jl_selftest_f64), so both kinds of
- * units work at once.  Unsupported (ppt, unroll) pairs return JL_EINVAL;
+ * are left and resumed later as full batches of 32.  Unsupported (ppt, unroll) pairs return JL_EINVAL;
  * jl_variant_list() enumerates the supported ones.
  */
 int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t height, int32_t max_iter,
                       int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
                       const uint8_t *palette, float *hist, int32_t ppt, int32_t unroll, int32_t threads,
-                      int32_t ctas_per_sm, int32_t emu, void *stream);
+                      int32_t ctas_per_sm, void *stream);
 
 /*
  * Writes up to `cap` supported (ppt, unroll) pairs for `precision` into
@@ -148,23 +144,14 @@ int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t
 int jl_variant_list(int32_t precision, int32_t *pairs, int32_t cap);
 
 /*
- * Issue-rate probe.  kind 0 (JL_FP32) / 1 (JL_FP64): 8 independent
- * multiply/add chains per thread on every SM (separate FMUL and FADD, no
- * FMA); kind 2: 32-bit xor + add chains; kind 3: 32-bit multiply-add chains;
- * kind 4: high half of 32x32-bit products (xor-chained); kind 5: packed
- * binary32 pairs, separate chains of add.rn.f32x2 and mul.rn.f32x2 (two
- * lane operations per instruction; no product feeds a sum); kinds 6, 7, 8:
- * 64-bit integer add, shift-and-xor (3 operations), compare-and-select
- * (2 operations) chains; kind 9: binary64 fused multiply-add chains (one
- * DFMA per step; compare with kind 1); kinds 10, 11: two chains per thread
- * of the binary64 escape step as the lane-refill kernel forms it (six
- * binary64 operations per step, counted as the lane operations), kind 11
- * with that kernel's per-step binary32 test work; kinds 12, 13: kind 10 with
- * two or three CTAs of 256 threads per SM (4 or 6 warps per scheduler; the
- * others run 8 CTAs per SM, as many as fit).  Returns the
- * achieved lane operations per second in *lane_ops_per_s (and the kernel
- * time in *seconds if non-NULL).  Kinds 0 and 1 are the denominators of the
- * escape kernels' ALU roofline.  Synchronises `stream`.
+ * Issue-rate probe, the denominator of the escape kernels' ALU roofline.
+ * kind 0 (JL_FP32) / 1 (JL_FP64): 8 independent multiply/add chains per
+ * thread, 8 CTAs of 256 threads on every SM (separate FMUL and FADD, DMUL
+ * and DADD, no FMA); kind 2: packed binary32 pairs, separate chains of
+ * add.rn.f32x2 and mul.rn.f32x2 (two lane operations per instruction; no
+ * product feeds a sum).  Returns the achieved lane operations per second in
+ * *lane_ops_per_s (and the kernel time in *seconds if non-NULL); JL_EINVAL
+ * for another kind.  Synchronises `stream`.
  */
 int jl_probe_peak(int32_t kind, int32_t iters, double *lane_ops_per_s, double *seconds, void *stream);
 
@@ -283,7 +270,6 @@ typedef struct {
     int32_t fp64_ppt, fp64_unroll, fp64_threads;
     int32_t variant_flags;  /* bit 0 / bit 1: the fp32 / fp64 (ppt, unroll) pair is given explicitly
                                (needed for the static kernel, ppt = unroll = 0) */
-    int32_t fp64_emu;       /* 0 = tuned or default; else as `emu` of jl_render_variant */
     int32_t tune;           /* 1: for each precision group without an explicit variant, time
                                candidate kernels (the tuned and the default variant, the tile
                                kernels, a few lane-refill shapes for binary64) on the plan's own
@@ -309,8 +295,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
 /* The kernel variant the plan uses for a precision group (chosen at creation:
  * explicit option, the plan's own timing with opts.tune, else the tuned or
  * default one); meaningful for groups that have frames. */
-int jl_batch_variant(const jl_batch *b, int32_t precision, int32_t *ppt, int32_t *unroll, int32_t *threads,
-                     int32_t *emu);
+int jl_batch_variant(const jl_batch *b, int32_t precision, int32_t *ppt, int32_t *unroll, int32_t *threads);
 
 /* Render every frame of the plan: one cudaGraphLaunch on `stream`
  * (asynchronous; nothing is allocated). */
@@ -356,11 +341,12 @@ int jl_render_frames_to_host(const jl_frame *frames, int32_t n, void *counts_hos
 
 /*
  * The same as a reusable plan: jl_host_plan_create validates the frames and
- * does the once-per-frame-set work (coordinate tables of every frame, `depth`
- * device slots, internal streams and events); jl_host_plan_run renders every frame into
- * the host buffers given at creation (which must stay valid while the plan
- * lives), with the copies overlapped, and returns when the last copy has
- * completed.  Runs on the device current at creation (JL_EINVAL otherwise).
+ * does the once-per-frame-set work (`depth` device slots, room for the
+ * coordinate tables, internal streams and events); every jl_host_plan_run
+ * computes each frame's coordinate tables from its description (the region
+ * covering of Sec. 2) and renders every frame into the host buffers given at
+ * creation (which must stay valid while the plan lives), with the copies
+ * overlapped, and returns when the last copy has completed.  Runs on the device current at creation (JL_EINVAL otherwise).
  * The palette (1024 bytes, or NULL for the default) is copied at creation.
  * jl_host_plan_destroy waits for outstanding work and frees everything.
  */
@@ -380,15 +366,12 @@ int32_t jl_host_plan_launches(const jl_host_plan *plan);
  * ------------------------------------------------------------------------ */
 typedef struct {
     int32_t ppt, unroll, threads, ctas_per_sm;
-    int32_t emu;            /* binary64 integer-pipe share, see jl_render_variant */
-    int32_t reserved;
     double ms;              /* mean time of the calibration set with this variant */
     int32_t candidates;     /* candidates timed (jl_tune_get: 1 if tuned, 0 if default) */
 } jl_tune_result;
 
 /*
- * Times every supported (ppt, unroll) x {128, 256} threads (x emu in {1, 2,
- * 3, 4} for binary64 with ppt > 0 at 256 threads) on the calibration
+ * Times every supported (ppt, unroll) x {128, 256} threads on the calibration
  * frames (their own rect, size, mode and C; `precision` and `max_iter` as
  * given), `reps` timed repetitions each after one warm-up, and records the
  * fastest for (current device, precision, bucket of max_iter: <=128, <=1024,
@@ -504,15 +487,6 @@ int jl_gemm_bf16(const void *A, int32_t lda, int32_t a_trans, const void *B, int
  * out[i] = 2 * in[i] for n device doubles, computed exactly as the kernels do
  * (bit-identical to IEEE x + x except for NaN payloads). */
 int jl_selftest_double(const double *in, double *out, int32_t n, void *stream);
-
-/* Self-test of the integer-pipe binary64 arithmetic the binary64 escape
- * kernels may use: op 0 out = a*b, op 1 out = a*a, op 2 out = a+b (n device
- * doubles each; b ignored for op 1).  special[i] = 1 marks operands or
- * results outside the emulated range (subnormal, infinite, NaN, overflow),
- * for which the kernels use the hardware instructions instead; elsewhere the
- * result equals the IEEE round-to-nearest-even result bit for bit. */
-int jl_selftest_f64(int32_t op, const double *a, const double *b, double *out, int32_t *special, int32_t n,
-                    void *stream);
 
 /* Writes the built-in 256-entry RGBA8 palette (1024 bytes) to `out` (host).
  * Entry 255 (never-escaped points) is opaque black. */

@@ -71,7 +71,7 @@ def render(c, rect, width, height, max_iter=100, precision="fp32", mode="julia",
     Returns a dict with 'counts' (torch uint8/uint16, shape (H, W)), 'rgba'
     (torch uint8, (H, W, 4)) and 'hist' (torch float32, max_iter + 1) for the
     outputs requested.  `out` may supply preallocated tensors under the same
-    keys.  `variant` = (ppt, unroll, threads, ctas_per_sm[, emu]) selects a
+    keys.  `variant` = (ppt, unroll, threads, ctas_per_sm) selects a
     kernel variant explicitly.  Asynchronous on `stream` (default: torch's current
     stream).
     """
@@ -99,10 +99,10 @@ def render(c, rect, width, height, max_iter=100, precision="fp32", mode="julia",
         rc = L.jl_render(cr, ci, _rect(rect), W, H, int(max_iter), prec, md, ct, cnt_ptr, rgba_ptr, pal_ptr,
                          hist_ptr, st)
     else:
-        v = [int(x) for x in variant] + [1] * (5 - len(variant))
-        ppt, unroll, threads, per_sm, emu = v[:5]
+        v = [int(x) for x in variant] + [0] * (4 - len(variant))
+        ppt, unroll, threads, per_sm = v[:4]
         rc = L.jl_render_variant(cr, ci, _rect(rect), W, H, int(max_iter), prec, md, ct, cnt_ptr, rgba_ptr,
-                                 pal_ptr, hist_ptr, ppt, unroll, threads, per_sm, emu, st)
+                                 pal_ptr, hist_ptr, ppt, unroll, threads, per_sm, st)
     check(rc)
     del pal
     return out
@@ -356,8 +356,6 @@ class Batch:
             if "fp64" in variants:
                 v64 = [int(v) for v in variants["fp64"]]
                 opts.fp64_ppt, opts.fp64_unroll, opts.fp64_threads = v64[:3]
-                if len(v64) > 3:
-                    opts.fp64_emu = v64[3]
                 opts.variant_flags |= 2
         opts.cycle_budget = int(cycle_budget)
         opts.tune = 1 if tune else 0
@@ -381,9 +379,9 @@ class Batch:
         return v.value
 
     def variant(self, precision):
-        """(ppt, unroll, threads, emu) of the kernel the plan uses for
+        """(ppt, unroll, threads) of the kernel the plan uses for
         precision 0 (binary32) or 1 (binary64)."""
-        v = [ctypes.c_int32(0) for _ in range(4)]
+        v = [ctypes.c_int32(0) for _ in range(3)]
         check(self._L.jl_batch_variant(self._h, int(precision), *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
 
@@ -446,14 +444,14 @@ def autotune(precision="fp32", max_iter=100, calib=None, reps=3):
         ptr, n = None, 0
     check(L.jl_autotune(_PREC[precision], int(max_iter), ptr, n, int(reps), ctypes.byref(res)))
     return {"ppt": res.ppt, "unroll": res.unroll, "threads": res.threads, "ctas_per_sm": res.ctas_per_sm,
-            "emu": res.emu, "ms": res.ms, "candidates": res.candidates}
+            "ms": res.ms, "candidates": res.candidates}
 
 
 def tune_get(precision="fp32", max_iter=100):
     res = _lib.TuneResult()
     check(_lib.lib().jl_tune_get(_PREC[precision], int(max_iter), ctypes.byref(res)))
     return {"ppt": res.ppt, "unroll": res.unroll, "threads": res.threads, "ctas_per_sm": res.ctas_per_sm,
-            "emu": res.emu, "tuned": bool(res.candidates), "ms": res.ms, "candidates": res.candidates}
+            "tuned": bool(res.candidates), "ms": res.ms, "candidates": res.candidates}
 
 
 def tune_clear():

@@ -43,7 +43,7 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("chunk_len", ctypes.c_int32), ("fp32_ppt", ctypes.c_int32), ("fp32_unroll", ctypes.c_int32),
                 ("fp32_threads", ctypes.c_int32), ("fp64_ppt", ctypes.c_int32), ("fp64_unroll", ctypes.c_int32),
                 ("fp64_threads", ctypes.c_int32), ("variant_flags", ctypes.c_int32),
-                ("fp64_emu", ctypes.c_int32), ("tune", ctypes.c_int32), ("cycle_budget", ctypes.c_int64)]
+                ("tune", ctypes.c_int32), ("cycle_budget", ctypes.c_int64)]
 
 
 class Map(ctypes.Structure):
@@ -56,8 +56,7 @@ class Map(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     """jl_tune_result (include/jl.h)."""
     _fields_ = [("ppt", ctypes.c_int32), ("unroll", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("emu", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("ms", ctypes.c_double), ("candidates", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("ms", ctypes.c_double), ("candidates", ctypes.c_int32)]
 
 
 _lib = None
@@ -79,13 +78,13 @@ SIGNATURES = {
     "jl_render_map": (ctypes.c_int, [ctypes.POINTER(Map), _d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp,
                                      _vp, _vp, _vp, _vp]),
     "jl_render_variant": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
-                                         _vp, _i32, _i32, _i32, _i32, _i32, _vp]),
+                                         _vp, _i32, _i32, _i32, _i32, _vp]),
     "jl_render_static": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp,
                                         _vp]),
     "jl_variant_list": (ctypes.c_int, [_i32, _vp, _i32]),
     "jl_probe_peak": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp]),
     "jl_batch_create": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
-    "jl_batch_variant": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "jl_batch_variant": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "jl_batch_launch": (ctypes.c_int, [_vp, _vp]),
     "jl_batch_status": (ctypes.c_int, [_vp, _vp, _vp]),
     "jl_batch_precisions": (ctypes.c_int, [_vp, _vp, _i32]),
@@ -113,7 +112,6 @@ SIGNATURES = {
     "jl_model_load": (ctypes.c_int, [ctypes.c_char_p, _vp]),
     "jl_gemm_bf16": (ctypes.c_int, [_vp, _i32, _i32, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp]),
     "jl_selftest_double": (ctypes.c_int, [_vp, _vp, _i32, _vp]),
-    "jl_selftest_f64": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, _vp]),
     "jl_render_to_host": (ctypes.c_int, [_d, _d, Rect, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
                                          _vp, _vp]),
 }

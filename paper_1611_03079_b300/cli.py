@@ -32,7 +32,7 @@ def main(argv=None):
     p.add_argument("--precision", default="fp32")
     p.add_argument("--mode", default="julia")
     p.add_argument("--repeat", type=int, default=1)
-    p.add_argument("--variant", type=int, nargs="+", default=None, help="ppt unroll threads ctas_per_sm [emu]")
+    p.add_argument("--variant", type=int, nargs="+", default=None, help="ppt unroll threads ctas_per_sm")
     p.add_argument("--out", default=None)
     p.add_argument("--probe", action="store_true", help="print the issue-rate probes and exit")
     a = p.parse_args(argv)
@@ -191,17 +191,10 @@ def probe():
     from paper_1611_03079_b300 import _lib
     torch.cuda.set_device(0)
     L = _lib.lib()
-    names = {0: "binary32 fmul+fadd", 1: "binary64 dmul+dadd", 2: "int32 xor+add", 3: "int32 mad",
-             4: "int32 mulhi+xor", 5: "binary32x2 packed add / mul chains", 6: "int64 add",
-             7: "int64 shift+xor", 8: "int64 compare+select", 9: "binary64 fused multiply-add",
-             10: "binary64 escape step (6 ops)", 11: "binary64 escape step (6 ops) with the binary32 test",
-             12: "binary64 escape step (6 ops), 4 warps per scheduler",
-             13: "binary64 escape step (6 ops), 6 warps per scheduler"}
+    names = {0: "binary32 fmul+fadd", 1: "binary64 dmul+dadd", 2: "binary32x2 packed add / mul chains"}
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     res = {}
-    for kind, iters in ((0, 200000), (1, 4000), (2, 200000), (3, 200000), (4, 100000), (5, 200000), (6, 20000),
-                        (7, 20000), (8, 20000), (9, 8000), (10, 2000), (11, 2000), (12, 8000),
-                        (13, 6000)):
+    for kind, iters in ((0, 200000), (1, 4000), (2, 200000)):
         ops, secs = ctypes.c_double(0), ctypes.c_double(0)
         _lib.check(L.jl_probe_peak(kind, iters, ctypes.byref(ops), ctypes.byref(secs), None))
         res[names[kind]] = {"G_lane_ops_s": ops.value / 1e9, "ms": secs.value * 1e3,

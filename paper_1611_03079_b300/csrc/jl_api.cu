@@ -269,15 +269,6 @@ int jl_selftest_double(const double *in, double *out, int32_t n, void *stream)
     return e == cudaSuccess ? JL_OK : cuda_fail(e, "jl_selftest_double");
 }
 
-int jl_selftest_f64(int32_t op, const double *a, const double *b, double *out, int32_t *special, int32_t n,
-                    void *stream)
-{
-    if (op < 0 || op > 2 || !a || (op != 1 && !b) || !out || !special || n < 1)
-        return fail(JL_EINVAL, "invalid arguments");
-    cudaError_t e = launch_f64emu(op, a, op == 1 ? a : b, out, special, n, static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? JL_OK : cuda_fail(e, "jl_selftest_f64");
-}
-
 int jl_default_palette(uint8_t *out)
 {
     if (!out)
@@ -306,7 +297,7 @@ int jl_render(double cr, double ci, jl_rect rect, int32_t width, int32_t height,
 int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t height, int32_t max_iter,
                       int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
                       const uint8_t *palette, float *hist, int32_t ppt, int32_t unroll, int32_t threads,
-                      int32_t ctas_per_sm, int32_t emu, void *stream)
+                      int32_t ctas_per_sm, void *stream)
 {
     Frame F;
     int prec = 0;
@@ -322,13 +313,10 @@ int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t
         return fail(JL_EINVAL, "threads must be a multiple of 32 in 32..256");
     if (ctas_per_sm < 0 || ctas_per_sm > 32)
         return fail(JL_EINVAL, "ctas_per_sm must be 0 (occupancy maximum) .. 32");
-    if (emu < 1 || emu > 8)
-        return fail(JL_EINVAL, "emu must be 1..8");
     F.counts = static_cast<uint8_t *>(counts);
     F.rgba = reinterpret_cast<uint32_t *>(rgba);
     F.hist_bins = reinterpret_cast<uint32_t *>(hist);
     Variant v{ppt, unroll, threads, ctas_per_sm};
-    v.emu = emu;
     return render_frame(F, prec, palette, static_cast<cudaStream_t>(stream), &v);
 }
 

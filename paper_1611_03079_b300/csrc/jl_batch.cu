@@ -200,10 +200,6 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 if (tt < 32 || tt > 256 || (tt & 31)) { rc = fail(JL_EINVAL, "threads option must be 32..256, multiple of 32"); break; }
                 v.threads = tt;
             }
-            if (g == 1 && o.fp64_emu) {
-                if (o.fp64_emu < 1 || o.fp64_emu > 8) { rc = fail(JL_EINVAL, "fp64_emu must be 1..8"); break; }
-                v.emu = o.fp64_emu;
-            }
             b->variant[g] = v;
             if (v.ppt == 0 && b->tiles[g] > 0x7fffffffll) { rc = fail(JL_EINVAL, "too many tiles for the static kernel"); break; }
             const size_t nb = host[g].size() * sizeof(Frame);
@@ -328,7 +324,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                     bool seen = false;
                     for (size_t cj = 0; cj < ci; ++cj)
                         seen = seen || (cand[cj].ppt == v.ppt && cand[cj].unroll == v.unroll &&
-                                        cand[cj].threads == v.threads && cand[cj].emu == v.emu);
+                                        cand[cj].threads == v.threads);
                     if (seen)
                         continue;
                     const EscapeArgs x = make_args(g, v);
@@ -410,8 +406,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
     return JL_OK;
 }
 
-int jl_batch_variant(const jl_batch *b, int32_t precision, int32_t *ppt, int32_t *unroll, int32_t *threads,
-                     int32_t *emu)
+int jl_batch_variant(const jl_batch *b, int32_t precision, int32_t *ppt, int32_t *unroll, int32_t *threads)
 {
     if (!b || (precision != JL_FP32 && precision != JL_FP64))
         return fail(JL_EINVAL, "invalid arguments");
@@ -422,8 +417,6 @@ int jl_batch_variant(const jl_batch *b, int32_t precision, int32_t *ppt, int32_t
         *unroll = v.unroll;
     if (threads)
         *threads = v.threads;
-    if (emu)
-        *emu = v.emu;
     return JL_OK;
 }
 

@@ -35,7 +35,6 @@
 #include <tuple>
 
 #include "jl_common.cuh"
-#include "jl_f64emu.cuh"
 #include "jl_internal.h"
 
 namespace jl {
@@ -118,30 +117,6 @@ __global__ void dbl2_kernel(const double *in, double *out, int n)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n)
         out[i] = dbl2(in[i]);
-}
-
-// Self-test of the integer-pipe binary64 arithmetic: op 0 = a*b, 1 = a*a, 2 = a+b.
-__global__ void f64emu_kernel(int op, const double *a, const double *b, double *out, int32_t *sp_out, int n)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
-        return;
-    bool sp = false;
-    double r;
-    if (op == 0)
-        r = f64e::mul(a[i], b[i], sp);
-    else if (op == 1)
-        r = f64e::sqr(a[i], sp);
-    else
-        r = f64e::add(a[i], b[i], sp);
-    out[i] = r;
-    sp_out[i] = sp ? 1 : 0;
-}
-
-cudaError_t launch_f64emu(int op, const double *a, const double *b, double *out, int32_t *sp, int n, cudaStream_t st)
-{
-    f64emu_kernel<<<(n + 255) / 256, 256, 0, st>>>(op, a, b, out, sp, n);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_dbl2(const double *in, double *out, int n, cudaStream_t st)
@@ -231,12 +206,6 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
     const int lane = threadIdx.x & 31;
     const unsigned lane_bit = 1u << lane;
     const unsigned lt_mask = lane_bit - 1u;
-    // binary64: warps of the CTA in groups of four (one per SM sub-partition);
-    // one group in every `emu_ratio` keeps the hardware binary64 pipe busy,
-    // the others run the integer-pipe arithmetic beside it.
-    // (the k-th CTA resident on an SM is blockIdx.x / num_sms for a persistent grid)
-    const int wgroup = (int)(blockIdx.x / (unsigned)max(a.num_sms, 1)) * (int)(blockDim.x >> 7) + (int)(threadIdx.x >> 7);
-    const bool emu_warp = sizeof(T) == 8 && a.emu_ratio > 1 && (wgroup % a.emu_ratio) != 0;
 
     // Frame f of the launch: the table in global memory for batches, the
     // launch parameters for single frames.
@@ -499,48 +468,20 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
                 sy[k] = (double)y[k];
                 cnt[k] = 0;
             }
-            if (emu_warp) {
-                // integer-pipe binary64 (bit-exact; any operand or result
-                // outside its range marks the block for the exact replay)
-                bool sp = false;
-                // not unrolled over steps: keeps this path's code small enough
-                // for the instruction caches (slots still give ILP)
-#pragma unroll 1
-                for (int u = 0; u < U; ++u) {
 #pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        const bool live_k = rem[k] >= 0;
-                        bool spk = false;
-                        double xx = (double)x[k], yy = (double)y[k];
-                        double x2 = f64e::sqr(xx, spk);
-                        double y2 = f64e::sqr(yy, spk);
-                        float r32 = __fadd_rn(hi_estimate(x2), hi_estimate(y2));
-                        cnt[k] += (r32 < 3.9999847412109375f) ? 1 : 0;
-                        amb |= live_k & (r32 >= 3.9999847412109375f) & (r32 <= 4.0000152587890625f);
-                        double t = f64e::mul(dbl2(xx), yy, spk);
-                        y[k] = (T)f64e::add(t, (double)ci[k], spk);
-                        const double u2 = f64e::add(x2, -y2, spk);
-                        x[k] = (T)f64e::add(u2, (double)cr[k], spk);
-                        sp |= live_k & spk;
-                    }
-                }
-                amb |= sp;
-            } else {
+            for (int u = 0; u < U; ++u) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-#pragma unroll
-                    for (int k = 0; k < PPT; ++k) {
-                        double xx = (double)x[k], yy = (double)y[k];
-                        double x2 = __dmul_rn(xx, xx);
-                        double y2 = __dmul_rn(yy, yy);
-                        float r32 = __fadd_rn(hi_estimate(x2), hi_estimate(y2));
-                        cnt[k] += (r32 < 3.9999847412109375f) ? 1 : 0;
-                        amb |= (rem[k] >= 0) & (r32 >= 3.9999847412109375f) & (r32 <= 4.0000152587890625f);
-                        double t = dbl2(xx);
-                        t = __dmul_rn(t, yy);
-                        y[k] = (T)__dadd_rn(t, (double)ci[k]);
-                        x[k] = (T)__dadd_rn(__dsub_rn(x2, y2), (double)cr[k]);
-                    }
+                for (int k = 0; k < PPT; ++k) {
+                    double xx = (double)x[k], yy = (double)y[k];
+                    double x2 = __dmul_rn(xx, xx);
+                    double y2 = __dmul_rn(yy, yy);
+                    float r32 = __fadd_rn(hi_estimate(x2), hi_estimate(y2));
+                    cnt[k] += (r32 < 3.9999847412109375f) ? 1 : 0;
+                    amb |= (rem[k] >= 0) & (r32 >= 3.9999847412109375f) & (r32 <= 4.0000152587890625f);
+                    double t = dbl2(xx);
+                    t = __dmul_rn(t, yy);
+                    y[k] = (T)__dadd_rn(t, (double)ci[k]);
+                    x[k] = (T)__dadd_rn(__dsub_rn(x2, y2), (double)cr[k]);
                 }
             }
             if (__any_sync(FULL, amb)) {
@@ -1484,8 +1425,6 @@ static cudaError_t launch_compact(const EscapeArgs &a, int T, cudaStream_t st)
 cudaError_t launch_escape(const EscapeArgs &a_in, int precision, const Variant &v, int num_sms, cudaStream_t st)
 {
     EscapeArgs a = a_in;
-    a.emu_ratio = (precision == JL_FP64 && v.emu > 1) ? v.emu : 1;
-    a.num_sms = num_sms;
     if (v.ppt == 0 && v.unroll > 0 && precision == JL_FP32)
         return launch_compact(a, v.unroll, st);
     if (v.ppt == 0)

@@ -51,8 +51,6 @@ struct EscapeArgs {
     int64_t total_tiles;               // static kernel: tiles in the launch
     int32_t n_frames;
     int32_t hist_smem;                 // 1: accumulate histogram bins in shared memory (one frame)
-    int32_t emu_ratio;                 // binary64: 1 in emu_ratio warp groups native, the rest emulated
-    int32_t num_sms;                   // SMs of the device (set by the launcher)
     int64_t total_chunks;
     unsigned long long *chunk_counter; // zeroed before the launch
     int32_t *status;                   // device status word (0 = ok), may be NULL
@@ -69,7 +67,6 @@ struct Variant {
     int unroll;   // steps per block between service points
     int threads;  // threads per CTA
     int ctas_per_sm;
-    int emu = 1;  // binary64 only: 1 = hardware pipe only; k > 1 = 1 of every k warp groups native
 };
 
 // Thread-local last error.
@@ -89,7 +86,6 @@ int variant_list(int precision, int32_t *pairs, int cap);
 int device_sm_count();
 cudaError_t occupancy_per_sm(const void *kern, int threads, size_t smem, int *out);
 cudaError_t launch_dbl2(const double *in, double *out, int n, cudaStream_t st);
-cudaError_t launch_f64emu(int op, const double *a, const double *b, double *out, int32_t *sp, int n, cudaStream_t st);
 
 // Validates a frame request and fills F (outputs and coordinate tables are
 // left NULL).  chunk_len: target pixels per work chunk (16 .. 1024).

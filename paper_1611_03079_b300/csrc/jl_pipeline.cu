@@ -60,6 +60,7 @@ struct jl_host_plan {
     std::vector<cudaEvent_t> rendered;        // per unit: its render is done
     std::vector<cudaEvent_t> copied;          // per slot: the last copy out of it
     cudaEvent_t fork = nullptr;
+    cudaEvent_t tables_ready = nullptr;       // the banded frame's coordinate tables are written
     void *slots = nullptr;
     size_t slot_bytes = 0;
     void *tables = nullptr;  // coordinate tables, a 256-byte control block per frame and per extra band
@@ -99,6 +100,8 @@ static void destroy_host_plan(jl_host_plan *p)
                 cudaEventDestroy(e);
     if (p->fork)
         cudaEventDestroy(p->fork);
+    if (p->tables_ready)
+        cudaEventDestroy(p->tables_ready);
     cudaFree(p->slots);
     cudaFree(p->tables);
     delete p;
@@ -215,21 +218,16 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(frame slots)"); break; }
         e = cudaMalloc(&p->tables, table_bytes);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(coordinate tables)"); break; }
-        // coordinate tables of every frame, once
-        for (int i = 0; i < n && rc == JL_OK; ++i) {
+        // where each frame's coordinate tables live (jl_host_plan_run fills them)
+        for (int i = 0; i < n; ++i) {
             Frame &F = p->F[(size_t)i];
             const size_t esz = p->prec[(size_t)i] == JL_FP64 ? 8 : 4;
             uint8_t *base = static_cast<uint8_t *>(p->tables) + table_off[(size_t)i];
             F.xs = base;
             F.ys = base + (size_t)F.W * esz;
-            e = launch_coords(nullptr, &F, 1, p->rs[0]);
-            if (e != cudaSuccess)
-                rc = cuda_fail(e, "coords kernel launch");
         }
-        if (rc != JL_OK)
-            break;
-        e = cudaStreamSynchronize(p->rs[0]);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "coordinate tables"); break; }
+        e = cudaEventCreateWithFlags(&p->tables_ready, cudaEventDisableTiming);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventCreate"); break; }
     } while (0);
     if (rc != JL_OK) {
         destroy_host_plan(p);
@@ -272,9 +270,24 @@ int jl_host_plan_run(jl_host_plan *p, void *stream)
         uint32_t *bins = p->hbytes[k] ? reinterpret_cast<uint32_t *>(b + pad256(p->cbytes[k]) + pad256(p->rbytes[k]))
                                       : nullptr;
         cudaStream_t c = p->cs[k % nc];
+        // step A1 of every run: the frame's coordinate tables from its
+        // descriptor (which reaches the device as the kernel's parameters),
+        // on the stream of its first unit; units on other streams (row bands)
+        // wait for them
+        e = launch_coords(nullptr, &F0, 1, p->rs[u0 % nr]);
+        if (e == cudaSuccess && u1 - u0 > 1)
+            e = cudaEventRecord(p->tables_ready, p->rs[u0 % nr]);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "coords kernel launch");
+            break;
+        }
         for (size_t u = u0; u < u1 && rc == JL_OK; ++u) {
             const Unit &U = p->units[u];
             cudaStream_t r = p->rs[u % nr];
+            if (u > u0 && (u % nr) != (u0 % nr) && (e = cudaStreamWaitEvent(r, p->tables_ready, 0)) != cudaSuccess) {
+                rc = cuda_fail(e, "cudaStreamWaitEvent(tables ready)");
+                break;
+            }
             // the slot's previous frame (k - depth) must be copied out first
             if (k >= (size_t)p->depth && (e = cudaStreamWaitEvent(r, p->copied[slot], 0)) != cudaSuccess) {
                 rc = cuda_fail(e, "cudaStreamWaitEvent(slot copied)");

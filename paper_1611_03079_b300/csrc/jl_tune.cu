@@ -59,7 +59,7 @@ using namespace jl;
 extern "C" int jl_render_variant(double cr, double ci, jl_rect rect, int32_t width, int32_t height, int32_t max_iter,
                                  int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
                                  const uint8_t *palette, float *hist, int32_t ppt, int32_t unroll, int32_t threads,
-                                 int32_t ctas_per_sm, int32_t emu, void *stream);
+                                 int32_t ctas_per_sm, void *stream);
 
 extern "C" {
 
@@ -131,11 +131,6 @@ int jl_autotune(int32_t precision, int32_t max_iter, const jl_frame *calib, int3
             if (v.ppt == 0 && ti == 1)
                 continue;  // the static kernel has one CTA shape
             cands.push_back(v);
-            if (precision == JL_FP64 && v.ppt > 0 && v.threads == 256)
-                for (int emu = 2; emu <= 4; ++emu) {
-                    v.emu = emu;
-                    cands.push_back(v);
-                }
         }
     }
     for (size_t ci = 0; ci < cands.size() && rc == JL_OK; ++ci) {
@@ -147,7 +142,7 @@ int jl_autotune(int32_t precision, int32_t max_iter, const jl_frame *calib, int3
                 for (const jl_frame &f : set) {
                     rc = jl_render_variant(f.cr, f.ci, f.rect, f.width, f.height, max_iter, precision, f.mode,
                                            JL_COUNT_NONE, nullptr, static_cast<uint8_t *>(buf), nullptr, nullptr,
-                                           v.ppt, v.unroll, v.threads, v.ctas_per_sm, v.emu, st);
+                                           v.ppt, v.unroll, v.threads, v.ctas_per_sm, st);
                     if (rc != JL_OK)
                         break;
                 }
@@ -188,7 +183,6 @@ int jl_autotune(int32_t precision, int32_t max_iter, const jl_frame *calib, int3
         out->unroll = best.v.unroll;
         out->threads = best.v.threads;
         out->ctas_per_sm = best.v.ctas_per_sm;
-        out->emu = best.v.emu;
         out->ms = best.ms;
         out->candidates = tried;
     }
@@ -213,7 +207,6 @@ int jl_tune_get(int32_t precision, int32_t max_iter, jl_tune_result *out)
     out->unroll = v.unroll;
     out->threads = v.threads;
     out->ctas_per_sm = v.ctas_per_sm;
-    out->emu = v.emu;
     out->ms = ms;
     out->candidates = tuned ? 1 : 0;
     return JL_OK;
@@ -229,7 +222,7 @@ int jl_tune_clear(void)
     return JL_OK;
 }
 
-// Text format, one line per entry:  device precision bucket ppt unroll threads ctas_per_sm emu ms
+// Text format, one line per entry:  device precision bucket ppt unroll threads ctas_per_sm ms
 int jl_tune_save(const char *path)
 {
     if (!path)
@@ -238,14 +231,14 @@ int jl_tune_save(const char *path)
     if (!fp)
         return fail(JL_EINVAL, std::string("cannot open ") + path);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    fprintf(fp, "# jl tuning table v2: device precision bucket ppt unroll threads ctas_per_sm emu ms\n");
+    fprintf(fp, "# jl tuning table v3: device precision bucket ppt unroll threads ctas_per_sm ms\n");
     for (int d = 0; d < kTuneDevices; ++d)
         for (int p = 0; p < 2; ++p)
             for (int b = 0; b < kBuckets; ++b) {
                 const TuneEntry &t = g_tune[d][p][b];
                 if (t.valid)
-                    fprintf(fp, "%d %d %d %d %d %d %d %d %.6f\n", d, p, b, t.v.ppt, t.v.unroll, t.v.threads,
-                            t.v.ctas_per_sm, t.v.emu, t.ms);
+                    fprintf(fp, "%d %d %d %d %d %d %d %.6f\n", d, p, b, t.v.ppt, t.v.unroll, t.v.threads,
+                            t.v.ctas_per_sm, t.ms);
             }
     fclose(fp);
     return JL_OK;
@@ -265,10 +258,9 @@ int jl_tune_load(const char *path)
     while (fgets(line, sizeof(line), fp)) {
         if (line[0] == '#' || line[0] == '\n')
             continue;
-        int d, p, b, ppt, un, th, cps, emu;
+        int d, p, b, ppt, un, th, cps;
         double ms;
-        if (sscanf(line, "%d %d %d %d %d %d %d %d %lf", &d, &p, &b, &ppt, &un, &th, &cps, &emu, &ms) != 9 ||
-            emu < 1 || emu > 8 || d < 0 ||
+        if (sscanf(line, "%d %d %d %d %d %d %d %lf", &d, &p, &b, &ppt, &un, &th, &cps, &ms) != 8 || d < 0 ||
             d >= kTuneDevices || p < 0 || p > 1 || b < 0 || b >= kBuckets || !variant_supported(p, ppt, un) ||
             th < 32 || th > 256 || (th & 31) || cps < 0 || cps > 32) {
             rc = fail(JL_EINVAL, std::string("malformed tuning line: ") + line);
@@ -277,7 +269,6 @@ int jl_tune_load(const char *path)
         TuneEntry t;
         t.valid = true;
         t.v = Variant{ppt, un, th, cps};
-        t.v.emu = emu;
         t.ms = ms;
         entries.push_back({(d * 2 + p) * kBuckets + b, t});
     }
