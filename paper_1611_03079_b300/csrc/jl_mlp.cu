@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "jl_internal.h"
@@ -61,7 +62,8 @@ struct GemmArgs {
     int ld_out32;
     float *colsum;           // [gridDim.x x 256] per-CTA column sums (EPI_MASK, EPI_SOFTMAX with target)
     // EPI_SOFTMAX
-    const float *target;     // [M x ldt] histogram targets or NULL
+    const float *target;     // [rows x ldt] histogram targets or NULL
+    const int32_t *trow;     // target row of batch row m (NULL: m)
     int ldt;
     float inv_m;             // 1 / batch rows for the gradient
     float *loss;             // [gridDim.x] per-CTA sums over rows of -sum_b t_b log p_b
@@ -74,6 +76,9 @@ struct GemmArgs {
     // (ld_out32 as given); a fixed-order reduction sums the splits.
     int ksplit, kc_per_split;
     long long split_stride;
+    // operands that the preceding kernel of the stream does not write: staged
+    // before waiting for it (programmatic dependent launch)
+    int pre_a, pre_b;
     // column split (not EPI_SOFTMAX, whose rows need every column): CTA
     // (x, y, z) computes columns [z * n_per_cta, (z + 1) * n_per_cta) of its
     // rows; 0 = all BN columns in one CTA.  A multiple of 64.
@@ -81,12 +86,14 @@ struct GemmArgs {
 };
 
 static constexpr int kBM = 128, kBK = 64;
+static constexpr int kTP = 65;  // epilogue tile pitch (words) for column blocks of <= 64
 static constexpr int kTileA = kBM * kBK * 2;   // 16 KB
 static constexpr int kTileB = 256 * kBK * 2;   // 32 KB
 static constexpr int kStage = kTileA + kTileB;
-static constexpr int kGemmSmem = 2 * kStage + 4 * 256 * 4 + 64;  // stages + column partials + barriers
+static constexpr int kStages = 4;  // K chunks in flight (K <= 256 is staged in one go)
+static constexpr int kGemmSmem = kStages * kStage + 4 * 256 * 4 + 128;  // stages + column partials + barriers
 static constexpr long long kWaitLimit = 2000000000ll;  // ~1 s at 2 GHz
-static constexpr int kSplitK = 16;  // K splits of the weight-gradient products (K = batch rows)
+static constexpr int kSplitK = 8;  // K splits of the weight-gradient products (K = batch rows)
 
 // Stage rows [row0, row0 + nrows) x k [k0, k0 + 64) of an operand into the
 // K-major core-matrix layout: piece (r, g) (8 consecutive k) at byte
@@ -151,6 +158,50 @@ __device__ __forceinline__ void stage_operand(uint8_t *dst, const __nv_bfloat16 
     }
 }
 
+// Asynchronous form of stage_operand for 16-byte aligned operands (ld a
+// multiple of 8 elements, 16-byte aligned base): every piece is one cp.async
+// of up to 16 bytes, zero-filled past rlim / klim.  trans = 0 (stored
+// rows x K): the K-major layout of stage_operand.  trans = 1 (stored K x rows,
+// A[k * ld + row]): MN-major core matrices instead -- core matrix (r / 8, k / 8)
+// at the same byte offset ((r / 8) * 8 + (k % 64) / 8) * 128, holding 8
+// K-rows of 16 bytes (8 consecutive rows of the operand) -- so the pieces are
+// contiguous in global memory and the MMA reads the operand as MN-major.
+__device__ __forceinline__ void stage_async(uint8_t *dst, const __nv_bfloat16 *src, int ld, int trans, int row0,
+                                            int nrows, int rlim, int k0, int klim)
+{
+    const int pieces = nrows * 8;
+    const int nmg = nrows >> 3;
+    for (int p = threadIdx.x; p < pieces; p += blockDim.x) {
+        int off;
+        uint32_t bytes;
+        const __nv_bfloat16 *sp = src;
+        if (!trans) {
+            // 8 consecutive threads fill one 128-byte core matrix
+            const int r = (p >> 6) * 8 + (p & 7);
+            const int g = (p >> 3) & 7;
+            off = ((r >> 3) * 8 + g) * 128 + (r & 7) * 16;
+            const int row = row0 + r, k = k0 + g * 8;
+            const int nk = klim - k;
+            bytes = (row < rlim && nk > 0) ? 2u * (uint32_t)min(nk, 8) : 0u;
+            if (bytes)
+                sp = src + (size_t)row * ld + k;
+        } else {
+            // 8 consecutive threads fill one core matrix (8 K-rows), and the
+            // next 8 the core matrix of the next 8 operand rows, so a warp
+            // reads 64 contiguous bytes from each of 8 K-rows
+            const int kr = ((p >> 3) / nmg) * 8 + (p & 7);
+            const int mg = (p >> 3) % nmg;
+            off = (mg * 8 + (kr >> 3)) * 128 + (kr & 7) * 16;
+            const int k = k0 + kr, m = row0 + mg * 8;
+            const int nm = rlim - m;
+            bytes = (k < klim && nm > 0) ? 2u * (uint32_t)min(nm, 8) : 0u;
+            if (bytes)
+                sp = src + (size_t)k * ld + m;
+        }
+        tc::cp_async16(dst + off, sp, bytes);
+    }
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -159,14 +210,26 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// 2^x with the hardware approximation (relative error about 2^-22).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+static constexpr int kGemmThreads = 512;  // 16 warps: 4 per scheduler in the epilogue
+
 template <int EPI>
-__global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ GemmArgs g)
+__global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __grid_constant__ GemmArgs g)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *stage0 = sm;
-    float *part = reinterpret_cast<float *>(sm + 2 * kStage);           // [4][256] column partials
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * kStage + 4 * 256 * 4);  // 3 mbarriers
-    uint32_t *holder = reinterpret_cast<uint32_t *>(bars + 3);
+    float *part = reinterpret_cast<float *>(sm + kStages * kStage);     // [256] column partials + [768] exchange
+    float *xch = part + 256;                                            // [4][128] per-quarter row values
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kStages * kStage + 4 * 256 * 4);  // kStages + 1 mbarriers
+    uint32_t *holder = reinterpret_cast<uint32_t *>(bars + kStages + 1);
+    __shared__ float lw[kGemmThreads / 32];
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -175,12 +238,11 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
     if (warp == 0)
         tc::tmem_alloc(holder, 256);
     if (threadIdx.x == 0) {
-        tc::mbar_init(&bars[0], 1);
-        tc::mbar_init(&bars[1], 1);
-        tc::mbar_init(&bars[2], 1);
+        for (int b = 0; b <= kStages; ++b)
+            tc::mbar_init(&bars[b], 1);
         tc::fence_mbar_init();
     }
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x)
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
         part[i] = 0.f;
     tc::tc_fence_before();
     __syncthreads();
@@ -191,30 +253,86 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
     const int npc = (EPI != EPI_SOFTMAX && g.n_per_cta > 0) ? g.n_per_cta : g.BN;
     const int n0 = (int)blockIdx.z * npc;
     const int nbn = min(npc, g.BN - n0);
-    const uint32_t idesc = tc::idesc_bf16(kBM, (uint32_t)nbn);
     int kc_begin = 0, kc_end = (g.K + kBK - 1) / kBK;
     if (EPI == EPI_F32 && g.ksplit > 1) {
         kc_begin = blockIdx.y * g.kc_per_split;
         kc_end = min(kc_end, kc_begin + g.kc_per_split);
     }
-    bool ok = true;
-    for (int kc = kc_begin; kc < kc_end; ++kc) {
-        const int lk = kc - kc_begin;  // chunk index within this CTA's range
-        const int s = lk & 1;
-        uint8_t *sA = stage0 + s * kStage;
-        uint8_t *sB = sA + kTileA;
-        if (lk >= 2) {
-            // buffer s was last read by the MMAs of chunk lk - 2
-            if (!tc::mbar_wait(&bars[s], ((lk - 2) >> 1) & 1, kWaitLimit))
-                ok = false;
+    // Operands whose 16-byte pieces are aligned are staged with cp.async
+    // (transposed ones MN-major, read as such by the MMA); others through
+    // registers, K-major (transposed ones gathered element by element).
+    const bool a_async = (g.lda & 7) == 0 && (reinterpret_cast<uintptr_t>(g.A) & 15) == 0;
+    const bool b_async = (g.ldb & 7) == 0 && (reinterpret_cast<uintptr_t>(g.B) & 15) == 0;
+    const uint32_t idesc = tc::idesc_bf16_t(kBM, (uint32_t)nbn, a_async && g.a_trans, b_async && g.b_trans);
+    const int nchunks = kc_end - kc_begin;
+    const int nst = min(nchunks, kStages);
+    // stage = A tile (128 x 64) + this CTA's B tile (nbn x 64)
+    const int stage_bytes = kTileA + nbn * kBK * 2;
+    // EPI_SOFTMAX with targets: the tile rows' targets are copied to a tile
+    // after the stages while the products run (the oldest copy group)
+    constexpr int kTPs = 129;  // target / gradient tile pitch (odd)
+    float *Tt = reinterpret_cast<float *>(stage0 + kStages * stage_bytes);
+    // targets are inputs of the call: copied before waiting for the preceding kernel
+    if (EPI == EPI_SOFTMAX && g.target) {
+        constexpr int kRowsPerWarp = kBM / (kGemmThreads / 32);
+        for (int rr = warp * kRowsPerWarp; rr < (warp + 1) * kRowsPerWarp; ++rr) {
+            const int grow = m0 + rr;
+            if (grow >= g.M)
+                break;
+            const int64_t trw = g.trow ? (int64_t)g.trow[grow] : (int64_t)grow;
+            const float *src = g.target + trw * g.ldt;
+            for (int cc = lane; cc < g.N; cc += 32)
+                tc::cp_async4(Tt + rr * kTPs + cc, src + cc);
         }
-        stage_operand(sA, g.A, g.lda, g.a_trans, m0, kBM, g.M, kc * kBK, g.K);
-        stage_operand(sB, g.B, g.ldb, g.b_trans, n0, nbn, g.N, kc * kBK, g.K);
+        tc::cp_async_commit();
+    }
+    auto stage = [&](int lk, bool do_a, bool do_b) {
+        uint8_t *sA = stage0 + (lk % kStages) * stage_bytes;
+        uint8_t *sB = sA + kTileA;
+        const int kc = kc_begin + lk;
+        if (do_a) {
+            if (a_async)
+                stage_async(sA, g.A, g.lda, g.a_trans, m0, kBM, g.M, kc * kBK, g.K);
+            else
+                stage_operand(sA, g.A, g.lda, g.a_trans, m0, kBM, g.M, kc * kBK, g.K);
+        }
+        if (do_b) {
+            if (b_async)
+                stage_async(sB, g.B, g.ldb, g.b_trans, n0, nbn, g.N, kc * kBK, g.K);
+            else
+                stage_operand(sB, g.B, g.ldb, g.b_trans, n0, nbn, g.N, kc * kBK, g.K);
+        }
+    };
+    auto issue = [&](int lk) {
+        stage(lk, true, true);
+        tc::cp_async_commit();
+    };
+    // the first chunks of the operands the preceding kernel does not write,
+    // then (once it has completed) the rest; the copy groups are committed
+    // oldest first, so waiting for chunk lk's second group covers its first
+    const bool pa = g.pre_a != 0, pb = g.pre_b != 0;
+    if (pa || pb) {
+        for (int lk = 0; lk < nst; ++lk)
+            stage(lk, pa, pb);
+        tc::cp_async_commit();
+    }
+    tc::griddep_wait();
+    tc::griddep_launch_dependents();
+    for (int lk = 0; lk < nst; ++lk) {
+        stage(lk, !pa, !pb);
+        tc::cp_async_commit();
+    }
+    int committed = nst;
+    bool ok = true;
+    for (int lk = 0; lk < nchunks; ++lk) {
+        const int s = lk % kStages;
+        // this thread's copies of chunk lk have landed (later chunks may still fly)
+        tc::cp_async_wait(min(committed - lk - 1, kStages - 1));
         tc::fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
             tc::tc_fence_after();
-            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+            const uint32_t a0 = tc::smem_u32(stage0 + s * stage_bytes), b0 = a0 + kTileA;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk) {
                 const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, 1024);
@@ -223,188 +341,273 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
             }
             tc::mma_commit(&bars[s]);
         }
+        if (lk + nst < nchunks) {
+            // stage s is refilled with chunk lk + nst once chunk lk's MMAs are done
+            if (!tc::mbar_wait(&bars[s], (lk / kStages) & 1, kWaitLimit))
+                ok = false;
+            issue(lk + nst);
+            ++committed;
+        }
     }
     if (threadIdx.x == 0)
-        tc::mma_commit(&bars[2]);
-    if (!tc::mbar_wait(&bars[2], 0, kWaitLimit))
+        tc::mma_commit(&bars[kStages]);
+    if (!tc::mbar_wait(&bars[kStages], 0, kWaitLimit))
         ok = false;
     if (!ok && g.status)
         atomicExch(g.status, (int32_t)JL_ETIMEOUT);
     tc::tc_fence_after();
 
-    // ---------------- epilogue: this thread owns tile row `r` ----------------
-    // Results pass through an fp32 tile in the (now idle) staging buffers,
-    // 65 words per row (odd, so one-row-per-thread accesses are free of bank
-    // conflicts); the tile is then written out a row at a time by whole
-    // warps (coalesced), and column sums are read down its columns.
-    const int r = warp * 32 + lane;
+    // ---------------- epilogue: thread (row r, column quarter q) ----------------
+    // Warp w reads tensor-memory lanes 32 (w % 4) .. +31 (rows) and takes the
+    // column quarter q = w / 4 of them, so four threads share a row and four
+    // warps share each scheduler.  Rows are written in whole 16-byte pieces
+    // (16-byte aligned rows; other layouts fall back to element stores).
+    // Column sums for the bias gradients go through an fp32 tile in the (now
+    // idle) staging buffers, summed down the columns in a fixed order.
+    const int r = (warp & 3) * 32 + lane;
+    const int q = warp >> 2;
     const int row = m0 + r;
     const bool in = row < g.M;
-    const uint32_t tw = taddr + ((uint32_t)(warp * 32) << 16);
-    constexpr int kTP = 65;                               // tile pitch (words)
+    const uint32_t tw = taddr + ((uint32_t)((warp & 3) * 32) << 16);
     float *T = reinterpret_cast<float *>(stage0);         // [128][kTP]
-    uint16_t *Mk = reinterpret_cast<uint16_t *>(stage0 + kBM * kTP * 4);  // [128][130] bf16 mask tile
+    float *psum = T + kBM * 129;                          // [<= 512] partial column sums
+
+    // sum over the 128 rows of columns [0, ncols) of `tile` (pitch tp) into
+    // out[c]: G row groups per column (G * ncols <= threads), each summed with
+    // four interleaved accumulators, then the groups in order
+    auto column_sums = [&](const float *tile, int ncols, int tp, float *out) {
+        const int G = 2 * ncols <= kGemmThreads / 4 ? 8 : (ncols <= kGemmThreads / 4 ? 4 : 2);
+        const int rows_g = kBM / G;
+        __syncthreads();
+        for (int t = threadIdx.x; t < G * ncols; t += blockDim.x) {
+            const int c = t % ncols, h = t / ncols;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            const float *col = tile + (h * rows_g) * tp + c;
+            for (int rr = 0; rr < rows_g; rr += 4) {
+                s0 += col[(rr + 0) * tp];
+                s1 += col[(rr + 1) * tp];
+                s2 += col[(rr + 2) * tp];
+                s3 += col[(rr + 3) * tp];
+            }
+            psum[h * ncols + c] = (s0 + s1) + (s2 + s3);
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+            float acc = 0.f;
+            for (int h = 0; h < G; ++h)
+                acc += psum[h * ncols + c];
+            out[c] = acc;
+        }
+    };
+    // the four quarters' values of each row, combined in quarter order
+    auto row_combine = [&](float v, bool is_max) -> float {
+        __syncthreads();
+        xch[q * kBM + r] = v;
+        __syncthreads();
+        const float a = xch[r], b = xch[kBM + r], c = xch[2 * kBM + r], d = xch[3 * kBM + r];
+        return is_max ? fmaxf(fmaxf(a, b), fmaxf(c, d)) : (a + b) + (c + d);
+    };
 
     if constexpr (EPI == EPI_SOFTMAX) {
-        float mx = -INFINITY;
-        for (int c0 = 0; c0 < g.BN; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tw + c0, v);
+        // quarter q holds logits q*32 .. q*32+31 of its row (BN <= 128)
+        constexpr float kLog2e = 1.4426950408889634f;
+        float z[32];
+        float mq = -INFINITY;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = c0 + j;
-                if (col < g.N)
-                    mx = fmaxf(mx, v[j] + g.bias[col]);
-            }
-        }
-        float sum = 0.f;
-        for (int c0 = 0; c0 < g.BN; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tw + c0, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = c0 + j;
-                if (col < g.N)
-                    sum += expf(v[j] + g.bias[col] - mx);
-            }
-        }
-        const float inv = 1.f / sum;
-        const float lse = mx + logf(sum);
-        float ce = 0.f, ent = 0.f;
-        // column blocks of 64: targets in, probabilities or gradients out, via the tile
-        for (int cb0 = 0; cb0 < g.BN; cb0 += 64) {
-            const int ncol = min(64, g.N - cb0);
-            __syncthreads();  // the previous block's readers of the tile are done
-            if (g.target) {
-                for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
-                    const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
-                    T[rr * kTP + cc] = (grow < g.M && cc < ncol) ? g.target[(size_t)grow * g.ldt + cb0 + cc] : 0.f;
-                }
-                __syncthreads();
-            }
-            for (int c0 = cb0; c0 < cb0 + 64 && c0 < g.BN; c0 += 16) {
+        for (int h = 0; h < 2; ++h) {
+            const int c0 = q * 32 + h * 16;
+            if (c0 < g.BN) {
                 float v[16];
                 tc::tmem_ld16(tw + c0, v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int col = c0 + j, tc_ = col - cb0;
-                    float out = 0.f;
+                    const int col = c0 + j;
+                    const float zz = col < g.N ? v[j] + g.bias[col] : -INFINITY;
+                    z[h * 16 + j] = zz;
+                    mq = fmaxf(mq, zz);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    z[h * 16 + j] = -INFINITY;
+            }
+        }
+        const float mx = row_combine(mq, true);
+        float sq = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (q * 32 + j < g.N)
+                sq += ex2_approx((z[j] - mx) * kLog2e);
+        const float sum = row_combine(sq, false);
+        const float inv = 1.f / sum;
+        const float lse = mx + logf(sum);
+        float ce = 0.f, ent = 0.f;
+        const bool vec_dz = g.target && g.out_bf16 && (g.ld_out & 7) == 0 &&
+                            (reinterpret_cast<uintptr_t>(g.out_bf16) & 15) == 0;
+#pragma unroll
+        for (int c8 = 0; c8 < 32; c8 += 8) {
+            const int c0 = q * 32 + c8;
+            if (c0 < g.BN) {
+                float out[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int col = c0 + j;
+                    out[j] = 0.f;
                     if (col < g.N) {
-                        const float z = v[j] + g.bias[col];
-                        const float p = expf(z - mx) * inv;
-                        const float lp = z - lse;
+                        const float zz = z[c8 + j];
+                        const float p = ex2_approx((zz - mx) * kLog2e) * inv;
+                        const float lp = zz - lse;
                         if (p > 0.f)
                             ent -= p * lp;
-                        out = p;
-                        if (g.target && g.probs && in)
+                        out[j] = p;
+                        if (g.probs && in)
                             g.probs[(size_t)row * g.ldp + col] = p;
                         if (g.target) {
-                            const float t = T[r * kTP + tc_];
-                            out = 0.f;
+                            const float t = Tt[r * kTPs + col];
+                            out[j] = 0.f;
                             if (in) {
                                 ce -= t * lp;
-                                out = (p - t) * g.inv_m;
+                                out[j] = (p - t) * g.inv_m;
                             }
+                            Tt[r * kTPs + col] = out[j];
                         }
+                    } else if (g.target) {
+                        Tt[r * kTPs + col] = 0.f;
                     }
-                    T[r * kTP + tc_] = in ? out : 0.f;
                 }
-            }
-            __syncthreads();
-            if (g.target) {
-                // column sums of the gradient (bias gradient partials)
-                for (int c = threadIdx.x; c < 64; c += blockDim.x) {
-                    float s2 = 0.f;
-                    for (int rr = 0; rr < kBM; ++rr)
-                        s2 += T[rr * kTP + c];
-                    if (cb0 + c < 256)
-                        part[cb0 + c] = s2;
-                }
-                if (g.out_bf16)
-                    for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
-                        const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
-                        if (grow < g.M && cb0 + cc < g.BN)
-                            g.out_bf16[(size_t)grow * g.ld_out + cb0 + cc] = __float2bfloat16_rn(T[rr * kTP + cc]);
+                if (g.target && g.out_bf16 && in) {
+                    if (vec_dz) {
+                        uint4 u;
+                        u.x = tc::pack_bf16x2(out[0], out[1]);
+                        u.y = tc::pack_bf16x2(out[2], out[3]);
+                        u.z = tc::pack_bf16x2(out[4], out[5]);
+                        u.w = tc::pack_bf16x2(out[6], out[7]);
+                        *reinterpret_cast<uint4 *>(g.out_bf16 + (size_t)row * g.ld_out + c0) = u;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            g.out_bf16[(size_t)row * g.ld_out + c0 + j] = __float2bfloat16_rn(out[j]);
                     }
-            } else if (g.probs) {
-                for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
-                    const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
-                    if (grow < g.M && cc < ncol)
-                        g.probs[(size_t)grow * g.ldp + cb0 + cc] = T[rr * kTP + cc];
                 }
             }
         }
-        if (in && g.score)
-            g.score[row] = ent;
-        if (g.target && g.loss) {
-            const float s2 = warp_sum(in ? ce : 0.f);
-            __shared__ float lw[4];
-            if (lane == 0)
-                lw[warp] = s2;
-            __syncthreads();
-            if (threadIdx.x == 0)
-                g.loss[blockIdx.x] = (lw[0] + lw[1]) + (lw[2] + lw[3]);
+        const float ent_row = row_combine(ent, false);
+        if (in && g.score && q == 0)
+            g.score[row] = ent_row;
+        if (g.target) {
+            // bias gradient partials: column sums of the (unrounded) gradient
+            if (!in)
+                for (int c = q * 32; c < q * 32 + 32 && c < g.BN; ++c)
+                    Tt[r * kTPs + c] = 0.f;
+            column_sums(Tt, g.N, kTPs, part);
+            if (g.loss) {
+                const float s2 = warp_sum(in ? ce : 0.f);
+                if (lane == 0)
+                    lw[warp] = s2;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    float acc = 0.f;
+                    for (int w = 0; w < kGemmThreads / 32; ++w)
+                        acc += lw[w];
+                    g.loss[blockIdx.x] = acc;
+                }
+            }
         }
     } else {
         float *o32 = nullptr;
         if constexpr (EPI == EPI_F32)
             o32 = g.out_f32 + (g.ksplit > 1 ? (size_t)blockIdx.y * (size_t)g.split_stride : 0);
-        for (int cb0 = n0; cb0 < n0 + nbn; cb0 += 64) {
-            const int ncol = min(64, g.N - cb0);
-            __syncthreads();  // the previous block's readers of the tile are done
+        bool vec_out;
+        if constexpr (EPI == EPI_F32)
+            vec_out = (g.ld_out32 & 3) == 0 && (reinterpret_cast<uintptr_t>(o32) & 15) == 0;
+        else
+            vec_out = (g.ld_out & 7) == 0 && (reinterpret_cast<uintptr_t>(g.out_bf16) & 15) == 0;
+        const bool vec_mask = EPI == EPI_MASK && (g.ldm & 7) == 0 &&
+                              (reinterpret_cast<uintptr_t>(g.mask) & 15) == 0;
+        const bool sums = EPI == EPI_MASK && g.colsum;
+        // quarter q takes columns n0 + 16 q (+ 64 k) of the CTA's nbn (<= 64 in every launch here)
+        for (int c0 = n0 + 16 * q; c0 < n0 + nbn; c0 += 64) {
+            float v[16];
+            tc::tmem_ld16(tw + (uint32_t)(c0 - n0), v);
+            uint32_t mk[8];
             if constexpr (EPI == EPI_MASK) {
-                for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
-                    const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
-                    Mk[rr * 130 + cc] = (grow < g.M && cc < ncol)
-                                            ? __bfloat16_as_ushort(g.mask[(size_t)grow * g.ldm + cb0 + cc])
-                                            : (uint16_t)0;
-                }
-                __syncthreads();
-            }
-            for (int c0 = cb0; c0 < cb0 + 64 && c0 < n0 + nbn; c0 += 16) {
-                float v[16];
-                tc::tmem_ld16(tw + (uint32_t)(c0 - n0), v);
+                if (in && vec_mask && c0 + 16 <= g.N) {
+                    const uint4 *mp = reinterpret_cast<const uint4 *>(g.mask + (size_t)row * g.ldm + c0);
+                    const uint4 a0 = mp[0], a1 = mp[1];
+                    mk[0] = a0.x; mk[1] = a0.y; mk[2] = a0.z; mk[3] = a0.w;
+                    mk[4] = a1.x; mk[5] = a1.y; mk[6] = a1.z; mk[7] = a1.w;
+                } else {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = c0 + j;
-                    float x = v[j];
-                    if (col >= g.N || !in) {
-                        x = 0.f;
-                    } else {
-                        if (g.bias)
-                            x += g.bias[col];
-                        if constexpr (EPI == EPI_BIAS_ACT) {
-                            if (g.relu)
-                                x = fmaxf(x, 0.f);
-                        }
-                        if constexpr (EPI == EPI_MASK) {
-                            const float mk = __bfloat162float(__ushort_as_bfloat16(Mk[r * 130 + (col - cb0)]));
-                            x = (mk > 0.f) ? x : 0.f;
-                        }
+                    for (int j = 0; j < 8; ++j) {
+                        const int col = c0 + 2 * j;
+                        const uint32_t lo = (in && col < g.N) ? __bfloat16_as_ushort(g.mask[(size_t)row * g.ldm + col]) : 0u;
+                        const uint32_t hi = (in && col + 1 < g.N)
+                                                ? __bfloat16_as_ushort(g.mask[(size_t)row * g.ldm + col + 1]) : 0u;
+                        mk[j] = lo | (hi << 16);
                     }
-                    T[r * kTP + (col - cb0)] = x;
                 }
             }
-            __syncthreads();
-            if constexpr (EPI == EPI_MASK) {
-                if (g.colsum)
-                    for (int c = threadIdx.x; c < 64; c += blockDim.x) {
-                        float s2 = 0.f;
-                        for (int rr = 0; rr < kBM; ++rr)
-                            s2 += T[rr * kTP + c];
-                        part[cb0 + c] = s2;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = c0 + j;
+                float x = v[j];
+                if (col >= g.N || !in) {
+                    x = 0.f;
+                } else {
+                    if (g.bias)
+                        x += g.bias[col];
+                    if constexpr (EPI == EPI_BIAS_ACT) {
+                        if (g.relu)
+                            x = fmaxf(x, 0.f);
                     }
+                    if constexpr (EPI == EPI_MASK) {
+                        // keep where the bf16 mask value is > 0 (sign bit clear, not +0)
+                        const uint32_t mb = (mk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                        x = (mb != 0u && mb < 0x8000u) ? x : 0.f;
+                    }
+                }
+                v[j] = x;
+                if (sums)
+                    T[r * kTP + (col - n0)] = x;
             }
-            for (int i = threadIdx.x; i < kBM * 64; i += blockDim.x) {
-                const int rr = i >> 6, cc = i & 63, grow = m0 + rr;
-                if (grow < g.M && cc < ncol) {
-                    if constexpr (EPI == EPI_F32)
-                        o32[(size_t)grow * g.ld_out32 + cb0 + cc] = T[rr * kTP + cc];
-                    else
-                        g.out_bf16[(size_t)grow * g.ld_out + cb0 + cc] = __float2bfloat16_rn(T[rr * kTP + cc]);
+            if (in) {
+                if constexpr (EPI == EPI_F32) {
+                    if (vec_out && c0 + 16 <= g.N) {
+                        float4 *op = reinterpret_cast<float4 *>(o32 + (size_t)row * g.ld_out32 + c0);
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4)
+                            op[k4] = make_float4(v[4 * k4], v[4 * k4 + 1], v[4 * k4 + 2], v[4 * k4 + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < g.N)
+                                o32[(size_t)row * g.ld_out32 + c0 + j] = v[j];
+                    }
+                } else {
+                    if (vec_out && c0 + 16 <= g.N) {
+                        uint4 q0, q1;
+                        q0.x = tc::pack_bf16x2(v[0], v[1]);
+                        q0.y = tc::pack_bf16x2(v[2], v[3]);
+                        q0.z = tc::pack_bf16x2(v[4], v[5]);
+                        q0.w = tc::pack_bf16x2(v[6], v[7]);
+                        q1.x = tc::pack_bf16x2(v[8], v[9]);
+                        q1.y = tc::pack_bf16x2(v[10], v[11]);
+                        q1.z = tc::pack_bf16x2(v[12], v[13]);
+                        q1.w = tc::pack_bf16x2(v[14], v[15]);
+                        uint4 *op = reinterpret_cast<uint4 *>(g.out_bf16 + (size_t)row * g.ld_out + c0);
+                        op[0] = q0;
+                        op[1] = q1;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < g.N)
+                                g.out_bf16[(size_t)row * g.ld_out + c0 + j] = __float2bfloat16_rn(v[j]);
+                    }
                 }
             }
         }
+        if (sums)
+            column_sums(T, nbn, kTP, part + n0);
     }
 
     if ((EPI == EPI_MASK || EPI == EPI_SOFTMAX) && g.colsum) {
@@ -418,14 +621,6 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
     __syncthreads();
     if (warp == 0)
         tc::tmem_dealloc(taddr, 256);
-}
-
-// 2^x with the hardware approximation (relative error about 2^-22).
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
 }
 
 // Fourier feature of frequency row (b0, b1): t = b0*cr + b1*ci turns,
@@ -878,13 +1073,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
 }
 
 // ---------------------------------------------------------------------------
-// Small kernels: features, Adam, weight casts, gathers, histogram L1.
+// Small kernels: features, Adam, weight casts, histogram L1.
 // ---------------------------------------------------------------------------
 // phi[i] = [sin(2 pi t_j), cos(2 pi t_j)], t_j = B_j . C_i, j < 32 (bf16 out).
 // Optional gather: row i takes C[idx[i]].
 __global__ void features_kernel(const float *__restrict__ c, const int32_t *__restrict__ idx, int64_t n,
                                 const float *__restrict__ Bm, __nv_bfloat16 *__restrict__ phi)
 {
+    tc::griddep_wait();
+    tc::griddep_launch_dependents();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = t >> 5;
     const int j = (int)(t & 31);
@@ -896,16 +1093,6 @@ __global__ void features_kernel(const float *__restrict__ c, const int32_t *__re
     fourier_pair(Bm[2 * j], Bm[2 * j + 1], cr, ci, s, co);
     phi[i * kIn + j] = __float2bfloat16_rn(s);
     phi[i * kIn + kFreq + j] = __float2bfloat16_rn(co);
-}
-
-__global__ void gather_rows_kernel(const float *__restrict__ src, const int32_t *__restrict__ idx, int n, int cols,
-                                   float *__restrict__ dst)
-{
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n * cols)
-        return;
-    const int i = (int)(t / cols), j = (int)(t % cols);
-    dst[t] = src[(size_t)idx[i] * cols + j];
 }
 
 // bf16 weight copies, contiguous: W1, W2, W3 as stored ([out][in]), then the
@@ -935,16 +1122,75 @@ __global__ void cast_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *
     }
 }
 
-// Adam on the whole parameter block; the step counter lives in device memory
-// so a captured graph can replay steps.  Also refreshes the bf16 copies.
-__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ grad, float *__restrict__ m,
-                            float *__restrict__ v, __nv_bfloat16 *__restrict__ wb, int32_t *__restrict__ step,
-                            float lr, float beta1, float beta2, float eps)
+// Where one batch's gradient partials live: the split-K partials of the
+// three weight-gradient products and the per-CTA column sums of the bias
+// gradients and of the losses.  They are summed in a fixed order wherever a
+// gradient is needed (deterministic, so a resumed run continues bit for bit).
+struct GradParts {
+    const float *ws1, *ws2, *ws3;  // [S][256 x 64], [S][256 x 256], [S][101 x 256]
+    const float *pb1, *pb2, *pb3;  // [ctas][256]
+    const float *loss_part;        // [ctas]
+    int S, ctas;
+};
+
+__device__ __forceinline__ float grad_of(const GradParts &q, int i)
 {
+    const float *src;
+    int stride, nterm;
+    if (i < kOffB1) {
+        src = q.ws1 + (i - kOffW1), stride = kHid * kIn, nterm = q.S;
+    } else if (i < kOffW2) {
+        src = q.pb1 + (i - kOffB1), stride = 256, nterm = q.ctas;
+    } else if (i < kOffB2) {
+        src = q.ws2 + (i - kOffW2), stride = kHid * kHid, nterm = q.S;
+    } else if (i < kOffW3) {
+        src = q.pb2 + (i - kOffB2), stride = 256, nterm = q.ctas;
+    } else if (i < kOffB3) {
+        src = q.ws3 + (i - kOffW3), stride = kBins * kHid, nterm = q.S;
+    } else {
+        src = q.pb3 + (i - kOffB3), stride = 256, nterm = q.ctas;
+    }
+    float acc = 0.f;
+    for (int r = 0; r < nterm; ++r)
+        acc += src[(size_t)r * stride];
+    return acc;
+}
+
+__device__ __forceinline__ float loss_of(const GradParts &q)
+{
+    float acc = 0.f;
+    for (int r = 0; r < q.ctas; ++r)
+        acc += q.loss_part[r];
+    return acc;
+}
+
+// The gradient of every parameter and the batch's loss sum, from the partials.
+__global__ void grad_reduce_kernel(const __grid_constant__ GradParts q, float *__restrict__ grad, float *loss)
+{
+    tc::griddep_wait();
+    tc::griddep_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = *step + 1;
+    if (i < kNumParams)
+        grad[i] = grad_of(q, i);
+    if (i == 0 && loss)
+        *loss = loss_of(q);
+}
+
+// Adam on the whole parameter block (step t, 1 for the first) with each
+// gradient summed from the batch's partials; also refreshes the bf16 copies
+// (W1 | W2 | W3 and the transposes W2^T, W3^T) and writes the batch's loss
+// sum to *loss.
+__global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restrict__ p, float *__restrict__ m,
+                            float *__restrict__ v, __nv_bfloat16 *__restrict__ wb, int t, float lr, float beta1,
+                            float beta2, float eps, float *loss)
+{
+    tc::griddep_wait();
+    tc::griddep_launch_dependents();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && loss)
+        *loss = loss_of(q);
     if (i < kNumParams) {
-        const float g = grad[i];
+        const float g = grad_of(q, i);
         const float mi = beta1 * m[i] + (1.f - beta1) * g;
         const float vi = beta2 * v[i] + (1.f - beta2) * g * g;
         m[i] = mi;
@@ -958,12 +1204,12 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ gra
         if (i < kOffB1) {
             wi = i - kOffW1;
         } else if (i >= kOffW2 && i < kOffB2) {
-            const int t = i - kOffW2, r = t / kHid, c = t - r * kHid;
-            wi = kHid * kIn + t;
+            const int o = i - kOffW2, r = o / kHid, c = o - r * kHid;
+            wi = kHid * kIn + o;
             wt = kWbT2 + c * kHid + r;
         } else if (i >= kOffW3 && i < kOffB3) {
-            const int t = i - kOffW3, r = t / kHid, c = t - r * kHid;
-            wi = kHid * kIn + kHid * kHid + t;
+            const int o = i - kOffW3, r = o / kHid, c = o - r * kHid;
+            wi = kHid * kIn + kHid * kHid + o;
             wt = kWbT3 + c * kBinsPad + r;
         }
         if (wi >= 0)
@@ -971,25 +1217,6 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ gra
         if (wt >= 0)
             wb[wt] = __float2bfloat16_rn(w);
     }
-}
-
-// out[c] = sum over r < rows of part[r * stride + c], in row order (deterministic).
-__global__ void partial_reduce_kernel(const float *__restrict__ part, int rows, int cols, int stride,
-                                      float *__restrict__ out)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols)
-        return;
-    float s = 0.f;
-    for (int r = 0; r < rows; ++r)
-        s += part[(size_t)r * stride + c];
-    out[c] = s;
-}
-
-__global__ void step_increment_kernel(int32_t *step)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0)
-        *step += 1;
 }
 
 // L1[i] = sum_b |p[i][b] - q[i][b]| over `bins` columns.
@@ -1303,11 +1530,10 @@ struct jl_model {
     // work buffers for a batch of up to `cap` rows
     int cap = 0;
     __nv_bfloat16 *phi = nullptr, *h1 = nullptr, *h2 = nullptr, *dz = nullptr, *dz2 = nullptr, *dz1 = nullptr;
-    float *tgt = nullptr;
-    float *loss_out = nullptr;  // where the next forward writes its loss sum (NULL: `loss`)
-    float *part = nullptr;      // per-CTA column sums [ctas x 256]
+    float *pb = nullptr;        // per-CTA column sums of the three bias gradients [3][ctas x 256]
     float *loss_part = nullptr; // per-CTA loss sums [ctas]
-    float *ws = nullptr;        // split-K partials of the weight gradients [kSplitK x 256 x 256]
+    float *ws = nullptr;        // split-K partials of dW1 | dW2 | dW3 [kSplitK blocks each]
+    int ksplit = 0, ctas = 0;   // partial blocks of the last backward pass
     // screening as one CUDA graph (forward + top-k), captured on an internal
     // stream for the last (c, n, k, outputs) seen and replayed on the caller's
     cudaStream_t cap_stream = nullptr;
@@ -1320,6 +1546,25 @@ struct jl_model {
 namespace jl {
 
 static bool g_gemm_attr_set[4] = {false, false, false, false};
+
+// Launch with programmatic stream serialization: the kernel may start while
+// the preceding kernel of the stream finishes (each kernel waits for it with
+// griddep_wait before using its results or writing anything).
+template <typename... P, typename... A>
+static cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
 
 template <int EPI>
 static cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t st)
@@ -1338,50 +1583,27 @@ static cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t st)
     GemmArgs b = a;
     b.n_per_cta = EPI == EPI_SOFTMAX ? 0 : 64;
     const int nz = b.n_per_cta ? (a.BN + b.n_per_cta - 1) / b.n_per_cta : 1;
-    kern<<<dim3(grid, splits, nz), 128, kGemmSmem, st>>>(b);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3(grid, splits, nz), dim3(kGemmThreads), (size_t)kGemmSmem, st, b);
 }
 
-// out[m * ld + n] = sum over s = 0 .. S-1, in that order, of ws[s][m][n]
-// (deterministic reduction of split-K partials).
-__global__ void splitk_reduce_kernel(const float *__restrict__ ws, int S, int M, int N, float *__restrict__ out,
-                                     int ld)
+// C = A B (fp32, M x N) over K split into up to `splits` ranges of whole
+// 64-wide chunks: partial products to ws (one M x N block per range, rows of
+// N), summed in a fixed order where the gradient is used.  Returns the number
+// of ranges in *used.
+static cudaError_t launch_gemm_partials(GemmArgs a, float *ws, int splits, int *used, cudaStream_t st)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)M * N)
-        return;
-    const int m = (int)(i / N), n = (int)(i % N);
-    float acc = 0.f;
-    for (int sp = 0; sp < S; ++sp)
-        acc += ws[(size_t)sp * M * N + i];
-    out[(size_t)m * ld + n] = acc;
-}
-
-// C (fp32, M x N, row stride ld_out32 at out) = A B over K split into
-// `splits` ranges of whole 64-wide chunks: partials in ws (splits x M x N), then
-// the fixed-order reduction.  ws must hold splits * M * N floats.
-static cudaError_t launch_gemm_f32_splitk(GemmArgs a, float *ws, int splits, cudaStream_t st)
-{
-    float *out = a.out_f32;
-    const int ld = a.ld_out32;
     const int nk = (a.K + kBK - 1) / kBK;
     if (splits > nk)
         splits = nk;
-    if (splits <= 1 || !ws) {
-        a.ksplit = 1;
-        return launch_gemm<EPI_F32>(a, st);
-    }
+    if (splits < 1)
+        splits = 1;
     a.kc_per_split = (nk + splits - 1) / splits;
     a.ksplit = (nk + a.kc_per_split - 1) / a.kc_per_split;
     a.out_f32 = ws;
     a.ld_out32 = a.N;
     a.split_stride = (long long)a.M * a.N;
-    cudaError_t e = launch_gemm<EPI_F32>(a, st);
-    if (e != cudaSuccess)
-        return e;
-    const int64_t total = (int64_t)a.M * a.N;
-    splitk_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(ws, a.ksplit, a.M, a.N, out, ld);
-    return cudaGetLastError();
+    *used = a.ksplit;
+    return launch_gemm<EPI_F32>(a, st);
 }
 
 static GemmArgs gemm_args(const __nv_bfloat16 *A, int lda, int at, const __nv_bfloat16 *B, int ldb, int bt, int M,
@@ -1403,6 +1625,8 @@ static GemmArgs gemm_args(const __nv_bfloat16 *A, int lda, int at, const __nv_bf
     return a;
 }
 
+static constexpr size_t kWs1 = (size_t)kHid * kIn, kWs2 = (size_t)kHid * kHid, kWs3 = (size_t)kBins * kHid;
+
 static void free_work(jl_model *md)
 {
     cudaFree(md->phi);
@@ -1411,12 +1635,11 @@ static void free_work(jl_model *md)
     cudaFree(md->dz);
     cudaFree(md->dz2);
     cudaFree(md->dz1);
-    cudaFree(md->tgt);
-    cudaFree(md->part);
+    cudaFree(md->pb);
     cudaFree(md->loss_part);
     cudaFree(md->ws);
     md->phi = md->h1 = md->h2 = md->dz = md->dz2 = md->dz1 = nullptr;
-    md->tgt = md->part = md->loss_part = md->ws = nullptr;
+    md->pb = md->loss_part = md->ws = nullptr;
     md->cap = 0;
 }
 
@@ -1437,15 +1660,13 @@ static int ensure_work(jl_model *md, int rows, bool train)
         e = cudaMalloc(&md->dz2, r * kHid * 2);
     if (e == cudaSuccess && train)
         e = cudaMalloc(&md->dz1, r * kHid * 2);
-    if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->tgt, r * kBins * 4);
     const size_t ctas = (r + kBM - 1) / kBM;
     if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->part, ctas * 256 * 4);
+        e = cudaMalloc(&md->pb, 3 * ctas * 256 * 4);
     if (e == cudaSuccess && train)
         e = cudaMalloc(&md->loss_part, ctas * 4);
     if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->ws, (size_t)kSplitK * kHid * kHid * 4);
+        e = cudaMalloc(&md->ws, (size_t)kSplitK * (kWs1 + kWs2 + kWs3) * 4);
     if (e != cudaSuccess) {
         free_work(md);
         return cuda_fail(e, "cudaMalloc(surrogate work buffers)");
@@ -1454,17 +1675,40 @@ static int ensure_work(jl_model *md, int rows, bool train)
     return JL_OK;
 }
 
+// The partials of the last backward pass, for grad_of / adam_kernel.
+static GradParts grad_parts(const jl_model *md)
+{
+    GradParts q;
+    const size_t cs = (size_t)md->ctas * 256;
+    q.ws1 = md->ws;
+    q.ws2 = md->ws + (size_t)kSplitK * kWs1;
+    q.ws3 = md->ws + (size_t)kSplitK * (kWs1 + kWs2);
+    q.pb1 = md->pb;
+    q.pb2 = md->pb + cs;
+    q.pb3 = md->pb + 2 * cs;
+    q.loss_part = md->loss_part;
+    q.S = md->ksplit;
+    q.ctas = md->ctas;
+    return q;
+}
+
 // Forward of n rows (n <= cap): phi, h1, h2 and the softmax epilogue.
+// With a target (training rows): trow maps batch row m to its target row
+// (NULL: row m), and the loss and bias-gradient partials of dZ go to md->loss_part
+// and the third block of md->pb.
 static cudaError_t forward_rows(jl_model *md, const float *c, const int32_t *idx, int64_t n, float *probs,
-                                float *score, const float *target, float inv_m, cudaStream_t st)
+                                float *score, const float *target, const int32_t *trow, float inv_m, cudaStream_t st)
 {
     const int64_t threads = n * 32;
-    features_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(c, idx, n, md->B, md->phi);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(features_kernel, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, st, c, idx, n,
+                               (const float *)md->B, md->phi);
     if (e != cudaSuccess)
         return e;
     const __nv_bfloat16 *W1 = md->wb, *W2 = md->wb + kHid * kIn, *W3 = md->wb + kHid * kIn + kHid * kHid;
+    // each product follows the kernel that wrote its A operand; the weights
+    // (B) were written earlier
     GemmArgs a = gemm_args(md->phi, kIn, 0, W1, kIn, 0, (int)n, kHid, kIn, md->status);
+    a.pre_b = 1;
     a.bias = md->params + kOffB1;
     a.relu = 1;
     a.out_bf16 = md->h1;
@@ -1472,6 +1716,7 @@ static cudaError_t forward_rows(jl_model *md, const float *c, const int32_t *idx
     if ((e = launch_gemm<EPI_BIAS_ACT>(a, st)) != cudaSuccess)
         return e;
     a = gemm_args(md->h1, kHid, 0, W2, kHid, 0, (int)n, kHid, kHid, md->status);
+    a.pre_b = 1;
     a.bias = md->params + kOffB2;
     a.relu = 1;
     a.out_bf16 = md->h2;
@@ -1479,81 +1724,72 @@ static cudaError_t forward_rows(jl_model *md, const float *c, const int32_t *idx
     if ((e = launch_gemm<EPI_BIAS_ACT>(a, st)) != cudaSuccess)
         return e;
     a = gemm_args(md->h2, kHid, 0, W3, kHid, 0, (int)n, kBins, kHid, md->status);
+    a.pre_b = 1;
     a.bias = md->params + kOffB3;
     a.probs = probs;
     a.ldp = kBins;
     a.score = score;
     a.target = target;
+    a.trow = trow;
     a.ldt = kBins;
     a.inv_m = inv_m;
     if (target) {
+        md->ctas = (int)((n + kBM - 1) / kBM);
         a.loss = md->loss_part;
         a.out_bf16 = md->dz;
         a.ld_out = kBinsPad;
-        a.colsum = md->part;
+        a.colsum = md->pb + 2 * (size_t)md->ctas * 256;
     }
     if ((e = launch_gemm<EPI_SOFTMAX>(a, st)) != cudaSuccess)
         return e;
-    if (target) {
-        const int ctas = (int)((n + kBM - 1) / kBM);
-        partial_reduce_kernel<<<1, 128, 0, st>>>(md->part, ctas, kBins, 256, md->grads + kOffB3);
-        partial_reduce_kernel<<<1, 32, 0, st>>>(md->loss_part, ctas, 1, 1, md->loss_out ? md->loss_out : md->loss);
-    }
     return cudaGetLastError();
 }
 
-// Backward of the batch in md's work buffers (after forward_rows with target).
+// Backward of the batch in md's work buffers (after forward_rows with target):
+// split-K partials of dW1, dW2, dW3 in md->ws and per-CTA column sums of the
+// bias gradients in md->pb, summed where they are used (grad_of).
 static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
 {
-    // dW3 = dZ^T H2  (101 x 256, K = n)
+    const GradParts q = grad_parts(md);
+    int used = 0;
+    // dW3 = dZ^T H2  (101 x 256, K = n; both operands stored K-major over the batch rows)
+    // (pre_a / pre_b: operands written before the preceding kernel)
     GemmArgs a = gemm_args(md->dz, kBinsPad, 1, md->h2, kHid, 1, kBins, kHid, n, md->status);
-    a.out_f32 = md->grads + kOffW3;
-    a.ld_out32 = kHid;
-    cudaError_t e = launch_gemm_f32_splitk(a, md->ws, kSplitK, st);
+    a.pre_b = 1;
+    cudaError_t e = launch_gemm_partials(a, const_cast<float *>(q.ws3), kSplitK, &used, st);
     if (e != cudaSuccess)
         return e;
+    md->ksplit = used;
     // dZ2 = (dZ W3) * [h2 > 0]   (n x 256, K = 101 padded to 112 with zeros on
     // both sides: dZ's columns past kBins and W3^T's), db2 = column sums
     a = gemm_args(md->dz, kBinsPad, 0, md->wb + kWbT3, kBinsPad, 0, n, kHid, kBinsPad, md->status);
+    a.pre_a = a.pre_b = 1;
     a.mask = md->h2;
     a.ldm = kHid;
     a.out_bf16 = md->dz2;
     a.ld_out = kHid;
-    a.colsum = md->part;
+    a.colsum = const_cast<float *>(q.pb2);
     if ((e = launch_gemm<EPI_MASK>(a, st)) != cudaSuccess)
         return e;
-    const int ctas = (n + kBM - 1) / kBM;
-    partial_reduce_kernel<<<2, 128, 0, st>>>(md->part, ctas, kHid, 256, md->grads + kOffB2);
     // dW2 = dZ2^T H1
     a = gemm_args(md->dz2, kHid, 1, md->h1, kHid, 1, kHid, kHid, n, md->status);
-    a.out_f32 = md->grads + kOffW2;
-    a.ld_out32 = kHid;
-    if ((e = launch_gemm_f32_splitk(a, md->ws, kSplitK, st)) != cudaSuccess)
+    a.pre_b = 1;
+    if ((e = launch_gemm_partials(a, const_cast<float *>(q.ws2), kSplitK, &used, st)) != cudaSuccess)
         return e;
     // dZ1 = (dZ2 W2) * [h1 > 0], db1
     a = gemm_args(md->dz2, kHid, 0, md->wb + kWbT2, kHid, 0, n, kHid, kHid, md->status);
+    a.pre_a = a.pre_b = 1;
     a.mask = md->h1;
     a.ldm = kHid;
     a.out_bf16 = md->dz1;
     a.ld_out = kHid;
-    a.colsum = md->part;
+    a.colsum = const_cast<float *>(q.pb1);
     if ((e = launch_gemm<EPI_MASK>(a, st)) != cudaSuccess)
         return e;
-    partial_reduce_kernel<<<2, 128, 0, st>>>(md->part, ctas, kHid, 256, md->grads + kOffB1);
     // dW1 = dZ1^T Phi (256 x 64)
     a = gemm_args(md->dz1, kHid, 1, md->phi, kIn, 1, kHid, kIn, n, md->status);
-    a.out_f32 = md->grads + kOffW1;
-    a.ld_out32 = kIn;
-    return launch_gemm_f32_splitk(a, md->ws, kSplitK, st);
-}
-
-static cudaError_t zero_grads(jl_model *md, cudaStream_t st)
-{
-    // every gradient (and the loss) is overwritten by the backward pass; the
-    // status word is the only thing cleared per step
-    (void)md;
-    (void)st;
-    return cudaSuccess;
+    a.pre_b = 1;
+    return launch_gemm_partials(a, const_cast<float *>(q.ws1), kSplitK, &used, st);
 }
 
 static void destroy_model(jl_model *md)
@@ -1728,7 +1964,7 @@ int jl_model_forward_layered(jl_model *md, const float *c, int64_t n, float *pro
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
         const int64_t rows = std::min<int64_t>(chunk, n - r0);
         cudaError_t e = forward_rows(md, c + 2 * r0, nullptr, rows, probs ? probs + r0 * kBins : nullptr,
-                                     score ? score + r0 : nullptr, nullptr, 0.f, st);
+                                     score ? score + r0 : nullptr, nullptr, nullptr, 0.f, st);
         if (e != cudaSuccess)
             return cuda_fail(e, "surrogate forward");
     }
@@ -1744,11 +1980,13 @@ int jl_model_grads(jl_model *md, const float *c, const float *target, int32_t n,
     int rc = ensure_work(md, n, true);
     if (rc != JL_OK)
         return rc;
-    cudaError_t e = zero_grads(md, st);
-    if (e == cudaSuccess)
-        e = forward_rows(md, c, nullptr, n, nullptr, nullptr, target, 1.f / (float)n, st);
+    cudaError_t e = forward_rows(md, c, nullptr, n, nullptr, nullptr, target, nullptr, 1.f / (float)n, st);
     if (e == cudaSuccess)
         e = backward_rows(md, n, st);
+    if (e == cudaSuccess) {
+        e = launch_pdl(grad_reduce_kernel, dim3((kNumParams + 255) / 256), dim3(256), 0, st, grad_parts(md), md->grads,
+                       md->loss);
+    }
     if (e != cudaSuccess)
         return cuda_fail(e, "surrogate gradients");
     rc = check_status(md, st);
@@ -1783,34 +2021,34 @@ int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const i
         return cuda_fail(e, "cudaMalloc(loss per step)");
     std::vector<float> hl((size_t)steps);
     const double total = (double)epochs * steps;
+    // Adam's step count: read once, advanced on the host, written back at the end
+    int32_t step0 = 0;
+    e = cudaMemcpyAsync(&step0, md->step, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaFree(loss_steps);
+        return cuda_fail(e, "step counter");
+    }
+    int32_t done = 0;  // steps launched
     for (int ep = 0; ep < epochs && rc == JL_OK; ++ep) {
         for (int s = 0; s < steps; ++s) {
             const int32_t *idx = order ? order + (size_t)ep * n + (size_t)s * batch : nullptr;
             const float *cb = order ? c : c + 2 * (size_t)s * batch;
-            const float *tb;
-            if (idx) {
-                const int64_t tt = (int64_t)batch * kBins;
-                gather_rows_kernel<<<(unsigned)((tt + 255) / 256), 256, 0, st>>>(hist, idx, batch, kBins, md->tgt);
-                tb = md->tgt;
-            } else {
-                tb = hist + (size_t)s * batch * kBins;
-            }
-            md->loss_out = loss_steps + s;
-            e = forward_rows(md, cb, idx, batch, nullptr, nullptr, tb, 1.f / (float)batch, st);
-            md->loss_out = nullptr;
+            // targets: row idx[m] of hist for batch row m (gathered by the softmax product)
+            const float *tb = idx ? hist : hist + (size_t)s * batch * kBins;
+            e = forward_rows(md, cb, idx, batch, nullptr, nullptr, tb, idx, 1.f / (float)batch, st);
             if (e == cudaSuccess)
                 e = backward_rows(md, batch, st);
             if (e == cudaSuccess) {
                 // cosine schedule from lr to lr_final over the steps of this call
                 const double t = ((double)ep * steps + s) / total;
                 const float lr_t = (float)(lr_final + 0.5 * (lr - lr_final) * (1.0 + cos(3.141592653589793 * t)));
-                adam_kernel<<<nparam_blocks, 256, 0, st>>>(md->params, md->grads, md->m, md->v, md->wb, md->step,
-                                                           lr_t, 0.9f, 0.999f, 1e-8f);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess) {
-                step_increment_kernel<<<1, 32, 0, st>>>(md->step);
-                e = cudaGetLastError();
+                const int step_t = step0 + ep * steps + s + 1;
+                e = launch_pdl(adam_kernel, dim3(nparam_blocks), dim3(256), 0, st, grad_parts(md), md->params, md->m,
+                               md->v, md->wb, step_t, lr_t, 0.9f, 0.999f, 1e-8f, loss_steps + s);
+                if (e == cudaSuccess)
+                    ++done;
             }
             if (e != cudaSuccess) {
                 rc = cuda_fail(e, "training step");
@@ -1831,7 +2069,11 @@ int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const i
             loss_curve[ep] = (float)(acc / steps);
         }
     }
-    cudaError_t e2 = cudaStreamSynchronize(st);
+    const int32_t step_end = step0 + done;
+    cudaError_t e2 = cudaMemcpyAsync(md->step, &step_end, 4, cudaMemcpyHostToDevice, st);
+    cudaError_t e3 = cudaStreamSynchronize(st);
+    if (e2 == cudaSuccess)
+        e2 = e3;
     cudaFree(loss_steps);
     if (rc == JL_OK && e2 != cudaSuccess)
         rc = cuda_fail(e2, "training");

@@ -197,6 +197,55 @@ __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
+// As idesc_bf16 with either operand MN-major instead of K-major ("transpose"
+// bits [15] for A and [16] for B): the operand's core matrices then hold 8
+// K-rows of 16 bytes along M (or N), with the same lbo (K direction) / sbo
+// (M or N direction) strides in the descriptor.
+__host__ __device__ constexpr uint32_t idesc_bf16_t(uint32_t M, uint32_t N, bool a_mn, bool b_mn)
+{
+    return idesc_bf16(M, N) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16);
+}
+
+// ---- asynchronous global -> shared copies (cp.async, 16 bytes) ----
+// Copies `src_bytes` (0..16) bytes from src and zero-fills the rest of the
+// 16-byte destination; with src_bytes == 0 nothing is read.  Both addresses
+// 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem),
+                 "r"(src_bytes)
+                 : "memory");
+}
+// 4-byte form (both addresses 4-byte aligned), cached at all levels.
+__device__ __forceinline__ void cp_async4(void *dst_smem, const void *src_gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most `pending` of this thread's committed groups are still
+// in flight (0..3).
+__device__ __forceinline__ void cp_async_wait(int pending)
+{
+    switch (pending) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    }
+}
+
+// ---- programmatic dependent launch ----
+// Wait until the preceding kernel of the stream has completed and its writes
+// are visible (returns at once when this kernel was launched normally).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Let the next kernel of the stream (launched with programmatic stream
+// serialization) start.  Called only after griddep_wait, so every kernel
+// before this one has completed by the time a dependent runs.
+__device__ __forceinline__ void griddep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate)
