@@ -60,6 +60,10 @@ def parse():
 
 
 FLOP_PER_C = 2 * (64 * 256 + 256 * 256 + 256 * 101)  # forward of the surrogate network
+# one training sample: the forward, the three weight-gradient products
+# (dW1, dW2, dW3: the forward's size again) and the two error products
+# dH2 = dZ W3 (101 x 256) and dH1 = dZ2 W2 (256 x 256)
+FLOP_TRAIN_PER_SAMPLE = 2 * FLOP_PER_C + 2 * (101 * 256 + 256 * 256)
 
 
 def run_survey(args, K, W):
@@ -91,6 +95,7 @@ def run_survey(args, K, W):
     curve = m.train(ctr, T, args.survey_epochs, batch=1024, lr=2e-3, lr_final=1e-5, order_seed=1)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    train_steps = args.survey_epochs * (ctr.shape[0] // 1024)
     P, _ = m.forward(held)
     held_l1 = float(sg.hist_l1(P, Th).mean())
     # plain batched rendering of every candidate (the method without the network)
@@ -138,7 +143,15 @@ def run_survey(args, K, W):
            "true_entropy_selected": float(ent[idx.long()].mean()), "true_entropy_all": float(ent.mean()),
            "roofline_forward": {"bound": "tensor", "kernel": "fused_forward_kernel",
                                 "achieved": FLOP_PER_C * n / t_fwd / 1e12, "unit": "TFLOP/s",
-                                "algorithmic_unit": "%d FLOP per C (bf16 products)" % FLOP_PER_C}}
+                                "algorithmic_unit": "%d FLOP per C (bf16 products)" % FLOP_PER_C},
+           "roofline_training": {"bound": "tensor", "kernels": "tc_gemm_kernel x 8 + features + adam per step",
+                                 "achieved": FLOP_TRAIN_PER_SAMPLE * 1024 * train_steps / t_train / 1e12,
+                                 "unit": "TFLOP/s", "steps": train_steps, "us_per_step": t_train / train_steps * 1e6,
+                                 "launches_per_step": 10,
+                                 "algorithmic_unit": "%d FLOP per training sample (bf16 products), batch 1024"
+                                                     % FLOP_TRAIN_PER_SAMPLE,
+                                 "timing": "host wall clock of jl_train over all epochs (includes the per-epoch "
+                                           "loss read-back)"}}
     tplan.close()
     plan.close()
     m.close()
@@ -685,6 +698,13 @@ def main():
             pk, src = 1800.0, "fallback 1.8 PFLOP/s"
         survey["roofline_forward"].update({"peak": pk, "frac": survey["roofline_forward"]["achieved"] / pk,
                                            "peak_source": src})
+        try:
+            pks = float(peaks_file["bf16_tflops_sustained"])
+            srcs = "measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+        except (NameError, KeyError, ValueError):
+            pks, srcs = 1400.0, "fallback 1.4 PFLOP/s sustained"
+        survey["roofline_training"].update({"peak": pks, "frac": survey["roofline_training"]["achieved"] / pks,
+                                            "peak_source": srcs})
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -697,6 +717,7 @@ def main():
                 "survey_summary": None if survey is None else {
                     k: survey[k] for k in ("screened_per_s", "speedup_vs_plain_render", "judge_l1_mean",
                                            "l1_target_met", "heldout_l1_mean", "train_s")},
+                "roofline_training": None if survey is None else survey["roofline_training"],
                 "roofline": roofline, "roofline_other_precision": roofline_other,
                 "by_precision": {("binary64" if p else "binary32"): by_prec[p] for p in (0, 1)},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
