@@ -1750,32 +1750,31 @@ static cudaError_t forward_rows(jl_model *md, const float *c, const int32_t *idx
 // bias gradients in md->pb, summed where they are used (grad_of).
 static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
 {
+    // Order: dZ2, dW3, dZ1, dW2, dW1.  Every product after dZ2 reads only data
+    // written two or more kernels back, so it stages both operands before
+    // waiting for its predecessor (pre_a, pre_b); the mask products, which
+    // carry the chain to dW1, follow each other closely.
     const GradParts q = grad_parts(md);
     int used = 0;
-    // dW3 = dZ^T H2  (101 x 256, K = n; both operands stored K-major over the batch rows)
-    // (pre_a / pre_b: operands written before the preceding kernel)
-    GemmArgs a = gemm_args(md->dz, kBinsPad, 1, md->h2, kHid, 1, kBins, kHid, n, md->status);
-    a.pre_b = 1;
-    cudaError_t e = launch_gemm_partials(a, const_cast<float *>(q.ws3), kSplitK, &used, st);
-    if (e != cudaSuccess)
-        return e;
-    md->ksplit = used;
     // dZ2 = (dZ W3) * [h2 > 0]   (n x 256, K = 101 padded to 112 with zeros on
-    // both sides: dZ's columns past kBins and W3^T's), db2 = column sums
-    a = gemm_args(md->dz, kBinsPad, 0, md->wb + kWbT3, kBinsPad, 0, n, kHid, kBinsPad, md->status);
-    a.pre_a = a.pre_b = 1;
+    // both sides: dZ's columns past kBins and W3^T's), db2 = column sums;
+    // dZ comes from the preceding kernel
+    GemmArgs a = gemm_args(md->dz, kBinsPad, 0, md->wb + kWbT3, kBinsPad, 0, n, kHid, kBinsPad, md->status);
+    a.pre_b = 1;
     a.mask = md->h2;
     a.ldm = kHid;
     a.out_bf16 = md->dz2;
     a.ld_out = kHid;
     a.colsum = const_cast<float *>(q.pb2);
-    if ((e = launch_gemm<EPI_MASK>(a, st)) != cudaSuccess)
+    cudaError_t e = launch_gemm<EPI_MASK>(a, st);
+    if (e != cudaSuccess)
         return e;
-    // dW2 = dZ2^T H1
-    a = gemm_args(md->dz2, kHid, 1, md->h1, kHid, 1, kHid, kHid, n, md->status);
-    a.pre_b = 1;
-    if ((e = launch_gemm_partials(a, const_cast<float *>(q.ws2), kSplitK, &used, st)) != cudaSuccess)
+    // dW3 = dZ^T H2  (101 x 256, K = n; both operands stored K-major over the batch rows)
+    a = gemm_args(md->dz, kBinsPad, 1, md->h2, kHid, 1, kBins, kHid, n, md->status);
+    a.pre_a = a.pre_b = 1;
+    if ((e = launch_gemm_partials(a, const_cast<float *>(q.ws3), kSplitK, &used, st)) != cudaSuccess)
         return e;
+    md->ksplit = used;
     // dZ1 = (dZ2 W2) * [h1 > 0], db1
     a = gemm_args(md->dz2, kHid, 0, md->wb + kWbT2, kHid, 0, n, kHid, kHid, md->status);
     a.pre_a = a.pre_b = 1;
@@ -1786,9 +1785,14 @@ static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
     a.colsum = const_cast<float *>(q.pb1);
     if ((e = launch_gemm<EPI_MASK>(a, st)) != cudaSuccess)
         return e;
+    // dW2 = dZ2^T H1
+    a = gemm_args(md->dz2, kHid, 1, md->h1, kHid, 1, kHid, kHid, n, md->status);
+    a.pre_a = a.pre_b = 1;
+    if ((e = launch_gemm_partials(a, const_cast<float *>(q.ws2), kSplitK, &used, st)) != cudaSuccess)
+        return e;
     // dW1 = dZ1^T Phi (256 x 64)
     a = gemm_args(md->dz1, kHid, 1, md->phi, kIn, 1, kHid, kIn, n, md->status);
-    a.pre_b = 1;
+    a.pre_a = a.pre_b = 1;
     return launch_gemm_partials(a, const_cast<float *>(q.ws1), kSplitK, &used, st);
 }
 
