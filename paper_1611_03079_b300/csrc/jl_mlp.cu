@@ -25,6 +25,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <utility>
 #include <vector>
@@ -648,9 +649,13 @@ __device__ __forceinline__ void fourier_pair(float b0, float b1, float cr, float
 static constexpr int kChK = 32;                              // K width of a weight chunk
 static constexpr int kImgW = 256 * kChK * 2;                 // 16 KB: 256 rows x 32 k
 static constexpr int kImgW3 = kBinsPad * 64 * 2;             // 14 KB: 112 rows x 64 k
-static constexpr int kChunksPerTile = 2 + 8 + 4;             // W1, W2, W3
+static constexpr int kChunksPerTile = 2 + 8 + 4;             // W1, W2, W3 (the forward's chunks)
 static constexpr int kRing = 4;                              // weight slots (16 KB)
-static constexpr int kPackElems = (10 * kImgW + 4 * kImgW3) / 2;  // bf16 elements
+// Packed images: chunks 0..13 as above, then for the training step's
+// backward W3^T (14..17: 256 rows x 32 bins, zero past bin 101) and W2^T
+// (18..25: 256 rows x 32 k).
+static constexpr int kPackChunks = kChunksPerTile + 4 + 8;
+static constexpr size_t kPackBytes = 22 * (size_t)kImgW + 4 * (size_t)kImgW3;
 // shared-memory map of the fused kernel (bytes): two 128-row halves
 static constexpr int kFsPhi = 0;                               // 2 x (128 x 64 bf16)
 static constexpr int kFsH = kFsPhi + 2 * kBM * kIn * 2;        // 2 x (128 x 256 bf16)
@@ -663,60 +668,65 @@ static_assert(kFusedSmem <= 232448, "fused forward exceeds the shared-memory lim
 static constexpr int kFusedEpiWarps = 16;                      // two per row (column halves)
 static constexpr int kFusedThreads = (kFusedEpiWarps + 2) * 32;  // + MMA warp + loader warp
 
-// Byte offset and size of chunk j (0..13) in the packed images.
+// Byte offset and size of chunk j (0..25) in the packed images.
 __host__ __device__ inline size_t chunk_offset(int j, uint32_t &bytes)
 {
     if (j < 10) {
         bytes = kImgW;
         return (size_t)j * kImgW;
     }
-    bytes = kImgW3;
-    return 10 * (size_t)kImgW + (size_t)(j - 10) * kImgW3;
+    if (j < kChunksPerTile) {
+        bytes = kImgW3;
+        return 10 * (size_t)kImgW + (size_t)(j - 10) * kImgW3;
+    }
+    bytes = kImgW;
+    return 10 * (size_t)kImgW + 4 * (size_t)kImgW3 + (size_t)(j - kChunksPerTile) * kImgW;
 }
 
-// One thread per 16-byte piece of the packed images.  Chunk j: 0, 1 -> W1
-// k 0..31, 32..63; 2..9 -> W2 k 32(j-2) ..; 10..13 -> W3 k 64(j-10) ..
-__global__ void pack_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *__restrict__ out)
+// bf16 of w at element (n, k) of the matrix that chunks j0.. hold as K-chunks
+// of 8 G columns: chunk j0 + k / (8 G), core matrix (n / 8, (k % 8G) / 8) at
+// ((n / 8) * G + (k % 8G) / 8) * 128, row n % 8 at 16 bytes, column k % 8 at 2.
+__device__ __forceinline__ void put_image(uint8_t *pack, int j0, int G, int n, int k, float w)
 {
-    const int piece = blockIdx.x * blockDim.x + threadIdx.x;
-    const int total = kPackElems / 8;
-    if (piece >= total)
-        return;
-    const int per_w = kImgW / 16, per_w3 = kImgW3 / 16;
-    int img, local;
-    if (piece < 10 * per_w) {
-        img = piece / per_w;
-        local = piece % per_w;
-    } else {
-        img = 10 + (piece - 10 * per_w) / per_w3;
-        local = (piece - 10 * per_w) % per_w3;
+    uint32_t bytes;
+    const int kw = 8 * G;
+    const size_t off = chunk_offset(j0 + k / kw, bytes);
+    const int kk = k % kw;
+    *reinterpret_cast<__nv_bfloat16 *>(pack + off + (((n >> 3) * G + (kk >> 3)) << 7) + ((n & 7) << 4) +
+                                       ((kk & 7) << 1)) = __float2bfloat16_rn(w);
+}
+
+// The image positions of parameter i (value w): W1 once, W2 and W3 twice
+// (as stored and transposed), biases none.
+__device__ __forceinline__ void pack_param(uint8_t *pack, int i, float w)
+{
+    if (i < kOffB1) {
+        const int o = (i - kOffW1) / kIn, k = (i - kOffW1) % kIn;
+        put_image(pack, 0, 4, o, k, w);
+    } else if (i >= kOffW2 && i < kOffB2) {
+        const int o = (i - kOffW2) / kHid, k = (i - kOffW2) % kHid;
+        put_image(pack, 2, 4, o, k, w);                 // W2[o][k]
+        put_image(pack, 18, 4, k, o, w);                // W2^T[k][o]
+    } else if (i >= kOffW3 && i < kOffB3) {
+        const int b = (i - kOffW3) / kHid, h = (i - kOffW3) % kHid;
+        put_image(pack, 10, 8, b, h, w);                // W3[b][h]
+        put_image(pack, 14, 4, h, b, w);                // W3^T[h][b]
     }
-    // inverse of offset ((r/8)*G + g)*128 + (r%8)*16 for a chunk of G 8-wide
-    // K groups (G = 4 for the 32-wide W1/W2 chunks, 8 for the 64-wide W3 ones)
-    const int G = img < 10 ? 4 : 8;
-    const int cm = local >> 3, rr = local & 7;
-    const int r = (cm / G) * 8 + rr;
-    const int g = cm % G;
-    const float *src;
-    int rows, ld, k0;
-    if (img < 2) {
-        src = p + kOffW1; rows = kHid; ld = kIn; k0 = img * kChK;
-    } else if (img < 10) {
-        src = p + kOffW2; rows = kHid; ld = kHid; k0 = (img - 2) * kChK;
-    } else {
-        src = p + kOffW3; rows = kBins; ld = kHid; k0 = (img - 10) * 64;
-    }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const float v = (r < rows) ? src[(size_t)r * ld + k0 + g * 8 + e] : 0.f;
-        out[(size_t)piece * 8 + e] = __float2bfloat16_rn(v);
-    }
+}
+
+// All image positions from the binary32 parameters (the padding stays as
+// the zeros written when the images were allocated).
+__global__ void pack_params_kernel(const float *__restrict__ p, uint8_t *__restrict__ pack)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kNumParams)
+        pack_param(pack, i, p[i]);
 }
 
 struct FusedArgs {
     const float *c;            // n x 2
     int64_t n;
-    const __nv_bfloat16 *pack; // packed images
+    const uint8_t *pack;       // packed images
     const float *params;       // binary32 parameter block (biases)
     const float *B;            // Fourier matrix 32 x 2
     float *probs;              // n x 101 or NULL
@@ -1177,11 +1187,10 @@ __global__ void grad_reduce_kernel(const __grid_constant__ GradParts q, float *_
 }
 
 // Adam on the whole parameter block (step t, 1 for the first) with each
-// gradient summed from the batch's partials; also refreshes the bf16 copies
-// (W1 | W2 | W3 and the transposes W2^T, W3^T) and writes the batch's loss
-// sum to *loss.
+// gradient summed from the batch's partials; also refreshes the packed bf16
+// weight images (pack_param) and writes the batch's loss sum to *loss.
 __global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restrict__ p, float *__restrict__ m,
-                            float *__restrict__ v, __nv_bfloat16 *__restrict__ wb, int t, float lr, float beta1,
+                            float *__restrict__ v, uint8_t *__restrict__ pack, int t, float lr, float beta1,
                             float beta2, float eps, float *loss)
 {
     tc::griddep_wait();
@@ -1200,23 +1209,524 @@ __global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restri
         const float upd = lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
         const float w = p[i] - upd;
         p[i] = w;
-        int wi = -1, wt = -1;
-        if (i < kOffB1) {
-            wi = i - kOffW1;
-        } else if (i >= kOffW2 && i < kOffB2) {
-            const int o = i - kOffW2, r = o / kHid, c = o - r * kHid;
-            wi = kHid * kIn + o;
-            wt = kWbT2 + c * kHid + r;
-        } else if (i >= kOffW3 && i < kOffB3) {
-            const int o = i - kOffW3, r = o / kHid, c = o - r * kHid;
-            wi = kHid * kIn + kHid * kHid + o;
-            wt = kWbT3 + c * kBinsPad + r;
-        }
-        if (wi >= 0)
-            wb[wi] = __float2bfloat16_rn(w);
-        if (wt >= 0)
-            wb[wt] = __float2bfloat16_rn(w);
+        pack_param(pack, i, w);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Fused training step: one CTA per 128-row tile of the batch runs the forward
+// and the backward of its rows with the activations kept on the SM, and
+// leaves the tile's partial gradients for adam_kernel / grad_reduce_kernel.
+//
+// Shared memory holds the tile's features Phi (128 x 64), H1 and H2
+// (128 x 256) and the logit error dZ (128 x 128, bins past 101 zero), each
+// in the K-major core-matrix layout of the forward products with every
+// column in one row group: core matrix (row / 8, column / 8) at byte
+// ((row / 8) * G + column / 8) * 128, G = columns / 8.  The weight-gradient
+// products contract over the rows and read the same buffers as MN-major
+// operands (same core matrices; K-direction stride G * 128 in the LBO field,
+// M/N-direction stride 128 in the SBO field).  They are computed transposed
+// (dW^T = X^T dY, the input unit on the tensor-memory lanes) so that each
+// warp stores 32 consecutive floats of a parameter row at a time.
+//
+// Weights arrive as the packed chunk images that adam_kernel maintains
+// (pack_param), by cp.async.bulk into a ring of 16 KB slots: three of their
+// own, plus two in the dZ buffer while dZ is not live.  Roles: thread 0
+// issues the MMAs of a product as its chunks land (full barriers) and frees
+// each slot by tcgen05.commit (empty barriers); thread 32 refills freed
+// slots; the first chunks of each product are requested while the previous
+// epilogue runs.  Phases:
+//   P1  D = Phi W1^T        -> H1 = relu(D + b1)
+//   P2  D = H1 W2^T         -> H2 = relu(D + b2)
+//   P3  D = H2 W3^T         -> softmax; dZ = (p - t) / batch rows, loss, db3
+//   P4  dW3^T = H2^T dZ  and  P5  D = dZ W3 -> dZ2 = D * [H2 > 0] over H2, db2
+//   P6  dW2^T = H1^T dZ2
+//   P7  D = dZ2 W2          -> dZ1 = D * [H1 > 0] over H1, db1
+//   P8  dW1^T = Phi^T dZ1   (M = 128 over Phi's 64 columns: lanes 64.. unused)
+// Bias gradients are column sums of the unrounded binary32 errors in a fixed
+// order (a butterfly within each warp, then the four row groups in order).
+// Every wait is bounded; one that gives up sets *status to JL_ETIMEOUT.
+// ---------------------------------------------------------------------------
+static constexpr int kTrThreads = 512;
+static constexpr int kTrPhi = 0;
+static constexpr int kTrH1 = kTrPhi + kBM * kIn * 2;
+static constexpr int kTrH2 = kTrH1 + kBM * kHid * 2;
+static constexpr int kTrDZ = kTrH2 + kBM * kHid * 2;     // dZ, or ring slots 3 and 4
+static constexpr int kTrDZCols = 128;                     // dZ columns held (bins, zero past 101)
+static constexpr int kTrRing = kTrDZ + kBM * kTrDZCols * 2;  // ring slots 0..2
+static constexpr int kTrBar = kTrRing + 3 * kImgW;        // full[5], empty[5], acc, TMEM holder
+static constexpr int kTrLw = kTrBar + 128;                // [16] per-warp loss sums
+static constexpr int kTrB3 = kTrLw + 64;                  // b3 (112 fp32, zero past 101)
+static constexpr int kTrScratch = kTrB3 + kBinsPad * 4;   // [4][128] fp32 exchange; b1 | b2 until P3
+static constexpr int kTrSmem = kTrScratch + 4 * kBM * 4;
+static_assert(kTrSmem <= 232448, "training step exceeds the shared-memory limit");
+static constexpr int kTrTP = kBins;                       // target staging pitch (odd)
+static_assert(kBM * kTrTP * 4 <= kBM * kHid * 2, "targets are staged in the H2 buffer");
+
+struct TrainArgs {
+    const float *c;          // C of batch row m at c[2 * idx[m]] (idx NULL: c[2 m])
+    const int32_t *idx;
+    int n;                   // batch rows
+    const float *target;     // target histogram of batch row m: row trow[m] (NULL: m), 101 floats
+    const int32_t *trow;
+    float inv_m;             // 1 / batch rows
+    const float *B;          // Fourier matrix 32 x 2
+    const float *params;     // binary32 parameters (the biases are read)
+    const uint8_t *pack;     // packed weight images (chunk_offset)
+    float *ws1, *ws2, *ws3;  // per-tile dW1 [256 x 64], dW2 [256 x 256], dW3 [101 x 256]
+    float *pb1, *pb2, *pb3;  // per-tile bias-gradient sums [256]
+    float *loss_part;        // per-tile loss sums
+    int32_t *status;
+};
+
+// Byte offset of element (row, col) in a full-width K-major buffer of G
+// column groups.
+__device__ __forceinline__ int tr_off(int row, int col, int G)
+{
+    return (((row >> 3) * G + (col >> 3)) << 7) + ((row & 7) << 4) + ((col & 7) << 1);
+}
+
+// bf16 of v[0..15] (with relu: of max(v, 0)) into columns col0 .. col0 + 15
+// (col0 a multiple of 8) of row `row`: two 16-byte stores.
+__device__ __forceinline__ void tr_store16(uint8_t *buf, int row, int col0, int G, const float (&v)[16], bool relu)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float *w = v + 8 * h;
+        uint4 u;
+        if (relu) {
+            u = make_uint4(tc::pack_relu_bf16x2(w[0], w[1]), tc::pack_relu_bf16x2(w[2], w[3]),
+                           tc::pack_relu_bf16x2(w[4], w[5]), tc::pack_relu_bf16x2(w[6], w[7]));
+        } else {
+            u = make_uint4(tc::pack_bf16x2(w[0], w[1]), tc::pack_bf16x2(w[2], w[3]), tc::pack_bf16x2(w[4], w[5]),
+                           tc::pack_bf16x2(w[6], w[7]));
+        }
+        *reinterpret_cast<uint4 *>(buf + tr_off(row, col0 + 8 * h, G)) = u;
+    }
+}
+
+// Column sums over a warp: lane L holds 32 values (its row, columns 0..31);
+// afterwards lane L returns the sum of column L over the 32 lanes (a
+// butterfly in a fixed order, 31 exchanges; v is overwritten).
+__device__ __forceinline__ float tr_colsum32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+            const float send = upper ? v[j] : v[j + s];
+            const float keep = upper ? v[j + s] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
+}
+
+// One product's weight stream: chunks j0 .. j0 + n - 1 of the packed
+// images, K-chunks of kw (32 or 64), N rows, through ns ring slots.
+struct TrStream {
+    int j0, n, kw, N, ns;
+};
+
+__global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_constant__ TrainArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *sPhi = sm + kTrPhi, *sH1 = sm + kTrH1, *sH2 = sm + kTrH2, *sDZ = sm + kTrDZ;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kTrBar);
+    uint64_t *empty = full + 5;
+    uint64_t *accbar = full + 10;
+    uint32_t *holder = reinterpret_cast<uint32_t *>(full + 11);
+    float *lw = reinterpret_cast<float *>(sm + kTrLw);
+    float *b3s = reinterpret_cast<float *>(sm + kTrB3);
+    float *scratch = reinterpret_cast<float *>(sm + kTrScratch);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x;
+    const int m0 = tile * kBM;
+    // epilogue role: row r of the tile (tensor-memory lane), column quarter qd
+    const int r = (warp & 3) * 32 + lane;
+    const int qd = warp >> 2;
+    const int row = m0 + r;
+    const bool in = row < a.n;
+
+    if (warp == 0)
+        tc::tmem_alloc(holder, 512);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 11; ++i)
+            tc::mbar_init(&full[i], 1);
+        tc::fence_mbar_init();
+    }
+
+    // ---- inputs of the call, read before waiting for the preceding kernel ----
+    // targets of the tile's rows, staged through the (idle) H2 buffer: each
+    // warp copies 8 rows, lanes along the bins
+    {
+        float *T = reinterpret_cast<float *>(sH2);
+        for (int rr = warp * 8; rr < warp * 8 + 8; ++rr) {
+            const int grow = m0 + rr;
+            if (grow >= a.n)
+                break;
+            const int64_t trw = a.trow ? (int64_t)a.trow[grow] : (int64_t)grow;
+            const float *src = a.target + trw * kBins;
+            for (int cc = lane; cc < kBins; cc += 32)
+                tc::cp_async4(T + rr * kTrTP + cc, src + cc);
+        }
+        tc::cp_async_commit();
+    }
+    // features: thread t takes row t / 4 and frequencies 8 (t % 4) .. + 7,
+    // whose sines and cosines are one 16-byte core-matrix row each
+    {
+        const int rr = threadIdx.x >> 2, f0 = (threadIdx.x & 3) * 8;
+        const int grow = m0 + rr;
+        float sv[8], cv[8];
+        if (grow < a.n) {
+            const int64_t src = a.idx ? (int64_t)a.idx[grow] : (int64_t)grow;
+            const float cr = a.c[2 * src], ci = a.c[2 * src + 1];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                fourier_pair(a.B[2 * (f0 + j)], a.B[2 * (f0 + j) + 1], cr, ci, sv[j], cv[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                sv[j] = cv[j] = 0.f;
+        }
+        const uint4 us = make_uint4(tc::pack_bf16x2(sv[0], sv[1]), tc::pack_bf16x2(sv[2], sv[3]),
+                                    tc::pack_bf16x2(sv[4], sv[5]), tc::pack_bf16x2(sv[6], sv[7]));
+        const uint4 uc = make_uint4(tc::pack_bf16x2(cv[0], cv[1]), tc::pack_bf16x2(cv[2], cv[3]),
+                                    tc::pack_bf16x2(cv[4], cv[5]), tc::pack_bf16x2(cv[6], cv[7]));
+        *reinterpret_cast<uint4 *>(sPhi + tr_off(rr, f0, kIn / 8)) = us;
+        *reinterpret_cast<uint4 *>(sPhi + tr_off(rr, kFreq + f0, kIn / 8)) = uc;
+    }
+    tc::cp_async_wait(0);
+    __syncthreads();
+    float tg[32];  // targets of row `row`, bins 32 qd .. 32 qd + 31
+    {
+        const float *T = reinterpret_cast<const float *>(sH2);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int col = 32 * qd + j;
+            tg[j] = (in && col < kBins) ? T[r * kTrTP + col] : 0.f;
+        }
+    }
+
+    // weights, biases and the partial buffers belong to the preceding kernel (Adam) until it completes
+    tc::griddep_wait();
+    tc::griddep_launch_dependents();
+    for (int i = threadIdx.x; i < 2 * kHid; i += blockDim.x)
+        scratch[i] = a.params[i < kHid ? kOffB1 + i : kOffB2 + (i - kHid)];
+    if (threadIdx.x < kBinsPad)
+        b3s[threadIdx.x] = threadIdx.x < kBins ? a.params[kOffB3 + threadIdx.x] : 0.f;
+
+    bool ok = true;
+    uint32_t taddr = 0;
+    // slot bookkeeping (each in the one thread that uses it): parity bits of
+    // the loads issued per slot (loader), of the loads consumed (MMA issuer)
+    uint32_t lpar = 0, lused = 0, fpar = 0;
+    uint32_t accn = 0;  // completions of the accumulator barrier waited for
+    const uint32_t aPhi = tc::smem_u32(sPhi), aH1 = tc::smem_u32(sH1), aH2 = tc::smem_u32(sH2),
+                   aDZ = tc::smem_u32(sDZ);
+    auto slot_addr = [&](int s) -> uint8_t * { return s < 3 ? sm + kTrRing + s * kImgW : sDZ + (s - 3) * kImgW; };
+
+    // loader: chunk c of stream w into its slot, once the slot's previous
+    // products have completed
+    auto load = [&](const TrStream &w, int c) {
+        const int s = c % w.ns;
+        const uint32_t bit = 1u << s;
+        if (lused & bit) {
+            if (!tc::mbar_wait(&empty[s], ((lpar >> s) & 1u) ^ 1u, kWaitLimit))
+                ok = false;
+        }
+        uint32_t bytes;
+        const size_t off = chunk_offset(w.j0 + c, bytes);
+        tc::bulk_load(slot_addr(s), a.pack + off, bytes, &full[s]);
+        lpar ^= bit;
+        lused |= bit;
+    };
+    // the first chunks of w (their slots are free: every earlier product has completed)
+    auto prefetch = [&](const TrStream &w) {
+        if (threadIdx.x == 32)
+            for (int c = 0; c < min(w.n, w.ns); ++c)
+                load(w, c);
+    };
+    // D[dcol] = A x W^T over stream w: A the K-major activation buffer at
+    // a_addr (aG column groups).  The MMA issuer consumes the chunks as they
+    // land; the loader refills the slots they free.
+    auto run = [&](const TrStream &w, uint32_t a_addr, int aG, uint32_t dcol) {
+        if (threadIdx.x == 0) {
+            const uint32_t idesc = tc::idesc_bf16(kBM, (uint32_t)w.N);
+            const int G = w.kw / 8;
+            for (int c = 0; c < w.n; ++c) {
+                const int s = c % w.ns;
+                if (!tc::mbar_wait(&full[s], (fpar >> s) & 1u, kWaitLimit))
+                    ok = false;
+                fpar ^= 1u << s;
+                tc::tc_fence_after();
+                const uint32_t b0 = tc::smem_u32(slot_addr(s));
+                for (int kk = 0; kk < w.kw / 16; ++kk) {
+                    const uint64_t ad = tc::smem_desc(a_addr + (uint32_t)((c * G + 2 * kk) << 7), 128, (uint32_t)aG * 128);
+                    const uint64_t bd = tc::smem_desc(b0 + (uint32_t)(kk * 256), 128, (uint32_t)G * 128);
+                    tc::mma_bf16(taddr + dcol, ad, bd, idesc, (c | kk) != 0);
+                }
+                tc::mma_commit(&empty[s]);
+            }
+        } else if (threadIdx.x == 32) {
+            for (int c = w.ns; c < w.n; ++c)
+                load(w, c);
+        }
+    };
+    // every product issued so far has completed
+    auto commit_wait = [&]() {
+        if (threadIdx.x == 0)
+            tc::mma_commit(accbar);
+        if (!tc::mbar_wait(accbar, accn & 1, kWaitLimit))
+            ok = false;
+        ++accn;
+        __syncwarp();
+        tc::tc_fence_after();
+    };
+    // shared-memory writes of an epilogue visible to the tensor core, its
+    // tensor-memory reads finished, before the next product is issued
+    auto epilogue_done = [&]() {
+        tc::fence_proxy_async_smem();
+        tc::tc_fence_before();
+        __syncthreads();
+    };
+    // column sums of the tile for columns c0 .. c0 + 31 (this thread: row r,
+    // v[j] = column c0 + j; the four quarters hold disjoint column ranges) to
+    // out[c0 + j] for c0 + j < nvalid
+    auto colsums32 = [&](float (&v)[32], int c0, int nvalid, float *out) {
+        const float s = tr_colsum32(v, lane);
+        __syncthreads();
+        scratch[(warp & 3) * kBM + qd * 32 + lane] = s;
+        __syncthreads();
+        if ((warp & 3) == 0 && c0 + lane < nvalid) {
+            const int cc = qd * 32 + lane;
+            out[c0 + lane] = (scratch[cc] + scratch[kBM + cc]) + (scratch[2 * kBM + cc] + scratch[3 * kBM + cc]);
+        }
+    };
+    // the four quarters' values of each row, combined in quarter order
+    auto row_combine = [&](float x, bool is_max) -> float {
+        __syncthreads();
+        scratch[qd * kBM + r] = x;
+        __syncthreads();
+        const float p0 = scratch[r], p1 = scratch[kBM + r], p2 = scratch[2 * kBM + r], p3 = scratch[3 * kBM + r];
+        return is_max ? fmaxf(fmaxf(p0, p1), fmaxf(p2, p3)) : (p0 + p1) + (p2 + p3);
+    };
+    // one thread issues a weight-gradient product D[dcol] = X^T Y over the
+    // tile's 128 rows: X (M side, column offset xm0) and Y (N side) are
+    // full-width buffers read MN-major
+    auto issue_wgrad = [&](uint32_t x_addr, int xG, int xm0, uint32_t y_addr, int yG, int N, uint32_t dcol) {
+        const uint32_t idesc = tc::idesc_bf16_t(kBM, (uint32_t)N, true, true);
+#pragma unroll
+        for (int kk = 0; kk < kBM / 16; ++kk) {
+            const uint64_t ad = tc::smem_desc(x_addr + (uint32_t)(kk * 2 * xG * 128 + (xm0 / 8) * 128),
+                                              (uint32_t)xG * 128, 128);
+            const uint64_t bd = tc::smem_desc(y_addr + (uint32_t)(kk * 2 * yG * 128), (uint32_t)yG * 128, 128);
+            tc::mma_bf16(taddr + dcol, ad, bd, idesc, kk != 0);
+        }
+    };
+
+    const TrStream w1{0, 2, 32, kHid, 5}, w2{2, 8, 32, kHid, 5}, w3{10, 4, 64, kBinsPad, 5};
+    const TrStream w3t{14, 4, 32, kHid, 3}, w2t{18, 8, 32, kHid, 5};
+    float *ws1 = a.ws1 + (size_t)tile * kHid * kIn;
+    float *ws2 = a.ws2 + (size_t)tile * kHid * kHid;
+    float *ws3 = a.ws3 + (size_t)tile * kBins * kHid;
+
+    prefetch(w1);
+    tc::fence_proxy_async_smem();  // the features
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    taddr = *holder;
+    const uint32_t tw = taddr + ((uint32_t)((warp & 3) * 32) << 16);
+
+    // bias + relu of the accumulator at column dcol into the K-major buffer
+    auto hidden_epilogue = [&](uint32_t dcol, const float *bias, uint8_t *dst) {
+#pragma unroll 1
+        for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tw + dcol + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                v[j] = in ? v[j] + bias[c0 + j] : 0.f;
+            tr_store16(dst, r, c0, kHid / 8, v, true);
+        }
+    };
+    // error through a ReLU: the accumulator at column 0 kept where the
+    // activation in buf is > 0 (bf16 sign clear, not +0), written over the
+    // activation as bf16; bias-gradient sums of the unrounded values to pb
+    auto mask_epilogue = [&](uint8_t *buf, float *pb) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            float cs[32];
+#pragma unroll
+            for (int g16 = 0; g16 < 2; ++g16) {
+                const int c0 = 64 * qd + 32 * h + 16 * g16;
+                float v[16];
+                tc::tmem_ld16(tw + (uint32_t)c0, v);
+                const uint4 ma = *reinterpret_cast<const uint4 *>(buf + tr_off(r, c0, kHid / 8));
+                const uint4 mb = *reinterpret_cast<const uint4 *>(buf + tr_off(r, c0 + 8, kHid / 8));
+                const uint32_t mk[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const uint32_t bits = (mk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+                    v[j] = (in && bits != 0u && bits < 0x8000u) ? v[j] : 0.f;
+                    cs[16 * g16 + j] = v[j];
+                }
+                tr_store16(buf, r, c0, kHid / 8, v, false);
+            }
+            colsums32(cs, 64 * qd + 32 * h, kHid, pb);
+        }
+    };
+    // transposed weight-gradient accumulator (lane = input unit u, column =
+    // output unit o) to out[o * ld + u] for columns [c0, c0 + 16) below ncols:
+    // each store instruction writes 32 consecutive floats
+    auto store_wgrad16 = [&](uint32_t dcol, int c0, int ncols, float *out, int ld, int u) {
+        float v[16];
+        tc::tmem_ld16(tw + dcol + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (c0 + j < ncols)
+                out[(size_t)(c0 + j) * ld + u] = v[j];
+    };
+
+    // ---------------- P1, P2: hidden layers ----------------
+    run(w1, aPhi, kIn / 8, 0);
+    commit_wait();
+    prefetch(w2);
+    hidden_epilogue(0, scratch, sH1);
+    epilogue_done();
+    run(w2, aH1, kHid / 8, 256);
+    commit_wait();
+    prefetch(w3);
+    hidden_epilogue(256, scratch + kHid, sH2);
+    epilogue_done();
+
+    // ---------------- P3: logits, softmax, cross-entropy error ----------------
+    run(w3, aH2, kHid / 8, 0);
+    commit_wait();
+    prefetch(w3t);
+    {
+        constexpr float kLog2e = 1.4426950408889634f;
+        float z[32];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c0 = 32 * qd + 16 * h;
+            float v[16];
+            if (c0 < kBinsPad) {
+                tc::tmem_ld16(tw + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    v[j] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                z[16 * h + j] = c0 + j < kBins ? v[j] + b3s[c0 + j] : -INFINITY;
+        }
+        float mq = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            mq = fmaxf(mq, z[j]);
+        const float mx = row_combine(mq, true);
+        float sq = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (32 * qd + j < kBins)
+                sq += ex2_approx((z[j] - mx) * kLog2e);
+        const float sum = row_combine(sq, false);
+        const float inv = 1.f / sum;
+        const float lse = mx + logf(sum);
+        float ce = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            float d = 0.f;
+            if (32 * qd + j < kBins && in) {
+                const float p = ex2_approx((z[j] - mx) * kLog2e) * inv;
+                ce -= tg[j] * (z[j] - lse);
+                d = (p - tg[j]) * a.inv_m;
+            }
+            z[j] = d;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                v[j] = z[16 * h + j];
+            tr_store16(sDZ, r, 32 * qd + 16 * h, kTrDZCols / 8, v, false);
+        }
+        const float sw = warp_sum(ce);
+        if (lane == 0)
+            lw[warp] = sw;
+        colsums32(z, 32 * qd, kBins, a.pb3 + (size_t)tile * 256);
+        if (threadIdx.x == 0) {
+            float acc = 0.f;
+            for (int i = 0; i < kTrThreads / 32; ++i)
+                acc += lw[i];
+            a.loss_part[tile] = acc;
+        }
+    }
+    epilogue_done();
+
+    // ------- P4 dW3^T = H2^T dZ (columns 256 and 384), P5 D = dZ W3 (columns 0..255) -------
+    if (threadIdx.x == 0) {
+        tc::tc_fence_after();
+        issue_wgrad(aH2, kHid / 8, 0, aDZ, kTrDZCols / 8, kBinsPad, 256);
+        issue_wgrad(aH2, kHid / 8, kBM, aDZ, kTrDZCols / 8, kBinsPad, 384);
+    }
+    run(w3t, aDZ, kTrDZCols / 8, 0);
+    commit_wait();
+    prefetch(w2t);
+    // dW3[b][u]: lanes over the hidden unit u, quarters over the bins
+#pragma unroll 1
+    for (int hh = 0; hh < 2; ++hh)
+#pragma unroll 1
+        for (int c0 = 32 * qd; c0 < 32 * qd + 32 && c0 < kBinsPad; c0 += 16)
+            store_wgrad16((uint32_t)(256 + hh * 128), c0, kBins, ws3, kHid, hh * kBM + r);
+    mask_epilogue(sH2, a.pb2 + (size_t)tile * 256);
+    epilogue_done();
+
+    // ---------------- P6: dW2^T = H1^T dZ2, input units in two halves ----------------
+    if (threadIdx.x == 0) {
+        tc::tc_fence_after();
+        issue_wgrad(aH1, kHid / 8, 0, aH2, kHid / 8, kHid, 0);
+        issue_wgrad(aH1, kHid / 8, kBM, aH2, kHid / 8, kHid, 256);
+    }
+    commit_wait();
+#pragma unroll 1
+    for (int hh = 0; hh < 2; ++hh)
+#pragma unroll 1
+        for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 16)
+            store_wgrad16((uint32_t)(hh * 256), c0, kHid, ws2, kHid, hh * kBM + r);
+    epilogue_done();
+
+    // ---------------- P7: dZ1 = (dZ2 W2) * [H1 > 0] over H1, db1 ----------------
+    run(w2t, aH2, kHid / 8, 0);
+    commit_wait();
+    mask_epilogue(sH1, a.pb1 + (size_t)tile * 256);
+    epilogue_done();
+
+    // ---------------- P8: dW1^T = Phi^T dZ1 ----------------
+    if (threadIdx.x == 0) {
+        tc::tc_fence_after();
+        issue_wgrad(aPhi, kIn / 8, 0, aH1, kHid / 8, kHid, 0);
+    }
+    commit_wait();
+    if ((warp & 3) < 2) {
+        // lanes 0..63 hold the 64 input features
+#pragma unroll 1
+        for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 16)
+            store_wgrad16(0, c0, kHid, ws1, kIn, r);
+    }
+
+    if (!ok && a.status)
+        atomicExch(a.status, (int32_t)JL_ETIMEOUT);
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        tc::tmem_dealloc(taddr, 512);
 }
 
 // L1[i] = sum_b |p[i][b] - q[i][b]| over `bins` columns.
@@ -1522,7 +2032,7 @@ struct jl_model {
     float *grads = nullptr;
     float *m = nullptr, *v = nullptr;
     __nv_bfloat16 *wb = nullptr;  // bf16 W1 | W2 | W3 | W2^T | W3^T (see kWbAll)
-    __nv_bfloat16 *wpack = nullptr;  // packed shared-memory images for the fused forward
+    uint8_t *wpack = nullptr;        // packed bf16 weight images (chunk_offset), kept current by Adam
     float *B = nullptr;        // Fourier matrix 32 x 2
     int32_t *step = nullptr;   // Adam step counter (device)
     float *loss = nullptr;     // device accumulator
@@ -1666,7 +2176,7 @@ static int ensure_work(jl_model *md, int rows, bool train)
     if (e == cudaSuccess && train)
         e = cudaMalloc(&md->loss_part, ctas * 4);
     if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->ws, (size_t)kSplitK * (kWs1 + kWs2 + kWs3) * 4);
+        e = cudaMalloc(&md->ws, std::max<size_t>(ctas, kSplitK) * (kWs1 + kWs2 + kWs3) * 4);
     if (e != cudaSuccess) {
         free_work(md);
         return cuda_fail(e, "cudaMalloc(surrogate work buffers)");
@@ -1681,8 +2191,8 @@ static GradParts grad_parts(const jl_model *md)
     GradParts q;
     const size_t cs = (size_t)md->ctas * 256;
     q.ws1 = md->ws;
-    q.ws2 = md->ws + (size_t)kSplitK * kWs1;
-    q.ws3 = md->ws + (size_t)kSplitK * (kWs1 + kWs2);
+    q.ws2 = md->ws + (size_t)md->ksplit * kWs1;
+    q.ws3 = md->ws + (size_t)md->ksplit * (kWs1 + kWs2);
     q.pb1 = md->pb;
     q.pb2 = md->pb + cs;
     q.pb3 = md->pb + 2 * cs;
@@ -1796,6 +2306,43 @@ static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
     return launch_gemm_partials(a, const_cast<float *>(q.ws1), kSplitK, &used, st);
 }
 
+// One fused training step over n batch rows (n <= cap): forward, softmax
+// error and backward of every 128-row tile in one launch (train_step_kernel),
+// leaving one partial per tile in md's gradient buffers for grad_of.
+static cudaError_t train_rows(jl_model *md, const float *c, const int32_t *idx, int n, const float *target,
+                              const int32_t *trow, float inv_m, cudaStream_t st)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(train_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrSmem);
+        if (e != cudaSuccess)
+            return e;
+        attr_set = true;
+    }
+    const int tiles = (n + kBM - 1) / kBM;
+    md->ctas = md->ksplit = tiles;
+    const GradParts q = grad_parts(md);
+    TrainArgs a;
+    a.c = c;
+    a.idx = idx;
+    a.n = n;
+    a.target = target;
+    a.trow = trow;
+    a.inv_m = inv_m;
+    a.B = md->B;
+    a.params = md->params;
+    a.pack = md->wpack;
+    a.ws1 = const_cast<float *>(q.ws1);
+    a.ws2 = const_cast<float *>(q.ws2);
+    a.ws3 = const_cast<float *>(q.ws3);
+    a.pb1 = const_cast<float *>(q.pb1);
+    a.pb2 = const_cast<float *>(q.pb2);
+    a.pb3 = const_cast<float *>(q.pb3);
+    a.loss_part = md->loss_part;
+    a.status = md->status;
+    return launch_pdl(train_step_kernel, dim3((unsigned)tiles), dim3(kTrThreads), (size_t)kTrSmem, st, a);
+}
+
 static void destroy_model(jl_model *md)
 {
     if (!md)
@@ -1821,6 +2368,7 @@ static void destroy_model(jl_model *md)
 static int refresh_bf16(jl_model *md, cudaStream_t st)
 {
     cast_weights_kernel<<<(kWbAll + 255) / 256, 256, 0, st>>>(md->params, md->wb);
+    pack_params_kernel<<<(kNumParams + 255) / 256, 256, 0, st>>>(md->params, md->wpack);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? JL_OK : cuda_fail(e, "cast weights");
 }
@@ -1859,7 +2407,8 @@ int jl_model_create(const float *fourier_B, const float *init_params, jl_model *
     if (e == cudaSuccess) e = cudaMalloc(&md->m, pb);
     if (e == cudaSuccess) e = cudaMalloc(&md->v, pb);
     if (e == cudaSuccess) e = cudaMalloc(&md->wb, (size_t)kWbAll * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&md->wpack, (size_t)kPackElems * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&md->wpack, kPackBytes);
+    if (e == cudaSuccess) e = cudaMemset(md->wpack, 0, kPackBytes);
     if (e == cudaSuccess) e = cudaMalloc(&md->B, kFreq * 2 * 4);
     if (e == cudaSuccess) e = cudaMalloc(&md->step, 4);
     if (e == cudaSuccess) e = cudaMalloc(&md->loss, 4);
@@ -1924,12 +2473,7 @@ int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, floa
     if (!md || !c || n < 1)
         return fail(JL_EINVAL, "invalid arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // refresh the packed weight images from the binary32 parameters
-    const int pieces = kPackElems / 8;
-    pack_weights_kernel<<<(pieces + 255) / 256, 256, 0, st>>>(md->params, md->wpack);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return cuda_fail(e, "pack weights");
+    cudaError_t e;
     static bool attr_set = false;
     if (!attr_set) {
         e = cudaFuncSetAttribute(fused_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
@@ -1965,6 +2509,8 @@ int jl_model_forward_layered(jl_model *md, const float *c, int64_t n, float *pro
     int rc = ensure_work(md, (int)std::min<int64_t>(n, chunk), false);
     if (rc != JL_OK)
         return rc;
+    // the plain bf16 weights this path reads, from the current parameters
+    cast_weights_kernel<<<(kWbW + 255) / 256, 256, 0, st>>>(md->params, md->wb);
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
         const int64_t rows = std::min<int64_t>(chunk, n - r0);
         cudaError_t e = forward_rows(md, c + 2 * r0, nullptr, rows, probs ? probs + r0 * kBins : nullptr,
@@ -1984,9 +2530,7 @@ int jl_model_grads(jl_model *md, const float *c, const float *target, int32_t n,
     int rc = ensure_work(md, n, true);
     if (rc != JL_OK)
         return rc;
-    cudaError_t e = forward_rows(md, c, nullptr, n, nullptr, nullptr, target, nullptr, 1.f / (float)n, st);
-    if (e == cudaSuccess)
-        e = backward_rows(md, n, st);
+    cudaError_t e = train_rows(md, c, nullptr, n, target, nullptr, 1.f / (float)n, st);
     if (e == cudaSuccess) {
         e = launch_pdl(grad_reduce_kernel, dim3((kNumParams + 255) / 256), dim3(256), 0, st, grad_parts(md), md->grads,
                        md->loss);
@@ -2041,16 +2585,14 @@ int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const i
             const float *cb = order ? c : c + 2 * (size_t)s * batch;
             // targets: row idx[m] of hist for batch row m (gathered by the softmax product)
             const float *tb = idx ? hist : hist + (size_t)s * batch * kBins;
-            e = forward_rows(md, cb, idx, batch, nullptr, nullptr, tb, idx, 1.f / (float)batch, st);
-            if (e == cudaSuccess)
-                e = backward_rows(md, batch, st);
+            e = train_rows(md, cb, idx, batch, tb, idx, 1.f / (float)batch, st);
             if (e == cudaSuccess) {
                 // cosine schedule from lr to lr_final over the steps of this call
                 const double t = ((double)ep * steps + s) / total;
                 const float lr_t = (float)(lr_final + 0.5 * (lr - lr_final) * (1.0 + cos(3.141592653589793 * t)));
                 const int step_t = step0 + ep * steps + s + 1;
                 e = launch_pdl(adam_kernel, dim3(nparam_blocks), dim3(256), 0, st, grad_parts(md), md->params, md->m,
-                               md->v, md->wb, step_t, lr_t, 0.9f, 0.999f, 1e-8f, loss_steps + s);
+                               md->v, md->wpack, step_t, lr_t, 0.9f, 0.999f, 1e-8f, loss_steps + s);
                 if (e == cudaSuccess)
                     ++done;
             }
