@@ -428,12 +428,15 @@ int jl_model_set_state(jl_model *md, const float *params, const float *m, const 
  * with activations kept on chip.  Asynchronous on `stream`. */
 int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, float *score, void *stream);
 
-/* The same forward built from one tensor-core product launch per layer (the
- * layers training uses); a reference for jl_model_forward's fused kernel. */
+/* The same forward built from one launch of the general tensor-core product
+ * kernel per layer; a reference for jl_model_forward's fused kernel. */
 int jl_model_forward_layered(jl_model *md, const float *c, int64_t n, float *probs, float *score, void *stream);
 
 /* Loss and gradients (host outputs, NULL skipped) of one batch of n <= 65536
- * rows against target histograms; no parameter update.  Synchronous. */
+ * rows against target histograms; no parameter update.  One launch of the
+ * fused training-step kernel (forward, softmax error and backward of every
+ * 128-row tile, per-tile partials) and a fixed-order sum of the partials.
+ * Synchronous. */
 int jl_model_grads(jl_model *md, const float *c, const float *target, int32_t n, float *loss_host, float *grads_host,
                    void *stream);
 
@@ -442,8 +445,10 @@ int jl_model_grads(jl_model *md, const float *c, const float *target, int32_t n,
  * sample indices (one permutation per pass, chosen by the caller), or NULL
  * to take samples in order.  The learning rate follows a cosine from lr at
  * the first step of the call to lr_final after the last (lr_final == lr:
- * constant).  loss_curve: host, `epochs` mean batch losses, or NULL.
- * Synchronous. */
+ * constant).  loss_curve: host, `epochs` mean batch losses, or NULL.  Each
+ * step is two launches: the fused training-step kernel and Adam (which sums
+ * the per-tile partials in a fixed order, so a resumed run continues bit for
+ * bit).  Synchronous. */
 int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const int32_t *order, int32_t epochs,
              int32_t batch, float lr, float lr_final, float *loss_curve, void *stream);
 
@@ -456,9 +461,10 @@ int jl_topk(const float *score, int64_t n, int32_t k, int32_t *out_idx, float *o
  * histogram, written to `score`, n floats), then the top k by score
  * (1 <= k <= min(n, 16384)).  When a call has the same (c, n, k, output)
  * pointers as the previous call on the model, its work is captured as a CUDA
- * graph and replayed by later such calls (one graph launch instead of ~14
- * kernel launches); weights updated by training are picked up (the graph
- * re-packs them).  On a stream that is itself being captured, the launches are
+ * graph and replayed by later such calls (one graph launch instead of about
+ * a dozen kernel launches); weights updated by training are picked up (the
+ * graph reads the packed weight images, which every update rewrites in
+ * place).  On a stream that is itself being captured, the launches are
  * issued directly.  Calls on one model must not overlap in time. */
 int jl_survey(jl_model *md, const float *c, int64_t n, int32_t k, int32_t *top_idx, float *top_score, float *score,
               void *stream);

@@ -9,15 +9,22 @@
 // bfloat16 weights and activations, binary32 accumulation, cross-entropy
 // against the target histogram, Adam on binary32 master weights.
 //
-// Every matrix product -- forward and backward -- is one launch of
-// `tc_gemm_kernel`: a 128-row tile per CTA, the whole N (<= 256) in one
-// tensor-memory accumulator, K in 64-wide chunks double-buffered in shared
-// memory (K-major core-matrix layout, operands transposed while staging when
-// the global layout is the other way round), tcgen05.mma issued by one
-// thread, completion tracked by tcgen05.commit on mbarriers, and a fused
-// epilogue read back with tcgen05.ld: bias + ReLU -> bf16, plain fp32, ReLU
-// mask -> bf16 + column sums (bias gradients), or softmax with cross-entropy
-// gradient, loss and entropy score.
+// Kernels:
+//   train_step_kernel   one training step per 128-row tile of the batch in one
+//                       launch: features, the three products with bias + ReLU,
+//                       softmax and cross-entropy error, and the backward
+//                       products (dX and the transposed dW) with activations
+//                       in shared memory; per-tile gradient partials out
+//   adam_kernel         sums the partials in a fixed order, Adam on binary32
+//                       master weights, refreshes the packed bf16 images
+//   fused_forward_kernel  screening forward (features -> softmax entropy)
+//   tc_gemm_kernel      one product with a fused epilogue (bias + ReLU ->
+//                       bf16, softmax, or plain fp32): the layered forward and
+//                       the standalone product jl_gemm_bf16
+// All products are tcgen05.mma issued by one thread, operands in shared
+// memory in the no-swizzle core-matrix layouts (K-major, or MN-major where an
+// operand is read transposed), accumulators in tensor memory read back with
+// tcgen05.ld, completion tracked by tcgen05.commit on mbarriers.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -37,6 +44,7 @@ namespace jl {
 
 static constexpr int kFreq = 32, kIn = 64, kHid = 256, kBins = 101;
 static constexpr int kBinsPad = 112;  // N of the last product (multiple of 16)
+static constexpr int kTrTP = 104;     // padded target row in training: 101 bins + 3 (16-byte rows)
 // Parameter block (binary32, this order): W1[256x64] b1[256] W2[256x256] b2[256] W3[101x256] b3[101]
 static constexpr int kOffW1 = 0;
 static constexpr int kOffB1 = kOffW1 + kHid * kIn;
@@ -46,55 +54,39 @@ static constexpr int kOffW3 = kOffB2 + kHid;
 static constexpr int kOffB3 = kOffW3 + kBins * kHid;
 static constexpr int kNumParams = kOffB3 + kBins;  // 108,389
 
-enum Epi { EPI_BIAS_ACT = 0, EPI_F32 = 1, EPI_MASK = 2, EPI_SOFTMAX = 3 };
+enum Epi { EPI_BIAS_ACT = 0, EPI_SOFTMAX = 1, EPI_F32 = 2 };
 
 struct GemmArgs {
     const __nv_bfloat16 *A;  // trans 0: A[m * lda + k]; trans 1: A[k * lda + m]
     const __nv_bfloat16 *B;  // trans 0: B[n * ldb + k]; trans 1: B[k * ldb + n]
     int lda, ldb, a_trans, b_trans;
     int M, N, K, BN;         // BN: N rounded up to a multiple of 16 (<= 256)
-    const float *bias;       // [N] or NULL
+    const float *bias;       // [N]
     int relu;
-    const __nv_bfloat16 *mask;  // EPI_MASK: keep where mask[m * ldm + n] > 0
-    int ldm;
-    __nv_bfloat16 *out_bf16;
+    __nv_bfloat16 *out_bf16; // EPI_BIAS_ACT: [M x ld_out], ld_out a multiple of 8, 16-byte aligned
     int ld_out;
-    float *out_f32;
+    float *out_f32;          // EPI_F32: [M x ld_out32]
     int ld_out32;
-    float *colsum;           // [gridDim.x x 256] per-CTA column sums (EPI_MASK, EPI_SOFTMAX with target)
-    // EPI_SOFTMAX
-    const float *target;     // [rows x ldt] histogram targets or NULL
-    const int32_t *trow;     // target row of batch row m (NULL: m)
-    int ldt;
-    float inv_m;             // 1 / batch rows for the gradient
-    float *loss;             // [gridDim.x] per-CTA sums over rows of -sum_b t_b log p_b
-    float *probs;            // [M x ldp] or NULL
+    float *probs;            // EPI_SOFTMAX: [M x ldp] or NULL
     int ldp;
-    float *score;            // [M] entropy of p or NULL
+    float *score;            // EPI_SOFTMAX: [M] entropy of p or NULL
     int32_t *status;         // set to JL_ETIMEOUT if a wait gave up
-    // EPI_F32 split-K: CTA (x, y) covers K chunks [y * kc_per_split, (y + 1) * kc_per_split)
-    // and writes its partial M x N product to out_f32 + y * split_stride
-    // (ld_out32 as given); a fixed-order reduction sums the splits.
-    int ksplit, kc_per_split;
-    long long split_stride;
-    // operands that the preceding kernel of the stream does not write: staged
-    // before waiting for it (programmatic dependent launch)
-    int pre_a, pre_b;
-    // column split (not EPI_SOFTMAX, whose rows need every column): CTA
-    // (x, y, z) computes columns [z * n_per_cta, (z + 1) * n_per_cta) of its
-    // rows; 0 = all BN columns in one CTA.  A multiple of 64.
+    // B is not written by the preceding kernel of the stream: its chunks are
+    // staged before waiting for it (programmatic dependent launch)
+    int pre_b;
+    // EPI_BIAS_ACT column split: CTA (x, z) computes columns
+    // [z * n_per_cta, (z + 1) * n_per_cta) of its rows (a multiple of 64);
+    // 0 = all BN columns in one CTA
     int n_per_cta;
 };
 
 static constexpr int kBM = 128, kBK = 64;
-static constexpr int kTP = 65;  // epilogue tile pitch (words) for column blocks of <= 64
 static constexpr int kTileA = kBM * kBK * 2;   // 16 KB
 static constexpr int kTileB = 256 * kBK * 2;   // 32 KB
 static constexpr int kStage = kTileA + kTileB;
 static constexpr int kStages = 4;  // K chunks in flight (K <= 256 is staged in one go)
-static constexpr int kGemmSmem = kStages * kStage + 4 * 256 * 4 + 128;  // stages + column partials + barriers
+static constexpr int kGemmSmem = kStages * kStage + 4 * kBM * 4 + 128;  // stages + row exchange + barriers
 static constexpr long long kWaitLimit = 2000000000ll;  // ~1 s at 2 GHz
-static constexpr int kSplitK = 8;  // K splits of the weight-gradient products (K = batch rows)
 
 // Stage rows [row0, row0 + nrows) x k [k0, k0 + 64) of an operand into the
 // K-major core-matrix layout: piece (r, g) (8 consecutive k) at byte
@@ -226,11 +218,9 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __grid_cons
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *stage0 = sm;
-    float *part = reinterpret_cast<float *>(sm + kStages * kStage);     // [256] column partials + [768] exchange
-    float *xch = part + 256;                                            // [4][128] per-quarter row values
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kStages * kStage + 4 * 256 * 4);  // kStages + 1 mbarriers
+    float *xch = reinterpret_cast<float *>(sm + kStages * kStage);                       // [4][128] row values
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kStages * kStage + 4 * kBM * 4);  // kStages + 1 mbarriers
     uint32_t *holder = reinterpret_cast<uint32_t *>(bars + kStages + 1);
-    __shared__ float lw[kGemmThreads / 32];
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -243,8 +233,6 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __grid_cons
             tc::mbar_init(&bars[b], 1);
         tc::fence_mbar_init();
     }
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
-        part[i] = 0.f;
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -254,43 +242,19 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __grid_cons
     const int npc = (EPI != EPI_SOFTMAX && g.n_per_cta > 0) ? g.n_per_cta : g.BN;
     const int n0 = (int)blockIdx.z * npc;
     const int nbn = min(npc, g.BN - n0);
-    int kc_begin = 0, kc_end = (g.K + kBK - 1) / kBK;
-    if (EPI == EPI_F32 && g.ksplit > 1) {
-        kc_begin = blockIdx.y * g.kc_per_split;
-        kc_end = min(kc_end, kc_begin + g.kc_per_split);
-    }
     // Operands whose 16-byte pieces are aligned are staged with cp.async
     // (transposed ones MN-major, read as such by the MMA); others through
     // registers, K-major (transposed ones gathered element by element).
     const bool a_async = (g.lda & 7) == 0 && (reinterpret_cast<uintptr_t>(g.A) & 15) == 0;
     const bool b_async = (g.ldb & 7) == 0 && (reinterpret_cast<uintptr_t>(g.B) & 15) == 0;
     const uint32_t idesc = tc::idesc_bf16_t(kBM, (uint32_t)nbn, a_async && g.a_trans, b_async && g.b_trans);
-    const int nchunks = kc_end - kc_begin;
+    const int nchunks = (g.K + kBK - 1) / kBK;
     const int nst = min(nchunks, kStages);
     // stage = A tile (128 x 64) + this CTA's B tile (nbn x 64)
     const int stage_bytes = kTileA + nbn * kBK * 2;
-    // EPI_SOFTMAX with targets: the tile rows' targets are copied to a tile
-    // after the stages while the products run (the oldest copy group)
-    constexpr int kTPs = 129;  // target / gradient tile pitch (odd)
-    float *Tt = reinterpret_cast<float *>(stage0 + kStages * stage_bytes);
-    // targets are inputs of the call: copied before waiting for the preceding kernel
-    if (EPI == EPI_SOFTMAX && g.target) {
-        constexpr int kRowsPerWarp = kBM / (kGemmThreads / 32);
-        for (int rr = warp * kRowsPerWarp; rr < (warp + 1) * kRowsPerWarp; ++rr) {
-            const int grow = m0 + rr;
-            if (grow >= g.M)
-                break;
-            const int64_t trw = g.trow ? (int64_t)g.trow[grow] : (int64_t)grow;
-            const float *src = g.target + trw * g.ldt;
-            for (int cc = lane; cc < g.N; cc += 32)
-                tc::cp_async4(Tt + rr * kTPs + cc, src + cc);
-        }
-        tc::cp_async_commit();
-    }
-    auto stage = [&](int lk, bool do_a, bool do_b) {
-        uint8_t *sA = stage0 + (lk % kStages) * stage_bytes;
+    auto stage = [&](int kc, bool do_a, bool do_b) {
+        uint8_t *sA = stage0 + (kc % kStages) * stage_bytes;
         uint8_t *sB = sA + kTileA;
-        const int kc = kc_begin + lk;
         if (do_a) {
             if (a_async)
                 stage_async(sA, g.A, g.lda, g.a_trans, m0, kBM, g.M, kc * kBK, g.K);
@@ -304,31 +268,27 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __grid_cons
                 stage_operand(sB, g.B, g.ldb, g.b_trans, n0, nbn, g.N, kc * kBK, g.K);
         }
     };
-    auto issue = [&](int lk) {
-        stage(lk, true, true);
-        tc::cp_async_commit();
-    };
-    // the first chunks of the operands the preceding kernel does not write,
-    // then (once it has completed) the rest; the copy groups are committed
-    // oldest first, so waiting for chunk lk's second group covers its first
-    const bool pa = g.pre_a != 0, pb = g.pre_b != 0;
-    if (pa || pb) {
-        for (int lk = 0; lk < nst; ++lk)
-            stage(lk, pa, pb);
+    // the first chunks of B (not written by the preceding kernel), then,
+    // once that kernel has completed, A; the copy groups are committed oldest
+    // first, so waiting for chunk kc's second group covers its first
+    const bool pb = g.pre_b != 0;
+    if (pb) {
+        for (int kc = 0; kc < nst; ++kc)
+            stage(kc, false, true);
         tc::cp_async_commit();
     }
     tc::griddep_wait();
     tc::griddep_launch_dependents();
-    for (int lk = 0; lk < nst; ++lk) {
-        stage(lk, !pa, !pb);
+    for (int kc = 0; kc < nst; ++kc) {
+        stage(kc, true, !pb);
         tc::cp_async_commit();
     }
     int committed = nst;
     bool ok = true;
-    for (int lk = 0; lk < nchunks; ++lk) {
-        const int s = lk % kStages;
-        // this thread's copies of chunk lk have landed (later chunks may still fly)
-        tc::cp_async_wait(min(committed - lk - 1, kStages - 1));
+    for (int kc = 0; kc < nchunks; ++kc) {
+        const int s = kc % kStages;
+        // this thread's copies of chunk kc have landed (later chunks may still fly)
+        tc::cp_async_wait(min(committed - kc - 1, kStages - 1));
         tc::fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -338,15 +298,16 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __grid_cons
             for (int kk = 0; kk < kBK / 16; ++kk) {
                 const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, 1024);
                 const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, 1024);
-                tc::mma_bf16(taddr, ad, bd, idesc, (lk | kk) != 0);
+                tc::mma_bf16(taddr, ad, bd, idesc, (kc | kk) != 0);
             }
             tc::mma_commit(&bars[s]);
         }
-        if (lk + nst < nchunks) {
-            // stage s is refilled with chunk lk + nst once chunk lk's MMAs are done
-            if (!tc::mbar_wait(&bars[s], (lk / kStages) & 1, kWaitLimit))
+        if (kc + nst < nchunks) {
+            // stage s is refilled with chunk kc + nst once chunk kc's MMAs are done
+            if (!tc::mbar_wait(&bars[s], (kc / kStages) & 1, kWaitLimit))
                 ok = false;
-            issue(lk + nst);
+            stage(kc + nst, true, true);
+            tc::cp_async_commit();
             ++committed;
         }
     }
@@ -361,55 +322,22 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __grid_cons
     // ---------------- epilogue: thread (row r, column quarter q) ----------------
     // Warp w reads tensor-memory lanes 32 (w % 4) .. +31 (rows) and takes the
     // column quarter q = w / 4 of them, so four threads share a row and four
-    // warps share each scheduler.  Rows are written in whole 16-byte pieces
-    // (16-byte aligned rows; other layouts fall back to element stores).
-    // Column sums for the bias gradients go through an fp32 tile in the (now
-    // idle) staging buffers, summed down the columns in a fixed order.
+    // warps share each scheduler.
     const int r = (warp & 3) * 32 + lane;
     const int q = warp >> 2;
     const int row = m0 + r;
     const bool in = row < g.M;
     const uint32_t tw = taddr + ((uint32_t)((warp & 3) * 32) << 16);
-    float *T = reinterpret_cast<float *>(stage0);         // [128][kTP]
-    float *psum = T + kBM * 129;                          // [<= 512] partial column sums
-
-    // sum over the 128 rows of columns [0, ncols) of `tile` (pitch tp) into
-    // out[c]: G row groups per column (G * ncols <= threads), each summed with
-    // four interleaved accumulators, then the groups in order
-    auto column_sums = [&](const float *tile, int ncols, int tp, float *out) {
-        const int G = 2 * ncols <= kGemmThreads / 4 ? 8 : (ncols <= kGemmThreads / 4 ? 4 : 2);
-        const int rows_g = kBM / G;
-        __syncthreads();
-        for (int t = threadIdx.x; t < G * ncols; t += blockDim.x) {
-            const int c = t % ncols, h = t / ncols;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            const float *col = tile + (h * rows_g) * tp + c;
-            for (int rr = 0; rr < rows_g; rr += 4) {
-                s0 += col[(rr + 0) * tp];
-                s1 += col[(rr + 1) * tp];
-                s2 += col[(rr + 2) * tp];
-                s3 += col[(rr + 3) * tp];
-            }
-            psum[h * ncols + c] = (s0 + s1) + (s2 + s3);
-        }
-        __syncthreads();
-        for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-            float acc = 0.f;
-            for (int h = 0; h < G; ++h)
-                acc += psum[h * ncols + c];
-            out[c] = acc;
-        }
-    };
-    // the four quarters' values of each row, combined in quarter order
-    auto row_combine = [&](float v, bool is_max) -> float {
-        __syncthreads();
-        xch[q * kBM + r] = v;
-        __syncthreads();
-        const float a = xch[r], b = xch[kBM + r], c = xch[2 * kBM + r], d = xch[3 * kBM + r];
-        return is_max ? fmaxf(fmaxf(a, b), fmaxf(c, d)) : (a + b) + (c + d);
-    };
 
     if constexpr (EPI == EPI_SOFTMAX) {
+        // the four quarters' values of each row, combined in quarter order
+        auto row_combine = [&](float v, bool is_max) -> float {
+            __syncthreads();
+            xch[q * kBM + r] = v;
+            __syncthreads();
+            const float a = xch[r], b = xch[kBM + r], c = xch[2 * kBM + r], d = xch[3 * kBM + r];
+            return is_max ? fmaxf(fmaxf(a, b), fmaxf(c, d)) : (a + b) + (c + d);
+        };
         // quarter q holds logits q*32 .. q*32+31 of its row (BN <= 128)
         constexpr float kLog2e = 1.4426950408889634f;
         float z[32];
@@ -442,181 +370,72 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __grid_cons
         const float sum = row_combine(sq, false);
         const float inv = 1.f / sum;
         const float lse = mx + logf(sum);
-        float ce = 0.f, ent = 0.f;
-        const bool vec_dz = g.target && g.out_bf16 && (g.ld_out & 7) == 0 &&
-                            (reinterpret_cast<uintptr_t>(g.out_bf16) & 15) == 0;
+        float ent = 0.f;
 #pragma unroll
-        for (int c8 = 0; c8 < 32; c8 += 8) {
-            const int c0 = q * 32 + c8;
-            if (c0 < g.BN) {
-                float out[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int col = c0 + j;
-                    out[j] = 0.f;
-                    if (col < g.N) {
-                        const float zz = z[c8 + j];
-                        const float p = ex2_approx((zz - mx) * kLog2e) * inv;
-                        const float lp = zz - lse;
-                        if (p > 0.f)
-                            ent -= p * lp;
-                        out[j] = p;
-                        if (g.probs && in)
-                            g.probs[(size_t)row * g.ldp + col] = p;
-                        if (g.target) {
-                            const float t = Tt[r * kTPs + col];
-                            out[j] = 0.f;
-                            if (in) {
-                                ce -= t * lp;
-                                out[j] = (p - t) * g.inv_m;
-                            }
-                            Tt[r * kTPs + col] = out[j];
-                        }
-                    } else if (g.target) {
-                        Tt[r * kTPs + col] = 0.f;
-                    }
-                }
-                if (g.target && g.out_bf16 && in) {
-                    if (vec_dz) {
-                        uint4 u;
-                        u.x = tc::pack_bf16x2(out[0], out[1]);
-                        u.y = tc::pack_bf16x2(out[2], out[3]);
-                        u.z = tc::pack_bf16x2(out[4], out[5]);
-                        u.w = tc::pack_bf16x2(out[6], out[7]);
-                        *reinterpret_cast<uint4 *>(g.out_bf16 + (size_t)row * g.ld_out + c0) = u;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            g.out_bf16[(size_t)row * g.ld_out + c0 + j] = __float2bfloat16_rn(out[j]);
-                    }
-                }
+        for (int j = 0; j < 32; ++j) {
+            const int col = q * 32 + j;
+            if (col < g.N) {
+                const float p = ex2_approx((z[j] - mx) * kLog2e) * inv;
+                if (p > 0.f)
+                    ent -= p * (z[j] - lse);
+                if (g.probs && in)
+                    g.probs[(size_t)row * g.ldp + col] = p;
             }
         }
         const float ent_row = row_combine(ent, false);
         if (in && g.score && q == 0)
             g.score[row] = ent_row;
-        if (g.target) {
-            // bias gradient partials: column sums of the (unrounded) gradient
-            if (!in)
-                for (int c = q * 32; c < q * 32 + 32 && c < g.BN; ++c)
-                    Tt[r * kTPs + c] = 0.f;
-            column_sums(Tt, g.N, kTPs, part);
-            if (g.loss) {
-                const float s2 = warp_sum(in ? ce : 0.f);
-                if (lane == 0)
-                    lw[warp] = s2;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    float acc = 0.f;
-                    for (int w = 0; w < kGemmThreads / 32; ++w)
-                        acc += lw[w];
-                    g.loss[blockIdx.x] = acc;
-                }
-            }
-        }
-    } else {
-        float *o32 = nullptr;
-        if constexpr (EPI == EPI_F32)
-            o32 = g.out_f32 + (g.ksplit > 1 ? (size_t)blockIdx.y * (size_t)g.split_stride : 0);
-        bool vec_out;
-        if constexpr (EPI == EPI_F32)
-            vec_out = (g.ld_out32 & 3) == 0 && (reinterpret_cast<uintptr_t>(o32) & 15) == 0;
-        else
-            vec_out = (g.ld_out & 7) == 0 && (reinterpret_cast<uintptr_t>(g.out_bf16) & 15) == 0;
-        const bool vec_mask = EPI == EPI_MASK && (g.ldm & 7) == 0 &&
-                              (reinterpret_cast<uintptr_t>(g.mask) & 15) == 0;
-        const bool sums = EPI == EPI_MASK && g.colsum;
-        // quarter q takes columns n0 + 16 q (+ 64 k) of the CTA's nbn (<= 64 in every launch here)
+    } else if constexpr (EPI == EPI_F32) {
+        const bool vec_out = (g.ld_out32 & 3) == 0 && (reinterpret_cast<uintptr_t>(g.out_f32) & 15) == 0;
         for (int c0 = n0 + 16 * q; c0 < n0 + nbn; c0 += 64) {
             float v[16];
             tc::tmem_ld16(tw + (uint32_t)(c0 - n0), v);
-            uint32_t mk[8];
-            if constexpr (EPI == EPI_MASK) {
-                if (in && vec_mask && c0 + 16 <= g.N) {
-                    const uint4 *mp = reinterpret_cast<const uint4 *>(g.mask + (size_t)row * g.ldm + c0);
-                    const uint4 a0 = mp[0], a1 = mp[1];
-                    mk[0] = a0.x; mk[1] = a0.y; mk[2] = a0.z; mk[3] = a0.w;
-                    mk[4] = a1.x; mk[5] = a1.y; mk[6] = a1.z; mk[7] = a1.w;
-                } else {
+            if (!in)
+                continue;
+            float *o = g.out_f32 + (size_t)row * g.ld_out32 + c0;
+            if (vec_out && c0 + 16 <= g.N) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int col = c0 + 2 * j;
-                        const uint32_t lo = (in && col < g.N) ? __bfloat16_as_ushort(g.mask[(size_t)row * g.ldm + col]) : 0u;
-                        const uint32_t hi = (in && col + 1 < g.N)
-                                                ? __bfloat16_as_ushort(g.mask[(size_t)row * g.ldm + col + 1]) : 0u;
-                        mk[j] = lo | (hi << 16);
-                    }
-                }
+                for (int k4 = 0; k4 < 4; ++k4)
+                    reinterpret_cast<float4 *>(o)[k4] = make_float4(v[4 * k4], v[4 * k4 + 1], v[4 * k4 + 2],
+                                                                    v[4 * k4 + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j < g.N)
+                        o[j] = v[j];
             }
+        }
+    } else {
+        // quarter q takes columns n0 + 16 q (+ 64 k) of the CTA's nbn
+        for (int c0 = n0 + 16 * q; c0 < n0 + nbn; c0 += 64) {
+            float v[16];
+            tc::tmem_ld16(tw + (uint32_t)(c0 - n0), v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int col = c0 + j;
-                float x = v[j];
-                if (col >= g.N || !in) {
-                    x = 0.f;
-                } else {
-                    if (g.bias)
-                        x += g.bias[col];
-                    if constexpr (EPI == EPI_BIAS_ACT) {
-                        if (g.relu)
-                            x = fmaxf(x, 0.f);
-                    }
-                    if constexpr (EPI == EPI_MASK) {
-                        // keep where the bf16 mask value is > 0 (sign bit clear, not +0)
-                        const uint32_t mb = (mk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-                        x = (mb != 0u && mb < 0x8000u) ? x : 0.f;
-                    }
+                float x = 0.f;
+                if (col < g.N && in) {
+                    x = v[j] + g.bias[col];
+                    if (g.relu)
+                        x = fmaxf(x, 0.f);
                 }
                 v[j] = x;
-                if (sums)
-                    T[r * kTP + (col - n0)] = x;
             }
             if (in) {
-                if constexpr (EPI == EPI_F32) {
-                    if (vec_out && c0 + 16 <= g.N) {
-                        float4 *op = reinterpret_cast<float4 *>(o32 + (size_t)row * g.ld_out32 + c0);
-#pragma unroll
-                        for (int k4 = 0; k4 < 4; ++k4)
-                            op[k4] = make_float4(v[4 * k4], v[4 * k4 + 1], v[4 * k4 + 2], v[4 * k4 + 3]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < g.N)
-                                o32[(size_t)row * g.ld_out32 + c0 + j] = v[j];
-                    }
+                if (c0 + 16 <= g.N) {
+                    uint4 *op = reinterpret_cast<uint4 *>(g.out_bf16 + (size_t)row * g.ld_out + c0);
+                    op[0] = make_uint4(tc::pack_bf16x2(v[0], v[1]), tc::pack_bf16x2(v[2], v[3]),
+                                       tc::pack_bf16x2(v[4], v[5]), tc::pack_bf16x2(v[6], v[7]));
+                    op[1] = make_uint4(tc::pack_bf16x2(v[8], v[9]), tc::pack_bf16x2(v[10], v[11]),
+                                       tc::pack_bf16x2(v[12], v[13]), tc::pack_bf16x2(v[14], v[15]));
                 } else {
-                    if (vec_out && c0 + 16 <= g.N) {
-                        uint4 q0, q1;
-                        q0.x = tc::pack_bf16x2(v[0], v[1]);
-                        q0.y = tc::pack_bf16x2(v[2], v[3]);
-                        q0.z = tc::pack_bf16x2(v[4], v[5]);
-                        q0.w = tc::pack_bf16x2(v[6], v[7]);
-                        q1.x = tc::pack_bf16x2(v[8], v[9]);
-                        q1.y = tc::pack_bf16x2(v[10], v[11]);
-                        q1.z = tc::pack_bf16x2(v[12], v[13]);
-                        q1.w = tc::pack_bf16x2(v[14], v[15]);
-                        uint4 *op = reinterpret_cast<uint4 *>(g.out_bf16 + (size_t)row * g.ld_out + c0);
-                        op[0] = q0;
-                        op[1] = q1;
-                    } else {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < g.N)
-                                g.out_bf16[(size_t)row * g.ld_out + c0 + j] = __float2bfloat16_rn(v[j]);
-                    }
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < g.N)
+                            g.out_bf16[(size_t)row * g.ld_out + c0 + j] = __float2bfloat16_rn(v[j]);
                 }
             }
         }
-        if (sums)
-            column_sums(T, nbn, kTP, part + n0);
-    }
-
-    if ((EPI == EPI_MASK || EPI == EPI_SOFTMAX) && g.colsum) {
-        // deterministic: per-CTA column sums (fixed row order), summed across
-        // CTAs in a fixed order later
-        __syncthreads();
-        for (int c = n0 + threadIdx.x; c < g.N && c < n0 + nbn; c += blockDim.x)
-            g.colsum[(size_t)blockIdx.x * 256 + c] = part[c];
     }
     tc::tc_fence_before();
     __syncthreads();
@@ -654,7 +473,6 @@ static constexpr int kRing = 4;                              // weight slots (16
 // Packed images: chunks 0..13 as above, then for the training step's
 // backward W3^T (14..17: 256 rows x 32 bins, zero past bin 101) and W2^T
 // (18..25: 256 rows x 32 k).
-static constexpr int kPackChunks = kChunksPerTile + 4 + 8;
 static constexpr size_t kPackBytes = 22 * (size_t)kImgW + 4 * (size_t)kImgW3;
 // shared-memory map of the fused kernel (bytes): two 128-row halves
 static constexpr int kFsPhi = 0;                               // 2 x (128 x 64 bf16)
@@ -1105,36 +923,36 @@ __global__ void features_kernel(const float *__restrict__ c, const int32_t *__re
     phi[i * kIn + kFreq + j] = __float2bfloat16_rn(co);
 }
 
-// bf16 weight copies, contiguous: W1, W2, W3 as stored ([out][in]), then the
-// transposes W2^T ([in][out], kHid x kHid) and W3^T ([in][out], kHid rows of
-// kBinsPad, zero past kBins) that the backward products read as K-major
-// operands (16-byte staging instead of 2-byte gathers).
+// bf16 weight copies, contiguous: W1, W2, W3 as stored ([out][in]); the
+// operands of the layered forward.
 static constexpr int kWbW = kHid * kIn + kHid * kHid + kBins * kHid;  // W1 | W2 | W3
-static constexpr int kWbT2 = kWbW;                                     // W2^T
-static constexpr int kWbT3 = kWbT2 + kHid * kHid;                      // W3^T
-static constexpr int kWbAll = kWbT3 + kHid * kBinsPad;
 
 __global__ void cast_weights_kernel(const float *__restrict__ p, __nv_bfloat16 *__restrict__ wb)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < kHid * kIn) {
+    if (i < kHid * kIn)
         wb[i] = __float2bfloat16_rn(p[kOffW1 + i]);
-    } else if (i < kHid * kIn + kHid * kHid) {
+    else if (i < kHid * kIn + kHid * kHid)
         wb[i] = __float2bfloat16_rn(p[kOffW2 + (i - kHid * kIn)]);
-    } else if (i < kWbW) {
+    else if (i < kWbW)
         wb[i] = __float2bfloat16_rn(p[kOffW3 + (i - kHid * kIn - kHid * kHid)]);
-    } else if (i < kWbT3) {
-        const int t = i - kWbT2, n = t / kHid, k = t - n * kHid;  // W2^T[n][k] = W2[k][n]
-        wb[i] = __float2bfloat16_rn(p[kOffW2 + k * kHid + n]);
-    } else if (i < kWbAll) {
-        const int t = i - kWbT3, n = t / kBinsPad, k = t - n * kBinsPad;  // W3^T[n][k] = W3[k][n]
-        wb[i] = __float2bfloat16_rn(k < kBins ? p[kOffW3 + k * kHid + n] : 0.f);
+}
+
+// Target histograms (n rows of 101) copied to rows of kTrTP floats, zero
+// padded, so that the training step fetches each row with one bulk copy.
+__global__ void pad_targets_kernel(const float *__restrict__ src, int64_t n, float *__restrict__ dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n * kTrTP) {
+        const int64_t row = i / kTrTP;
+        const int col = (int)(i - row * kTrTP);
+        dst[i] = col < kBins ? src[row * kBins + col] : 0.f;
     }
 }
 
-// Where one batch's gradient partials live: the split-K partials of the
-// three weight-gradient products and the per-CTA column sums of the bias
-// gradients and of the losses.  They are summed in a fixed order wherever a
+// Where one batch's gradient partials live: the per-tile partials of the
+// three weight gradients and the per-tile column sums of the bias gradients
+// and of the losses (train_step_kernel writes one of each per 128-row tile).  They are summed in a fixed order wherever a
 // gradient is needed (deterministic, so a resumed run continues bit for bit).
 struct GradParts {
     const float *ws1, *ws2, *ws3;  // [S][256 x 64], [S][256 x 256], [S][101 x 256]
@@ -1160,8 +978,20 @@ __device__ __forceinline__ float grad_of(const GradParts &q, int i)
     } else {
         src = q.pb3 + (i - kOffB3), stride = 256, nterm = q.ctas;
     }
+    // the terms in index order; loaded eight at a time so that their
+    // latencies overlap (the sum itself stays sequential)
     float acc = 0.f;
-    for (int r = 0; r < nterm; ++r)
+    int r = 0;
+    for (; r + 8 <= nterm; r += 8) {
+        float t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            t[u] = src[(size_t)(r + u) * stride];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            acc += t[u];
+    }
+    for (; r < nterm; ++r)
         acc += src[(size_t)r * stride];
     return acc;
 }
@@ -1186,12 +1016,13 @@ __global__ void grad_reduce_kernel(const __grid_constant__ GradParts q, float *_
         *loss = loss_of(q);
 }
 
-// Adam on the whole parameter block (step t, 1 for the first) with each
-// gradient summed from the batch's partials; also refreshes the packed bf16
+// Adam on the whole parameter block with each gradient summed from the
+// batch's partials; bc1 = 1 - beta1^t and bc2 = 1 - beta2^t are the bias
+// corrections of step t (1 for the first).  Also refreshes the packed bf16
 // weight images (pack_param) and writes the batch's loss sum to *loss.
 __global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restrict__ p, float *__restrict__ m,
-                            float *__restrict__ v, uint8_t *__restrict__ pack, int t, float lr, float beta1,
-                            float beta2, float eps, float *loss)
+                            float *__restrict__ v, uint8_t *__restrict__ pack, float bc1, float bc2, float lr,
+                            float beta1, float beta2, float eps, float *loss)
 {
     tc::griddep_wait();
     tc::griddep_launch_dependents();
@@ -1204,8 +1035,6 @@ __global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restri
         const float vi = beta2 * v[i] + (1.f - beta2) * g * g;
         m[i] = mi;
         v[i] = vi;
-        const float bc1 = 1.f - powf(beta1, (float)t);
-        const float bc2 = 1.f - powf(beta2, (float)t);
         const float upd = lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
         const float w = p[i] - upd;
         p[i] = w;
@@ -1239,10 +1068,15 @@ __global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restri
 //   P1  D = Phi W1^T        -> H1 = relu(D + b1)
 //   P2  D = H1 W2^T         -> H2 = relu(D + b2)
 //   P3  D = H2 W3^T         -> softmax; dZ = (p - t) / batch rows, loss, db3
-//   P4  dW3^T = H2^T dZ  and  P5  D = dZ W3 -> dZ2 = D * [H2 > 0] over H2, db2
-//   P6  dW2^T = H1^T dZ2
+//   P4  dW3^T = H2^T dZ;  P5  D = dZ W3 -> dZ2 = D * [H2 > 0] over H2, db2
+//   P6  dW2^T = H1^T dZ2 (two halves of the input units)
 //   P7  D = dZ2 W2          -> dZ1 = D * [H1 > 0] over H1, db1
 //   P8  dW1^T = Phi^T dZ1   (M = 128 over Phi's 64 columns: lanes 64.. unused)
+// Three CTAs share a tile (blockIdx.y = role): each runs P1..P3 for the
+// tile's rows, then role 0 takes the chain P5, P7, P8 (dZ2, dZ1, dW1, db1),
+// role 1 the loss, db3, P4 (dW3) and, after its own P5, dW2 for input units
+// 0..127, role 2 db2 and dW2 for units 128..255 -- so the long
+// partial-gradient stores and the sums run beside the chain instead of on it.
 // Bias gradients are column sums of the unrounded binary32 errors in a fixed
 // order (a butterfly within each warp, then the four row groups in order).
 // Every wait is bounded; one that gives up sets *status to JL_ETIMEOUT.
@@ -1260,14 +1094,14 @@ static constexpr int kTrB3 = kTrLw + 64;                  // b3 (112 fp32, zero 
 static constexpr int kTrScratch = kTrB3 + kBinsPad * 4;   // [4][128] fp32 exchange; b1 | b2 until P3
 static constexpr int kTrSmem = kTrScratch + 4 * kBM * 4;
 static_assert(kTrSmem <= 232448, "training step exceeds the shared-memory limit");
-static constexpr int kTrTP = kBins;                       // target staging pitch (odd)
 static_assert(kBM * kTrTP * 4 <= kBM * kHid * 2, "targets are staged in the H2 buffer");
 
 struct TrainArgs {
     const float *c;          // C of batch row m at c[2 * idx[m]] (idx NULL: c[2 m])
     const int32_t *idx;
     int n;                   // batch rows
-    const float *target;     // target histogram of batch row m: row trow[m] (NULL: m), 101 floats
+    const float *target;     // target histogram of batch row m: row trow[m] (NULL: m), kTrTP floats per
+                             // row (101 bins, then padding; 16-byte aligned rows)
     const int32_t *trow;
     float inv_m;             // 1 / batch rows
     const float *B;          // Fourier matrix 32 x 2
@@ -1277,7 +1111,19 @@ struct TrainArgs {
     float *pb1, *pb2, *pb3;  // per-tile bias-gradient sums [256]
     float *loss_part;        // per-tile loss sums
     int32_t *status;
+    // the next step's batch (as c, idx, n, target, trow above; next_n = 0:
+    // none): its rows are prefetched into L2 at the end of this step
+    const float *next_c;
+    const int32_t *next_idx;
+    int next_n;
+    const float *next_target;
+    const int32_t *next_trow;
 };
+
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // Byte offset of element (row, col) in a full-width K-major buffer of G
 // column groups.
@@ -1336,13 +1182,15 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + kTrBar);
     uint64_t *empty = full + 5;
     uint64_t *accbar = full + 10;
-    uint32_t *holder = reinterpret_cast<uint32_t *>(full + 11);
+    uint64_t *tbar = full + 11;  // the tile's target rows
+    uint32_t *holder = reinterpret_cast<uint32_t *>(full + 12);
     float *lw = reinterpret_cast<float *>(sm + kTrLw);
     float *b3s = reinterpret_cast<float *>(sm + kTrB3);
     float *scratch = reinterpret_cast<float *>(sm + kTrScratch);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x;
+    const int role = blockIdx.y;  // the share of the backward this CTA takes
     const int m0 = tile * kBM;
     // epilogue role: row r of the tile (tensor-memory lane), column quarter qd
     const int r = (warp & 3) * 32 + lane;
@@ -1352,27 +1200,28 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
 
     if (warp == 0)
         tc::tmem_alloc(holder, 512);
+    const int nrows = max(0, min(kBM, a.n - m0));  // the tile's rows in the batch
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 11; ++i)
+        for (int i = 0; i < 12; ++i)
             tc::mbar_init(&full[i], 1);
         tc::fence_mbar_init();
+        // the target rows' bytes, announced before any copy is issued
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(tbar)),
+                     "r"((uint32_t)(nrows * kTrTP * 4))
+                     : "memory");
     }
+    __syncthreads();
 
     // ---- inputs of the call, read before waiting for the preceding kernel ----
-    // targets of the tile's rows, staged through the (idle) H2 buffer: each
-    // warp copies 8 rows, lanes along the bins
-    {
-        float *T = reinterpret_cast<float *>(sH2);
-        for (int rr = warp * 8; rr < warp * 8 + 8; ++rr) {
-            const int grow = m0 + rr;
-            if (grow >= a.n)
-                break;
-            const int64_t trw = a.trow ? (int64_t)a.trow[grow] : (int64_t)grow;
-            const float *src = a.target + trw * kBins;
-            for (int cc = lane; cc < kBins; cc += 32)
-                tc::cp_async4(T + rr * kTrTP + cc, src + cc);
-        }
-        tc::cp_async_commit();
+    // targets of the tile's rows, staged through the (idle) H2 buffer: one
+    // bulk copy of a padded row per thread, completing on tbar
+    if ((int)threadIdx.x < nrows) {
+        const int grow = m0 + threadIdx.x;
+        const int64_t trw = a.trow ? (int64_t)a.trow[grow] : (int64_t)grow;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_u32(sH2 + threadIdx.x * kTrTP * 4)),
+                     "l"(a.target + trw * kTrTP), "r"((uint32_t)(kTrTP * 4)), "r"(tc::smem_u32(tbar))
+                     : "memory");
     }
     // features: thread t takes row t / 4 and frequencies 8 (t % 4) .. + 7,
     // whose sines and cosines are one 16-byte core-matrix row each
@@ -1398,27 +1247,26 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
         *reinterpret_cast<uint4 *>(sPhi + tr_off(rr, f0, kIn / 8)) = us;
         *reinterpret_cast<uint4 *>(sPhi + tr_off(rr, kFreq + f0, kIn / 8)) = uc;
     }
-    tc::cp_async_wait(0);
-    __syncthreads();
-    float tg[32];  // targets of row `row`, bins 32 qd .. 32 qd + 31
+    bool ok = tc::mbar_wait(tbar, 0, kWaitLimit);
+    float tg[32];  // targets of row `row`, bins 32 qd .. 32 qd + 31 (as 16-byte reads)
     {
-        const float *T = reinterpret_cast<const float *>(sH2);
+        const float4 *T4 = reinterpret_cast<const float4 *>(sH2 + (size_t)r * kTrTP * 4 + 32 * qd * 4);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int col = 32 * qd + j;
-            tg[j] = (in && col < kBins) ? T[r * kTrTP + col] : 0.f;
+        for (int j4 = 0; j4 < 8; ++j4) {
+            // quarter 3 reads past the row's 104 floats into the next row (or
+            // the idle rest of the buffer); those bins are not used
+            const float4 t4 = T4[j4];
+            const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                tg[4 * j4 + e] = (in && 32 * qd + 4 * j4 + e < kBins) ? tv[e] : 0.f;
         }
     }
 
     // weights, biases and the partial buffers belong to the preceding kernel (Adam) until it completes
     tc::griddep_wait();
     tc::griddep_launch_dependents();
-    for (int i = threadIdx.x; i < 2 * kHid; i += blockDim.x)
-        scratch[i] = a.params[i < kHid ? kOffB1 + i : kOffB2 + (i - kHid)];
-    if (threadIdx.x < kBinsPad)
-        b3s[threadIdx.x] = threadIdx.x < kBins ? a.params[kOffB3 + threadIdx.x] : 0.f;
 
-    bool ok = true;
     uint32_t taddr = 0;
     // slot bookkeeping (each in the one thread that uses it): parity bits of
     // the loads issued per slot (loader), of the loads consumed (MMA issuer)
@@ -1534,6 +1382,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
     float *ws3 = a.ws3 + (size_t)tile * kBins * kHid;
 
     prefetch(w1);
+    // biases: b1 | b2 in the exchange buffer (idle until the softmax), b3 apart
+    for (int i = threadIdx.x; i < 2 * kHid; i += blockDim.x)
+        scratch[i] = a.params[i < kHid ? kOffB1 + i : kOffB2 + (i - kHid)];
+    if (threadIdx.x < kBinsPad)
+        b3s[threadIdx.x] = threadIdx.x < kBins ? a.params[kOffB3 + threadIdx.x] : 0.f;
     tc::fence_proxy_async_smem();  // the features
     tc::tc_fence_before();
     __syncthreads();
@@ -1547,46 +1400,53 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
         for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tw + dcol + (uint32_t)c0, v);
+            // the 16 biases as four broadcast 16-byte reads
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                v[j] = in ? v[j] + bias[c0 + j] : 0.f;
+            for (int j4 = 0; j4 < 4; ++j4) {
+                const float4 b4 = reinterpret_cast<const float4 *>(bias + c0)[j4];
+                v[4 * j4 + 0] = in ? v[4 * j4 + 0] + b4.x : 0.f;
+                v[4 * j4 + 1] = in ? v[4 * j4 + 1] + b4.y : 0.f;
+                v[4 * j4 + 2] = in ? v[4 * j4 + 2] + b4.z : 0.f;
+                v[4 * j4 + 3] = in ? v[4 * j4 + 3] + b4.w : 0.f;
+            }
             tr_store16(dst, r, c0, kHid / 8, v, true);
         }
     };
     // error through a ReLU: the accumulator at column 0 kept where the
     // activation in buf is > 0 (bf16 sign clear, not +0), written over the
     // activation as bf16; bias-gradient sums of the unrounded values to pb
+    // (unless NULL)
     auto mask_epilogue = [&](uint8_t *buf, float *pb) {
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
-            float cs[32];
+            const int c0 = 64 * qd + 32 * h;
+            float v[32];
+            tc::tmem_ld32(tw + (uint32_t)c0, v);
 #pragma unroll
-            for (int g16 = 0; g16 < 2; ++g16) {
-                const int c0 = 64 * qd + 32 * h + 16 * g16;
-                float v[16];
-                tc::tmem_ld16(tw + (uint32_t)c0, v);
-                const uint4 ma = *reinterpret_cast<const uint4 *>(buf + tr_off(r, c0, kHid / 8));
-                const uint4 mb = *reinterpret_cast<const uint4 *>(buf + tr_off(r, c0 + 8, kHid / 8));
-                const uint32_t mk[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+            for (int g8 = 0; g8 < 4; ++g8) {
+                const uint4 mq = *reinterpret_cast<const uint4 *>(buf + tr_off(r, c0 + 8 * g8, kHid / 8));
+                const uint32_t mk[4] = {mq.x, mq.y, mq.z, mq.w};
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < 8; ++j) {
                     const uint32_t bits = (mk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-                    v[j] = (in && bits != 0u && bits < 0x8000u) ? v[j] : 0.f;
-                    cs[16 * g16 + j] = v[j];
+                    float &x = v[8 * g8 + j];
+                    x = (in && bits != 0u && bits < 0x8000u) ? x : 0.f;
                 }
-                tr_store16(buf, r, c0, kHid / 8, v, false);
             }
-            colsums32(cs, 64 * qd + 32 * h, kHid, pb);
+            tr_store16(buf, r, c0, kHid / 8, *reinterpret_cast<const float(*)[16]>(v), false);
+            tr_store16(buf, r, c0 + 16, kHid / 8, *reinterpret_cast<const float(*)[16]>(v + 16), false);
+            if (pb)
+                colsums32(v, c0, kHid, pb);
         }
     };
     // transposed weight-gradient accumulator (lane = input unit u, column =
     // output unit o) to out[o * ld + u] for columns [c0, c0 + 16) below ncols:
     // each store instruction writes 32 consecutive floats
-    auto store_wgrad16 = [&](uint32_t dcol, int c0, int ncols, float *out, int ld, int u) {
-        float v[16];
-        tc::tmem_ld16(tw + dcol + (uint32_t)c0, v);
+    auto store_wgrad32 = [&](uint32_t dcol, int c0, int ncols, float *out, int ld, int u) {
+        float v[32];
+        tc::tmem_ld32(tw + dcol + (uint32_t)c0, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
+        for (int j = 0; j < 32; ++j)
             if (c0 + j < ncols)
                 out[(size_t)(c0 + j) * ld + u] = v[j];
     };
@@ -1621,30 +1481,45 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
                 for (int j = 0; j < 16; ++j)
                     v[j] = 0.f;
             }
+            if (c0 < kBinsPad) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                z[16 * h + j] = c0 + j < kBins ? v[j] + b3s[c0 + j] : -INFINITY;
+                for (int j4 = 0; j4 < 4; ++j4) {
+                    const float4 b4 = reinterpret_cast<const float4 *>(b3s + c0)[j4];
+                    z[16 * h + 4 * j4 + 0] = c0 + 4 * j4 + 0 < kBins ? v[4 * j4 + 0] + b4.x : -INFINITY;
+                    z[16 * h + 4 * j4 + 1] = c0 + 4 * j4 + 1 < kBins ? v[4 * j4 + 1] + b4.y : -INFINITY;
+                    z[16 * h + 4 * j4 + 2] = c0 + 4 * j4 + 2 < kBins ? v[4 * j4 + 2] + b4.z : -INFINITY;
+                    z[16 * h + 4 * j4 + 3] = c0 + 4 * j4 + 3 < kBins ? v[4 * j4 + 3] + b4.w : -INFINITY;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    z[16 * h + j] = -INFINITY;
+            }
         }
         float mq = -INFINITY;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
             mq = fmaxf(mq, z[j]);
         const float mx = row_combine(mq, true);
+        // z - max and its exponential, each formed once
+        float ez[32];
         float sq = 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (32 * qd + j < kBins)
-                sq += ex2_approx((z[j] - mx) * kLog2e);
+        for (int j = 0; j < 32; ++j) {
+            z[j] = z[j] - mx;
+            ez[j] = 32 * qd + j < kBins ? ex2_approx(z[j] * kLog2e) : 0.f;
+            sq += ez[j];
+        }
         const float sum = row_combine(sq, false);
-        const float inv = 1.f / sum;
-        const float lse = mx + logf(sum);
+        const float inv = __frcp_rn(sum);  // 1 / sum, correctly rounded
+        const float lsum = logf(sum);
         float ce = 0.f;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             float d = 0.f;
             if (32 * qd + j < kBins && in) {
-                const float p = ex2_approx((z[j] - mx) * kLog2e) * inv;
-                ce -= tg[j] * (z[j] - lse);
+                const float p = ez[j] * inv;
+                ce -= tg[j] * (z[j] - lsum);
                 d = (p - tg[j]) * a.inv_m;
             }
             z[j] = d;
@@ -1657,68 +1532,87 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
                 v[j] = z[16 * h + j];
             tr_store16(sDZ, r, 32 * qd + 16 * h, kTrDZCols / 8, v, false);
         }
-        const float sw = warp_sum(ce);
-        if (lane == 0)
-            lw[warp] = sw;
-        colsums32(z, 32 * qd, kBins, a.pb3 + (size_t)tile * 256);
-        if (threadIdx.x == 0) {
-            float acc = 0.f;
-            for (int i = 0; i < kTrThreads / 32; ++i)
-                acc += lw[i];
-            a.loss_part[tile] = acc;
+        if (role == 1) {
+            const float sw = warp_sum(ce);
+            if (lane == 0)
+                lw[warp] = sw;
+            colsums32(z, 32 * qd, kBins, a.pb3 + (size_t)tile * 256);
+            if (threadIdx.x == 0) {
+                float acc = 0.f;
+                for (int i = 0; i < kTrThreads / 32; ++i)
+                    acc += lw[i];
+                a.loss_part[tile] = acc;
+            }
         }
     }
     epilogue_done();
 
-    // ------- P4 dW3^T = H2^T dZ (columns 256 and 384), P5 D = dZ W3 (columns 0..255) -------
-    if (threadIdx.x == 0) {
-        tc::tc_fence_after();
-        issue_wgrad(aH2, kHid / 8, 0, aDZ, kTrDZCols / 8, kBinsPad, 256);
-        issue_wgrad(aH2, kHid / 8, kBM, aDZ, kTrDZCols / 8, kBinsPad, 384);
-    }
-    run(w3t, aDZ, kTrDZCols / 8, 0);
-    commit_wait();
-    prefetch(w2t);
-    // dW3[b][u]: lanes over the hidden unit u, quarters over the bins
+    if (role == 0) {
+        // ---------- P5 D = dZ W3 -> dZ2 (over H2), db2; P7 -> dZ1 (over H1), db1; P8 dW1^T = Phi^T dZ1 ----------
+        run(w3t, aDZ, kTrDZCols / 8, 0);
+        commit_wait();
+        prefetch(w2t);
+        mask_epilogue(sH2, nullptr);
+        epilogue_done();
+        run(w2t, aH2, kHid / 8, 0);
+        commit_wait();
+        mask_epilogue(sH1, a.pb1 + (size_t)tile * 256);
+        epilogue_done();
+        if (threadIdx.x == 0) {
+            tc::tc_fence_after();
+            issue_wgrad(aPhi, kIn / 8, 0, aH1, kHid / 8, kHid, 0);
+        }
+        commit_wait();
+        if ((warp & 3) < 2) {
+            // lanes 0..63 hold the 64 input features
 #pragma unroll 1
-    for (int hh = 0; hh < 2; ++hh)
+            for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 32)
+                store_wgrad32(0, c0, kHid, ws1, kIn, r);
+        }
+    } else {
+        // ---------- (role 1: P4 dW3^T = H2^T dZ at columns 256, 384) P5 -> dZ2; P6 dW2^T = H1^T dZ2 ----------
+        if (role == 1 && threadIdx.x == 0) {
+            tc::tc_fence_after();
+            issue_wgrad(aH2, kHid / 8, 0, aDZ, kTrDZCols / 8, kBinsPad, 256);
+            issue_wgrad(aH2, kHid / 8, kBM, aDZ, kTrDZCols / 8, kBinsPad, 384);
+        }
+        run(w3t, aDZ, kTrDZCols / 8, 0);
+        commit_wait();
+        if (role == 1) {
+            // dW3[b][u]: lanes over the hidden unit u, quarters over the bins
+            // (quarter 3 reads columns 96..127 of an accumulator 112 wide: the
+            // last 16 lie in the next accumulator or unused columns, and are
+            // not stored)
 #pragma unroll 1
-        for (int c0 = 32 * qd; c0 < 32 * qd + 32 && c0 < kBinsPad; c0 += 16)
-            store_wgrad16((uint32_t)(256 + hh * 128), c0, kBins, ws3, kHid, hh * kBM + r);
-    mask_epilogue(sH2, a.pb2 + (size_t)tile * 256);
-    epilogue_done();
-
-    // ---------------- P6: dW2^T = H1^T dZ2, input units in two halves ----------------
-    if (threadIdx.x == 0) {
-        tc::tc_fence_after();
-        issue_wgrad(aH1, kHid / 8, 0, aH2, kHid / 8, kHid, 0);
-        issue_wgrad(aH1, kHid / 8, kBM, aH2, kHid / 8, kHid, 256);
-    }
-    commit_wait();
+            for (int hh = 0; hh < 2; ++hh)
+                store_wgrad32((uint32_t)(256 + hh * 128), 32 * qd, kBins, ws3, kHid, hh * kBM + r);
+        }
+        mask_epilogue(sH2, role == 2 ? a.pb2 + (size_t)tile * 256 : nullptr);
+        epilogue_done();
+        // input units 128 (role - 1) .. + 127 of dW2
+        const int u0 = (role - 1) * kBM;
+        if (threadIdx.x == 0) {
+            tc::tc_fence_after();
+            issue_wgrad(aH1, kHid / 8, u0, aH2, kHid / 8, kHid, 0);
+        }
+        commit_wait();
 #pragma unroll 1
-    for (int hh = 0; hh < 2; ++hh)
-#pragma unroll 1
-        for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 16)
-            store_wgrad16((uint32_t)(hh * 256), c0, kHid, ws2, kHid, hh * kBM + r);
-    epilogue_done();
-
-    // ---------------- P7: dZ1 = (dZ2 W2) * [H1 > 0] over H1, db1 ----------------
-    run(w2t, aH2, kHid / 8, 0);
-    commit_wait();
-    mask_epilogue(sH1, a.pb1 + (size_t)tile * 256);
-    epilogue_done();
-
-    // ---------------- P8: dW1^T = Phi^T dZ1 ----------------
-    if (threadIdx.x == 0) {
-        tc::tc_fence_after();
-        issue_wgrad(aPhi, kIn / 8, 0, aH1, kHid / 8, kHid, 0);
-    }
-    commit_wait();
-    if ((warp & 3) < 2) {
-        // lanes 0..63 hold the 64 input features
-#pragma unroll 1
-        for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 16)
-            store_wgrad16(0, c0, kHid, ws1, kIn, r);
+        for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 32)
+            store_wgrad32(0, c0, kHid, ws2, kHid, u0 + r);
+        // role 2 (the shortest share): the next step's C values and target
+        // rows of this tile's rows into L2, so that its input phase, which
+        // starts when Adam's blocks leave the SM, reads them from there
+        if (role == 2 && threadIdx.x < kBM && m0 + (int)threadIdx.x < a.next_n) {
+            const int grow = m0 + threadIdx.x;
+            const int64_t src = a.next_idx ? (int64_t)a.next_idx[grow] : (int64_t)grow;
+            const int64_t trw = a.next_trow ? (int64_t)a.next_trow[grow] : (int64_t)grow;
+            prefetch_l2(a.next_c + 2 * src);
+            const char *t = reinterpret_cast<const char *>(a.next_target + trw * kTrTP);
+#pragma unroll
+            for (int b = 0; b < kTrTP * 4; b += 128)
+                prefetch_l2(t + b);
+            prefetch_l2(t + kTrTP * 4 - 1);
+        }
     }
 
     if (!ok && a.status)
@@ -2031,19 +1925,23 @@ struct jl_model {
     float *params = nullptr;   // binary32 master [kNumParams]
     float *grads = nullptr;
     float *m = nullptr, *v = nullptr;
-    __nv_bfloat16 *wb = nullptr;  // bf16 W1 | W2 | W3 | W2^T | W3^T (see kWbAll)
+    __nv_bfloat16 *wb = nullptr;  // bf16 W1 | W2 | W3 for the layered forward (refreshed by it)
     uint8_t *wpack = nullptr;        // packed bf16 weight images (chunk_offset), kept current by Adam
     float *B = nullptr;        // Fourier matrix 32 x 2
     int32_t *step = nullptr;   // Adam step counter (device)
     float *loss = nullptr;     // device accumulator
     int32_t *status = nullptr;
-    // work buffers for a batch of up to `cap` rows
+    // layered-forward work buffers for up to `cap` rows
     int cap = 0;
-    __nv_bfloat16 *phi = nullptr, *h1 = nullptr, *h2 = nullptr, *dz = nullptr, *dz2 = nullptr, *dz1 = nullptr;
-    float *pb = nullptr;        // per-CTA column sums of the three bias gradients [3][ctas x 256]
-    float *loss_part = nullptr; // per-CTA loss sums [ctas]
-    float *ws = nullptr;        // split-K partials of dW1 | dW2 | dW3 [kSplitK blocks each]
-    int ksplit = 0, ctas = 0;   // partial blocks of the last backward pass
+    __nv_bfloat16 *phi = nullptr, *h1 = nullptr, *h2 = nullptr;  // layered forward activations
+    // training partials for a batch of up to `tcap` rows, per 128-row tile
+    int tcap = 0;
+    float *pb = nullptr;        // column sums of the three bias gradients [3][tiles x 256]
+    float *loss_part = nullptr; // loss sums [tiles]
+    float *ws = nullptr;        // dW1 | dW2 | dW3 partials [tiles blocks each]
+    int tiles = 0;              // tiles of the last training step
+    float *tpad = nullptr;      // padded copy of the targets of a call [tpad_rows x kTrTP]
+    int64_t tpad_rows = 0;
     // screening as one CUDA graph (forward + top-k), captured on an internal
     // stream for the last (c, n, k, outputs) seen and replayed on the caller's
     cudaStream_t cap_stream = nullptr;
@@ -2087,33 +1985,12 @@ static cudaError_t launch_gemm(const GemmArgs &a, cudaStream_t st)
         g_gemm_attr_set[EPI] = true;
     }
     const int grid = (a.M + kBM - 1) / kBM;
-    const int splits = (EPI == EPI_F32 && a.ksplit > 1) ? a.ksplit : 1;
-    // columns in blocks of 64 per CTA (a batch of 1024 rows is only 8 row
-    // tiles: with whole rows per CTA most SMs would idle)
+    // columns in blocks of 64 per CTA (a few row tiles would leave most SMs
+    // idle with whole rows per CTA); the softmax needs every column of a row
     GemmArgs b = a;
     b.n_per_cta = EPI == EPI_SOFTMAX ? 0 : 64;
     const int nz = b.n_per_cta ? (a.BN + b.n_per_cta - 1) / b.n_per_cta : 1;
-    return launch_pdl(kern, dim3(grid, splits, nz), dim3(kGemmThreads), (size_t)kGemmSmem, st, b);
-}
-
-// C = A B (fp32, M x N) over K split into up to `splits` ranges of whole
-// 64-wide chunks: partial products to ws (one M x N block per range, rows of
-// N), summed in a fixed order where the gradient is used.  Returns the number
-// of ranges in *used.
-static cudaError_t launch_gemm_partials(GemmArgs a, float *ws, int splits, int *used, cudaStream_t st)
-{
-    const int nk = (a.K + kBK - 1) / kBK;
-    if (splits > nk)
-        splits = nk;
-    if (splits < 1)
-        splits = 1;
-    a.kc_per_split = (nk + splits - 1) / splits;
-    a.ksplit = (nk + a.kc_per_split - 1) / a.kc_per_split;
-    a.out_f32 = ws;
-    a.ld_out32 = a.N;
-    a.split_stride = (long long)a.M * a.N;
-    *used = a.ksplit;
-    return launch_gemm<EPI_F32>(a, st);
+    return launch_pdl(kern, dim3(grid, 1, nz), dim3(kGemmThreads), (size_t)kGemmSmem, st, b);
 }
 
 static GemmArgs gemm_args(const __nv_bfloat16 *A, int lda, int at, const __nv_bfloat16 *B, int ldb, int bt, int M,
@@ -2142,76 +2019,81 @@ static void free_work(jl_model *md)
     cudaFree(md->phi);
     cudaFree(md->h1);
     cudaFree(md->h2);
-    cudaFree(md->dz);
-    cudaFree(md->dz2);
-    cudaFree(md->dz1);
     cudaFree(md->pb);
     cudaFree(md->loss_part);
     cudaFree(md->ws);
-    md->phi = md->h1 = md->h2 = md->dz = md->dz2 = md->dz1 = nullptr;
+    md->phi = md->h1 = md->h2 = nullptr;
     md->pb = md->loss_part = md->ws = nullptr;
-    md->cap = 0;
+    md->cap = md->tcap = 0;
 }
 
+// Work buffers for `rows` rows: layered-forward activations (train false) or
+// the per-tile gradient partials of a training batch (train true).
 static int ensure_work(jl_model *md, int rows, bool train)
 {
-    if (rows <= md->cap && (!train || md->dz))
+    if (train ? rows <= md->tcap : rows <= md->cap)
         return JL_OK;
-    free_work(md);
     const size_t r = (size_t)rows;
-    cudaError_t e = cudaMalloc(&md->phi, r * kIn * 2);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&md->h1, r * kHid * 2);
-    if (e == cudaSuccess)
-        e = cudaMalloc(&md->h2, r * kHid * 2);
-    if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->dz, r * kBinsPad * 2);
-    if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->dz2, r * kHid * 2);
-    if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->dz1, r * kHid * 2);
-    const size_t ctas = (r + kBM - 1) / kBM;
-    if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->pb, 3 * ctas * 256 * 4);
-    if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->loss_part, ctas * 4);
-    if (e == cudaSuccess && train)
-        e = cudaMalloc(&md->ws, std::max<size_t>(ctas, kSplitK) * (kWs1 + kWs2 + kWs3) * 4);
+    cudaError_t e = cudaSuccess;
+    if (!train) {
+        cudaFree(md->phi);
+        cudaFree(md->h1);
+        cudaFree(md->h2);
+        md->phi = md->h1 = md->h2 = nullptr;
+        md->cap = 0;
+        e = cudaMalloc(&md->phi, r * kIn * 2);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&md->h1, r * kHid * 2);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&md->h2, r * kHid * 2);
+        if (e == cudaSuccess)
+            md->cap = rows;
+    } else {
+        cudaFree(md->pb);
+        cudaFree(md->loss_part);
+        cudaFree(md->ws);
+        md->pb = md->loss_part = md->ws = nullptr;
+        md->tcap = 0;
+        const size_t tiles = (r + kBM - 1) / kBM;
+        e = cudaMalloc(&md->pb, 3 * tiles * 256 * 4);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&md->loss_part, tiles * 4);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&md->ws, tiles * (kWs1 + kWs2 + kWs3) * 4);
+        if (e == cudaSuccess)
+            md->tcap = rows;
+    }
     if (e != cudaSuccess) {
         free_work(md);
         return cuda_fail(e, "cudaMalloc(surrogate work buffers)");
     }
-    md->cap = rows;
     return JL_OK;
 }
 
-// The partials of the last backward pass, for grad_of / adam_kernel.
+// The partials of the last training step, for grad_of / adam_kernel.
 static GradParts grad_parts(const jl_model *md)
 {
     GradParts q;
-    const size_t cs = (size_t)md->ctas * 256;
+    const size_t cs = (size_t)md->tiles * 256;
     q.ws1 = md->ws;
-    q.ws2 = md->ws + (size_t)md->ksplit * kWs1;
-    q.ws3 = md->ws + (size_t)md->ksplit * (kWs1 + kWs2);
+    q.ws2 = md->ws + (size_t)md->tiles * kWs1;
+    q.ws3 = md->ws + (size_t)md->tiles * (kWs1 + kWs2);
     q.pb1 = md->pb;
     q.pb2 = md->pb + cs;
     q.pb3 = md->pb + 2 * cs;
     q.loss_part = md->loss_part;
-    q.S = md->ksplit;
-    q.ctas = md->ctas;
+    q.S = md->tiles;
+    q.ctas = md->tiles;
     return q;
 }
 
-// Forward of n rows (n <= cap): phi, h1, h2 and the softmax epilogue.
-// With a target (training rows): trow maps batch row m to its target row
-// (NULL: row m), and the loss and bias-gradient partials of dZ go to md->loss_part
-// and the third block of md->pb.
-static cudaError_t forward_rows(jl_model *md, const float *c, const int32_t *idx, int64_t n, float *probs,
-                                float *score, const float *target, const int32_t *trow, float inv_m, cudaStream_t st)
+// Layered forward of n rows (n <= cap): phi, h1, h2 and the softmax
+// epilogue (probs and / or entropy score).
+static cudaError_t forward_rows(jl_model *md, const float *c, int64_t n, float *probs, float *score, cudaStream_t st)
 {
     const int64_t threads = n * 32;
-    cudaError_t e = launch_pdl(features_kernel, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, st, c, idx, n,
-                               (const float *)md->B, md->phi);
+    cudaError_t e = launch_pdl(features_kernel, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, st, c,
+                               (const int32_t *)nullptr, n, (const float *)md->B, md->phi);
     if (e != cudaSuccess)
         return e;
     const __nv_bfloat16 *W1 = md->wb, *W2 = md->wb + kHid * kIn, *W3 = md->wb + kHid * kIn + kHid * kHid;
@@ -2239,78 +2121,18 @@ static cudaError_t forward_rows(jl_model *md, const float *c, const int32_t *idx
     a.probs = probs;
     a.ldp = kBins;
     a.score = score;
-    a.target = target;
-    a.trow = trow;
-    a.ldt = kBins;
-    a.inv_m = inv_m;
-    if (target) {
-        md->ctas = (int)((n + kBM - 1) / kBM);
-        a.loss = md->loss_part;
-        a.out_bf16 = md->dz;
-        a.ld_out = kBinsPad;
-        a.colsum = md->pb + 2 * (size_t)md->ctas * 256;
-    }
     if ((e = launch_gemm<EPI_SOFTMAX>(a, st)) != cudaSuccess)
         return e;
     return cudaGetLastError();
-}
-
-// Backward of the batch in md's work buffers (after forward_rows with target):
-// split-K partials of dW1, dW2, dW3 in md->ws and per-CTA column sums of the
-// bias gradients in md->pb, summed where they are used (grad_of).
-static cudaError_t backward_rows(jl_model *md, int n, cudaStream_t st)
-{
-    // Order: dZ2, dW3, dZ1, dW2, dW1.  Every product after dZ2 reads only data
-    // written two or more kernels back, so it stages both operands before
-    // waiting for its predecessor (pre_a, pre_b); the mask products, which
-    // carry the chain to dW1, follow each other closely.
-    const GradParts q = grad_parts(md);
-    int used = 0;
-    // dZ2 = (dZ W3) * [h2 > 0]   (n x 256, K = 101 padded to 112 with zeros on
-    // both sides: dZ's columns past kBins and W3^T's), db2 = column sums;
-    // dZ comes from the preceding kernel
-    GemmArgs a = gemm_args(md->dz, kBinsPad, 0, md->wb + kWbT3, kBinsPad, 0, n, kHid, kBinsPad, md->status);
-    a.pre_b = 1;
-    a.mask = md->h2;
-    a.ldm = kHid;
-    a.out_bf16 = md->dz2;
-    a.ld_out = kHid;
-    a.colsum = const_cast<float *>(q.pb2);
-    cudaError_t e = launch_gemm<EPI_MASK>(a, st);
-    if (e != cudaSuccess)
-        return e;
-    // dW3 = dZ^T H2  (101 x 256, K = n; both operands stored K-major over the batch rows)
-    a = gemm_args(md->dz, kBinsPad, 1, md->h2, kHid, 1, kBins, kHid, n, md->status);
-    a.pre_a = a.pre_b = 1;
-    if ((e = launch_gemm_partials(a, const_cast<float *>(q.ws3), kSplitK, &used, st)) != cudaSuccess)
-        return e;
-    md->ksplit = used;
-    // dZ1 = (dZ2 W2) * [h1 > 0], db1
-    a = gemm_args(md->dz2, kHid, 0, md->wb + kWbT2, kHid, 0, n, kHid, kHid, md->status);
-    a.pre_a = a.pre_b = 1;
-    a.mask = md->h1;
-    a.ldm = kHid;
-    a.out_bf16 = md->dz1;
-    a.ld_out = kHid;
-    a.colsum = const_cast<float *>(q.pb1);
-    if ((e = launch_gemm<EPI_MASK>(a, st)) != cudaSuccess)
-        return e;
-    // dW2 = dZ2^T H1
-    a = gemm_args(md->dz2, kHid, 1, md->h1, kHid, 1, kHid, kHid, n, md->status);
-    a.pre_a = a.pre_b = 1;
-    if ((e = launch_gemm_partials(a, const_cast<float *>(q.ws2), kSplitK, &used, st)) != cudaSuccess)
-        return e;
-    // dW1 = dZ1^T Phi (256 x 64)
-    a = gemm_args(md->dz1, kHid, 1, md->phi, kIn, 1, kHid, kIn, n, md->status);
-    a.pre_a = a.pre_b = 1;
-    return launch_gemm_partials(a, const_cast<float *>(q.ws1), kSplitK, &used, st);
 }
 
 // One fused training step over n batch rows (n <= cap): forward, softmax
 // error and backward of every 128-row tile in one launch (train_step_kernel),
 // leaving one partial per tile in md's gradient buffers for grad_of.
 static cudaError_t train_rows(jl_model *md, const float *c, const int32_t *idx, int n, const float *target,
-                              const int32_t *trow, float inv_m, cudaStream_t st)
+                              const int32_t *trow, float inv_m, cudaStream_t st, const float *next_c = nullptr,
+                              const int32_t *next_idx = nullptr, int next_n = 0, const float *next_target = nullptr,
+                              const int32_t *next_trow = nullptr)
 {
     static bool attr_set = false;
     if (!attr_set) {
@@ -2320,7 +2142,7 @@ static cudaError_t train_rows(jl_model *md, const float *c, const int32_t *idx, 
         attr_set = true;
     }
     const int tiles = (n + kBM - 1) / kBM;
-    md->ctas = md->ksplit = tiles;
+    md->tiles = tiles;
     const GradParts q = grad_parts(md);
     TrainArgs a;
     a.c = c;
@@ -2340,7 +2162,30 @@ static cudaError_t train_rows(jl_model *md, const float *c, const int32_t *idx, 
     a.pb3 = const_cast<float *>(q.pb3);
     a.loss_part = md->loss_part;
     a.status = md->status;
-    return launch_pdl(train_step_kernel, dim3((unsigned)tiles), dim3(kTrThreads), (size_t)kTrSmem, st, a);
+    a.next_c = next_c;
+    a.next_idx = next_idx;
+    a.next_n = next_n;
+    a.next_target = next_target;
+    a.next_trow = next_trow;
+    return launch_pdl(train_step_kernel, dim3((unsigned)tiles, 3), dim3(kTrThreads), (size_t)kTrSmem, st, a);
+}
+
+// The targets of a call (n rows of 101) as padded rows in md->tpad.
+static int pad_targets(jl_model *md, const float *target, int64_t n, cudaStream_t st)
+{
+    if (n > md->tpad_rows) {
+        cudaFree(md->tpad);
+        md->tpad = nullptr;
+        md->tpad_rows = 0;
+        cudaError_t e = cudaMalloc(&md->tpad, (size_t)n * kTrTP * 4);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "cudaMalloc(padded targets)");
+        md->tpad_rows = n;
+    }
+    const int64_t total = n * kTrTP;
+    pad_targets_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(target, n, md->tpad);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? JL_OK : cuda_fail(e, "pad targets");
 }
 
 static void destroy_model(jl_model *md)
@@ -2348,6 +2193,7 @@ static void destroy_model(jl_model *md)
     if (!md)
         return;
     free_work(md);
+    cudaFree(md->tpad);
     if (md->survey_exec)
         cudaGraphExecDestroy(md->survey_exec);
     if (md->cap_stream)
@@ -2367,7 +2213,7 @@ static void destroy_model(jl_model *md)
 
 static int refresh_bf16(jl_model *md, cudaStream_t st)
 {
-    cast_weights_kernel<<<(kWbAll + 255) / 256, 256, 0, st>>>(md->params, md->wb);
+    cast_weights_kernel<<<(kWbW + 255) / 256, 256, 0, st>>>(md->params, md->wb);
     pack_params_kernel<<<(kNumParams + 255) / 256, 256, 0, st>>>(md->params, md->wpack);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? JL_OK : cuda_fail(e, "cast weights");
@@ -2406,7 +2252,7 @@ int jl_model_create(const float *fourier_B, const float *init_params, jl_model *
     if (e == cudaSuccess) e = cudaMalloc(&md->grads, pb);
     if (e == cudaSuccess) e = cudaMalloc(&md->m, pb);
     if (e == cudaSuccess) e = cudaMalloc(&md->v, pb);
-    if (e == cudaSuccess) e = cudaMalloc(&md->wb, (size_t)kWbAll * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&md->wb, (size_t)kWbW * 2);
     if (e == cudaSuccess) e = cudaMalloc(&md->wpack, kPackBytes);
     if (e == cudaSuccess) e = cudaMemset(md->wpack, 0, kPackBytes);
     if (e == cudaSuccess) e = cudaMalloc(&md->B, kFreq * 2 * 4);
@@ -2498,7 +2344,7 @@ int jl_model_forward(jl_model *md, const float *c, int64_t n, float *probs, floa
     return e == cudaSuccess ? JL_OK : cuda_fail(e, "fused forward");
 }
 
-// The forward built from the general product kernel (the path training uses);
+// The forward built from one launch of the general product kernel per layer;
 // kept as a reference for the fused kernel.
 int jl_model_forward_layered(jl_model *md, const float *c, int64_t n, float *probs, float *score, void *stream)
 {
@@ -2513,8 +2359,8 @@ int jl_model_forward_layered(jl_model *md, const float *c, int64_t n, float *pro
     cast_weights_kernel<<<(kWbW + 255) / 256, 256, 0, st>>>(md->params, md->wb);
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
         const int64_t rows = std::min<int64_t>(chunk, n - r0);
-        cudaError_t e = forward_rows(md, c + 2 * r0, nullptr, rows, probs ? probs + r0 * kBins : nullptr,
-                                     score ? score + r0 : nullptr, nullptr, nullptr, 0.f, st);
+        cudaError_t e = forward_rows(md, c + 2 * r0, rows, probs ? probs + r0 * kBins : nullptr,
+                                     score ? score + r0 : nullptr, st);
         if (e != cudaSuccess)
             return cuda_fail(e, "surrogate forward");
     }
@@ -2524,13 +2370,15 @@ int jl_model_forward_layered(jl_model *md, const float *c, int64_t n, float *pro
 int jl_model_grads(jl_model *md, const float *c, const float *target, int32_t n, float *loss_host, float *grads_host,
                    void *stream)
 {
-    if (!md || !c || !target || n < 1)
-        return fail(JL_EINVAL, "invalid arguments");
+    if (!md || !c || !target || n < 1 || n > 65536)
+        return fail(JL_EINVAL, "invalid arguments (1 <= n <= 65536)");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_work(md, n, true);
+    if (rc == JL_OK)
+        rc = pad_targets(md, target, n, st);
     if (rc != JL_OK)
         return rc;
-    cudaError_t e = train_rows(md, c, nullptr, n, target, nullptr, 1.f / (float)n, st);
+    cudaError_t e = train_rows(md, c, nullptr, n, md->tpad, nullptr, 1.f / (float)n, st);
     if (e == cudaSuccess) {
         e = launch_pdl(grad_reduce_kernel, dim3((kNumParams + 255) / 256), dim3(256), 0, st, grad_parts(md), md->grads,
                        md->loss);
@@ -2559,15 +2407,18 @@ int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const i
         return fail(JL_EINVAL, "invalid arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = ensure_work(md, batch, true);
+    if (rc == JL_OK)
+        rc = pad_targets(md, hist, n, st);
     if (rc != JL_OK)
         return rc;
     const int steps = n / batch;  // the last partial batch of an epoch is dropped
     const int nparam_blocks = (kNumParams + 255) / 256;
+    // batch losses of every step, read back once at the end (no per-epoch drain)
+    const size_t nsteps = (size_t)epochs * steps;
     float *loss_steps = nullptr;
-    cudaError_t e = cudaMalloc(&loss_steps, (size_t)steps * 4);
+    cudaError_t e = cudaMalloc(&loss_steps, nsteps * 4);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaMalloc(loss per step)");
-    std::vector<float> hl((size_t)steps);
     const double total = (double)epochs * steps;
     // Adam's step count: read once, advanced on the host, written back at the end
     int32_t step0 = 0;
@@ -2581,18 +2432,32 @@ int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const i
     int32_t done = 0;  // steps launched
     for (int ep = 0; ep < epochs && rc == JL_OK; ++ep) {
         for (int s = 0; s < steps; ++s) {
-            const int32_t *idx = order ? order + (size_t)ep * n + (size_t)s * batch : nullptr;
-            const float *cb = order ? c : c + 2 * (size_t)s * batch;
-            // targets: row idx[m] of hist for batch row m (gathered by the softmax product)
-            const float *tb = idx ? hist : hist + (size_t)s * batch * kBins;
-            e = train_rows(md, cb, idx, batch, tb, idx, 1.f / (float)batch, st);
+            // batch (ep, s): C of batch row m and its target row idx[m] (of the
+            // padded copy of hist, gathered by the training-step kernel), or
+            // rows s * batch + m
+            auto batch_of = [&](int bep, int bs, const int32_t *&bidx, const float *&bc, const float *&bt) {
+                bidx = order ? order + (size_t)bep * n + (size_t)bs * batch : nullptr;
+                bc = order ? c : c + 2 * (size_t)bs * batch;
+                bt = order ? md->tpad : md->tpad + (size_t)bs * batch * kTrTP;
+            };
+            const int32_t *idx, *nidx = nullptr;
+            const float *cb, *tb, *ncb = nullptr, *ntb = nullptr;
+            batch_of(ep, s, idx, cb, tb);
+            const bool last = ep == epochs - 1 && s == steps - 1;
+            if (!last)
+                batch_of(s + 1 < steps ? ep : ep + 1, s + 1 < steps ? s + 1 : 0, nidx, ncb, ntb);
+            e = train_rows(md, cb, idx, batch, tb, idx, 1.f / (float)batch, st, ncb, nidx, last ? 0 : batch, ntb,
+                           nidx);
             if (e == cudaSuccess) {
                 // cosine schedule from lr to lr_final over the steps of this call
                 const double t = ((double)ep * steps + s) / total;
                 const float lr_t = (float)(lr_final + 0.5 * (lr - lr_final) * (1.0 + cos(3.141592653589793 * t)));
                 const int step_t = step0 + ep * steps + s + 1;
+                const float b1 = 0.9f, b2 = 0.999f;
+                // the bias corrections in binary32, as 1 - powf(beta, t)
+                const float bc1 = 1.f - powf(b1, (float)step_t), bc2 = 1.f - powf(b2, (float)step_t);
                 e = launch_pdl(adam_kernel, dim3(nparam_blocks), dim3(256), 0, st, grad_parts(md), md->params, md->m,
-                               md->v, md->wpack, step_t, lr_t, 0.9f, 0.999f, 1e-8f, loss_steps + s);
+                               md->v, md->wpack, bc1, bc2, lr_t, b1, b2, 1e-8f, loss_steps + (size_t)ep * steps + s);
                 if (e == cudaSuccess)
                     ++done;
             }
@@ -2601,26 +2466,26 @@ int jl_train(jl_model *md, const float *c, const float *hist, int32_t n, const i
                 break;
             }
         }
-        if (rc == JL_OK && loss_curve) {
-            e = cudaMemcpyAsync(hl.data(), loss_steps, (size_t)steps * 4, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess)
-                e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) {
-                rc = cuda_fail(e, "loss readback");
-                break;
-            }
-            double acc = 0.0;
-            for (int s = 0; s < steps; ++s)
-                acc += hl[(size_t)s] / (double)batch;
-            loss_curve[ep] = (float)(acc / steps);
-        }
     }
     const int32_t step_end = step0 + done;
     cudaError_t e2 = cudaMemcpyAsync(md->step, &step_end, 4, cudaMemcpyHostToDevice, st);
+    std::vector<float> hl;
+    if (rc == JL_OK && loss_curve && e2 == cudaSuccess) {
+        hl.resize(nsteps);
+        e2 = cudaMemcpyAsync(hl.data(), loss_steps, nsteps * 4, cudaMemcpyDeviceToHost, st);
+    }
     cudaError_t e3 = cudaStreamSynchronize(st);
     if (e2 == cudaSuccess)
         e2 = e3;
     cudaFree(loss_steps);
+    if (rc == JL_OK && e2 == cudaSuccess && loss_curve) {
+        for (int ep = 0; ep < epochs; ++ep) {
+            double acc = 0.0;
+            for (int s = 0; s < steps; ++s)
+                acc += hl[(size_t)ep * steps + s] / (double)batch;
+            loss_curve[ep] = (float)(acc / steps);
+        }
+    }
     if (rc == JL_OK && e2 != cudaSuccess)
         rc = cuda_fail(e2, "training");
     if (rc != JL_OK)

@@ -155,15 +155,25 @@ class Surrogate:
                                        S.data_ptr() if score else None, st))
         return P, S
 
-    def train(self, c, hist, epochs, batch=1024, lr=1e-3, lr_final=None, order_seed=0, loss_curve=True):
+    @staticmethod
+    def epoch_order(n, epochs, order_seed=0):
+        """The sample order train() uses: one seeded permutation of n samples
+        per epoch (host int32 array, epochs * n)."""
+        rng = np.random.default_rng(order_seed)
+        return np.concatenate([rng.permutation(n).astype(np.int32) for _ in range(epochs)])
+
+    def train(self, c, hist, epochs, batch=1024, lr=1e-3, lr_final=None, order_seed=0, loss_curve=True, order=None):
         """Adam training with a cosine learning-rate schedule from lr to
         lr_final (default: constant lr); one seeded permutation of the
-        samples per epoch (drawn here on the host and passed to the library)."""
+        samples per epoch (epoch_order, drawn on the host), or `order`: those
+        permutations already on the device (int32, epochs * n)."""
         import torch
         n = c.shape[0]
-        rng = np.random.default_rng(order_seed)
-        order = np.concatenate([rng.permutation(n).astype(np.int32) for _ in range(epochs)])
-        od = torch.from_numpy(order).to(c.device)
+        if order is None:
+            od = torch.from_numpy(self.epoch_order(n, epochs, order_seed)).to(c.device)
+        else:
+            od = order
+            assert od.dtype == torch.int32 and od.numel() == epochs * n and od.device == c.device
         curve = np.zeros(epochs, np.float32)
         st = torch.cuda.current_stream().cuda_stream
         check(self._L.jl_train(self._h, c.data_ptr(), hist.data_ptr(), n, od.data_ptr(), int(epochs), int(batch),
