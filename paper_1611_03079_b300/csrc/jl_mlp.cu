@@ -1072,11 +1072,13 @@ __global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restri
 //   P6  dW2^T = H1^T dZ2 (two halves of the input units)
 //   P7  D = dZ2 W2          -> dZ1 = D * [H1 > 0] over H1, db1
 //   P8  dW1^T = Phi^T dZ1   (M = 128 over Phi's 64 columns: lanes 64.. unused)
-// Three CTAs share a tile (blockIdx.y = role): each runs P1..P3 for the
-// tile's rows, then role 0 takes the chain P5, P7, P8 (dZ2, dZ1, dW1, db1),
-// role 1 the loss, db3, P4 (dW3) and, after its own P5, dW2 for input units
-// 0..127, role 2 db2 and dW2 for units 128..255 -- so the long
-// partial-gradient stores and the sums run beside the chain instead of on it.
+// Four CTAs share a tile (blockIdx.y = role): each runs P1..P3 for the
+// tile's rows, then roles 0 and 2 take the chain P5, P7, P8 for hidden units
+// 0..127 and 128..255 (each streams those rows of the W2^T chunks, and forms
+// its half of dZ1, db1 and dW1), role 1 the loss, db3, P4 (dW3) and, after
+// its own P5, dW2 for input units 0..127, role 3 db2 and dW2 for units
+// 128..255 -- so the long partial-gradient stores and the sums run beside
+// the chain instead of on it, and the chain itself is halved.
 // Bias gradients are column sums of the unrounded binary32 errors in a fixed
 // order (a butterfly within each warp, then the four row groups in order).
 // Every wait is bounded; one that gives up sets *status to JL_ETIMEOUT.
@@ -1170,9 +1172,11 @@ __device__ __forceinline__ float tr_colsum32(float (&v)[32], int lane)
 }
 
 // One product's weight stream: chunks j0 .. j0 + n - 1 of the packed
-// images, K-chunks of kw (32 or 64), N rows, through ns ring slots.
+// images, K-chunks of kw (32 or 64), N rows, through ns ring slots; with
+// blen > 0, bytes [boff, boff + blen) of each chunk only (a block of its rows).
 struct TrStream {
     int j0, n, kw, N, ns;
+    int boff = 0, blen = 0;
 };
 
 __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_constant__ TrainArgs a)
@@ -1276,57 +1280,79 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
                    aDZ = tc::smem_u32(sDZ);
     auto slot_addr = [&](int s) -> uint8_t * { return s < 3 ? sm + kTrRing + s * kImgW : sDZ + (s - 3) * kImgW; };
 
-    // loader: chunk c of stream w into its slot, once the slot's previous
-    // products have completed
-    auto load = [&](const TrStream &w, int c) {
-        const int s = c % w.ns;
+    // a wait whose phase has usually completed already: one probe, then the
+    // bounded loop
+    auto wait_phase = [&](uint64_t *bar, uint32_t parity) {
+        if (!tc::mbar_try_wait(bar, parity) && !tc::mbar_wait(bar, parity, kWaitLimit))
+            ok = false;
+    };
+    // loader: chunk c of stream w into slot s (= c mod w.ns), once the slot's
+    // previous products have completed
+    auto load = [&](const TrStream &w, int c, int s) {
         const uint32_t bit = 1u << s;
-        if (lused & bit) {
-            if (!tc::mbar_wait(&empty[s], ((lpar >> s) & 1u) ^ 1u, kWaitLimit))
-                ok = false;
-        }
+        if (lused & bit)
+            wait_phase(&empty[s], ((lpar >> s) & 1u) ^ 1u);
         uint32_t bytes;
-        const size_t off = chunk_offset(w.j0 + c, bytes);
+        size_t off = chunk_offset(w.j0 + c, bytes);
+        if (w.blen > 0) {
+            off += (size_t)w.boff;
+            bytes = (uint32_t)w.blen;
+        }
         tc::bulk_load(slot_addr(s), a.pack + off, bytes, &full[s]);
         lpar ^= bit;
         lused |= bit;
     };
     // the first chunks of w (their slots are free: every earlier product has completed)
+    // (the other lanes of a warp whose lane 0 has a single-thread role wait
+    // at __syncwarp rather than spin beside it, and the warp is converged
+    // again before its next warp-wide tensor-memory access)
     auto prefetch = [&](const TrStream &w) {
         if (threadIdx.x == 32)
             for (int c = 0; c < min(w.n, w.ns); ++c)
-                load(w, c);
+                load(w, c, c);
+        __syncwarp();
     };
     // D[dcol] = A x W^T over stream w: A the K-major activation buffer at
     // a_addr (aG column groups).  The MMA issuer consumes the chunks as they
     // land; the loader refills the slots they free.
+    // (The issue loop is kept short: a descriptor's start-address field,
+    // bits 0..13 = address / 16, is advanced by adding offsets / 16 to a
+    // descriptor built once -- no carry, shared memory being below 256 KB --
+    // and the slot index is a running counter.)
     auto run = [&](const TrStream &w, uint32_t a_addr, int aG, uint32_t dcol) {
         if (threadIdx.x == 0) {
             const uint32_t idesc = tc::idesc_bf16(kBM, (uint32_t)w.N);
             const int G = w.kw / 8;
+            const uint64_t ad0 = tc::smem_desc(a_addr, 128, (uint32_t)aG * 128);
+            const uint64_t bring = tc::smem_desc(tc::smem_u32(sm + kTrRing), 128, (uint32_t)G * 128);
+            const uint64_t bdz = tc::smem_desc(tc::smem_u32(sDZ), 128, (uint32_t)G * 128);
+            const uint32_t d = taddr + dcol;
+            int s = 0;
             for (int c = 0; c < w.n; ++c) {
-                const int s = c % w.ns;
-                if (!tc::mbar_wait(&full[s], (fpar >> s) & 1u, kWaitLimit))
-                    ok = false;
+                wait_phase(&full[s], (fpar >> s) & 1u);
                 fpar ^= 1u << s;
                 tc::tc_fence_after();
-                const uint32_t b0 = tc::smem_u32(slot_addr(s));
-                for (int kk = 0; kk < w.kw / 16; ++kk) {
-                    const uint64_t ad = tc::smem_desc(a_addr + (uint32_t)((c * G + 2 * kk) << 7), 128, (uint32_t)aG * 128);
-                    const uint64_t bd = tc::smem_desc(b0 + (uint32_t)(kk * 256), 128, (uint32_t)G * 128);
-                    tc::mma_bf16(taddr + dcol, ad, bd, idesc, (c | kk) != 0);
-                }
+                const uint64_t b0 = s < 3 ? bring + (uint64_t)(s * (kImgW >> 4)) : bdz + (uint64_t)((s - 3) * (kImgW >> 4));
+                const uint64_t a0 = ad0 + (uint64_t)(c * G * 8);  // K columns 8 G c .. : (c G 128 bytes) / 16
+                for (int kk = 0; kk < w.kw / 16; ++kk)
+                    tc::mma_bf16(d, a0 + (uint64_t)(16 * kk), b0 + (uint64_t)(16 * kk), idesc, (c | kk) != 0);
                 tc::mma_commit(&empty[s]);
+                s = s + 1 == w.ns ? 0 : s + 1;
             }
         } else if (threadIdx.x == 32) {
-            for (int c = w.ns; c < w.n; ++c)
-                load(w, c);
+            int s = 0;  // chunk w.ns goes to slot 0
+            for (int c = w.ns; c < w.n; ++c) {
+                load(w, c, s);
+                s = s + 1 == w.ns ? 0 : s + 1;
+            }
         }
+        __syncwarp();
     };
     // every product issued so far has completed
     auto commit_wait = [&]() {
         if (threadIdx.x == 0)
             tc::mma_commit(accbar);
+        __syncwarp();
         if (!tc::mbar_wait(accbar, accn & 1, kWaitLimit))
             ok = false;
         ++accn;
@@ -1362,21 +1388,23 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
         return is_max ? fmaxf(fmaxf(p0, p1), fmaxf(p2, p3)) : (p0 + p1) + (p2 + p3);
     };
     // one thread issues a weight-gradient product D[dcol] = X^T Y over the
-    // tile's 128 rows: X (M side, column offset xm0) and Y (N side) are
-    // full-width buffers read MN-major
-    auto issue_wgrad = [&](uint32_t x_addr, int xG, int xm0, uint32_t y_addr, int yG, int N, uint32_t dcol) {
+    // tile's 128 rows: X (M side, columns xm0 ..) and Y (N side, columns
+    // yn0 ..) are full-width buffers read MN-major
+    auto issue_wgrad = [&](uint32_t x_addr, int xG, int xm0, uint32_t y_addr, int yG, int N, uint32_t dcol,
+                           int yn0 = 0) {
         const uint32_t idesc = tc::idesc_bf16_t(kBM, (uint32_t)N, true, true);
 #pragma unroll
         for (int kk = 0; kk < kBM / 16; ++kk) {
             const uint64_t ad = tc::smem_desc(x_addr + (uint32_t)(kk * 2 * xG * 128 + (xm0 / 8) * 128),
                                               (uint32_t)xG * 128, 128);
-            const uint64_t bd = tc::smem_desc(y_addr + (uint32_t)(kk * 2 * yG * 128), (uint32_t)yG * 128, 128);
+            const uint64_t bd = tc::smem_desc(y_addr + (uint32_t)(kk * 2 * yG * 128 + (yn0 / 8) * 128),
+                                              (uint32_t)yG * 128, 128);
             tc::mma_bf16(taddr + dcol, ad, bd, idesc, kk != 0);
         }
     };
 
     const TrStream w1{0, 2, 32, kHid, 5}, w2{2, 8, 32, kHid, 5}, w3{10, 4, 64, kBinsPad, 5};
-    const TrStream w3t{14, 4, 32, kHid, 3}, w2t{18, 8, 32, kHid, 5};
+    const TrStream w3t{14, 4, 32, kHid, 3};
     float *ws1 = a.ws1 + (size_t)tile * kHid * kIn;
     float *ws2 = a.ws2 + (size_t)tile * kHid * kHid;
     float *ws3 = a.ws3 + (size_t)tile * kBins * kHid;
@@ -1416,12 +1444,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
     // activation in buf is > 0 (bf16 sign clear, not +0), written over the
     // activation as bf16; bias-gradient sums of the unrounded values to pb
     // (unless NULL)
-    auto mask_epilogue = [&](uint8_t *buf, float *pb) {
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            const int c0 = 64 * qd + 32 * h;
+    // (32 columns: accumulator column tcol, buffer column c0)
+    auto mask_cols = [&](uint8_t *buf, float *pb, int tcol, int c0) {
+        {
             float v[32];
-            tc::tmem_ld32(tw + (uint32_t)c0, v);
+            tc::tmem_ld32(tw + (uint32_t)tcol, v);
 #pragma unroll
             for (int g8 = 0; g8 < 4; ++g8) {
                 const uint4 mq = *reinterpret_cast<const uint4 *>(buf + tr_off(r, c0 + 8 * g8, kHid / 8));
@@ -1438,6 +1465,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
             if (pb)
                 colsums32(v, c0, kHid, pb);
         }
+    };
+    auto mask_epilogue = [&](uint8_t *buf, float *pb) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h)
+            mask_cols(buf, pb, 64 * qd + 32 * h, 64 * qd + 32 * h);
     };
     // transposed weight-gradient accumulator (lane = input unit u, column =
     // output unit o) to out[o * ld + u] for columns [c0, c0 + 16) below ncols:
@@ -1547,30 +1579,33 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
     }
     epilogue_done();
 
-    if (role == 0) {
-        // ---------- P5 D = dZ W3 -> dZ2 (over H2), db2; P7 -> dZ1 (over H1), db1; P8 dW1^T = Phi^T dZ1 ----------
+    if (role == 0 || role == 2) {
+        // ---------- the chain for hidden units 128 h .. 128 h + 127 (h = role / 2):
+        // P5 -> dZ2 (all columns); P7 on those units (rows 128 h.. of every
+        // W2^T chunk) -> dZ1 over H1, db1; P8 dW1^T = Phi^T dZ1 for those units ----------
+        const int half = role >> 1;
+        const TrStream w2h{18, 8, 32, kBM, 5, half * (kImgW / 2), kImgW / 2};
         run(w3t, aDZ, kTrDZCols / 8, 0);
         commit_wait();
-        prefetch(w2t);
+        prefetch(w2h);
         mask_epilogue(sH2, nullptr);
         epilogue_done();
-        run(w2t, aH2, kHid / 8, 0);
+        run(w2h, aH2, kHid / 8, 0);
         commit_wait();
-        mask_epilogue(sH1, a.pb1 + (size_t)tile * 256);
+        mask_cols(sH1, a.pb1 + (size_t)tile * 256, 32 * qd, kBM * half + 32 * qd);
         epilogue_done();
         if (threadIdx.x == 0) {
             tc::tc_fence_after();
-            issue_wgrad(aPhi, kIn / 8, 0, aH1, kHid / 8, kHid, 0);
+            issue_wgrad(aPhi, kIn / 8, 0, aH1, kHid / 8, kBM, 0, kBM * half);
         }
         commit_wait();
         if ((warp & 3) < 2) {
-            // lanes 0..63 hold the 64 input features
-#pragma unroll 1
-            for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 32)
-                store_wgrad32(0, c0, kHid, ws1, kIn, r);
+            // lanes 0..63 hold the 64 input features; columns: the 128 units
+            store_wgrad32(0, 32 * qd, kBM, ws1 + (size_t)kBM * half * kIn, kIn, r);
         }
     } else {
-        // ---------- (role 1: P4 dW3^T = H2^T dZ at columns 256, 384) P5 -> dZ2; P6 dW2^T = H1^T dZ2 ----------
+        // ---------- (role 1: P4 dW3^T = H2^T dZ at columns 256, 384) P5 -> dZ2;
+        // P6 dW2^T = H1^T dZ2 for input units 0..127 (role 1) or 128..255 (role 3) ----------
         if (role == 1 && threadIdx.x == 0) {
             tc::tc_fence_after();
             issue_wgrad(aH2, kHid / 8, 0, aDZ, kTrDZCols / 8, kBinsPad, 256);
@@ -1587,10 +1622,9 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
             for (int hh = 0; hh < 2; ++hh)
                 store_wgrad32((uint32_t)(256 + hh * 128), 32 * qd, kBins, ws3, kHid, hh * kBM + r);
         }
-        mask_epilogue(sH2, role == 2 ? a.pb2 + (size_t)tile * 256 : nullptr);
+        mask_epilogue(sH2, role == 3 ? a.pb2 + (size_t)tile * 256 : nullptr);
         epilogue_done();
-        // input units 128 (role - 1) .. + 127 of dW2
-        const int u0 = (role - 1) * kBM;
+        const int u0 = role == 1 ? 0 : kBM;
         if (threadIdx.x == 0) {
             tc::tc_fence_after();
             issue_wgrad(aH1, kHid / 8, u0, aH2, kHid / 8, kHid, 0);
@@ -1599,10 +1633,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
 #pragma unroll 1
         for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 32)
             store_wgrad32(0, c0, kHid, ws2, kHid, u0 + r);
-        // role 2 (the shortest share): the next step's C values and target
+        // role 3 (the shortest share): the next step's C values and target
         // rows of this tile's rows into L2, so that its input phase, which
         // starts when Adam's blocks leave the SM, reads them from there
-        if (role == 2 && threadIdx.x < kBM && m0 + (int)threadIdx.x < a.next_n) {
+        if (role == 3 && threadIdx.x < kBM && m0 + (int)threadIdx.x < a.next_n) {
             const int grow = m0 + threadIdx.x;
             const int64_t src = a.next_idx ? (int64_t)a.next_idx[grow] : (int64_t)grow;
             const int64_t trw = a.next_trow ? (int64_t)a.next_trow[grow] : (int64_t)grow;
@@ -2167,7 +2201,7 @@ static cudaError_t train_rows(jl_model *md, const float *c, const int32_t *idx, 
     a.next_n = next_n;
     a.next_target = next_target;
     a.next_trow = next_trow;
-    return launch_pdl(train_step_kernel, dim3((unsigned)tiles, 3), dim3(kTrThreads), (size_t)kTrSmem, st, a);
+    return launch_pdl(train_step_kernel, dim3((unsigned)tiles, 4), dim3(kTrThreads), (size_t)kTrSmem, st, a);
 }
 
 // The targets of a call (n rows of 101) as padded rows in md->tpad.
