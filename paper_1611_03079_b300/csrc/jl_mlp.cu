@@ -1072,18 +1072,19 @@ __global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restri
 //   P6  dW2^T = H1^T dZ2 (two halves of the input units)
 //   P7  D = dZ2 W2          -> dZ1 = D * [H1 > 0] over H1, db1
 //   P8  dW1^T = Phi^T dZ1   (M = 128 over Phi's 64 columns: lanes 64.. unused)
-// Four CTAs share a tile (blockIdx.y = role): each runs P1..P3 for the
+// Five CTAs share a tile (blockIdx.y = role): each runs P1..P3 for the
 // tile's rows, then roles 0 and 2 take the chain P5, P7, P8 for hidden units
 // 0..127 and 128..255 (each streams those rows of the W2^T chunks, and forms
-// its half of dZ1, db1 and dW1), role 1 the loss, db3, P4 (dW3) and, after
-// its own P5, dW2 for input units 0..127, role 3 db2 and dW2 for units
-// 128..255 -- so the long partial-gradient stores and the sums run beside
-// the chain instead of on it, and the chain itself is halved.
+// its half of dZ1, db1 and dW1), roles 1 and 3 their own P5 and dW2 for input
+// units 0..127 (with db2) and 128..255, role 4 the loss, db3 and P4 (dW3) --
+// so the long partial-gradient stores and the sums run beside the chain
+// instead of on it, and the chain itself is halved.
 // Bias gradients are column sums of the unrounded binary32 errors in a fixed
 // order (a butterfly within each warp, then the four row groups in order).
 // Every wait is bounded; one that gives up sets *status to JL_ETIMEOUT.
 // ---------------------------------------------------------------------------
 static constexpr int kTrThreads = 512;
+static constexpr int kTrRoles = 5;  // CTAs per 128-row tile
 static constexpr int kTrPhi = 0;
 static constexpr int kTrH1 = kTrPhi + kBM * kIn * 2;
 static constexpr int kTrH2 = kTrH1 + kBM * kHid * 2;
@@ -1498,7 +1499,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
     // ---------------- P3: logits, softmax, cross-entropy error ----------------
     run(w3, aH2, kHid / 8, 0);
     commit_wait();
-    prefetch(w3t);
+    if (role != 4)
+        prefetch(w3t);
     {
         constexpr float kLog2e = 1.4426950408889634f;
         float z[32];
@@ -1564,7 +1566,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
                 v[j] = z[16 * h + j];
             tr_store16(sDZ, r, 32 * qd + 16 * h, kTrDZCols / 8, v, false);
         }
-        if (role == 1) {
+        if (role == 4) {
             const float sw = warp_sum(ce);
             if (lane == 0)
                 lw[warp] = sw;
@@ -1603,26 +1605,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
             // lanes 0..63 hold the 64 input features; columns: the 128 units
             store_wgrad32(0, 32 * qd, kBM, ws1 + (size_t)kBM * half * kIn, kIn, r);
         }
-    } else {
-        // ---------- (role 1: P4 dW3^T = H2^T dZ at columns 256, 384) P5 -> dZ2;
-        // P6 dW2^T = H1^T dZ2 for input units 0..127 (role 1) or 128..255 (role 3) ----------
-        if (role == 1 && threadIdx.x == 0) {
-            tc::tc_fence_after();
-            issue_wgrad(aH2, kHid / 8, 0, aDZ, kTrDZCols / 8, kBinsPad, 256);
-            issue_wgrad(aH2, kHid / 8, kBM, aDZ, kTrDZCols / 8, kBinsPad, 384);
-        }
+    } else if (role == 1 || role == 3) {
+        // ---------- P5 -> dZ2 (db2: role 1); P6 dW2^T = H1^T dZ2 for input
+        // units 0..127 (role 1) or 128..255 (role 3) ----------
         run(w3t, aDZ, kTrDZCols / 8, 0);
         commit_wait();
-        if (role == 1) {
-            // dW3[b][u]: lanes over the hidden unit u, quarters over the bins
-            // (quarter 3 reads columns 96..127 of an accumulator 112 wide: the
-            // last 16 lie in the next accumulator or unused columns, and are
-            // not stored)
-#pragma unroll 1
-            for (int hh = 0; hh < 2; ++hh)
-                store_wgrad32((uint32_t)(256 + hh * 128), 32 * qd, kBins, ws3, kHid, hh * kBM + r);
-        }
-        mask_epilogue(sH2, role == 3 ? a.pb2 + (size_t)tile * 256 : nullptr);
+        mask_epilogue(sH2, role == 1 ? a.pb2 + (size_t)tile * 256 : nullptr);
         epilogue_done();
         const int u0 = role == 1 ? 0 : kBM;
         if (threadIdx.x == 0) {
@@ -1633,10 +1621,25 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
 #pragma unroll 1
         for (int c0 = 64 * qd; c0 < 64 * qd + 64; c0 += 32)
             store_wgrad32(0, c0, kHid, ws2, kHid, u0 + r);
-        // role 3 (the shortest share): the next step's C values and target
-        // rows of this tile's rows into L2, so that its input phase, which
-        // starts when Adam's blocks leave the SM, reads them from there
-        if (role == 3 && threadIdx.x < kBM && m0 + (int)threadIdx.x < a.next_n) {
+    } else {
+        // ---------- role 4: P4 dW3^T = H2^T dZ (input units in two halves, columns 256 and 384) ----------
+        if (threadIdx.x == 0) {
+            tc::tc_fence_after();
+            issue_wgrad(aH2, kHid / 8, 0, aDZ, kTrDZCols / 8, kBinsPad, 256);
+            issue_wgrad(aH2, kHid / 8, kBM, aDZ, kTrDZCols / 8, kBinsPad, 384);
+        }
+        commit_wait();
+        // dW3[b][u]: lanes over the hidden unit u, quarters over the bins
+        // (quarter 3 reads columns 96..127 of an accumulator 112 wide: the
+        // last 16 lie in the next accumulator or unused columns, and are not
+        // stored)
+#pragma unroll 1
+        for (int hh = 0; hh < 2; ++hh)
+            store_wgrad32((uint32_t)(256 + hh * 128), 32 * qd, kBins, ws3, kHid, hh * kBM + r);
+        // (the shortest share) the next step's C values and target rows of
+        // this tile's rows into L2, so that its input phase, which starts
+        // when Adam's blocks leave the SM, reads them from there
+        if (threadIdx.x < kBM && m0 + (int)threadIdx.x < a.next_n) {
             const int grow = m0 + threadIdx.x;
             const int64_t src = a.next_idx ? (int64_t)a.next_idx[grow] : (int64_t)grow;
             const int64_t trw = a.next_trow ? (int64_t)a.next_trow[grow] : (int64_t)grow;
@@ -2201,7 +2204,7 @@ static cudaError_t train_rows(jl_model *md, const float *c, const int32_t *idx, 
     a.next_n = next_n;
     a.next_target = next_target;
     a.next_trow = next_trow;
-    return launch_pdl(train_step_kernel, dim3((unsigned)tiles, 4), dim3(kTrThreads), (size_t)kTrSmem, st, a);
+    return launch_pdl(train_step_kernel, dim3((unsigned)tiles, kTrRoles), dim3(kTrThreads), (size_t)kTrSmem, st, a);
 }
 
 // The targets of a call (n rows of 101) as padded rows in md->tpad.
