@@ -1024,19 +1024,30 @@ __global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restri
                             float *__restrict__ v, uint8_t *__restrict__ pack, float bc1, float bc2, float lr,
                             float beta1, float beta2, float eps, float *loss)
 {
-    tc::griddep_wait();
+    // The next training step may be scheduled at once (its blocks take SMs
+    // as this step's blocks leave them, and read nothing this kernel writes
+    // before their own wait); the moments and parameters were final before
+    // the training step this kernel follows began, so they are read before
+    // waiting for it.
     tc::griddep_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float m0 = 0.f, v0 = 0.f, p0 = 0.f;
+    if (i < kNumParams) {
+        m0 = m[i];
+        v0 = v[i];
+        p0 = p[i];
+    }
+    tc::griddep_wait();
     if (i == 0 && loss)
         *loss = loss_of(q);
     if (i < kNumParams) {
         const float g = grad_of(q, i);
-        const float mi = beta1 * m[i] + (1.f - beta1) * g;
-        const float vi = beta2 * v[i] + (1.f - beta2) * g * g;
+        const float mi = beta1 * m0 + (1.f - beta1) * g;
+        const float vi = beta2 * v0 + (1.f - beta2) * g * g;
         m[i] = mi;
         v[i] = vi;
         const float upd = lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-        const float w = p[i] - upd;
+        const float w = p0 - upd;
         p[i] = w;
         pack_param(pack, i, w);
     }
@@ -1076,7 +1087,8 @@ __global__ void adam_kernel(const __grid_constant__ GradParts q, float *__restri
 // tile's rows, then roles 0 and 2 take the chain P5, P7, P8 for hidden units
 // 0..127 and 128..255 (each streams those rows of the W2^T chunks, and forms
 // its half of dZ1, db1 and dW1), roles 1 and 3 their own P5 and dW2 for input
-// units 0..127 (with db2) and 128..255, role 4 the loss, db3 and P4 (dW3) --
+// units 0..127 and 128..255 (each with those units' db2), role 4 the loss,
+// db3 and P4 (dW3) --
 // so the long partial-gradient stores and the sums run beside the chain
 // instead of on it, and the chain itself is halved.
 // Bias gradients are column sums of the unrounded binary32 errors in a fixed
@@ -1370,12 +1382,14 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
     // column sums of the tile for columns c0 .. c0 + 31 (this thread: row r,
     // v[j] = column c0 + j; the four quarters hold disjoint column ranges) to
     // out[c0 + j] for c0 + j < nvalid
-    auto colsums32 = [&](float (&v)[32], int c0, int nvalid, float *out) {
-        const float s = tr_colsum32(v, lane);
+    // (active false, uniform over the quarter: no sums for these columns;
+    // the barriers are still taken)
+    auto colsums32 = [&](float (&v)[32], int c0, int nvalid, float *out, bool active = true) {
+        const float s = active ? tr_colsum32(v, lane) : 0.f;
         __syncthreads();
         scratch[(warp & 3) * kBM + qd * 32 + lane] = s;
         __syncthreads();
-        if ((warp & 3) == 0 && c0 + lane < nvalid) {
+        if (active && (warp & 3) == 0 && c0 + lane < nvalid) {
             const int cc = qd * 32 + lane;
             out[c0 + lane] = (scratch[cc] + scratch[kBM + cc]) + (scratch[2 * kBM + cc] + scratch[3 * kBM + cc]);
         }
@@ -1446,7 +1460,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
     // activation as bf16; bias-gradient sums of the unrounded values to pb
     // (unless NULL)
     // (32 columns: accumulator column tcol, buffer column c0)
-    auto mask_cols = [&](uint8_t *buf, float *pb, int tcol, int c0) {
+    auto mask_cols = [&](uint8_t *buf, float *pb, int tcol, int c0, int sum_lo = 0, int sum_hi = kHid) {
         {
             float v[32];
             tc::tmem_ld32(tw + (uint32_t)tcol, v);
@@ -1464,13 +1478,13 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
             tr_store16(buf, r, c0, kHid / 8, *reinterpret_cast<const float(*)[16]>(v), false);
             tr_store16(buf, r, c0 + 16, kHid / 8, *reinterpret_cast<const float(*)[16]>(v + 16), false);
             if (pb)
-                colsums32(v, c0, kHid, pb);
+                colsums32(v, c0, kHid, pb, c0 >= sum_lo && c0 < sum_hi);
         }
     };
-    auto mask_epilogue = [&](uint8_t *buf, float *pb) {
+    auto mask_epilogue = [&](uint8_t *buf, float *pb, int sum_lo = 0, int sum_hi = kHid) {
 #pragma unroll 1
         for (int h = 0; h < 2; ++h)
-            mask_cols(buf, pb, 64 * qd + 32 * h, 64 * qd + 32 * h);
+            mask_cols(buf, pb, 64 * qd + 32 * h, 64 * qd + 32 * h, sum_lo, sum_hi);
     };
     // transposed weight-gradient accumulator (lane = input unit u, column =
     // output unit o) to out[o * ld + u] for columns [c0, c0 + 16) below ncols:
@@ -1546,16 +1560,20 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
         }
         const float sum = row_combine(sq, false);
         const float inv = __frcp_rn(sum);  // 1 / sum, correctly rounded
-        const float lsum = logf(sum);
+        // cross-entropy terms -t (z - max - log sum) for the loss (role 4 only)
         float ce = 0.f;
+        if (role == 4) {
+            const float lsum = logf(sum);
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (32 * qd + j < kBins && in)
+                    ce -= tg[j] * (z[j] - lsum);
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
             float d = 0.f;
-            if (32 * qd + j < kBins && in) {
-                const float p = ez[j] * inv;
-                ce -= tg[j] * (z[j] - lsum);
-                d = (p - tg[j]) * a.inv_m;
-            }
+            if (32 * qd + j < kBins && in)
+                d = (ez[j] * inv - tg[j]) * a.inv_m;
             z[j] = d;
         }
 #pragma unroll
@@ -1606,11 +1624,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_step_kernel(const __grid_
             store_wgrad32(0, 32 * qd, kBM, ws1 + (size_t)kBM * half * kIn, kIn, r);
         }
     } else if (role == 1 || role == 3) {
-        // ---------- P5 -> dZ2 (db2: role 1); P6 dW2^T = H1^T dZ2 for input
-        // units 0..127 (role 1) or 128..255 (role 3) ----------
+        // ---------- P5 -> dZ2 and db2 for units 0..127 (role 1) or 128..255
+        // (role 3); P6 dW2^T = H1^T dZ2 for input units 0..127 (role 1) or
+        // 128..255 (role 3) ----------
         run(w3t, aDZ, kTrDZCols / 8, 0);
         commit_wait();
-        mask_epilogue(sH2, role == 1 ? a.pb2 + (size_t)tile * 256 : nullptr);
+        mask_epilogue(sH2, a.pb2 + (size_t)tile * 256, role == 1 ? 0 : kBM, role == 1 ? kBM : kHid);
         epilogue_done();
         const int u0 = role == 1 ? 0 : kBM;
         if (threadIdx.x == 0) {
