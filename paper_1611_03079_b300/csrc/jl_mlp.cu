@@ -470,6 +470,7 @@ static constexpr int kImgW = 256 * kChK * 2;                 // 16 KB: 256 rows 
 static constexpr int kImgW3 = kBinsPad * 64 * 2;             // 14 KB: 112 rows x 64 k
 static constexpr int kChunksPerTile = 2 + 8 + 4;             // W1, W2, W3 (the forward's chunks)
 static constexpr int kRing = 4;                              // weight slots (16 KB)
+static_assert((kRing & (kRing - 1)) == 0, "the ring size is a power of two");
 // Packed images: chunks 0..13 as above, then for the training step's
 // backward W3^T (14..17: 256 rows x 32 bins, zero past bin 101) and W2^T
 // (18..25: 256 rows x 32 k).
@@ -651,22 +652,26 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fused_forward_kernel(const _
             // release the slot to the loader when they complete
             // ksteps: K steps of 16 in the chunk (2 for W1/W2, 4 for W3);
             // b_sbo: the chunk image's 8-row group stride (128 * K groups)
+            // (descriptors are built once per call and advanced by adding
+            // offsets / 16 to their start-address field; the wait probes the
+            // barrier once before entering the bounded, abort-aware loop)
             auto run_chunk = [&](int q, uint32_t a0, uint32_t a1, uint32_t a_sbo, uint32_t n_rows, bool first,
                                  int ksteps, uint32_t b_sbo) -> bool {
-                const int b = q % kRing;
-                if (!tc::mbar_wait_or_abort(&full[b], (q / kRing) & 1, kWaitLimit, abort_flag))
+                const int b = q & (kRing - 1);
+                const uint32_t par = (uint32_t)(q / kRing) & 1u;
+                if (!tc::mbar_try_wait(&full[b], par) &&
+                    !tc::mbar_wait_or_abort(&full[b], par, kWaitLimit, abort_flag))
                     return false;
                 tc::tc_fence_after();
                 const uint32_t idesc = tc::idesc_bf16(kBM, n_rows);
-                const uint32_t bb = tc::smem_u32(sWB + b * kImgW);
+                const uint64_t bd0 = tc::smem_desc(tc::smem_u32(sWB + b * kImgW), 128, b_sbo);
+                const uint64_t ad0 = tc::smem_desc(a0, 128, a_sbo), ad1 = tc::smem_desc(a1, 128, a_sbo);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const uint32_t ab = h ? a1 : a0;
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        const uint64_t ad = tc::smem_desc(ab + kk * 256, 128, a_sbo);
-                        const uint64_t bd = tc::smem_desc(bb + kk * 256, 128, b_sbo);
-                        tc::mma_bf16(taddr + (uint32_t)(h * 256), ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
-                    }
+                    const uint64_t ab = h ? ad1 : ad0;
+                    for (int kk = 0; kk < ksteps; ++kk)
+                        tc::mma_bf16(taddr + (uint32_t)(h * 256), ab + (uint64_t)(16 * kk), bd0 + (uint64_t)(16 * kk),
+                                     idesc, (first && kk == 0) ? 0u : 1u);
                 }
                 tc::mma_commit(&empty[b]);
                 return true;
