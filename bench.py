@@ -623,7 +623,12 @@ def main():
                 "peak_source": "measured on this GPU by jl_probe_peak (independent multiply/add chains, no FMA; "
                                "binary32: the larger of scalar FMUL/FADD, %.0f G lane-ops/s, and packed "
                                "add/mul.f32x2, %.0f)" % (probes[0] / 1e9, probes[2] / 1e9),
-                "algorithmic_unit": "8 %s lane ops per escape-time iteration" % ("binary64" if dom else "binary32"),
+                "algorithmic_unit": "8 %s lane ops per escape-time iteration (x*x, y*y, x+x, (x+x)*y, +ci, "
+                                    "x2-y2, +cr, x2+y2)%s" % ("binary64" if dom else "binary32",
+                                                             "; the kernel issues 6 of them on the FP64 pipe: x+x is "
+                                                             "an exponent increment on the integer pipe and the "
+                                                             "escape test is estimated in binary32 (exact binary64 "
+                                                             "replay near the threshold)" if dom else ""),
                 "timing": "CUDA events around a plan of the %s sweep frames alone" % ("binary64" if dom else
                                                                                     "binary32")}
     roofline_other = {"precision": "binary32" if dom else "binary64", "achieved": by_prec[1 - dom]["achieved_gops"],
