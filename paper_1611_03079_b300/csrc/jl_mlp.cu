@@ -1866,6 +1866,9 @@ __global__ void topk_tie_select_kernel(const float *__restrict__ score, int64_t 
                                        const uint32_t *__restrict__ counts, uint32_t *__restrict__ sel_key,
                                        uint32_t *__restrict__ sel_idx)
 {
+    // a block without ties in its range selects nothing
+    if (counts[blockIdx.x] == 0)
+        return;
     const uint32_t thr = st->prefix;
     __shared__ uint32_t base_s;
     __shared__ uint32_t warp_tot[32];
@@ -1924,7 +1927,7 @@ __global__ void topk_tie_select_kernel(const float *__restrict__ score, int64_t 
 // precede it (composite keys are unique, so the positions are a permutation).
 // Grid (pair blocks of 256, splits of the pairs compared against); partial
 // ranks are added atomically into `rank` (zeroed by topk_init_kernel).
-static constexpr int kRankSplit = 8;
+static constexpr int kRankSplit = 32;
 static constexpr int kRankTile = 1024;
 
 __device__ __forceinline__ uint64_t topk_comp(uint32_t key, uint32_t idx)
