@@ -11,18 +11,32 @@ namespace jl {
 // formed directly: zero/subnormal -> magnitude shifted left by one (a carry
 // into the exponent field gives the correct normal number); exponent field
 // 1..2045 -> exponent + 1; 2046 -> signed infinity (what round-to-nearest
-// gives on overflow); 2047 (inf, NaN) -> unchanged (NaN stays NaN).
+// gives on overflow); 2047 (inf, NaN) -> unchanged (NaN stays NaN).  Only
+// 32-bit operations on the two words: a 64-bit integer add was measured to
+// occupy the binary64 unit (one more binary64-pipe operation per step, the
+// same count as a binary64 x + x).
 __device__ __forceinline__ double dbl2(double x)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long sign = b & 0x8000000000000000ull;
-    const unsigned long long mag = b & 0x7fffffffffffffffull;
-    const unsigned e = (unsigned)(mag >> 52);
-    unsigned long long r = b + (1ull << 52);
-    r = (e == 0) ? (sign | (mag << 1)) : r;
-    r = (e == 2046) ? (sign | 0x7ff0000000000000ull) : r;
-    r = (e == 2047) ? b : r;
-    return __longlong_as_double((long long)r);
+    const uint32_t hi = (uint32_t)__double2hiint(x);
+    const uint32_t lo = (uint32_t)__double2loint(x);
+    const uint32_t sign = hi & 0x80000000u;
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    // exponent + 1: 2^52 has a zero low word, so only the high word changes
+    uint32_t rhi = hi + (1u << 20), rlo = lo;
+    if (e == 0) {
+        // magnitude (hi & 0x7fffffff, lo) shifted left by one, below 2^53
+        rhi = sign | ((hi & 0x7fffffffu) << 1) | (lo >> 31);
+        rlo = lo << 1;
+    }
+    if (e == 2046) {
+        rhi = sign | 0x7ff00000u;
+        rlo = 0u;
+    }
+    if (e == 2047) {
+        rhi = hi;
+        rlo = lo;
+    }
+    return __hiloint2double((int)rhi, (int)rlo);
 }
 
 // Binary32 estimate of a non-negative binary64 value from its high word,
