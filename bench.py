@@ -612,7 +612,7 @@ def main():
     d = by_prec[dom]
     # DRAM bytes (read + write) of one launch of each precision's plan, from the
     # ncu capture of the same launch in profiles/escape_kernel_sweep4096.md
-    traffic = {1: 12908800 + 753326080, 0: 30964992 + 780568320} if args.size == 4096 else {}
+    traffic = {1: 14427648 + 754297856, 0: 30964992 + 780568320} if args.size == 4096 else {}
     roofline = {"bound": "alu", "kernel": "escape_kernel<%s>" % ("double" if dom else "float"),
                 "achieved": d["achieved_gops"], "peak": d["peak_gops"], "unit": "Gop/s",
                 "frac": d["frac"], "traffic": traffic.get(dom),
