@@ -269,7 +269,11 @@ typedef struct {
     int32_t fp32_ppt, fp32_unroll, fp32_threads;  /* all 0 = tuned or default variant */
     int32_t fp64_ppt, fp64_unroll, fp64_threads;
     int32_t variant_flags;  /* bit 0 / bit 1: the fp32 / fp64 (ppt, unroll) pair is given explicitly
-                               (needed for the static kernel, ppt = unroll = 0) */
+                               (needed for the static kernel, ppt = unroll = 0);
+                               bit 2: no certified binary32 pass for binary64 frames (every binary64
+                               pixel then runs on the binary64 kernel; for comparisons);
+                               bit 3: record timing events around the kernels inside the graph
+                               (jl_batch_phase_ms) */
     int32_t tune;           /* 1: for each precision group without an explicit variant, time
                                candidate kernels (the tuned and the default variant, the tile
                                kernels, a few lane-refill shapes for binary64) on the plan's own
@@ -309,6 +313,24 @@ int jl_batch_precisions(const jl_batch *b, int32_t *out, int32_t cap);
 
 /* Pixel totals of the binary32 and binary64 frames of the plan. */
 int jl_batch_pixels(const jl_batch *b, int64_t *fp32_pixels, int64_t *fp64_pixels);
+
+/* Binary64 pixels of the last launch that the certified binary32 pass left to
+ * the binary64 kernel (its list length) and the sum of their counts (the
+ * iterations that kernel ran); 0 and 0 when the plan has no binary64 frames or
+ * the pass is off.  Synchronises `stream`; either pointer may be NULL.  The
+ * certified pass runs a binary32 orbit with a rigorous bound on its distance
+ * to the binary64 orbit and keeps a pixel only when the bound settles every
+ * binary64 test of the pixel (the counts are the binary64 counts either way;
+ * paper Sec. 3, precision of deep zooms). */
+int jl_batch_cert_stats(jl_batch *b, void *stream, int64_t *listed_out, int64_t *listed_iterations_out);
+
+/* Device time (ms) of the phases of the last completed launch of a plan
+ * created with opts.variant_flags bit 3 (timing events recorded inside its
+ * graph): ms_out[0] the binary32 escape kernel, ms_out[1] the certified
+ * binary32 pass of the binary64 frames, ms_out[2] the binary64 escape kernel;
+ * -1 for a phase the plan does not run.  The launch must have completed
+ * (synchronise its stream first).  JL_EINVAL without the flag. */
+int jl_batch_phase_ms(const jl_batch *b, float *ms_out);
 
 /* Frees the plan (after its launches have completed). */
 void jl_batch_destroy(jl_batch *b);

@@ -313,9 +313,12 @@ class Batch:
     (default False).  Outputs are allocated here as flat device buffers;
     `counts(i)`, `rgba(i)` and `hist(i)` return per-frame views.  `tune=True`
     lets the plan time candidate kernels on its own frames at creation.
+    `certify=False` turns off the certified binary32 pass of binary64 frames;
+    `phases=True` records timing events around the kernels (`phase_ms`).
     """
 
-    def __init__(self, frames, palette=None, chunk_len=0, variants=None, cycle_budget=0, tune=False):
+    def __init__(self, frames, palette=None, chunk_len=0, variants=None, cycle_budget=0, tune=False,
+                 certify=True, phases=False):
         import torch
         self._L = _lib.lib()
         self.frames = list(frames)
@@ -357,6 +360,10 @@ class Batch:
                 v64 = [int(v) for v in variants["fp64"]]
                 opts.fp64_ppt, opts.fp64_unroll, opts.fp64_threads = v64[:3]
                 opts.variant_flags |= 2
+        if not certify:
+            opts.variant_flags |= 4
+        if phases:
+            opts.variant_flags |= 8
         opts.cycle_budget = int(cycle_budget)
         opts.tune = 1 if tune else 0
         pal, pal_ptr = _palette_ptr(palette)
@@ -395,6 +402,22 @@ class Batch:
         a, b = ctypes.c_int64(0), ctypes.c_int64(0)
         check(self._L.jl_batch_pixels(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def cert_stats(self, stream=None):
+        """(pixels, iterations) of the last launch's binary64 frames that the
+        certified binary32 pass left to the binary64 kernel."""
+        import torch
+        st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+        v, it = ctypes.c_int64(0), ctypes.c_int64(0)
+        check(self._L.jl_batch_cert_stats(self._h, st, ctypes.byref(v), ctypes.byref(it)))
+        return v.value, it.value
+
+    def phase_ms(self):
+        """Device ms of the last completed launch: [binary32 kernel, certified
+        pass, binary64 kernel] (-1 where absent); needs phases=True."""
+        ms = (ctypes.c_float * 3)()
+        check(self._L.jl_batch_phase_ms(self._h, ms))
+        return [float(v) for v in ms]
 
     def counts(self, i):
         import torch

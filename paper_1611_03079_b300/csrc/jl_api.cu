@@ -146,6 +146,8 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
     F->tile_begin = 0;
     F->precision = prec;
     F->colour_magic = (1ull << 40) / (uint64_t)max_iter + 1ull;
+    if (prec == JL_FP64 && mode == JL_JULIA)
+        F->cert_ec = cert_error_constant(F->cr, F->ci, F->cr32, F->ci32);
     // Monotone escape is proven for |C| <= 2 - 2^-12 (Julia); Mandelbrot pixels
     // are classified one by one in the kernel.  |C|^2 < 3.99 is inside that.
     if (mode == JL_JULIA) {
@@ -165,14 +167,17 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
 }
 
 // Launches the escape kernel of one frame whose coordinate tables (F.xs,
-// F.ys) are already filled: clears the 16-byte control block `ctl` (work
-// counter, status) and the histogram, runs the kernel and finalises the
-// histogram.  All pointers are device pointers.
-int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStream_t st, const Variant *vopt)
+// F.ys) are already filled: clears the 32-byte control block `ctl` (work
+// counter, status, the certified pass's list count and list counter) and the
+// histogram, runs the kernel and finalises the histogram.  A binary64 frame
+// with binary32 tables and a list of cert_cap >= W * H entries takes the
+// certified binary32 pass.  All pointers are device pointers.
+int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStream_t st, const Variant *vopt,
+                 uint64_t *cert_list, int64_t cert_cap)
 {
     unsigned long long *counter = static_cast<unsigned long long *>(ctl);
     int32_t *status = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ctl) + 8);
-    cudaError_t e = cudaMemsetAsync(ctl, 0, 16, st);
+    cudaError_t e = cudaMemsetAsync(ctl, 0, 32, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaMemsetAsync(counter)");
     if (F.hist_bins) {
@@ -190,6 +195,15 @@ int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStre
     a.chunk_counter = counter;
     a.status = status;
     a.cycle_budget = 0;
+    if (prec == JL_FP64 && cert_list && cert_cap >= (int64_t)F.W * F.H && F.xs32 && F.ys32) {
+        a.cert_list = cert_list;
+        a.cert_cap = cert_cap;
+        a.cert_count = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(ctl) + 16);
+        a.list_counter = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(ctl) + 24);
+    } else {
+        F.xs32 = nullptr;
+        F.ys32 = nullptr;
+    }
     uint8_t pal[1024];
     if (palette)
         memcpy(pal, palette, 1024);
@@ -219,7 +233,10 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
     const size_t esz = prec == JL_FP64 ? 8 : 4;
     const size_t coord_bytes = ((size_t)F.W + (size_t)F.H) * esz;
     const size_t coord_pad = (coord_bytes + 255) & ~(size_t)255;
-    const size_t scratch_bytes = coord_pad + 256;
+    // binary64: binary32 tables and the list of the certified pass (8 B per pixel)
+    const size_t c32_pad = prec == JL_FP64 ? ((((size_t)F.W + (size_t)F.H) * 4 + 255) & ~(size_t)255) : 0;
+    const size_t list_bytes = prec == JL_FP64 ? (size_t)F.W * (size_t)F.H * 8 : 0;
+    const size_t scratch_bytes = coord_pad + 256 + c32_pad + list_bytes;
     void *scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, st);
     if (e != cudaSuccess)
@@ -227,12 +244,18 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
     uint8_t *base = static_cast<uint8_t *>(scratch);
     F.xs = base;
     F.ys = base + (size_t)F.W * esz;
+    uint64_t *list = nullptr;
+    if (prec == JL_FP64) {
+        F.xs32 = reinterpret_cast<float *>(base + coord_pad + 256);
+        F.ys32 = F.xs32 + F.W;
+        list = reinterpret_cast<uint64_t *>(base + coord_pad + 256 + c32_pad);
+    }
     int rc = JL_OK;
     e = launch_coords(nullptr, &F, 1, st);
     if (e != cudaSuccess)
         rc = cuda_fail(e, "coords kernel launch");
     if (rc == JL_OK)
-        rc = launch_frame(F, prec, palette, base + coord_pad, st, vopt);
+        rc = launch_frame(F, prec, palette, base + coord_pad, st, vopt, list, (int64_t)F.W * F.H);
     cudaError_t e2 = cudaFreeAsync(scratch, st);
     if (rc == JL_OK && e2 != cudaSuccess)
         rc = cuda_fail(e2, "cudaFreeAsync(scratch)");

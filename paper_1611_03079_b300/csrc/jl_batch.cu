@@ -33,7 +33,16 @@ struct jl_batch {
     int n_group[2] = {0, 0};
     int64_t chunks[2] = {0, 0};
     void *coords_dev = nullptr;
-    uint8_t *ctl_dev = nullptr;            // counters (2 x 8 B) + status (4 B), zeroed per launch
+    uint64_t *list_dev = nullptr;          // binary64 group: the certified pass's list (8 B per pixel)
+    // control words, zeroed per launch: work counters of the two groups (0, 8),
+    // status (16), the certified pass's list count (32), list counter (40) and
+    // the listed pixels' iterations (48)
+    uint8_t *ctl_dev = nullptr;
+    // opts.variant_flags bit 3: timing events recorded inside the graph around
+    // the binary32 kernel (0, 1) and the binary64 kernels (2, 3 after the
+    // certified pass, 4)
+    bool phases = false, cert_used = false;
+    cudaEvent_t ph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t s0 = nullptr, s1 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
@@ -62,8 +71,13 @@ static void destroy_plan(jl_batch *b)
     }
     if (b->coords_dev)
         cudaFree(b->coords_dev);
+    if (b->list_dev)
+        cudaFree(b->list_dev);
     if (b->ctl_dev)
         cudaFree(b->ctl_dev);
+    for (cudaEvent_t &ev : b->ph)
+        if (ev)
+            cudaEventDestroy(ev);
     if (b->fork)
         cudaEventDestroy(b->fork);
     if (b->join)
@@ -145,11 +159,14 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
     int rc = JL_OK;
     do {
         // ---- coordinate tables (one allocation, 256-byte aligned pieces) ----
+        // (binary64 frames: also their binary32 roundings for the certified pass)
         size_t coord_bytes = 0;
         for (int g = 0; g < 2; ++g)
             for (const Frame &F : host[g])
                 coord_bytes += (((size_t)F.W * (g ? 8 : 4) + 255) & ~(size_t)255) +
-                               (((size_t)F.H * (g ? 8 : 4) + 255) & ~(size_t)255);
+                               (((size_t)F.H * (g ? 8 : 4) + 255) & ~(size_t)255) +
+                               (g ? (((size_t)F.W * 4 + 255) & ~(size_t)255) + (((size_t)F.H * 4 + 255) & ~(size_t)255)
+                                  : 0);
         e = cudaMalloc(&b->coords_dev, coord_bytes ? coord_bytes : 256);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(coordinate tables)"); break; }
         size_t off = 0;
@@ -163,6 +180,12 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 off += ((size_t)F.W * es + 255) & ~(size_t)255;
                 F.ys = static_cast<uint8_t *>(b->coords_dev) + off;
                 off += ((size_t)F.H * es + 255) & ~(size_t)255;
+                if (g) {
+                    F.xs32 = reinterpret_cast<const float *>(static_cast<uint8_t *>(b->coords_dev) + off);
+                    off += ((size_t)F.W * 4 + 255) & ~(size_t)255;
+                    F.ys32 = reinterpret_cast<const float *>(static_cast<uint8_t *>(b->coords_dev) + off);
+                    off += ((size_t)F.H * 4 + 255) & ~(size_t)255;
+                }
                 F.chunk_begin = chunk;
                 chunk += F.chunk_count;
                 b->pixels[g] += (int64_t)F.W * F.H;
@@ -173,6 +196,10 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
         }
         e = cudaMalloc(&b->ctl_dev, 256);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(control words)"); break; }
+        if (b->pixels[1] > 0) {
+            e = cudaMalloc(&b->list_dev, (size_t)b->pixels[1] * sizeof(uint64_t));
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(certified pass list)"); break; }
+        }
         e = cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking);
         if (e == cudaSuccess)
             e = cudaStreamCreateWithFlags(&b->s1, cudaStreamNonBlocking);
@@ -180,6 +207,9 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+        b->phases = (o.variant_flags & 8) != 0;
+        for (int k = 0; k < 5 && e == cudaSuccess && b->phases; ++k)
+            e = cudaEventCreate(&b->ph[k]);
         if (e != cudaSuccess) { rc = cuda_fail(e, "stream/event creation"); break; }
 
         for (int g = 0; g < 2 && rc == JL_OK; ++g) {
@@ -261,9 +291,9 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             EscapeArgs x;
             memset(&x, 0, sizeof(EscapeArgs));
             x.frames = b->frames_dev[g];
-            x.chunk_frame = v.ppt ? b->chunk_frame_dev[g] : nullptr;
-            x.tile_frame = v.ppt ? nullptr : b->tile_dev[g];
-            x.tile_local = v.ppt ? nullptr : b->tile_dev[g] + b->tiles[g];
+            x.chunk_frame = b->chunk_frame_dev[g];
+            x.tile_frame = b->tile_dev[g];
+            x.tile_local = b->tile_dev[g] ? b->tile_dev[g] + b->tiles[g] : nullptr;
             x.total_tiles = b->tiles[g];
             x.n_frames = b->n_group[g];
             x.hist_smem = 0;
@@ -271,6 +301,13 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             x.chunk_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 8 * g);
             x.status = reinterpret_cast<int32_t *>(b->ctl_dev + 16);
             x.cycle_budget = o.cycle_budget;
+            if (g == 1 && b->list_dev && !(o.variant_flags & 4)) {
+                x.cert_list = b->list_dev;
+                x.cert_cap = b->pixels[1];
+                x.cert_count = reinterpret_cast<unsigned long long *>(b->ctl_dev + 32);
+                x.list_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 40);
+                x.list_iters = reinterpret_cast<unsigned long long *>(b->ctl_dev + 48);
+            }
             // output specialisation: 1 = every frame uint16 counts + RGBA8, 2 =
             // every frame RGBA8 only, 3 = every frame uint8 counts + RGBA8
             // (none with a histogram), else 0
@@ -330,7 +367,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                     const EscapeArgs x = make_args(g, v);
                     float ms = 0.f;
                     for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-                        e = cudaMemsetAsync(b->ctl_dev, 0, 32, b->s0);
+                        e = cudaMemsetAsync(b->ctl_dev, 0, 64, b->s0);
                         if (e == cudaSuccess)
                             e = cudaEventRecord(t0, b->s0);
                         if (e == cudaSuccess)
@@ -364,7 +401,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             args[g] = make_args(g, b->variant[g]);
         e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamBeginCapture"); break; }
-        cudaError_t ce = cudaMemsetAsync(b->ctl_dev, 0, 32, b->s0);
+        cudaError_t ce = cudaMemsetAsync(b->ctl_dev, 0, 64, b->s0);
         // region covering: coordinate tables of every frame, each launch
         for (int g = 0; g < 2 && ce == cudaSuccess; ++g)
             if (b->n_group[g])
@@ -372,22 +409,33 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
         for (int g = 0; g < 2 && ce == cudaSuccess && any_hist; ++g)
             if (b->n_group[g])
                 ce = launch_hist_zero(b->frames_dev[g], b->n_group[g], b->s0);
+        b->cert_used = b->n_group[1] && args[1].cert_list && b->variant[1].ppt > 0 && args[1].tile_frame;
+        // one group's kernels on stream s, with its timing events when asked for
+        auto group = [&](int g, cudaStream_t s) -> cudaError_t {
+            cudaEvent_t e0 = b->phases ? b->ph[g ? 2 : 0] : nullptr, e1 = b->phases ? b->ph[g ? 4 : 1] : nullptr;
+            cudaEvent_t mid = (b->phases && g) ? b->ph[3] : nullptr;
+            cudaError_t r = e0 ? cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal) : cudaSuccess;
+            if (r == cudaSuccess)
+                r = launch_escape(args[g], g, b->variant[g], sms, s, mid);
+            if (r == cudaSuccess && e1)
+                r = cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+            return r;
+        };
         const bool both = b->n_group[0] && b->n_group[1];
         if (ce == cudaSuccess && both) {
             ce = cudaEventRecord(b->fork, b->s0);
             if (ce == cudaSuccess)
                 ce = cudaStreamWaitEvent(b->s1, b->fork, 0);
             if (ce == cudaSuccess)
-                ce = launch_escape(args[1], JL_FP64, b->variant[1], sms, b->s1);
+                ce = group(1, b->s1);
             if (ce == cudaSuccess)
                 ce = cudaEventRecord(b->join, b->s1);
             if (ce == cudaSuccess)
-                ce = launch_escape(args[0], JL_FP32, b->variant[0], sms, b->s0);
+                ce = group(0, b->s0);
             if (ce == cudaSuccess)
                 ce = cudaStreamWaitEvent(b->s0, b->join, 0);
         } else if (ce == cudaSuccess) {
-            const int g = b->n_group[0] ? 0 : 1;
-            ce = launch_escape(args[g], g, b->variant[g], sms, b->s0);
+            ce = group(b->n_group[0] ? 0 : 1, b->s0);
         }
         for (int g = 0; g < 2 && ce == cudaSuccess && any_hist; ++g)
             if (b->n_group[g])
@@ -442,6 +490,49 @@ int jl_batch_status(jl_batch *b, void *stream, int32_t *status_out)
     if (e != cudaSuccess)
         return cuda_fail(e, "reading batch status");
     *status_out = v;
+    return JL_OK;
+}
+
+int jl_batch_cert_stats(jl_batch *b, void *stream, int64_t *listed_out, int64_t *listed_iterations_out)
+{
+    if (!b)
+        return fail(JL_EINVAL, "invalid batch plan");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long v[3] = {0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(v, b->ctl_dev + 32, 24, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading the certified pass's counters");
+    if (listed_out)
+        *listed_out = (int64_t)v[0];
+    if (listed_iterations_out)
+        *listed_iterations_out = (int64_t)v[2];
+    return JL_OK;
+}
+
+int jl_batch_phase_ms(const jl_batch *b, float *ms_out)
+{
+    if (!b || !ms_out)
+        return fail(JL_EINVAL, "invalid arguments");
+    if (!b->phases)
+        return fail(JL_EINVAL, "the plan was created without phase events (opts.variant_flags bit 3)");
+    for (int k = 0; k < 3; ++k)
+        ms_out[k] = -1.f;
+    cudaError_t e = cudaSuccess;
+    if (b->n_group[0])
+        e = cudaEventElapsedTime(&ms_out[0], b->ph[0], b->ph[1]);
+    if (e == cudaSuccess && b->n_group[1]) {
+        if (b->cert_used) {
+            e = cudaEventElapsedTime(&ms_out[1], b->ph[2], b->ph[3]);
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&ms_out[2], b->ph[3], b->ph[4]);
+        } else {
+            e = cudaEventElapsedTime(&ms_out[2], b->ph[2], b->ph[4]);
+        }
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "reading phase events");
     return JL_OK;
 }
 

@@ -30,6 +30,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <math.h>
+
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -63,14 +65,19 @@ __global__ void coords_kernel(const __grid_constant__ CoordArgs a)
     const double lo = axis ? F.ymin : F.xmin;
     const double d = axis ? F.dy : F.dx;
     void *out = const_cast<void *>(axis ? F.ys : F.xs);
+    // binary64 frames: also the binary32 roundings for the certified pass
+    float *out32 = F.precision == JL_FP64 ? const_cast<float *>(axis ? F.ys32 : F.xs32) : nullptr;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         // lo + (i + 0.5) * d, binary64, no contraction.
         double t = __dadd_rn((double)i, 0.5);
         double v = __dadd_rn(lo, __dmul_rn(t, d));
-        if (F.precision == JL_FP64)
+        if (F.precision == JL_FP64) {
             static_cast<double *>(out)[i] = v;
-        else
+            if (out32)
+                out32[i] = __double2float_rn(v);
+        } else {
             static_cast<float *>(out)[i] = __double2float_rn(v);
+        }
     }
 }
 
@@ -196,7 +203,9 @@ struct WorkT<double> {
     static __device__ __forceinline__ double ci(const Frame &F) { return F.ci; }
 };
 
-template <typename T, int PPT, int U, bool BATCH>
+// LIST (binary64): the pixels are the entries of the certified pass's list
+// (a.cert_list, *a.cert_count of them) instead of the frames' row chunks.
+template <typename T, int PPT, int U, bool BATCH, bool LIST>
 __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ EscapeArgs a)
 {
     extern __shared__ uint32_t smem[];
@@ -239,6 +248,14 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
     unsigned long long next_c = 0;  // valid in lane 0: prefetched chunk id
     if (lane == 0)
         next_c = atomicAdd(a.chunk_counter, 1ull);
+    // LIST: entries of the list and its 32-entry pieces (the chunks here)
+    long long list_n = 0, q_l0 = 0;
+    if constexpr (LIST) {
+        list_n = (long long)*a.cert_count;
+        if (list_n > a.cert_cap)
+            list_n = a.cert_cap;
+    }
+    const long long total_chunks = LIST ? (list_n + 31) >> 5 : a.total_chunks;
 
     auto advance = [&]() -> bool {
         if (q_done)
@@ -248,14 +265,20 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
         if (a.cycle_budget > 0 && (clock64() - t_start) > a.cycle_budget)
             over_budget = true;
         over_budget = __any_sync(FULL, over_budget);
-        if ((long long)c >= a.total_chunks || over_budget) {
-            if (over_budget && lane == 0 && a.status && (long long)c < a.total_chunks)
+        if ((long long)c >= total_chunks || over_budget) {
+            if (over_budget && lane == 0 && a.status && (long long)c < total_chunks)
                 atomicExch(a.status, (int)JL_ETIMEOUT);
             q_done = true;
             return false;
         }
         if (lane == 0)
             next_c = atomicAdd(a.chunk_counter, 1ull);
+        if constexpr (LIST) {
+            q_l0 = (long long)c << 5;
+            q_pos = 0;
+            q_end = (int)min(32ll, list_n - q_l0);
+            return true;
+        }
         int f = 0;
         if constexpr (BATCH)
             f = a.chunk_frame[c];
@@ -314,6 +337,12 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
         }
         if (F.rgba)
             F.rgba[p] = pal[colour_index((uint32_t)count, (uint32_t)F.max_iter, F.colour_magic)];
+        if (LIST && a.list_iters) {
+            const unsigned act = __activemask();
+            const unsigned tot = __reduce_add_sync(act, (unsigned)count);
+            if ((act & lt_mask) == 0)
+                atomicAdd(a.list_iters, (unsigned long long)tot);
+        }
         if (F.hist_bins) {
             if (!BATCH && a.hist_smem) {
                 atomicAdd(&hbins[count], 1u);
@@ -342,7 +371,37 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
             const bool mine = (remaining & lane_bit) != 0;
             const int rank = __popc(remaining & lt_mask);
             const bool got = mine && rank < take;
-            if (got) {
+            if (LIST && got) {
+                // list entry (frame << 32) | (row << 16) | column
+                const uint64_t ent = a.cert_list[q_l0 + q_pos + rank];
+                const int f = (int)(ent >> 32);
+                const int j = (int)((ent >> 16) & 0xffffu);
+                const int i = (int)(ent & 0xffffu);
+                const Frame &F = FR(f);
+                const T xv = static_cast<const T *>(F.xs)[i];
+                const T yv = static_cast<const T *>(F.ys)[j];
+                fid[k] = f;
+                pix[k] = j * F.W + i;
+                rem[k] = F.max_iter;
+                bool unsafe;
+                if (F.mode == JL_JULIA) {
+                    x[k] = xv;
+                    y[k] = yv;
+                    cr[k] = WorkT<T>::cr(F);
+                    ci[k] = WorkT<T>::ci(F);
+                    unsafe = !F.safe;
+                } else {
+                    x[k] = T(0);
+                    y[k] = T(0);
+                    cr[k] = xv;
+                    ci[k] = yv;
+                    unsafe = in_unsafe_band(xv, yv);
+                }
+                if (unsafe || F.max_iter < U) {
+                    const int c = exact_from(x[k], y[k], cr[k], ci[k], 0, F.max_iter);
+                    rem[k] = -1 - c;
+                }
+            } else if (got) {
                 const int o = q_pos + rank;
                 const int jj = (int)(((uint32_t)o * q_magic) >> 20);
                 const int i = q_x0 + o - jj * q_span;
@@ -1173,6 +1232,242 @@ __global__ void __launch_bounds__(256, 4) escape_compact_kernel(const __grid_con
 }
 
 // ---------------------------------------------------------------------------
+// Certified binary32 pass for binary64 frames.
+//
+// A binary64 frame's counts are those of the binary64 orbit Z_{n+1} = Z_n^2 + C
+// (round to nearest, no FMA) with the test x2 + y2 > 4 taken in binary64, and
+// the binary64 pipe of this part issues ~74x fewer operations per clock than
+// the binary32 one.  This pass runs a binary32 orbit W_n beside that orbit with
+// a running bound E_n >= |Z_n - W_n| (complex modulus) and takes a binary64 test
+// from binary32 values only where the bound settles it:
+//     (|W| - E)^2 <= |Z|^2 <= (|W| + E)^2.
+// A certified test is the binary64 test's own outcome, so a pixel whose tests
+// are all certified, up to its escape or to the limit, gets exactly its
+// binary64 count.  A pixel with a test the bound cannot settle goes to a list
+// that the binary64 kernel (LIST) renders from Z_0.
+//
+// u = 2^-24.  The orbit is rounded to nearest; the bound arithmetic rounds
+// toward +inf (toward -inf for the lower bound), so it never understates.
+//   orbit   y2 = y*y, r = fma(x, x, y2), x' = fma(x, x, fma(-y, y, cr)),
+//           y' = fma(x + x, y, ci);  |W|^2 is within r (1 +- 2^-20)
+//   modulus s = sqrt.approx(r) (1 + 2^-10) >= |W|  (the PTX approximation is
+//           within ~2^-23 relative; the factor leaves 2^10 of room)
+//   pass    U = r (1 + 2^-20) + E (2 s + E) + EC < 4  =>  binary64 x2 + y2 <= 4
+//           (U <= 4 - 2^-22, and the binary64 sum of squares is within 2^-51
+//           of |Z|^2 relative)
+//   escape  L = r (1 - 2^-20) - 2 s E > 4  =>  binary64 x2 + y2 > 4
+//   bound   E' = E (2 s + E) + EC + 2.5 u r
+// The new bound adds up |Z^2 - W^2| <= E (2|W| + E); |C - C32|_1; the binary32
+// rounding of the step, at most u (1 + 2^-19)(|x'| + |y'| + |cr| + y2) in the
+// 1-norm, which is <= 2.5 u r + u (1 + 2^-19)(2|cr| + |ci|) because
+// |x'| + |y'| <= sqrt(2) |W|^2 + |C|_1 to first order; and the binary64
+// rounding of the step, <= 2^-48 + 2^-52 |C|_1 while |Z|^2 <= 4, plus underflow
+// terms below 2^-146.  EC collects the terms that do not depend on W:
+//   Julia:      EC = |C - C32|_1 + 2^-22 (|cr32| + |ci32|) + 2^-47 for the frame
+//               (`cert_error_constant`); E_0 = u (1 + 2^-20)(|x| + |y|) + 2^-140,
+//               the rounding of the pixel's coordinates;
+//   Mandelbrot: C32 is the pixel, E_0 = 0 (Z_0 = 0 on both sides) and
+//               EC = 3 u (1 + 2^-18)(|cr| + |ci|) + 2^-47.
+// A NaN or infinity anywhere makes both tests false: the pixel goes to the list.
+// ---------------------------------------------------------------------------
+static constexpr float kCertS2 = 0x1.004p+1f;     // 2 (1 + 2^-10)
+static constexpr float kCertR1 = 0x1.00001p+0f;   // 1 + 2^-20
+static constexpr float kCertR0 = 0x1.ffffep-1f;   // 1 - 2^-20
+static constexpr float kCertK2 = 0x1.4p-23f;      // 2.5 u
+static constexpr float kCertE0 = 0x1.00001p-24f;  // u (1 + 2^-20)
+static constexpr float kCertMC = 0x1.80006p-23f;  // 3 u (1 + 2^-18)
+
+float cert_error_constant(double cr, double ci, float cr32, float ci32)
+{
+    const double v = (fabs(cr - (double)cr32) + fabs(ci - (double)ci32) +
+                      0x1p-22 * (fabs((double)cr32) + fabs((double)ci32)) + 0x1p-47) * (1.0 + 0x1p-40);
+    float f = (float)v;
+    if ((double)f < v)
+        f = nextafterf(f, INFINITY);
+    return f;
+}
+
+__device__ __forceinline__ float sqrt_approx(float r)
+{
+    float s;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(s) : "f"(r));
+    return s;
+}
+
+// One certified step from (W_n, E_n): 1 = the binary64 test of Z_n passed
+// (the state then holds W_{n+1}, E_{n+1}); 0 = it failed (escape at n);
+// -1 = not settled by the bound.
+__device__ __forceinline__ int cert_step(float &x, float &y, float &e, float cr, float ci, float ec)
+{
+    const float y2 = __fmul_rn(y, y);
+    const float r = __fmaf_rn(x, x, y2);
+    const float s = sqrt_approx(r);
+    const float ge = __fmaf_ru(e, __fmaf_ru(kCertS2, s, e), ec);
+    if (__fmaf_ru(r, kCertR1, ge) < 4.0f) {
+        const float nx = __fmaf_rn(x, x, __fmaf_rn(-y, y, cr));
+        y = __fmaf_rn(__fadd_rn(x, x), y, ci);
+        x = nx;
+        e = __fmaf_ru(kCertK2, r, ge);
+        return 1;
+    }
+    const float m = __fmul_ru(__fmul_ru(kCertS2, s), e);
+    return __fmaf_rd(r, kCertR0, -m) > 4.0f ? 0 : -1;
+}
+
+// Binary64 count of a pixel from the certified pass (tests n = 0 .. mi-1 from
+// W_0 = (x, y), E_0 = e), or -1 when a test is not settled.  Blocks of four
+// steps with one branch; a block with a test that is not a certified pass is
+// replayed one step at a time from its start to find that test.
+__device__ __forceinline__ int cert_count(float x, float y, float e, float cr, float ci, float ec, int mi)
+{
+    int n = 0;
+    for (; n + 4 <= mi; n += 4) {
+        const float x0 = x, y0 = y, e0 = e;
+        bool ok = true;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float y2 = __fmul_rn(y, y);
+            const float r = __fmaf_rn(x, x, y2);
+            const float s = sqrt_approx(r);
+            const float ge = __fmaf_ru(e, __fmaf_ru(kCertS2, s, e), ec);
+            ok &= __fmaf_ru(r, kCertR1, ge) < 4.0f;
+            const float nx = __fmaf_rn(x, x, __fmaf_rn(-y, y, cr));
+            y = __fmaf_rn(__fadd_rn(x, x), y, ci);
+            x = nx;
+            e = __fmaf_ru(kCertK2, r, ge);
+        }
+        if (!ok) {
+            x = x0;
+            y = y0;
+            e = e0;
+            break;
+        }
+    }
+    for (; n < mi; ++n) {
+        const int rc = cert_step(x, y, e, cr, ci, ec);
+        if (rc <= 0)
+            return rc == 0 ? n : -1;
+    }
+    return mi;
+}
+
+// Tile kernel of the certified pass: the static kernel's 32 x 32 tiles, 8 x 16
+// parts claimed from the launch counter, 8 x 4 patches.  Certified pixels are
+// stored; the others are appended to the list, one counter increment per
+// patch.  A list that is full (never, when cert_cap >= the launch's pixels)
+// leaves its pixel to exact binary64 steps here.
+template <bool BATCH, int OUT>
+__global__ void __launch_bounds__(256, 4) cert_kernel(const __grid_constant__ EscapeArgs a)
+{
+    __shared__ uint32_t pal[256];
+    extern __shared__ uint32_t hbins[];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        pal[t] = a.palette[t];
+    const int nb = (!BATCH && a.hist_smem) ? a.single.max_iter + 1 : 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x)
+        hbins[t] = 0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long t_start = clock64();
+    const long long total_units = a.total_tiles * 8;
+    const unsigned long long claim = (unsigned long long)a.claim;
+    unsigned long long next_u = 0;
+    if (lane == 0)
+        next_u = atomicAdd(a.chunk_counter, claim);
+    long long cur = 0, end = 0;
+    for (;;) {
+        if (cur == end) {
+            cur = (long long)__shfl_sync(FULL, next_u, 0);
+            end = cur + (long long)claim;
+            if (lane == 0)
+                next_u = atomicAdd(a.chunk_counter, claim);
+        }
+        const long long unit = cur++;
+        if (unit >= total_units)
+            break;
+        if (a.cycle_budget > 0 && __any_sync(FULL, (clock64() - t_start) > a.cycle_budget)) {
+            if (lane == 0 && a.status)
+                atomicExch(a.status, (int)JL_ETIMEOUT);
+            break;
+        }
+        const long long tile = unit >> 3;
+        const int part = (int)(unit & 7);
+        const int dx = (part & 3) * 8 + (lane & 7);
+        const int dy = (part >> 2) * 4 + (lane >> 3);
+        int fr = 0;
+        if constexpr (BATCH)
+            fr = a.tile_frame[tile];
+        const Frame &F = BATCH ? a.frames[fr] : a.single;
+        const int W = F.W, H = F.H, mi = F.max_iter;
+        const bool julia = F.mode == JL_JULIA;
+        const float fcr = F.cr32, fci = F.ci32, fec = F.cert_ec;
+        const float *xs32 = F.xs32;
+        const float *ys32 = F.ys32;
+        TileOut o;
+        o.counts = F.counts;
+        o.rgba = F.rgba;
+        o.bins = F.hist_bins;
+        o.magic = F.colour_magic;
+        o.m32 = (uint32_t)((o.magic - 1u) >> 8) + 1u;
+        o.mi = mi;
+        o.u8 = F.count_type == JL_COUNT_U8;
+        o.small = mi <= 4096;
+        const uint32_t lt = BATCH ? (uint32_t)a.tile_local[tile] : (uint32_t)(tile - F.tile_begin);
+        const uint32_t ty = (uint32_t)(((uint64_t)lt * F.tiles_x_magic) >> 40);
+        const uint32_t tx = lt - ty * (uint32_t)F.tiles_x;
+        const int i = (int)tx * 32 + dx;
+        const float xv = i < W ? xs32[i] : 0.f;
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            const int j = (int)ty * 32 + dy + 8 * q;
+            const bool valid = i < W && j < H;
+            if (!__any_sync(FULL, valid))
+                break;  // rows beyond the frame: so are the later patches of this tile
+            int count = 0;
+            if (valid) {
+                const float yv = ys32[j];
+                const float ax = fabsf(xv), ay = fabsf(yv);
+                if (julia)
+                    count = cert_count(xv, yv, __fmaf_ru(kCertE0, __fadd_ru(ax, ay), 0x1p-140f), fcr, fci, fec, mi);
+                else
+                    count = cert_count(0.f, 0.f, 0.f, xv, yv, __fmaf_ru(kCertMC, __fadd_ru(ax, ay), 0x1p-47f), mi);
+            }
+            const bool undecided = valid && count < 0;
+            const unsigned um = __ballot_sync(FULL, undecided);
+            unsigned long long base = 0;
+            if (um) {
+                if (lane == 0)
+                    base = atomicAdd(a.cert_count, (unsigned long long)__popc(um));
+                base = __shfl_sync(FULL, base, 0);
+            }
+            if (undecided) {
+                const unsigned long long k = base + (unsigned long long)__popc(um & lt_mask);
+                if (k < (unsigned long long)a.cert_cap) {
+                    a.cert_list[k] = ((uint64_t)(uint32_t)fr << 32) | ((uint64_t)(uint32_t)j << 16) | (uint32_t)i;
+                    continue;
+                }
+                // no room in the list: exact binary64 steps here
+                const double x64 = static_cast<const double *>(F.xs)[i];
+                const double y64 = static_cast<const double *>(F.ys)[j];
+                count = julia ? exact_from(x64, y64, F.cr, F.ci, 0, mi) : exact_from(0.0, 0.0, x64, y64, 0, mi);
+            }
+            if (valid)
+                store_tile<BATCH, OUT>(a, o, pal, hbins, fr, (uint32_t)j * (uint32_t)W + (uint32_t)i, count, lt_mask);
+        }
+    }
+    if (nb) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            const uint32_t v = hbins[t];
+            if (v)
+                atomicAdd(&a.single.hist_bins[t], v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 // Resident CTAs per SM of a kernel for a block size and dynamic shared
@@ -1252,10 +1547,10 @@ cudaError_t launch_hist_zero(const Frame *frames_dev, int n, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <typename T, int PPT, int U>
+template <typename T, int PPT, int U, bool LIST = false>
 static cudaError_t launch_one(const EscapeArgs &a, const Variant &v, int num_sms, size_t smem, cudaStream_t st)
 {
-    auto kern = a.frames ? escape_kernel<T, PPT, U, true> : escape_kernel<T, PPT, U, false>;
+    auto kern = a.frames ? escape_kernel<T, PPT, U, true, LIST> : escape_kernel<T, PPT, U, false, LIST>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
@@ -1270,9 +1565,9 @@ static cudaError_t launch_one(const EscapeArgs &a, const Variant &v, int num_sms
             per_sm = 1;
     }
     long long grid = (long long)num_sms * per_sm;
-    // never more warps than chunks
+    // never more warps than chunks (the list's length is known only on the device)
     long long max_ctas = (a.total_chunks + (v.threads / 32) - 1) / (v.threads / 32);
-    if (grid > max_ctas)
+    if (!LIST && grid > max_ctas)
         grid = max_ctas;
     if (grid < 1)
         grid = 1;
@@ -1422,9 +1717,68 @@ static cudaError_t launch_compact(const EscapeArgs &a, int T, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_escape(const EscapeArgs &a_in, int precision, const Variant &v, int num_sms, cudaStream_t st)
+// The certified binary32 pass of a binary64 launch (tile kernel).
+static cudaError_t launch_cert(const EscapeArgs &a, cudaStream_t st)
+{
+    size_t smem = 0;
+    if (a.hist_smem && !a.frames)
+        smem = (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
+    auto kern = a.frames ? cert_kernel<true, 0> : cert_kernel<false, 0>;
+    if (launch_out_mode(a) == 1)
+        kern = a.frames ? cert_kernel<true, 1> : cert_kernel<false, 1>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (a.total_tiles < 1)
+        return cudaErrorInvalidValue;
+    int per_sm = 0;
+    cudaError_t e = occupancy_per_sm(reinterpret_cast<const void *>(kern), 256, smem, &per_sm);
+    if (e != cudaSuccess)
+        return e;
+    const int sms = device_sm_count();
+    long long grid = (long long)(sms > 0 ? sms : 148) * (per_sm > 0 ? per_sm : 1);
+    if (grid > a.total_tiles)
+        grid = a.total_tiles;
+    EscapeArgs b = a;
+    b.claim = tile_claim(a.total_tiles, grid);
+    kern<<<(unsigned)grid, 256, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+// Whether a binary64 launch with variant v takes the certified pass: a
+// lane-refill variant, a list, the counters, and binary32 tables with tile
+// tables (batches) or in the single frame.
+static bool use_cert(const EscapeArgs &a, int precision, const Variant &v)
+{
+    if (precision != JL_FP64 || v.ppt == 0 || !a.cert_list || !a.cert_count || !a.list_counter)
+        return false;
+    return a.frames ? (a.tile_frame && a.tile_local) : (a.single.xs32 && a.single.ys32);
+}
+
+cudaError_t launch_escape(const EscapeArgs &a_in, int precision, const Variant &v, int num_sms, cudaStream_t st,
+                          cudaEvent_t mid)
 {
     EscapeArgs a = a_in;
+    if (use_cert(a, precision, v)) {
+        cudaError_t e = launch_cert(a, st);
+        if (e == cudaSuccess && mid)
+            e = cudaEventRecordWithFlags(mid, st, cudaEventRecordExternal);
+        if (e != cudaSuccess)
+            return e;
+        EscapeArgs b = a;
+        b.chunk_counter = a.list_counter;
+        size_t smem = 256 * sizeof(uint32_t);
+        if (b.hist_smem && !b.frames)
+            smem += (size_t)(b.single.max_iter + 1) * sizeof(uint32_t);
+#define JL_DISPATCH_LIST(T, P, UU)                                                            \
+        if (sizeof(T) == 8 && v.ppt == P && v.unroll == UU)                                   \
+            return launch_one<T, P, UU, true>(b, v, num_sms, smem, st);
+        JL_VARIANTS_F64(JL_DISPATCH_LIST)
+#undef JL_DISPATCH_LIST
+        return cudaErrorInvalidValue;
+    }
     if (v.ppt == 0 && v.unroll > 0 && precision == JL_FP32)
         return launch_compact(a, v.unroll, st);
     if (v.ppt == 0)

@@ -40,6 +40,10 @@ struct Frame {
     uint32_t *hist_bins;           // device uint32[max_iter + 1] or NULL
     const void *xs;                // coordinate table: W values of the working type
     const void *ys;                // coordinate table: H values of the working type
+    const float *xs32;             // binary64 frames: the tables rounded once to binary32 (certified
+    const float *ys32;             // binary32 pass), written with xs/ys; NULL: no certified pass
+    float cert_ec;                 // binary64 Julia frames: per-step error constant of the certified pass
+    int32_t pad3;
 };
 
 // Launch parameters of the escape kernels (passed by value as a grid constant).
@@ -57,6 +61,16 @@ struct EscapeArgs {
     long long cycle_budget;            // per-CTA clock64 budget; <= 0: unlimited
     int32_t claim;                     // tile kernels: 8 x 16 parts per counter claim (set by the launcher)
     int32_t out_mode;                  // batches: 1 = uint16 counts + RGBA8, 2 = RGBA8 only, 3 = uint8 counts + RGBA8 (every frame, no histograms)
+    // binary64 frames: the certified binary32 pass appends the pixels it could
+    // not decide to cert_list ((frame << 32) | (row << 16) | column, at most
+    // cert_cap entries; the count in *cert_count), which the binary64 kernel
+    // then renders, taking 32-entry pieces from *list_counter.  cert_list NULL:
+    // no certified pass (the binary64 kernels cover every pixel).
+    uint64_t *cert_list;
+    int64_t cert_cap;
+    unsigned long long *cert_count;    // zeroed before the launch
+    unsigned long long *list_counter;  // zeroed before the launch
+    unsigned long long *list_iters;    // zeroed before the launch, or NULL: iterations of the listed pixels
     uint32_t palette[256];
     Frame single;
 };
@@ -77,8 +91,10 @@ int cuda_fail(cudaError_t e, const char *what);
 // Launchers implemented in jl_escape.cu.
 // `frames_dev` is a device table of n frames, or NULL with `single` used instead.
 cudaError_t launch_coords(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st);
+// A binary64 launch with the certified pass records `mid` (when not NULL)
+// between the pass and the binary64 kernel.
 cudaError_t launch_escape(const EscapeArgs &args, int precision, const Variant &v, int num_sms,
-                          cudaStream_t st);
+                          cudaStream_t st, cudaEvent_t mid = nullptr);
 cudaError_t launch_hist_finalize(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st);
 cudaError_t launch_hist_zero(const Frame *frames_dev, int n, cudaStream_t st);
 bool variant_supported(int precision, int ppt, int unroll);
@@ -96,10 +112,17 @@ int default_palette_bytes(uint8_t *out);
 int select_precision(const jl_rect &r, int W, int H);
 
 // Launches the escape kernel of one frame whose coordinate tables are filled:
-// clears the 16-byte control block `ctl` (work counter, status) and the
-// histogram, runs the tuned (or `vopt`'s) variant, finalises the histogram.
-// Allocates nothing.
-int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStream_t st, const Variant *vopt);
+// clears the 32-byte control block `ctl` (work counter, status, the certified
+// pass's list count and list counter) and the histogram, runs the tuned (or
+// `vopt`'s) variant, finalises the histogram.  Binary64 frames with binary32
+// tables (F.xs32) and a list of cert_cap >= W * H entries take the certified
+// binary32 pass first.  Allocates nothing.
+int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStream_t st, const Variant *vopt,
+                 uint64_t *cert_list = nullptr, int64_t cert_cap = 0);
+
+// Per-step error constant of the certified binary32 pass for a binary64
+// Julia frame (see jl_escape.cu), rounded up to binary32.
+float cert_error_constant(double cr, double ci, float cr32, float ci32);
 
 // Default variants, and the autotuned one when the tuner has run.
 Variant default_variant(int precision, int max_iter);

@@ -30,9 +30,6 @@
 
 #include "jl_internal.h"
 
-namespace jl {
-int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStream_t st, const Variant *vopt);
-}
 
 using namespace jl;
 
@@ -64,6 +61,10 @@ struct jl_host_plan {
     void *slots = nullptr;
     size_t slot_bytes = 0;
     void *tables = nullptr;  // coordinate tables, a 256-byte control block per frame and per extra band
+    // binary64 units: the certified pass's list of each render stream (units
+    // on one stream run one after the other), list_cap entries each
+    uint64_t *lists = nullptr;
+    int64_t list_cap = 0;
 };
 
 static size_t pad256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -104,6 +105,7 @@ static void destroy_host_plan(jl_host_plan *p)
         cudaEventDestroy(p->tables_ready);
     cudaFree(p->slots);
     cudaFree(p->tables);
+    cudaFree(p->lists);
     delete p;
 }
 
@@ -166,6 +168,8 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
         const size_t esz = p->prec[(size_t)i] == JL_FP64 ? 8 : 4;
         table_off[(size_t)i] = table_bytes;
         table_bytes += pad256(((size_t)q.width + (size_t)q.height) * esz);
+        if (p->prec[(size_t)i] == JL_FP64)  // binary32 roundings for the certified pass
+            table_bytes += pad256(((size_t)q.width + (size_t)q.height) * 4);
         p->ctl_off[(size_t)i] = table_bytes;
         table_bytes += 256;
     }
@@ -188,12 +192,19 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
             }
         }
     p->slot_bytes = slot_bytes;
+    const int nr = n < kRenderStreams ? n : kRenderStreams, nc = n < kCopyStreams ? n : kCopyStreams;
+    for (size_t u = 0; u < p->units.size(); ++u) {
+        const Unit &U = p->units[u];
+        if (p->prec[(size_t)U.frame] == JL_FP64) {
+            const int64_t px = (int64_t)U.rows * p->F[(size_t)U.frame].W;
+            p->list_cap = px > p->list_cap ? px : p->list_cap;
+        }
+    }
     if (depth == 0) {
         size_t fit = kDefaultSlotBudget / slot_bytes;
         depth = (int)(fit < (size_t)kDefaultSlots ? (fit < 1 ? 1 : fit) : kDefaultSlots);
     }
     p->depth = depth > n ? n : depth;
-    const int nr = n < kRenderStreams ? n : kRenderStreams, nc = n < kCopyStreams ? n : kCopyStreams;
     int rc = JL_OK;
     cudaError_t e = cudaGetDevice(&p->device);
     do {
@@ -218,6 +229,10 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(frame slots)"); break; }
         e = cudaMalloc(&p->tables, table_bytes);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(coordinate tables)"); break; }
+        if (p->list_cap > 0) {
+            e = cudaMalloc(&p->lists, (size_t)p->list_cap * sizeof(uint64_t) * (size_t)nr);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(certified pass lists)"); break; }
+        }
         // where each frame's coordinate tables live (jl_host_plan_run fills them)
         for (int i = 0; i < n; ++i) {
             Frame &F = p->F[(size_t)i];
@@ -225,6 +240,10 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
             uint8_t *base = static_cast<uint8_t *>(p->tables) + table_off[(size_t)i];
             F.xs = base;
             F.ys = base + (size_t)F.W * esz;
+            if (esz == 8) {
+                F.xs32 = reinterpret_cast<const float *>(base + pad256(((size_t)F.W + (size_t)F.H) * 8));
+                F.ys32 = F.xs32 + F.W;
+            }
         }
         e = cudaEventCreateWithFlags(&p->tables_ready, cudaEventDisableTiming);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventCreate"); break; }
@@ -301,11 +320,15 @@ int jl_host_plan_run(jl_host_plan *p, void *stream)
             if (U.rows != F0.H) {
                 F.H = U.rows;
                 F.ys = static_cast<const uint8_t *>(F0.ys) + (size_t)U.row0 * esz;
+                if (F0.ys32)
+                    F.ys32 = F0.ys32 + U.row0;
                 F.chunk_count = F0.rows_per_chunk > 1 ? (U.rows + F0.rows_per_chunk - 1) / F0.rows_per_chunk
                                                       : U.rows * F0.chunks_per_row;
                 F.tile_count = F0.tiles_x * ((U.rows + 31) / 32);
             }
-            rc = launch_frame(F, p->prec[k], pal, static_cast<uint8_t *>(p->tables) + U.ctl_off, r, nullptr);
+            uint64_t *list = p->lists ? p->lists + (size_t)p->list_cap * (u % nr) : nullptr;
+            rc = launch_frame(F, p->prec[k], pal, static_cast<uint8_t *>(p->tables) + U.ctl_off, r, nullptr, list,
+                              p->list_cap);
             if (rc != JL_OK)
                 break;
             if ((e = cudaEventRecord(p->rendered[u], r)) != cudaSuccess ||
