@@ -558,7 +558,6 @@ def main():
     plan = jl.Batch(frames, palette=pal, tune=True)
     sub = {p: [i for i in range(len(frames)) if frames[i]["precision"] == p] for p in (0, 1)}
     chosen = {"fp32": plan.variant(0), "fp64": plan.variant(1)}
-    sub_plans = {p: jl.Batch([frames[i] for i in sub[p]], palette=pal, variants=chosen) for p in (0, 1)}
     W_ = max(args.warmup, 3)
     for _ in range(W_):
         plan.launch()
@@ -589,10 +588,14 @@ def main():
     total_iters = sum(iters)
     value = world * K * total_iters / (total_ms * 1e-3) / 1e9
 
-    # per-precision breakdown and roofline (escape kernels, ALU bound)
-    by_prec = {}
+    # per-precision breakdown and rooflines (ALU bound): each precision's frames
+    # as a plan of their own, with timing events recorded inside its graph
+    # around each kernel (binary64: the certified binary32 pass, then the
+    # binary64 kernel on the pixels it left)
+    by_prec, kern = {}, {}
+    cert_stats = (0, 0)
     for prec in (0, 1):
-        sp = sub_plans[prec]
+        sp = jl.Batch([frames[i] for i in sub[prec]], palette=pal, variants=chosen, phases=True)
         for _ in range(2):
             sp.launch(stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -602,38 +605,68 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) * 1e-3 / K
+        ph = []
+        for _ in range(K):
+            sp.launch(stream)
+            torch.cuda.synchronize()
+            ph.append(sp.phase_ms())
+        ph = [statistics.mean(v[k] for v in ph) for k in range(3)]
         it = sum(iters[i] for i in sub[prec])
+        px = sum(frames[i]["W"] * frames[i]["H"] for i in sub[prec])
         ops = OPS_PER_ITER * it / t
         by_prec[prec] = {"giter_s": it / t / 1e9, "time_ms": t * 1e3, "iterations": it,
                          "achieved_gops": ops / 1e9, "peak_gops": peaks[prec] / 1e9, "frac": ops / peaks[prec],
-                         "frames": len(sub[prec])}
+                         "frames": len(sub[prec]), "kernel_ms": ph}
+        if prec == 0:
+            kern["escape_compact_kernel" if chosen["fp32"][0] == 0 and chosen["fp32"][1] > 0 else
+                 "escape_kernel<float>"] = dict(ms=ph[0], ops=OPS_PER_ITER * it, peak=peaks[0], prec="binary32",
+                                                bytes=6 * px, unit_note="8 binary32 lane ops per iteration")
+        elif ph[1] > 0:
+            listed, listed_it = sp.cert_stats(stream)
+            cert_stats = (listed, listed_it)
+            by_prec[prec].update({"cert_listed_pixels": listed, "cert_listed_iterations": listed_it})
+            kern["cert_kernel"] = dict(
+                ms=ph[1], ops=OPS_PER_ITER * (it - listed_it), peak=peaks[0], prec="binary32",
+                bytes=6 * (px - listed) + 8 * listed,
+                unit_note="8 lane ops per binary64 iteration the certified binary32 pass settles (%d of %d); "
+                          "the pass issues ~12 binary32 operations per step (the orbit with FMA plus its "
+                          "error bound) and also runs the steps of the %d pixels it lists before their "
+                          "unsettled test" % (it - listed_it, it, listed))
+            kern["escape_kernel<double> (list)"] = dict(
+                ms=ph[2], ops=OPS_PER_ITER * listed_it, peak=peaks[1], prec="binary64", bytes=14 * listed,
+                unit_note="8 binary64 lane ops per iteration of the listed pixels; the kernel issues 6 of them "
+                          "on the FP64 pipe: x+x is an exponent increment on the integer pipe and the escape "
+                          "test is estimated in binary32 (exact binary64 replay near the threshold)")
+        else:
+            kern["escape_kernel<double>"] = dict(ms=ph[2], ops=OPS_PER_ITER * it, peak=peaks[1], prec="binary64",
+                                                 bytes=6 * px, unit_note="8 binary64 lane ops per iteration")
         sp.close()
-    dom = max((0, 1), key=lambda p: by_prec[p]["time_ms"])
-    d = by_prec[dom]
-    # DRAM bytes (read + write) of one launch of each precision's plan, from the
-    # ncu capture of the same launch in profiles/escape_kernel_sweep4096.md
-    traffic = {1: 14427648 + 754297856, 0: 30964992 + 780568320} if args.size == 4096 else {}
-    roofline = {"bound": "alu", "kernel": "escape_kernel<%s>" % ("double" if dom else "float"),
-                "achieved": d["achieved_gops"], "peak": d["peak_gops"], "unit": "Gop/s",
-                "frac": d["frac"], "traffic": traffic.get(dom),
-                "traffic_note": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of "
-                                "this plan launch, profiles/escape_kernel_sweep4096.md); algorithmic bytes per "
-                                "launch: %d (uint16 count + RGBA8 per pixel)" % (6 * sum(
-                                    frames[i]["W"] * frames[i]["H"] for i in sub[dom])),
+    for k, v in kern.items():
+        v["achieved"] = v["ops"] / (v["ms"] * 1e-3) / 1e9
+        v["frac"] = v["achieved"] * 1e9 / v["peak"]
+    dom_k = max(kern, key=lambda k: kern[k]["ms"])
+    d = kern[dom_k]
+    # DRAM bytes (read + write) per launch of each kernel, from one ncu capture
+    # of the same plan launch (profiles/escape_kernel_sweep4096.md)
+    traffic = {"escape_kernel<double> (list)": 77456896 + 46401280, "cert_kernel": 68922624 + 789412096,
+               "escape_compact_kernel": 30964992 + 780568320} if args.size == 4096 else {}
+    roofline = {"bound": "alu", "kernel": dom_k, "precision": d["prec"],
+                "achieved": d["achieved"], "peak": d["peak"] / 1e9, "unit": "Gop/s", "frac": d["frac"],
+                "traffic": traffic.get(dom_k),
+                "traffic_note": "bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture "
+                                "of this plan launch, profiles/escape_kernel_sweep4096.md); algorithmic bytes per "
+                                "launch: %d (uint16 count + RGBA8 per pixel it stores, 8 B per list entry)"
+                                % d["bytes"],
                 "peak_source": "measured on this GPU by jl_probe_peak (independent multiply/add chains, no FMA; "
                                "binary32: the larger of scalar FMUL/FADD, %.0f G lane-ops/s, and packed "
                                "add/mul.f32x2, %.0f)" % (probes[0] / 1e9, probes[2] / 1e9),
-                "algorithmic_unit": "8 %s lane ops per escape-time iteration (x*x, y*y, x+x, (x+x)*y, +ci, "
-                                    "x2-y2, +cr, x2+y2)%s" % ("binary64" if dom else "binary32",
-                                                             "; the kernel issues 6 of them on the FP64 pipe: x+x is "
-                                                             "an exponent increment on the integer pipe and the "
-                                                             "escape test is estimated in binary32 (exact binary64 "
-                                                             "replay near the threshold)" if dom else ""),
-                "timing": "CUDA events around a plan of the %s sweep frames alone" % ("binary64" if dom else
-                                                                                    "binary32")}
-    roofline_other = {"precision": "binary32" if dom else "binary64", "achieved": by_prec[1 - dom]["achieved_gops"],
-                      "peak": by_prec[1 - dom]["peak_gops"], "unit": "Gop/s", "frac": by_prec[1 - dom]["frac"],
-                      "traffic": traffic.get(1 - dom)}
+                "algorithmic_unit": d["unit_note"] + " (x*x, y*y, x+x, (x+x)*y, +ci, x2-y2, +cr, x2+y2)",
+                "ms_per_launch": d["ms"],
+                "timing": "CUDA events recorded inside the graph around this kernel, plan of the %s sweep "
+                          "frames alone, mean of %d synchronised launches" % (d["prec"], K)}
+    roofline_other = [{"kernel": k, "precision": v["prec"], "achieved": v["achieved"], "peak": v["peak"] / 1e9,
+                       "unit": "Gop/s", "frac": v["frac"], "ms_per_launch": v["ms"], "traffic": traffic.get(k),
+                       "algorithmic_unit": v["unit_note"]} for k, v in kern.items() if k != dom_k]
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -726,12 +759,16 @@ def main():
                     k: survey[k] for k in ("screened_per_s", "speedup_vs_plain_render", "judge_l1_mean",
                                            "l1_target_met", "heldout_l1_mean", "train_s")},
                 "roofline_training": None if survey is None else survey["roofline_training"],
-                "roofline": roofline, "roofline_other_precision": roofline_other,
+                "roofline": roofline, "roofline_other_kernels": roofline_other,
                 "by_precision": {("binary64" if p else "binary32"): by_prec[p] for p in (0, 1)},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 4 * K,
-                "gpu_launches_note": "one CUDA-graph launch per step holding 4 kernels of this library "
-                                     "(coordinate tables and escape kernel, binary32 and binary64)",
+                "gpu_launches": (5 if chosen["fp64"][0] > 0 else 4) * K,
+                "gpu_launches_note": "one CUDA-graph launch per step holding %d kernels of this library "
+                                     "(coordinate tables of each precision group, the binary32 escape kernel%s)"
+                                     % (5 if chosen["fp64"][0] > 0 else 4,
+                                        ", the certified binary32 pass of the binary64 frames and the binary64 "
+                                        "kernel on the pixels it lists" if chosen["fp64"][0] > 0 else
+                                        ", the binary64 escape kernel"),
                 "autotuned_variants": tuned,
                 "survey": survey,
                 "mismatch_rate_fp32_vs_fp64_sweep": mismatch,
