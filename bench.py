@@ -593,7 +593,6 @@ def main():
     # around each kernel (binary64: the certified binary32 pass, then the
     # binary64 kernel on the pixels it left)
     by_prec, kern = {}, {}
-    cert_stats = (0, 0)
     for prec in (0, 1):
         sp = jl.Batch([frames[i] for i in sub[prec]], palette=pal, variants=chosen, phases=True)
         for _ in range(2):
@@ -610,7 +609,7 @@ def main():
             sp.launch(stream)
             torch.cuda.synchronize()
             ph.append(sp.phase_ms())
-        ph = [statistics.mean(v[k] for v in ph) for k in range(3)]
+        ph = [statistics.mean(v[k] for v in ph) for k in range(4)]
         it = sum(iters[i] for i in sub[prec])
         px = sum(frames[i]["W"] * frames[i]["H"] for i in sub[prec])
         ops = OPS_PER_ITER * it / t
@@ -622,23 +621,30 @@ def main():
                  "escape_kernel<float>"] = dict(ms=ph[0], ops=OPS_PER_ITER * it, peak=peaks[0], prec="binary32",
                                                 bytes=6 * px, unit_note="8 binary32 lane ops per iteration")
         elif ph[1] > 0:
-            listed, listed_it = sp.cert_stats(stream)
-            cert_stats = (listed, listed_it)
-            by_prec[prec].update({"cert_listed_pixels": listed, "cert_listed_iterations": listed_it})
+            l32, l64, it_df, it64 = sp.cert_stats(stream)
+            by_prec[prec].update({"cert_listed_binary32_pass": l32, "cert_listed_to_binary64": l64,
+                                  "iterations_settled_double_float": it_df, "iterations_binary64": it64})
             kern["cert_kernel"] = dict(
-                ms=ph[1], ops=OPS_PER_ITER * (it - listed_it), peak=peaks[0], prec="binary32",
-                bytes=6 * (px - listed) + 8 * listed,
+                ms=ph[1], ops=OPS_PER_ITER * (it - it_df - it64), peak=peaks[0], prec="binary32",
+                bytes=6 * (px - l32) + 8 * l32,
                 unit_note="8 lane ops per binary64 iteration the certified binary32 pass settles (%d of %d); "
                           "the pass issues ~12 binary32 operations per step (the orbit with FMA plus its "
                           "error bound) and also runs the steps of the %d pixels it lists before their "
-                          "unsettled test" % (it - listed_it, it, listed))
+                          "unsettled test" % (it - it_df - it64, it, l32))
+            if ph[2] > 0:
+                kern["cert2_kernel"] = dict(
+                    ms=ph[2], ops=OPS_PER_ITER * it_df, peak=peaks[0], prec="binary32",
+                    bytes=8 * l32 + 6 * (l32 - l64) + 8 * l64,
+                    unit_note="8 lane ops per binary64 iteration the double-float pass settles (%d); the pass "
+                              "issues ~60 binary32 operations per step (float-pair orbit, exact product and sum "
+                              "splits, bound) on the %d pixels the binary32 pass lists" % (it_df, l32))
             kern["escape_kernel<double> (list)"] = dict(
-                ms=ph[2], ops=OPS_PER_ITER * listed_it, peak=peaks[1], prec="binary64", bytes=14 * listed,
+                ms=ph[3], ops=OPS_PER_ITER * it64, peak=peaks[1], prec="binary64", bytes=14 * l64,
                 unit_note="8 binary64 lane ops per iteration of the listed pixels; the kernel issues 6 of them "
                           "on the FP64 pipe: x+x is an exponent increment on the integer pipe and the escape "
                           "test is estimated in binary32 (exact binary64 replay near the threshold)")
         else:
-            kern["escape_kernel<double>"] = dict(ms=ph[2], ops=OPS_PER_ITER * it, peak=peaks[1], prec="binary64",
+            kern["escape_kernel<double>"] = dict(ms=ph[3], ops=OPS_PER_ITER * it, peak=peaks[1], prec="binary64",
                                                  bytes=6 * px, unit_note="8 binary64 lane ops per iteration")
         sp.close()
     for k, v in kern.items():

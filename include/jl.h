@@ -273,7 +273,9 @@ typedef struct {
                                bit 2: no certified binary32 pass for binary64 frames (every binary64
                                pixel then runs on the binary64 kernel; for comparisons);
                                bit 3: record timing events around the kernels inside the graph
-                               (jl_batch_phase_ms) */
+                               (jl_batch_phase_ms);
+                               bit 4: no double-float pass after the binary32 one (the binary64
+                               kernel renders every pixel the binary32 pass lists) */
     int32_t tune;           /* 1: for each precision group without an explicit variant, time
                                candidate kernels (the tuned and the default variant, the tile
                                kernels, a few lane-refill shapes for binary64) on the plan's own
@@ -314,22 +316,25 @@ int jl_batch_precisions(const jl_batch *b, int32_t *out, int32_t cap);
 /* Pixel totals of the binary32 and binary64 frames of the plan. */
 int jl_batch_pixels(const jl_batch *b, int64_t *fp32_pixels, int64_t *fp64_pixels);
 
-/* Binary64 pixels of the last launch that the certified binary32 pass left to
- * the binary64 kernel (its list length) and the sum of their counts (the
- * iterations that kernel ran); 0 and 0 when the plan has no binary64 frames or
- * the pass is off.  Synchronises `stream`; either pointer may be NULL.  The
- * certified pass runs a binary32 orbit with a rigorous bound on its distance
- * to the binary64 orbit and keeps a pixel only when the bound settles every
- * binary64 test of the pixel (the counts are the binary64 counts either way;
- * paper Sec. 3, precision of deep zooms). */
-int jl_batch_cert_stats(jl_batch *b, void *stream, int64_t *listed_out, int64_t *listed_iterations_out);
+/* Counters of the last launch's binary64 frames, into out[0..3]: the pixels
+ * the certified binary32 pass left unsettled; the pixels left to the binary64
+ * kernel after the double-float pass (equal to out[0] when that pass is off);
+ * the iterations (sum of counts) of the pixels the double-float pass settled;
+ * the iterations the binary64 kernel ran.  Zeros when the plan has no binary64
+ * frames or the passes are off.  Synchronises `stream`.  The certified passes
+ * run a binary32 (then double-float) orbit with a rigorous bound on its
+ * distance to the binary64 orbit and keep a pixel only when the bound settles
+ * every binary64 test of the pixel (the counts are the binary64 counts either
+ * way; paper Sec. 3, precision of deep zooms). */
+int jl_batch_cert_stats(jl_batch *b, void *stream, int64_t *out);
 
 /* Device time (ms) of the phases of the last completed launch of a plan
  * created with opts.variant_flags bit 3 (timing events recorded inside its
  * graph): ms_out[0] the binary32 escape kernel, ms_out[1] the certified
- * binary32 pass of the binary64 frames, ms_out[2] the binary64 escape kernel;
- * -1 for a phase the plan does not run.  The launch must have completed
- * (synchronise its stream first).  JL_EINVAL without the flag. */
+ * binary32 pass of the binary64 frames, ms_out[2] the double-float pass,
+ * ms_out[3] the binary64 escape kernel; -1 for a phase the plan does not run.
+ * The launch must have completed (synchronise its stream first).  JL_EINVAL
+ * without the flag. */
 int jl_batch_phase_ms(const jl_batch *b, float *ms_out);
 
 /* Frees the plan (after its launches have completed). */

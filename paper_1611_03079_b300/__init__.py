@@ -313,12 +313,13 @@ class Batch:
     (default False).  Outputs are allocated here as flat device buffers;
     `counts(i)`, `rgba(i)` and `hist(i)` return per-frame views.  `tune=True`
     lets the plan time candidate kernels on its own frames at creation.
-    `certify=False` turns off the certified binary32 pass of binary64 frames;
+    `certify=False` turns off the certified passes of binary64 frames,
+    `certify2=False` only the double-float one;
     `phases=True` records timing events around the kernels (`phase_ms`).
     """
 
     def __init__(self, frames, palette=None, chunk_len=0, variants=None, cycle_budget=0, tune=False,
-                 certify=True, phases=False):
+                 certify=True, certify2=True, phases=False):
         import torch
         self._L = _lib.lib()
         self.frames = list(frames)
@@ -364,6 +365,8 @@ class Batch:
             opts.variant_flags |= 4
         if phases:
             opts.variant_flags |= 8
+        if not certify2:
+            opts.variant_flags |= 16
         opts.cycle_budget = int(cycle_budget)
         opts.tune = 1 if tune else 0
         pal, pal_ptr = _palette_ptr(palette)
@@ -404,18 +407,20 @@ class Batch:
         return a.value, b.value
 
     def cert_stats(self, stream=None):
-        """(pixels, iterations) of the last launch's binary64 frames that the
-        certified binary32 pass left to the binary64 kernel."""
+        """For the last launch's binary64 frames: (pixels left by the binary32
+        pass, pixels left to the binary64 kernel, iterations the double-float
+        pass settled, iterations the binary64 kernel ran)."""
         import torch
         st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
-        v, it = ctypes.c_int64(0), ctypes.c_int64(0)
-        check(self._L.jl_batch_cert_stats(self._h, st, ctypes.byref(v), ctypes.byref(it)))
-        return v.value, it.value
+        v = (ctypes.c_int64 * 4)()
+        check(self._L.jl_batch_cert_stats(self._h, st, v))
+        return tuple(int(x) for x in v)
 
     def phase_ms(self):
-        """Device ms of the last completed launch: [binary32 kernel, certified
-        pass, binary64 kernel] (-1 where absent); needs phases=True."""
-        ms = (ctypes.c_float * 3)()
+        """Device ms of the last completed launch: [binary32 kernel, binary32
+        certified pass, double-float pass, binary64 kernel] (-1 where absent);
+        needs phases=True."""
+        ms = (ctypes.c_float * 4)()
         check(self._L.jl_batch_phase_ms(self._h, ms))
         return [float(v) for v in ms]
 

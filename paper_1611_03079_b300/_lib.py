@@ -89,7 +89,7 @@ SIGNATURES = {
     "jl_batch_status": (ctypes.c_int, [_vp, _vp, _vp]),
     "jl_batch_precisions": (ctypes.c_int, [_vp, _vp, _i32]),
     "jl_batch_pixels": (ctypes.c_int, [_vp, _vp, _vp]),
-    "jl_batch_cert_stats": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "jl_batch_cert_stats": (ctypes.c_int, [_vp, _vp, _vp]),
     "jl_batch_phase_ms": (ctypes.c_int, [_vp, _vp]),
     "jl_batch_destroy": (None, [_vp]),
     "jl_render_batch": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),

@@ -105,7 +105,7 @@ def sweep_plan(a):
     print(json.dumps({"frames": len(frames), "pixels": pix, "output_bytes": 6 * pix, "iterations": iters,
                       "ms": times, "best_ms": min(times), "giter_s": iters / (min(times) * 1e-3) / 1e9,
                       "variant": list(b.variant(prec)), "status": b.status(),
-                      "cert_listed_pixels_iterations": list(b.cert_stats())}))
+                      "cert_stats": list(b.cert_stats())}))
     b.close()
 
 

@@ -146,8 +146,10 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
     F->tile_begin = 0;
     F->precision = prec;
     F->colour_magic = (1ull << 40) / (uint64_t)max_iter + 1ull;
-    if (prec == JL_FP64 && mode == JL_JULIA)
+    if (prec == JL_FP64 && mode == JL_JULIA) {
         F->cert_ec = cert_error_constant(F->cr, F->ci, F->cr32, F->ci32);
+        cert2_frame_constants(F->cr, F->ci, F->cr32, F->ci32, &F->cr_lo32, &F->ci_lo32, &F->cert2_kc);
+    }
     // Monotone escape is proven for |C| <= 2 - 2^-12 (Julia); Mandelbrot pixels
     // are classified one by one in the kernel.  |C|^2 < 3.99 is inside that.
     if (mode == JL_JULIA) {
@@ -167,17 +169,18 @@ int make_frame(double cr, double ci, const jl_rect &rect, int W, int H, int max_
 }
 
 // Launches the escape kernel of one frame whose coordinate tables (F.xs,
-// F.ys) are already filled: clears the 32-byte control block `ctl` (work
-// counter, status, the certified pass's list count and list counter) and the
-// histogram, runs the kernel and finalises the histogram.  A binary64 frame
-// with binary32 tables and a list of cert_cap >= W * H entries takes the
-// certified binary32 pass.  All pointers are device pointers.
+// F.ys) are already filled: clears the 48-byte control block `ctl` (work
+// counter, status, the certified passes' list counts and list counters) and
+// the histogram, runs the kernel and finalises the histogram.  A binary64
+// frame with binary32 tables and a list of cert_cap >= W * H entries takes the
+// certified binary32 pass (and the double-float pass with a second list).
+// All pointers are device pointers.
 int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStream_t st, const Variant *vopt,
-                 uint64_t *cert_list, int64_t cert_cap)
+                 uint64_t *cert_list, int64_t cert_cap, uint64_t *cert_list2)
 {
     unsigned long long *counter = static_cast<unsigned long long *>(ctl);
     int32_t *status = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ctl) + 8);
-    cudaError_t e = cudaMemsetAsync(ctl, 0, 32, st);
+    cudaError_t e = cudaMemsetAsync(ctl, 0, 48, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "cudaMemsetAsync(counter)");
     if (F.hist_bins) {
@@ -200,6 +203,11 @@ int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStre
         a.cert_cap = cert_cap;
         a.cert_count = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(ctl) + 16);
         a.list_counter = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(ctl) + 24);
+        if (cert_list2) {
+            a.cert_list2 = cert_list2;
+            a.cert_count2 = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(ctl) + 32);
+            a.list2_counter = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(ctl) + 40);
+        }
     } else {
         F.xs32 = nullptr;
         F.ys32 = nullptr;
@@ -233,9 +241,9 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
     const size_t esz = prec == JL_FP64 ? 8 : 4;
     const size_t coord_bytes = ((size_t)F.W + (size_t)F.H) * esz;
     const size_t coord_pad = (coord_bytes + 255) & ~(size_t)255;
-    // binary64: binary32 tables and the list of the certified pass (8 B per pixel)
+    // binary64: binary32 tables and the two lists of the certified passes (8 B per pixel each)
     const size_t c32_pad = prec == JL_FP64 ? ((((size_t)F.W + (size_t)F.H) * 4 + 255) & ~(size_t)255) : 0;
-    const size_t list_bytes = prec == JL_FP64 ? (size_t)F.W * (size_t)F.H * 8 : 0;
+    const size_t list_bytes = prec == JL_FP64 ? (size_t)F.W * (size_t)F.H * 16 : 0;
     const size_t scratch_bytes = coord_pad + 256 + c32_pad + list_bytes;
     void *scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, st);
@@ -255,7 +263,8 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
     if (e != cudaSuccess)
         rc = cuda_fail(e, "coords kernel launch");
     if (rc == JL_OK)
-        rc = launch_frame(F, prec, palette, base + coord_pad, st, vopt, list, (int64_t)F.W * F.H);
+        rc = launch_frame(F, prec, palette, base + coord_pad, st, vopt, list, (int64_t)F.W * F.H,
+                          list ? list + (size_t)F.W * F.H : nullptr);
     cudaError_t e2 = cudaFreeAsync(scratch, st);
     if (rc == JL_OK && e2 != cudaSuccess)
         rc = cuda_fail(e2, "cudaFreeAsync(scratch)");

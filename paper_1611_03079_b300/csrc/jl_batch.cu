@@ -33,16 +33,18 @@ struct jl_batch {
     int n_group[2] = {0, 0};
     int64_t chunks[2] = {0, 0};
     void *coords_dev = nullptr;
-    uint64_t *list_dev = nullptr;          // binary64 group: the certified pass's list (8 B per pixel)
+    uint64_t *list_dev = nullptr;          // binary64 group: the certified passes' two lists (8 B per pixel each)
     // control words, zeroed per launch: work counters of the two groups (0, 8),
-    // status (16), the certified pass's list count (32), list counter (40) and
-    // the listed pixels' iterations (48)
+    // status (16), the binary32 pass's list count (32), the binary64 kernel's
+    // list counter (40), the binary64 kernel's iterations (48), the
+    // double-float pass's list count (56), its counter on the first list (64)
+    // and the iterations of the pixels it settles (72)
     uint8_t *ctl_dev = nullptr;
     // opts.variant_flags bit 3: timing events recorded inside the graph around
     // the binary32 kernel (0, 1) and the binary64 kernels (2, 3 after the
-    // certified pass, 4)
-    bool phases = false, cert_used = false;
-    cudaEvent_t ph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // binary32 pass, 5 after the double-float pass, 4)
+    bool phases = false, cert_used = false, cert2_used = false;
+    cudaEvent_t ph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t s0 = nullptr, s1 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
@@ -197,7 +199,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
         e = cudaMalloc(&b->ctl_dev, 256);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(control words)"); break; }
         if (b->pixels[1] > 0) {
-            e = cudaMalloc(&b->list_dev, (size_t)b->pixels[1] * sizeof(uint64_t));
+            e = cudaMalloc(&b->list_dev, (size_t)b->pixels[1] * sizeof(uint64_t) * 2);
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(certified pass list)"); break; }
         }
         e = cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking);
@@ -208,7 +210,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
         b->phases = (o.variant_flags & 8) != 0;
-        for (int k = 0; k < 5 && e == cudaSuccess && b->phases; ++k)
+        for (int k = 0; k < 6 && e == cudaSuccess && b->phases; ++k)
             e = cudaEventCreate(&b->ph[k]);
         if (e != cudaSuccess) { rc = cuda_fail(e, "stream/event creation"); break; }
 
@@ -307,6 +309,12 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 x.cert_count = reinterpret_cast<unsigned long long *>(b->ctl_dev + 32);
                 x.list_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 40);
                 x.list_iters = reinterpret_cast<unsigned long long *>(b->ctl_dev + 48);
+                if (!(o.variant_flags & 16)) {
+                    x.cert_list2 = b->list_dev + b->pixels[1];
+                    x.cert_count2 = reinterpret_cast<unsigned long long *>(b->ctl_dev + 56);
+                    x.list2_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 64);
+                    x.cert2_iters = reinterpret_cast<unsigned long long *>(b->ctl_dev + 72);
+                }
             }
             // output specialisation: 1 = every frame uint16 counts + RGBA8, 2 =
             // every frame RGBA8 only, 3 = every frame uint8 counts + RGBA8
@@ -367,7 +375,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                     const EscapeArgs x = make_args(g, v);
                     float ms = 0.f;
                     for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-                        e = cudaMemsetAsync(b->ctl_dev, 0, 64, b->s0);
+                        e = cudaMemsetAsync(b->ctl_dev, 0, 80, b->s0);
                         if (e == cudaSuccess)
                             e = cudaEventRecord(t0, b->s0);
                         if (e == cudaSuccess)
@@ -401,7 +409,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             args[g] = make_args(g, b->variant[g]);
         e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamBeginCapture"); break; }
-        cudaError_t ce = cudaMemsetAsync(b->ctl_dev, 0, 64, b->s0);
+        cudaError_t ce = cudaMemsetAsync(b->ctl_dev, 0, 80, b->s0);
         // region covering: coordinate tables of every frame, each launch
         for (int g = 0; g < 2 && ce == cudaSuccess; ++g)
             if (b->n_group[g])
@@ -410,13 +418,14 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             if (b->n_group[g])
                 ce = launch_hist_zero(b->frames_dev[g], b->n_group[g], b->s0);
         b->cert_used = b->n_group[1] && args[1].cert_list && b->variant[1].ppt > 0 && args[1].tile_frame;
+        b->cert2_used = b->cert_used && args[1].cert_list2;
         // one group's kernels on stream s, with its timing events when asked for
         auto group = [&](int g, cudaStream_t s) -> cudaError_t {
             cudaEvent_t e0 = b->phases ? b->ph[g ? 2 : 0] : nullptr, e1 = b->phases ? b->ph[g ? 4 : 1] : nullptr;
-            cudaEvent_t mid = (b->phases && g) ? b->ph[3] : nullptr;
+            cudaEvent_t mid = (b->phases && g) ? b->ph[3] : nullptr, mid2 = (b->phases && g) ? b->ph[5] : nullptr;
             cudaError_t r = e0 ? cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal) : cudaSuccess;
             if (r == cudaSuccess)
-                r = launch_escape(args[g], g, b->variant[g], sms, s, mid);
+                r = launch_escape(args[g], g, b->variant[g], sms, s, mid, mid2);
             if (r == cudaSuccess && e1)
                 r = cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
             return r;
@@ -493,21 +502,21 @@ int jl_batch_status(jl_batch *b, void *stream, int32_t *status_out)
     return JL_OK;
 }
 
-int jl_batch_cert_stats(jl_batch *b, void *stream, int64_t *listed_out, int64_t *listed_iterations_out)
+int jl_batch_cert_stats(jl_batch *b, void *stream, int64_t *out)
 {
-    if (!b)
-        return fail(JL_EINVAL, "invalid batch plan");
+    if (!b || !out)
+        return fail(JL_EINVAL, "invalid arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    unsigned long long v[3] = {0, 0, 0};
-    cudaError_t e = cudaMemcpyAsync(v, b->ctl_dev + 32, 24, cudaMemcpyDeviceToHost, st);
+    unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(v, b->ctl_dev + 32, 48, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
-        return cuda_fail(e, "reading the certified pass's counters");
-    if (listed_out)
-        *listed_out = (int64_t)v[0];
-    if (listed_iterations_out)
-        *listed_iterations_out = (int64_t)v[2];
+        return cuda_fail(e, "reading the certified passes' counters");
+    out[0] = (int64_t)v[0];
+    out[1] = (int64_t)(b->cert2_used ? v[3] : v[0]);
+    out[2] = (int64_t)v[5];
+    out[3] = (int64_t)v[2];
     return JL_OK;
 }
 
@@ -517,7 +526,7 @@ int jl_batch_phase_ms(const jl_batch *b, float *ms_out)
         return fail(JL_EINVAL, "invalid arguments");
     if (!b->phases)
         return fail(JL_EINVAL, "the plan was created without phase events (opts.variant_flags bit 3)");
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 4; ++k)
         ms_out[k] = -1.f;
     cudaError_t e = cudaSuccess;
     if (b->n_group[0])
@@ -525,10 +534,12 @@ int jl_batch_phase_ms(const jl_batch *b, float *ms_out)
     if (e == cudaSuccess && b->n_group[1]) {
         if (b->cert_used) {
             e = cudaEventElapsedTime(&ms_out[1], b->ph[2], b->ph[3]);
+            if (e == cudaSuccess && b->cert2_used)
+                e = cudaEventElapsedTime(&ms_out[2], b->ph[3], b->ph[5]);
             if (e == cudaSuccess)
-                e = cudaEventElapsedTime(&ms_out[2], b->ph[3], b->ph[4]);
+                e = cudaEventElapsedTime(&ms_out[3], b->ph[5], b->ph[4]);
         } else {
-            e = cudaEventElapsedTime(&ms_out[2], b->ph[2], b->ph[4]);
+            e = cudaEventElapsedTime(&ms_out[3], b->ph[2], b->ph[4]);
         }
     }
     if (e != cudaSuccess)

@@ -1468,6 +1468,295 @@ __global__ void __launch_bounds__(256, 4) cert_kernel(const __grid_constant__ Es
 }
 
 // ---------------------------------------------------------------------------
+// Second certified pass: double-float orbit over the binary32 pass's list.
+//
+// The pixels the binary32 pass cannot settle are mostly escaping pixels whose
+// orbits stay long near the Julia set: the distance bound grows with the
+// derivative of the iterate and reaches the test's margin after ~200 steps.
+// This pass carries W as pairs of binary32 values (x = xh + xl, ~48 bits) so
+// that the bound starts and grows ~2^24 times lower, with the same rule: a
+// test is decided from W only when [(|W| - E)^2, (|W| + E)^2] lies on one side
+// of 4, and a pixel with an unsettled test goes on to the binary64 kernel.
+//
+// Step (u = 2^-24; every operation round to nearest, products split exactly
+// with FMA: a*b = p + e, e = fma(a, b, -p); sums of two values split exactly
+// by TwoSum (6 operations) where the exact rounding error is needed):
+//   x^2 - y^2 + cr:  TwoSum(p1 - p2) -> (t, et), TwoSum(t + crh) -> (sx, esx),
+//                    lx = ((fma(-2yh, yl, fma(2xh, xl, crl)) + (e1 - e2)) + et) + esx
+//   2xy + ci:        TwoSum(2 p3 + cih) -> (sy, esy),
+//                    ly = fma(2, e3, fma(2xl, yh, fma(2xh, yl, cil))) + esy
+//   renormalised:    (xh', xl') = TwoSum(sx + lx), (yh', yl') = TwoSum(sy + ly)
+// Exact real and imaginary parts differ from sx + lx and sy + ly only by the
+// roundings of the ten low-part operations (each at most u times the
+// magnitude of its terms) and the dropped xl^2 - yl^2 and 2 xl yl.  With
+// Lambda = |xl| + |yl| and |xh| + |yh| <= 2 sqrt(2) (|Wh| < 2 after a pass):
+//   delta <= 6.01 u (2 (|xh| + |yh|) Lambda + |Cl|_1 + u (20.1 + |Ch|_1)) + Lambda^2
+//         <= Lambda (36 u + Lambda) + 6.01 u |Cl|_1 + 6.01 u^2 (20.1 + |Ch|_1) + 2^-145
+// (the e terms are at most u times their products and sums, |t|, p1 + p2 and
+// 2|p3| <= |Wh|^2 < 4, |sx| + |sy| <= 8 + |Ch|_1).  Test: Wh = xh + i yh is
+// within Et = E + Lambda of Z, and the binary32 pass's test applies to
+// (Wh, Et).  Bound: E' = E (2 (s + Lambda) + E) + delta + |C - Cdf|_1 +
+// binary64 step rounding (2^-48 + 2^-52 |C|_1).  KC collects the W-independent
+// terms: per frame for Julia (`cert2_frame_constants`), per pixel for
+// Mandelbrot (C = the pixel as a float pair).  Initial E: the pixel's
+// coordinates as float pairs, u (1 + 2^-20) Lambda_0 + 2^-140 (Julia), 0
+// (Mandelbrot: Z_0 = 0).
+// ---------------------------------------------------------------------------
+static constexpr float kDfKL = 0x1.2p-19f;    // 36 u
+static constexpr float kDfMl = 0x1.dp-22f;    // 7.25 u: Mandelbrot KC per unit of |Cl|_1
+static constexpr float kDfMh = 0x1.9p-46f;    // 6.25 u^2: Mandelbrot KC per unit of |Ch|_1
+static constexpr float kDfM0 = 0x1p-41f;      // 128 u^2: Mandelbrot KC constant
+
+void cert2_frame_constants(double cr, double ci, float cr32, float ci32, float *cr_lo, float *ci_lo, float *kc)
+{
+    // cr - cr32 is exact (Sterbenz); so is its difference with its own rounding
+    const double dr = cr - (double)cr32, di = ci - (double)ci32;
+    *cr_lo = (float)dr;
+    *ci_lo = (float)di;
+    const double u = 0x1p-24;
+    const double dC = fabs(dr - (double)*cr_lo) + fabs(di - (double)*ci_lo);
+    const double ah = fabs((double)cr32) + fabs((double)ci32), al = fabs((double)*cr_lo) + fabs((double)*ci_lo);
+    const double v = (6.01 * u * al + 6.01 * u * u * (20.1 + ah) + dC + 0x1p-48 + 0x1.03p-52 * (ah + al) +
+                      0x1p-139) * (1.0 + 0x1p-40);
+    float f = (float)v;
+    if ((double)f < v)
+        f = nextafterf(f, INFINITY);
+    *kc = f;
+}
+
+// s + e = a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// State of the double-float pass for one pixel.
+struct DfState {
+    float xh, xl, yh, yl, e;
+};
+
+// The test of the double-float pass: 1 = a certified pass, 0 = a certified
+// escape, -1 = not settled.  s and lam are returned for the bound update.
+__device__ __forceinline__ int df_test(const DfState &w, float &s, float &lam)
+{
+    lam = __fadd_ru(fabsf(w.xl), fabsf(w.yl));
+    const float et = __fadd_ru(w.e, lam);
+    const float r = __fmaf_rn(w.xh, w.xh, __fmul_rn(w.yh, w.yh));
+    s = sqrt_approx(r);
+    const float ge = __fmaf_ru(et, __fmaf_ru(kCertS2, s, et), 0x1p-60f);
+    if (__fmaf_ru(r, kCertR1, ge) < 4.0f)
+        return 1;
+    const float m = __fmul_ru(__fmul_ru(kCertS2, s), et);
+    return __fmaf_rd(r, kCertR0, -m) > 4.0f ? 0 : -1;
+}
+
+// One double-float step with its bound update (after a certified pass).
+__device__ __forceinline__ void df_update(DfState &w, float s, float lam, float crh, float crl, float cih, float cil,
+                                          float kc)
+{
+    const float p1 = __fmul_rn(w.xh, w.xh), e1 = __fmaf_rn(w.xh, w.xh, -p1);
+    const float p2 = __fmul_rn(w.yh, w.yh), e2 = __fmaf_rn(w.yh, w.yh, -p2);
+    const float p3 = __fmul_rn(w.xh, w.yh), e3 = __fmaf_rn(w.xh, w.yh, -p3);
+    float t, et, sx, esx, sy, esy;
+    two_sum(p1, -p2, t, et);
+    two_sum(t, crh, sx, esx);
+    two_sum(__fadd_rn(p3, p3), cih, sy, esy);
+    const float x2 = __fadd_rn(w.xh, w.xh), y2 = __fadd_rn(w.yh, w.yh);
+    float lx = __fmaf_rn(-y2, w.yl, __fmaf_rn(x2, w.xl, crl));
+    lx = __fadd_rn(__fadd_rn(__fadd_rn(lx, __fsub_rn(e1, e2)), et), esx);
+    float ly = __fmaf_rn(2.0f, e3, __fmaf_rn(__fadd_rn(w.xl, w.xl), w.yh, __fmaf_rn(x2, w.yl, cil)));
+    ly = __fadd_rn(ly, esy);
+    // bound first (it uses the old E and Lambda)
+    const float g2 = __fmaf_ru(kCertS2, s, __fmaf_ru(2.0f, lam, w.e));
+    w.e = __fmaf_ru(w.e, g2, __fmaf_ru(lam, __fadd_ru(kDfKL, lam), kc));
+    two_sum(sx, lx, w.xh, w.xl);
+    two_sum(sy, ly, w.yh, w.yl);
+}
+
+// Up to four tests of the double-float pass from test n (limit mi): the
+// pixel's count (>= 0) when settled, -1 when a test is not settled, -2 when
+// the tests passed so far leave it live (n advanced).  Four tests run as a
+// block with one branch; a block with a test that is not a certified pass is
+// replayed one test at a time from its start.
+__device__ __forceinline__ int df_run4(DfState &w, int &n, int mi, float crh, float crl, float cih, float cil, float kc)
+{
+    if (n >= mi)
+        return mi;
+    if (n + 4 <= mi) {
+        const DfState w0 = w;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float s, lam;
+            ok &= df_test(w, s, lam) == 1;
+            df_update(w, s, lam, crh, crl, cih, cil, kc);
+        }
+        if (ok) {
+            n += 4;
+            return n >= mi ? mi : -2;
+        }
+        w = w0;
+    }
+    for (int k = 0; k < 4 && n < mi; ++k, ++n) {
+        float s, lam;
+        const int rc = df_test(w, s, lam);
+        if (rc == 0)
+            return n;
+        if (rc < 0)
+            return -1;
+        df_update(w, s, lam, crh, crl, cih, cil, kc);
+    }
+    return n >= mi ? mi : -2;
+}
+
+// Lane-refill kernel of the double-float pass: warps take 32-entry pieces of
+// the binary32 pass's list from *list2_counter; a lane whose pixel is settled
+// (stored) or not settled (appended to cert_list2, one counter increment per
+// warp and round of blocks) takes the next entry of its warp's piece.  A full
+// second list (never, when cert_cap >= the launch's pixels) leaves its pixel
+// to exact binary64 steps here.
+template <bool BATCH, int OUT>
+__global__ void __launch_bounds__(256) cert2_kernel(const __grid_constant__ EscapeArgs a)
+{
+    __shared__ uint32_t pal[256];
+    extern __shared__ uint32_t hbins[];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        pal[t] = a.palette[t];
+    const int nb = (!BATCH && a.hist_smem) ? a.single.max_iter + 1 : 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x)
+        hbins[t] = 0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long t_start = clock64();
+    long long n1 = (long long)*a.cert_count;
+    if (n1 > a.cert_cap)
+        n1 = a.cert_cap;
+    const long long pieces = (n1 + 31) >> 5;
+    unsigned long long next_c = 0;
+    if (lane == 0)
+        next_c = atomicAdd(a.list2_counter, 1ull);
+    long long q_base = 0;
+    int q_pos = 0, q_end = 0;
+    bool q_done = false;
+
+    DfState w{0.f, 0.f, 0.f, 0.f, 0.f};
+    float crh = 0.f, crl = 0.f, cih = 0.f, cil = 0.f, kc = 0.f;
+    int n = 0, mi = 0, fr = 0, pi = 0, pj = 0;
+    bool live = false;
+
+    for (;;) {
+        // refill the lanes without a pixel from the warp's piece of the list
+        unsigned want = __ballot_sync(FULL, !live);
+        while (want && !q_done) {
+            if (q_pos >= q_end) {
+                const unsigned long long c = __shfl_sync(FULL, next_c, 0);
+                bool over = a.cycle_budget > 0 && (clock64() - t_start) > a.cycle_budget;
+                over = __any_sync(FULL, over);
+                if ((long long)c >= pieces || over) {
+                    if (over && lane == 0 && a.status && (long long)c < pieces)
+                        atomicExch(a.status, (int)JL_ETIMEOUT);
+                    q_done = true;
+                    break;
+                }
+                if (lane == 0)
+                    next_c = atomicAdd(a.list2_counter, 1ull);
+                q_base = (long long)c << 5;
+                q_pos = 0;
+                q_end = (int)min(32ll, n1 - q_base);
+                continue;
+            }
+            const int take = min(q_end - q_pos, __popc(want));
+            const int rank = __popc(want & lt_mask);
+            const bool got = ((want >> lane) & 1u) && rank < take;
+            if (got) {
+                const uint64_t ent = a.cert_list[q_base + q_pos + rank];
+                fr = (int)(ent >> 32);
+                pj = (int)((ent >> 16) & 0xffffu);
+                pi = (int)(ent & 0xffffu);
+                const Frame &F = BATCH ? a.frames[fr] : a.single;
+                const double x64 = static_cast<const double *>(F.xs)[pi];
+                const double y64 = static_cast<const double *>(F.ys)[pj];
+                // the coordinates as float pairs (x64 - xh is exact in binary64)
+                const float xh = __double2float_rn(x64), yh = __double2float_rn(y64);
+                const float xl = __double2float_rn(__dsub_rn(x64, (double)xh));
+                const float yl = __double2float_rn(__dsub_rn(y64, (double)yh));
+                const float l0 = __fadd_ru(fabsf(xl), fabsf(yl));
+                mi = F.max_iter;
+                n = 0;
+                if (F.mode == JL_JULIA) {
+                    w = DfState{xh, xl, yh, yl, __fmaf_ru(kCertE0, l0, 0x1p-140f)};
+                    crh = F.cr32;
+                    crl = F.cr_lo32;
+                    cih = F.ci32;
+                    cil = F.ci_lo32;
+                    kc = F.cert2_kc;
+                } else {
+                    w = DfState{0.f, 0.f, 0.f, 0.f, 0.f};
+                    crh = xh;
+                    crl = xl;
+                    cih = yh;
+                    cil = yl;
+                    kc = __fmaf_ru(kDfMl, l0, __fmaf_ru(kDfMh, __fadd_ru(fabsf(xh), fabsf(yh)), kDfM0));
+                }
+                live = true;
+            }
+            want &= ~__ballot_sync(FULL, got);
+            q_pos += take;
+        }
+        if (!__any_sync(FULL, live))
+            break;
+        int res = -2;
+        if (live)
+            res = df_run4(w, n, mi, crh, crl, cih, cil, kc);
+        const bool und = live && res == -1;
+        const unsigned um = __ballot_sync(FULL, und);
+        if (um) {
+            unsigned long long base = 0;
+            if (lane == 0)
+                base = atomicAdd(a.cert_count2, (unsigned long long)__popc(um));
+            base = __shfl_sync(FULL, base, 0);
+            if (und) {
+                const unsigned long long k = base + (unsigned long long)__popc(um & lt_mask);
+                if (k < (unsigned long long)a.cert_cap) {
+                    a.cert_list2[k] = ((uint64_t)(uint32_t)fr << 32) | ((uint64_t)(uint32_t)pj << 16) | (uint32_t)pi;
+                } else {
+                    // no room in the second list: exact binary64 steps here
+                    const Frame &F = BATCH ? a.frames[fr] : a.single;
+                    const double x64 = static_cast<const double *>(F.xs)[pi];
+                    const double y64 = static_cast<const double *>(F.ys)[pj];
+                    res = F.mode == JL_JULIA ? exact_from(x64, y64, F.cr, F.ci, 0, mi)
+                                             : exact_from(0.0, 0.0, x64, y64, 0, mi);
+                }
+            }
+        }
+        if (live && res >= 0) {
+            const Frame &F = BATCH ? a.frames[fr] : a.single;
+            store_result<BATCH, OUT>(a, pal, hbins, fr, (uint32_t)pj * (uint32_t)F.W + (uint32_t)pi, res, mi, lt_mask);
+            if (a.cert2_iters) {
+                const unsigned act = __activemask();
+                const unsigned tot = __reduce_add_sync(act, (unsigned)res);
+                if ((act & lt_mask) == 0)
+                    atomicAdd(a.cert2_iters, (unsigned long long)tot);
+            }
+        }
+        if (res != -2)
+            live = false;
+    }
+    if (nb) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+            const uint32_t v = hbins[t];
+            if (v)
+                atomicAdd(&a.single.hist_bins[t], v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 // Resident CTAs per SM of a kernel for a block size and dynamic shared
@@ -1747,6 +2036,30 @@ static cudaError_t launch_cert(const EscapeArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// The double-float pass over the binary32 pass's list (persistent lane-refill
+// kernel; the list's length is known only on the device).
+static cudaError_t launch_cert2(const EscapeArgs &a, int num_sms, cudaStream_t st)
+{
+    size_t smem = 0;
+    if (a.hist_smem && !a.frames)
+        smem = (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
+    auto kern = a.frames ? cert2_kernel<true, 0> : cert2_kernel<false, 0>;
+    if (launch_out_mode(a) == 1)
+        kern = a.frames ? cert2_kernel<true, 1> : cert2_kernel<false, 1>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = occupancy_per_sm(reinterpret_cast<const void *>(kern), 256, smem, &per_sm);
+    if (e != cudaSuccess)
+        return e;
+    const long long grid = (long long)(num_sms > 0 ? num_sms : 148) * (per_sm > 0 ? per_sm : 1);
+    kern<<<(unsigned)grid, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 // Whether a binary64 launch with variant v takes the certified pass: a
 // lane-refill variant, a list, the counters, and binary32 tables with tile
 // tables (batches) or in the single frame.
@@ -1758,17 +2071,27 @@ static bool use_cert(const EscapeArgs &a, int precision, const Variant &v)
 }
 
 cudaError_t launch_escape(const EscapeArgs &a_in, int precision, const Variant &v, int num_sms, cudaStream_t st,
-                          cudaEvent_t mid)
+                          cudaEvent_t mid, cudaEvent_t mid2)
 {
     EscapeArgs a = a_in;
     if (use_cert(a, precision, v)) {
         cudaError_t e = launch_cert(a, st);
         if (e == cudaSuccess && mid)
             e = cudaEventRecordWithFlags(mid, st, cudaEventRecordExternal);
+        const bool two = a.cert_list2 && a.cert_count2 && a.list2_counter;
+        if (e == cudaSuccess && two)
+            e = launch_cert2(a, num_sms, st);
+        if (e == cudaSuccess && mid2)
+            e = cudaEventRecordWithFlags(mid2, st, cudaEventRecordExternal);
         if (e != cudaSuccess)
             return e;
         EscapeArgs b = a;
         b.chunk_counter = a.list_counter;
+        if (two) {
+            // the binary64 kernel renders the double-float pass's list
+            b.cert_list = a.cert_list2;
+            b.cert_count = a.cert_count2;
+        }
         size_t smem = 256 * sizeof(uint32_t);
         if (b.hist_smem && !b.frames)
             smem += (size_t)(b.single.max_iter + 1) * sizeof(uint32_t);

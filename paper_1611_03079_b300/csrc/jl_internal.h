@@ -43,7 +43,9 @@ struct Frame {
     const float *xs32;             // binary64 frames: the tables rounded once to binary32 (certified
     const float *ys32;             // binary32 pass), written with xs/ys; NULL: no certified pass
     float cert_ec;                 // binary64 Julia frames: per-step error constant of the certified pass
-    int32_t pad3;
+    float cr_lo32, ci_lo32;        // binary64 Julia frames: C - (cr32, ci32) rounded to binary32 (C as
+                                   // float pairs for the double-float pass)
+    float cert2_kc;                // binary64 Julia frames: per-step constant of the double-float pass
 };
 
 // Launch parameters of the escape kernels (passed by value as a grid constant).
@@ -71,6 +73,14 @@ struct EscapeArgs {
     unsigned long long *cert_count;    // zeroed before the launch
     unsigned long long *list_counter;  // zeroed before the launch
     unsigned long long *list_iters;    // zeroed before the launch, or NULL: iterations of the listed pixels
+    // second certified pass (double-float) over cert_list: the pixels it cannot
+    // settle go to cert_list2 (cap cert_cap, count *cert_count2), which the
+    // binary64 kernel then renders instead of cert_list; it takes 32-entry
+    // pieces of cert_list from *list2_counter.  NULL: no second pass.
+    uint64_t *cert_list2;
+    unsigned long long *cert_count2;   // zeroed before the launch
+    unsigned long long *list2_counter; // zeroed before the launch
+    unsigned long long *cert2_iters;   // zeroed before the launch, or NULL: iterations the second pass settles
     uint32_t palette[256];
     Frame single;
 };
@@ -91,10 +101,10 @@ int cuda_fail(cudaError_t e, const char *what);
 // Launchers implemented in jl_escape.cu.
 // `frames_dev` is a device table of n frames, or NULL with `single` used instead.
 cudaError_t launch_coords(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st);
-// A binary64 launch with the certified pass records `mid` (when not NULL)
-// between the pass and the binary64 kernel.
+// A binary64 launch with the certified passes records `mid` (when not NULL)
+// after the binary32 pass and `mid2` after the double-float pass.
 cudaError_t launch_escape(const EscapeArgs &args, int precision, const Variant &v, int num_sms,
-                          cudaStream_t st, cudaEvent_t mid = nullptr);
+                          cudaStream_t st, cudaEvent_t mid = nullptr, cudaEvent_t mid2 = nullptr);
 cudaError_t launch_hist_finalize(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st);
 cudaError_t launch_hist_zero(const Frame *frames_dev, int n, cudaStream_t st);
 bool variant_supported(int precision, int ppt, int unroll);
@@ -112,17 +122,21 @@ int default_palette_bytes(uint8_t *out);
 int select_precision(const jl_rect &r, int W, int H);
 
 // Launches the escape kernel of one frame whose coordinate tables are filled:
-// clears the 32-byte control block `ctl` (work counter, status, the certified
-// pass's list count and list counter) and the histogram, runs the tuned (or
+// clears the 48-byte control block `ctl` (work counter, status, the certified
+// passes' list counts and list counters) and the histogram, runs the tuned (or
 // `vopt`'s) variant, finalises the histogram.  Binary64 frames with binary32
 // tables (F.xs32) and a list of cert_cap >= W * H entries take the certified
-// binary32 pass first.  Allocates nothing.
+// binary32 pass first, and the double-float pass when a second list of the
+// same capacity is given.  Allocates nothing.
 int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStream_t st, const Variant *vopt,
-                 uint64_t *cert_list = nullptr, int64_t cert_cap = 0);
+                 uint64_t *cert_list = nullptr, int64_t cert_cap = 0, uint64_t *cert_list2 = nullptr);
 
 // Per-step error constant of the certified binary32 pass for a binary64
 // Julia frame (see jl_escape.cu), rounded up to binary32.
 float cert_error_constant(double cr, double ci, float cr32, float ci32);
+// The low parts and the per-step constant of the double-float pass for a
+// binary64 Julia frame (see jl_escape.cu).
+void cert2_frame_constants(double cr, double ci, float cr32, float ci32, float *cr_lo, float *ci_lo, float *kc);
 
 // Default variants, and the autotuned one when the tuner has run.
 Variant default_variant(int precision, int max_iter);

@@ -61,8 +61,8 @@ struct jl_host_plan {
     void *slots = nullptr;
     size_t slot_bytes = 0;
     void *tables = nullptr;  // coordinate tables, a 256-byte control block per frame and per extra band
-    // binary64 units: the certified pass's list of each render stream (units
-    // on one stream run one after the other), list_cap entries each
+    // binary64 units: the certified passes' two lists of each render stream
+    // (units on one stream run one after the other), list_cap entries each
     uint64_t *lists = nullptr;
     int64_t list_cap = 0;
 };
@@ -230,7 +230,7 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
         e = cudaMalloc(&p->tables, table_bytes);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(coordinate tables)"); break; }
         if (p->list_cap > 0) {
-            e = cudaMalloc(&p->lists, (size_t)p->list_cap * sizeof(uint64_t) * (size_t)nr);
+            e = cudaMalloc(&p->lists, (size_t)p->list_cap * sizeof(uint64_t) * 2 * (size_t)nr);
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(certified pass lists)"); break; }
         }
         // where each frame's coordinate tables live (jl_host_plan_run fills them)
@@ -326,9 +326,9 @@ int jl_host_plan_run(jl_host_plan *p, void *stream)
                                                       : U.rows * F0.chunks_per_row;
                 F.tile_count = F0.tiles_x * ((U.rows + 31) / 32);
             }
-            uint64_t *list = p->lists ? p->lists + (size_t)p->list_cap * (u % nr) : nullptr;
+            uint64_t *list = p->lists ? p->lists + (size_t)p->list_cap * 2 * (u % nr) : nullptr;
             rc = launch_frame(F, p->prec[k], pal, static_cast<uint8_t *>(p->tables) + U.ctl_off, r, nullptr, list,
-                              p->list_cap);
+                              p->list_cap, list ? list + p->list_cap : nullptr);
             if (rc != JL_OK)
                 break;
             if ((e = cudaEventRecord(p->rendered[u], r)) != cudaSuccess ||

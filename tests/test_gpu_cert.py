@@ -70,11 +70,11 @@ def frames_and_refs():
     return fr, [_oracle(f) for f in fr]
 
 
-@pytest.mark.parametrize("certify", [True, False])
-def test_batch_counts_equal_binary64_oracle(cuda, frames_and_refs, certify):
+@pytest.mark.parametrize("certify,certify2", [(True, True), (True, False), (False, True)])
+def test_batch_counts_equal_binary64_oracle(cuda, frames_and_refs, certify, certify2):
     import torch
     fr, refs = frames_and_refs
-    b = jl.Batch(fr, palette=PAL, certify=certify)
+    b = jl.Batch(fr, palette=PAL, certify=certify, certify2=certify2)
     b.launch()
     torch.cuda.synchronize()
     assert b.status() == 0
@@ -83,14 +83,18 @@ def test_batch_counts_equal_binary64_oracle(cuda, frames_and_refs, certify):
         mism = int((g != k).sum())
         assert mism == 0, "frame %d %s: %d count mismatches (certify=%s)" % (i, f, mism, certify)
         assert (b.rgba(i).cpu().numpy() == oracle.colour(k, f["max_iter"], PAL)).all()
-    listed, iters = b.cert_stats()
+    l32, l64, it_df, it64 = b.cert_stats()
     total = sum(f["W"] * f["H"] for f in fr)
+    total_it = sum(int(k.astype(np.int64).sum()) for k in refs)
     if certify:
-        assert 0 < listed < total
-        # the listed pixels' iterations are part of the frames' iterations
-        assert 0 <= iters <= sum(int(k.astype(np.int64).sum()) for k in refs)
+        assert 0 < l32 < total and 0 <= l64 <= l32
+        # the iterations settled by the double-float pass and run in binary64
+        # are parts of the frames' iterations
+        assert 0 <= it_df and 0 <= it64 and it_df + it64 <= total_it
+        if not certify2:
+            assert l64 == l32 and it_df == 0
     else:
-        assert listed == 0 and iters == 0
+        assert (l32, l64, it_df, it64) == (0, 0, 0, 0)
 
 
 def test_certified_pass_settles_most_sweep_pixels(cuda):
@@ -101,18 +105,20 @@ def test_certified_pass_settles_most_sweep_pixels(cuda):
     b = jl.Batch(fr, palette=PAL)
     b.launch()
     torch.cuda.synchronize()
-    listed, iters = b.cert_stats()
+    l32, l64, it_df, it64 = b.cert_stats()
     total = sum(f["W"] * f["H"] for f in fr)
-    assert 0 < listed < 0.05 * total, (listed, total)
-    assert 0 < iters < sum(int(_oracle(f).astype(np.int64).sum()) for f in fr)
+    assert 0 < l32 < 0.05 * total, (l32, total)
+    # the double-float pass settles most of what the binary32 pass lists
+    assert l64 < 0.5 * l32 and it_df > 0, (l32, l64, it_df)
+    assert it_df + it64 < sum(int(_oracle(f).astype(np.int64).sum()) for f in fr)
     for i in (1, 7):
         assert (_np_counts(b.counts(i)) == _oracle(fr[i])).all()
-    # phase events: the certified pass and the binary64 kernel both timed
+    # phase events: both certified passes and the binary64 kernel timed
     p = jl.Batch(fr, palette=PAL, phases=True)
     p.launch()
     torch.cuda.synchronize()
     ms = p.phase_ms()
-    assert ms[0] == -1.0 and ms[1] > 0 and ms[2] > 0, ms
+    assert ms[0] == -1.0 and ms[1] > 0 and ms[2] > 0 and ms[3] > 0, ms
 
 
 def _variants64():
