@@ -198,7 +198,8 @@ int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStre
     a.chunk_counter = counter;
     a.status = status;
     a.cycle_budget = 0;
-    if (prec == JL_FP64 && cert_list && cert_cap >= (int64_t)F.W * F.H && F.xs32 && F.ys32) {
+    if (prec == JL_FP64 && cert_list && cert_cap >= (int64_t)F.W * F.H && F.xs32 && F.ys32 && F.xs32lo &&
+        F.ys32lo) {
         a.cert_list = cert_list;
         a.cert_cap = cert_cap;
         a.cert_count = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(ctl) + 16);
@@ -211,6 +212,8 @@ int launch_frame(Frame &F, int prec, const uint8_t *palette, void *ctl, cudaStre
     } else {
         F.xs32 = nullptr;
         F.ys32 = nullptr;
+        F.xs32lo = nullptr;
+        F.ys32lo = nullptr;
     }
     uint8_t pal[1024];
     if (palette)
@@ -242,7 +245,7 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
     const size_t coord_bytes = ((size_t)F.W + (size_t)F.H) * esz;
     const size_t coord_pad = (coord_bytes + 255) & ~(size_t)255;
     // binary64: binary32 tables and the two lists of the certified passes (8 B per pixel each)
-    const size_t c32_pad = prec == JL_FP64 ? ((((size_t)F.W + (size_t)F.H) * 4 + 255) & ~(size_t)255) : 0;
+    const size_t c32_pad = prec == JL_FP64 ? ((((size_t)F.W + (size_t)F.H) * 8 + 255) & ~(size_t)255) : 0;
     const size_t list_bytes = prec == JL_FP64 ? (size_t)F.W * (size_t)F.H * 16 : 0;
     const size_t scratch_bytes = coord_pad + 256 + c32_pad + list_bytes;
     void *scratch = nullptr;
@@ -256,6 +259,8 @@ int render_frame(Frame &F, int prec, const uint8_t *palette, cudaStream_t st, co
     if (prec == JL_FP64) {
         F.xs32 = reinterpret_cast<float *>(base + coord_pad + 256);
         F.ys32 = F.xs32 + F.W;
+        F.xs32lo = F.ys32 + F.H;
+        F.ys32lo = F.xs32lo + F.W;
         list = reinterpret_cast<uint64_t *>(base + coord_pad + 256 + c32_pad);
     }
     int rc = JL_OK;

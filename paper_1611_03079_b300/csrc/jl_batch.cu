@@ -47,6 +47,7 @@ struct jl_batch {
     cudaEvent_t ph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t s0 = nullptr, s1 = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t certs_done = nullptr;      // the binary64 group's certified passes are done
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     jl::Variant variant[2];
@@ -84,6 +85,8 @@ static void destroy_plan(jl_batch *b)
         cudaEventDestroy(b->fork);
     if (b->join)
         cudaEventDestroy(b->join);
+    if (b->certs_done)
+        cudaEventDestroy(b->certs_done);
     if (b->s0)
         cudaStreamDestroy(b->s0);
     if (b->s1)
@@ -167,7 +170,8 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             for (const Frame &F : host[g])
                 coord_bytes += (((size_t)F.W * (g ? 8 : 4) + 255) & ~(size_t)255) +
                                (((size_t)F.H * (g ? 8 : 4) + 255) & ~(size_t)255) +
-                               (g ? (((size_t)F.W * 4 + 255) & ~(size_t)255) + (((size_t)F.H * 4 + 255) & ~(size_t)255)
+                               (g ? 2 * ((((size_t)F.W * 4 + 255) & ~(size_t)255) +
+                                         (((size_t)F.H * 4 + 255) & ~(size_t)255))
                                   : 0);
         e = cudaMalloc(&b->coords_dev, coord_bytes ? coord_bytes : 256);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(coordinate tables)"); break; }
@@ -186,6 +190,10 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                     F.xs32 = reinterpret_cast<const float *>(static_cast<uint8_t *>(b->coords_dev) + off);
                     off += ((size_t)F.W * 4 + 255) & ~(size_t)255;
                     F.ys32 = reinterpret_cast<const float *>(static_cast<uint8_t *>(b->coords_dev) + off);
+                    off += ((size_t)F.H * 4 + 255) & ~(size_t)255;
+                    F.xs32lo = reinterpret_cast<const float *>(static_cast<uint8_t *>(b->coords_dev) + off);
+                    off += ((size_t)F.W * 4 + 255) & ~(size_t)255;
+                    F.ys32lo = reinterpret_cast<const float *>(static_cast<uint8_t *>(b->coords_dev) + off);
                     off += ((size_t)F.H * 4 + 255) & ~(size_t)255;
                 }
                 F.chunk_begin = chunk;
@@ -209,6 +217,8 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&b->certs_done, cudaEventDisableTiming);
         b->phases = (o.variant_flags & 8) != 0;
         for (int k = 0; k < 6 && e == cudaSuccess && b->phases; ++k)
             e = cudaEventCreate(&b->ph[k]);
@@ -425,7 +435,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             cudaEvent_t mid = (b->phases && g) ? b->ph[3] : nullptr, mid2 = (b->phases && g) ? b->ph[5] : nullptr;
             cudaError_t r = e0 ? cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal) : cudaSuccess;
             if (r == cudaSuccess)
-                r = launch_escape(args[g], g, b->variant[g], sms, s, mid, mid2);
+                r = launch_escape(args[g], g, b->variant[g], sms, s, mid, mid2, g ? b->certs_done : nullptr);
             if (r == cudaSuccess && e1)
                 r = cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
             return r;
@@ -439,6 +449,11 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 ce = group(1, b->s1);
             if (ce == cudaSuccess)
                 ce = cudaEventRecord(b->join, b->s1);
+            // With the certified passes the binary64 group starts with two
+            // binary32-pipe kernels, then its binary64 kernel leaves the
+            // binary32 pipe idle: the binary32 frames run beside the latter.
+            if (ce == cudaSuccess && b->cert_used)
+                ce = cudaStreamWaitEvent(b->s0, b->certs_done, 0);
             if (ce == cudaSuccess)
                 ce = group(0, b->s0);
             if (ce == cudaSuccess)

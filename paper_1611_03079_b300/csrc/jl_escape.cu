@@ -65,16 +65,22 @@ __global__ void coords_kernel(const __grid_constant__ CoordArgs a)
     const double lo = axis ? F.ymin : F.xmin;
     const double d = axis ? F.dy : F.dx;
     void *out = const_cast<void *>(axis ? F.ys : F.xs);
-    // binary64 frames: also the binary32 roundings for the certified pass
+    // binary64 frames: also the binary32 roundings for the certified pass and
+    // the remainders (exact in binary64) rounded to binary32 for the double-float pass
     float *out32 = F.precision == JL_FP64 ? const_cast<float *>(axis ? F.ys32 : F.xs32) : nullptr;
+    float *out32lo = F.precision == JL_FP64 ? const_cast<float *>(axis ? F.ys32lo : F.xs32lo) : nullptr;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         // lo + (i + 0.5) * d, binary64, no contraction.
         double t = __dadd_rn((double)i, 0.5);
         double v = __dadd_rn(lo, __dmul_rn(t, d));
         if (F.precision == JL_FP64) {
             static_cast<double *>(out)[i] = v;
-            if (out32)
-                out32[i] = __double2float_rn(v);
+            if (out32) {
+                const float h = __double2float_rn(v);
+                out32[i] = h;
+                if (out32lo)
+                    out32lo[i] = __double2float_rn(__dsub_rn(v, (double)h));
+            }
         } else {
             static_cast<float *>(out)[i] = __double2float_rn(v);
         }
@@ -372,8 +378,10 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
             const int rank = __popc(remaining & lt_mask);
             const bool got = mine && rank < take;
             if (LIST && got) {
-                // list entry (frame << 32) | (row << 16) | column
-                const uint64_t ent = a.cert_list[q_l0 + q_pos + rank];
+                // list entry (frame << 32) | (row << 16) | column, taken from the
+                // list's end: the double-float pass appends a pixel when its test
+                // fails, so the longest-lived pixels come last and start first here
+                const uint64_t ent = a.cert_list[list_n - 1 - (q_l0 + q_pos + rank)];
                 const int f = (int)(ent >> 32);
                 const int j = (int)((ent >> 16) & 0xffffu);
                 const int i = (int)(ent & 0xffffu);
@@ -1314,33 +1322,44 @@ __device__ __forceinline__ int cert_step(float &x, float &y, float &e, float cr,
     return __fmaf_rd(r, kCertR0, -m) > 4.0f ? 0 : -1;
 }
 
+// Escape certified from a step's kept values (r, s, E): 0 = escape, -1 = not settled.
+__device__ __forceinline__ int cert_exit(float r, float s, float e)
+{
+    const float m = __fmul_ru(__fmul_ru(kCertS2, s), e);
+    return __fmaf_rd(r, kCertR0, -m) > 4.0f ? 0 : -1;
+}
+
 // Binary64 count of a pixel from the certified pass (tests n = 0 .. mi-1 from
 // W_0 = (x, y), E_0 = e), or -1 when a test is not settled.  Blocks of four
-// steps with one branch; a block with a test that is not a certified pass is
-// replayed one step at a time from its start to find that test.
+// steps with one branch; each step keeps its r, s and E, so the first test of
+// a block that is not a certified pass is classified (escape or not settled)
+// from those without running the block again.
 __device__ __forceinline__ int cert_count(float x, float y, float e, float cr, float ci, float ec, int mi)
 {
     int n = 0;
     for (; n + 4 <= mi; n += 4) {
-        const float x0 = x, y0 = y, e0 = e;
-        bool ok = true;
+        float rk[4], sk[4], ek[4];
+        bool pk[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const float y2 = __fmul_rn(y, y);
             const float r = __fmaf_rn(x, x, y2);
             const float s = sqrt_approx(r);
             const float ge = __fmaf_ru(e, __fmaf_ru(kCertS2, s, e), ec);
-            ok &= __fmaf_ru(r, kCertR1, ge) < 4.0f;
+            pk[u] = __fmaf_ru(r, kCertR1, ge) < 4.0f;
+            rk[u] = r;
+            sk[u] = s;
+            ek[u] = e;
             const float nx = __fmaf_rn(x, x, __fmaf_rn(-y, y, cr));
             y = __fmaf_rn(__fadd_rn(x, x), y, ci);
             x = nx;
             e = __fmaf_ru(kCertK2, r, ge);
         }
-        if (!ok) {
-            x = x0;
-            y = y0;
-            e = e0;
-            break;
+        if (!(pk[0] && pk[1] && pk[2] && pk[3])) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (!pk[u])
+                    return cert_exit(rk[u], sk[u], ek[u]) == 0 ? n + u : -1;
         }
     }
     for (; n < mi; ++n) {
@@ -1537,22 +1556,8 @@ struct DfState {
     float xh, xl, yh, yl, e;
 };
 
-// The test of the double-float pass: 1 = a certified pass, 0 = a certified
-// escape, -1 = not settled.  s and lam are returned for the bound update.
-__device__ __forceinline__ int df_test(const DfState &w, float &s, float &lam)
-{
-    lam = __fadd_ru(fabsf(w.xl), fabsf(w.yl));
-    const float et = __fadd_ru(w.e, lam);
-    const float r = __fmaf_rn(w.xh, w.xh, __fmul_rn(w.yh, w.yh));
-    s = sqrt_approx(r);
-    const float ge = __fmaf_ru(et, __fmaf_ru(kCertS2, s, et), 0x1p-60f);
-    if (__fmaf_ru(r, kCertR1, ge) < 4.0f)
-        return 1;
-    const float m = __fmul_ru(__fmul_ru(kCertS2, s), et);
-    return __fmaf_rd(r, kCertR0, -m) > 4.0f ? 0 : -1;
-}
-
-// One double-float step with its bound update (after a certified pass).
+// One double-float step with its bound update (after a certified pass); the
+// new pairs are renormalised by TwoSum.
 __device__ __forceinline__ void df_update(DfState &w, float s, float lam, float crh, float crl, float cih, float cil,
                                           float kc)
 {
@@ -1577,37 +1582,35 @@ __device__ __forceinline__ void df_update(DfState &w, float s, float lam, float 
 
 // Up to four tests of the double-float pass from test n (limit mi): the
 // pixel's count (>= 0) when settled, -1 when a test is not settled, -2 when
-// the tests passed so far leave it live (n advanced).  Four tests run as a
-// block with one branch; a block with a test that is not a certified pass is
-// replayed one test at a time from its start.
+// the tests passed so far leave it live (n advanced).  Four steps always run
+// (the state after a failed or an uncounted test is not used again); each
+// keeps its test's r, s and Et, so the first test that is not a certified
+// pass is classified from those without running the block again.
 __device__ __forceinline__ int df_run4(DfState &w, int &n, int mi, float crh, float crl, float cih, float cil, float kc)
 {
     if (n >= mi)
         return mi;
-    if (n + 4 <= mi) {
-        const DfState w0 = w;
-        bool ok = true;
+    float rk[4], sk[4], ek[4];
+    bool pk[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float s, lam;
-            ok &= df_test(w, s, lam) == 1;
-            df_update(w, s, lam, crh, crl, cih, cil, kc);
-        }
-        if (ok) {
-            n += 4;
-            return n >= mi ? mi : -2;
-        }
-        w = w0;
-    }
-    for (int k = 0; k < 4 && n < mi; ++k, ++n) {
-        float s, lam;
-        const int rc = df_test(w, s, lam);
-        if (rc == 0)
-            return n;
-        if (rc < 0)
-            return -1;
+    for (int k = 0; k < 4; ++k) {
+        const float lam = __fadd_ru(fabsf(w.xl), fabsf(w.yl));
+        const float et = __fadd_ru(w.e, lam);
+        const float r = __fmaf_rn(w.xh, w.xh, __fmul_rn(w.yh, w.yh));
+        const float s = sqrt_approx(r);
+        const float ge = __fmaf_ru(et, __fmaf_ru(kCertS2, s, et), 0x1p-60f);
+        pk[k] = __fmaf_ru(r, kCertR1, ge) < 4.0f;
+        rk[k] = r;
+        sk[k] = s;
+        ek[k] = et;
         df_update(w, s, lam, crh, crl, cih, cil, kc);
     }
+    const int m = min(4, mi - n);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < m && !pk[k])
+            return cert_exit(rk[k], sk[k], ek[k]) == 0 ? n + k : -1;
+    n += m;
     return n >= mi ? mi : -2;
 }
 
@@ -1678,12 +1681,9 @@ __global__ void __launch_bounds__(256) cert2_kernel(const __grid_constant__ Esca
                 pj = (int)((ent >> 16) & 0xffffu);
                 pi = (int)(ent & 0xffffu);
                 const Frame &F = BATCH ? a.frames[fr] : a.single;
-                const double x64 = static_cast<const double *>(F.xs)[pi];
-                const double y64 = static_cast<const double *>(F.ys)[pj];
-                // the coordinates as float pairs (x64 - xh is exact in binary64)
-                const float xh = __double2float_rn(x64), yh = __double2float_rn(y64);
-                const float xl = __double2float_rn(__dsub_rn(x64, (double)xh));
-                const float yl = __double2float_rn(__dsub_rn(y64, (double)yh));
+                // the coordinates as float pairs (tables written with the binary64 ones)
+                const float xh = F.xs32[pi], yh = F.ys32[pj];
+                const float xl = F.xs32lo[pi], yl = F.ys32lo[pj];
                 const float l0 = __fadd_ru(fabsf(xl), fabsf(yl));
                 mi = F.max_iter;
                 n = 0;
@@ -2067,11 +2067,12 @@ static bool use_cert(const EscapeArgs &a, int precision, const Variant &v)
 {
     if (precision != JL_FP64 || v.ppt == 0 || !a.cert_list || !a.cert_count || !a.list_counter)
         return false;
-    return a.frames ? (a.tile_frame && a.tile_local) : (a.single.xs32 && a.single.ys32);
+    return a.frames ? (a.tile_frame && a.tile_local)
+                    : (a.single.xs32 && a.single.ys32 && a.single.xs32lo && a.single.ys32lo);
 }
 
 cudaError_t launch_escape(const EscapeArgs &a_in, int precision, const Variant &v, int num_sms, cudaStream_t st,
-                          cudaEvent_t mid, cudaEvent_t mid2)
+                          cudaEvent_t mid, cudaEvent_t mid2, cudaEvent_t done)
 {
     EscapeArgs a = a_in;
     if (use_cert(a, precision, v)) {
@@ -2083,6 +2084,8 @@ cudaError_t launch_escape(const EscapeArgs &a_in, int precision, const Variant &
             e = launch_cert2(a, num_sms, st);
         if (e == cudaSuccess && mid2)
             e = cudaEventRecordWithFlags(mid2, st, cudaEventRecordExternal);
+        if (e == cudaSuccess && done)
+            e = cudaEventRecord(done, st);
         if (e != cudaSuccess)
             return e;
         EscapeArgs b = a;

@@ -46,6 +46,9 @@ struct Frame {
     float cr_lo32, ci_lo32;        // binary64 Julia frames: C - (cr32, ci32) rounded to binary32 (C as
                                    // float pairs for the double-float pass)
     float cert2_kc;                // binary64 Julia frames: per-step constant of the double-float pass
+    int32_t pad4;
+    const float *xs32lo;           // binary64 frames: x - xs32 and y - ys32 rounded to binary32 (the
+    const float *ys32lo;           // coordinates as float pairs for the double-float pass), with xs32
 };
 
 // Launch parameters of the escape kernels (passed by value as a grid constant).
@@ -102,9 +105,12 @@ int cuda_fail(cudaError_t e, const char *what);
 // `frames_dev` is a device table of n frames, or NULL with `single` used instead.
 cudaError_t launch_coords(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st);
 // A binary64 launch with the certified passes records `mid` (when not NULL)
-// after the binary32 pass and `mid2` after the double-float pass.
+// after the binary32 pass and `mid2` after the double-float pass (external
+// event nodes when captured, for timing), and `done` (a plain record, for a
+// dependency of other work) after the passes.
 cudaError_t launch_escape(const EscapeArgs &args, int precision, const Variant &v, int num_sms,
-                          cudaStream_t st, cudaEvent_t mid = nullptr, cudaEvent_t mid2 = nullptr);
+                          cudaStream_t st, cudaEvent_t mid = nullptr, cudaEvent_t mid2 = nullptr,
+                          cudaEvent_t done = nullptr);
 cudaError_t launch_hist_finalize(const Frame *frames_dev, const Frame *single, int n, cudaStream_t st);
 cudaError_t launch_hist_zero(const Frame *frames_dev, int n, cudaStream_t st);
 bool variant_supported(int precision, int ppt, int unroll);

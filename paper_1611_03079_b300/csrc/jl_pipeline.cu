@@ -168,8 +168,8 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
         const size_t esz = p->prec[(size_t)i] == JL_FP64 ? 8 : 4;
         table_off[(size_t)i] = table_bytes;
         table_bytes += pad256(((size_t)q.width + (size_t)q.height) * esz);
-        if (p->prec[(size_t)i] == JL_FP64)  // binary32 roundings for the certified pass
-            table_bytes += pad256(((size_t)q.width + (size_t)q.height) * 4);
+        if (p->prec[(size_t)i] == JL_FP64)  // binary32 roundings and remainders for the certified passes
+            table_bytes += pad256(((size_t)q.width + (size_t)q.height) * 8);
         p->ctl_off[(size_t)i] = table_bytes;
         table_bytes += 256;
     }
@@ -243,6 +243,8 @@ int jl_host_plan_create(const jl_frame *frames, int32_t n, void *counts_host, ui
             if (esz == 8) {
                 F.xs32 = reinterpret_cast<const float *>(base + pad256(((size_t)F.W + (size_t)F.H) * 8));
                 F.ys32 = F.xs32 + F.W;
+                F.xs32lo = F.ys32 + F.H;
+                F.ys32lo = F.xs32lo + F.W;
             }
         }
         e = cudaEventCreateWithFlags(&p->tables_ready, cudaEventDisableTiming);
@@ -320,8 +322,10 @@ int jl_host_plan_run(jl_host_plan *p, void *stream)
             if (U.rows != F0.H) {
                 F.H = U.rows;
                 F.ys = static_cast<const uint8_t *>(F0.ys) + (size_t)U.row0 * esz;
-                if (F0.ys32)
+                if (F0.ys32) {
                     F.ys32 = F0.ys32 + U.row0;
+                    F.ys32lo = F0.ys32lo + U.row0;
+                }
                 F.chunk_count = F0.rows_per_chunk > 1 ? (U.rows + F0.rows_per_chunk - 1) / F0.rows_per_chunk
                                                       : U.rows * F0.chunks_per_row;
                 F.tile_count = F0.tiles_x * ((U.rows + 31) / 32);
