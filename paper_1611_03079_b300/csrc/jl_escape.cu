@@ -35,6 +35,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "jl_common.cuh"
 #include "jl_internal.h"
@@ -527,61 +528,103 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
                 need[k] = (fid[k] >= 0) && (!live_k || esc || rem[k] < U);
             }
         } else {
-            double sx[PPT], sy[PPT];
-            bool amb = false;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                sx[k] = (double)x[k];
-                sy[k] = (double)y[k];
-                cnt[k] = 0;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
+            // Binary64 block; GUARD: only the first nslot slots (the others are
+            // empty in every lane of the warp).
+            auto block64 = [&](auto guard, int nslot) {
+                constexpr bool GUARD = decltype(guard)::value;
+                double sx[PPT], sy[PPT];
+                bool amb = false;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    double xx = (double)x[k], yy = (double)y[k];
-                    double x2 = __dmul_rn(xx, xx);
-                    double y2 = __dmul_rn(yy, yy);
-                    float r32 = __fadd_rn(hi_estimate(x2), hi_estimate(y2));
-                    cnt[k] += (r32 < 3.9999847412109375f) ? 1 : 0;
-                    amb |= (rem[k] >= 0) & (r32 >= 3.9999847412109375f) & (r32 <= 4.0000152587890625f);
-                    double t = dbl2(xx);
-                    t = __dmul_rn(t, yy);
-                    y[k] = (T)__dadd_rn(t, (double)ci[k]);
-                    x[k] = (T)__dadd_rn(__dsub_rn(x2, y2), (double)cr[k]);
-                }
-            }
-            if (__any_sync(FULL, amb)) {
-                // replay the block with exact binary64 tests
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) {
-                    x[k] = (T)sx[k];
-                    y[k] = (T)sy[k];
+                    sx[k] = (double)x[k];
+                    sy[k] = (double)y[k];
                     cnt[k] = 0;
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) {
+                        if (GUARD && k >= nslot)
+                            continue;
                         double xx = (double)x[k], yy = (double)y[k];
                         double x2 = __dmul_rn(xx, xx);
                         double y2 = __dmul_rn(yy, yy);
-                        cnt[k] += (__dadd_rn(x2, y2) <= 4.0) ? 1 : 0;
+                        float r32 = __fadd_rn(hi_estimate(x2), hi_estimate(y2));
+                        cnt[k] += (r32 < 3.9999847412109375f) ? 1 : 0;
+                        amb |= (rem[k] >= 0) & (r32 >= 3.9999847412109375f) & (r32 <= 4.0000152587890625f);
                         double t = dbl2(xx);
                         t = __dmul_rn(t, yy);
                         y[k] = (T)__dadd_rn(t, (double)ci[k]);
                         x[k] = (T)__dadd_rn(__dsub_rn(x2, y2), (double)cr[k]);
                     }
                 }
-            }
+                if (__any_sync(FULL, amb)) {
+                    // replay the block with exact binary64 tests
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const bool live_k = rem[k] >= 0 && fid[k] >= 0;
-                const bool esc = cnt[k] < U;
-                if (live_k && !esc)
-                    rem[k] -= U;
-                need[k] = (fid[k] >= 0) && (!live_k || esc || rem[k] < U);
+                    for (int k = 0; k < PPT; ++k) {
+                        x[k] = (T)sx[k];
+                        y[k] = (T)sy[k];
+                        cnt[k] = 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+#pragma unroll
+                        for (int k = 0; k < PPT; ++k) {
+                            if (GUARD && k >= nslot)
+                                continue;
+                            double xx = (double)x[k], yy = (double)y[k];
+                            double x2 = __dmul_rn(xx, xx);
+                            double y2 = __dmul_rn(yy, yy);
+                            cnt[k] += (__dadd_rn(x2, y2) <= 4.0) ? 1 : 0;
+                            double t = dbl2(xx);
+                            t = __dmul_rn(t, yy);
+                            y[k] = (T)__dadd_rn(t, (double)ci[k]);
+                            x[k] = (T)__dadd_rn(__dsub_rn(x2, y2), (double)cr[k]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    const bool live_k = rem[k] >= 0 && fid[k] >= 0;
+                    const bool esc = cnt[k] < U;
+                    if (live_k && !esc)
+                        rem[k] -= U;
+                    need[k] = (fid[k] >= 0) && (!live_k || esc || rem[k] < U);
+                }
+            };
+            int nslot = PPT;
+            if (PPT > 1 && q_done) {
+                // No pixels are left to take: each lane moves its pixels to its
+                // lowest slots, and slots that no lane uses are not computed (a
+                // binary64 warp instruction costs the narrow pipe the same
+                // whatever its lanes hold).
+#pragma unroll
+                for (int k = 1; k < PPT; ++k) {
+#pragma unroll
+                    for (int j = 0; j < k; ++j) {
+                        if (fid[j] < 0 && fid[k] >= 0) {
+                            x[j] = x[k];
+                            y[j] = y[k];
+                            cr[j] = cr[k];
+                            ci[j] = ci[k];
+                            rem[j] = rem[k];
+                            fid[j] = fid[k];
+                            pix[j] = pix[k];
+                            fid[k] = -1;
+                            rem[k] = 0x3fffffff;
+                        }
+                    }
+                }
+                int used = 0;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    used += fid[k] >= 0 ? 1 : 0;
+                nslot = (int)__reduce_max_sync(FULL, (unsigned)used);
             }
+            if (nslot == PPT)
+                block64(std::integral_constant<bool, false>(), PPT);
+            else
+                block64(std::integral_constant<bool, true>(), nslot);
         }
     }
 
