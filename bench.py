@@ -35,6 +35,8 @@ WORKLOAD = ("throughput sweep: 16 renders of 4096x4096 (Julia [-1.6,1.6]^2, C in
             "-0.7269+0.1889i, -0.4+0.6i}; Mandelbrot [-2.5,1]x[-1.75,1.75]) x limit {100,1000} x "
             "{binary32, binary64}; uint16 counts + RGBA8")
 OPS_PER_ITER = 8  # 3 multiplies + 5 adds per escape-time step (no FMA)
+CERT_OPS = 10     # binary32 arithmetic of one step of the certified binary32 pass
+CERT2_OPS = 62    # binary32 arithmetic of one step of the double-float pass
 # The oracle's sample of the sweep: every 8th row of each frame (512 rows of
 # 4096, interleaved over the host threads), about a second of all-core work.
 ORACLE_ROW_STRIDE = 8
@@ -621,23 +623,28 @@ def main():
                  "escape_kernel<float>"] = dict(ms=ph[0], ops=OPS_PER_ITER * it, peak=peaks[0], prec="binary32",
                                                 bytes=6 * px, unit_note="8 binary32 lane ops per iteration")
         elif ph[1] > 0:
-            l32, l64, it_df, it64 = sp.cert_stats(stream)
+            l32, l64, it_df, it64, st32, st_df = sp.cert_stats(stream)
             by_prec[prec].update({"cert_listed_binary32_pass": l32, "cert_listed_to_binary64": l64,
-                                  "iterations_settled_double_float": it_df, "iterations_binary64": it64})
+                                  "iterations_settled_double_float": it_df, "iterations_binary64": it64,
+                                  "tests_binary32_pass": st32, "tests_double_float_pass": st_df})
             kern["cert_kernel"] = dict(
-                ms=ph[1], ops=OPS_PER_ITER * (it - it_df - it64), peak=peaks[0], prec="binary32",
+                ms=ph[1], ops=CERT_OPS * st32, peak=peaks[0], prec="binary32",
                 bytes=6 * (px - l32) + 8 * l32,
-                unit_note="8 lane ops per binary64 iteration the certified binary32 pass settles (%d of %d); "
-                          "the pass issues ~12 binary32 operations per step (the orbit with FMA plus its "
-                          "error bound) and also runs the steps of the %d pixels it lists before their "
-                          "unsettled test" % (it - it_df - it64, it, l32))
+                unit_note="%d binary32 lane ops per test the certified binary32 pass decides (%d tests: every "
+                          "binary64 pixel's tests up to its escape, its limit or its unsettled test): the orbit "
+                          "step y*y, fma(x,x,y2), fma(-y,y,cr), fma(x,x,.), x+x, fma(2x,y,ci) and the bound "
+                          "fma(2s',E), fma(E,.,EC), fma(r,.,.) for the test, fma(2.5u,r,.) for E'; the approximate "
+                          "square root (XU pipe) and the compare are not counted; it settles %d of the %d "
+                          "binary64 iterations" % (CERT_OPS, st32, it - it_df - it64, it))
             if ph[2] > 0:
                 kern["cert2_kernel"] = dict(
-                    ms=ph[2], ops=OPS_PER_ITER * it_df, peak=peaks[0], prec="binary32",
+                    ms=ph[2], ops=CERT2_OPS * st_df, peak=peaks[0], prec="binary32",
                     bytes=8 * l32 + 6 * (l32 - l64) + 8 * l64,
-                    unit_note="8 lane ops per binary64 iteration the double-float pass settles (%d); the pass "
-                              "issues ~60 binary32 operations per step (float-pair orbit, exact product and sum "
-                              "splits, bound) on the %d pixels the binary32 pass lists" % (it_df, l32))
+                    unit_note="%d binary32 lane ops per test the double-float pass decides (%d tests of the %d "
+                              "pixels the binary32 pass lists): the test on the high parts (7), the float-pair "
+                              "step with exact product splits (6), three TwoSums (18), the low parts (14), two "
+                              "renormalising TwoSums (12) and the bound (5); it settles %d iterations"
+                              % (CERT2_OPS, st_df, l32, it_df))
             kern["escape_kernel<double> (list)"] = dict(
                 ms=ph[3], ops=OPS_PER_ITER * it64, peak=peaks[1], prec="binary64", bytes=14 * l64,
                 unit_note="8 binary64 lane ops per iteration of the listed pixels; the kernel issues 6 of them "

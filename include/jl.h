@@ -316,12 +316,14 @@ int jl_batch_precisions(const jl_batch *b, int32_t *out, int32_t cap);
 /* Pixel totals of the binary32 and binary64 frames of the plan. */
 int jl_batch_pixels(const jl_batch *b, int64_t *fp32_pixels, int64_t *fp64_pixels);
 
-/* Counters of the last launch's binary64 frames, into out[0..3]: the pixels
+/* Counters of the last launch's binary64 frames, into out[0..5]: the pixels
  * the certified binary32 pass left unsettled; the pixels left to the binary64
  * kernel after the double-float pass (equal to out[0] when that pass is off);
  * the iterations (sum of counts) of the pixels the double-float pass settled;
- * the iterations the binary64 kernel ran.  Zeros when the plan has no binary64
- * frames or the passes are off.  Synchronises `stream`.  The certified passes
+ * the iterations the binary64 kernel ran; the tests (steps) the binary32 pass
+ * and the double-float pass decided (each pixel's tests up to its escape, its
+ * limit or its unsettled test).  Zeros when the plan has no binary64 frames or
+ * the passes are off.  Synchronises `stream`.  The certified passes
  * run a binary32 (then double-float) orbit with a rigorous bound on its
  * distance to the binary64 orbit and keep a pixel only when the bound settles
  * every binary64 test of the pixel (the counts are the binary64 counts either

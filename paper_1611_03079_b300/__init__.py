@@ -409,10 +409,11 @@ class Batch:
     def cert_stats(self, stream=None):
         """For the last launch's binary64 frames: (pixels left by the binary32
         pass, pixels left to the binary64 kernel, iterations the double-float
-        pass settled, iterations the binary64 kernel ran)."""
+        pass settled, iterations the binary64 kernel ran, tests the binary32
+        pass decided, tests the double-float pass decided)."""
         import torch
         st = (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
-        v = (ctypes.c_int64 * 4)()
+        v = (ctypes.c_int64 * 6)()
         check(self._L.jl_batch_cert_stats(self._h, st, v))
         return tuple(int(x) for x in v)
 

@@ -37,8 +37,9 @@ struct jl_batch {
     // control words, zeroed per launch: work counters of the two groups (0, 8),
     // status (16), the binary32 pass's list count (32), the binary64 kernel's
     // list counter (40), the binary64 kernel's iterations (48), the
-    // double-float pass's list count (56), its counter on the first list (64)
-    // and the iterations of the pixels it settles (72)
+    // double-float pass's list count (56), its counter on the first list (64),
+    // the iterations of the pixels it settles (72), and the tests decided by the
+    // binary32 pass (80) and the double-float pass (88)
     uint8_t *ctl_dev = nullptr;
     // opts.variant_flags bit 3: timing events recorded inside the graph around
     // the binary32 kernel (0, 1) and the binary64 kernels (2, 3 after the
@@ -319,11 +320,13 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 x.cert_count = reinterpret_cast<unsigned long long *>(b->ctl_dev + 32);
                 x.list_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 40);
                 x.list_iters = reinterpret_cast<unsigned long long *>(b->ctl_dev + 48);
+                x.cert_steps = reinterpret_cast<unsigned long long *>(b->ctl_dev + 80);
                 if (!(o.variant_flags & 16)) {
                     x.cert_list2 = b->list_dev + b->pixels[1];
                     x.cert_count2 = reinterpret_cast<unsigned long long *>(b->ctl_dev + 56);
                     x.list2_counter = reinterpret_cast<unsigned long long *>(b->ctl_dev + 64);
                     x.cert2_iters = reinterpret_cast<unsigned long long *>(b->ctl_dev + 72);
+                    x.cert2_steps = reinterpret_cast<unsigned long long *>(b->ctl_dev + 88);
                 }
             }
             // output specialisation: 1 = every frame uint16 counts + RGBA8, 2 =
@@ -385,7 +388,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                     const EscapeArgs x = make_args(g, v);
                     float ms = 0.f;
                     for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
-                        e = cudaMemsetAsync(b->ctl_dev, 0, 80, b->s0);
+                        e = cudaMemsetAsync(b->ctl_dev, 0, 96, b->s0);
                         if (e == cudaSuccess)
                             e = cudaEventRecord(t0, b->s0);
                         if (e == cudaSuccess)
@@ -419,7 +422,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             args[g] = make_args(g, b->variant[g]);
         e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaStreamBeginCapture"); break; }
-        cudaError_t ce = cudaMemsetAsync(b->ctl_dev, 0, 80, b->s0);
+        cudaError_t ce = cudaMemsetAsync(b->ctl_dev, 0, 96, b->s0);
         // region covering: coordinate tables of every frame, each launch
         for (int g = 0; g < 2 && ce == cudaSuccess; ++g)
             if (b->n_group[g])
@@ -522,8 +525,8 @@ int jl_batch_cert_stats(jl_batch *b, void *stream, int64_t *out)
     if (!b || !out)
         return fail(JL_EINVAL, "invalid arguments");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
-    cudaError_t e = cudaMemcpyAsync(v, b->ctl_dev + 32, 48, cudaMemcpyDeviceToHost, st);
+    unsigned long long v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(v, b->ctl_dev + 32, 64, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
@@ -532,6 +535,8 @@ int jl_batch_cert_stats(jl_batch *b, void *stream, int64_t *out)
     out[1] = (int64_t)(b->cert2_used ? v[3] : v[0]);
     out[2] = (int64_t)v[5];
     out[3] = (int64_t)v[2];
+    out[4] = (int64_t)v[6];
+    out[5] = (int64_t)v[7];
     return JL_OK;
 }
 

@@ -1373,7 +1373,7 @@ __device__ __forceinline__ int cert_exit(float r, float s, float e)
 }
 
 // Binary64 count of a pixel from the certified pass (tests n = 0 .. mi-1 from
-// W_0 = (x, y), E_0 = e), or -1 when a test is not settled.  Blocks of four
+// W_0 = (x, y), E_0 = e), or -1 - n when test n is not settled.  Blocks of four
 // steps with one branch; each step keeps its r, s and E, so the first test of
 // a block that is not a certified pass is classified (escape or not settled)
 // from those without running the block again.
@@ -1402,13 +1402,13 @@ __device__ __forceinline__ int cert_count(float x, float y, float e, float cr, f
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (!pk[u])
-                    return cert_exit(rk[u], sk[u], ek[u]) == 0 ? n + u : -1;
+                    return cert_exit(rk[u], sk[u], ek[u]) == 0 ? n + u : -1 - (n + u);
         }
     }
     for (; n < mi; ++n) {
         const int rc = cert_step(x, y, e, cr, ci, ec);
         if (rc <= 0)
-            return rc == 0 ? n : -1;
+            return rc == 0 ? n : -1 - n;
     }
     return mi;
 }
@@ -1432,6 +1432,7 @@ __global__ void __launch_bounds__(256, 4) cert_kernel(const __grid_constant__ Es
 
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned steps = 0;  // tests this thread decided
     const long long t_start = clock64();
     const long long total_units = a.total_tiles * 8;
     const unsigned long long claim = (unsigned long long)a.claim;
@@ -1497,6 +1498,9 @@ __global__ void __launch_bounds__(256, 4) cert_kernel(const __grid_constant__ Es
                     count = cert_count(0.f, 0.f, 0.f, xv, yv, __fmaf_ru(kCertMC, __fadd_ru(ax, ay), 0x1p-47f), mi);
             }
             const bool undecided = valid && count < 0;
+            // tests decided (for the launch's step counter)
+            if (valid)
+                steps += count < 0 ? (unsigned)(-count) : (unsigned)(count < mi ? count + 1 : mi);
             const unsigned um = __ballot_sync(FULL, undecided);
             unsigned long long base = 0;
             if (um) {
@@ -1518,6 +1522,11 @@ __global__ void __launch_bounds__(256, 4) cert_kernel(const __grid_constant__ Es
             if (valid)
                 store_tile<BATCH, OUT>(a, o, pal, hbins, fr, (uint32_t)j * (uint32_t)W + (uint32_t)i, count, lt_mask);
         }
+    }
+    if (a.cert_steps) {
+        const unsigned tot = __reduce_add_sync(FULL, steps);
+        if (lane == 0)
+            atomicAdd(a.cert_steps, (unsigned long long)tot);
     }
     if (nb) {
         __syncthreads();
@@ -1650,9 +1659,14 @@ __device__ __forceinline__ int df_run4(DfState &w, int &n, int mi, float crh, fl
     }
     const int m = min(4, mi - n);
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (k < m && !pk[k])
-            return cert_exit(rk[k], sk[k], ek[k]) == 0 ? n + k : -1;
+    for (int k = 0; k < 4; ++k) {
+        if (k < m && !pk[k]) {
+            if (cert_exit(rk[k], sk[k], ek[k]) == 0)
+                return n + k;
+            n += k;  // the test that is not settled
+            return -1;
+        }
+    }
     n += m;
     return n >= mi ? mi : -2;
 }
@@ -1677,6 +1691,7 @@ __global__ void __launch_bounds__(256) cert2_kernel(const __grid_constant__ Esca
 
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned steps = 0;  // tests this thread decided
     const long long t_start = clock64();
     long long n1 = (long long)*a.cert_count;
     if (n1 > a.cert_cap)
@@ -1756,6 +1771,8 @@ __global__ void __launch_bounds__(256) cert2_kernel(const __grid_constant__ Esca
         if (live)
             res = df_run4(w, n, mi, crh, crl, cih, cil, kc);
         const bool und = live && res == -1;
+        if (live && res != -2)
+            steps += res >= 0 ? (unsigned)(res < mi ? res + 1 : mi) : (unsigned)(n + 1);
         const unsigned um = __ballot_sync(FULL, und);
         if (um) {
             unsigned long long base = 0;
@@ -1788,6 +1805,11 @@ __global__ void __launch_bounds__(256) cert2_kernel(const __grid_constant__ Esca
         }
         if (res != -2)
             live = false;
+    }
+    if (a.cert2_steps) {
+        const unsigned tot = __reduce_add_sync(FULL, steps);
+        if (lane == 0)
+            atomicAdd(a.cert2_steps, (unsigned long long)tot);
     }
     if (nb) {
         __syncthreads();

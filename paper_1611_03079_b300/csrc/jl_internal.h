@@ -84,6 +84,8 @@ struct EscapeArgs {
     unsigned long long *cert_count2;   // zeroed before the launch
     unsigned long long *list2_counter; // zeroed before the launch
     unsigned long long *cert2_iters;   // zeroed before the launch, or NULL: iterations the second pass settles
+    unsigned long long *cert_steps;    // zeroed before the launch, or NULL: tests the binary32 pass decided
+    unsigned long long *cert2_steps;   // zeroed before the launch, or NULL: tests the double-float pass decided
     uint32_t palette[256];
     Frame single;
 };

@@ -83,18 +83,21 @@ def test_batch_counts_equal_binary64_oracle(cuda, frames_and_refs, certify, cert
         mism = int((g != k).sum())
         assert mism == 0, "frame %d %s: %d count mismatches (certify=%s)" % (i, f, mism, certify)
         assert (b.rgba(i).cpu().numpy() == oracle.colour(k, f["max_iter"], PAL)).all()
-    l32, l64, it_df, it64 = b.cert_stats()
+    l32, l64, it_df, it64, st32, st_df = b.cert_stats()
     total = sum(f["W"] * f["H"] for f in fr)
     total_it = sum(int(k.astype(np.int64).sum()) for k in refs)
     if certify:
         assert 0 < l32 < total and 0 <= l64 <= l32
+        # every pixel decides at least one test in the binary32 pass, every
+        # listed pixel at least one in the double-float pass
+        assert st32 >= total and (st_df >= l32 if certify2 else st_df == 0)
         # the iterations settled by the double-float pass and run in binary64
         # are parts of the frames' iterations
         assert 0 <= it_df and 0 <= it64 and it_df + it64 <= total_it
         if not certify2:
             assert l64 == l32 and it_df == 0
     else:
-        assert (l32, l64, it_df, it64) == (0, 0, 0, 0)
+        assert (l32, l64, it_df, it64, st32, st_df) == (0, 0, 0, 0, 0, 0)
 
 
 def test_certified_pass_settles_most_sweep_pixels(cuda):
@@ -105,9 +108,12 @@ def test_certified_pass_settles_most_sweep_pixels(cuda):
     b = jl.Batch(fr, palette=PAL)
     b.launch()
     torch.cuda.synchronize()
-    l32, l64, it_df, it64 = b.cert_stats()
+    l32, l64, it_df, it64, st32, st_df = b.cert_stats()
     total = sum(f["W"] * f["H"] for f in fr)
     assert 0 < l32 < 0.05 * total, (l32, total)
+    # the binary32 pass decides each settled pixel's tests up to its escape
+    assert st32 >= sum(int(np.minimum(_oracle(f).astype(np.int64) + 1, f["max_iter"]).sum()) for f in fr) - \
+        it_df - it64 - 2 * l32
     # the double-float pass settles most of what the binary32 pass lists
     assert l64 < 0.5 * l32 and it_df > 0, (l32, l64, it_df)
     assert it_df + it64 < sum(int(_oracle(f).astype(np.int64).sum()) for f in fr)
