@@ -1373,36 +1373,36 @@ __device__ __forceinline__ int cert_exit(float r, float s, float e)
 }
 
 // Binary64 count of a pixel from the certified pass (tests n = 0 .. mi-1 from
-// W_0 = (x, y), E_0 = e), or -1 - n when test n is not settled.  Blocks of four
-// steps with one branch; each step keeps its r, s and E, so the first test of
-// a block that is not a certified pass is classified (escape or not settled)
-// from those without running the block again.
+// W_0 = (x, y), E_0 = e), or -1 - n when test n is not settled.  Blocks of
+// CB steps with one branch: the largest U of a block is compared with 4 (a
+// NaN U cannot come first: with finite inputs r, s and g are finite or +inf
+// and E > 0 after step 0 (E_0 = 0 only with W_0 = 0), so the first U that is
+// not finite is +inf, which the maximum keeps); a block with a test that is
+// not a certified pass is replayed one test at a time from its start.
+template <int CB>
 __device__ __forceinline__ int cert_count(float x, float y, float e, float cr, float ci, float ec, int mi)
 {
     int n = 0;
-    for (; n + 4 <= mi; n += 4) {
-        float rk[4], sk[4], ek[4];
-        bool pk[4];
+    for (; n + CB <= mi; n += CB) {
+        const float x0 = x, y0 = y, e0 = e;
+        float umax = 0.f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < CB; ++u) {
             const float y2 = __fmul_rn(y, y);
             const float r = __fmaf_rn(x, x, y2);
             const float s = sqrt_approx(r);
             const float ge = __fmaf_ru(e, __fmaf_ru(kCertS2, s, e), ec);
-            pk[u] = __fmaf_ru(r, kCertR1, ge) < 4.0f;
-            rk[u] = r;
-            sk[u] = s;
-            ek[u] = e;
+            umax = fmaxf(umax, __fmaf_ru(r, kCertR1, ge));
             const float nx = __fmaf_rn(x, x, __fmaf_rn(-y, y, cr));
             y = __fmaf_rn(__fadd_rn(x, x), y, ci);
             x = nx;
             e = __fmaf_ru(kCertK2, r, ge);
         }
-        if (!(pk[0] && pk[1] && pk[2] && pk[3])) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (!pk[u])
-                    return cert_exit(rk[u], sk[u], ek[u]) == 0 ? n + u : -1 - (n + u);
+        if (!(umax < 4.0f)) {
+            x = x0;
+            y = y0;
+            e = e0;
+            break;
         }
     }
     for (; n < mi; ++n) {
@@ -1493,9 +1493,9 @@ __global__ void __launch_bounds__(256, 4) cert_kernel(const __grid_constant__ Es
                 const float yv = ys32[j];
                 const float ax = fabsf(xv), ay = fabsf(yv);
                 if (julia)
-                    count = cert_count(xv, yv, __fmaf_ru(kCertE0, __fadd_ru(ax, ay), 0x1p-140f), fcr, fci, fec, mi);
+                    count = cert_count<4>(xv, yv, __fmaf_ru(kCertE0, __fadd_ru(ax, ay), 0x1p-140f), fcr, fci, fec, mi);
                 else
-                    count = cert_count(0.f, 0.f, 0.f, xv, yv, __fmaf_ru(kCertMC, __fadd_ru(ax, ay), 0x1p-47f), mi);
+                    count = cert_count<4>(0.f, 0.f, 0.f, xv, yv, __fmaf_ru(kCertMC, __fadd_ru(ax, ay), 0x1p-47f), mi);
             }
             const bool undecided = valid && count < 0;
             // tests decided (for the launch's step counter)
