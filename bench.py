@@ -791,6 +791,7 @@ def main():
                                         "and the binary64 kernel on the pixels they list" if chosen["fp64"][0] > 0
                                         else ", the binary64 escape kernel"),
                 "autotuned_variants": tuned,
+                "plan_variants": {k: list(v) for k, v in chosen.items()},
                 "survey": survey,
                 "mismatch_rate_fp32_vs_fp64_sweep": mismatch,
                 **extra,

@@ -371,6 +371,7 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
                 if (g == 1) {
                     cand.push_back(Variant{2, 4, 256, 0});
                     cand.push_back(Variant{4, 4, 128, 0});
+                    cand.push_back(Variant{2, 4, 128, 0});
                     cand.push_back(Variant{4, 4, 256, 0});
                 }
                 float best_ms = 0.f;
