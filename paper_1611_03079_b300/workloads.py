@@ -183,6 +183,34 @@ def random_views(n, seed, max_side=97):
     return out
 
 
+def boundary_views(n, seed, max_side=48):
+    """Small binary64 frames centred on points of Julia and Mandelbrot set
+    boundaries (where an escape test is closest to its threshold for the most
+    steps), widths 10^-13 .. 4, limits up to 3000, both modes, for parity tests
+    of binary64 paths.  Julia centres by inverse iteration (julia_boundary_points)
+    for a random C; Mandelbrot centres on the main cardioid's boundary
+    e^{it}/2 - e^{2it}/4 or the period-2 disk's -1 + e^{it}/4."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        W = int(rng.integers(1, max_side + 1))
+        H = int(rng.integers(1, max_side + 1))
+        w = float(10 ** rng.uniform(-13, 0.6))
+        h = w * H / W
+        mode = int(rng.integers(0, 2))
+        if mode == JULIA:
+            c = complex(*rng.uniform(-1.2, 1.2, size=2))
+            z = julia_boundary_points(c, 1, seed=int(rng.integers(0, 1 << 30)), burn_in=200)[0]
+        else:
+            c = None
+            t = float(rng.uniform(0.0, 2.0 * math.pi))
+            e1 = complex(math.cos(t), math.sin(t))
+            z = e1 / 2 - e1 * e1 / 4 if rng.integers(0, 2) else -1 + e1 / 4
+        out.append(dict(c=c, rect=(z.real - w / 2, z.real + w / 2, z.imag - h / 2, z.imag + h / 2), W=W, H=H,
+                        max_iter=int(rng.choice([1, 3, 4, 5, 100, 1000, 3000])), mode=mode, precision=FP64))
+    return out
+
+
 # ---- generic maps (Sec. 2: other functions than Z^2 + C; Fig. 4) ----------
 # Map descriptions are plain data: {"kind": "power", "degree": d} or
 # {"kind": "rational", "num": [a_0 .. a_n], "den": [b_0 .. b_m]} with complex

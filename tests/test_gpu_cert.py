@@ -173,3 +173,25 @@ def test_batch_histograms_binary64(cuda):
         assert (b.hist(i).cpu().numpy() == oracle.hist(k, f["max_iter"])).all()
         assert (b.rgba(i).cpu().numpy() == oracle.colour(k, f["max_iter"], PAL)).all()
     assert (_np_counts(b.counts(1)) == _oracle(fr[1])).all()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_boundary_views_binary64(cuda, seed):
+    """Binary64 frames centred on Julia and Mandelbrot boundary points, widths
+    down to 1e-13 and limits up to 3000 (the certified passes' hardest tests),
+    as one plan with both passes and as single frames: bit-exact counts."""
+    import torch
+    fr = [dict(f, count_type="u16") for f in wl.boundary_views(60, seed=40 + seed)]
+    refs = [_oracle(f) for f in fr]
+    b = jl.Batch(fr, palette=PAL)
+    b.launch()
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    for i, (f, k) in enumerate(zip(fr, refs)):
+        g = _np_counts(b.counts(i))
+        assert (g == k).all(), "frame %d %s: %d mismatches" % (i, f, int((g != k).sum()))
+    for f, k in list(zip(fr, refs))[:12]:
+        out = jl.render(f["c"], f["rect"], f["W"], f["H"], f["max_iter"], precision=FP64, mode=f["mode"],
+                        count_type="u16", rgba=False, palette=PAL)
+        torch.cuda.synchronize()
+        assert (out["counts"].view(torch.int16).cpu().numpy().view(np.uint16) == k).all(), f
