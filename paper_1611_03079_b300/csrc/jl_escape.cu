@@ -23,9 +23,17 @@
 //        slot fell inside the band is replayed with exact binary64 tests.
 //    Pixels for which monotonicity is not proven (|C| within 2^-12 of 2) and
 //    tails shorter than U steps are iterated one exact step at a time.
-//  * Every arithmetic operation is an explicit round-to-nearest intrinsic
-//    (__fmul_rn, __fadd_rn, __dmul_rn, ...), which the compiler never
-//    contracts into an FMA; the library is also built with -fmad=false.
+//  * Binary64 frames first go through two certified passes (`cert_kernel`,
+//    `cert2_kernel`): a binary32, then a float-pair, orbit with a rigorous
+//    bound on its distance to the binary64 orbit decides each binary64 test
+//    it can; only the pixels with a test neither settles are iterated in
+//    binary64 (the lane-refill kernel over their list).  The counts are the
+//    binary64 counts either way.
+//  * Every arithmetic operation of an orbit whose counts are reported is an
+//    explicit round-to-nearest intrinsic (__fmul_rn, __fadd_rn, __dmul_rn,
+//    ...), which the compiler never contracts into an FMA; the library is
+//    also built with -fmad=false.  The certified passes' approximate orbits
+//    use FMA deliberately (their bound accounts for every rounding).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
