@@ -631,6 +631,11 @@ def main():
                                                 bytes=6 * px, unit_note="8 binary32 lane ops per iteration")
         elif ph[1] > 0:
             l32, l64, it_df, it64, st32, st_df = sp.cert_stats(stream)
+            by_prec[prec]["frac_note"] = (
+                "8 binary64 ops per iteration over the binary64 issue rate; above 1 because the certified "
+                "binary32 and double-float passes settle %.1f %% of these iterations on the binary32 pipe "
+                "(bit-exact binary64 counts); per-kernel fractions in roofline / roofline_other_kernels"
+                % (100.0 * (it - it64) / max(it, 1)))
             by_prec[prec].update({"cert_listed_binary32_pass": l32, "cert_listed_to_binary64": l64,
                                   "iterations_settled_double_float": it_df, "iterations_binary64": it64,
                                   "tests_binary32_pass": st32, "tests_double_float_pass": st_df})
