@@ -102,7 +102,15 @@ int jl_select_precision(jl_rect rect, int32_t width, int32_t height);
  *               uint32 bin storage during the call and holds the normalised
  *               histogram when the stream reaches the end of the call
  *   stream      cudaStream_t
- * At least one of counts, rgba, hist must be non-NULL.
+ * At least one of counts, rgba, hist must be non-NULL.  The call takes
+ * stream-ordered device scratch (cudaMallocAsync, freed in stream order):
+ * the coordinate tables, and for binary64 frames their float-pair roundings
+ * and the two lists of the certified passes (16 bytes per pixel): a binary32
+ * and then a float-pair orbit, each with a rigorous bound on its distance to
+ * the binary64 orbit, settle the pixels whose every binary64 escape test the
+ * bound decides; the rest are iterated in binary64.  The counts are the
+ * binary64 counts either way (jl_render_static allocates nothing and iterates
+ * every binary64 pixel in binary64).
  */
 int jl_render(double cr, double ci, jl_rect rect, int32_t width, int32_t height, int32_t max_iter,
               int32_t precision, int32_t mode, int32_t count_type, void *counts, uint8_t *rgba,
@@ -172,7 +180,9 @@ int jl_probe_peak(int32_t kind, int32_t iters, double *lane_ops_per_s, double *s
  * Arguments, outputs and results are those of jl_render (counts, rgba and
  * hist are caller-owned device buffers; palette is a host pointer or NULL),
  * and so is the kernel: the autotuned variant when jl_autotune has run or a
- * tuning table was loaded, else the default one.
+ * tuning table was loaded, else the default one.  Binary64 frames skip the
+ * certified passes (they need per-pixel lists): every pixel is iterated in
+ * binary64, with the same counts.
  * The scratch it needs (coordinate tables, work counter, status word) lives
  * in one file-scope device array of JL_STATIC_SCRATCH_BYTES bytes, which
  * every GPU that loads the library holds until the process exits.
