@@ -1581,6 +1581,7 @@ __global__ void __launch_bounds__(256, 4) cert_kernel(const __grid_constant__ Es
 // coordinates as float pairs, u (1 + 2^-20) Lambda_0 + 2^-140 (Julia), 0
 // (Mandelbrot: Z_0 = 0).
 // ---------------------------------------------------------------------------
+static constexpr int kDfBlock = 16;           // steps per block of the double-float pass
 static constexpr float kDfKL = 0x1.2p-19f;    // 36 u
 static constexpr float kDfMl = 0x1.dp-22f;    // 7.25 u: Mandelbrot KC per unit of |Cl|_1
 static constexpr float kDfMh = 0x1.9p-46f;    // 6.25 u^2: Mandelbrot KC per unit of |Ch|_1
@@ -1640,20 +1641,25 @@ __device__ __forceinline__ void df_update(DfState &w, float s, float lam, float 
     two_sum(sy, ly, w.yh, w.yl);
 }
 
-// Up to four tests of the double-float pass from test n (limit mi): the
+// Up to NB tests of the double-float pass from test n (limit mi): the
 // pixel's count (>= 0) when settled, -1 when a test is not settled, -2 when
-// the tests passed so far leave it live (n advanced).  Four steps always run
+// the tests passed so far leave it live (n advanced).  NB steps always run
 // (the state after a failed or an uncounted test is not used again); each
 // keeps its test's r, s and Et, so the first test that is not a certified
-// pass is classified from those without running the block again.
-__device__ __forceinline__ int df_run4(DfState &w, int &n, int mi, float crh, float crl, float cih, float cil, float kc)
+// pass is classified from those without running the block again.  The
+// pixels of this pass live for ~200 steps, so long blocks pay: per block a
+// round of refills, stores and list appends with few lanes active (sweep
+// pass 3.01 ms with blocks of 4, 2.64 with 8, 2.42 with 16, 2.39 with 24,
+// 2.72 with 32).
+template <int NB>
+__device__ __forceinline__ int df_run(DfState &w, int &n, int mi, float crh, float crl, float cih, float cil, float kc)
 {
     if (n >= mi)
         return mi;
-    float rk[4], sk[4], ek[4];
-    bool pk[4];
+    float rk[NB], sk[NB], ek[NB];
+    bool pk[NB];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NB; ++k) {
         const float lam = __fadd_ru(fabsf(w.xl), fabsf(w.yl));
         const float et = __fadd_ru(w.e, lam);
         const float r = __fmaf_rn(w.xh, w.xh, __fmul_rn(w.yh, w.yh));
@@ -1665,9 +1671,9 @@ __device__ __forceinline__ int df_run4(DfState &w, int &n, int mi, float crh, fl
         ek[k] = et;
         df_update(w, s, lam, crh, crl, cih, cil, kc);
     }
-    const int m = min(4, mi - n);
+    const int m = min(NB, mi - n);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NB; ++k) {
         if (k < m && !pk[k]) {
             if (cert_exit(rk[k], sk[k], ek[k]) == 0)
                 return n + k;
@@ -1777,7 +1783,7 @@ __global__ void __launch_bounds__(256) cert2_kernel(const __grid_constant__ Esca
             break;
         int res = -2;
         if (live)
-            res = df_run4(w, n, mi, crh, crl, cih, cil, kc);
+            res = df_run<kDfBlock>(w, n, mi, crh, crl, cih, cil, kc);
         const bool und = live && res == -1;
         if (live && res != -2)
             steps += res >= 0 ? (unsigned)(res < mi ? res + 1 : mi) : (unsigned)(n + 1);
