@@ -218,6 +218,24 @@ struct WorkT<double> {
     static __device__ __forceinline__ double ci(const Frame &F) { return F.ci; }
 };
 
+// One pixel's state in the binary64 kernel's end-of-launch packing area.
+struct TailSlot {
+    double x, y, cr, ci;
+    int32_t rem, fid, pix, pad;
+};
+
+// Dynamic shared memory of the lane-refill kernel: the palette, the
+// histogram of a single frame (hist_words, 0 for none), and for binary64 with
+// several slots per lane the warps' packing areas.
+static size_t refill_smem_bytes(bool dbl, int ppt, int threads, size_t hist_words)
+{
+    size_t words = ((256 + hist_words + 1) & ~(size_t)1);
+    size_t bytes = words * sizeof(uint32_t);
+    if (dbl && ppt > 1)
+        bytes += (size_t)(threads / 32) * (size_t)ppt * 32 * sizeof(TailSlot);
+    return bytes;
+}
+
 // LIST (binary64): the pixels are the entries of the certified pass's list
 // (a.cert_list, *a.cert_count of them) instead of the frames' row chunks.
 template <typename T, int PPT, int U, bool BATCH, bool LIST>
@@ -226,6 +244,10 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
     extern __shared__ uint32_t smem[];
     uint32_t *pal = smem;
     uint32_t *hbins = smem + 256;
+    // binary64 with several slots: each warp's area for packing its pixels at
+    // the end of the launch, after the palette and the histogram (8-aligned)
+    const int nb_words = (!BATCH && a.hist_smem) ? a.single.max_iter + 1 : 0;
+    TailSlot *tail_slots = reinterpret_cast<TailSlot *>(smem + ((256 + nb_words + 1) & ~1));
 
     const int lane = threadIdx.x & 31;
     const unsigned lane_bit = 1u << lane;
@@ -602,32 +624,57 @@ __global__ void __launch_bounds__(256) escape_kernel(const __grid_constant__ Esc
             };
             int nslot = PPT;
             if (PPT > 1 && q_done) {
-                // No pixels are left to take: each lane moves its pixels to its
-                // lowest slots, and slots that no lane uses are not computed (a
+                // No pixels are left to take: the warp's pixels are packed
+                // into its lowest slots across all lanes (through shared
+                // memory), and the slots no lane then uses are not computed (a
                 // binary64 warp instruction costs the narrow pipe the same
                 // whatever its lanes hold).
+                unsigned bal[PPT];
+                int base[PPT];
+                int tot = 0;
 #pragma unroll
-                for (int k = 1; k < PPT; ++k) {
+                for (int k = 0; k < PPT; ++k) {
+                    bal[k] = __ballot_sync(FULL, fid[k] >= 0);
+                    base[k] = tot;
+                    tot += __popc(bal[k]);
+                }
+                nslot = (tot + 31) >> 5;
+                if (nslot < PPT) {
+                    TailSlot *ts = tail_slots + (threadIdx.x >> 5) * (PPT * 32);
 #pragma unroll
-                    for (int j = 0; j < k; ++j) {
-                        if (fid[j] < 0 && fid[k] >= 0) {
-                            x[j] = x[k];
-                            y[j] = y[k];
-                            cr[j] = cr[k];
-                            ci[j] = ci[k];
-                            rem[j] = rem[k];
-                            fid[j] = fid[k];
-                            pix[j] = pix[k];
-                            fid[k] = -1;
-                            rem[k] = 0x3fffffff;
+                    for (int k = 0; k < PPT; ++k) {
+                        if (fid[k] >= 0) {
+                            TailSlot &d = ts[base[k] + __popc(bal[k] & lt_mask)];
+                            d.x = x[k];
+                            d.y = y[k];
+                            d.cr = cr[k];
+                            d.ci = ci[k];
+                            d.rem = rem[k];
+                            d.fid = fid[k];
+                            d.pix = pix[k];
                         }
                     }
-                }
-                int used = 0;
+                    __syncwarp();
 #pragma unroll
-                for (int k = 0; k < PPT; ++k)
-                    used += fid[k] >= 0 ? 1 : 0;
-                nslot = (int)__reduce_max_sync(FULL, (unsigned)used);
+                    for (int k = 0; k < PPT; ++k) {
+                        const int g = k * 32 + lane;
+                        if (g < tot) {
+                            const TailSlot &d = ts[g];
+                            x[k] = d.x;
+                            y[k] = d.y;
+                            cr[k] = d.cr;
+                            ci[k] = d.ci;
+                            rem[k] = d.rem;
+                            fid[k] = d.fid;
+                            pix[k] = d.pix;
+                        } else {
+                            x[k] = y[k] = cr[k] = ci[k] = T(0);
+                            rem[k] = 0x3fffffff;
+                            fid[k] = -1;
+                        }
+                    }
+                    __syncwarp();
+                }
             }
             if (nslot == PPT)
                 block64(std::integral_constant<bool, false>(), PPT);
@@ -2174,9 +2221,8 @@ cudaError_t launch_escape(const EscapeArgs &a_in, int precision, const Variant &
             b.cert_list = a.cert_list2;
             b.cert_count = a.cert_count2;
         }
-        size_t smem = 256 * sizeof(uint32_t);
-        if (b.hist_smem && !b.frames)
-            smem += (size_t)(b.single.max_iter + 1) * sizeof(uint32_t);
+        const size_t smem = refill_smem_bytes(true, v.ppt, v.threads,
+                                              (b.hist_smem && !b.frames) ? (size_t)b.single.max_iter + 1 : 0);
 #define JL_DISPATCH_LIST(T, P, UU)                                                            \
         if (sizeof(T) == 8 && v.ppt == P && v.unroll == UU)                                   \
             return launch_one<T, P, UU, true>(b, v, num_sms, smem, st);
@@ -2188,9 +2234,8 @@ cudaError_t launch_escape(const EscapeArgs &a_in, int precision, const Variant &
         return launch_compact(a, v.unroll, st);
     if (v.ppt == 0)
         return precision == JL_FP64 ? launch_static<double>(a, st) : launch_static<float>(a, st);
-    size_t smem = 256 * sizeof(uint32_t);
-    if (a.hist_smem && !a.frames)
-        smem += (size_t)(a.single.max_iter + 1) * sizeof(uint32_t);
+    const size_t smem = refill_smem_bytes(precision == JL_FP64, v.ppt, v.threads,
+                                          (a.hist_smem && !a.frames) ? (size_t)a.single.max_iter + 1 : 0);
 #define JL_DISPATCH(T, P, UU)                                                                 \
     if (((sizeof(T) == 8) == (precision == JL_FP64)) && v.ppt == P && v.unroll == UU)         \
         return launch_one<T, P, UU>(a, v, num_sms, smem, st);
