@@ -673,8 +673,8 @@ def main():
     d = kern[dom_k]
     # DRAM bytes (read + write) per launch of each kernel, from one ncu capture
     # of the same plan launch (profiles/escape_kernel_sweep4096.md)
-    traffic = {"cert_kernel": 70792960 + 808565248, "cert2_kernel": 80958464 + 51610624,
-               "escape_kernel<double> (list)": 7665408 + 4656384,
+    traffic = {"cert_kernel": 68235264 + 789473792, "cert2_kernel": 82094592 + 147096832,
+               "escape_kernel<double> (list)": 7837952 + 4592640,
                "escape_compact_kernel": 30964992 + 780568320} if args.size == 4096 else {}
     roofline = {"bound": "alu", "kernel": dom_k, "precision": d["prec"],
                 "achieved": d["achieved"], "peak": d["peak"] / 1e9, "unit": "Gop/s", "frac": d["frac"],
