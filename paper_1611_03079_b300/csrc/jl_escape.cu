@@ -1442,7 +1442,20 @@ __device__ __forceinline__ int cert_exit(float r, float s, float e)
 // and E > 0 after step 0 (E_0 = 0 only with W_0 = 0), so the first U that is
 // not finite is +inf, which the maximum keeps); a block with a test that is
 // not a certified pass is replayed one test at a time from its start.
-template <int CB>
+//
+// MONO: only the block's last U is formed.  With B_n = |W_n| + E_n, the
+// update of E adds at least E (2|W| + E) and the bound on the binary32 step's
+// rounding, so B_{n+1} >= B_n^2 - |C32| for the computed values, whatever Z
+// does.  If the first binary64 test to fail is test m, E_m still bounds
+// |Z_m - W_m| (the tests before m passed), so B_m >= |Z_m| > 2 - 2^-50:
+// with |C32| <= 2 - 2^-12, B_{m+1} > 2 + 2^-13 and B stays above 2, so every
+// later U >= B^2 > 4, and U_m >= 4 by the test's own certificate.  Hence a
+// last U < 4 certifies every test of the block.  For Mandelbrot pixels with
+// |C32| >= 2 (W_0 = 0, W_1 = C32), B_n >= |C32| for all n >= 1, so the first
+// block's last U > 4 and its replay finds the escape at test 1.  The omitted
+// 2 |W| E of a flushed subnormal r (below 2^-61 B) leaves B_{n+1} > 2 here.
+// A NaN or infinite last U fails the compare and replays the block.
+template <int CB, bool MONO>
 __device__ __forceinline__ int cert_count(float x, float y, float e, float cr, float ci, float ec, int mi)
 {
     int n = 0;
@@ -1455,7 +1468,10 @@ __device__ __forceinline__ int cert_count(float x, float y, float e, float cr, f
             const float r = __fmaf_rn(x, x, y2);
             const float s = sqrt_approx(r);
             const float ge = __fmaf_ru(e, __fmaf_ru(kCertS2, s, e), ec);
-            umax = fmaxf(umax, __fmaf_ru(r, kCertR1, ge));
+            if (!MONO)
+                umax = fmaxf(umax, __fmaf_ru(r, kCertR1, ge));
+            else if (u == CB - 1)
+                umax = __fmaf_ru(r, kCertR1, ge);
             const float nx = __fmaf_rn(x, x, __fmaf_rn(-y, y, cr));
             y = __fmaf_rn(__fadd_rn(x, x), y, ci);
             x = nx;
@@ -1555,10 +1571,16 @@ __global__ void __launch_bounds__(256, 4) cert_kernel(const __grid_constant__ Es
             if (valid) {
                 const float yv = ys32[j];
                 const float ax = fabsf(xv), ay = fabsf(yv);
-                if (julia)
-                    count = cert_count<4>(xv, yv, __fmaf_ru(kCertE0, __fadd_ru(ax, ay), 0x1p-140f), fcr, fci, fec, mi);
-                else
-                    count = cert_count<4>(0.f, 0.f, 0.f, xv, yv, __fmaf_ru(kCertMC, __fadd_ru(ax, ay), 0x1p-47f), mi);
+                if (julia) {
+                    const float e0 = __fmaf_ru(kCertE0, __fadd_ru(ax, ay), 0x1p-140f);
+                    count = F.safe ? cert_count<6, true>(xv, yv, e0, fcr, fci, fec, mi)
+                                   : cert_count<4, false>(xv, yv, e0, fcr, fci, fec, mi);
+                } else {
+                    // (a pixel outside the band |C|^2 in (3.99, 4.01) has |C32| <= 2 - 2^-12 or >= 2)
+                    const float ec = __fmaf_ru(kCertMC, __fadd_ru(ax, ay), 0x1p-47f);
+                    count = !in_unsafe_band(xv, yv) ? cert_count<6, true>(0.f, 0.f, 0.f, xv, yv, ec, mi)
+                                                    : cert_count<4, false>(0.f, 0.f, 0.f, xv, yv, ec, mi);
+                }
             }
             const bool undecided = valid && count < 0;
             // tests decided (for the launch's step counter)
