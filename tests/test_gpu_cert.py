@@ -27,10 +27,15 @@ def _frames():
         if f["precision"] == FP64:
             fr.append(dict(f, count_type="u16"))
     sq = (-2.2, 2.2, -2.2, 2.2)
+    # |C|^2 = 4, > 4, ~4, 3.998 (per-step tests), 0, 0.5625, and 3.980 / 3.9896 (just inside the
+    # |C32| <= 2 - 2^-12 range where a block forms only its last test)
     for c in (complex(-2.0, 0.0), complex(2.5, 0.1), complex(-1.9999, 0.0), complex(1.414, 1.414),
-              complex(0.0, 0.0), complex(-0.75, 0.0)):
+              complex(0.0, 0.0), complex(-0.75, 0.0), complex(-1.995, 0.0), complex(0.0, 1.9974)):
         fr.append(dict(c=c, rect=sq, W=64, H=61, max_iter=300, mode=wl.JULIA, precision=FP64, count_type="u16"))
     fr.append(dict(c=None, rect=(-2.05, -1.95, -0.05, 0.05), W=97, H=61, max_iter=500, mode=wl.MANDELBROT,
+                   precision=FP64, count_type="u16"))
+    # Mandelbrot pixels on both edges of the band |C|^2 in (3.99, 4.01)
+    fr.append(dict(c=None, rect=(-0.01, 0.01, 1.994, 2.004), W=37, H=101, max_iter=800, mode=wl.MANDELBROT,
                    precision=FP64, count_type="u16"))
     c = complex(-0.7269, 0.1889)
     for k, z in enumerate(wl.julia_boundary_points(c, 3, seed=5)):
