@@ -202,12 +202,13 @@ def test_throughput_sweep_full_size_sampled(cuda, sweep_batch, idx):
 def test_throughput_sweep_bench_outputs(cuda, sweep_batch):
     """The sweep as bench.py renders it (uint16 counts and RGBA8, no
     histograms, so the tile kernels take their store path without per-frame
-    tests) gives the same bytes as the plan above, whose counts are checked
-    against the oracle."""
+    tests; a tuned plan, which times its candidate kernels on these frames
+    and keeps the fastest) gives the same bytes as the plan above, whose
+    counts are checked against the oracle."""
     import torch
     frames, b = sweep_batch
     bf = [dict(f, hist=False) for f in frames]
-    b2 = jl.Batch(bf, palette=PAL)
+    b2 = jl.Batch(bf, palette=PAL, tune=True)
     b2.launch()
     torch.cuda.synchronize()
     for i in range(len(frames)):
