@@ -252,11 +252,17 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy(frame table)"); break; }
             // Work tables, both kinds (a tuned plan may try either).  Lane-refill
             // kernel: chunk -> frame, in frame order.  Tile kernels: 32x32 tiles
-            // with the frames interleaved (round-robin over the frames that still
-            // have tiles), then each tile's index within its frame, so that warps
-            // claiming work meet cheap and costly frames alike rather than one
-            // frame's far field at a time (cheap tiles claimed in a burst make
-            // the launch counter the bottleneck).
+            // of the frames with the highest limit first, each limit's frames
+            // interleaved (round-robin over the frames that still have tiles),
+            // then each tile's index within its frame.  Warps claiming work
+            // meet the far field and the costly regions of several frames alike
+            // rather than one frame's far field at a time (cheap tiles claimed in
+            // a burst make the launch counter the bottleneck), and the launch
+            // ends on cheap tiles rather than on a few long ones; the certified
+            // pass's list, appended in this order, then starts with the
+            // long-lived pixels, so the double-float pass ends on short ones
+            // (sweep step 9.51 -> 9.35 ms against one round-robin over all
+            // frames; the double-float pass 2.32 -> 2.23 ms).
             {
                 std::vector<int32_t> cf((size_t)b->chunks[g]);
                 for (size_t f = 0; f < host[g].size(); ++f) {
@@ -272,17 +278,25 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             if (b->tiles[g] <= 0x7fffffffll) {
                 const size_t T = (size_t)b->tiles[g];
                 std::vector<int32_t> tf(2 * T);
-                int32_t most = 0;
+                std::vector<int32_t> lims;
                 for (const Frame &F : host[g])
-                    most = std::max(most, F.tile_count);
+                    lims.push_back(F.max_iter);
+                std::sort(lims.begin(), lims.end());
+                lims.erase(std::unique(lims.begin(), lims.end()), lims.end());
                 size_t pos = 0;
-                for (int32_t k = 0; k < most; ++k)
-                    for (size_t f = 0; f < host[g].size(); ++f)
-                        if (k < host[g][f].tile_count) {
-                            tf[pos] = (int32_t)f;
-                            tf[T + pos] = k;
-                            ++pos;
-                        }
+                for (auto li = lims.rbegin(); li != lims.rend(); ++li) {
+                    int32_t most = 0;
+                    for (const Frame &F : host[g])
+                        if (F.max_iter == *li)
+                            most = std::max(most, F.tile_count);
+                    for (int32_t k = 0; k < most; ++k)
+                        for (size_t f = 0; f < host[g].size(); ++f)
+                            if (host[g][f].max_iter == *li && k < host[g][f].tile_count) {
+                                tf[pos] = (int32_t)f;
+                                tf[T + pos] = k;
+                                ++pos;
+                            }
+                }
                 e = cudaMalloc(&b->tile_dev[g], std::max<size_t>(tf.size(), 1) * sizeof(int32_t));
                 if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(tile table)"); break; }
                 e = cudaMemcpy(b->tile_dev[g], tf.data(), tf.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
