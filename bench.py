@@ -674,8 +674,8 @@ def main():
     d = kern[dom_k]
     # DRAM bytes (read + write) per launch of each kernel, from one ncu capture
     # of the same plan launch (profiles/escape_kernel_sweep4096.md)
-    traffic = {"cert_kernel": 67366912 + 788390912, "cert2_kernel": 82716928 + 147190272,
-               "escape_kernel<double> (list)": 7601408 + 4598528,
+    traffic = {"cert_kernel": 65916160 + 786704384, "cert2_kernel": 82806784 + 149423360,
+               "escape_kernel<double> (list)": 7740672 + 4626432,
                "escape_compact_kernel": 30964992 + 780568320} if args.size == 4096 else {}
     roofline = {"bound": "alu", "kernel": dom_k, "precision": d["prec"],
                 "achieved": d["achieved"], "peak": d["peak"] / 1e9, "unit": "Gop/s", "frac": d["frac"],
