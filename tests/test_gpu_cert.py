@@ -180,7 +180,7 @@ def test_batch_histograms_binary64(cuda):
     assert (_np_counts(b.counts(1)) == _oracle(fr[1])).all()
 
 
-@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("seed", range(10))
 def test_boundary_views_binary64(cuda, seed):
     """Binary64 frames centred on Julia and Mandelbrot boundary points, widths
     down to 1e-13 and limits up to 3000 (the certified passes' hardest tests),
