@@ -278,24 +278,37 @@ int jl_batch_create(const jl_frame *frames, int32_t n, void *counts_base, uint8_
             if (b->tiles[g] <= 0x7fffffffll) {
                 const size_t T = (size_t)b->tiles[g];
                 std::vector<int32_t> tf(2 * T);
-                std::vector<int32_t> lims;
-                for (const Frame &F : host[g])
-                    lims.push_back(F.max_iter);
-                std::sort(lims.begin(), lims.end());
-                lims.erase(std::unique(lims.begin(), lims.end()), lims.end());
+                // frame indices by limit, highest first (stable: input order within a limit)
+                std::vector<int32_t> by_lim(host[g].size());
+                for (size_t f = 0; f < by_lim.size(); ++f)
+                    by_lim[f] = (int32_t)f;
+                std::stable_sort(by_lim.begin(), by_lim.end(), [&](int32_t u, int32_t v) {
+                    return host[g][u].max_iter > host[g][v].max_iter;
+                });
                 size_t pos = 0;
-                for (auto li = lims.rbegin(); li != lims.rend(); ++li) {
+                for (size_t g0 = 0; g0 < by_lim.size();) {
+                    size_t g1 = g0;
                     int32_t most = 0;
-                    for (const Frame &F : host[g])
-                        if (F.max_iter == *li)
-                            most = std::max(most, F.tile_count);
-                    for (int32_t k = 0; k < most; ++k)
-                        for (size_t f = 0; f < host[g].size(); ++f)
-                            if (host[g][f].max_iter == *li && k < host[g][f].tile_count) {
-                                tf[pos] = (int32_t)f;
-                                tf[T + pos] = k;
-                                ++pos;
-                            }
+                    while (g1 < by_lim.size() && host[g][by_lim[g1]].max_iter == host[g][by_lim[g0]].max_iter) {
+                        most = std::max(most, host[g][by_lim[g1]].tile_count);
+                        ++g1;
+                    }
+                    // round-robin over this limit's frames; frames that run out of
+                    // tiles drop out of the rotation
+                    std::vector<int32_t> act(by_lim.begin() + (long)g0, by_lim.begin() + (long)g1);
+                    for (int32_t k = 0; k < most && !act.empty(); ++k) {
+                        size_t keep = 0;
+                        for (size_t q = 0; q < act.size(); ++q) {
+                            const int32_t f = act[q];
+                            tf[pos] = f;
+                            tf[T + pos] = k;
+                            ++pos;
+                            if (k + 1 < host[g][f].tile_count)
+                                act[keep++] = f;
+                        }
+                        act.resize(keep);
+                    }
+                    g0 = g1;
                 }
                 e = cudaMalloc(&b->tile_dev[g], std::max<size_t>(tf.size(), 1) * sizeof(int32_t));
                 if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc(tile table)"); break; }
