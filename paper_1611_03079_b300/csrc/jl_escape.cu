@@ -1435,13 +1435,11 @@ __device__ __forceinline__ int cert_exit(float r, float s, float e)
     return __fmaf_rd(r, kCertR0, -m) > 4.0f ? 0 : -1;
 }
 
-// Binary64 count of a pixel from the certified pass (tests n = 0 .. mi-1 from
-// W_0 = (x, y), E_0 = e), or -1 - n when test n is not settled.  Blocks of
-// CB steps with one branch: the largest U of a block is compared with 4 (a
-// NaN U cannot come first: with finite inputs r, s and g are finite or +inf
-// and E > 0 after step 0 (E_0 = 0 only with W_0 = 0), so the first U that is
-// not finite is +inf, which the maximum keeps); a block with a test that is
-// not a certified pass is replayed one test at a time from its start.
+// One block of CB certified steps; false (state restored to the block's
+// start) when its test is not a certified pass.  The largest U of the block is
+// compared with 4 (a NaN U cannot come first: with finite inputs r, s and g
+// are finite or +inf and E > 0 after step 0 (E_0 = 0 only with W_0 = 0), so the
+// first U that is not finite is +inf, which the maximum keeps).
 //
 // MONO: only the block's last U is formed.  With B_n = |W_n| + E_n, the
 // update of E adds at least E (2|W| + E) and the bound on the binary32 step's
@@ -1455,8 +1453,6 @@ __device__ __forceinline__ int cert_exit(float r, float s, float e)
 // block's last U > 4 and its replay finds the escape at test 1.  The omitted
 // 2 |W| E of a flushed subnormal r (below 2^-61 B) leaves B_{n+1} > 2 here.
 // A NaN or infinite last U fails the compare and replays the block.
-// One block of CB certified steps; false (state restored to the block's
-// start) when its test is not a certified pass.
 template <int CB, bool MONO>
 __device__ __forceinline__ bool cert_block(float &x, float &y, float &e, float cr, float ci, float ec)
 {
@@ -1485,10 +1481,13 @@ __device__ __forceinline__ bool cert_block(float &x, float &y, float &e, float c
     return false;
 }
 
-// CB0: length of the first block (shorter blocks waste fewer steps on the
-// many pixels that escape within the first few tests), then blocks of CB
-// (sweep pass 2.54 ms with blocks of 6 throughout, 2.52 with a first block
-// of 2, 2.51 with 3).
+// Binary64 count of a pixel from the certified pass (tests n = 0 .. mi-1 from
+// W_0 = (x, y), E_0 = e), or -1 - n when test n is not settled.  A first block
+// of CB0 steps (shorter blocks waste fewer steps on the many pixels that
+// escape within the first few tests), then blocks of CB (sweep pass 2.54 ms
+// with blocks of 6 throughout, 2.52 with a first block of 2, 2.51 with 3); the
+// block whose test is not a certified pass, and the tests after the last full
+// block, run one test at a time.
 template <int CB0, int CB, bool MONO>
 __device__ __forceinline__ int cert_count(float x, float y, float e, float cr, float ci, float ec, int mi)
 {
